@@ -1,0 +1,404 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test pins the oracle to something other than itself: printed values of a
+worked example, closed forms, exact-arithmetic theorems, brute force on tiny
+inputs, textbook special cases and finite differences.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import adjoint, dynamics, elk, newton
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _small_massaction(B=3, d=4, R=6, seed=0, integrator="rk4", dt=1e-2):
+    p = synth.massaction(B, d, R, T=1, seed=seed, dt=dt, integrator=integrator)
+    return dynamics.MassAction(p["topology"], p["params"], dt, integrator, d=d), p
+
+
+def _small_gru(B=2, T=12, d=4, seed=0):
+    p = synth.gru(B, T, d, d, seed)
+    return dynamics.GRU(p["W"], p["U"], p["x"]), p
+
+
+def _fd_jac(f, s, h=1e-6):
+    B, d = s.shape
+    J = np.empty((B, d, d))
+    for j in range(d):
+        e = np.zeros(d)
+        e[j] = h
+        J[:, :, j] = (f(s + e) - f(s - e)) / (2 * h)
+    return J
+
+
+# --- worked example (Appendix A) ----------------------------------------------
+
+def test_worked_example_tang():
+    g = json.load(open(os.path.join(GOLDEN, "tang_example.json")))
+    dyn = dynamics.Linear(np.array([[2.0]]))
+    s0 = np.array([[g["s0"]]])
+    T = g["T"]
+    s_star = newton.rollout(dyn, s0, T)[0, :, 0]
+    assert np.array_equal(s_star, g["s_star"])
+    s = np.array(g["s_init"]).reshape(1, T, 1)
+    r = newton.residual(dyn, s0, s)[0, :, 0]
+    assert np.array_equal(r, g["r_init"])
+    # the update s - G r with the non-lower-triangular G of the counterexample
+    G = np.array(g["G_not_lower_triangular"])
+    cur = np.array(g["s_init"])
+    for expect in g["update_iterates"]:
+        rr = newton.residual(dyn, s0, cur.reshape(1, T, 1))[0, :, 0]
+        cur = cur - G @ rr
+        assert np.array_equal(cur, expect)
+    # DEER (G = J^{-1}) from the same start reaches s* in one iteration
+    one = newton.quasi_newton_step(dyn, s0, s, "full")[0, :, 0]
+    assert np.array_equal(one, g["s_star"])
+    out = newton.solve(dyn, s0, T, "full", tol=0.0, init="user", user=s)
+    assert out["iters"][0] == 1 and out["converged"][0]
+
+
+# --- dynamics pinned by closed forms / invariants / finite differences ------------
+
+def test_brusselator_stationary_point_and_textbook_jacobian():
+    a, b = 1.0, 3.0
+    dyn = dynamics.Brusselator(np.array([[a, b]]), 0.01)
+    fp = np.array([[a, b / a]])
+    assert np.allclose(dyn.rhs(fp), 0.0, atol=1e-15)
+    # textbook linearisation of the Brusselator at (a, b/a): [[b-1, a^2], [-b, -a^2]]
+    assert np.allclose(dyn.rhs_jac(fp)[0], [[b - 1, a * a], [-b, -a * a]], atol=1e-14)
+    s = np.array([[0.7, 2.1]])
+    assert np.allclose(dyn.jac(1, s), _fd_jac(lambda v: dyn.f(1, v), s), rtol=1e-8, atol=1e-10)
+    # explicit Euler: f(s) = s + dt g(s)
+    assert np.allclose(dyn.f(1, s), s + 0.01 * dyn.rhs(s), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("integrator", ["euler", "rk4"])
+def test_massaction_conservation_and_jacobian_fd(integrator):
+    dyn, p = _small_massaction(B=4, d=6, R=9, seed=3, integrator=integrator)
+    rng = np.random.default_rng(0)
+    c = rng.uniform(0.1, 1.0, size=(4, 6))
+    m = p["masses"].astype(np.float64)
+    # every reaction conserves sum_i m_i c_i
+    assert np.allclose(np.sum(m * dyn.rhs(c), axis=1), 0.0, atol=1e-12)
+    assert np.allclose(np.sum(m * dyn.f(1, c), axis=1), np.sum(m * c, axis=1), atol=1e-12)
+    assert np.allclose(dyn.rhs_jac(c), _fd_jac(dyn.rhs, c), rtol=1e-7, atol=1e-9)
+    assert np.allclose(dyn.jac(1, c), _fd_jac(lambda v: dyn.f(1, v), c), rtol=1e-7, atol=1e-9)
+    # d f / d k by central differences on each rate constant
+    P = dyn.dparams(1, c)
+    for r in range(p["R"]):
+        kp = p["params"].copy(); kp[:, r] += 1e-6
+        km = p["params"].copy(); km[:, r] -= 1e-6
+        fp_ = dynamics.MassAction(p["topology"], kp, dyn.dt, integrator, d=6).f(1, c)
+        fm_ = dynamics.MassAction(p["topology"], km, dyn.dt, integrator, d=6).f(1, c)
+        assert np.allclose(P[:, :, r], (fp_ - fm_) / 2e-6, rtol=1e-6, atol=1e-10)
+
+
+def test_rk4_is_quartic_taylor_on_linear_network():
+    """On a conversion-only network g(c) = M c, so one classical RK4 step equals
+    the degree-4 Taylor polynomial of exp(hM) applied to s; its error against the
+    exact flow shrinks ~2^5 per halving of h (local order 5)."""
+    from scipy.linalg import expm
+    net = synth.linear_conversion_network(d=5, R=8, seed=1)
+    d = 5
+    for h in (0.05, 0.1):
+        dyn = dynamics.MassAction(net["topology"], net["params"], h, "rk4", d=d)
+        M = np.stack([dyn.rhs(np.eye(d)[j][None])[0] for j in range(d)], axis=1)  # columns g(e_j)
+        hM = h * M
+        P4 = np.eye(d) + hM + hM @ hM / 2 + hM @ hM @ hM / 6 + hM @ hM @ hM @ hM / 24
+        s = net["s0"]
+        assert np.allclose(dyn.f(1, s)[0], P4 @ s[0], rtol=1e-13, atol=1e-15)
+    errs = []
+    for h in (0.2, 0.1):
+        dyn = dynamics.MassAction(net["topology"], net["params"], h, "rk4", d=d)
+        M = np.stack([dyn.rhs(np.eye(d)[j][None])[0] for j in range(d)], axis=1)
+        errs.append(np.linalg.norm(dyn.f(1, net["s0"])[0] - expm(h * M) @ net["s0"][0]))
+    ratio = errs[0] / errs[1]
+    assert 20 < ratio < 45
+
+
+def test_gru_special_cases_and_jacobian():
+    d = 4
+    rng = np.random.default_rng(5)
+    h = rng.uniform(-0.9, 0.9, size=(1, d))
+    x = rng.standard_normal((1, 1, d))
+    zero = np.zeros((3, d, d))
+    # W = U = 0: z = r = 1/2, h~ = 0, so h' = h / 2
+    g0 = dynamics.GRU(zero, zero, x)
+    assert np.allclose(g0.f(1, h), 0.5 * h, atol=1e-15)
+    # update gate saturated open (W_z x = +50) and U = 0: h' = tanh(W_h x)
+    W = np.zeros((3, d, d))
+    W[0] = np.eye(d) * (50.0 / x[0, 0])[:, None]
+    W[2] = rng.standard_normal((d, d))
+    g1 = dynamics.GRU(W, zero, x)
+    assert np.allclose(g1.f(1, h), np.tanh(W[2] @ x[0, 0]), atol=1e-12)
+    # update gate saturated closed (W_z x = -50): h' = h
+    W[0] = -W[0]
+    g2 = dynamics.GRU(W, zero, x)
+    assert np.allclose(g2.f(1, h), h, atol=1e-12)
+    dyn, _ = _small_gru(B=3, T=2, d=5, seed=2)
+    s = np.random.default_rng(1).uniform(-0.8, 0.8, size=(3, 5))
+    assert np.allclose(dyn.jac(1, s), _fd_jac(lambda v: dyn.f(1, v), s), rtol=1e-7, atol=1e-9)
+
+
+# --- Prop. global_convergence (exact-arithmetic, bitwise in correction form) -------
+
+class _RandomTransition:
+    """Wraps a dynamics object but reports an arbitrary (random) matrix as its Jacobian,
+    so that mode='full' runs Eq. gen_qdeer with arbitrary A~_t."""
+
+    def __init__(self, dyn, seed):
+        self.dyn, self.d, self.rng = dyn, dyn.d, np.random.default_rng(seed)
+        self.n_params = 0
+
+    def f(self, t, s):
+        return self.dyn.f(t, s)
+
+    def jac(self, t, s):
+        return 0.3 * self.rng.standard_normal((s.shape[0], self.d, self.d))
+
+
+@pytest.mark.parametrize("mode", ["full", "diag", "identity", "zero", "random"])
+def test_prefix_exactness_and_T_iterations(mode):
+    dyn, p = _small_massaction(B=2, d=4, R=6, seed=7)
+    T = 24
+    s0 = p["s0"]
+    if mode == "random":
+        dyn, mode = _RandomTransition(dyn, 11), "full"
+    s_star = newton.rollout(dyn, s0, T)
+    s = newton.initial_guess(dyn, s0, T, "zeros")
+    for i in range(1, T + 1):
+        s = newton.quasi_newton_step(dyn, s0, s, mode)
+        # after iteration i the first i states are exactly the rollout
+        assert np.array_equal(s[:, :i], s_star[:, :i])
+    assert np.array_equal(s, s_star)
+    out = newton.solve(dyn, s0, T, mode, tol=0.0, init="zeros")
+    assert np.all(out["converged"]) and np.all(out["iters"] <= T)
+
+
+def test_linear_recurrence_converges_in_one_iteration():
+    lds = synth.linear_lds(B=3, T=40, d=5, seed=2)
+    dyn = dynamics.Linear(lds["A"], lds["x"])
+    out = newton.solve(dyn, lds["s0"], 40, "full", tol=1e-11, init="zeros")
+    assert np.all(out["iters"] == 1)
+    assert np.allclose(out["s"], newton.rollout(dyn, lds["s0"], 40), rtol=1e-12, atol=1e-12)
+    # diagonal linear dynamics: quasi-DEER is exact, also one iteration
+    ldd = synth.linear_lds(B=2, T=40, d=4, seed=3, diagonal=True)
+    dd = dynamics.Linear(ldd["A"], ldd["x"])
+    assert np.all(newton.solve(dd, ldd["s0"], 40, "diag", tol=1e-11, init="zeros")["iters"] == 1)
+    # a permutation LDS (group word problem, Sec. 6.4): one Newton iteration
+    perm = np.eye(5)[np.random.default_rng(0).permutation(5)]
+    dp = dynamics.Linear(perm, lds["x"][:, :, :5])
+    assert np.all(newton.solve(dp, lds["s0"], 40, "full", tol=1e-11, init="zeros")["iters"] == 1)
+
+
+@pytest.mark.parametrize("which", ["massaction", "gru", "brusselator"])
+@pytest.mark.parametrize("mode", ["full", "diag"])
+def test_forward_substitution_equals_dense_lu(which, mode):
+    """One (quasi-)Newton update by forward substitution equals s - J~^{-1} r with the
+    block-bidiagonal J~ of Eq. big_j built explicitly and LU-solved (T d <= 256)."""
+    if which == "massaction":
+        dyn, p = _small_massaction(B=1, d=4, R=6, seed=1)
+        s0, T = p["s0"], 40
+    elif which == "gru":
+        dyn, p = _small_gru(B=1, T=32, d=6, seed=4)
+        s0, T = p["s0"], 32
+    else:
+        pb = synth.brusselator(T=64)
+        dyn, s0, T = dynamics.Brusselator(pb["params"], pb["dt"]), pb["s0"], 64
+    s = newton.initial_guess(dyn, s0, T, "zeros") + 0.3 * np.random.default_rng(0).standard_normal((1, T, dyn.d))
+    a = newton.quasi_newton_step(dyn, s0, s, mode)[0]
+    b = newton.dense_newton_step(dyn, s0[0], s[0], mode)
+    assert np.allclose(a, b, rtol=1e-11, atol=1e-12)
+
+
+def test_J_inverse_blocks_are_products():
+    """Eq. J_inv: block (t, tau) of J^{-1} is A_t A_{t-1} ... A_{tau+1}."""
+    dyn, p = _small_massaction(B=1, d=3, R=5, seed=2)
+    T, d = 4, 3
+    s = np.random.default_rng(1).uniform(0, 1, size=(T, d))
+    Jinv = np.linalg.inv(newton.dense_jacobian(dyn, p["s0"][0], s))
+    A = [None] + [dyn.jac(t, s[None, t - 2])[0] for t in range(2, T + 1)]
+    for t in range(1, T + 1):
+        for tau in range(1, t + 1):
+            blk = Jinv[(t - 1) * d:t * d, (tau - 1) * d:tau * d]
+            prod = np.eye(d)
+            for k in range(tau + 1, t + 1):
+                prod = A[k - 1] @ prod
+            assert np.allclose(blk, prod, atol=1e-13)
+    for t in range(1, T + 1):
+        for tau in range(t + 1, T + 1):
+            assert np.all(Jinv[(t - 1) * d:t * d, (tau - 1) * d:tau * d] == 0)
+
+
+def test_jacobi_error_closed_form_and_slope():
+    """s_{t+1} = alpha s_t, Jacobi from zeros: e_t^{(i)} = 0 for t <= i and -alpha^t s_0
+    otherwise, so log10 ||e^{(i)}|| falls with slope log10(alpha) (Sec. 6.3)."""
+    alpha, T = 0.5, 60
+    dyn = dynamics.Linear(np.eye(2) * alpha)
+    s0 = np.array([[1.0, -2.0]])
+    s_star = newton.rollout(dyn, s0, T)
+    s = np.zeros((1, T, 2))
+    norms = []
+    for i in range(1, 30):
+        s = newton.quasi_newton_step(dyn, s0, s, "zero")
+        e = s - s_star
+        t = np.arange(1, T + 1)
+        expect = np.where((t <= i)[:, None], 0.0, -(alpha ** t)[:, None] * s0[0][None])
+        assert np.allclose(e[0], expect, rtol=1e-14, atol=0)
+        norms.append(np.linalg.norm(e))
+    slope = np.polyfit(np.arange(1, 30), np.log10(norms), 1)[0]
+    assert abs(slope - math.log10(alpha)) < 1e-6
+
+
+@pytest.mark.parametrize("T", [3, 5, 10, 33])
+def test_picard_inverse_norm_closed_form(T):
+    """Lemma PicardNorm: ||J~_P^{-1}||_2 = 1 / (2 sin(pi / (2 (2T + 1))))."""
+    dyn = dynamics.Linear(np.eye(2) * 0.3)
+    J = newton.dense_jacobian(dyn, np.zeros(2), np.zeros((T, 2)), mode="identity")
+    got = np.linalg.norm(np.linalg.inv(J), 2)
+    assert abs(got - 1.0 / (2.0 * math.sin(math.pi / (2 * (2 * T + 1))))) < 1e-10 * got
+
+
+def test_picard_is_prefix_sum_of_euler_increments():
+    """Prop. picard on an Euler ODE: s_{t+1}^{(i+1)} = s_0 + sum_{tau<=t} g(s_tau^{(i)}) dt."""
+    pb = synth.brusselator(T=50)
+    dyn = dynamics.Brusselator(pb["params"], pb["dt"])
+    s0 = pb["s0"]
+    s = 1.0 + 0.1 * np.random.default_rng(2).standard_normal((1, 50, 2))
+    got = newton.quasi_newton_step(dyn, s0, s, "identity")[0]
+    prev = np.concatenate([s0, s[0, :-1]], axis=0)
+    incr = pb["dt"] * dyn.rhs(prev)
+    expect = s0[0] + np.cumsum(incr, axis=0)
+    assert np.allclose(got, expect, rtol=1e-13, atol=1e-13)
+
+
+# --- fixed point, rates ------------------------------------------------------
+
+@pytest.mark.parametrize("mode", ["full", "diag", "identity", "zero"])
+def test_fixed_point_is_rollout_nonlinear(mode):
+    dyn, p = _small_gru(B=2, T=48, d=4, seed=9)
+    out = newton.solve(dyn, p["s0"], 48, mode, tol=1e-13, init="zeros")
+    assert np.all(out["converged"])
+    assert np.allclose(out["s"], newton.rollout(dyn, p["s0"], 48), rtol=0, atol=1e-12)
+
+
+def _order(r):
+    """Observed order of convergence: slope of log r_{i+1} against log r_i."""
+    r = np.log(np.asarray(r))
+    return np.polyfit(r[:-1], r[1:], 1)[0]
+
+
+def test_newton_tail_is_quadratic_and_quasi_is_linear():
+    """Basin of quadratic convergence (Thm. basin_size): ||r^+|| <= (L/2mu) ||r||^2 for
+    Newton; the diagonal quasi-Newton update converges only linearly."""
+    pb = synth.brusselator(T=256)
+    dyn = dynamics.Brusselator(pb["params"], pb["dt"])
+    full = newton.solve(dyn, pb["s0"], 256, "full", tol=1e-300, max_iters=40, init="s0", record=True)
+    r = np.array([h[0][0] for h in full["history"]])
+    r = r[r > 1e-13][-3:]
+    assert _order(r) > 1.7
+    md, pd = _small_massaction(B=1, d=4, R=6, seed=3, dt=0.05)
+    quasi = newton.solve(md, pd["s0"], 200, "diag", tol=1e-300, max_iters=60, init="s0", record=True)
+    rq = np.array([h[0][0] for h in quasi["history"]])
+    rq = rq[(rq > 1e-13) & (rq < 1e-4)]
+    assert len(rq) >= 8
+    assert 0.8 < _order(rq) < 1.25
+
+
+def test_reset_heuristic_keeps_global_convergence():
+    """An expanding linearisation overflows; resetting overflowed entries to zero still
+    converges within T iterations (Sec. 3.2)."""
+    dyn = dynamics.Linear(np.array([[3.0]]))
+    rng = np.random.default_rng(0)
+    dyn.x = rng.standard_normal((1, 40, 1))
+    T = 40
+    tiny = _RandomTransition(dyn, 3)
+    tiny.jac = lambda t, s: np.full((s.shape[0], 1, 1), 1e12)
+    out = newton.solve(tiny, np.zeros((1, 1)), T, "full", tol=0.0, init="zeros", reset=True,
+                       reset_threshold=1e30)
+    assert out["converged"][0] and out["iters"][0] <= T
+    assert np.array_equal(out["s"], newton.rollout(dyn, np.zeros((1, 1)), T))
+
+
+# --- damped (ELK) --------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", ["full", "diag"])
+def test_lm_step_is_kalman_smoother_mean(mode):
+    dyn, p = _small_gru(B=1, T=24, d=3, seed=6)
+    s = 0.5 * np.random.default_rng(3).standard_normal((1, 24, 3))
+    lam = 2.5
+    lm = elk.lm_step_dense(dyn, p["s0"][0], s[0], mode, lam)
+    sm = elk.elk_smoother_step(dyn, p["s0"], s, mode, lam)[0]
+    assert np.allclose(lm, sm, rtol=1e-10, atol=1e-11)
+    filt = elk.elk_filter_step(dyn, p["s0"], s, mode, lam)[0]
+    assert np.allclose(filt[-1], sm[-1], rtol=1e-10, atol=1e-11)
+    assert not np.allclose(filt[0], sm[0], atol=1e-6)
+
+
+def test_elk_limits_and_scale_clip_reductions():
+    dyn, p = _small_gru(B=2, T=20, d=3, seed=8)
+    s = 0.5 * np.random.default_rng(4).standard_normal((2, 20, 3))
+    s0 = p["s0"]
+    deer = newton.quasi_newton_step(dyn, s0, s, "full")
+    # lambda -> 0 (sigma^2 -> inf): the ELK filter step is the DEER step
+    assert np.allclose(elk.elk_filter_step(dyn, s0, s, "full", lam=0.0), deer, rtol=1e-12, atol=1e-12)
+    assert np.allclose(elk.elk_filter_step(dyn, s0, s, "full", lam=1e-12), deer, rtol=1e-8, atol=1e-9)
+    # huge lambda: the step stays at the previous iterate (vanishing trust region)
+    assert np.allclose(elk.elk_filter_step(dyn, s0, s, "full", lam=1e12), s, atol=1e-9)
+    # scale-ELK: k = 0 is DEER, k = 1 is Jacobi
+    assert np.allclose(newton.quasi_newton_step(dyn, s0, s, "full", "scale", 0.0), deer, atol=1e-14)
+    assert np.allclose(newton.quasi_newton_step(dyn, s0, s, "full", "scale", 1.0),
+                       newton.quasi_newton_step(dyn, s0, s, "zero"), atol=1e-14)
+    # clip-ELK equals quasi-DEER when the clip bound is never active
+    prev = np.concatenate([s0[:, None], s[:, :-1]], axis=1)
+    amax = max(np.max(np.abs(np.diagonal(dyn.jac(t, prev[:, t - 1]), axis1=1, axis2=2)))
+               for t in range(1, 21))
+    assert np.allclose(newton.quasi_newton_step(dyn, s0, s, "diag", "clip", amax + 1e-9),
+                       newton.quasi_newton_step(dyn, s0, s, "diag"), atol=1e-14)
+    assert not np.allclose(newton.quasi_newton_step(dyn, s0, s, "diag", "clip", 0.5 * amax),
+                           newton.quasi_newton_step(dyn, s0, s, "diag"), atol=1e-6)
+    # ... and with rho = 0 it is Jacobi
+    assert np.allclose(newton.quasi_newton_step(dyn, s0, s, "diag", "clip", 0.0),
+                       newton.quasi_newton_step(dyn, s0, s, "zero"), atol=1e-14)
+
+
+def test_elk_attenuation_bound():
+    """Sec. 4.3: the filtered mean is an LDS with transition Gamma_t A_t and
+    ||Gamma_t||_2 <= 1 / (1 + lambda). Check the scalar case numerically."""
+    lam = 3.0
+    sigma2 = 1.0 / lam
+    rng = np.random.default_rng(0)
+    a = rng.uniform(-2, 2, size=100)
+    P = 0.0
+    for at in a:
+        Pm = at * at * P + 1.0
+        gamma = sigma2 / (Pm + sigma2)
+        assert gamma <= 1.0 / (1.0 + lam) + 1e-15
+        P = gamma * Pm
+
+
+# --- adjoint -----------------------------------------------------------------
+
+def test_adjoint_equals_forward_sensitivity_and_fd():
+    dyn, p = _small_massaction(B=2, d=4, R=6, seed=5, dt=1e-2)
+    T = 30
+    s0 = p["s0"]
+    s = newton.rollout(dyn, s0, T)
+    kp = synth.perturbed_rates(p["params"], seed=1)
+    y = newton.rollout(dynamics.MassAction(p["topology"], kp, dyn.dt, "rk4", d=4), s0, T)
+    g = adjoint.sq_loss_cotangent(s, y)
+    dth, ds0, _ = adjoint.adjoint_grad(dyn, s0, s, g)
+    fth, fs0 = adjoint.forward_sensitivity_grad(dyn, s0, s, g)
+    assert np.allclose(dth, fth, rtol=1e-10, atol=1e-14)
+    assert np.allclose(ds0, fs0, rtol=1e-10, atol=1e-14)
+    mk = lambda k: dynamics.MassAction(p["topology"], k, dyn.dt, "rk4", d=4)
+    idx = [(0, 0), (0, 3), (1, 2), (1, 5)]
+    fd = adjoint.fd_grad(mk, p["params"], s0, T, y, idx, h=1e-6)
+    got = np.array([dth[b, j] for b, j in idx])
+    assert np.allclose(got, fd, rtol=1e-5, atol=1e-9)
