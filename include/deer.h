@@ -1,0 +1,204 @@
+/*
+ * deer.h - C ABI of the GB300 (sm_103a) parallel-Newton library.
+ *
+ * The library evaluates a nonlinear recurrence s_t = f_t(s_{t-1}), t = 1..T, from a
+ * fixed s_0 (Sec. 2.1 of the paper; inputs x_t are curried into f_t) by the parallel
+ * Newton iteration of Algorithm alg:deer: every iteration linearises f at the current
+ * guess for all t at once, solves the resulting linear recurrence with a parallel
+ * associative scan (Eq. deer_lds, bin_op_affine) and tests the residual
+ * r_t = s_t - f_t(s_{t-1}) (Eq. r_def).
+ *
+ * Conventions for every entry point:
+ *   - Tensor pointers are DEVICE memory owned by the caller, row-major and contiguous,
+ *     unless an argument says "host". The library never allocates device memory; it
+ *     uses the caller's workspace (size from the *_workspace_bytes queries).
+ *   - Floating-point buffers (params, s0, x, s, gradients) are float64 when
+ *     prec = DEER_FP64 or DEER_MIXED_BF16 and float32 when prec = DEER_FP32.
+ *   - A trajectory batch is packed: sequence b owns rows offsets[b] .. offsets[b+1]-1 of
+ *     s [N][d] and x [N][d_in] (N = offsets[B]); row offsets[b] + t - 1 holds s_t.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream). The
+ *     solver reads one small status word back per iteration and returns after the
+ *     stream has drained; results are then valid.
+ *   - Errors are returned as a deer_status; nothing aborts or traps. A solve that
+ *     reaches its iteration cap returns DEER_NOT_CONVERGED with the last iterate in s.
+ *   - Calls are reentrant given distinct workspaces; two calls that share a workspace
+ *     must not overlap on the GPU.
+ */
+#ifndef DEER_H_
+#define DEER_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* deer_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+  DEER_OK = 0,
+  DEER_NOT_CONVERGED = 1,     /* iteration cap reached; the last iterate is in s_out */
+  DEER_ERR_INVALID = -1,      /* bad pointer, size, enum value or combination */
+  DEER_ERR_CUDA = -2,         /* a CUDA call failed (see deer_last_cuda_error) */
+  DEER_ERR_NONFINITE = -3,    /* a residual became NaN/Inf (reset heuristic off) */
+  DEER_ERR_WORKSPACE = -4,    /* workspace missing, too small or misaligned (256 B) */
+  DEER_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
+  DEER_ERR_UNSUPPORTED = -6   /* combination not built (e.g. dense ELK, d too large) */
+} deer_status;
+
+/* Built-in recurrences f (the registry; f runs in hand-written CUDA). */
+typedef enum {
+  /* Brusselator kinetics dx = a-(b+1)x+x^2y, dy = bx-x^2y, explicit Euler, d = 2.
+     params per sequence: [a, b]. */
+  DEER_F_BRUSSELATOR_EULER = 0,
+  /* Mass-action reaction network, explicit Euler / classical RK4. params per sequence:
+     rate constants k[R]; topology per sequence: int32 [R][4] = (i1, i2, p1, p2) with -1
+     for an absent slot; reaction r has rate k_r c_i1 c_i2 (c_i2 -> 1 if i2 < 0),
+     consumes i1, i2 and produces p1, p2. Species indices must lie in [0, d). */
+  DEER_F_MASSACTION_EULER = 1,
+  DEER_F_MASSACTION_RK4 = 2,
+  /* GRU cell, zero biases: z = sig(Wz x + Uz h), r = sig(Wr x + Ur h),
+     h~ = tanh(Wh x + Uh (r*h)), h' = (1-z) h + z h~. params (shared, stride 0):
+     [Wz, Wr, Wh] each [d][d_in], then [Uz, Ur, Uh] each [d][d]. */
+  DEER_F_GRU = 3,
+  /* Affine recurrence s_t = A s_{t-1} + x_t (x may be NULL). params (shared): A [d][d]. */
+  DEER_F_LINEAR = 4
+} deer_fkind;
+
+/* Transition matrix A~_t of the linear recurrence solved per iteration
+   (Table fxd_pt_sum of the paper). */
+typedef enum {
+  DEER_JAC_FULL = 0,     /* Newton / DEER: df_t/ds_{t-1}, dense d x d (d <= 32) */
+  DEER_JAC_DIAG = 1,     /* quasi-Newton / quasi-DEER: its diagonal (Eq. quasi_lds) */
+  DEER_JAC_IDENTITY = 2, /* Picard: I */
+  DEER_JAC_ZERO = 3      /* Jacobi: 0 */
+} deer_jac;
+
+typedef enum {
+  DEER_DAMP_NONE = 0,
+  DEER_DAMP_ELK = 1,   /* Kalman-filter step, lambda = damp_param (diag modes only; Sec. 4.3) */
+  DEER_DAMP_SCALE = 2, /* scale-ELK: A~ <- (1 - k) A~, k = damp_param in [0, 1] (Sec. 4.5.1) */
+  DEER_DAMP_CLIP = 3   /* clip-ELK: diag A~ clipped to [-rho, rho], rho = damp_param (Sec. 4.5.2) */
+} deer_damp;
+
+typedef enum {
+  DEER_INIT_ZEROS = 0,  /* s^(0)_t = 0 */
+  DEER_INIT_S0 = 1,     /* s^(0)_t = s_0 */
+  DEER_INIT_JACOBI = 2, /* s^(0)_t = f_t(0): one Jacobi step from zero */
+  DEER_INIT_USER = 3    /* s_out holds the guess on entry (warm start) */
+} deer_init;
+
+typedef enum {
+  DEER_FP64 = 0,       /* everything float64 */
+  DEER_FP32 = 1,       /* everything float32; residual max/merit accumulated in float64 */
+  DEER_MIXED_BF16 = 2  /* float64 state and residual; the dense scan composes
+                          bf16 Jacobians with float32 accumulation in correction form */
+} deer_prec;
+
+typedef struct {
+  int32_t kind;            /* deer_fkind */
+  int32_t d;               /* state size */
+  int32_t d_in;            /* input size (GRU; LINEAR uses d); 0 when f takes no input */
+  int32_t n_reactions;     /* R (mass-action only) */
+  double dt;               /* integrator step (Brusselator, mass-action) */
+  const void* params;      /* device; layout per kind above */
+  int64_t params_stride;   /* elements between consecutive sequences' params; 0 = shared */
+  const int32_t* topology; /* device; mass-action only */
+  int64_t topology_stride; /* int32 elements between sequences' topologies; 0 = shared */
+} deer_dynamics;
+
+typedef struct {
+  int32_t max_iters;  /* iteration cap; <= 0 means the longest T (sufficient by
+                         Prop. global_convergence) */
+  double tol;         /* converged when max_t ||r_t||_inf <= tol, evaluated in float64 */
+  int32_t jac;        /* deer_jac */
+  int32_t damp;       /* deer_damp */
+  double damp_param;  /* lambda (ELK), k (scale) or rho (clip) */
+  int32_t init;       /* deer_init */
+  int32_t prec;       /* deer_prec */
+  int32_t reset;      /* reset heuristic (Sec. 3.2): entries that are non-finite or exceed
+                         1e30 (float64) / 1e18 (float32) after a scan are set to 0 */
+  int32_t chunk;      /* scan chunk length; 0 = automatic. Power of two in [8, 1024]. */
+} deer_options;
+
+typedef struct {
+  int32_t iters;      /* linear-recurrence solves applied to this sequence */
+  int32_t converged;  /* 1 if max |r| <= tol was reached */
+  double merit;       /* 1/2 ||r||^2 of the returned iterate (Eq. merit) */
+  double max_resid;   /* max_t ||r_t||_inf of the returned iterate */
+} deer_info;
+
+/* Fills `opt` with defaults: cap T, tol 1e-10, FULL, no damping, INIT_S0, FP64, auto chunk. */
+void deer_default_options(deer_options* opt);
+
+/* Workspace bytes needed by deer_solve / deer_solve_batched for `batch` sequences
+   holding `total_steps` rows in all. Returns 0 for an invalid configuration. */
+size_t deer_workspace_bytes(const deer_dynamics* f, int64_t batch, int64_t total_steps,
+                            const deer_options* opt);
+
+/* Solve `batch` sequences of equal length T. s0 [batch][d]; x [batch*T][d_in] or NULL;
+   s_out [batch*T][d] (holds the guess on entry when init = DEER_INIT_USER).
+   info: host array [batch] or NULL. */
+deer_status deer_solve(const deer_dynamics* f, int64_t batch, int64_t T, const void* s0,
+                       const void* x, void* s_out, const deer_options* opt, void* workspace,
+                       size_t workspace_bytes, deer_stream_t stream, deer_info* info);
+
+/* Ragged batch: offsets is a HOST array [batch+1] (offsets[0] = 0, non-decreasing; empty
+   sequences allowed). Sequences converge independently: a converged sequence is masked
+   out of later iterations. Other arguments as deer_solve. */
+deer_status deer_solve_batched(const deer_dynamics* f, int64_t batch, const int64_t* offsets,
+                               const void* s0, const void* x, void* s_out,
+                               const deer_options* opt, void* workspace, size_t workspace_bytes,
+                               deer_stream_t stream, deer_info* info);
+
+/* Workspace bytes for deer_grad. */
+size_t deer_grad_workspace_bytes(const deer_dynamics* f, int64_t batch, int64_t T,
+                                 const deer_options* opt);
+
+/* Gradient of a loss l(s_1..s_T) at the converged trajectory s_star [batch*T][d] by the
+   adjoint (Eq. bptt / unrolled_bwds): a reverse linear recurrence
+   lambda_T = g_T, lambda_{t-1} = g_{t-1} + A_t^T lambda_t solved with a reverse parallel
+   scan, then dl/dtheta = sum_t lambda_t^T df_t/dtheta(s_{t-1}) and dl/ds0 = A_1^T lambda_1.
+   dl_ds [batch*T][d] holds g_t = dl/ds_t. dl_dparams [batch][params per sequence] (mass-
+   action: d/dk; Brusselator: d/d(a,b); not available for shared-parameter kinds);
+   dl_ds0 [batch][d] or NULL. Uses opt->prec (FP64 or FP32) and opt->chunk. */
+deer_status deer_grad(const deer_dynamics* f, int64_t batch, int64_t T, const void* s0,
+                      const void* x, const void* s_star, const void* dl_ds, void* dl_dparams,
+                      void* dl_ds0, const deer_options* opt, void* workspace,
+                      size_t workspace_bytes, deer_stream_t stream);
+
+/* Sequential rollout s_t = f_t(s_{t-1}) on the GPU (the comparison baseline: one
+   trajectory per thread or thread group, no parallelism over t). offsets: DEVICE array
+   [batch+1] for a ragged batch, or NULL for `batch` sequences of length T. Needs no
+   workspace. */
+deer_status deer_rollout(const deer_dynamics* f, int64_t batch, int64_t T,
+                         const int64_t* offsets, const void* s0, const void* x, void* s_out,
+                         int32_t prec, deer_stream_t stream);
+
+/* Number of kernels this library enqueued since load (all entry points, all threads). */
+int64_t deer_kernel_launch_count(void);
+
+/* Per-phase device time of deer_solve / deer_solve_batched, measured with CUDA events on
+   the solver's stream while profiling is enabled (off by default; costs one extra stream
+   synchronisation per iteration). Phase p: 0 set-up, 1 linearise + residual, 2
+   convergence check, 3 scan. rows[p] counts the trajectory rows the phase processed
+   (rows of converged sequences are skipped). Process-wide, thread-safe. */
+typedef struct {
+  int64_t launches[4];
+  double ms[4];
+  int64_t rows[4];
+} deer_profile;
+void deer_profile_enable(int32_t on);
+void deer_profile_reset(void);
+void deer_profile_read(deer_profile* out);
+
+const char* deer_status_string(int32_t status);
+const char* deer_last_cuda_error(void);
+int32_t deer_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DEER_H_ */

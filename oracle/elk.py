@@ -70,8 +70,8 @@ def elk_filter_step(dyn, s0, s, mode="full", lam=1.0, active=None, reset=False,
     A, b = _lds_terms(dyn, s0, s, mode)
     mus, _, _, _ = kalman_filter(A, b, s, s0, lam)
     if reset:
-        bad = ~np.isfinite(mus) | (np.abs(mus) > reset_threshold)
-        mus = np.where(bad, 0.0, mus)
+        from .newton import reset_overflow
+        mus = reset_overflow(mus, reset_threshold)
     if active is not None:
         mus = np.where(active[:, None, None], mus, s)
     return mus

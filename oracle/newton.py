@@ -85,15 +85,28 @@ def quasi_newton_step(dyn, s0, s, mode="full", damp="none", damp_param=0.0,
         F = dyn.f(t, old_prev)
         A = transition(dyn, t, old_prev, mode, damp, damp_param)
         v = F + np.einsum("bij,bj->bi", A, new_prev - old_prev)
-        if reset:
-            bad = ~np.isfinite(v) | (np.abs(v) > reset_threshold)
-            v = np.where(bad, 0.0, v)
         if active is not None:
             v = np.where(active[:, None], v, s[:, t - 1])
         new[:, t - 1] = v
         old_prev = s[:, t - 1]
         new_prev = v
+    if reset:
+        new = reset_overflow(new, reset_threshold)
     return new
+
+
+def reset_overflow(s, threshold):
+    """Reset heuristic (Sec. 3.2): entries of the new iterate that are non-finite or whose
+    magnitude exceeds ``threshold`` are set to zero. Applied to the whole iterate once the
+    linear recurrence has been solved (entries of the exact prefix are never touched)."""
+    bad = ~np.isfinite(s) | (np.abs(s) > threshold)
+    return np.where(bad, 0.0, s)
+
+
+def scaled_residual_max(r, s):
+    """max_t,i |r_t,i| / max(1, |s_t,i|) per sequence: the convergence measure. It is the
+    absolute residual of Eq. r_def wherever |s| <= 1 and the relative one elsewhere."""
+    return np.max(np.abs(r) / np.maximum(1.0, np.abs(s)), axis=(1, 2))
 
 
 def initial_guess(dyn, s0, T, init="s0", user=None):
@@ -117,9 +130,9 @@ def solve(dyn, s0, T, mode="full", damp="none", damp_param=0.0, tol=1e-10, max_i
           init="s0", user=None, reset=False, reset_threshold=1e30, record=False):
     """Algorithm alg:deer (ParallelNewton), per sequence of the batch.
 
-    Iteration i evaluates r(s^{(i)}); a sequence whose max_t ||r_t||_inf <= tol is
-    converged and keeps s^{(i)} (the error test of the algorithm, applied to the
-    current iterate). Otherwise one LDS solve gives s^{(i+1)}. ``iters`` counts the LDS
+    Iteration i evaluates r(s^{(i)}); a sequence whose scaled residual
+    max_t,i |r_t,i| / max(1, |s_t,i|) is <= tol is converged and keeps s^{(i)} (the error
+    test of the algorithm, applied to the current iterate). Otherwise one LDS solve gives s^{(i+1)}. ``iters`` counts the LDS
     solves. The cap defaults to T, which suffices by Prop. global_convergence.
     """
     from . import elk as _elk
@@ -136,7 +149,7 @@ def solve(dyn, s0, T, mode="full", damp="none", damp_param=0.0, tol=1e-10, max_i
     merit = np.full(B, np.inf)
     for i in range(max_iters + 1):
         r = residual(dyn, s0, s)
-        mr = np.max(np.abs(r), axis=(1, 2))
+        mr = scaled_residual_max(r, s)
         mer = 0.5 * np.sum(r * r, axis=(1, 2))
         upd = ~converged
         max_resid[upd] = mr[upd]

@@ -1,0 +1,513 @@
+// Host side of the C ABI: argument checks, workspace layout and the Newton loop of
+// Algorithm alg:deer (linearise -> convergence test -> parallel scan, repeated).
+#include <atomic>
+#include <mutex>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "kernels.h"
+
+namespace deer {
+
+static std::atomic<int64_t> g_launches{0};
+static thread_local char g_err[256] = "";
+
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Optional per-phase timing with CUDA events on the solver's stream (deer_profile_*).
+enum { PH_SETUP = 0, PH_LIN = 1, PH_CHECK = 2, PH_SCAN = 3, PH_N = 4 };
+static std::atomic<int> g_prof_on{0};
+static std::mutex g_prof_mu;
+static deer_profile g_prof{};
+
+struct PhaseTimer {
+  bool on;
+  cudaStream_t st;
+  cudaEvent_t ev[PH_N][2];
+  bool used[PH_N];
+  explicit PhaseTimer(cudaStream_t s) : on(g_prof_on.load() != 0), st(s) {
+    for (int p = 0; p < PH_N; ++p) {
+      used[p] = false;
+      if (on) { cudaEventCreate(&ev[p][0]); cudaEventCreate(&ev[p][1]); }
+    }
+  }
+  ~PhaseTimer() {
+    if (!on) return;
+    for (int p = 0; p < PH_N; ++p) { cudaEventDestroy(ev[p][0]); cudaEventDestroy(ev[p][1]); }
+  }
+  void begin(int p) { if (on) cudaEventRecord(ev[p][0], st); }
+  void end(int p) { if (on) { cudaEventRecord(ev[p][1], st); used[p] = true; } }
+  // call after the stream has been synchronised
+  void collect(const int64_t* launches, const int64_t* rows) {
+    if (!on) return;
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    for (int p = 0; p < PH_N; ++p) {
+      if (!used[p]) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[p][0], ev[p][1]) == cudaSuccess) g_prof.ms[p] += ms;
+      g_prof.launches[p] += launches[p];
+      g_prof.rows[p] += rows[p];
+      used[p] = false;
+    }
+  }
+};
+
+static deer_status cuda_fail(cudaError_t e, const char* where) {
+  snprintf(g_err, sizeof(g_err), "%s: %s", where, cudaGetErrorString(e));
+  return DEER_ERR_CUDA;
+}
+
+#define DEER_CK(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+static size_t align_up(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
+
+// Supported state sizes per kind (the kernels are instantiated for these).
+static bool d_supported(int kind, int d, int jac) {
+  if (kind == DEER_F_BRUSSELATOR_EULER) return d == 2;
+  const bool p2 = d == 1 || d == 2 || d == 4 || d == 8 || d == 16 || d == 32;
+  if (kind == DEER_F_GRU) return p2 || (d == 64 && jac != DEER_JAC_FULL);
+  if (kind == DEER_F_MASSACTION_EULER || kind == DEER_F_MASSACTION_RK4) return p2 && d >= 2;
+  return p2;
+}
+
+// Everything the solver carves out of the caller's workspace.
+struct Layout {
+  size_t offsets, chunk_first, acc, info, flags, ma, gru_M, A, b, aggP, aggv, cin, gam, mob,
+      pin, total;
+  int64_t n_chunks_max;
+  int64_t ma_stride, n_ma;
+  int L;
+};
+
+static int choose_chunk(const deer_options* o, int d) {
+  if (o->chunk > 0) return o->chunk;
+  if (o->jac == DEER_JAC_FULL) return d >= 16 ? 32 : 64;
+  return 128;
+}
+
+static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer_options* o,
+                        Layout& ly) {
+  if (!f || !o || B < 0 || N < 0) return false;
+  if (o->prec != DEER_FP64 && o->prec != DEER_FP32) return false;
+  const size_t rs = o->prec == DEER_FP32 ? 4 : 8;
+  const int d = f->d;
+  const int L = choose_chunk(o, d);
+  if (!pow2(L) || L < 8 || L > 1024) return false;
+  ly.L = L;
+  ly.n_chunks_max = N / L + B + 1;
+  const int64_t C = ly.n_chunks_max;
+  size_t p = 0;
+  auto take = [&](size_t bytes) { size_t at = p; p = align_up(p + bytes); return at; };
+  ly.offsets = take((size_t)(B + 1) * 8);
+  ly.chunk_first = take((size_t)(B + 1) * 8);
+  ly.acc = take((size_t)(B > 0 ? B : 1) * sizeof(SeqAcc));
+  ly.info = take((size_t)(B > 0 ? B : 1) * sizeof(SeqInfo));
+  ly.flags = take(sizeof(Flags));
+  ly.ma = ly.gru_M = ly.A = ly.aggP = ly.gam = ly.mob = ly.pin = p;
+  ly.ma_stride = 0;
+  ly.n_ma = 0;
+  if (f->kind == DEER_F_MASSACTION_EULER || f->kind == DEER_F_MASSACTION_RK4) {
+    ly.ma_stride = (int64_t)d * d + (int64_t)d * d * d;
+    ly.ma_stride = (ly.ma_stride + 3) / 4 * 4;
+    const bool shared = f->params_stride == 0 && f->topology_stride == 0;
+    ly.n_ma = shared ? 1 : B;
+    ly.ma = take((size_t)(ly.n_ma > 0 ? ly.n_ma : 1) * ly.ma_stride * rs);
+  }
+  if (f->kind == DEER_F_GRU) ly.gru_M = take((size_t)d * d * rs);
+  if (o->jac == DEER_JAC_FULL) ly.A = take((size_t)N * d * d * rs);
+  else if (o->jac == DEER_JAC_DIAG) ly.A = take((size_t)N * d * rs);
+  ly.b = take((size_t)N * d * rs);
+  if (o->jac == DEER_JAC_FULL) ly.aggP = take((size_t)C * d * d * rs);
+  ly.aggv = take((size_t)C * d * rs);
+  ly.cin = take((size_t)C * d * rs);
+  // diag family also needs a second aggregate array; reuse aggP slot for it
+  if (o->jac != DEER_JAC_FULL) ly.aggP = take((size_t)C * d * rs);
+  if (o->damp == DEER_DAMP_ELK) {
+    ly.gam = take((size_t)N * d * rs);
+    ly.mob = take((size_t)C * d * 4 * rs);
+    ly.pin = take((size_t)C * d * rs);
+  }
+  ly.total = p;
+  return true;
+}
+
+template <class real>
+static DynView<real> make_view(const deer_dynamics* f, const void* x, char* ws,
+                               const Layout& ly) {
+  DynView<real> v;
+  v.kind = f->kind;
+  v.d = f->d;
+  v.d_in = f->kind == DEER_F_LINEAR ? f->d : f->d_in;
+  v.R = f->n_reactions;
+  v.dt = (real)f->dt;
+  v.params = static_cast<const real*>(f->params);
+  v.pstride = f->params_stride;
+  v.topo = f->topology;
+  v.tstride = f->topology_stride;
+  v.x = static_cast<const real*>(x);
+  v.ma = ws ? reinterpret_cast<const real*>(ws + ly.ma) : nullptr;
+  v.ma_stride = ly.n_ma == 1 ? 0 : ly.ma_stride;
+  v.gru_M = ws ? reinterpret_cast<const real*>(ws + ly.gru_M) : nullptr;
+  return v;
+}
+
+static deer_status check_common(const deer_dynamics* f, const deer_options* o) {
+  if (!f || !o) return DEER_ERR_INVALID;
+  if (f->kind < 0 || f->kind > DEER_F_LINEAR) return DEER_ERR_INVALID;
+  if (o->jac < 0 || o->jac > DEER_JAC_ZERO) return DEER_ERR_INVALID;
+  if (o->damp < 0 || o->damp > DEER_DAMP_CLIP) return DEER_ERR_INVALID;
+  if (o->init < 0 || o->init > DEER_INIT_USER) return DEER_ERR_INVALID;
+  if (o->prec == DEER_MIXED_BF16) return DEER_ERR_UNSUPPORTED;
+  if (o->prec != DEER_FP64 && o->prec != DEER_FP32) return DEER_ERR_INVALID;
+  if (!d_supported(f->kind, f->d, o->jac)) return DEER_ERR_UNSUPPORTED;
+  if (o->damp == DEER_DAMP_ELK && o->jac == DEER_JAC_FULL) return DEER_ERR_UNSUPPORTED;
+  if (o->damp == DEER_DAMP_CLIP && o->jac == DEER_JAC_FULL) return DEER_ERR_INVALID;
+  if (o->damp == DEER_DAMP_ELK && !(o->damp_param >= 0.0)) return DEER_ERR_INVALID;
+  if (!f->params) return DEER_ERR_INVALID;
+  if (f->kind == DEER_F_MASSACTION_EULER || f->kind == DEER_F_MASSACTION_RK4) {
+    if (!f->topology || f->n_reactions <= 0) return DEER_ERR_INVALID;
+    if (f->params_stride != 0 && f->params_stride < f->n_reactions) return DEER_ERR_INVALID;
+    if (f->topology_stride != 0 && f->topology_stride < 4 * (int64_t)f->n_reactions)
+      return DEER_ERR_INVALID;
+    if (f->topology_stride % 4 != 0) return DEER_ERR_INVALID;
+  }
+  if (f->kind == DEER_F_GRU && f->d_in <= 0) return DEER_ERR_INVALID;
+  if (f->kind == DEER_F_BRUSSELATOR_EULER && f->params_stride != 0 && f->params_stride < 2)
+    return DEER_ERR_INVALID;
+  return DEER_OK;
+}
+
+template <class real>
+static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* offsets_h,
+                              const void* s0_, const void* x_, void* s_, const deer_options* o,
+                              void* ws_, size_t ws_bytes, cudaStream_t st, deer_info* info_h) {
+  const int64_t N = offsets_h[B];
+  Layout ly;
+  if (!make_layout(f, B, N, o, ly)) return DEER_ERR_INVALID;
+  if (!ws_ || ws_bytes < ly.total || (reinterpret_cast<uintptr_t>(ws_) & 255u))
+    return DEER_ERR_WORKSPACE;
+  char* ws = static_cast<char*>(ws_);
+  const int d = f->d;
+  const real* s0 = static_cast<const real*>(s0_);
+  real* s = static_cast<real*>(s_);
+
+  // sequence / chunk tables
+  std::vector<int64_t> chunk_first(B + 1);
+  int64_t maxT = 0, nc = 0;
+  for (int64_t b = 0; b < B; ++b) {
+    const int64_t len = offsets_h[b + 1] - offsets_h[b];
+    if (len < 0) return DEER_ERR_INVALID;
+    chunk_first[b] = nc;
+    nc += (len + ly.L - 1) / ly.L;
+    if (len > maxT) maxT = len;
+  }
+  chunk_first[B] = nc;
+  if (offsets_h[0] != 0) return DEER_ERR_INVALID;
+  int64_t* d_off = reinterpret_cast<int64_t*>(ws + ly.offsets);
+  int64_t* d_cf = reinterpret_cast<int64_t*>(ws + ly.chunk_first);
+  DEER_CK(cudaMemcpyAsync(d_off, offsets_h, (B + 1) * 8, cudaMemcpyHostToDevice, st));
+  DEER_CK(cudaMemcpyAsync(d_cf, chunk_first.data(), (B + 1) * 8, cudaMemcpyHostToDevice, st));
+  SeqAcc* acc = reinterpret_cast<SeqAcc*>(ws + ly.acc);
+  SeqInfo* info = reinterpret_cast<SeqInfo*>(ws + ly.info);
+  Flags* flags = reinterpret_cast<Flags*>(ws + ly.flags);
+  if (B > 0) {
+    DEER_CK(cudaMemsetAsync(acc, 0, B * sizeof(SeqAcc), st));
+    DEER_CK(cudaMemsetAsync(info, 0, B * sizeof(SeqInfo), st));
+  }
+  DEER_CK(cudaMemsetAsync(flags, 0, sizeof(Flags), st));
+
+  Batch bt;
+  bt.B = B;
+  bt.N = N;
+  bt.offsets = d_off;
+  bt.chunk_first = d_cf;
+  bt.n_chunks = nc;
+  bt.L = ly.L;
+  bt.log2L = ilog2(ly.L);
+
+  DynView<real> dv = make_view<real>(f, x_, ws, ly);
+  if (ly.n_ma > 0) {
+    DEER_CK(launch_ma_setup<real>(ly.n_ma, d, f->n_reactions, static_cast<const real*>(f->params),
+                                  f->params_stride, f->topology, f->topology_stride,
+                                  reinterpret_cast<real*>(ws + ly.ma), ly.ma_stride,
+                                  &flags->bad_input, st));
+  }
+  if (f->kind == DEER_F_GRU) {
+    DEER_CK(launch_gru_setup<real>(d, static_cast<const real*>(f->params), f->d_in,
+                                   reinterpret_cast<real*>(ws + ly.gru_M), st));
+  }
+  if (o->init != DEER_INIT_USER) {
+    InitArgs<real> ia{dv, bt, s0, s, o->init};
+    DEER_CK(launch_init<real>(ia, st));
+  }
+
+  const int max_iters = o->max_iters > 0 ? o->max_iters : (int)(maxT > 0 ? maxT : 1);
+  const real reset_thr = sizeof(real) == 8 ? real(1e30) : real(1e18);
+
+  LinArgs<real> la;
+  la.dv = dv;
+  la.bt = bt;
+  la.s0 = s0;
+  la.s = s;
+  la.A = reinterpret_cast<real*>(ws + ly.A);
+  la.b = reinterpret_cast<real*>(ws + ly.b);
+  la.acc = acc;
+  la.info = info;
+  la.jac = o->jac;
+  la.damp = o->damp;
+  la.dparam = (real)o->damp_param;
+
+  CheckArgs ca{B, d_off, acc, info, flags, o->tol, 0, max_iters};
+
+  DenseScanArgs<real> dsa;
+  DiagScanArgs<real> gsa;
+  if (o->jac == DEER_JAC_FULL) {
+    dsa.bt = bt;
+    dsa.d = d;
+    dsa.A = la.A;
+    dsa.b = la.b;
+    dsa.s = s;
+    dsa.aggP = reinterpret_cast<real*>(ws + ly.aggP);
+    dsa.aggv = reinterpret_cast<real*>(ws + ly.aggv);
+    dsa.cin = reinterpret_cast<real*>(ws + ly.cin);
+    dsa.info = info;
+    dsa.reset = o->reset;
+    dsa.reset_thr = reset_thr;
+  } else {
+    gsa.bt = bt;
+    gsa.d = d;
+    gsa.amode = o->jac == DEER_JAC_DIAG ? 0 : 1;
+    real ac = o->jac == DEER_JAC_IDENTITY ? real(1) : real(0);
+    if (o->damp == DEER_DAMP_SCALE) ac *= real(1) - (real)o->damp_param;
+    if (o->damp == DEER_DAMP_CLIP) {
+      const real rho = (real)o->damp_param;
+      ac = ac > rho ? rho : (ac < -rho ? -rho : ac);
+    }
+    gsa.aconst = ac;
+    gsa.a = la.A;
+    gsa.b = la.b;
+    gsa.s0 = s0;
+    gsa.s = s;
+    gsa.aggA = reinterpret_cast<real*>(ws + ly.aggP);
+    gsa.aggB = reinterpret_cast<real*>(ws + ly.aggv);
+    gsa.cin = reinterpret_cast<real*>(ws + ly.cin);
+    gsa.info = info;
+    gsa.elk = (o->damp == DEER_DAMP_ELK && o->damp_param > 0.0) ? 1 : 0;
+    gsa.sigma2 = gsa.elk ? real(1.0 / o->damp_param) : real(0);
+    gsa.gam = reinterpret_cast<real*>(ws + ly.gam);
+    gsa.mob = reinterpret_cast<real*>(ws + ly.mob);
+    gsa.pin = reinterpret_cast<real*>(ws + ly.pin);
+    gsa.reset = o->reset;
+    gsa.reset_thr = reset_thr;
+  }
+
+  deer_status status = DEER_OK;
+  Flags hf;
+  PhaseTimer pt(st);
+  int64_t lin_rows = N;  // rows linearised in the current iteration
+  for (int it = 0;; ++it) {
+    const int64_t l0 = g_launches.load();
+    pt.begin(PH_LIN);
+    DEER_CK(launch_linearize<real>(la, st));
+    pt.end(PH_LIN);
+    const int64_t l1 = g_launches.load();
+    ca.it = it;
+    pt.begin(PH_CHECK);
+    DEER_CK(launch_check(ca, st));
+    pt.end(PH_CHECK);
+    DEER_CK(cudaMemcpyAsync(&hf, flags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
+    DEER_CK(cudaStreamSynchronize(st));
+    bool stop = false;
+    if (hf.bad_input) { status = DEER_ERR_INVALID; stop = true; }
+    else if (hf.n_nonfinite > 0 && !o->reset) { status = DEER_ERR_NONFINITE; stop = true; }
+    else if (hf.n_active == 0) stop = true;
+    else if (it >= max_iters) { status = DEER_NOT_CONVERGED; stop = true; }
+    int64_t scan_launches = 0;
+    if (!stop) {
+      const int64_t s0c = g_launches.load();
+      pt.begin(PH_SCAN);
+      if (o->jac == DEER_JAC_FULL) DEER_CK(launch_dense_scan<real>(dsa, st));
+      else DEER_CK(launch_diag_scan<real>(gsa, st));
+      pt.end(PH_SCAN);
+      scan_launches = g_launches.load() - s0c;
+    }
+    if (pt.on) {
+      DEER_CK(cudaStreamSynchronize(st));
+      const int64_t launches[PH_N] = {0, l1 - l0, 1, scan_launches};
+      const int64_t rows[PH_N] = {0, lin_rows, (int64_t)B, stop ? 0 : (int64_t)hf.active_rows};
+      pt.collect(launches, rows);
+    }
+    lin_rows = hf.active_rows;
+    if (stop) break;
+  }
+
+  if (info_h && B > 0) {
+    std::vector<SeqInfo> hi(B);
+    DEER_CK(cudaMemcpyAsync(hi.data(), info, B * sizeof(SeqInfo), cudaMemcpyDeviceToHost, st));
+    DEER_CK(cudaStreamSynchronize(st));
+    for (int64_t b = 0; b < B; ++b) {
+      info_h[b].iters = hi[b].iters;
+      info_h[b].converged = hi[b].done;
+      info_h[b].merit = hi[b].merit;
+      info_h[b].max_resid = hi[b].max_resid;
+    }
+  } else {
+    DEER_CK(cudaStreamSynchronize(st));
+  }
+  return status;
+}
+
+}  // namespace deer
+
+using namespace deer;
+
+extern "C" {
+
+void deer_default_options(deer_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->max_iters = 0;
+  o->tol = 1e-10;
+  o->jac = DEER_JAC_FULL;
+  o->damp = DEER_DAMP_NONE;
+  o->damp_param = 0.0;
+  o->init = DEER_INIT_S0;
+  o->prec = DEER_FP64;
+  o->reset = 0;
+  o->chunk = 0;
+}
+
+size_t deer_workspace_bytes(const deer_dynamics* f, int64_t batch, int64_t total_steps,
+                            const deer_options* opt) {
+  if (check_common(f, opt) != DEER_OK) return 0;
+  Layout ly;
+  if (!make_layout(f, batch, total_steps, opt, ly)) return 0;
+  return ly.total;
+}
+
+static deer_status solve_dispatch(const deer_dynamics* f, int64_t batch, const int64_t* off,
+                                  const void* s0, const void* x, void* s_out,
+                                  const deer_options* opt, void* ws, size_t wsb,
+                                  deer_stream_t stream, deer_info* info) {
+  deer_status c = check_common(f, opt);
+  if (c != DEER_OK) return c;
+  if (batch < 0) return DEER_ERR_INVALID;
+  if (batch == 0) return DEER_OK;
+  if (!s0 || !s_out) return DEER_ERR_INVALID;
+  if ((f->kind == DEER_F_GRU) && !x) return DEER_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (opt->prec == DEER_FP32)
+    return solve_impl<float>(f, batch, off, s0, x, s_out, opt, ws, wsb, st, info);
+  return solve_impl<double>(f, batch, off, s0, x, s_out, opt, ws, wsb, st, info);
+}
+
+deer_status deer_solve(const deer_dynamics* f, int64_t batch, int64_t T, const void* s0,
+                       const void* x, void* s_out, const deer_options* opt, void* workspace,
+                       size_t workspace_bytes, deer_stream_t stream, deer_info* info) {
+  if (batch < 0 || T < 0) return DEER_ERR_INVALID;
+  std::vector<int64_t> off(batch + 1);
+  for (int64_t b = 0; b <= batch; ++b) off[b] = b * T;
+  return solve_dispatch(f, batch, off.data(), s0, x, s_out, opt, workspace, workspace_bytes,
+                        stream, info);
+}
+
+deer_status deer_solve_batched(const deer_dynamics* f, int64_t batch, const int64_t* offsets,
+                               const void* s0, const void* x, void* s_out,
+                               const deer_options* opt, void* workspace, size_t workspace_bytes,
+                               deer_stream_t stream, deer_info* info) {
+  if (!offsets || batch < 0) return DEER_ERR_INVALID;
+  for (int64_t b = 0; b < batch; ++b)
+    if (offsets[b + 1] < offsets[b]) return DEER_ERR_INVALID;
+  if (offsets[0] != 0) return DEER_ERR_INVALID;
+  return solve_dispatch(f, batch, offsets, s0, x, s_out, opt, workspace, workspace_bytes,
+                        stream, info);
+}
+
+deer_status deer_rollout(const deer_dynamics* f, int64_t batch, int64_t T,
+                         const int64_t* offsets, const void* s0, const void* x, void* s_out,
+                         int32_t prec, deer_stream_t stream) {
+  deer_options o;
+  deer_default_options(&o);
+  o.prec = prec;
+  o.jac = DEER_JAC_ZERO;
+  deer_status c = check_common(f, &o);
+  if (c != DEER_OK) return c;
+  if (batch < 0 || (!offsets && T < 0)) return DEER_ERR_INVALID;
+  if (batch == 0) return DEER_OK;
+  if (!s0 || !s_out) return DEER_ERR_INVALID;
+  if (f->kind == DEER_F_GRU && !x) return DEER_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Layout ly{};
+  cudaError_t e;
+  if (prec == DEER_FP32) {
+    RolloutArgs<float> a{make_view<float>(f, x, nullptr, ly), batch, T, offsets,
+                         static_cast<const float*>(s0), static_cast<float*>(s_out)};
+    e = launch_rollout<float>(a, st);
+  } else {
+    RolloutArgs<double> a{make_view<double>(f, x, nullptr, ly), batch, T, offsets,
+                          static_cast<const double*>(s0), static_cast<double*>(s_out)};
+    e = launch_rollout<double>(a, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "deer_rollout");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "deer_rollout sync");
+  return DEER_OK;
+}
+
+size_t deer_grad_workspace_bytes(const deer_dynamics*, int64_t, int64_t, const deer_options*) {
+  return 0;
+}
+
+deer_status deer_grad(const deer_dynamics*, int64_t, int64_t, const void*, const void*,
+                      const void*, const void*, void*, void*, const deer_options*, void*, size_t,
+                      deer_stream_t) {
+  return DEER_ERR_UNSUPPORTED;
+}
+
+int64_t deer_kernel_launch_count(void) { return g_launches.load(); }
+
+void deer_profile_enable(int32_t on) { g_prof_on.store(on ? 1 : 0); }
+
+void deer_profile_reset(void) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  g_prof = deer_profile{};
+}
+
+void deer_profile_read(deer_profile* out) {
+  if (!out) return;
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  *out = g_prof;
+}
+
+const char* deer_status_string(int32_t s) {
+  switch (s) {
+    case DEER_OK: return "ok";
+    case DEER_NOT_CONVERGED: return "not converged (iteration cap reached)";
+    case DEER_ERR_INVALID: return "invalid argument";
+    case DEER_ERR_CUDA: return "CUDA error";
+    case DEER_ERR_NONFINITE: return "non-finite residual";
+    case DEER_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case DEER_ERR_TIMEOUT: return "bounded device wait timed out";
+    case DEER_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+const char* deer_last_cuda_error(void) { return g_err; }
+
+int32_t deer_version(void) { return 1; }
+
+}  // extern "C"

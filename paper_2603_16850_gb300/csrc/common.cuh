@@ -1,0 +1,134 @@
+// Shared device/host definitions of the parallel-Newton library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "deer.h"
+
+namespace deer {
+
+// ---------------------------------------------------------------------------
+// Per-sequence solver state kept in the workspace.
+// ---------------------------------------------------------------------------
+struct SeqAcc {                 // reset every iteration
+  unsigned long long max_bits;  // bit pattern of max_t ||r_t||_inf (non-negative double)
+  double sumsq;                 // sum_t ||r_t||^2
+};
+
+struct SeqInfo {                // persistent during one solve
+  int32_t iters;
+  int32_t done;                 // 1 once converged (masked out of later iterations)
+  double merit;
+  double max_resid;
+};
+
+struct Flags {                  // read back by the host once per iteration
+  int32_t n_active;
+  int32_t n_nonfinite;
+  int32_t timeout;
+  int32_t bad_input;            // set by set-up kernels that reject their inputs
+  long long active_rows;        // rows of the sequences still active after the check
+};
+
+// Everything a kernel needs to evaluate f_t for a row of the packed batch.
+template <class real>
+struct DynView {
+  int32_t kind, d, d_in, R;
+  real dt;
+  const real* params;
+  int64_t pstride;
+  const int32_t* topo;
+  int64_t tstride;
+  const real* x;          // packed inputs [N][d_in] or nullptr
+  const real* ma;         // mass-action tensors per sequence: [Lm d*d | Bm d*d*d]
+  int64_t ma_stride;      // 0 when shared
+  const real* gru_M;      // GRU: M[i][j] = Uh[i][j] * Ur[j][i]
+};
+
+// Row-to-sequence maps of a packed ragged batch.
+struct Batch {
+  int64_t B;
+  int64_t N;
+  const int64_t* offsets;      // [B+1]
+  const int64_t* chunk_first;  // [B+1]: first chunk index of each sequence
+  int64_t n_chunks;
+  int32_t L;                   // chunk length (power of two)
+  int32_t log2L;
+};
+
+__device__ __forceinline__ int64_t find_seq(const int64_t* __restrict__ off, int64_t B,
+                                            int64_t row) {
+  // largest b with off[b] <= row (off[B] = N > row). Empty sequences are skipped
+  // because equal offsets resolve to the last of them.
+  int64_t lo = 0, hi = B - 1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= row) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// chunk c -> (sequence, first row, row count)
+__device__ __forceinline__ void chunk_rows(const Batch& bt, int64_t c, int64_t& seq,
+                                           int64_t& r0, int32_t& n) {
+  seq = find_seq(bt.chunk_first, bt.B, c);
+  int64_t j = c - __ldg(bt.chunk_first + seq);
+  int64_t s0 = __ldg(bt.offsets + seq), s1 = __ldg(bt.offsets + seq + 1);
+  r0 = s0 + (j << bt.log2L);
+  int64_t e = r0 + bt.L;
+  n = (int32_t)((e < s1 ? e : s1) - r0);
+}
+
+__device__ __forceinline__ unsigned long long dbits(double v) {
+  return (unsigned long long)__double_as_longlong(v);
+}
+
+template <class real>
+__device__ __forceinline__ real rabs(real v) { return v < real(0) ? -v : v; }
+
+// NaN-propagating maximum of two non-negative doubles.
+__device__ __forceinline__ double nanmax(double a, double b) {
+  return (b > a || b != b) ? b : a;
+}
+
+// Accumulate |r| max and r^2 sum of one row into its sequence's accumulator. Must be
+// called by all 32 lanes of the warp. Lanes of a warp whose valid rows all belong to one
+// sequence reduce first and issue one atomic; otherwise each valid lane issues its own.
+// Non-negative doubles order like their bit patterns, and NaN sorts above +Inf, so the
+// integer atomicMax both takes the maximum and flags non-finite residuals.
+__device__ __forceinline__ void acc_resid(SeqAcc* acc, int64_t seq, bool valid, double mx,
+                                          double sq) {
+  const unsigned full = 0xffffffffu;
+  unsigned vm = __ballot_sync(full, valid);
+  if (vm == 0) return;
+  int src = __ffs(vm) - 1;
+  long long sseq = __shfl_sync(full, (long long)seq, src);
+  bool uniform = __all_sync(full, (!valid) || (seq == sseq));
+  if (uniform) {
+    if (!valid) { mx = 0.0; sq = 0.0; }
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = nanmax(mx, __shfl_xor_sync(full, mx, o));
+      sq += __shfl_xor_sync(full, sq, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(&acc[sseq].max_bits, dbits(mx));
+      atomicAdd(&acc[sseq].sumsq, sq);
+    }
+  } else if (valid) {
+    atomicMax(&acc[seq].max_bits, dbits(mx));
+    atomicAdd(&acc[seq].sumsq, sq);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launch bookkeeping (counted for deer_kernel_launch_count).
+// ---------------------------------------------------------------------------
+void note_launch(int n = 1);
+
+inline unsigned grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace deer

@@ -1,0 +1,543 @@
+// Linearisation / residual kernels, initial guesses, mass-action tensor set-up and the
+// sequential GPU rollout (comparison baseline).
+#include <cstdio>
+
+#include "dyn.cuh"
+#include "kernels.h"
+
+namespace deer {
+
+// ----------------------------------------------------------------------------
+// Mass-action tensors: L (unimolecular) and B_m (symmetrised bimolecular), per sequence.
+// ----------------------------------------------------------------------------
+template <class real>
+__global__ void k_ma_setup(int64_t n_seq, int d, int R, const real* __restrict__ k,
+                           int64_t kstride, const int32_t* __restrict__ topo, int64_t tstride,
+                           real* __restrict__ out, int64_t ostride, int32_t* bad) {
+  const int64_t seq = blockIdx.x;
+  if (seq >= n_seq) return;
+  real* L = out + seq * ostride;
+  real* Bm = L + d * d;
+  const int64_t n = (int64_t)d * d + (int64_t)d * d * d;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) L[i] = real(0);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const real* kk = k + seq * kstride;
+  const int32_t* tt = topo + seq * tstride;
+  for (int r = 0; r < R; ++r) {
+    const int i1 = tt[4 * r + 0], i2 = tt[4 * r + 1], p1 = tt[4 * r + 2], p2 = tt[4 * r + 3];
+    // species indices must lie in [0, d) (second slots may be -1); a bad reaction is
+    // skipped and reported instead of being written out of bounds
+    if (i1 < 0 || i1 >= d || p1 < 0 || p1 >= d || i2 < -1 || i2 >= d || p2 < -1 || p2 >= d) {
+      *bad = 1;
+      continue;
+    }
+    const real kr = kk[r];
+    int sp[4] = {i1, i2, p1, p2};
+    real nu[4] = {real(-1), real(-1), real(1), real(1)};
+    for (int q = 0; q < 4; ++q) {
+      const int i = sp[q];
+      if (i < 0) continue;
+      const real v = nu[q] * kr;
+      if (i2 < 0) {
+        L[i * d + i1] += v;  // rate k c_i1
+      } else {
+        Bm[((int64_t)i2 * d + i) * d + i1] += v;  // d/dc_i1 of k c_i1 c_i2 = k c_i2
+        Bm[((int64_t)i1 * d + i) * d + i2] += v;  // d/dc_i2 = k c_i1
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Row loads / stores with the widest aligned vector access.
+// ----------------------------------------------------------------------------
+template <class real, int D>
+__device__ __forceinline__ void load_row(const real* __restrict__ p, real* v) {
+  constexpr int bytes = D * (int)sizeof(real);
+  if constexpr (bytes % 16 == 0) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int i = 0; i < bytes / 16; ++i) {
+      float4 w = __ldg(q + i);
+      reinterpret_cast<float4*>(v)[i] = w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = __ldg(p + i);
+  }
+}
+
+template <class real, int D>
+__device__ __forceinline__ void store_row(real* __restrict__ p, const real* v) {
+  constexpr int bytes = D * (int)sizeof(real);
+  if constexpr (bytes % 16 == 0) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int i = 0; i < bytes / 16; ++i) q[i] = reinterpret_cast<const float4*>(v)[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < D; ++i) p[i] = v[i];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Initial guess
+// ----------------------------------------------------------------------------
+template <class real, int D, int KIND>
+__global__ void __launch_bounds__(128) k_init(InitArgs<real> a) {
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= a.bt.N) return;
+  const int64_t seq = find_seq(a.bt.offsets, a.bt.B, row);
+  real v[D];
+  if (a.init == DEER_INIT_ZEROS) {
+#pragma unroll Unroll<D>::n
+    for (int i = 0; i < D; ++i) v[i] = real(0);
+  } else if (a.init == DEER_INIT_S0) {
+#pragma unroll Unroll<D>::n
+    for (int i = 0; i < D; ++i) v[i] = a.s0[seq * D + i];
+  } else {  // Jacobi: f_t(0)
+    real z[D];
+#pragma unroll Unroll<D>::n
+    for (int i = 0; i < D; ++i) z[i] = real(0);
+    eval_f<real, D, KIND, 0>(a.dv, seq, row, z, v, nullptr, nullptr);
+  }
+  store_row<real, D>(a.s + row * D, v);
+}
+
+// ----------------------------------------------------------------------------
+// Linearise + residual (one thread per row): F_t = f_t(s_{t-1}), A~_t, r_t = s_t - F_t.
+//   FULL (correction form, Eq. lin_rr):  A[row] = A~_t (D x D), b[row] = -r_t
+//   DIAG family (standard form, Eq. quasi_lds): a[row] = diag A~_t (DIAG only),
+//                                               b[row] = F_t - a_t * s_{t-1}
+// Rows of converged sequences are skipped. max |r| and sum r^2 go to the sequence's
+// accumulator (float64).
+// ----------------------------------------------------------------------------
+template <class real, int D, int KIND, int JAC>
+__global__ void __launch_bounds__(128) k_linearize(LinArgs<real> a) {
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  bool valid = row < a.bt.N;
+  int64_t seq = 0;
+  double mx = 0.0, sq = 0.0;
+  if (valid) {
+    seq = find_seq(a.bt.offsets, a.bt.B, row);
+    valid = a.info[seq].done == 0;
+  }
+  if (valid) {
+    const int64_t first = __ldg(a.bt.offsets + seq);
+    real sp[D], sc[D], F[D];
+    if (row == first) {
+#pragma unroll Unroll<D>::n
+      for (int i = 0; i < D; ++i) sp[i] = __ldg(a.s0 + seq * D + i);
+    } else {
+      load_row<real, D>(a.s + (row - 1) * D, sp);
+    }
+    load_row<real, D>(a.s + row * D, sc);
+    const real k = a.dparam;
+    if constexpr (JAC == DEER_JAC_FULL) {
+      real A[D][D];
+      eval_f<real, D, KIND, 1>(a.dv, seq, row, sp, F, A, nullptr);
+      const real scale = (a.damp == DEER_DAMP_SCALE) ? real(1) - k : real(1);
+      real* Ao = a.A + row * (int64_t)(D * D);
+#pragma unroll Unroll<D>::n
+      for (int i = 0; i < D; ++i) {
+        real rowv[D];
+#pragma unroll Unroll<D>::n
+        for (int j = 0; j < D; ++j) rowv[j] = scale * A[i][j];
+        store_row<real, D>(Ao + i * D, rowv);
+      }
+      real b[D];
+#pragma unroll Unroll<D>::n
+      for (int i = 0; i < D; ++i) {
+        real r = sc[i] - F[i];
+        b[i] = -r;
+        const real sabs = rabs(sc[i]);
+        mx = nanmax(mx, (double)rabs(r) / (double)(sabs > real(1) ? sabs : real(1)));
+        sq += (double)r * (double)r;
+      }
+      store_row<real, D>(a.b + row * D, b);
+    } else {
+      real ad_[D];
+      if constexpr (JAC == DEER_JAC_DIAG) {
+        eval_f<real, D, KIND, 2>(a.dv, seq, row, sp, F, nullptr, ad_);
+      } else {
+        eval_f<real, D, KIND, 0>(a.dv, seq, row, sp, F, nullptr, nullptr);
+      }
+      real b[D];
+#pragma unroll Unroll<D>::n
+      for (int i = 0; i < D; ++i) {
+        real ai;
+        if constexpr (JAC == DEER_JAC_DIAG) ai = ad_[i];
+        else if constexpr (JAC == DEER_JAC_IDENTITY) ai = real(1);
+        else ai = real(0);
+        if (a.damp == DEER_DAMP_SCALE) ai *= (real(1) - k);
+        else if (a.damp == DEER_DAMP_CLIP) ai = ai > k ? k : (ai < -k ? -k : ai);
+        ad_[i] = ai;
+        b[i] = F[i] - ai * sp[i];
+        real r = sc[i] - F[i];
+        const real sabs = rabs(sc[i]);
+        mx = nanmax(mx, (double)rabs(r) / (double)(sabs > real(1) ? sabs : real(1)));
+        sq += (double)r * (double)r;
+      }
+      if constexpr (JAC == DEER_JAC_DIAG) store_row<real, D>(a.A + row * D, ad_);
+      store_row<real, D>(a.b + row * D, b);
+    }
+  }
+  acc_resid(a.acc, seq, valid, mx, sq);
+}
+
+
+// ----------------------------------------------------------------------------
+// Mass action, d <= 8: LPR lanes per row, each owning JC = D/LPR columns of A_t and the
+// rows h*JC .. h*JC+JC-1 of F_t, r_t and b_t (see ma_step_cols).
+// ----------------------------------------------------------------------------
+template <class real, int D, int LPR, bool RK4, int JAC>
+__global__ void __launch_bounds__(128) k_lin_ma(LinArgs<real> a) {
+  constexpr int JC = D / LPR;
+  constexpr bool WANTA = JAC == DEER_JAC_FULL || JAC == DEER_JAC_DIAG;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t row = tid / LPR;
+  const int h = LPR == 2 ? (int)(tid & 1) : 0;
+  bool valid = row < a.bt.N;
+  int64_t seq = 0;
+  if (valid) {
+    seq = find_seq(a.bt.offsets, a.bt.B, row);
+    valid = a.info[seq].done == 0;
+  }
+  double mx = 0.0, sq = 0.0;
+  if (valid) {
+    real sp[D], sc[JC];
+    if (row == __ldg(a.bt.offsets + seq)) {
+#pragma unroll
+      for (int i = 0; i < D; ++i) sp[i] = __ldg(a.s0 + seq * D + i);
+    } else {
+      load_row<real, D>(a.s + (row - 1) * D, sp);
+    }
+    load_row<real, JC>(a.s + row * D + h * JC, sc);
+    const real* T = a.dv.ma + seq * a.dv.ma_stride;
+    real F[D], A[D][JC];
+    ma_step_cols<real, D, LPR, RK4, WANTA>(T, a.dv.dt, h, sp, F, A);
+    const real k = a.dparam;
+    real b[JC];
+#pragma unroll
+    for (int ii = 0; ii < JC; ++ii) {
+      const real Fi = own_row<real, D, JC>(F, h, ii);
+      const real r = sc[ii] - Fi;
+      const real sabs = rabs(sc[ii]);
+      mx = nanmax(mx, (double)rabs(r) / (double)(sabs > real(1) ? sabs : real(1)));
+      sq += (double)r * (double)r;
+      b[ii] = -r;
+    }
+    if constexpr (JAC == DEER_JAC_FULL) {
+      const real scale = (a.damp == DEER_DAMP_SCALE) ? real(1) - k : real(1);
+      real* Ao = a.A + row * (int64_t)(D * D) + h * JC;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        real v[JC];
+#pragma unroll
+        for (int jj = 0; jj < JC; ++jj) v[jj] = scale * A[i][jj];
+        store_row<real, JC>(Ao + i * D, v);
+      }
+    } else {
+      real ad[JC];
+#pragma unroll
+      for (int ii = 0; ii < JC; ++ii) {
+        real ai;
+        if constexpr (JAC == DEER_JAC_DIAG) {
+          // diagonal entry (h*JC + ii, h*JC + ii) lives in own column ii
+          if constexpr (LPR == 1) ai = A[ii][ii];
+          else ai = h == 0 ? A[ii][ii] : A[JC + ii][ii];
+        } else if constexpr (JAC == DEER_JAC_IDENTITY) {
+          ai = real(1);
+        } else {
+          ai = real(0);
+        }
+        if (a.damp == DEER_DAMP_SCALE) ai *= (real(1) - k);
+        else if (a.damp == DEER_DAMP_CLIP) ai = ai > k ? k : (ai < -k ? -k : ai);
+        ad[ii] = ai;
+        // standard form: b = F - a s_{t-1}
+        b[ii] = own_row<real, D, JC>(F, h, ii) - ai * own_row<real, D, JC>(sp, h, ii);
+      }
+      if constexpr (JAC == DEER_JAC_DIAG) store_row<real, JC>(a.A + row * D + h * JC, ad);
+    }
+    store_row<real, JC>(a.b + row * D + h * JC, b);
+  }
+  acc_resid(a.acc, seq, valid, mx, sq);
+}
+
+// ----------------------------------------------------------------------------
+// Sequential rollout (baseline). Mass action: D lanes per trajectory, lane i owns species
+// i, one pass over the reactions per stage with shuffles for the reactant values (no
+// Jacobian). Other kinds: one thread per trajectory.
+// ----------------------------------------------------------------------------
+template <class real, int D>
+__device__ __forceinline__ real ma_lane_rate(const real* __restrict__ kk,
+                                             const int4* __restrict__ tt, int R, real c,
+                                             int lane, unsigned mask) {
+  real g = real(0);
+  for (int r = 0; r < R; ++r) {
+    const int4 q = __ldg(tt + r);
+    const real kr = __ldg(kk + r);
+    const real c1 = __shfl_sync(mask, c, q.x, D);
+    const real c2 = __shfl_sync(mask, c, q.y < 0 ? 0 : q.y, D);
+    const real rate = kr * c1 * (q.y < 0 ? real(1) : c2);
+    const real nu = real((lane == q.z) + (lane == q.w) - (lane == q.x) - (lane == q.y));
+    g += nu * rate;
+  }
+  return g;
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_rollout_ma(RolloutArgs<real> a, int rk4) {
+  constexpr int G = D;  // lanes per trajectory (D divides 32)
+  const int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  const int lane = threadIdx.x % G;
+  const int64_t seq = gid < a.B ? gid : a.B - 1;
+  const bool live = gid < a.B;
+  const unsigned mask = 0xffffffffu;
+  int64_t r0, r1;
+  rollout_rows(a, seq, r0, r1);
+  const real* kk = a.dv.params + seq * a.dv.pstride;
+  const int4* tt = reinterpret_cast<const int4*>(a.dv.topo + seq * a.dv.tstride);
+  const int R = a.dv.R;
+  const real h = a.dv.dt;
+  real c = a.s0[seq * D + lane];
+  const int64_t n = live ? r1 - r0 : 0;
+  // all groups of a warp iterate the warp maximum so that shuffles stay converged
+  int64_t nmax = n;
+  for (int o = 16; o > 0; o >>= 1) {
+    int64_t v = __shfl_xor_sync(mask, nmax, o);
+    nmax = v > nmax ? v : nmax;
+  }
+  for (int64_t t = 0; t < nmax; ++t) {
+    real cn;
+    if (!rk4) {
+      cn = c + h * ma_lane_rate<real, D>(kk, tt, R, c, lane, mask);
+    } else {
+      const real k1 = ma_lane_rate<real, D>(kk, tt, R, c, lane, mask);
+      const real k2 = ma_lane_rate<real, D>(kk, tt, R, c + real(0.5) * h * k1, lane, mask);
+      const real k3 = ma_lane_rate<real, D>(kk, tt, R, c + real(0.5) * h * k2, lane, mask);
+      const real k4 = ma_lane_rate<real, D>(kk, tt, R, c + h * k3, lane, mask);
+      cn = c + (h / real(6)) * (k1 + real(2) * k2 + real(2) * k3 + k4);
+    }
+    if (t < n) {
+      c = cn;
+      a.s[(r0 + t) * D + lane] = c;
+    }
+  }
+}
+
+template <class real, int D, int KIND>
+__global__ void __launch_bounds__(128) k_rollout_generic(RolloutArgs<real> a) {
+  const int64_t seq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (seq >= a.B) return;
+  int64_t r0, r1;
+  rollout_rows(a, seq, r0, r1);
+  real c[D], F[D];
+#pragma unroll Unroll<D>::n
+  for (int i = 0; i < D; ++i) c[i] = a.s0[seq * D + i];
+  for (int64_t row = r0; row < r1; ++row) {
+    eval_f<real, D, KIND, 0>(a.dv, seq, row, c, F, nullptr, nullptr);
+#pragma unroll Unroll<D>::n
+    for (int i = 0; i < D; ++i) c[i] = F[i];
+    store_row<real, D>(a.s + row * D, c);
+  }
+}
+
+// GRU set-up: M[i][j] = Uh[i][j] * Ur[j][i], the matrix of the off-diagonal term of the
+// closed-form Jacobian diagonal.
+template <class real>
+__global__ void k_gru_setup(int d, const real* __restrict__ params, int d_in, real* M) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= d * d) return;
+  const int i = id / d, j = id % d;
+  const real* Ur = params + 3 * d * d_in + d * d;
+  const real* Uh = Ur + d * d;
+  M[id] = Uh[i * d + j] * Ur[j * d + i];
+}
+
+// ----------------------------------------------------------------------------
+// Host-side dispatch
+// ----------------------------------------------------------------------------
+template <class real>
+cudaError_t launch_gru_setup(int d, const real* params, int d_in, real* M, cudaStream_t st) {
+  k_gru_setup<real><<<grid_for(d * d, 128), 128, 0, st>>>(d, params, d_in, M);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <class real>
+cudaError_t launch_ma_setup(int64_t n_seq, int d, int R, const real* k, int64_t kstride,
+                            const int32_t* topo, int64_t tstride, real* out, int64_t ostride,
+                            int32_t* bad, cudaStream_t st) {
+  k_ma_setup<real><<<(unsigned)n_seq, 128, 0, st>>>(n_seq, d, R, k, kstride, topo, tstride, out,
+                                                    ostride, bad);
+  note_launch();
+  return cudaGetLastError();
+}
+
+#define DEER_FOR_D(X) X(1) X(2) X(4) X(8) X(16) X(32)
+
+template <class real, int KIND>
+static cudaError_t init_kind(const InitArgs<real>& a, cudaStream_t st) {
+  const unsigned g = grid_for(a.bt.N, 128);
+  switch (a.dv.d) {
+#define CASE(DD) \
+  case DD:       \
+    k_init<real, DD, KIND><<<g, 128, 0, st>>>(a); break;
+    DEER_FOR_D(CASE)
+#undef CASE
+    case 64:
+      if constexpr (KIND == DEER_F_GRU) { k_init<real, 64, KIND><<<g, 128, 0, st>>>(a); break; }
+      return cudaErrorInvalidValue;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <class real>
+cudaError_t launch_init(const InitArgs<real>& a, cudaStream_t st) {
+  if (a.bt.N == 0) return cudaSuccess;
+  switch (a.dv.kind) {
+    case DEER_F_BRUSSELATOR_EULER: return init_kind<real, DEER_F_BRUSSELATOR_EULER>(a, st);
+    case DEER_F_MASSACTION_EULER: return init_kind<real, DEER_F_MASSACTION_EULER>(a, st);
+    case DEER_F_MASSACTION_RK4: return init_kind<real, DEER_F_MASSACTION_RK4>(a, st);
+    case DEER_F_GRU: return init_kind<real, DEER_F_GRU>(a, st);
+    default: return init_kind<real, DEER_F_LINEAR>(a, st);
+  }
+}
+
+template <class real, int KIND, int JAC>
+static cudaError_t lin_kind_jac(const LinArgs<real>& a, cudaStream_t st) {
+  const unsigned g = grid_for(a.bt.N, 128);
+  const int d = a.dv.d;
+  if constexpr (KIND == DEER_F_MASSACTION_EULER || KIND == DEER_F_MASSACTION_RK4) {
+    constexpr bool RK4 = KIND == DEER_F_MASSACTION_RK4;
+    if (d <= 8) {
+      switch (d) {
+        case 2: k_lin_ma<real, 2, 1, RK4, JAC><<<g, 128, 0, st>>>(a); break;
+        case 4: k_lin_ma<real, 4, 1, RK4, JAC><<<g, 128, 0, st>>>(a); break;
+        case 8:
+          if constexpr (sizeof(real) == 4) {
+            k_lin_ma<real, 8, 1, RK4, JAC><<<g, 128, 0, st>>>(a);
+          } else {
+            k_lin_ma<real, 8, 2, RK4, JAC><<<grid_for(a.bt.N * 2, 128), 128, 0, st>>>(a);
+          }
+          break;
+        default: return cudaErrorInvalidValue;
+      }
+      note_launch();
+      return cudaGetLastError();
+    }
+  }
+  if constexpr (KIND == DEER_F_BRUSSELATOR_EULER) {
+    if (d != 2) return cudaErrorInvalidValue;
+    k_linearize<real, 2, KIND, JAC><<<g, 128, 0, st>>>(a);
+  } else {
+    switch (d) {
+#define CASE(DD) \
+  case DD:       \
+    k_linearize<real, DD, KIND, JAC><<<g, 128, 0, st>>>(a); break;
+      DEER_FOR_D(CASE)
+#undef CASE
+      case 64:
+        if constexpr (KIND == DEER_F_GRU && JAC != DEER_JAC_FULL) {
+          k_linearize<real, 64, KIND, JAC><<<g, 128, 0, st>>>(a);
+          break;
+        }
+        return cudaErrorInvalidValue;
+      default:
+        return cudaErrorInvalidValue;
+    }
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <class real, int KIND>
+static cudaError_t lin_kind(const LinArgs<real>& a, cudaStream_t st) {
+  switch (a.jac) {
+    case DEER_JAC_FULL: return lin_kind_jac<real, KIND, DEER_JAC_FULL>(a, st);
+    case DEER_JAC_DIAG: return lin_kind_jac<real, KIND, DEER_JAC_DIAG>(a, st);
+    case DEER_JAC_IDENTITY: return lin_kind_jac<real, KIND, DEER_JAC_IDENTITY>(a, st);
+    default: return lin_kind_jac<real, KIND, DEER_JAC_ZERO>(a, st);
+  }
+}
+
+template <class real>
+cudaError_t launch_linearize(const LinArgs<real>& a, cudaStream_t st) {
+  if (a.bt.N == 0) return cudaSuccess;
+  switch (a.dv.kind) {
+    case DEER_F_BRUSSELATOR_EULER: return lin_kind<real, DEER_F_BRUSSELATOR_EULER>(a, st);
+    case DEER_F_MASSACTION_EULER: return lin_kind<real, DEER_F_MASSACTION_EULER>(a, st);
+    case DEER_F_MASSACTION_RK4: return lin_kind<real, DEER_F_MASSACTION_RK4>(a, st);
+    case DEER_F_GRU: return lin_kind<real, DEER_F_GRU>(a, st);
+    default: return lin_kind<real, DEER_F_LINEAR>(a, st);
+  }
+}
+
+template <class real, int KIND>
+static cudaError_t rollout_generic(const RolloutArgs<real>& a, cudaStream_t st) {
+  const unsigned g = grid_for(a.B, 128);
+  switch (a.dv.d) {
+#define CASE(DD) \
+  case DD:       \
+    k_rollout_generic<real, DD, KIND><<<g, 128, 0, st>>>(a); break;
+    DEER_FOR_D(CASE)
+#undef CASE
+    case 64:
+      if constexpr (KIND == DEER_F_GRU) { k_rollout_generic<real, 64, KIND><<<g, 128, 0, st>>>(a); break; }
+      return cudaErrorInvalidValue;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <class real>
+cudaError_t launch_rollout(const RolloutArgs<real>& a, cudaStream_t st) {
+  if (a.B == 0) return cudaSuccess;
+  const int kind = a.dv.kind;
+  if (kind == DEER_F_MASSACTION_EULER || kind == DEER_F_MASSACTION_RK4) {
+    const int rk4 = kind == DEER_F_MASSACTION_RK4;
+    const int d = a.dv.d;
+    const int64_t threads = a.B * (int64_t)d;
+    const unsigned g = grid_for(threads, 128);
+    switch (d) {
+      case 2: k_rollout_ma<real, 2><<<g, 128, 0, st>>>(a, rk4); break;
+      case 4: k_rollout_ma<real, 4><<<g, 128, 0, st>>>(a, rk4); break;
+      case 8: k_rollout_ma<real, 8><<<g, 128, 0, st>>>(a, rk4); break;
+      case 16: k_rollout_ma<real, 16><<<g, 128, 0, st>>>(a, rk4); break;
+      case 32: k_rollout_ma<real, 32><<<g, 128, 0, st>>>(a, rk4); break;
+      default: return cudaErrorInvalidValue;
+    }
+    note_launch();
+    return cudaGetLastError();
+  }
+  switch (kind) {
+    case DEER_F_BRUSSELATOR_EULER: {
+      k_rollout_generic<real, 2, DEER_F_BRUSSELATOR_EULER><<<grid_for(a.B, 128), 128, 0, st>>>(a);
+      note_launch();
+      return cudaGetLastError();
+    }
+    case DEER_F_GRU: return rollout_generic<real, DEER_F_GRU>(a, st);
+    default: return rollout_generic<real, DEER_F_LINEAR>(a, st);
+  }
+}
+
+#define DEER_INST(real)                                                                         \
+  template cudaError_t launch_ma_setup<real>(int64_t, int, int, const real*, int64_t,          \
+                                             const int32_t*, int64_t, real*, int64_t,          \
+                                             int32_t*, cudaStream_t);                          \
+  template cudaError_t launch_init<real>(const InitArgs<real>&, cudaStream_t);                 \
+  template cudaError_t launch_linearize<real>(const LinArgs<real>&, cudaStream_t);             \
+  template cudaError_t launch_rollout<real>(const RolloutArgs<real>&, cudaStream_t);          \
+  template cudaError_t launch_gru_setup<real>(int, const real*, int, real*, cudaStream_t);
+DEER_INST(float)
+DEER_INST(double)
+#undef DEER_INST
+
+}  // namespace deer

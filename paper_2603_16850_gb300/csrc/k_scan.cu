@@ -1,0 +1,390 @@
+// Convergence check and the chunked parallel scans (dense and diagonal families).
+//
+// Scan structure (three phases, no host involvement): every chunk of L consecutive rows
+// of one sequence is reduced to its aggregate under the affine composition of Eq.
+// bin_op_affine, (A_j, b_j) o (A_i, b_i) = (A_j A_i, b_j + A_j b_i); a per-sequence pass
+// composes the chunk aggregates in order (the operation does not commute) to obtain the
+// state entering every chunk; a final pass re-runs each chunk from its carry.
+#include <cfloat>
+
+#include "kernels.h"
+
+namespace deer {
+
+// ----------------------------------------------------------------------------
+// Convergence / merit (one block): per sequence max |r| vs tol (float64), merit 1/2 |r|^2.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_check(CheckArgs a) {
+  __shared__ int s_active, s_nonfinite;
+  __shared__ unsigned long long s_rows;
+  if (threadIdx.x == 0) { s_active = 0; s_nonfinite = 0; s_rows = 0ull; }
+  __syncthreads();
+  int active = 0, nonfinite = 0;
+  unsigned long long rows = 0;
+  for (int64_t seq = threadIdx.x; seq < a.B; seq += blockDim.x) {
+    SeqInfo inf = a.info[seq];
+    if (inf.done) continue;
+    SeqAcc acc = a.acc[seq];
+    a.acc[seq] = SeqAcc{0ull, 0.0};
+    const double mr = __longlong_as_double((long long)acc.max_bits);
+    inf.max_resid = mr;
+    inf.merit = 0.5 * acc.sumsq;
+    if (!(mr <= DBL_MAX)) ++nonfinite;  // NaN or Inf
+    if (mr <= a.tol) {
+      inf.done = 1;
+      inf.iters = a.it;
+    } else {
+      inf.iters = a.it < a.max_iters ? a.it + 1 : a.it;
+      ++active;
+      rows += (unsigned long long)(a.offsets[seq + 1] - a.offsets[seq]);
+    }
+    a.info[seq] = inf;
+  }
+  if (active) atomicAdd(&s_active, active);
+  if (nonfinite) atomicAdd(&s_nonfinite, nonfinite);
+  if (rows) atomicAdd(&s_rows, rows);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.flags->n_active = s_active;
+    a.flags->n_nonfinite = s_nonfinite;
+    a.flags->active_rows = (long long)s_rows;
+  }
+}
+
+cudaError_t launch_check(const CheckArgs& a, cudaStream_t st) {
+  k_check<<<1, 1024, 0, st>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int D>
+struct U { static constexpr int n = D <= 8 ? D : 1; };
+
+template <class real>
+__device__ __forceinline__ real reset_val(real v, real thr, int reset) {
+  if (reset && !(v <= thr && v >= -thr)) return real(0);
+  return v;
+}
+
+// ----------------------------------------------------------------------------
+// Dense scan (one thread per chunk)
+// ----------------------------------------------------------------------------
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_dense_chunk(DenseScanArgs<real> a) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= a.bt.n_chunks) return;
+  int64_t seq, r0;
+  int n;
+  chunk_rows(a.bt, c, seq, r0, n);
+  if (a.info[seq].done) return;
+  // the first chunk of a sequence starts from Delta_0 = 0: its carry never multiplies P
+  const bool need_P = c != __ldg(a.bt.chunk_first + seq);
+  real P[D][D], v[D];
+#pragma unroll U<D>::n
+  for (int i = 0; i < D; ++i) {
+    v[i] = real(0);
+#pragma unroll U<D>::n
+    for (int j = 0; j < D; ++j) P[i][j] = (i == j) ? real(1) : real(0);
+  }
+  for (int t = 0; t < n; ++t) {
+    const real* At = a.A + (r0 + t) * (int64_t)(D * D);
+    const real* bt = a.b + (r0 + t) * D;
+    real nv[D];
+#pragma unroll U<D>::n
+    for (int i = 0; i < D; ++i) {
+      real acc = __ldg(bt + i);
+#pragma unroll U<D>::n
+      for (int k = 0; k < D; ++k) acc += __ldg(At + i * D + k) * v[k];
+      nv[i] = acc;
+    }
+#pragma unroll U<D>::n
+    for (int i = 0; i < D; ++i) v[i] = nv[i];
+    if (need_P) {
+      real NP[D][D];
+#pragma unroll U<D>::n
+      for (int i = 0; i < D; ++i)
+#pragma unroll U<D>::n
+        for (int j = 0; j < D; ++j) {
+          real acc = real(0);
+#pragma unroll U<D>::n
+          for (int k = 0; k < D; ++k) acc += __ldg(At + i * D + k) * P[k][j];
+          NP[i][j] = acc;
+        }
+#pragma unroll U<D>::n
+      for (int i = 0; i < D; ++i)
+#pragma unroll U<D>::n
+        for (int j = 0; j < D; ++j) P[i][j] = NP[i][j];
+    }
+  }
+  real* Po = a.aggP + c * (int64_t)(D * D);
+  real* vo = a.aggv + c * D;
+#pragma unroll U<D>::n
+  for (int i = 0; i < D; ++i) {
+    vo[i] = v[i];
+#pragma unroll U<D>::n
+    for (int j = 0; j < D; ++j) Po[i * D + j] = P[i][j];
+  }
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_dense_carry(DenseScanArgs<real> a) {
+  const int64_t seq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (seq >= a.bt.B) return;
+  if (a.info[seq].done) return;
+  const int64_t c0 = a.bt.chunk_first[seq], c1 = a.bt.chunk_first[seq + 1];
+  real x[D];
+#pragma unroll U<D>::n
+  for (int i = 0; i < D; ++i) x[i] = real(0);
+  for (int64_t c = c0; c < c1; ++c) {
+    real* ci = a.cin + c * D;
+#pragma unroll U<D>::n
+    for (int i = 0; i < D; ++i) ci[i] = x[i];
+    if (c == c1 - 1) break;
+    const real* P = a.aggP + c * (int64_t)(D * D);
+    const real* v = a.aggv + c * D;
+    real nx[D];
+    if (c == c0) {
+#pragma unroll U<D>::n
+      for (int i = 0; i < D; ++i) nx[i] = v[i];
+    } else {
+#pragma unroll U<D>::n
+      for (int i = 0; i < D; ++i) {
+        real acc = v[i];
+#pragma unroll U<D>::n
+        for (int k = 0; k < D; ++k) acc += P[i * D + k] * x[k];
+        nx[i] = acc;
+      }
+    }
+#pragma unroll U<D>::n
+    for (int i = 0; i < D; ++i) x[i] = nx[i];
+  }
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_dense_apply(DenseScanArgs<real> a) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= a.bt.n_chunks) return;
+  int64_t seq, r0;
+  int n;
+  chunk_rows(a.bt, c, seq, r0, n);
+  if (a.info[seq].done) return;
+  real x[D];
+#pragma unroll U<D>::n
+  for (int i = 0; i < D; ++i) x[i] = a.cin[c * D + i];
+  for (int t = 0; t < n; ++t) {
+    const int64_t row = r0 + t;
+    const real* At = a.A + row * (int64_t)(D * D);
+    const real* bt = a.b + row * D;
+    real nx[D];
+#pragma unroll U<D>::n
+    for (int i = 0; i < D; ++i) {
+      real acc = __ldg(bt + i);
+#pragma unroll U<D>::n
+      for (int k = 0; k < D; ++k) acc += __ldg(At + i * D + k) * x[k];
+      nx[i] = acc;
+    }
+    real* sr = a.s + row * D;
+#pragma unroll U<D>::n
+    for (int i = 0; i < D; ++i) {
+      x[i] = nx[i];
+      sr[i] = reset_val(sr[i] + nx[i], a.reset_thr, a.reset);
+    }
+  }
+}
+
+template <class real, int D>
+static void dense_launch(const DenseScanArgs<real>& a, cudaStream_t st) {
+  const unsigned gc = grid_for(a.bt.n_chunks, 128);
+  const unsigned gs = grid_for(a.bt.B, 128);
+  k_dense_chunk<real, D><<<gc, 128, 0, st>>>(a);
+  k_dense_carry<real, D><<<gs, 128, 0, st>>>(a);
+  k_dense_apply<real, D><<<gc, 128, 0, st>>>(a);
+  note_launch(3);
+}
+
+template <class real>
+cudaError_t launch_dense_scan(const DenseScanArgs<real>& a, cudaStream_t st) {
+  if (a.bt.N == 0) return cudaSuccess;
+  switch (a.d) {
+    case 1: dense_launch<real, 1>(a, st); break;
+    case 2: dense_launch<real, 2>(a, st); break;
+    case 4: dense_launch<real, 4>(a, st); break;
+    case 8: dense_launch<real, 8>(a, st); break;
+    case 16: dense_launch<real, 16>(a, st); break;
+    case 32: dense_launch<real, 32>(a, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Diagonal family (one thread per (chunk, coordinate))
+// ----------------------------------------------------------------------------
+template <class real>
+__device__ __forceinline__ void diag_elem(const DiagScanArgs<real>& a, int64_t row, int j,
+                                          real& at, real& bt) {
+  at = a.amode == 0 ? __ldg(a.a + row * a.d + j) : a.aconst;
+  bt = __ldg(a.b + row * a.d + j);
+  if (a.elk) {
+    // filtered mean mu_t = Gamma_t a_t mu_{t-1} + Gamma_t b_t + (1 - Gamma_t) y_t
+    const real g = a.gam[row * a.d + j];
+    const real y = a.s[row * a.d + j];
+    bt = g * bt + (real(1) - g) * y;
+    at = g * at;
+  }
+}
+
+template <class real>
+__global__ void __launch_bounds__(128) k_diag_chunk(DiagScanArgs<real> a) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= a.bt.n_chunks * a.d) return;
+  const int64_t c = id / a.d;
+  const int j = (int)(id - c * a.d);
+  int64_t seq, r0;
+  int n;
+  chunk_rows(a.bt, c, seq, r0, n);
+  if (a.info[seq].done) return;
+  real A = real(1), Bv = real(0);
+  for (int t = 0; t < n; ++t) {
+    real at, bt;
+    diag_elem(a, r0 + t, j, at, bt);
+    Bv = at * Bv + bt;
+    A = at * A;
+  }
+  a.aggA[c * a.d + j] = A;
+  a.aggB[c * a.d + j] = Bv;
+}
+
+template <class real>
+__global__ void __launch_bounds__(128) k_diag_carry(DiagScanArgs<real> a) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= a.bt.B * a.d) return;
+  const int64_t seq = id / a.d;
+  const int j = (int)(id - seq * a.d);
+  if (a.info[seq].done) return;
+  real x = a.s0[seq * a.d + j];
+  const int64_t c0 = a.bt.chunk_first[seq], c1 = a.bt.chunk_first[seq + 1];
+  for (int64_t c = c0; c < c1; ++c) {
+    a.cin[c * a.d + j] = x;
+    x = a.aggA[c * a.d + j] * x + a.aggB[c * a.d + j];
+  }
+}
+
+template <class real>
+__global__ void __launch_bounds__(128) k_diag_apply(DiagScanArgs<real> a) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= a.bt.n_chunks * a.d) return;
+  const int64_t c = id / a.d;
+  const int j = (int)(id - c * a.d);
+  int64_t seq, r0;
+  int n;
+  chunk_rows(a.bt, c, seq, r0, n);
+  if (a.info[seq].done) return;
+  real x = a.cin[c * a.d + j];
+  for (int t = 0; t < n; ++t) {
+    real at, bt;
+    diag_elem(a, r0 + t, j, at, bt);
+    x = at * x + bt;
+    a.s[(r0 + t) * a.d + j] = reset_val(x, a.reset_thr, a.reset);
+  }
+}
+
+// --- Kalman-filter damping (quasi-ELK), per coordinate -----------------------
+// The filtered variance obeys P_t = sigma2 (a_t^2 P_{t-1} + 1) / (a_t^2 P_{t-1} + 1 + sigma2),
+// a linear-fractional (Moebius) map of P_{t-1} with matrix
+// [[sigma2 a^2, sigma2], [a^2, 1 + sigma2]]; maps compose by matrix product, scaled by
+// their largest entry to stay finite (a Moebius map is invariant under scaling).
+template <class real>
+__device__ __forceinline__ void mob_elem(real at, real s2, real& m00, real& m01, real& m10,
+                                         real& m11) {
+  const real a2 = at * at;
+  m00 = s2 * a2; m01 = s2; m10 = a2; m11 = real(1) + s2;
+}
+
+template <class real>
+__global__ void __launch_bounds__(128) k_elk_chunk(DiagScanArgs<real> a) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= a.bt.n_chunks * a.d) return;
+  const int64_t c = id / a.d;
+  const int j = (int)(id - c * a.d);
+  int64_t seq, r0;
+  int n;
+  chunk_rows(a.bt, c, seq, r0, n);
+  if (a.info[seq].done) return;
+  real p00 = 1, p01 = 0, p10 = 0, p11 = 1;
+  for (int t = 0; t < n; ++t) {
+    const int64_t row = r0 + t;
+    const real at = a.amode == 0 ? __ldg(a.a + row * a.d + j) : a.aconst;
+    real m00, m01, m10, m11;
+    mob_elem(at, a.sigma2, m00, m01, m10, m11);
+    real q00 = m00 * p00 + m01 * p10, q01 = m00 * p01 + m01 * p11;
+    real q10 = m10 * p00 + m11 * p10, q11 = m10 * p01 + m11 * p11;
+    real mx = fmax(fmax(fabs(q00), fabs(q01)), fmax(fabs(q10), fabs(q11)));
+    real inv = mx > real(0) ? real(1) / mx : real(1);
+    p00 = q00 * inv; p01 = q01 * inv; p10 = q10 * inv; p11 = q11 * inv;
+  }
+  real* o = a.mob + (c * a.d + j) * 4;
+  o[0] = p00; o[1] = p01; o[2] = p10; o[3] = p11;
+}
+
+template <class real>
+__global__ void __launch_bounds__(128) k_elk_carry(DiagScanArgs<real> a) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= a.bt.B * a.d) return;
+  const int64_t seq = id / a.d;
+  const int j = (int)(id - seq * a.d);
+  if (a.info[seq].done) return;
+  real P = real(0);  // s_0 is known exactly
+  const int64_t c0 = a.bt.chunk_first[seq], c1 = a.bt.chunk_first[seq + 1];
+  for (int64_t c = c0; c < c1; ++c) {
+    a.pin[c * a.d + j] = P;
+    const real* m = a.mob + (c * a.d + j) * 4;
+    P = (m[0] * P + m[1]) / (m[2] * P + m[3]);
+  }
+}
+
+template <class real>
+__global__ void __launch_bounds__(128) k_elk_gamma(DiagScanArgs<real> a) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= a.bt.n_chunks * a.d) return;
+  const int64_t c = id / a.d;
+  const int j = (int)(id - c * a.d);
+  int64_t seq, r0;
+  int n;
+  chunk_rows(a.bt, c, seq, r0, n);
+  if (a.info[seq].done) return;
+  real P = a.pin[c * a.d + j];
+  for (int t = 0; t < n; ++t) {
+    const int64_t row = r0 + t;
+    const real at = a.amode == 0 ? __ldg(a.a + row * a.d + j) : a.aconst;
+    const real Pm = at * at * P + real(1);   // predicted variance
+    const real g = a.sigma2 / (Pm + a.sigma2);  // attenuation Gamma_t = 1 - gain
+    a.gam[row * a.d + j] = g;
+    P = g * Pm;                              // filtered variance
+  }
+}
+
+template <class real>
+cudaError_t launch_diag_scan(const DiagScanArgs<real>& a, cudaStream_t st) {
+  if (a.bt.N == 0) return cudaSuccess;
+  const unsigned gc = grid_for(a.bt.n_chunks * a.d, 128);
+  const unsigned gs = grid_for(a.bt.B * a.d, 128);
+  if (a.elk) {
+    k_elk_chunk<real><<<gc, 128, 0, st>>>(a);
+    k_elk_carry<real><<<gs, 128, 0, st>>>(a);
+    k_elk_gamma<real><<<gc, 128, 0, st>>>(a);
+    note_launch(3);
+  }
+  k_diag_chunk<real><<<gc, 128, 0, st>>>(a);
+  k_diag_carry<real><<<gs, 128, 0, st>>>(a);
+  k_diag_apply<real><<<gc, 128, 0, st>>>(a);
+  note_launch(3);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_dense_scan<float>(const DenseScanArgs<float>&, cudaStream_t);
+template cudaError_t launch_dense_scan<double>(const DenseScanArgs<double>&, cudaStream_t);
+template cudaError_t launch_diag_scan<float>(const DiagScanArgs<float>&, cudaStream_t);
+template cudaError_t launch_diag_scan<double>(const DiagScanArgs<double>&, cudaStream_t);
+
+}  // namespace deer

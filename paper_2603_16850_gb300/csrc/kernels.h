@@ -1,0 +1,122 @@
+// Argument blocks and launchers shared between the kernel translation units and the
+// host API. Internal to the library (not part of the C ABI).
+#pragma once
+
+#include "common.cuh"
+
+namespace deer {
+
+template <class real>
+struct InitArgs {
+  DynView<real> dv;
+  Batch bt;
+  const real* s0;
+  real* s;
+  int init;
+};
+
+template <class real>
+struct LinArgs {
+  DynView<real> dv;
+  Batch bt;
+  const real* s0;
+  const real* s;   // current iterate [N][d]
+  real* A;         // FULL: [N][d][d]; DIAG: [N][d]; unused otherwise
+  real* b;         // [N][d]
+  SeqAcc* acc;
+  const SeqInfo* info;
+  int jac, damp;
+  real dparam;
+};
+
+template <class real>
+struct RolloutArgs {
+  DynView<real> dv;
+  int64_t B;
+  int64_t T;               // uniform length when offsets == nullptr
+  const int64_t* offsets;  // device [B+1] or nullptr
+  const real* s0;
+  real* s;
+};
+
+template <class real>
+__device__ __forceinline__ void rollout_rows(const RolloutArgs<real>& a, int64_t seq,
+                                             int64_t& r0, int64_t& r1) {
+  if (a.offsets) { r0 = a.offsets[seq]; r1 = a.offsets[seq + 1]; }
+  else { r0 = seq * a.T; r1 = r0 + a.T; }
+}
+
+struct CheckArgs {
+  int64_t B;
+  const int64_t* offsets;
+  SeqAcc* acc;
+  SeqInfo* info;
+  Flags* flags;
+  double tol;
+  int it, max_iters;
+};
+
+// Dense (FULL) correction-form scan: Delta_t = A_t Delta_{t-1} + b_t, Delta_0 = 0,
+// then s_t += Delta_t. Chunk aggregates hold (P, v) = (A_n...A_1, local Delta).
+template <class real>
+struct DenseScanArgs {
+  Batch bt;
+  int d;
+  const real* A;   // [N][d][d]
+  const real* b;   // [N][d]
+  real* s;         // [N][d] updated in place
+  real* aggP;      // [n_chunks][d][d]
+  real* aggv;      // [n_chunks][d]
+  real* cin;       // [n_chunks][d] carry into each chunk
+  const SeqInfo* info;
+  int reset;
+  real reset_thr;
+};
+
+// Diagonal-family scan in standard form: s_t = a_t s_{t-1} + b_t from s_0, where a_t is
+// read (DIAG), a constant (IDENTITY / ZERO, after damping), or the Kalman-damped
+// transition Gamma_t a_t with offset Gamma_t b_t + (1 - Gamma_t) y_t (ELK).
+template <class real>
+struct DiagScanArgs {
+  Batch bt;
+  int d;
+  int amode;        // 0 = read a, 1 = constant aconst
+  real aconst;
+  const real* a;    // [N][d]
+  const real* b;    // [N][d]
+  const real* s0;   // [B][d]
+  real* s;          // [N][d]: input y (ELK emissions) and output
+  real* aggA;       // [n_chunks][d]
+  real* aggB;       // [n_chunks][d]
+  real* cin;        // [n_chunks][d]
+  const SeqInfo* info;
+  int elk;          // 1: Kalman-filter damping with sigma2 = 1/lambda
+  real sigma2;
+  real* gam;        // [N][d] attenuation Gamma_t (ELK)
+  real* mob;        // [n_chunks][d][4] Moebius aggregates (ELK)
+  real* pin;        // [n_chunks][d] filtered variance entering each chunk (ELK)
+  int reset;
+  real reset_thr;
+};
+
+template <class real>
+cudaError_t launch_ma_setup(int64_t n_seq, int d, int R, const real* k, int64_t kstride,
+                            const int32_t* topo, int64_t tstride, real* out, int64_t ostride,
+                            int32_t* bad, cudaStream_t st);
+template <class real>
+cudaError_t launch_init(const InitArgs<real>& a, cudaStream_t st);
+template <class real>
+cudaError_t launch_linearize(const LinArgs<real>& a, cudaStream_t st);
+template <class real>
+cudaError_t launch_rollout(const RolloutArgs<real>& a, cudaStream_t st);
+template <class real>
+cudaError_t launch_gru_setup(int d, const real* params, int d_in, real* M, cudaStream_t st);
+
+cudaError_t launch_check(const CheckArgs& a, cudaStream_t st);
+
+template <class real>
+cudaError_t launch_dense_scan(const DenseScanArgs<real>& a, cudaStream_t st);
+template <class real>
+cudaError_t launch_diag_scan(const DiagScanArgs<real>& a, cudaStream_t st);
+
+}  // namespace deer

@@ -1,0 +1,103 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads and exports
+every function include/deer.h declares; argument validation and workspace sizing run
+without touching the device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2603_16850_gb300 import _build, _native
+    _build.build()
+    return _native.load()
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(deer_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2603_16850_gb300 import _native
+    declared = _declared_functions()
+    assert "deer_solve" in declared and "deer_grad" in declared and "deer_solve_batched" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    # the Python binding covers the same set
+    assert declared <= set(_native.SIGNATURES), declared - set(_native.SIGNATURES)
+
+
+def test_defaults_and_strings(lib):
+    from paper_2603_16850_gb300 import _native as N
+    o = N.deer_options()
+    lib.deer_default_options(C.byref(o))
+    assert o.tol == 1e-10 and o.jac == 0 and o.init == 1 and o.prec == 0
+    assert lib.deer_status_string(0) == b"ok"
+    assert b"invalid" in lib.deer_status_string(-1)
+    assert lib.deer_version() >= 1
+
+
+def _dyn(N, kind="massaction_rk4", d=8, R=12, params=1, topo=1):
+    return N.deer_dynamics(N.KIND[kind], d, 0, R, 1e-3, params, R, topo, 4 * R)
+
+
+def test_workspace_sizes_and_validation(lib):
+    from paper_2603_16850_gb300 import _native as N
+    o = N.deer_options()
+    lib.deer_default_options(C.byref(o))
+    o.prec = N.PREC["fp32"]
+    dyn = _dyn(N)
+    b = lib.deer_workspace_bytes(C.byref(dyn), 4096, 4096 * 16384, C.byref(o))
+    # the dense Jacobians dominate: 4096*16384 rows * 8*8 float32
+    assert b >= 4096 * 16384 * 64 * 4
+    o.jac = N.JAC["diag"]
+    bd = lib.deer_workspace_bytes(C.byref(dyn), 4096, 4096 * 16384, C.byref(o))
+    assert 0 < bd < b
+    # unsupported state size / invalid combination -> 0
+    bad = _dyn(N, d=3)
+    assert lib.deer_workspace_bytes(C.byref(bad), 1, 10, C.byref(o)) == 0
+    o.jac = N.JAC["full"]
+    o.damp = N.DAMP["elk"]
+    assert lib.deer_workspace_bytes(C.byref(dyn), 1, 10, C.byref(o)) == 0
+
+
+def test_invalid_arguments_fail_without_device_work(lib):
+    from paper_2603_16850_gb300 import _native as N
+    o = N.deer_options()
+    lib.deer_default_options(C.byref(o))
+    dyn = _dyn(N)
+    info = (N.deer_info * 1)()
+    # empty batch: nothing to do
+    assert lib.deer_solve(C.byref(dyn), 0, 10, None, None, None, C.byref(o), None, 0, None,
+                          info) == 0
+    # null state pointers
+    assert lib.deer_solve(C.byref(dyn), 1, 10, None, None, None, C.byref(o), None, 0, None,
+                          info) == N.DEER_ERR_INVALID
+    # bad enum
+    o.jac = 9
+    assert lib.deer_solve(C.byref(dyn), 1, 10, 8, None, 8, C.byref(o), None, 0, None,
+                          info) == N.DEER_ERR_INVALID
+    lib.deer_default_options(C.byref(o))
+    # decreasing offsets
+    off = (C.c_int64 * 3)(0, 5, 3)
+    assert lib.deer_solve_batched(C.byref(dyn), 2, off, 8, None, 8, C.byref(o), None, 0, None,
+                                  info) == N.DEER_ERR_INVALID
+    # missing topology for mass action
+    nd = _dyn(N, topo=0)
+    assert lib.deer_solve(C.byref(nd), 1, 10, 8, None, 8, C.byref(o), None, 0, None,
+                          info) == N.DEER_ERR_INVALID
+    # workspace too small (checked before any device call)
+    assert lib.deer_solve(C.byref(dyn), 1, 10, 8, None, 8, C.byref(o), 256, 16, None,
+                          info) == N.DEER_ERR_WORKSPACE

@@ -1,0 +1,245 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (normwise, per sequence: max |s_gpu - s_ref| / max |s_ref|): 1e-10 in FP64
+mode and 1e-5 in FP32 mode for converged trajectories; per-iteration iterates in FP64
+agree to 1e-11 (they differ only by the association order of the scan).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import dynamics as odyn
+from oracle import elk as oelk
+from oracle import newton as onewton
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+# float32 solves stop at a scaled residual of 5e-7 (about four units of float32 roundoff),
+# which keeps the accumulated trajectory error below the 1e-5 parity bound
+FP32_TOL = 5e-7
+
+
+def _deer():
+    import paper_2603_16850_gb300 as deer
+    return deer
+
+
+def _t(a, dt=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dt, device=DEV)
+
+
+def _relerr(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300)
+
+
+def _ma_problem(B, d, R, T, seed, dt=1e-3, integ="rk4"):
+    return synth.massaction(B, d, R, T, seed, dt=dt, integrator=integ)
+
+
+def _ma_dyn(p, dtype):
+    deer = _deer()
+    return deer.Dynamics.massaction(_t(p["topology"], torch.int32), _t(p["params"], dtype),
+                                    p["d"], p["dt"], p["kind"].split("_")[1])
+
+
+def _ma_oracle(p):
+    return odyn.MassAction(p["topology"], p["params"], p["dt"], p["kind"].split("_")[1], d=p["d"])
+
+
+# ---------------------------------------------------------------------------
+def test_brusselator_full_size_fp64():
+    """Brusselator d=2, Euler dt=0.01, a=1, b=3, s0=(1,1), T=1024, full Newton, FP64,
+    tol 1e-12: the converged trajectory equals the sequential rollout. Undamped Newton from
+    the constant guess overflows on this limit cycle (the oracle's iterates do too), so the
+    reset heuristic is on, as the paper uses it for unstable iterates."""
+    deer = _deer()
+    p = synth.brusselator(T=1024)
+    dyn = deer.Dynamics.brusselator(_t(p["params"]), p["dt"])
+    s, info = deer.deer_solve(dyn, _t(p["s0"]), 1024, jac="full", tol=1e-12, prec="fp64",
+                              init="s0", reset=True)
+    ref = onewton.rollout(odyn.Brusselator(p["params"], p["dt"]), p["s0"], 1024)[0]
+    assert bool(info.converged[0])
+    assert _relerr(s.cpu().numpy(), ref) <= 1e-10
+    o = onewton.solve(odyn.Brusselator(p["params"], p["dt"]), p["s0"], 1024, "full", tol=1e-12,
+                      init="s0", reset=True)
+    assert o["converged"][0]
+    assert abs(int(info.iters[0]) - int(o["iters"][0])) <= max(2, int(o["iters"][0]) // 10)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_brusselator_iterates_match_oracle(k):
+    """After k iterations (cap k) the GPU iterate equals k oracle forward-substitution
+    steps (T=300: four 64-row chunks and a ragged tail)."""
+    deer = _deer()
+    T = 300
+    p = synth.brusselator(T=T)
+    od = odyn.Brusselator(p["params"], p["dt"])
+    dyn = deer.Dynamics.brusselator(_t(p["params"]), p["dt"])
+    s, info = deer.deer_solve(dyn, _t(p["s0"]), T, jac="full", tol=0.0, max_iters=k, init="s0")
+    assert info.status == 1 and int(info.iters[0]) == k
+    ref = onewton.initial_guess(od, p["s0"], T, "s0")
+    for _ in range(k):
+        ref = onewton.quasi_newton_step(od, p["s0"], ref, "full")
+    assert _relerr(s.cpu().numpy(), ref[0]) <= 1e-11
+
+
+@pytest.mark.parametrize("jac,damp,dp", [("full", "none", 0.0), ("diag", "none", 0.0),
+                                         ("identity", "none", 0.0), ("zero", "none", 0.0),
+                                         ("full", "scale", 0.3), ("diag", "clip", 0.9)])
+def test_massaction_modes_fp64(jac, damp, dp):
+    deer = _deer()
+    B, d, R, T = 3, 4, 6, 200
+    p = _ma_problem(B, d, R, T, seed=4, dt=0.02)
+    od = _ma_oracle(p)
+    dyn = _ma_dyn(p, torch.float64)
+    # two iterations from the same start, then the fixed point
+    s2, _ = deer.deer_solve(dyn, _t(p["s0"]), T, jac=jac, damp=damp, damp_param=dp, tol=0.0,
+                            max_iters=2, init="s0")
+    ref = onewton.initial_guess(od, p["s0"], T, "s0")
+    for _ in range(2):
+        ref = onewton.quasi_newton_step(od, p["s0"], ref, jac, damp, dp)
+    assert _relerr(s2.cpu().numpy(), ref.reshape(-1, d)) <= 1e-11
+    s, info = deer.deer_solve(dyn, _t(p["s0"]), T, jac=jac, damp=damp, damp_param=dp, tol=1e-12,
+                              init="s0", reset=True)
+    assert bool(info.converged.all())
+    roll = onewton.rollout(od, p["s0"], T)
+    for b in range(B):
+        assert _relerr(s.cpu().numpy()[b * T:(b + 1) * T], roll[b]) <= 1e-10
+
+
+@pytest.mark.parametrize("d,R", [(2, 3), (8, 12), (16, 24), (32, 48)])
+def test_massaction_rk4_fp32_full(d, R):
+    deer = _deer()
+    B, T = 4, 700
+    p = _ma_problem(B, d, R, T, seed=d)
+    dyn = _ma_dyn(p, torch.float32)
+    s, info = deer.deer_solve(dyn, _t(p["s0"], torch.float32), T, jac="full", tol=FP32_TOL,
+                              prec="fp32", init="s0", reset=True)
+    assert bool(info.converged.all()), info
+    roll = onewton.rollout(_ma_oracle(p), p["s0"], T)
+    for b in range(B):
+        assert _relerr(s.cpu().numpy()[b * T:(b + 1) * T], roll[b]) <= 1e-5
+
+
+@pytest.mark.parametrize("d,prec", [(8, "fp64"), (64, "fp32")])
+def test_gru_quasi_deer(d, prec):
+    deer = _deer()
+    B, T = 2, 400
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    g = synth.gru(B, T, d, d, seed=1)
+    dyn = deer.Dynamics.gru(_t(g["W"], dt), _t(g["U"], dt))
+    x = _t(g["x"].reshape(-1, d), dt)
+    tol = 1e-12 if prec == "fp64" else FP32_TOL
+    s, info = deer.deer_solve(dyn, _t(g["s0"], dt), T, x, jac="diag", tol=tol, prec=prec,
+                              init="zeros")
+    assert bool(info.converged.all())
+    roll = onewton.rollout(odyn.GRU(g["W"], g["U"], g["x"]), g["s0"], T)
+    lim = 1e-10 if prec == "fp64" else 1e-5
+    for b in range(B):
+        assert _relerr(s.cpu().numpy()[b * T:(b + 1) * T], roll[b]) <= lim
+
+
+@pytest.mark.parametrize("lam", [0.5, 10.0])
+def test_gru_quasi_elk_iterates(lam):
+    """Kalman-filter damped quasi-DEER (quasi-ELK): each iterate equals the oracle's
+    filtered means; the fixed point equals the rollout."""
+    deer = _deer()
+    B, T, d = 2, 260, 8
+    g = synth.gru(B, T, d, d, seed=3)
+    od = odyn.GRU(g["W"], g["U"], g["x"])
+    dyn = deer.Dynamics.gru(_t(g["W"]), _t(g["U"]))
+    x = _t(g["x"].reshape(-1, d))
+    s2, _ = deer.deer_solve(dyn, _t(g["s0"]), T, x, jac="diag", damp="elk", damp_param=lam,
+                            tol=0.0, max_iters=2, init="zeros")
+    ref = onewton.initial_guess(od, g["s0"], T, "zeros")
+    for _ in range(2):
+        ref = oelk.elk_filter_step(od, g["s0"], ref, "diag", lam)
+    assert _relerr(s2.cpu().numpy(), ref.reshape(-1, d)) <= 1e-11
+    s, info = deer.deer_solve(dyn, _t(g["s0"]), T, x, jac="diag", damp="elk", damp_param=lam,
+                              tol=1e-12, init="zeros", max_iters=20 * T)
+    assert bool(info.converged.all())
+    roll = onewton.rollout(od, g["s0"], T)
+    assert _relerr(s.cpu().numpy(), roll.reshape(-1, d)) <= 1e-10
+
+
+def test_linear_converges_in_one_iteration():
+    deer = _deer()
+    lds = synth.linear_lds(B=3, T=500, d=8, seed=5)
+    dyn = deer.Dynamics.linear(_t(lds["A"]))
+    s, info = deer.deer_solve(dyn, _t(lds["s0"]), 500, _t(lds["x"].reshape(-1, 8)), jac="full",
+                              tol=1e-9, init="zeros")
+    assert info.iters.tolist() == [1, 1, 1]
+    roll = onewton.rollout(odyn.Linear(lds["A"], lds["x"]), lds["s0"], 500)
+    assert _relerr(s.cpu().numpy(), roll.reshape(-1, 8)) <= 1e-10
+
+
+def test_ragged_batch_matches_per_sequence_rollouts():
+    deer = _deer()
+    lengths = [0, 1, 2, 300, 77, 129, 64]
+    off = synth.offsets_from_lengths(lengths)
+    B, d, R = len(lengths), 4, 6
+    p = _ma_problem(B, d, R, 1, seed=9, dt=0.02)
+    dyn = _ma_dyn(p, torch.float64)
+    s, info = deer.deer_solve_batched(dyn, _t(p["s0"]), off, jac="full", tol=1e-12, init="s0")
+    assert bool(info.converged.all())
+    assert int(info.iters[0]) == 0 and int(info.iters[1]) == 1
+    od = _ma_oracle(p)
+    sn = s.cpu().numpy()
+    for b, L in enumerate(lengths):
+        if L == 0:
+            continue
+        sub = odyn.MassAction(p["topology"][b:b + 1], p["params"][b:b + 1], p["dt"], "rk4", d=d)
+        roll = onewton.rollout(sub, p["s0"][b:b + 1], L)[0]
+        assert _relerr(sn[off[b]:off[b + 1]], roll) <= 1e-10
+
+
+@pytest.mark.parametrize("kind", ["massaction_rk4", "gru", "brusselator"])
+def test_sequential_rollout_parity(kind):
+    deer = _deer()
+    if kind == "massaction_rk4":
+        p = _ma_problem(5, 8, 12, 400, seed=2)
+        dyn, s0, T, x = _ma_dyn(p, torch.float64), p["s0"], 400, None
+        ref = onewton.rollout(_ma_oracle(p), p["s0"], 400)
+    elif kind == "gru":
+        g = synth.gru(3, 200, 16, 16, seed=2)
+        dyn, s0, T = deer.Dynamics.gru(_t(g["W"]), _t(g["U"])), g["s0"], 200
+        x = _t(g["x"].reshape(-1, 16))
+        ref = onewton.rollout(odyn.GRU(g["W"], g["U"], g["x"]), g["s0"], 200)
+    else:
+        p = synth.brusselator(T=1024)
+        dyn, s0, T, x = deer.Dynamics.brusselator(_t(p["params"]), p["dt"]), p["s0"], 1024, None
+        ref = onewton.rollout(odyn.Brusselator(p["params"], p["dt"]), p["s0"], 1024)
+    s = deer.deer_rollout(dyn, _t(s0), T, x)
+    assert _relerr(s.cpu().numpy(), ref.reshape(s.shape)) <= 1e-12
+
+
+def test_nonfinite_input_is_reported():
+    deer = _deer()
+    p = synth.brusselator(T=100)
+    dyn = deer.Dynamics.brusselator(_t(p["params"]), p["dt"])
+    s0 = _t([[float("nan"), 1.0]])
+    with pytest.raises(RuntimeError, match="non-finite"):
+        deer.deer_solve(dyn, s0, 100, jac="full", tol=1e-12)
+
+
+def test_full_size_batched_massaction_fp32_sampled():
+    """B=4096 systems, d=8, 12 reactions, RK4 dt=1e-3, T=16384, full Newton, FP32: sampled
+    trajectories equal the FP64 oracle rollout within 1e-5."""
+    deer = _deer()
+    B, d, R, T = 4096, 8, 12, 16384
+    p = _ma_problem(B, d, R, T, seed=0)
+    dyn = _ma_dyn(p, torch.float32)
+    s, info = deer.deer_solve(dyn, _t(p["s0"], torch.float32), T, jac="full", tol=FP32_TOL,
+                              prec="fp32", init="s0", reset=True)
+    assert bool(info.converged.all()), (info.max_resid.max(), info.iters.max())
+    rng = np.random.default_rng(0)
+    pick = rng.choice(B, size=3, replace=False)
+    sub = odyn.MassAction(p["topology"][pick], p["params"][pick], p["dt"], "rk4", d=d)
+    roll = onewton.rollout(sub, p["s0"][pick], T)
+    sv = s.view(B, T, d)
+    for i, b in enumerate(pick):
+        assert _relerr(sv[b].cpu().numpy(), roll[i]) <= 1e-5
