@@ -467,14 +467,137 @@ deer_status deer_rollout(const deer_dynamics* f, int64_t batch, int64_t T,
   return DEER_OK;
 }
 
-size_t deer_grad_workspace_bytes(const deer_dynamics*, int64_t, int64_t, const deer_options*) {
-  return 0;
+size_t deer_grad_workspace_bytes(const deer_dynamics* f, int64_t batch, int64_t T,
+                                 const deer_options* opt) {
+  if (!opt || batch < 0 || T < 0) return 0;
+  deer_options o = *opt;
+  o.jac = DEER_JAC_FULL;
+  o.damp = DEER_DAMP_NONE;
+  if (check_common(f, &o) != DEER_OK) return 0;
+  Layout ly;
+  if (!make_layout(f, batch, batch * T, &o, ly)) return 0;
+  const size_t rs = o.prec == DEER_FP32 ? 4 : 8;
+  return ly.total + align_up((size_t)batch * T * f->d * rs);
 }
 
-deer_status deer_grad(const deer_dynamics*, int64_t, int64_t, const void*, const void*,
-                      const void*, const void*, void*, void*, const deer_options*, void*, size_t,
-                      deer_stream_t) {
-  return DEER_ERR_UNSUPPORTED;
+}  // extern "C"
+
+namespace deer {
+template <class real>
+static deer_status grad_impl(const deer_dynamics* f, int64_t B, int64_t T, const void* s0_,
+                             const void* x_, const void* sstar_, const void* g_, void* dp_,
+                             void* ds0_, const deer_options* o, void* ws_, size_t ws_bytes,
+                             cudaStream_t st) {
+  const int64_t N = B * T;
+  Layout ly;
+  if (!make_layout(f, B, N, o, ly)) return DEER_ERR_INVALID;
+  const size_t rs = sizeof(real);
+  const size_t lam_off = ly.total;
+  const size_t need = ly.total + align_up((size_t)N * f->d * rs);
+  if (!ws_ || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws_) & 255u))
+    return DEER_ERR_WORKSPACE;
+  char* ws = static_cast<char*>(ws_);
+  const int d = f->d;
+  std::vector<int64_t> off(B + 1), cf(B + 1);
+  int64_t nc = 0;
+  for (int64_t b = 0; b <= B; ++b) {
+    off[b] = b * T;
+    cf[b] = nc;
+    if (b < B) nc += (T + ly.L - 1) / ly.L;
+  }
+  int64_t* d_off = reinterpret_cast<int64_t*>(ws + ly.offsets);
+  int64_t* d_cf = reinterpret_cast<int64_t*>(ws + ly.chunk_first);
+  DEER_CK(cudaMemcpyAsync(d_off, off.data(), (B + 1) * 8, cudaMemcpyHostToDevice, st));
+  DEER_CK(cudaMemcpyAsync(d_cf, cf.data(), (B + 1) * 8, cudaMemcpyHostToDevice, st));
+  SeqAcc* acc = reinterpret_cast<SeqAcc*>(ws + ly.acc);
+  SeqInfo* info = reinterpret_cast<SeqInfo*>(ws + ly.info);
+  Flags* flags = reinterpret_cast<Flags*>(ws + ly.flags);
+  DEER_CK(cudaMemsetAsync(acc, 0, B * sizeof(SeqAcc), st));
+  DEER_CK(cudaMemsetAsync(info, 0, B * sizeof(SeqInfo), st));
+  DEER_CK(cudaMemsetAsync(flags, 0, sizeof(Flags), st));
+  Batch bt{B, N, d_off, d_cf, nc, ly.L, ilog2(ly.L)};
+  DynView<real> dv = make_view<real>(f, x_, ws, ly);
+  if (ly.n_ma > 0) {
+    DEER_CK(launch_ma_setup<real>(ly.n_ma, d, f->n_reactions, static_cast<const real*>(f->params),
+                                  f->params_stride, f->topology, f->topology_stride,
+                                  reinterpret_cast<real*>(ws + ly.ma), ly.ma_stride,
+                                  &flags->bad_input, st));
+  }
+  if (f->kind == DEER_F_GRU) {
+    DEER_CK(launch_gru_setup<real>(d, static_cast<const real*>(f->params), f->d_in,
+                                   reinterpret_cast<real*>(ws + ly.gru_M), st));
+  }
+  // A_t at the fixed point (Eq. lil_j) for every row
+  LinArgs<real> la;
+  la.dv = dv;
+  la.bt = bt;
+  la.s0 = static_cast<const real*>(s0_);
+  la.s = static_cast<const real*>(sstar_);
+  la.A = reinterpret_cast<real*>(ws + ly.A);
+  la.b = reinterpret_cast<real*>(ws + ly.b);
+  la.acc = acc;
+  la.info = info;
+  la.jac = DEER_JAC_FULL;
+  la.damp = DEER_DAMP_NONE;
+  la.dparam = real(0);
+  DEER_CK(launch_linearize<real>(la, st));
+  // reverse scan lambda_t = A_{t+1}^T lambda_{t+1} + g_t
+  AdjScanArgs<real> sa;
+  sa.bt = bt;
+  sa.d = d;
+  sa.A = la.A;
+  sa.g = static_cast<const real*>(g_);
+  sa.lam = reinterpret_cast<real*>(ws + lam_off);
+  sa.aggP = reinterpret_cast<real*>(ws + ly.aggP);
+  sa.aggv = reinterpret_cast<real*>(ws + ly.aggv);
+  sa.cin = reinterpret_cast<real*>(ws + ly.cin);
+  DEER_CK(launch_adjoint_scan<real>(sa, st));
+  ParamGradArgs<real> pa;
+  pa.dv = dv;
+  pa.bt = bt;
+  pa.s0 = la.s0;
+  pa.s = la.s;
+  pa.lam = sa.lam;
+  pa.A = la.A;
+  pa.dparams = static_cast<real*>(dp_);
+  pa.pstride = f->kind == DEER_F_BRUSSELATOR_EULER ? 2 : f->n_reactions;
+  pa.ds0 = static_cast<real*>(ds0_);
+  if (pa.dparams) DEER_CK(cudaMemsetAsync(pa.dparams, 0, B * pa.pstride * rs, st));
+  DEER_CK(launch_param_grad<real>(pa, st));
+  Flags hf;
+  DEER_CK(cudaMemcpyAsync(&hf, flags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
+  DEER_CK(cudaStreamSynchronize(st));
+  if (hf.bad_input) return DEER_ERR_INVALID;
+  return DEER_OK;
+}
+}  // namespace deer
+
+extern "C" {
+
+deer_status deer_grad(const deer_dynamics* f, int64_t batch, int64_t T, const void* s0,
+                      const void* x, const void* s_star, const void* dl_ds, void* dl_dparams,
+                      void* dl_ds0, const deer_options* opt, void* workspace,
+                      size_t workspace_bytes, deer_stream_t stream) {
+  if (!opt || !f) return DEER_ERR_INVALID;
+  deer_options o = *opt;
+  o.jac = DEER_JAC_FULL;
+  o.damp = DEER_DAMP_NONE;
+  deer_status c = check_common(f, &o);
+  if (c != DEER_OK) return c;
+  if (batch < 0 || T < 0) return DEER_ERR_INVALID;
+  if (batch == 0 || T == 0) return DEER_OK;
+  if (!s0 || !s_star || !dl_ds) return DEER_ERR_INVALID;
+  if (f->kind == DEER_F_GRU && !x) return DEER_ERR_INVALID;
+  const bool per_seq = f->kind == DEER_F_BRUSSELATOR_EULER ||
+                       f->kind == DEER_F_MASSACTION_EULER || f->kind == DEER_F_MASSACTION_RK4;
+  if (dl_dparams && !per_seq) return DEER_ERR_UNSUPPORTED;
+  if (dl_dparams && f->params_stride == 0 && batch > 1) return DEER_ERR_UNSUPPORTED;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (o.prec == DEER_FP32)
+    return grad_impl<float>(f, batch, T, s0, x, s_star, dl_ds, dl_dparams, dl_ds0, &o,
+                            workspace, workspace_bytes, st);
+  return grad_impl<double>(f, batch, T, s0, x, s_star, dl_ds, dl_dparams, dl_ds0, &o, workspace,
+                           workspace_bytes, st);
 }
 
 int64_t deer_kernel_launch_count(void) { return g_launches.load(); }

@@ -356,6 +356,147 @@ __global__ void k_gru_setup(int d, const real* __restrict__ params, int d_in, re
   M[id] = Uh[i * d + j] * Ur[j * d + i];
 }
 
+
+// ----------------------------------------------------------------------------
+// Adjoint parameter gradient (one thread per row): the vector-Jacobian product
+// lambda_t^T df_t/dtheta (s_{t-1}) by reverse-mode through the integrator stages, summed
+// over the rows of each sequence (warp reduction, then one atomic per warp and
+// parameter), and dl/ds0 = A_1^T lambda_1. Mass action: theta = rate constants k;
+// Brusselator: theta = (a, b).
+// ----------------------------------------------------------------------------
+constexpr int kMaxD = 32;
+
+template <class real>
+__device__ __forceinline__ void ma_rate_vec(const real* kk, const int4* tt, int R, int d,
+                                            const real* c, real* g) {
+  for (int i = 0; i < d; ++i) g[i] = real(0);
+  for (int r = 0; r < R; ++r) {
+    const int4 q = __ldg(tt + r);
+    const real rate = __ldg(kk + r) * c[q.x] * (q.y >= 0 ? c[q.y] : real(1));
+    g[q.x] -= rate;
+    if (q.y >= 0) g[q.y] -= rate;
+    g[q.z] += rate;
+    if (q.w >= 0) g[q.w] += rate;
+  }
+}
+
+// out += G(c)^T u for the mass-action rate Jacobian G
+template <class real>
+__device__ __forceinline__ void ma_rate_vjp(const real* kk, const int4* tt, int R,
+                                            const real* c, const real* u, real* out) {
+  for (int r = 0; r < R; ++r) {
+    const int4 q = __ldg(tt + r);
+    real nu_u = u[q.z] - u[q.x];
+    if (q.y >= 0) nu_u -= u[q.y];
+    if (q.w >= 0) nu_u += u[q.w];
+    const real w = __ldg(kk + r) * nu_u;
+    if (q.y >= 0) {
+      out[q.x] += w * c[q.y];
+      out[q.y] += w * c[q.x];
+    } else {
+      out[q.x] += w;
+    }
+  }
+}
+
+template <class real>
+__global__ void __launch_bounds__(128) k_param_grad(ParamGradArgs<real> a, int rk4) {
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool valid = row < a.bt.N;
+  const int d = a.dv.d;
+  int64_t seq = 0;
+  if (valid) seq = find_seq(a.bt.offsets, a.bt.B, row);
+  const int64_t first = valid ? a.bt.offsets[seq] : 0;
+  const real* sp = valid ? (row == first ? a.s0 + seq * d : a.s + (row - 1) * d) : a.s0;
+  const real* lam = a.lam + (valid ? row : 0) * d;
+  if (valid && a.ds0 && row == first) {
+    const real* A1 = a.A + row * (int64_t)d * d;
+    for (int j = 0; j < d; ++j) {
+      real acc = real(0);
+      for (int i = 0; i < d; ++i) acc += A1[i * d + j] * lam[i];
+      a.ds0[seq * d + j] = acc;
+    }
+  }
+  if (!a.dparams) return;
+  const unsigned full = 0xffffffffu;
+  const unsigned vm = __ballot_sync(full, valid);
+  if (vm == 0) return;
+  const long long sseq = __shfl_sync(full, (long long)seq, __ffs(vm) - 1);
+  const bool uniform = __all_sync(full, !valid || seq == sseq);
+  auto put = [&](int j, real v) {
+    if (uniform) {
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(full, v, o);
+      if ((threadIdx.x & 31) == 0) atomicAdd(a.dparams + sseq * a.pstride + j, v);
+    } else if (valid) {
+      atomicAdd(a.dparams + seq * a.pstride + j, v);
+    }
+  };
+  if (a.dv.kind == DEER_F_BRUSSELATOR_EULER) {
+    const real dt = a.dv.dt;
+    const real ga = valid ? dt * lam[0] : real(0);
+    const real gb = valid ? dt * sp[0] * (lam[1] - lam[0]) : real(0);
+    put(0, ga);
+    put(1, gb);
+    return;
+  }
+  // mass action
+  const int R = a.dv.R;
+  const real* kk = a.dv.params + seq * a.dv.pstride;
+  const int4* tt = reinterpret_cast<const int4*>(a.dv.topo + seq * a.dv.tstride);
+  const real h = a.dv.dt;
+  real c[4][kMaxD], u[4][kMaxD], tmp[kMaxD];
+  const int nst = rk4 ? 4 : 1;
+  if (valid) {
+    for (int i = 0; i < d; ++i) c[0][i] = sp[i];
+    if (rk4) {
+      ma_rate_vec(kk, tt, R, d, c[0], tmp);
+      for (int i = 0; i < d; ++i) c[1][i] = sp[i] + real(0.5) * h * tmp[i];
+      ma_rate_vec(kk, tt, R, d, c[1], tmp);
+      for (int i = 0; i < d; ++i) c[2][i] = sp[i] + real(0.5) * h * tmp[i];
+      ma_rate_vec(kk, tt, R, d, c[2], tmp);
+      for (int i = 0; i < d; ++i) c[3][i] = sp[i] + h * tmp[i];
+      // cotangents of the stage slopes, from the last stage back
+      for (int i = 0; i < d; ++i) u[3][i] = h / real(6) * lam[i];
+      for (int i = 0; i < d; ++i) tmp[i] = real(0);
+      ma_rate_vjp(kk, tt, R, c[3], u[3], tmp);
+      for (int i = 0; i < d; ++i) u[2][i] = h / real(3) * lam[i] + h * tmp[i];
+      for (int i = 0; i < d; ++i) tmp[i] = real(0);
+      ma_rate_vjp(kk, tt, R, c[2], u[2], tmp);
+      for (int i = 0; i < d; ++i) u[1][i] = h / real(3) * lam[i] + real(0.5) * h * tmp[i];
+      for (int i = 0; i < d; ++i) tmp[i] = real(0);
+      ma_rate_vjp(kk, tt, R, c[1], u[1], tmp);
+      for (int i = 0; i < d; ++i) u[0][i] = h / real(6) * lam[i] + real(0.5) * h * tmp[i];
+    } else {
+      for (int i = 0; i < d; ++i) u[0][i] = h * lam[i];
+    }
+  }
+  // d f / d k_r contracted with lambda: sum over stages of phi_r(c_s) (nu_r . u_s)
+  for (int r = 0; r < R; ++r) {
+    real v = real(0);
+    if (valid) {
+      const int4 q = __ldg(tt + r);
+      for (int st = 0; st < nst; ++st) {
+        const real phi = c[st][q.x] * (q.y >= 0 ? c[st][q.y] : real(1));
+        real nu_u = u[st][q.z] - u[st][q.x];
+        if (q.y >= 0) nu_u -= u[st][q.y];
+        if (q.w >= 0) nu_u += u[st][q.w];
+        v += phi * nu_u;
+      }
+    }
+    put(r, v);
+  }
+}
+
+template <class real>
+cudaError_t launch_param_grad(const ParamGradArgs<real>& a, cudaStream_t st) {
+  if (a.bt.N == 0) return cudaSuccess;
+  if (a.dv.d > kMaxD) return cudaErrorInvalidValue;
+  const int rk4 = a.dv.kind == DEER_F_MASSACTION_RK4;
+  k_param_grad<real><<<grid_for(a.bt.N, 128), 128, 0, st>>>(a, rk4);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------------------
 // Host-side dispatch
 // ----------------------------------------------------------------------------
@@ -535,7 +676,8 @@ cudaError_t launch_rollout(const RolloutArgs<real>& a, cudaStream_t st) {
   template cudaError_t launch_init<real>(const InitArgs<real>&, cudaStream_t);                 \
   template cudaError_t launch_linearize<real>(const LinArgs<real>&, cudaStream_t);             \
   template cudaError_t launch_rollout<real>(const RolloutArgs<real>&, cudaStream_t);          \
-  template cudaError_t launch_gru_setup<real>(int, const real*, int, real*, cudaStream_t);
+  template cudaError_t launch_gru_setup<real>(int, const real*, int, real*, cudaStream_t);   \
+  template cudaError_t launch_param_grad<real>(const ParamGradArgs<real>&, cudaStream_t);
 DEER_INST(float)
 DEER_INST(double)
 #undef DEER_INST

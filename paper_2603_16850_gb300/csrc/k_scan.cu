@@ -388,3 +388,171 @@ template cudaError_t launch_diag_scan<float>(const DiagScanArgs<float>&, cudaStr
 template cudaError_t launch_diag_scan<double>(const DiagScanArgs<double>&, cudaStream_t);
 
 }  // namespace deer
+
+namespace deer {
+
+// ----------------------------------------------------------------------------
+// Reverse dense scan for the adjoint (one thread per chunk / per sequence), rows visited
+// from the end of the sequence: lambda_t = M_t lambda_{t+1} + g_t with M_t = A_{t+1}^T and
+// lambda_{T+1} = 0. Chunk aggregates compose in reverse row order.
+// ----------------------------------------------------------------------------
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_adj_chunk(AdjScanArgs<real> a) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= a.bt.n_chunks) return;
+  int64_t seq, r0;
+  int n;
+  chunk_rows(a.bt, c, seq, r0, n);
+  const int64_t rend = __ldg(a.bt.offsets + seq + 1);  // one past the last row
+  const bool need_P = c != __ldg(a.bt.chunk_first + seq + 1) - 1;  // last chunk: carry 0
+  real P[D][D], v[D];
+#pragma unroll U<D>::n
+  for (int i = 0; i < D; ++i) {
+    v[i] = real(0);
+#pragma unroll U<D>::n
+    for (int j = 0; j < D; ++j) P[i][j] = (i == j) ? real(1) : real(0);
+  }
+  for (int t = n - 1; t >= 0; --t) {
+    const int64_t row = r0 + t;
+    const real* gt = a.g + row * D;
+    if (row + 1 < rend) {
+      const real* An = a.A + (row + 1) * (int64_t)(D * D);  // M_t = A_{t+1}^T
+      real nv[D];
+#pragma unroll U<D>::n
+      for (int i = 0; i < D; ++i) {
+        real acc = __ldg(gt + i);
+#pragma unroll U<D>::n
+        for (int k = 0; k < D; ++k) acc += __ldg(An + k * D + i) * v[k];
+        nv[i] = acc;
+      }
+#pragma unroll U<D>::n
+      for (int i = 0; i < D; ++i) v[i] = nv[i];
+      if (need_P) {
+        real NP[D][D];
+#pragma unroll U<D>::n
+        for (int i = 0; i < D; ++i)
+#pragma unroll U<D>::n
+          for (int j = 0; j < D; ++j) {
+            real acc = real(0);
+#pragma unroll U<D>::n
+            for (int k = 0; k < D; ++k) acc += __ldg(An + k * D + i) * P[k][j];
+            NP[i][j] = acc;
+          }
+#pragma unroll U<D>::n
+        for (int i = 0; i < D; ++i)
+#pragma unroll U<D>::n
+          for (int j = 0; j < D; ++j) P[i][j] = NP[i][j];
+      }
+    } else {
+      // last row of the sequence: lambda_T = g_T, the carry (lambda_{T+1} = 0) is dropped
+#pragma unroll U<D>::n
+      for (int i = 0; i < D; ++i) {
+        v[i] = __ldg(gt + i);
+#pragma unroll U<D>::n
+        for (int j = 0; j < D; ++j) P[i][j] = real(0);
+      }
+    }
+  }
+  real* Po = a.aggP + c * (int64_t)(D * D);
+  real* vo = a.aggv + c * D;
+#pragma unroll U<D>::n
+  for (int i = 0; i < D; ++i) {
+    vo[i] = v[i];
+#pragma unroll U<D>::n
+    for (int j = 0; j < D; ++j) Po[i * D + j] = P[i][j];
+  }
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_adj_carry(AdjScanArgs<real> a) {
+  const int64_t seq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (seq >= a.bt.B) return;
+  const int64_t c0 = a.bt.chunk_first[seq], c1 = a.bt.chunk_first[seq + 1];
+  real x[D];
+#pragma unroll U<D>::n
+  for (int i = 0; i < D; ++i) x[i] = real(0);
+  for (int64_t c = c1 - 1; c >= c0; --c) {
+    real* ci = a.cin + c * D;
+#pragma unroll U<D>::n
+    for (int i = 0; i < D; ++i) ci[i] = x[i];
+    const real* P = a.aggP + c * (int64_t)(D * D);
+    const real* v = a.aggv + c * D;
+    real nx[D];
+#pragma unroll U<D>::n
+    for (int i = 0; i < D; ++i) {
+      real acc = v[i];
+#pragma unroll U<D>::n
+      for (int k = 0; k < D; ++k) acc += P[i * D + k] * x[k];
+      nx[i] = acc;
+    }
+#pragma unroll U<D>::n
+    for (int i = 0; i < D; ++i) x[i] = nx[i];
+  }
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_adj_apply(AdjScanArgs<real> a) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= a.bt.n_chunks) return;
+  int64_t seq, r0;
+  int n;
+  chunk_rows(a.bt, c, seq, r0, n);
+  const int64_t rend = __ldg(a.bt.offsets + seq + 1);
+  real x[D];
+#pragma unroll U<D>::n
+  for (int i = 0; i < D; ++i) x[i] = a.cin[c * D + i];
+  for (int t = n - 1; t >= 0; --t) {
+    const int64_t row = r0 + t;
+    const real* gt = a.g + row * D;
+    real nx[D];
+    if (row + 1 < rend) {
+      const real* An = a.A + (row + 1) * (int64_t)(D * D);
+#pragma unroll U<D>::n
+      for (int i = 0; i < D; ++i) {
+        real acc = __ldg(gt + i);
+#pragma unroll U<D>::n
+        for (int k = 0; k < D; ++k) acc += __ldg(An + k * D + i) * x[k];
+        nx[i] = acc;
+      }
+    } else {
+#pragma unroll U<D>::n
+      for (int i = 0; i < D; ++i) nx[i] = __ldg(gt + i);
+    }
+    real* lr = a.lam + row * D;
+#pragma unroll U<D>::n
+    for (int i = 0; i < D; ++i) {
+      x[i] = nx[i];
+      lr[i] = nx[i];
+    }
+  }
+}
+
+template <class real, int D>
+static void adj_launch(const AdjScanArgs<real>& a, cudaStream_t st) {
+  const unsigned gc = grid_for(a.bt.n_chunks, 128);
+  const unsigned gs = grid_for(a.bt.B, 128);
+  k_adj_chunk<real, D><<<gc, 128, 0, st>>>(a);
+  k_adj_carry<real, D><<<gs, 128, 0, st>>>(a);
+  k_adj_apply<real, D><<<gc, 128, 0, st>>>(a);
+  note_launch(3);
+}
+
+template <class real>
+cudaError_t launch_adjoint_scan(const AdjScanArgs<real>& a, cudaStream_t st) {
+  if (a.bt.N == 0) return cudaSuccess;
+  switch (a.d) {
+    case 1: adj_launch<real, 1>(a, st); break;
+    case 2: adj_launch<real, 2>(a, st); break;
+    case 4: adj_launch<real, 4>(a, st); break;
+    case 8: adj_launch<real, 8>(a, st); break;
+    case 16: adj_launch<real, 16>(a, st); break;
+    case 32: adj_launch<real, 32>(a, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_adjoint_scan<float>(const AdjScanArgs<float>&, cudaStream_t);
+template cudaError_t launch_adjoint_scan<double>(const AdjScanArgs<double>&, cudaStream_t);
+
+}  // namespace deer

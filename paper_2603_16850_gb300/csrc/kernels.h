@@ -120,3 +120,41 @@ template <class real>
 cudaError_t launch_diag_scan(const DiagScanArgs<real>& a, cudaStream_t st);
 
 }  // namespace deer
+
+namespace deer {
+
+// Reverse (adjoint) dense scan: lambda_t = A_{t+1}^T lambda_{t+1} + g_t within each
+// sequence, lambda_{T+1} = 0 (Eq. bptt_lds run backwards in time).
+template <class real>
+struct AdjScanArgs {
+  Batch bt;
+  int d;
+  const real* A;    // [N][d][d] Jacobians A_t at the fixed point
+  const real* g;    // [N][d] cotangents dl/ds_t
+  real* lam;        // [N][d] output adjoints
+  real* aggP;       // [n_chunks][d][d]
+  real* aggv;       // [n_chunks][d]
+  real* cin;        // [n_chunks][d]
+};
+
+template <class real>
+cudaError_t launch_adjoint_scan(const AdjScanArgs<real>& a, cudaStream_t st);
+
+// Parameter gradient sum_t lambda_t^T df_t/dtheta (s_{t-1}) and dl/ds0 = A_1^T lambda_1.
+template <class real>
+struct ParamGradArgs {
+  DynView<real> dv;
+  Batch bt;
+  const real* s0;
+  const real* s;       // fixed point [N][d]
+  const real* lam;     // [N][d]
+  const real* A;       // [N][d][d]
+  real* dparams;       // [B][P] or nullptr (accumulated with atomics: zero it first)
+  int64_t pstride;     // P
+  real* ds0;           // [B][d] or nullptr
+};
+
+template <class real>
+cudaError_t launch_param_grad(const ParamGradArgs<real>& a, cudaStream_t st);
+
+}  // namespace deer
