@@ -85,8 +85,8 @@ static bool d_supported(int kind, int d, int jac) {
 
 // Everything the solver carves out of the caller's workspace.
 struct Layout {
-  size_t offsets, chunk_first, acc, info, flags, ma, gru_M, A, b, aggP, aggv, cin, gam, mob,
-      pin, total;
+  size_t offsets, chunk_first, act_seq, act_row_off, act_chunk_off, acc, info, flags, ma, gru_M,
+      A, b, aggP, aggv, cin, gam, mob, pin, total;
   int64_t n_chunks_max;
   int64_t ma_stride, n_ma;
   int L;
@@ -113,6 +113,9 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
   auto take = [&](size_t bytes) { size_t at = p; p = align_up(p + bytes); return at; };
   ly.offsets = take((size_t)(B + 1) * 8);
   ly.chunk_first = take((size_t)(B + 1) * 8);
+  ly.act_seq = take((size_t)(B + 1) * 8);
+  ly.act_row_off = take((size_t)(B + 1) * 8);
+  ly.act_chunk_off = take((size_t)(B + 1) * 8);
   ly.acc = take((size_t)(B > 0 ? B : 1) * sizeof(SeqAcc));
   ly.info = take((size_t)(B > 0 ? B : 1) * sizeof(SeqInfo));
   ly.flags = take(sizeof(Flags));
@@ -237,6 +240,12 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   bt.n_chunks = nc;
   bt.L = ly.L;
   bt.log2L = ilog2(ly.L);
+  bt.act_seq = reinterpret_cast<int64_t*>(ws + ly.act_seq);
+  bt.act_row_off = reinterpret_cast<int64_t*>(ws + ly.act_row_off);
+  bt.act_chunk_off = reinterpret_cast<int64_t*>(ws + ly.act_chunk_off);
+  bt.n_act = B;
+  bt.act_rows = N;
+  bt.act_chunks = nc;
 
   DynView<real> dv = make_view<real>(f, x_, ws, ly);
   if (ly.n_ma > 0) {
@@ -270,7 +279,12 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   la.damp = o->damp;
   la.dparam = (real)o->damp_param;
 
-  CheckArgs ca{B, d_off, acc, info, flags, o->tol, 0, max_iters};
+  CheckArgs ca{B, d_off, d_cf, acc, info, flags,
+               reinterpret_cast<int64_t*>(ws + ly.act_seq),
+               reinterpret_cast<int64_t*>(ws + ly.act_row_off),
+               reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), o->tol, 0, max_iters, 1};
+  DEER_CK(launch_check(ca, st));  // every sequence starts active
+  ca.compact_only = 0;
 
   DenseScanArgs<real> dsa;
   DiagScanArgs<real> gsa;
@@ -320,6 +334,7 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   int64_t lin_rows = N;  // rows linearised in the current iteration
   for (int it = 0;; ++it) {
     const int64_t l0 = g_launches.load();
+    la.bt = bt;
     pt.begin(PH_LIN);
     DEER_CK(launch_linearize<real>(la, st));
     pt.end(PH_LIN);
@@ -336,6 +351,11 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     else if (hf.n_active == 0) stop = true;
     else if (it >= max_iters) { status = DEER_NOT_CONVERGED; stop = true; }
     int64_t scan_launches = 0;
+    bt.n_act = hf.n_active;
+    bt.act_rows = hf.active_rows;
+    bt.act_chunks = hf.active_chunks;
+    dsa.bt = bt;
+    gsa.bt = bt;
     if (!stop) {
       const int64_t s0c = g_launches.load();
       pt.begin(PH_SCAN);
@@ -515,7 +535,17 @@ static deer_status grad_impl(const deer_dynamics* f, int64_t B, int64_t T, const
   DEER_CK(cudaMemsetAsync(acc, 0, B * sizeof(SeqAcc), st));
   DEER_CK(cudaMemsetAsync(info, 0, B * sizeof(SeqInfo), st));
   DEER_CK(cudaMemsetAsync(flags, 0, sizeof(Flags), st));
-  Batch bt{B, N, d_off, d_cf, nc, ly.L, ilog2(ly.L)};
+  Batch bt{B, N, d_off, d_cf, nc, ly.L, ilog2(ly.L),
+           reinterpret_cast<int64_t*>(ws + ly.act_seq),
+           reinterpret_cast<int64_t*>(ws + ly.act_row_off),
+           reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), B, N, nc};
+  {
+    CheckArgs ca{B, d_off, d_cf, acc, info, flags,
+                 reinterpret_cast<int64_t*>(ws + ly.act_seq),
+                 reinterpret_cast<int64_t*>(ws + ly.act_row_off),
+                 reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), 0.0, 0, 0, 1};
+    DEER_CK(launch_check(ca, st));
+  }
   DynView<real> dv = make_view<real>(f, x_, ws, ly);
   if (ly.n_ma > 0) {
     DEER_CK(launch_ma_setup<real>(ly.n_ma, d, f->n_reactions, static_cast<const real*>(f->params),

@@ -29,6 +29,7 @@ struct Flags {                  // read back by the host once per iteration
   int32_t timeout;
   int32_t bad_input;            // set by set-up kernels that reject their inputs
   long long active_rows;        // rows of the sequences still active after the check
+  long long active_chunks;      // scan chunks of those sequences
 };
 
 // Everything a kernel needs to evaluate f_t for a row of the packed batch.
@@ -46,15 +47,21 @@ struct DynView {
   const real* gru_M;      // GRU: M[i][j] = Uh[i][j] * Ur[j][i]
 };
 
-// Row-to-sequence maps of a packed ragged batch.
+// Row-to-sequence maps of a packed ragged batch, and the compacted list of the sequences
+// that are still iterating (converged sequences drop out of every later launch, so the
+// work of an iteration scales with the rows still active).
 struct Batch {
   int64_t B;
   int64_t N;
-  const int64_t* offsets;      // [B+1]
-  const int64_t* chunk_first;  // [B+1]: first chunk index of each sequence
+  const int64_t* offsets;        // [B+1]
+  const int64_t* chunk_first;    // [B+1]: first chunk index of each sequence
   int64_t n_chunks;
-  int32_t L;                   // chunk length (power of two)
+  int32_t L;                     // chunk length (power of two)
   int32_t log2L;
+  const int64_t* act_seq;        // [n_act] active sequence ids, ascending
+  const int64_t* act_row_off;    // [n_act+1] exclusive prefix of their lengths
+  const int64_t* act_chunk_off;  // [n_act+1] exclusive prefix of their chunk counts
+  int64_t n_act, act_rows, act_chunks;  // sizes for the current launch
 };
 
 __device__ __forceinline__ int64_t find_seq(const int64_t* __restrict__ off, int64_t B,
@@ -67,6 +74,39 @@ __device__ __forceinline__ int64_t find_seq(const int64_t* __restrict__ off, int
     if (__ldg(off + mid) <= row) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// largest k < n with off[k] <= x (off ascending; ties resolve to the last, which skips
+// empty sequences)
+__device__ __forceinline__ int64_t find_k(const int64_t* __restrict__ off, int64_t n,
+                                          int64_t x) {
+  int64_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// active row index -> (sequence, packed row)
+__device__ __forceinline__ void act_row(const Batch& bt, int64_t ar, int64_t& seq,
+                                        int64_t& row) {
+  const int64_t k = find_k(bt.act_row_off, bt.n_act, ar);
+  seq = __ldg(bt.act_seq + k);
+  row = __ldg(bt.offsets + seq) + (ar - __ldg(bt.act_row_off + k));
+}
+
+// active chunk index -> (sequence, global chunk index, first row, row count)
+__device__ __forceinline__ void act_chunk(const Batch& bt, int64_t ac, int64_t& seq,
+                                          int64_t& c, int64_t& r0, int32_t& n) {
+  const int64_t k = find_k(bt.act_chunk_off, bt.n_act, ac);
+  seq = __ldg(bt.act_seq + k);
+  const int64_t j = ac - __ldg(bt.act_chunk_off + k);
+  c = __ldg(bt.chunk_first + seq) + j;
+  const int64_t s0 = __ldg(bt.offsets + seq), s1 = __ldg(bt.offsets + seq + 1);
+  r0 = s0 + (j << bt.log2L);
+  const int64_t e = r0 + bt.L;
+  n = (int32_t)((e < s1 ? e : s1) - r0);
 }
 
 // chunk c -> (sequence, first row, row count)

@@ -115,14 +115,11 @@ __global__ void __launch_bounds__(128) k_init(InitArgs<real> a) {
 // ----------------------------------------------------------------------------
 template <class real, int D, int KIND, int JAC>
 __global__ void __launch_bounds__(128) k_linearize(LinArgs<real> a) {
-  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  bool valid = row < a.bt.N;
-  int64_t seq = 0;
+  const int64_t ar = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool valid = ar < a.bt.act_rows;
+  int64_t seq = 0, row = 0;
   double mx = 0.0, sq = 0.0;
-  if (valid) {
-    seq = find_seq(a.bt.offsets, a.bt.B, row);
-    valid = a.info[seq].done == 0;
-  }
+  if (valid) act_row(a.bt, ar, seq, row);
   if (valid) {
     const int64_t first = __ldg(a.bt.offsets + seq);
     real sp[D], sc[D], F[D];
@@ -196,14 +193,11 @@ __global__ void __launch_bounds__(128) k_lin_ma(LinArgs<real> a) {
   constexpr int JC = D / LPR;
   constexpr bool WANTA = JAC == DEER_JAC_FULL || JAC == DEER_JAC_DIAG;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t row = tid / LPR;
+  const int64_t ar = tid / LPR;
   const int h = LPR == 2 ? (int)(tid & 1) : 0;
-  bool valid = row < a.bt.N;
-  int64_t seq = 0;
-  if (valid) {
-    seq = find_seq(a.bt.offsets, a.bt.B, row);
-    valid = a.info[seq].done == 0;
-  }
+  const bool valid = ar < a.bt.act_rows;
+  int64_t seq = 0, row = 0;
+  if (valid) act_row(a.bt, ar, seq, row);
   double mx = 0.0, sq = 0.0;
   if (valid) {
     real sp[D], sc[JC];
@@ -552,7 +546,7 @@ cudaError_t launch_init(const InitArgs<real>& a, cudaStream_t st) {
 
 template <class real, int KIND, int JAC>
 static cudaError_t lin_kind_jac(const LinArgs<real>& a, cudaStream_t st) {
-  const unsigned g = grid_for(a.bt.N, 128);
+  const unsigned g = grid_for(a.bt.act_rows, 128);
   const int d = a.dv.d;
   if constexpr (KIND == DEER_F_MASSACTION_EULER || KIND == DEER_F_MASSACTION_RK4) {
     constexpr bool RK4 = KIND == DEER_F_MASSACTION_RK4;
@@ -564,7 +558,7 @@ static cudaError_t lin_kind_jac(const LinArgs<real>& a, cudaStream_t st) {
           if constexpr (sizeof(real) == 4) {
             k_lin_ma<real, 8, 1, RK4, JAC><<<g, 128, 0, st>>>(a);
           } else {
-            k_lin_ma<real, 8, 2, RK4, JAC><<<grid_for(a.bt.N * 2, 128), 128, 0, st>>>(a);
+            k_lin_ma<real, 8, 2, RK4, JAC><<<grid_for(a.bt.act_rows * 2, 128), 128, 0, st>>>(a);
           }
           break;
         default: return cudaErrorInvalidValue;
@@ -609,7 +603,7 @@ static cudaError_t lin_kind(const LinArgs<real>& a, cudaStream_t st) {
 
 template <class real>
 cudaError_t launch_linearize(const LinArgs<real>& a, cudaStream_t st) {
-  if (a.bt.N == 0) return cudaSuccess;
+  if (a.bt.act_rows == 0) return cudaSuccess;
   switch (a.dv.kind) {
     case DEER_F_BRUSSELATOR_EULER: return lin_kind<real, DEER_F_BRUSSELATOR_EULER>(a, st);
     case DEER_F_MASSACTION_EULER: return lin_kind<real, DEER_F_MASSACTION_EULER>(a, st);

@@ -12,42 +12,96 @@
 namespace deer {
 
 // ----------------------------------------------------------------------------
-// Convergence / merit (one block): per sequence max |r| vs tol (float64), merit 1/2 |r|^2.
+// Convergence / merit (one block): per sequence max |r| / max(1, |s|) vs tol, merit
+// 1/2 |r|^2; then the sequences still iterating are compacted (in order) into the active
+// lists that size and index every later launch. Thread t owns a contiguous range of
+// sequences so that a block-wide exclusive scan gives each its output offsets.
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_check(CheckArgs a) {
-  __shared__ int s_active, s_nonfinite;
-  __shared__ unsigned long long s_rows;
-  if (threadIdx.x == 0) { s_active = 0; s_nonfinite = 0; s_rows = 0ull; }
-  __syncthreads();
-  int active = 0, nonfinite = 0;
-  unsigned long long rows = 0;
-  for (int64_t seq = threadIdx.x; seq < a.B; seq += blockDim.x) {
-    SeqInfo inf = a.info[seq];
-    if (inf.done) continue;
-    SeqAcc acc = a.acc[seq];
-    a.acc[seq] = SeqAcc{0ull, 0.0};
-    const double mr = __longlong_as_double((long long)acc.max_bits);
-    inf.max_resid = mr;
-    inf.merit = 0.5 * acc.sumsq;
-    if (!(mr <= DBL_MAX)) ++nonfinite;  // NaN or Inf
-    if (mr <= a.tol) {
-      inf.done = 1;
-      inf.iters = a.it;
-    } else {
-      inf.iters = a.it < a.max_iters ? a.it + 1 : a.it;
-      ++active;
-      rows += (unsigned long long)(a.offsets[seq + 1] - a.offsets[seq]);
-    }
-    a.info[seq] = inf;
+__device__ __forceinline__ void block_excl_scan3(long long& a, long long& b, long long& c,
+                                                 long long& ta, long long& tb, long long& tc) {
+  __shared__ long long sa[32], sb[32], sc[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned full = 0xffffffffu;
+  long long ia = a, ib = b, ic = c;  // inclusive warp scan
+  for (int o = 1; o < 32; o <<= 1) {
+    long long xa = __shfl_up_sync(full, ia, o), xb = __shfl_up_sync(full, ib, o),
+              xc = __shfl_up_sync(full, ic, o);
+    if (lane >= o) { ia += xa; ib += xb; ic += xc; }
   }
-  if (active) atomicAdd(&s_active, active);
+  if (lane == 31) { sa[warp] = ia; sb[warp] = ib; sc[warp] = ic; }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    long long va = lane < nw ? sa[lane] : 0, vb = lane < nw ? sb[lane] : 0,
+              vc = lane < nw ? sc[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      long long xa = __shfl_up_sync(full, va, o), xb = __shfl_up_sync(full, vb, o),
+                xc = __shfl_up_sync(full, vc, o);
+      if (lane >= o) { va += xa; vb += xb; vc += xc; }
+    }
+    if (lane < nw) { sa[lane] = va; sb[lane] = vb; sc[lane] = vc; }
+  }
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  const long long wa = warp > 0 ? sa[warp - 1] : 0, wb = warp > 0 ? sb[warp - 1] : 0,
+                  wc = warp > 0 ? sc[warp - 1] : 0;
+  ta = sa[nw - 1]; tb = sb[nw - 1]; tc = sc[nw - 1];
+  a = wa + ia - a; b = wb + ib - b; c = wc + ic - c;
+}
+
+__global__ void __launch_bounds__(1024) k_check(CheckArgs a) {
+  const int64_t per = (a.B + blockDim.x - 1) / blockDim.x;
+  const int64_t lo = threadIdx.x * per;
+  const int64_t hi = lo + per < a.B ? lo + per : a.B;
+  int nonfinite = 0;
+  long long n_act = 0, rows = 0, chunks = 0;
+  for (int64_t seq = lo; seq < hi; ++seq) {
+    SeqInfo inf = a.info[seq];
+    if (!inf.done && !a.compact_only) {
+      SeqAcc acc = a.acc[seq];
+      a.acc[seq] = SeqAcc{0ull, 0.0};
+      const double mr = __longlong_as_double((long long)acc.max_bits);
+      inf.max_resid = mr;
+      inf.merit = 0.5 * acc.sumsq;
+      if (!(mr <= DBL_MAX)) ++nonfinite;  // NaN or Inf
+      if (mr <= a.tol) {
+        inf.done = 1;
+        inf.iters = a.it;
+      } else {
+        inf.iters = a.it < a.max_iters ? a.it + 1 : a.it;
+      }
+      a.info[seq] = inf;
+    }
+    if (!inf.done) {
+      ++n_act;
+      rows += a.offsets[seq + 1] - a.offsets[seq];
+      chunks += a.chunk_first[seq + 1] - a.chunk_first[seq];
+    }
+  }
+  long long tn, tr, tc;
+  long long pn = n_act, pr = rows, pc = chunks;
+  block_excl_scan3(pn, pr, pc, tn, tr, tc);
+  for (int64_t seq = lo; seq < hi; ++seq) {
+    if (a.info[seq].done) continue;
+    a.act_seq[pn] = seq;
+    a.act_row_off[pn] = pr;
+    a.act_chunk_off[pn] = pc;
+    ++pn;
+    pr += a.offsets[seq + 1] - a.offsets[seq];
+    pc += a.chunk_first[seq + 1] - a.chunk_first[seq];
+  }
+  __shared__ int s_nonfinite;
+  if (threadIdx.x == 0) s_nonfinite = 0;
+  __syncthreads();
   if (nonfinite) atomicAdd(&s_nonfinite, nonfinite);
-  if (rows) atomicAdd(&s_rows, rows);
   __syncthreads();
   if (threadIdx.x == 0) {
-    a.flags->n_active = s_active;
+    a.act_row_off[tn] = tr;
+    a.act_chunk_off[tn] = tc;
+    a.flags->n_active = (int32_t)tn;
     a.flags->n_nonfinite = s_nonfinite;
-    a.flags->active_rows = (long long)s_rows;
+    a.flags->active_rows = tr;
+    a.flags->active_chunks = tc;
   }
 }
 
@@ -71,12 +125,11 @@ __device__ __forceinline__ real reset_val(real v, real thr, int reset) {
 // ----------------------------------------------------------------------------
 template <class real, int D>
 __global__ void __launch_bounds__(128) k_dense_chunk(DenseScanArgs<real> a) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= a.bt.n_chunks) return;
-  int64_t seq, r0;
+  const int64_t ac = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (ac >= a.bt.act_chunks) return;
+  int64_t seq, c, r0;
   int n;
-  chunk_rows(a.bt, c, seq, r0, n);
-  if (a.info[seq].done) return;
+  act_chunk(a.bt, ac, seq, c, r0, n);
   // the first chunk of a sequence starts from Delta_0 = 0: its carry never multiplies P
   const bool need_P = c != __ldg(a.bt.chunk_first + seq);
   real P[D][D], v[D];
@@ -128,9 +181,9 @@ __global__ void __launch_bounds__(128) k_dense_chunk(DenseScanArgs<real> a) {
 
 template <class real, int D>
 __global__ void __launch_bounds__(128) k_dense_carry(DenseScanArgs<real> a) {
-  const int64_t seq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (seq >= a.bt.B) return;
-  if (a.info[seq].done) return;
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= a.bt.n_act) return;
+  const int64_t seq = a.bt.act_seq[k];
   const int64_t c0 = a.bt.chunk_first[seq], c1 = a.bt.chunk_first[seq + 1];
   real x[D];
 #pragma unroll U<D>::n
@@ -162,12 +215,11 @@ __global__ void __launch_bounds__(128) k_dense_carry(DenseScanArgs<real> a) {
 
 template <class real, int D>
 __global__ void __launch_bounds__(128) k_dense_apply(DenseScanArgs<real> a) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= a.bt.n_chunks) return;
-  int64_t seq, r0;
+  const int64_t ac = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (ac >= a.bt.act_chunks) return;
+  int64_t seq, c, r0;
   int n;
-  chunk_rows(a.bt, c, seq, r0, n);
-  if (a.info[seq].done) return;
+  act_chunk(a.bt, ac, seq, c, r0, n);
   real x[D];
 #pragma unroll U<D>::n
   for (int i = 0; i < D; ++i) x[i] = a.cin[c * D + i];
@@ -194,8 +246,8 @@ __global__ void __launch_bounds__(128) k_dense_apply(DenseScanArgs<real> a) {
 
 template <class real, int D>
 static void dense_launch(const DenseScanArgs<real>& a, cudaStream_t st) {
-  const unsigned gc = grid_for(a.bt.n_chunks, 128);
-  const unsigned gs = grid_for(a.bt.B, 128);
+  const unsigned gc = grid_for(a.bt.act_chunks, 128);
+  const unsigned gs = grid_for(a.bt.n_act, 128);
   k_dense_chunk<real, D><<<gc, 128, 0, st>>>(a);
   k_dense_carry<real, D><<<gs, 128, 0, st>>>(a);
   k_dense_apply<real, D><<<gc, 128, 0, st>>>(a);
@@ -204,7 +256,7 @@ static void dense_launch(const DenseScanArgs<real>& a, cudaStream_t st) {
 
 template <class real>
 cudaError_t launch_dense_scan(const DenseScanArgs<real>& a, cudaStream_t st) {
-  if (a.bt.N == 0) return cudaSuccess;
+  if (a.bt.act_rows == 0) return cudaSuccess;
   switch (a.d) {
     case 1: dense_launch<real, 1>(a, st); break;
     case 2: dense_launch<real, 2>(a, st); break;
@@ -237,13 +289,12 @@ __device__ __forceinline__ void diag_elem(const DiagScanArgs<real>& a, int64_t r
 template <class real>
 __global__ void __launch_bounds__(128) k_diag_chunk(DiagScanArgs<real> a) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= a.bt.n_chunks * a.d) return;
-  const int64_t c = id / a.d;
-  const int j = (int)(id - c * a.d);
-  int64_t seq, r0;
+  if (id >= a.bt.act_chunks * a.d) return;
+  const int64_t ac = id / a.d;
+  const int j = (int)(id - ac * a.d);
+  int64_t seq, c, r0;
   int n;
-  chunk_rows(a.bt, c, seq, r0, n);
-  if (a.info[seq].done) return;
+  act_chunk(a.bt, ac, seq, c, r0, n);
   real A = real(1), Bv = real(0);
   for (int t = 0; t < n; ++t) {
     real at, bt;
@@ -258,10 +309,10 @@ __global__ void __launch_bounds__(128) k_diag_chunk(DiagScanArgs<real> a) {
 template <class real>
 __global__ void __launch_bounds__(128) k_diag_carry(DiagScanArgs<real> a) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= a.bt.B * a.d) return;
-  const int64_t seq = id / a.d;
-  const int j = (int)(id - seq * a.d);
-  if (a.info[seq].done) return;
+  if (id >= a.bt.n_act * a.d) return;
+  const int64_t k = id / a.d;
+  const int j = (int)(id - k * a.d);
+  const int64_t seq = a.bt.act_seq[k];
   real x = a.s0[seq * a.d + j];
   const int64_t c0 = a.bt.chunk_first[seq], c1 = a.bt.chunk_first[seq + 1];
   for (int64_t c = c0; c < c1; ++c) {
@@ -273,13 +324,12 @@ __global__ void __launch_bounds__(128) k_diag_carry(DiagScanArgs<real> a) {
 template <class real>
 __global__ void __launch_bounds__(128) k_diag_apply(DiagScanArgs<real> a) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= a.bt.n_chunks * a.d) return;
-  const int64_t c = id / a.d;
-  const int j = (int)(id - c * a.d);
-  int64_t seq, r0;
+  if (id >= a.bt.act_chunks * a.d) return;
+  const int64_t ac = id / a.d;
+  const int j = (int)(id - ac * a.d);
+  int64_t seq, c, r0;
   int n;
-  chunk_rows(a.bt, c, seq, r0, n);
-  if (a.info[seq].done) return;
+  act_chunk(a.bt, ac, seq, c, r0, n);
   real x = a.cin[c * a.d + j];
   for (int t = 0; t < n; ++t) {
     real at, bt;
@@ -304,13 +354,12 @@ __device__ __forceinline__ void mob_elem(real at, real s2, real& m00, real& m01,
 template <class real>
 __global__ void __launch_bounds__(128) k_elk_chunk(DiagScanArgs<real> a) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= a.bt.n_chunks * a.d) return;
-  const int64_t c = id / a.d;
-  const int j = (int)(id - c * a.d);
-  int64_t seq, r0;
+  if (id >= a.bt.act_chunks * a.d) return;
+  const int64_t ac = id / a.d;
+  const int j = (int)(id - ac * a.d);
+  int64_t seq, c, r0;
   int n;
-  chunk_rows(a.bt, c, seq, r0, n);
-  if (a.info[seq].done) return;
+  act_chunk(a.bt, ac, seq, c, r0, n);
   real p00 = 1, p01 = 0, p10 = 0, p11 = 1;
   for (int t = 0; t < n; ++t) {
     const int64_t row = r0 + t;
@@ -330,10 +379,10 @@ __global__ void __launch_bounds__(128) k_elk_chunk(DiagScanArgs<real> a) {
 template <class real>
 __global__ void __launch_bounds__(128) k_elk_carry(DiagScanArgs<real> a) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= a.bt.B * a.d) return;
-  const int64_t seq = id / a.d;
-  const int j = (int)(id - seq * a.d);
-  if (a.info[seq].done) return;
+  if (id >= a.bt.n_act * a.d) return;
+  const int64_t k = id / a.d;
+  const int j = (int)(id - k * a.d);
+  const int64_t seq = a.bt.act_seq[k];
   real P = real(0);  // s_0 is known exactly
   const int64_t c0 = a.bt.chunk_first[seq], c1 = a.bt.chunk_first[seq + 1];
   for (int64_t c = c0; c < c1; ++c) {
@@ -346,13 +395,12 @@ __global__ void __launch_bounds__(128) k_elk_carry(DiagScanArgs<real> a) {
 template <class real>
 __global__ void __launch_bounds__(128) k_elk_gamma(DiagScanArgs<real> a) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= a.bt.n_chunks * a.d) return;
-  const int64_t c = id / a.d;
-  const int j = (int)(id - c * a.d);
-  int64_t seq, r0;
+  if (id >= a.bt.act_chunks * a.d) return;
+  const int64_t ac = id / a.d;
+  const int j = (int)(id - ac * a.d);
+  int64_t seq, c, r0;
   int n;
-  chunk_rows(a.bt, c, seq, r0, n);
-  if (a.info[seq].done) return;
+  act_chunk(a.bt, ac, seq, c, r0, n);
   real P = a.pin[c * a.d + j];
   for (int t = 0; t < n; ++t) {
     const int64_t row = r0 + t;
@@ -366,9 +414,9 @@ __global__ void __launch_bounds__(128) k_elk_gamma(DiagScanArgs<real> a) {
 
 template <class real>
 cudaError_t launch_diag_scan(const DiagScanArgs<real>& a, cudaStream_t st) {
-  if (a.bt.N == 0) return cudaSuccess;
-  const unsigned gc = grid_for(a.bt.n_chunks * a.d, 128);
-  const unsigned gs = grid_for(a.bt.B * a.d, 128);
+  if (a.bt.act_rows == 0) return cudaSuccess;
+  const unsigned gc = grid_for(a.bt.act_chunks * a.d, 128);
+  const unsigned gs = grid_for(a.bt.n_act * a.d, 128);
   if (a.elk) {
     k_elk_chunk<real><<<gc, 128, 0, st>>>(a);
     k_elk_carry<real><<<gs, 128, 0, st>>>(a);

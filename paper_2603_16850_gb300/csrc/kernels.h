@@ -49,11 +49,16 @@ __device__ __forceinline__ void rollout_rows(const RolloutArgs<real>& a, int64_t
 struct CheckArgs {
   int64_t B;
   const int64_t* offsets;
+  const int64_t* chunk_first;
   SeqAcc* acc;
   SeqInfo* info;
   Flags* flags;
+  int64_t* act_seq;        // outputs: compacted active set
+  int64_t* act_row_off;
+  int64_t* act_chunk_off;
   double tol;
   int it, max_iters;
+  int compact_only;        // 1: rebuild the active set from info without testing
 };
 
 // Dense (FULL) correction-form scan: Delta_t = A_t Delta_{t-1} + b_t, Delta_0 = 0,

@@ -16,9 +16,10 @@ from oracle import newton as onewton
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda"
-# float32 solves stop at a scaled residual of 5e-7 (about four units of float32 roundoff),
-# which keeps the accumulated trajectory error below the 1e-5 parity bound
-FP32_TOL = 5e-7
+# float32 solves stop at a scaled residual of 1e-7 (below one unit of float32 roundoff at
+# |s| = 1, yet reached in a few iterations); looser tests leave residuals with a common
+# sign that add up along conserved directions of the kinetics
+FP32_TOL = 1e-7
 
 
 def _deer():
@@ -234,10 +235,12 @@ def test_full_size_batched_massaction_fp32_sampled():
     p = _ma_problem(B, d, R, T, seed=0)
     dyn = _ma_dyn(p, torch.float32)
     s, info = deer.deer_solve(dyn, _t(p["s0"], torch.float32), T, jac="full", tol=FP32_TOL,
-                              prec="fp32", init="s0", reset=True)
+                              prec="fp32", init="zeros", reset=True)
     assert bool(info.converged.all()), (info.max_resid.max(), info.iters.max())
+    assert float(info.max_resid.max()) <= FP32_TOL
     rng = np.random.default_rng(0)
-    pick = rng.choice(B, size=3, replace=False)
+    # two random systems and the one that needed the most iterations
+    pick = np.concatenate([rng.choice(B, size=2, replace=False), [int(info.iters.argmax())]])
     sub = odyn.MassAction(p["topology"][pick], p["params"][pick], p["dt"], "rk4", d=d)
     roll = onewton.rollout(sub, p["s0"][pick], T)
     sv = s.view(B, T, d)
