@@ -120,6 +120,10 @@ typedef struct {
   int32_t reset;      /* reset heuristic (Sec. 3.2): entries that are non-finite or exceed
                          1e30 (float64) / 1e18 (float32) after a scan are set to 0 */
   int32_t chunk;      /* scan chunk length; 0 = automatic. Power of two in [8, 1024]. */
+  int32_t confirm;    /* a sequence converges when `confirm` consecutive iterates pass the
+                         test (<= 1 means one). With 2 the returned iterate has had one more
+                         Newton step after first passing, which removes the smooth part of
+                         the remaining error when the test sits near float32 roundoff. */
 } deer_options;
 
 typedef struct {
@@ -129,7 +133,8 @@ typedef struct {
   double max_resid;   /* max_t ||r_t||_inf of the returned iterate */
 } deer_info;
 
-/* Fills `opt` with defaults: cap T, tol 1e-10, FULL, no damping, INIT_S0, FP64, auto chunk. */
+/* Fills `opt` with defaults: cap T, tol 1e-10, FULL, no damping, INIT_S0, FP64, auto chunk,
+   confirm 1. */
 void deer_default_options(deer_options* opt);
 
 /* Workspace bytes needed by deer_solve / deer_solve_batched for `batch` sequences

@@ -127,13 +127,15 @@ def initial_guess(dyn, s0, T, init="s0", user=None):
 
 
 def solve(dyn, s0, T, mode="full", damp="none", damp_param=0.0, tol=1e-10, max_iters=None,
-          init="s0", user=None, reset=False, reset_threshold=1e30, record=False):
+          init="s0", user=None, reset=False, reset_threshold=1e30, record=False, confirm=1):
     """Algorithm alg:deer (ParallelNewton), per sequence of the batch.
 
     Iteration i evaluates r(s^{(i)}); a sequence whose scaled residual
     max_t,i |r_t,i| / max(1, |s_t,i|) is <= tol is converged and keeps s^{(i)} (the error
     test of the algorithm, applied to the current iterate). Otherwise one LDS solve gives s^{(i+1)}. ``iters`` counts the LDS
     solves. The cap defaults to T, which suffices by Prop. global_convergence.
+    With ``confirm`` > 1 a sequence converges only after that many consecutive iterates
+    pass the test.
     """
     from . import elk as _elk
 
@@ -147,6 +149,7 @@ def solve(dyn, s0, T, mode="full", damp="none", damp_param=0.0, tol=1e-10, max_i
     hist = []
     max_resid = np.full(B, np.inf)
     merit = np.full(B, np.inf)
+    passes = np.zeros(B, dtype=np.int64)
     for i in range(max_iters + 1):
         r = residual(dyn, s0, s)
         mr = scaled_residual_max(r, s)
@@ -156,7 +159,8 @@ def solve(dyn, s0, T, mode="full", damp="none", damp_param=0.0, tol=1e-10, max_i
         merit[upd] = mer[upd]
         if record:
             hist.append((mr.copy(), mer.copy()))
-        converged |= mr <= tol
+        passes = np.where(mr <= tol, passes + 1, 0)
+        converged |= passes >= max(confirm, 1)
         if np.all(converged) or i == max_iters:
             break
         active = ~converged

@@ -107,7 +107,8 @@ def _dtype(prec: str):
     return torch.float32 if prec == "fp32" else torch.float64
 
 
-def _options(jac, damp, damp_param, tol, max_iters, init, prec, reset, chunk) -> N.deer_options:
+def _options(jac, damp, damp_param, tol, max_iters, init, prec, reset, chunk,
+             confirm=1) -> N.deer_options:
     o = N.deer_options()
     o.max_iters = int(max_iters)
     o.tol = float(tol)
@@ -118,6 +119,7 @@ def _options(jac, damp, damp_param, tol, max_iters, init, prec, reset, chunk) ->
     o.prec = N.PREC[prec]
     o.reset = int(bool(reset))
     o.chunk = int(chunk)
+    o.confirm = int(confirm)
     return o
 
 
@@ -138,7 +140,7 @@ def deer_workspace_bytes(dyn: Dynamics, batch: int, total_steps: int, **opts) ->
 
 def _opt_defaults(opts):
     base = dict(jac="full", damp="none", damp_param=0.0, tol=1e-10, max_iters=0, init="s0",
-                prec="fp64", reset=False, chunk=0)
+                prec="fp64", reset=False, chunk=0, confirm=1)
     base.update(opts)
     return base
 
@@ -192,7 +194,7 @@ def deer_solve(dyn: Dynamics, s0: torch.Tensor, T: int, x: Optional[torch.Tensor
 
     Options (see deer_options in include/deer.h): jac ('full'|'diag'|'identity'|'zero'),
     damp ('none'|'elk'|'scale'|'clip'), damp_param, tol, max_iters, init
-    ('zeros'|'s0'|'jacobi'|'user'), prec ('fp64'|'fp32'), reset, chunk.
+    ('zeros'|'s0'|'jacobi'|'user'), prec ('fp64'|'fp32'), reset, chunk, confirm.
     """
     opts = _opt_defaults(opts)
     host = not s0.is_cuda

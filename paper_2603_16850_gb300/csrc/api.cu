@@ -282,7 +282,8 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   CheckArgs ca{B, d_off, d_cf, acc, info, flags,
                reinterpret_cast<int64_t*>(ws + ly.act_seq),
                reinterpret_cast<int64_t*>(ws + ly.act_row_off),
-               reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), o->tol, 0, max_iters, 1};
+               reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), o->tol, 0, max_iters, 1,
+               o->confirm > 1 ? o->confirm : 1};
   DEER_CK(launch_check(ca, st));  // every sequence starts active
   ca.compact_only = 0;
 
@@ -408,6 +409,7 @@ void deer_default_options(deer_options* o) {
   o->prec = DEER_FP64;
   o->reset = 0;
   o->chunk = 0;
+  o->confirm = 1;
 }
 
 size_t deer_workspace_bytes(const deer_dynamics* f, int64_t batch, int64_t total_steps,
@@ -543,7 +545,7 @@ static deer_status grad_impl(const deer_dynamics* f, int64_t B, int64_t T, const
     CheckArgs ca{B, d_off, d_cf, acc, info, flags,
                  reinterpret_cast<int64_t*>(ws + ly.act_seq),
                  reinterpret_cast<int64_t*>(ws + ly.act_row_off),
-                 reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), 0.0, 0, 0, 1};
+                 reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), 0.0, 0, 0, 1, 1};
     DEER_CK(launch_check(ca, st));
   }
   DynView<real> dv = make_view<real>(f, x_, ws, ly);

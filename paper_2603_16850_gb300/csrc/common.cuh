@@ -21,6 +21,8 @@ struct SeqInfo {                // persistent during one solve
   int32_t done;                 // 1 once converged (masked out of later iterations)
   double merit;
   double max_resid;
+  int32_t passes;               // consecutive iterates that passed the test
+  int32_t pad;
 };
 
 struct Flags {                  // read back by the host once per iteration

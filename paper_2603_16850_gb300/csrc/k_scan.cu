@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(1024) k_check(CheckArgs a) {
       inf.max_resid = mr;
       inf.merit = 0.5 * acc.sumsq;
       if (!(mr <= DBL_MAX)) ++nonfinite;  // NaN or Inf
-      if (mr <= a.tol) {
+      inf.passes = mr <= a.tol ? inf.passes + 1 : 0;
+      if (inf.passes >= a.confirm) {
         inf.done = 1;
         inf.iters = a.it;
       } else {

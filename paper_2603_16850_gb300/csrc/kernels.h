@@ -59,6 +59,7 @@ struct CheckArgs {
   double tol;
   int it, max_iters;
   int compact_only;        // 1: rebuild the active set from info without testing
+  int confirm;             // consecutive passing iterates needed
 };
 
 // Dense (FULL) correction-form scan: Delta_t = A_t Delta_{t-1} + b_t, Delta_0 = 0,

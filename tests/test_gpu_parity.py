@@ -16,10 +16,13 @@ from oracle import newton as onewton
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda"
-# float32 solves stop at a scaled residual of 1e-7 (below one unit of float32 roundoff at
-# |s| = 1, yet reached in a few iterations); looser tests leave residuals with a common
-# sign that add up along conserved directions of the kinetics
-FP32_TOL = 1e-7
+# float32 solves: scaled residual 5e-7 (a few units of float32 roundoff, so the test can
+# always be met) on two consecutive iterates. The second pass puts one more Newton step
+# on top of the first, which removes the smooth part of the remaining error; a single
+# pass leaves residuals with a common sign that add up along the conserved directions
+# of the kinetics.
+FP32_TOL = 5e-7
+FP32 = dict(tol=FP32_TOL, confirm=2, prec="fp32")
 
 
 def _deer():
@@ -118,8 +121,8 @@ def test_massaction_rk4_fp32_full(d, R):
     B, T = 4, 700
     p = _ma_problem(B, d, R, T, seed=d)
     dyn = _ma_dyn(p, torch.float32)
-    s, info = deer.deer_solve(dyn, _t(p["s0"], torch.float32), T, jac="full", tol=FP32_TOL,
-                              prec="fp32", init="s0", reset=True)
+    s, info = deer.deer_solve(dyn, _t(p["s0"], torch.float32), T, jac="full", init="s0",
+                              reset=True, **FP32)
     assert bool(info.converged.all()), info
     roll = onewton.rollout(_ma_oracle(p), p["s0"], T)
     for b in range(B):
@@ -134,9 +137,8 @@ def test_gru_quasi_deer(d, prec):
     g = synth.gru(B, T, d, d, seed=1)
     dyn = deer.Dynamics.gru(_t(g["W"], dt), _t(g["U"], dt))
     x = _t(g["x"].reshape(-1, d), dt)
-    tol = 1e-12 if prec == "fp64" else FP32_TOL
-    s, info = deer.deer_solve(dyn, _t(g["s0"], dt), T, x, jac="diag", tol=tol, prec=prec,
-                              init="zeros")
+    extra = dict(tol=1e-12, prec="fp64") if prec == "fp64" else FP32
+    s, info = deer.deer_solve(dyn, _t(g["s0"], dt), T, x, jac="diag", init="zeros", **extra)
     assert bool(info.converged.all())
     roll = onewton.rollout(odyn.GRU(g["W"], g["U"], g["x"]), g["s0"], T)
     lim = 1e-10 if prec == "fp64" else 1e-5
@@ -234,8 +236,8 @@ def test_full_size_batched_massaction_fp32_sampled():
     B, d, R, T = 4096, 8, 12, 16384
     p = _ma_problem(B, d, R, T, seed=0)
     dyn = _ma_dyn(p, torch.float32)
-    s, info = deer.deer_solve(dyn, _t(p["s0"], torch.float32), T, jac="full", tol=FP32_TOL,
-                              prec="fp32", init="zeros", reset=True)
+    s, info = deer.deer_solve(dyn, _t(p["s0"], torch.float32), T, jac="full", init="zeros",
+                              reset=True, **FP32)
     assert bool(info.converged.all()), (info.max_resid.max(), info.iters.max())
     assert float(info.max_resid.max()) <= FP32_TOL
     rng = np.random.default_rng(0)
