@@ -86,13 +86,21 @@ static bool d_supported(int kind, int d, int jac) {
 // Everything the solver carves out of the caller's workspace.
 struct Layout {
   size_t offsets, chunk_first, act_seq, act_row_off, act_chunk_off, acc, info, flags, ma, gru_M,
-      A, b, aggP, aggv, cin, gam, mob, pin, total;
+      A, b, aggP, aggv, cin, gam, mob, pin, lb_ticket, lb_flags, lb_agg, lb_pre, total;
   int64_t n_chunks_max;
   int64_t ma_stride, n_ma;
   int L;
 };
 
+// Diagonal-family solves without Kalman damping run the single-pass look-back scan when
+// d is a multiple of 4; its tile length is fixed by d.
+static bool use_diag_lookback(const deer_options* o, int d) {
+  return o->jac != DEER_JAC_FULL && o->damp != DEER_DAMP_ELK && d % 4 == 0 && d >= 4 &&
+         d <= 64;
+}
+
 static int choose_chunk(const deer_options* o, int d) {
+  if (use_diag_lookback(o, d)) return diag_lb_chunk(d);
   if (o->chunk > 0) return o->chunk;
   if (o->jac == DEER_JAC_FULL) return d >= 16 ? 32 : 64;
   return 128;
@@ -142,6 +150,13 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
     ly.gam = take((size_t)N * d * rs);
     ly.mob = take((size_t)C * d * 4 * rs);
     ly.pin = take((size_t)C * d * rs);
+  }
+  ly.lb_ticket = ly.lb_flags = ly.lb_agg = ly.lb_pre = p;
+  if (use_diag_lookback(o, d)) {
+    ly.lb_ticket = take(256);
+    ly.lb_flags = take((size_t)C * 4);
+    ly.lb_agg = take((size_t)C * d * 2 * rs);
+    ly.lb_pre = take((size_t)C * d * rs);
   }
   ly.total = p;
   return true;
@@ -329,6 +344,28 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     gsa.reset_thr = reset_thr;
   }
 
+  const bool lookback = use_diag_lookback(o, d);
+  DiagLBArgs<real> lba;
+  if (lookback) {
+    lba.bt = bt;
+    lba.d = d;
+    lba.amode = gsa.amode;
+    lba.aconst = gsa.aconst;
+    lba.a = gsa.a;
+    lba.b = gsa.b;
+    lba.s0 = s0;
+    lba.s = s;
+    lba.ticket = reinterpret_cast<unsigned*>(ws + ly.lb_ticket);
+    lba.flags = reinterpret_cast<unsigned*>(ws + ly.lb_flags);
+    lba.agg = reinterpret_cast<real*>(ws + ly.lb_agg);
+    lba.pre = reinterpret_cast<real*>(ws + ly.lb_pre);
+    lba.epoch = 0;
+    lba.status = flags;
+    lba.reset = o->reset;
+    lba.reset_thr = reset_thr;
+    DEER_CK(cudaMemsetAsync(lba.flags, 0, (size_t)ly.n_chunks_max * 4, st));
+  }
+
   deer_status status = DEER_OK;
   Flags hf;
   PhaseTimer pt(st);
@@ -348,6 +385,7 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     DEER_CK(cudaStreamSynchronize(st));
     bool stop = false;
     if (hf.bad_input) { status = DEER_ERR_INVALID; stop = true; }
+    else if (hf.timeout) { status = DEER_ERR_TIMEOUT; stop = true; }
     else if (hf.n_nonfinite > 0 && !o->reset) { status = DEER_ERR_NONFINITE; stop = true; }
     else if (hf.n_active == 0) stop = true;
     else if (it >= max_iters) { status = DEER_NOT_CONVERGED; stop = true; }
@@ -360,8 +398,15 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     if (!stop) {
       const int64_t s0c = g_launches.load();
       pt.begin(PH_SCAN);
-      if (o->jac == DEER_JAC_FULL) DEER_CK(launch_dense_scan<real>(dsa, st));
-      else DEER_CK(launch_diag_scan<real>(gsa, st));
+      if (o->jac == DEER_JAC_FULL) {
+        DEER_CK(launch_dense_scan<real>(dsa, st));
+      } else if (lookback) {
+        lba.bt = bt;
+        lba.epoch += 1;
+        DEER_CK(launch_diag_lookback<real>(lba, st));
+      } else {
+        DEER_CK(launch_diag_scan<real>(gsa, st));
+      }
       pt.end(PH_SCAN);
       scan_launches = g_launches.load() - s0c;
     }

@@ -1,0 +1,253 @@
+// Single-pass diagonal scan with decoupled look-back (quasi-DEER / Picard / Jacobi LDS,
+// Eq. quasi_lds in standard form): s_t = a_t * s_{t-1} + b_t, coordinate-wise, s_0 given.
+//
+// One CTA per tile = one chunk of L rows of one sequence, all d coordinates. Each thread
+// owns RPT consecutive rows of 4 coordinates (16-byte vector accesses). The tile scans its
+// rows in registers and shared memory (Kogge-Stone over the row sub-ranges), publishes its
+// aggregate, resolves the state entering the tile by looking back over the published
+// aggregates / prefixes of the preceding tiles of the same sequence, and writes s. a, b are
+// read once and s written once: 12 bytes per coordinate-step in float32.
+#include "kernels.h"
+
+namespace deer {
+
+template <class real>
+struct V4 { real x, y, z, w; };
+
+template <class real>
+__device__ __forceinline__ V4<real> ld4(const real* p) {
+  if constexpr (sizeof(real) == 4) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return {v.x, v.y, v.z, v.w};
+  } else {
+    double2 u = __ldg(reinterpret_cast<const double2*>(p));
+    double2 v = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    return {u.x, u.y, v.x, v.y};
+  }
+}
+
+template <class real>
+__device__ __forceinline__ void st4(real* p, const real (&v)[4]) {
+  if constexpr (sizeof(real) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int D>
+struct LBShape {
+  static constexpr int G = D / 4;                       // 4-coordinate groups
+  static constexpr int Q = 256 / G;                     // row sub-ranges per tile
+  static constexpr int L = D >= 8 ? 8192 / D : 1024;    // rows per tile
+  static constexpr int RPT = L / Q;                     // rows per thread
+};
+
+constexpr unsigned kSpinLimit = 1u << 22;  // bounded wait (about 0.3 s with backoff)
+
+template <class real, int D>
+__global__ void __launch_bounds__(256) k_diag_lb(DiagLBArgs<real> a) {
+  using S = LBShape<D>;
+  constexpr int Q = S::Q, G = S::G, RPT = S::RPT;
+  __shared__ real sA[Q][D];
+  __shared__ real sB[Q][D];
+  __shared__ real s_in[D];
+  __shared__ unsigned s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(a.ticket, 1u);
+  __syncthreads();
+  const int64_t ac = s_tile;
+  if (ac >= a.bt.act_chunks) return;  // uniform over the CTA
+  int64_t seq, c, r0;
+  int n;
+  act_chunk(a.bt, ac, seq, c, r0, n);
+  const int g = threadIdx.x % G, q = threadIdx.x / G;
+  const int k0 = 4 * g;
+
+  // load this thread's rows (identity elements past the end of a ragged tile)
+  real av[RPT][4], bv[RPT][4];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int lr = q * RPT + i;
+    if (lr < n) {
+      const int64_t off = (r0 + lr) * D + k0;
+      const V4<real> bb = ld4(a.b + off);
+      bv[i][0] = bb.x; bv[i][1] = bb.y; bv[i][2] = bb.z; bv[i][3] = bb.w;
+      if (a.amode == 0) {
+        const V4<real> aa = ld4(a.a + off);
+        av[i][0] = aa.x; av[i][1] = aa.y; av[i][2] = aa.z; av[i][3] = aa.w;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) av[i][k] = a.aconst;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) { av[i][k] = real(1); bv[i][k] = real(0); }
+    }
+  }
+  // thread aggregate (composition in row order)
+  real A[4], Bv[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) { A[k] = real(1); Bv[k] = real(0); }
+#pragma unroll
+  for (int i = 0; i < RPT; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Bv[k] = av[i][k] * Bv[k] + bv[i][k];
+      A[k] = av[i][k] * A[k];
+    }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) { sA[q][k0 + k] = A[k]; sB[q][k0 + k] = Bv[k]; }
+  __syncthreads();
+  // inclusive Kogge-Stone scan over the sub-ranges, per coordinate
+#pragma unroll
+  for (int off = 1; off < Q; off <<= 1) {
+    real pa[4], pb[4];
+    const bool has = q >= off;
+    if (has) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) { pa[k] = sA[q - off][k0 + k]; pb[k] = sB[q - off][k0 + k]; }
+    }
+    __syncthreads();
+    if (has) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        Bv[k] = A[k] * pb[k] + Bv[k];
+        A[k] = A[k] * pa[k];
+        sA[q][k0 + k] = A[k];
+        sB[q][k0 + k] = Bv[k];
+      }
+    }
+    __syncthreads();
+  }
+
+  // publish the tile aggregate and resolve the incoming state (first warp)
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const bool first = c == __ldg(a.bt.chunk_first + seq);
+    const unsigned ep = a.epoch << 2;
+    real* agg = a.agg + c * (int64_t)(2 * D);
+    real* pre = a.pre + c * (int64_t)D;
+    if (first) {
+      for (int k = lane; k < D; k += 32) {
+        const real sin = a.s0[seq * D + k];
+        s_in[k] = sin;
+        __stcg(pre + k, sA[Q - 1][k] * sin + sB[Q - 1][k]);
+      }
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_release(a.flags + c, ep | 2u);
+    } else {
+      for (int k = lane; k < D; k += 32) {
+        __stcg(agg + 2 * k, sA[Q - 1][k]);
+        __stcg(agg + 2 * k + 1, sB[Q - 1][k]);
+      }
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_release(a.flags + c, ep | 1u);
+      // look back over the predecessors of this sequence
+      real XA[(D + 31) / 32], XB[(D + 31) / 32];
+#pragma unroll
+      for (int j = 0; j < (D + 31) / 32; ++j) { XA[j] = real(1); XB[j] = real(0); }
+      int64_t p = c - 1;
+      unsigned spins = 0;
+      bool timed_out = false;
+      while (true) {
+        unsigned f = 0;
+        if (lane == 0) {
+          while (true) {
+            f = ld_acquire(a.flags + p);
+            if ((f >> 2) == a.epoch && (f & 3u) != 0u) break;
+            if (++spins > kSpinLimit) { f = 0; break; }
+            __nanosleep(64);
+          }
+        }
+        f = __shfl_sync(0xffffffffu, f, 0);
+        if (f == 0) { timed_out = true; break; }
+        if ((f & 3u) == 2u) {
+          const real* pp = a.pre + p * (int64_t)D;
+#pragma unroll
+          for (int j = 0; j < (D + 31) / 32; ++j) {
+            const int k = lane + 32 * j;
+            if (k < D) s_in[k] = XA[j] * __ldcg(pp + k) + XB[j];
+          }
+          break;
+        }
+        const real* ap = a.agg + p * (int64_t)(2 * D);
+#pragma unroll
+        for (int j = 0; j < (D + 31) / 32; ++j) {
+          const int k = lane + 32 * j;
+          if (k < D) {
+            const real Ap = __ldcg(ap + 2 * k), Bp = __ldcg(ap + 2 * k + 1);
+            XB[j] = XA[j] * Bp + XB[j];
+            XA[j] = XA[j] * Ap;
+          }
+        }
+        --p;
+      }
+      if (timed_out) {
+        if (lane == 0) atomicExch(&a.status->timeout, 1);
+        for (int k = lane; k < D; k += 32) s_in[k] = real(0);
+      }
+      for (int k = lane; k < D; k += 32) __stcg(pre + k, sA[Q - 1][k] * s_in[k] + sB[Q - 1][k]);
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_release(a.flags + c, ep | 2u);
+    }
+  }
+  __syncthreads();
+
+  // state entering this thread's rows = exclusive prefix applied to the tile's input
+  real x[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const real sin = s_in[k0 + k];
+    x[k] = q > 0 ? sA[q - 1][k0 + k] * sin + sB[q - 1][k0 + k] : sin;
+  }
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int lr = q * RPT + i;
+    if (lr < n) {
+      real o[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        x[k] = av[i][k] * x[k] + bv[i][k];
+        o[k] = (a.reset && !(x[k] <= a.reset_thr && x[k] >= -a.reset_thr)) ? real(0) : x[k];
+      }
+      st4(a.s + (r0 + lr) * D + k0, o);
+    }
+  }
+}
+
+template <class real>
+cudaError_t launch_diag_lookback(const DiagLBArgs<real>& a, cudaStream_t st) {
+  if (a.bt.act_chunks == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)a.bt.act_chunks;
+  switch (a.d) {
+    case 4: k_diag_lb<real, 4><<<grid, 256, 0, st>>>(a); break;
+    case 8: k_diag_lb<real, 8><<<grid, 256, 0, st>>>(a); break;
+    case 16: k_diag_lb<real, 16><<<grid, 256, 0, st>>>(a); break;
+    case 32: k_diag_lb<real, 32><<<grid, 256, 0, st>>>(a); break;
+    case 64: k_diag_lb<real, 64><<<grid, 256, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_diag_lookback<float>(const DiagLBArgs<float>&, cudaStream_t);
+template cudaError_t launch_diag_lookback<double>(const DiagLBArgs<double>&, cudaStream_t);
+
+}  // namespace deer

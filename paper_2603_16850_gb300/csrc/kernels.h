@@ -164,3 +164,35 @@ template <class real>
 cudaError_t launch_param_grad(const ParamGradArgs<real>& a, cudaStream_t st);
 
 }  // namespace deer
+
+namespace deer {
+
+// Single-pass diagonal scan with decoupled look-back (standard form, no damping):
+// one CTA per active chunk (tile), tiles taken in order from a ticket counter.
+template <class real>
+struct DiagLBArgs {
+  Batch bt;
+  int d;
+  int amode;            // 0 = read a, 1 = constant aconst
+  real aconst;
+  const real* a;        // [N][d]
+  const real* b;        // [N][d]
+  const real* s0;       // [B][d]
+  real* s;              // [N][d] output
+  unsigned* ticket;     // tile counter, zeroed before the launch
+  unsigned* flags;      // [n_chunks] (epoch << 2) | state, state 1 = aggregate, 2 = prefix
+  real* agg;            // [n_chunks][d][2] tile aggregates (A, B)
+  real* pre;            // [n_chunks][d] state at the end of the tile
+  unsigned epoch;       // distinct per launch within one solve (starts at 1)
+  Flags* status;        // timeout reporting
+  int reset;
+  real reset_thr;
+};
+
+// chunk length used by the look-back kernel for state size d (d % 4 == 0)
+inline int diag_lb_chunk(int d) { return d >= 8 ? 8192 / d : 1024; }
+
+template <class real>
+cudaError_t launch_diag_lookback(const DiagLBArgs<real>& a, cudaStream_t st);
+
+}  // namespace deer
