@@ -181,6 +181,25 @@ deer_status deer_rollout(const deer_dynamics* f, int64_t batch, int64_t T,
                          const int64_t* offsets, const void* s0, const void* x, void* s_out,
                          int32_t prec, deer_stream_t stream);
 
+/* deer_solve for callers that cannot allocate device memory when they solve: code that
+   runs while the allocator must not be touched (a cudaMalloc synchronises the device),
+   loops with a hard latency budget, embedders with a fixed memory pool. There is no
+   counterpart in the paper; this is a packaging of deer_solve. It takes no workspace: the
+   library keeps one fixed scratch area of deer_noalloc_scratch_bytes() (32 MiB) per device
+   in a __device__ array, present on every GPU that loads the library until the process
+   exits. Problems whose workspace (deer_workspace_bytes plus one deer_info per sequence)
+   does not fit are rejected with DEER_ERR_WORKSPACE (deer_last_cuda_error says how many
+   bytes they needed). The first call on a device looks up the array's device address with
+   the device current; make that first call before any stream capture. Every call reuses
+   the same array and clears what must start at zero, so calls that overlap on the GPU
+   (other streams or threads) race and must be serialised by the caller. Arguments and
+   results as deer_solve; nothing is allocated on the device or the host. */
+deer_status deer_solve_noalloc(const deer_dynamics* f, int64_t batch, int64_t T,
+                               const void* s0, const void* x, void* s_out,
+                               const deer_options* opt, deer_stream_t stream,
+                               deer_info* info);
+size_t deer_noalloc_scratch_bytes(void);
+
 /* Number of kernels this library enqueued since load (all entry points, all threads). */
 int64_t deer_kernel_launch_count(void);
 

@@ -69,6 +69,11 @@ SIGNATURES = {
                               C.POINTER(deer_options), C.c_void_p, C.c_size_t, C.c_void_p]),
     "deer_rollout": (C.c_int32, [C.POINTER(deer_dynamics), C.c_int64, C.c_int64, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "deer_solve_noalloc": (C.c_int32, [C.POINTER(deer_dynamics), C.c_int64, C.c_int64,
+                                       C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.POINTER(deer_options), C.c_void_p,
+                                       C.POINTER(deer_info)]),
+    "deer_noalloc_scratch_bytes": (C.c_size_t, []),
     "deer_kernel_launch_count": (C.c_int64, []),
     "deer_profile_enable": (None, [C.c_int32]),
     "deer_profile_reset": (None, []),

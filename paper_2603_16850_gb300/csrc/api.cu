@@ -711,3 +711,218 @@ const char* deer_last_cuda_error(void) { return g_err; }
 int32_t deer_version(void) { return 1; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// No-allocation entry point (deer_solve_noalloc).
+//
+// Some callers cannot allocate device memory when they solve: code that runs while other
+// work holds the allocator (a cudaMalloc synchronises the device), real-time loops whose
+// latency budget forbids allocation, and embedders whose memory pool is fixed up front.
+// For them the library carries one fixed scratch area per device in a file-scope
+// __device__ array and solves small problems inside it. The array exists on every GPU
+// that loads the library until the process exits; calls share it, so calls that overlap
+// on the GPU (two streams, two host threads) race and must be serialised by the caller.
+// Everything that must start at zero is cleared by each call.
+// ---------------------------------------------------------------------------
+namespace deer {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static void* g_noalloc_ptr[kMaxDevices] = {};
+static std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device, looked up once per device.
+static cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+// offsets[b] = b T and chunk_first[b] = b ceil(T / L) for a batch of equal lengths
+__global__ void k_uniform_tables(int64_t B, int64_t T, int64_t cps, int64_t* off,
+                                 int64_t* cf) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b > B) return;
+  off[b] = b * T;
+  cf[b] = b * cps;
+}
+
+__global__ void k_info_out(int64_t B, const SeqInfo* in, deer_info* out) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const SeqInfo s = in[b];
+  out[b] = deer_info{s.iters, s.done, s.merit, s.max_resid};
+}
+
+template <class real>
+static deer_status solve_noalloc_impl(const deer_dynamics* f, int64_t B, int64_t T,
+                                      const void* s0_, const void* x_, void* s_,
+                                      const deer_options* o, char* ws, cudaStream_t st,
+                                      deer_info* info_h) {
+  const int64_t N = B * T;
+  Layout ly;
+  if (!make_layout(f, B, N, o, ly)) return DEER_ERR_INVALID;
+  const size_t info_bytes = align_up((size_t)B * sizeof(deer_info));
+  if (ly.total + info_bytes > kNoAllocScratchBytes) {
+    snprintf(g_err, sizeof(g_err),
+             "deer_solve_noalloc: problem needs %zu bytes of scratch, the fixed area holds %zu",
+             ly.total + info_bytes, kNoAllocScratchBytes);
+    return DEER_ERR_WORKSPACE;
+  }
+  const int d = f->d;
+  const real* s0 = static_cast<const real*>(s0_);
+  real* s = static_cast<real*>(s_);
+  const int64_t cps = (T + ly.L - 1) / ly.L;
+  const int64_t nc = B * cps;
+  int64_t* d_off = reinterpret_cast<int64_t*>(ws + ly.offsets);
+  int64_t* d_cf = reinterpret_cast<int64_t*>(ws + ly.chunk_first);
+  k_uniform_tables<<<grid_for(B + 1, 128), 128, 0, st>>>(B, T, cps, d_off, d_cf);
+  note_launch();
+  DEER_CK(cudaGetLastError());
+  SeqAcc* acc = reinterpret_cast<SeqAcc*>(ws + ly.acc);
+  SeqInfo* info = reinterpret_cast<SeqInfo*>(ws + ly.info);
+  Flags* flags = reinterpret_cast<Flags*>(ws + ly.flags);
+  DEER_CK(cudaMemsetAsync(acc, 0, B * sizeof(SeqAcc), st));
+  DEER_CK(cudaMemsetAsync(info, 0, B * sizeof(SeqInfo), st));
+  DEER_CK(cudaMemsetAsync(flags, 0, sizeof(Flags), st));
+
+  Batch bt{B, N, d_off, d_cf, nc, ly.L, ilog2(ly.L),
+           reinterpret_cast<int64_t*>(ws + ly.act_seq),
+           reinterpret_cast<int64_t*>(ws + ly.act_row_off),
+           reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), B, N, nc};
+  DynView<real> dv = make_view<real>(f, x_, ws, ly);
+  if (ly.n_ma > 0) {
+    DEER_CK(launch_ma_setup<real>(ly.n_ma, d, f->n_reactions, static_cast<const real*>(f->params),
+                                  f->params_stride, f->topology, f->topology_stride,
+                                  reinterpret_cast<real*>(ws + ly.ma), ly.ma_stride,
+                                  &flags->bad_input, st));
+  }
+  if (f->kind == DEER_F_GRU) {
+    DEER_CK(launch_gru_setup<real>(d, static_cast<const real*>(f->params), f->d_in,
+                                   reinterpret_cast<real*>(ws + ly.gru_M), st));
+  }
+  if (o->init != DEER_INIT_USER) {
+    InitArgs<real> ia{dv, bt, s0, s, o->init};
+    DEER_CK(launch_init<real>(ia, st));
+  }
+  const int max_iters = o->max_iters > 0 ? o->max_iters : (int)(T > 0 ? T : 1);
+  const real reset_thr = sizeof(real) == 8 ? real(1e30) : real(1e18);
+
+  LinArgs<real> la{dv, bt, s0, s, reinterpret_cast<real*>(ws + ly.A),
+                   reinterpret_cast<real*>(ws + ly.b), acc, info, o->jac, o->damp,
+                   (real)o->damp_param};
+  CheckArgs ca{B, d_off, d_cf, acc, info, flags,
+               reinterpret_cast<int64_t*>(ws + ly.act_seq),
+               reinterpret_cast<int64_t*>(ws + ly.act_row_off),
+               reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), o->tol, 0, max_iters, 1,
+               o->confirm > 1 ? o->confirm : 1};
+  DEER_CK(launch_check(ca, st));
+  ca.compact_only = 0;
+
+  DenseScanArgs<real> dsa{bt, d, la.A, la.b, s, reinterpret_cast<real*>(ws + ly.aggP),
+                          reinterpret_cast<real*>(ws + ly.aggv),
+                          reinterpret_cast<real*>(ws + ly.cin), info, o->reset, reset_thr};
+  real ac = o->jac == DEER_JAC_IDENTITY ? real(1) : real(0);
+  if (o->damp == DEER_DAMP_SCALE) ac *= real(1) - (real)o->damp_param;
+  if (o->damp == DEER_DAMP_CLIP) {
+    const real rho = (real)o->damp_param;
+    ac = ac > rho ? rho : (ac < -rho ? -rho : ac);
+  }
+  const int elk = (o->damp == DEER_DAMP_ELK && o->damp_param > 0.0) ? 1 : 0;
+  DiagScanArgs<real> gsa{bt, d, o->jac == DEER_JAC_DIAG ? 0 : 1, ac, la.A, la.b, s0, s,
+                         reinterpret_cast<real*>(ws + ly.aggP),
+                         reinterpret_cast<real*>(ws + ly.aggv),
+                         reinterpret_cast<real*>(ws + ly.cin), info, elk,
+                         elk ? real(1.0 / o->damp_param) : real(0),
+                         reinterpret_cast<real*>(ws + ly.gam),
+                         reinterpret_cast<real*>(ws + ly.mob),
+                         reinterpret_cast<real*>(ws + ly.pin), o->reset, reset_thr};
+  const bool lookback = use_diag_lookback(o, d);
+  DiagLBArgs<real> lba{bt, d, gsa.amode, gsa.aconst, la.A, la.b, s0, s,
+                       reinterpret_cast<unsigned*>(ws + ly.lb_ticket),
+                       reinterpret_cast<unsigned*>(ws + ly.lb_flags),
+                       reinterpret_cast<real*>(ws + ly.lb_agg),
+                       reinterpret_cast<real*>(ws + ly.lb_pre), 0u, flags, o->reset, reset_thr};
+  if (lookback) DEER_CK(cudaMemsetAsync(lba.flags, 0, (size_t)ly.n_chunks_max * 4, st));
+
+  deer_status status = DEER_OK;
+  Flags hf;
+  for (int it = 0;; ++it) {
+    la.bt = bt;
+    DEER_CK(launch_linearize<real>(la, st));
+    ca.it = it;
+    DEER_CK(launch_check(ca, st));
+    DEER_CK(cudaMemcpyAsync(&hf, flags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
+    DEER_CK(cudaStreamSynchronize(st));
+    bool stop = false;
+    if (hf.bad_input) { status = DEER_ERR_INVALID; stop = true; }
+    else if (hf.timeout) { status = DEER_ERR_TIMEOUT; stop = true; }
+    else if (hf.n_nonfinite > 0 && !o->reset) { status = DEER_ERR_NONFINITE; stop = true; }
+    else if (hf.n_active == 0) stop = true;
+    else if (it >= max_iters) { status = DEER_NOT_CONVERGED; stop = true; }
+    bt.n_act = hf.n_active;
+    bt.act_rows = hf.active_rows;
+    bt.act_chunks = hf.active_chunks;
+    if (stop) break;
+    if (o->jac == DEER_JAC_FULL) {
+      dsa.bt = bt;
+      DEER_CK(launch_dense_scan<real>(dsa, st));
+    } else if (lookback) {
+      lba.bt = bt;
+      lba.epoch += 1;
+      DEER_CK(launch_diag_lookback<real>(lba, st));
+    } else {
+      gsa.bt = bt;
+      DEER_CK(launch_diag_scan<real>(gsa, st));
+    }
+  }
+  if (info_h) {
+    deer_info* dinfo = reinterpret_cast<deer_info*>(ws + ly.total);
+    k_info_out<<<grid_for(B, 128), 128, 0, st>>>(B, info, dinfo);
+    note_launch();
+    DEER_CK(cudaGetLastError());
+    DEER_CK(cudaMemcpyAsync(info_h, dinfo, B * sizeof(deer_info), cudaMemcpyDeviceToHost, st));
+  }
+  DEER_CK(cudaStreamSynchronize(st));
+  return status;
+}
+
+}  // namespace deer
+
+extern "C" {
+
+deer_status deer_solve_noalloc(const deer_dynamics* f, int64_t batch, int64_t T,
+                               const void* s0, const void* x, void* s_out,
+                               const deer_options* opt, deer_stream_t stream,
+                               deer_info* info) {
+  deer_status c = check_common(f, opt);
+  if (c != DEER_OK) return c;
+  if (batch < 0 || T < 0) return DEER_ERR_INVALID;
+  if (batch == 0 || T == 0) return DEER_OK;
+  if (!s0 || !s_out) return DEER_ERR_INVALID;
+  if (f->kind == DEER_F_GRU && !x) return DEER_ERR_INVALID;
+  void* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "deer_solve_noalloc scratch lookup");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(scratch);
+  if (opt->prec == DEER_FP32)
+    return solve_noalloc_impl<float>(f, batch, T, s0, x, s_out, opt, ws, st, info);
+  return solve_noalloc_impl<double>(f, batch, T, s0, x, s_out, opt, ws, st, info);
+}
+
+size_t deer_noalloc_scratch_bytes(void) { return kNoAllocScratchBytes; }
+
+}  // extern "C"
