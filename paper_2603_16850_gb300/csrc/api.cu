@@ -86,7 +86,7 @@ static bool d_supported(int kind, int d, int jac) {
 // Everything the solver carves out of the caller's workspace.
 struct Layout {
   size_t offsets, chunk_first, act_seq, act_row_off, act_chunk_off, acc, info, flags, ma, gru_M,
-      A, b, aggP, aggv, cin, gam, mob, pin, lb_ticket, lb_flags, lb_agg, lb_pre, total;
+      A, b, aggP, aggv, cin, gam, mob, pin, sprev, lb_ticket, lb_flags, lb_agg, lb_pre, total;
   int64_t n_chunks_max;
   int64_t ma_stride, n_ma;
   int L;
@@ -138,9 +138,16 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
     ly.ma = take((size_t)(ly.n_ma > 0 ? ly.n_ma : 1) * ly.ma_stride * rs);
   }
   if (f->kind == DEER_F_GRU) ly.gru_M = take((size_t)d * d * rs);
-  if (o->jac == DEER_JAC_FULL) ly.A = take((size_t)N * d * d * rs);
-  else if (o->jac == DEER_JAC_DIAG) ly.A = take((size_t)N * d * rs);
-  ly.b = take((size_t)N * d * rs);
+  if (o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d)) {
+    // chunk-interleaved Jacobians / offsets of the fused path, padded to whole chunks
+    const size_t rows = (size_t)((C + 31) / 32 * 32) * L;
+    ly.A = take(rows * d * d * rs);
+    ly.b = take(rows * d * rs);
+  } else {
+    if (o->jac == DEER_JAC_FULL) ly.A = take((size_t)N * d * d * rs);
+    else if (o->jac == DEER_JAC_DIAG) ly.A = take((size_t)N * d * rs);
+    ly.b = take((size_t)N * d * rs);
+  }
   if (o->jac == DEER_JAC_FULL) ly.aggP = take((size_t)C * d * d * rs);
   ly.aggv = take((size_t)C * d * rs);
   ly.cin = take((size_t)C * d * rs);
@@ -151,6 +158,9 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
     ly.mob = take((size_t)C * d * 4 * rs);
     ly.pin = take((size_t)C * d * rs);
   }
+  ly.sprev = p;
+  if (o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d))
+    ly.sprev = take((size_t)C * d * rs);
   ly.lb_ticket = ly.lb_flags = ly.lb_agg = ly.lb_pre = p;
   if (use_diag_lookback(o, d)) {
     ly.lb_ticket = take(256);
@@ -344,6 +354,27 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     gsa.reset_thr = reset_thr;
   }
 
+  const bool fused = o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d);
+  FusedArgs<real> fa;
+  if (fused) {
+    fa.dv = dv;
+    fa.bt = bt;
+    fa.s0 = s0;
+    fa.s = s;
+    fa.Ai = la.A;
+    fa.bi = la.b;
+    fa.aggP = reinterpret_cast<real*>(ws + ly.aggP);
+    fa.aggv = reinterpret_cast<real*>(ws + ly.aggv);
+    fa.cin = reinterpret_cast<real*>(ws + ly.cin);
+    fa.sprev = reinterpret_cast<real*>(ws + ly.sprev);
+    fa.acc = acc;
+    fa.damp = o->damp;
+    fa.dparam = (real)o->damp_param;
+    fa.reset = o->reset;
+    fa.reset_thr = reset_thr;
+    fa.mode = 0;
+  }
+
   const bool lookback = use_diag_lookback(o, d);
   DiagLBArgs<real> lba;
   if (lookback) {
@@ -371,10 +402,26 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   PhaseTimer pt(st);
   int64_t lin_rows = N;  // rows linearised in the current iteration
   for (int it = 0;; ++it) {
+    int64_t carry_launches = 0;
+    if (fused && it > 0) {
+      // compose the aggregates of the previous pass into per-chunk carries
+      const int64_t c0l = g_launches.load();
+      fa.bt = bt;
+      pt.begin(PH_SCAN);
+      DEER_CK(launch_dense_fused_carry<real>(fa, st));
+      pt.end(PH_SCAN);
+      carry_launches = g_launches.load() - c0l;
+    }
     const int64_t l0 = g_launches.load();
     la.bt = bt;
     pt.begin(PH_LIN);
-    DEER_CK(launch_linearize<real>(la, st));
+    if (fused) {
+      fa.bt = bt;
+      fa.mode = it > 0 ? 1 : 0;
+      DEER_CK(launch_dense_fused<real>(fa, st));
+    } else {
+      DEER_CK(launch_linearize<real>(la, st));
+    }
     pt.end(PH_LIN);
     const int64_t l1 = g_launches.load();
     ca.it = it;
@@ -389,13 +436,13 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     else if (hf.n_nonfinite > 0 && !o->reset) { status = DEER_ERR_NONFINITE; stop = true; }
     else if (hf.n_active == 0) stop = true;
     else if (it >= max_iters) { status = DEER_NOT_CONVERGED; stop = true; }
-    int64_t scan_launches = 0;
+    int64_t scan_launches = carry_launches;
     bt.n_act = hf.n_active;
     bt.act_rows = hf.active_rows;
     bt.act_chunks = hf.active_chunks;
     dsa.bt = bt;
     gsa.bt = bt;
-    if (!stop) {
+    if (!stop && !fused) {
       const int64_t s0c = g_launches.load();
       pt.begin(PH_SCAN);
       if (o->jac == DEER_JAC_FULL) {
@@ -413,7 +460,9 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     if (pt.on) {
       DEER_CK(cudaStreamSynchronize(st));
       const int64_t launches[PH_N] = {0, l1 - l0, 1, scan_launches};
-      const int64_t rows[PH_N] = {0, lin_rows, (int64_t)B, stop ? 0 : (int64_t)hf.active_rows};
+      const int64_t rows[PH_N] = {0, lin_rows, (int64_t)B,
+                                  fused ? (carry_launches ? lin_rows : 0)
+                                        : (stop ? 0 : (int64_t)hf.active_rows)};
       pt.collect(launches, rows);
     }
     lin_rows = hf.active_rows;

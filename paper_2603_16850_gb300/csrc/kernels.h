@@ -196,3 +196,44 @@ template <class real>
 cudaError_t launch_diag_lookback(const DiagLBArgs<real>& a, cudaStream_t st);
 
 }  // namespace deer
+
+namespace deer {
+
+// Fused dense (full-Jacobian) iteration for d <= 8, one thread per chunk of L rows:
+//   mode 0: linearise at the current iterate and reduce every chunk to its aggregate;
+//   mode 1: first apply the pending scan (Delta_t = A_t Delta_{t-1} - r_t from the chunk's
+//           carry, s_t += Delta_t), then linearise at the new iterate in the same pass.
+// A_t and b_t = -r_t live in a chunk-interleaved layout (element e of row t of chunk c at
+// ((c/32 * L + t) * E + e) * 32 + c%32, E = d*d or d) so that the 32 lanes of a warp, which
+// walk 32 chunks in step, touch 128 contiguous bytes per access.
+template <class real>
+struct FusedArgs {
+  DynView<real> dv;
+  Batch bt;
+  const real* s0;
+  real* s;
+  real* Ai;          // interleaved Jacobians
+  real* bi;          // interleaved offsets -r_t
+  real* aggP;        // [n_chunks][d][d]
+  real* aggv;        // [n_chunks][d]
+  real* cin;         // [n_chunks][d]  Delta entering each chunk
+  real* sprev;       // [n_chunks][d]  new state at the row before each chunk
+  SeqAcc* acc;
+  int damp;
+  real dparam;
+  int reset;
+  real reset_thr;
+  int mode;
+};
+
+template <class real>
+cudaError_t launch_dense_fused(const FusedArgs<real>& a, cudaStream_t st);
+template <class real>
+cudaError_t launch_dense_fused_carry(const FusedArgs<real>& a, cudaStream_t st);
+
+inline bool dense_fused_supported(int kind, int d) {
+  (void)kind;
+  return d == 1 || d == 2 || d == 4 || d == 8;
+}
+
+}  // namespace deer
