@@ -86,7 +86,8 @@ static bool d_supported(int kind, int d, int jac) {
 // Everything the solver carves out of the caller's workspace.
 struct Layout {
   size_t offsets, chunk_first, act_seq, act_row_off, act_chunk_off, acc, info, flags, ma, gru_M,
-      A, b, aggP, aggv, cin, gam, mob, pin, sprev, lb_ticket, lb_flags, lb_agg, lb_pre, total;
+      A, b, aggP, aggv, cin, gam, mob, pin, sprev, lb_ticket, lb_flags, lb_agg, lb_pre, xproj,
+      total;
   int64_t n_chunks_max;
   int64_t ma_stride, n_ma;
   int L;
@@ -158,6 +159,9 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
     ly.mob = take((size_t)C * d * 4 * rs);
     ly.pin = take((size_t)C * d * rs);
   }
+  ly.xproj = p;
+  if (gru_tiled_supported(f->kind, d, f->d_in, o->jac, o->prec))
+    ly.xproj = take((size_t)N * 3 * d * rs);
   ly.sprev = p;
   if (o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d))
     ly.sprev = take((size_t)C * d * rs);
@@ -282,6 +286,27 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   if (f->kind == DEER_F_GRU) {
     DEER_CK(launch_gru_setup<real>(d, static_cast<const real*>(f->params), f->d_in,
                                    reinterpret_cast<real*>(ws + ly.gru_M), st));
+  }
+  const bool gru_tiled = gru_tiled_supported(f->kind, d, f->d_in, o->jac, o->prec);
+  GruTileArgs gta;
+  if constexpr (sizeof(real) == 4) {
+    if (gru_tiled) {
+      // input projections W x_t, once per solve
+      DEER_CK(launch_gru_xproj(static_cast<const float*>(f->params),
+                               static_cast<const float*>(x_), N,
+                               reinterpret_cast<float*>(ws + ly.xproj), st));
+      gta.dv = dv;
+      gta.bt = bt;
+      gta.s0 = s0;
+      gta.s = s;
+      gta.xproj = reinterpret_cast<const float*>(ws + ly.xproj);
+      gta.A = reinterpret_cast<float*>(ws + ly.A);
+      gta.b = reinterpret_cast<float*>(ws + ly.b);
+      gta.acc = acc;
+      gta.jac = o->jac;
+      gta.damp = o->damp;
+      gta.dparam = (float)o->damp_param;
+    }
   }
   if (o->init != DEER_INIT_USER) {
     InitArgs<real> ia{dv, bt, s0, s, o->init};
@@ -419,6 +444,11 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
       fa.bt = bt;
       fa.mode = it > 0 ? 1 : 0;
       DEER_CK(launch_dense_fused<real>(fa, st));
+    } else if (gru_tiled) {
+      if constexpr (sizeof(real) == 4) {
+        gta.bt = bt;
+        DEER_CK(launch_gru_lin_tiled(gta, st));
+      }
     } else {
       DEER_CK(launch_linearize<real>(la, st));
     }

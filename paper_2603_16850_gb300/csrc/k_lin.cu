@@ -544,12 +544,16 @@ cudaError_t launch_init(const InitArgs<real>& a, cudaStream_t st) {
   }
 }
 
+template <class real, int JAC>
+cudaError_t launch_lin_ma_wide(const LinArgs<real>& a, cudaStream_t st);
+
 template <class real, int KIND, int JAC>
 static cudaError_t lin_kind_jac(const LinArgs<real>& a, cudaStream_t st) {
   const unsigned g = grid_for(a.bt.act_rows, 128);
   const int d = a.dv.d;
   if constexpr (KIND == DEER_F_MASSACTION_EULER || KIND == DEER_F_MASSACTION_RK4) {
     constexpr bool RK4 = KIND == DEER_F_MASSACTION_RK4;
+    if (d == 16 || d == 32) return launch_lin_ma_wide<real, JAC>(a, st);
     if (d <= 8) {
       switch (d) {
         case 2: k_lin_ma<real, 2, 1, RK4, JAC><<<g, 128, 0, st>>>(a); break;
@@ -676,4 +680,158 @@ DEER_INST(float)
 DEER_INST(double)
 #undef DEER_INST
 
+}  // namespace deer
+
+namespace deer {
+
+// ----------------------------------------------------------------------------
+// Mass action, d = 16 / 32: D lanes per row, lane i owns species i (its state, slope and
+// row i of the stage Jacobians). Rates come from one pass over the reactions with
+// shuffles for the reactant concentrations; the sparse rate Jacobian G is scattered into
+// shared memory by the (at most four) lanes each reaction touches; the chain
+// K_j = G_j (I + c_j K_{j-1}) reads the previous K rows from shared memory as broadcasts.
+// ----------------------------------------------------------------------------
+template <class real, int D, bool RK4, int JAC>
+__global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
+  constexpr int GROUPS = 128 / D;          // rows per block
+  constexpr bool WANTA = JAC == DEER_JAC_FULL || JAC == DEER_JAC_DIAG;
+  __shared__ real sG[GROUPS][D][D + 1];
+  __shared__ real sK[GROUPS][D][D];
+  const int grp = threadIdx.x / D, lane = threadIdx.x % D;
+  const unsigned gmask = D == 32 ? 0xffffffffu : (0xffffu << (16 * ((threadIdx.x >> 4) & 1)));
+  const int64_t ar = blockIdx.x * (int64_t)GROUPS + grp;
+  const bool valid = ar < a.bt.act_rows;
+  int64_t seq = 0, row = 0;
+  if (valid) act_row(a.bt, ar, seq, row);
+  double mx = 0.0, sq = 0.0;
+  // all lanes run the loops (shuffles within a row group stay converged); invalid rows
+  // compute on row 0 of sequence 0 and store nothing
+  const real s_prev = valid ? (row == __ldg(a.bt.offsets + seq) ? a.s0[seq * D + lane]
+                                                              : a.s[(row - 1) * D + lane])
+                            : real(0);
+  const real* kk = a.dv.params + seq * a.dv.pstride;
+  const int4* tt = reinterpret_cast<const int4*>(a.dv.topo + seq * a.dv.tstride);
+  const int R = a.dv.R;
+  const real h = a.dv.dt;
+  real c = s_prev, acc = real(0), g = real(0);
+  real Kacc[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) Kacc[j] = real(0);
+  const int nst = RK4 ? 4 : 1;
+  for (int stage = 0; stage < nst; ++stage) {
+    const real cK = stage == 0 ? real(0) : (stage == 3 ? h : real(0.5) * h);
+    const real w = (stage == 1 || stage == 2) ? real(2) : real(1);
+    if (WANTA) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) sG[grp][lane][j] = real(0);
+    }
+    __syncwarp(gmask);
+    g = real(0);
+    for (int r = 0; r < R; ++r) {
+      const int4 q = __ldg(tt + r);
+      const real kr = __ldg(kk + r);
+      const real c1 = __shfl_sync(gmask, c, q.x, D);
+      const real c2 = __shfl_sync(gmask, c, q.y < 0 ? 0 : q.y, D);
+      const real f2 = q.y < 0 ? real(1) : c2;
+      const real nu = real((lane == q.z) + (lane == q.w) - (lane == q.x) - (lane == q.y));
+      g += nu * (kr * c1 * f2);
+      if (WANTA && nu != real(0)) {
+        sG[grp][lane][q.x] += nu * kr * f2;                  // d rate / d c_i1
+        if (q.y >= 0) sG[grp][lane][q.y] += nu * kr * c1;    // d rate / d c_i2
+      }
+    }
+    if (WANTA) {
+      __syncwarp(gmask);
+      real Gi[D], Kn[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) Gi[j] = sG[grp][lane][j];
+#pragma unroll
+      for (int j = 0; j < D; ++j) Kn[j] = Gi[j];
+      if (stage > 0) {
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+          const real gm = cK * Gi[m];
+#pragma unroll
+          for (int j = 0; j < D; ++j) Kn[j] += gm * sK[grp][m][j];
+        }
+      }
+      __syncwarp(gmask);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        sK[grp][lane][j] = Kn[j];
+        Kacc[j] += w * Kn[j];
+      }
+      __syncwarp(gmask);
+    }
+    acc += w * g;
+    const real cs = stage == 2 ? h : real(0.5) * h;
+    c = s_prev + cs * g;
+  }
+  const real hw = RK4 ? h / real(6) : h;
+  const real F = s_prev + hw * acc;
+  if (valid) {
+    const real sc = a.s[row * D + lane];
+    const real rr = sc - F;
+    const real sabs = rabs(sc);
+    mx = (double)rabs(rr) / (double)(sabs > real(1) ? sabs : real(1));
+    if (rr != rr) mx = rr;  // keep NaN
+    sq = (double)rr * (double)rr;
+    const real k = a.dparam;
+    if constexpr (JAC == DEER_JAC_FULL) {
+      const real scale = a.damp == DEER_DAMP_SCALE ? real(1) - k : real(1);
+      real* Ao = a.A + row * (int64_t)(D * D) + lane * D;
+#pragma unroll
+      for (int j = 0; j < D; ++j) Ao[j] = scale * (hw * Kacc[j] + (j == lane ? real(1) : real(0)));
+      a.b[row * D + lane] = -rr;
+    } else {
+      real ai;
+      if constexpr (JAC == DEER_JAC_DIAG) {
+        ai = real(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+          if (j == lane) ai = real(1) + hw * Kacc[j];
+      } else if constexpr (JAC == DEER_JAC_IDENTITY) {
+        ai = real(1);
+      } else {
+        ai = real(0);
+      }
+      if (a.damp == DEER_DAMP_SCALE) ai *= (real(1) - k);
+      else if (a.damp == DEER_DAMP_CLIP) ai = ai > k ? k : (ai < -k ? -k : ai);
+      if constexpr (JAC == DEER_JAC_DIAG) a.A[row * D + lane] = ai;
+      a.b[row * D + lane] = F - ai * s_prev;
+    }
+  }
+  acc_resid(a.acc, seq, valid, mx, sq);
+}
+
+template <class real, int JAC>
+cudaError_t launch_lin_ma_wide(const LinArgs<real>& a, cudaStream_t st) {
+  const bool rk4 = a.dv.kind == DEER_F_MASSACTION_RK4;
+  const int d = a.dv.d;
+  const int64_t rows_per_block = 128 / d;
+  const unsigned g = grid_for(a.bt.act_rows, (int)rows_per_block);
+  if (d == 16) {
+    if (rk4) k_lin_ma_wide<real, 16, true, JAC><<<g, 128, 0, st>>>(a);
+    else k_lin_ma_wide<real, 16, false, JAC><<<g, 128, 0, st>>>(a);
+  } else if (d == 32) {
+    if (rk4) k_lin_ma_wide<real, 32, true, JAC><<<g, 128, 0, st>>>(a);
+    else k_lin_ma_wide<real, 32, false, JAC><<<g, 128, 0, st>>>(a);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace deer
+
+namespace deer {
+template cudaError_t launch_lin_ma_wide<float, DEER_JAC_FULL>(const LinArgs<float>&, cudaStream_t);
+template cudaError_t launch_lin_ma_wide<float, DEER_JAC_DIAG>(const LinArgs<float>&, cudaStream_t);
+template cudaError_t launch_lin_ma_wide<float, DEER_JAC_IDENTITY>(const LinArgs<float>&, cudaStream_t);
+template cudaError_t launch_lin_ma_wide<float, DEER_JAC_ZERO>(const LinArgs<float>&, cudaStream_t);
+template cudaError_t launch_lin_ma_wide<double, DEER_JAC_FULL>(const LinArgs<double>&, cudaStream_t);
+template cudaError_t launch_lin_ma_wide<double, DEER_JAC_DIAG>(const LinArgs<double>&, cudaStream_t);
+template cudaError_t launch_lin_ma_wide<double, DEER_JAC_IDENTITY>(const LinArgs<double>&, cudaStream_t);
+template cudaError_t launch_lin_ma_wide<double, DEER_JAC_ZERO>(const LinArgs<double>&, cudaStream_t);
 }  // namespace deer

@@ -255,6 +255,9 @@ static void dense_launch(const DenseScanArgs<real>& a, cudaStream_t st) {
   note_launch(3);
 }
 
+template <class real, int D>
+void dense_launch_wide(const DenseScanArgs<real>& a, cudaStream_t st);
+
 template <class real>
 cudaError_t launch_dense_scan(const DenseScanArgs<real>& a, cudaStream_t st) {
   if (a.bt.act_rows == 0) return cudaSuccess;
@@ -263,8 +266,8 @@ cudaError_t launch_dense_scan(const DenseScanArgs<real>& a, cudaStream_t st) {
     case 2: dense_launch<real, 2>(a, st); break;
     case 4: dense_launch<real, 4>(a, st); break;
     case 8: dense_launch<real, 8>(a, st); break;
-    case 16: dense_launch<real, 16>(a, st); break;
-    case 32: dense_launch<real, 32>(a, st); break;
+    case 16: dense_launch_wide<real, 16>(a, st); break;
+    case 32: dense_launch_wide<real, 32>(a, st); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -603,5 +606,124 @@ cudaError_t launch_adjoint_scan(const AdjScanArgs<real>& a, cudaStream_t st) {
 
 template cudaError_t launch_adjoint_scan<float>(const AdjScanArgs<float>&, cudaStream_t);
 template cudaError_t launch_adjoint_scan<double>(const AdjScanArgs<double>&, cudaStream_t);
+
+}  // namespace deer
+
+namespace deer {
+
+// ----------------------------------------------------------------------------
+// Dense scan, d = 16 / 32: D lanes per chunk (per sequence in the carry pass). Lane j
+// owns column j of the chunk product P and entry j of the vectors; the Jacobian rows are
+// read as warp-wide broadcasts, vector entries travel by shuffles.
+// ----------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ unsigned group_mask() {
+  return D == 32 ? 0xffffffffu : (0xffffu << (16 * ((threadIdx.x >> 4) & 1)));
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_dense_chunk_wide(DenseScanArgs<real> a) {
+  constexpr int G = 128 / D;
+  const int grp = threadIdx.x / D, lane = threadIdx.x % D;
+  const unsigned gm = group_mask<D>();
+  const int64_t ac = blockIdx.x * (int64_t)G + grp;
+  const bool valid = ac < a.bt.act_chunks;
+  int64_t seq = 0, c = 0, r0 = 0;
+  int n = 0;
+  if (valid) act_chunk(a.bt, ac, seq, c, r0, n);
+  const bool need_P = valid && c != __ldg(a.bt.chunk_first + seq);
+  real Pc[D];  // column `lane` of P
+  real v = real(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) Pc[i] = i == lane ? real(1) : real(0);
+  for (int t = 0; t < n; ++t) {
+    const real* At = a.A + (r0 + t) * (int64_t)(D * D);
+    // v <- A v + b: lane i forms row i, v entries by shuffle
+    real nv = __ldg(a.b + (r0 + t) * D + lane);
+#pragma unroll
+    for (int k = 0; k < D; ++k) nv += __ldg(At + lane * D + k) * __shfl_sync(gm, v, k, D);
+    v = nv;
+    if (need_P) {
+      real np[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        real x = real(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) x += __ldg(At + i * D + k) * Pc[k];
+        np[i] = x;
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i) Pc[i] = np[i];
+    }
+  }
+  if (valid) {
+    real* Po = a.aggP + c * (int64_t)(D * D);
+#pragma unroll
+    for (int i = 0; i < D; ++i) Po[i * D + lane] = Pc[i];
+    a.aggv[c * D + lane] = v;
+  }
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_dense_carry_wide(DenseScanArgs<real> a) {
+  constexpr int G = 128 / D;
+  const int grp = threadIdx.x / D, lane = threadIdx.x % D;
+  const unsigned gm = group_mask<D>();
+  const int64_t kq = blockIdx.x * (int64_t)G + grp;
+  const bool valid = kq < a.bt.n_act;
+  const int64_t seq = valid ? a.bt.act_seq[kq] : 0;
+  const int64_t c0 = valid ? a.bt.chunk_first[seq] : 0;
+  const int64_t c1 = valid ? a.bt.chunk_first[seq + 1] : 0;
+  real x = real(0);
+  for (int64_t c = c0; c < c1; ++c) {
+    a.cin[c * D + lane] = x;
+    const real* P = a.aggP + c * (int64_t)(D * D);
+    real y = a.aggv[c * D + lane];
+    if (c > c0) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) y += P[lane * D + k] * __shfl_sync(gm, x, k, D);
+    }
+    x = y;
+  }
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_dense_apply_wide(DenseScanArgs<real> a) {
+  constexpr int G = 128 / D;
+  const int grp = threadIdx.x / D, lane = threadIdx.x % D;
+  const unsigned gm = group_mask<D>();
+  const int64_t ac = blockIdx.x * (int64_t)G + grp;
+  const bool valid = ac < a.bt.act_chunks;
+  int64_t seq = 0, c = 0, r0 = 0;
+  int n = 0;
+  if (valid) act_chunk(a.bt, ac, seq, c, r0, n);
+  real x = valid ? a.cin[c * D + lane] : real(0);
+  for (int t = 0; t < n; ++t) {
+    const int64_t row = r0 + t;
+    const real* At = a.A + row * (int64_t)(D * D) + lane * D;
+    real y = __ldg(a.b + row * D + lane);
+#pragma unroll
+    for (int k = 0; k < D; ++k) y += __ldg(At + k) * __shfl_sync(gm, x, k, D);
+    x = y;
+    real* sp = a.s + row * D + lane;
+    *sp = reset_val(*sp + y, a.reset_thr, a.reset);
+  }
+}
+
+template <class real, int D>
+void dense_launch_wide(const DenseScanArgs<real>& a, cudaStream_t st) {
+  constexpr int G = 128 / D;
+  const unsigned gc = grid_for(a.bt.act_chunks, G);
+  const unsigned gs = grid_for(a.bt.n_act, G);
+  k_dense_chunk_wide<real, D><<<gc, 128, 0, st>>>(a);
+  k_dense_carry_wide<real, D><<<gs, 128, 0, st>>>(a);
+  k_dense_apply_wide<real, D><<<gc, 128, 0, st>>>(a);
+  note_launch(3);
+}
+
+template void dense_launch_wide<float, 16>(const DenseScanArgs<float>&, cudaStream_t);
+template void dense_launch_wide<float, 32>(const DenseScanArgs<float>&, cudaStream_t);
+template void dense_launch_wide<double, 16>(const DenseScanArgs<double>&, cudaStream_t);
+template void dense_launch_wide<double, 32>(const DenseScanArgs<double>&, cudaStream_t);
 
 }  // namespace deer

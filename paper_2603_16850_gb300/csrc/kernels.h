@@ -237,3 +237,32 @@ inline bool dense_fused_supported(int kind, int d) {
 }
 
 }  // namespace deer
+
+namespace deer {
+
+// GRU linearisation for d = d_in = 64 in float32 (quasi-DEER family): rows are processed in
+// tiles of 64 time steps by persistent CTAs holding U_z^T, U_r^T, U_h^T and M^T (M_ij =
+// U_h,ij U_r,ji) in shared memory; the input projections W x_t are computed once per solve.
+struct GruTileArgs {
+  DynView<float> dv;
+  Batch bt;
+  const float* s0;
+  const float* s;
+  const float* xproj;   // [N][3][64] = W_z x_t, W_r x_t, W_h x_t
+  float* A;             // [N][64] diag A~_t (DIAG only)
+  float* b;             // [N][64]
+  SeqAcc* acc;
+  int jac, damp;
+  float dparam;
+};
+
+cudaError_t launch_gru_xproj(const float* W, const float* x, int64_t N, float* out,
+                             cudaStream_t st);
+cudaError_t launch_gru_lin_tiled(const GruTileArgs& a, cudaStream_t st);
+
+inline bool gru_tiled_supported(int kind, int d, int d_in, int jac, int prec) {
+  return kind == DEER_F_GRU && d == 64 && d_in == 64 && jac != DEER_JAC_FULL &&
+         prec == DEER_FP32;
+}
+
+}  // namespace deer
