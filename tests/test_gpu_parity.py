@@ -115,6 +115,27 @@ def test_massaction_modes_fp64(jac, damp, dp):
         assert _relerr(s.cpu().numpy()[b * T:(b + 1) * T], roll[b]) <= 1e-10
 
 
+@pytest.mark.parametrize("d,R,jac", [(16, 24, "full"), (32, 48, "full"), (16, 24, "diag")])
+def test_massaction_wide_fp64_iterates(d, R, jac):
+    """d = 16 / 32 (lane-per-species Jacobians, lane-per-column scans): two iterations and
+    the fixed point against the oracle in FP64 (T = 150: several chunks and a tail)."""
+    deer = _deer()
+    B, T = 2, 150
+    p = _ma_problem(B, d, R, T, seed=d + 1, dt=0.01)
+    od = _ma_oracle(p)
+    dyn = _ma_dyn(p, torch.float64)
+    s2, _ = deer.deer_solve(dyn, _t(p["s0"]), T, jac=jac, tol=0.0, max_iters=2, init="s0")
+    ref = onewton.initial_guess(od, p["s0"], T, "s0")
+    for _ in range(2):
+        ref = onewton.quasi_newton_step(od, p["s0"], ref, jac)
+    assert _relerr(s2.cpu().numpy(), ref.reshape(-1, d)) <= 1e-11
+    s, info = deer.deer_solve(dyn, _t(p["s0"]), T, jac=jac, tol=1e-12, init="s0", reset=True,
+                              max_iters=400)
+    assert bool(info.converged.all())
+    roll = onewton.rollout(od, p["s0"], T)
+    assert _relerr(s.cpu().numpy(), roll.reshape(-1, d)) <= 1e-10
+
+
 @pytest.mark.parametrize("d,R", [(2, 3), (8, 12), (16, 24), (32, 48)])
 def test_massaction_rk4_fp32_full(d, R):
     deer = _deer()
