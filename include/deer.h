@@ -92,8 +92,11 @@ typedef enum {
 typedef enum {
   DEER_FP64 = 0,       /* everything float64 */
   DEER_FP32 = 1,       /* everything float32; residual max/merit accumulated in float64 */
-  DEER_MIXED_BF16 = 2  /* float64 state and residual; the dense scan composes
-                          bf16 Jacobians with float32 accumulation in correction form */
+  DEER_MIXED_BF16 = 2  /* float64 state, dynamics value and residual; the Jacobian is formed
+                          in float32 and stored as bf16 E = A - I, and the dense scan composes
+                          (I + E) with float32 accumulation in correction form. Mass-action
+                          kinetics with d = 16 or 32 and DEER_JAC_FULL (no damping or
+                          scale-ELK); not available in deer_grad or deer_solve_noalloc. */
 } deer_prec;
 
 typedef struct {

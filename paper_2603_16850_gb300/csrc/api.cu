@@ -110,8 +110,9 @@ static int choose_chunk(const deer_options* o, int d) {
 static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer_options* o,
                         Layout& ly) {
   if (!f || !o || B < 0 || N < 0) return false;
-  if (o->prec != DEER_FP64 && o->prec != DEER_FP32) return false;
+  if (o->prec != DEER_FP64 && o->prec != DEER_FP32 && o->prec != DEER_MIXED_BF16) return false;
   const size_t rs = o->prec == DEER_FP32 ? 4 : 8;
+  const bool mixed = o->prec == DEER_MIXED_BF16;
   const int d = f->d;
   const int L = choose_chunk(o, d);
   if (!pow2(L) || L < 8 || L > 1024) return false;
@@ -139,7 +140,11 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
     ly.ma = take((size_t)(ly.n_ma > 0 ? ly.n_ma : 1) * ly.ma_stride * rs);
   }
   if (f->kind == DEER_F_GRU) ly.gru_M = take((size_t)d * d * rs);
-  if (o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d)) {
+  if (mixed) {
+    // bfloat16 E = A - I, float32 offsets and aggregates
+    ly.A = take((size_t)N * d * d * 2);
+    ly.b = take((size_t)N * d * 4);
+  } else if (o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d)) {
     // chunk-interleaved Jacobians / offsets of the fused path, padded to whole chunks
     const size_t rows = (size_t)((C + 31) / 32 * 32) * L;
     ly.A = take(rows * d * d * rs);
@@ -149,9 +154,10 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
     else if (o->jac == DEER_JAC_DIAG) ly.A = take((size_t)N * d * rs);
     ly.b = take((size_t)N * d * rs);
   }
-  if (o->jac == DEER_JAC_FULL) ly.aggP = take((size_t)C * d * d * rs);
-  ly.aggv = take((size_t)C * d * rs);
-  ly.cin = take((size_t)C * d * rs);
+  const size_t ars = mixed ? 4 : rs;
+  if (o->jac == DEER_JAC_FULL) ly.aggP = take((size_t)C * d * d * ars);
+  ly.aggv = take((size_t)C * d * ars);
+  ly.cin = take((size_t)C * d * ars);
   // diag family also needs a second aggregate array; reuse aggP slot for it
   if (o->jac != DEER_JAC_FULL) ly.aggP = take((size_t)C * d * rs);
   if (o->damp == DEER_DAMP_ELK) {
@@ -163,7 +169,7 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
   if (gru_tiled_supported(f->kind, d, f->d_in, o->jac, o->prec))
     ly.xproj = take((size_t)N * 3 * d * rs);
   ly.sprev = p;
-  if (o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d))
+  if (!mixed && o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d))
     ly.sprev = take((size_t)C * d * rs);
   ly.lb_ticket = ly.lb_flags = ly.lb_agg = ly.lb_pre = p;
   if (use_diag_lookback(o, d)) {
@@ -202,8 +208,12 @@ static deer_status check_common(const deer_dynamics* f, const deer_options* o) {
   if (o->jac < 0 || o->jac > DEER_JAC_ZERO) return DEER_ERR_INVALID;
   if (o->damp < 0 || o->damp > DEER_DAMP_CLIP) return DEER_ERR_INVALID;
   if (o->init < 0 || o->init > DEER_INIT_USER) return DEER_ERR_INVALID;
-  if (o->prec == DEER_MIXED_BF16) return DEER_ERR_UNSUPPORTED;
-  if (o->prec != DEER_FP64 && o->prec != DEER_FP32) return DEER_ERR_INVALID;
+  if (o->prec != DEER_FP64 && o->prec != DEER_FP32 && o->prec != DEER_MIXED_BF16)
+    return DEER_ERR_INVALID;
+  if (o->prec == DEER_MIXED_BF16 &&
+      (!mixed_supported(f->kind, f->d, o->jac) ||
+       (o->damp != DEER_DAMP_NONE && o->damp != DEER_DAMP_SCALE)))
+    return DEER_ERR_UNSUPPORTED;
   if (!d_supported(f->kind, f->d, o->jac)) return DEER_ERR_UNSUPPORTED;
   if (o->damp == DEER_DAMP_ELK && o->jac == DEER_JAC_FULL) return DEER_ERR_UNSUPPORTED;
   if (o->damp == DEER_DAMP_CLIP && o->jac == DEER_JAC_FULL) return DEER_ERR_INVALID;
@@ -379,7 +389,33 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     gsa.reset_thr = reset_thr;
   }
 
-  const bool fused = o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d);
+  const bool mixed = o->prec == DEER_MIXED_BF16;
+  MixedLinArgs mla;
+  MixedScanArgs msa;
+  if constexpr (sizeof(real) == 8) {
+    if (mixed) {
+      mla.dv = dv;
+      mla.bt = bt;
+      mla.s0 = s0;
+      mla.s = s;
+      mla.E = reinterpret_cast<__nv_bfloat16*>(ws + ly.A);
+      mla.b = reinterpret_cast<float*>(ws + ly.b);
+      mla.acc = acc;
+      mla.damp = o->damp;
+      mla.dparam = o->damp_param;
+      msa.bt = bt;
+      msa.d = d;
+      msa.E = mla.E;
+      msa.b = mla.b;
+      msa.s = s;
+      msa.aggP = reinterpret_cast<float*>(ws + ly.aggP);
+      msa.aggv = reinterpret_cast<float*>(ws + ly.aggv);
+      msa.cin = reinterpret_cast<float*>(ws + ly.cin);
+      msa.reset = o->reset;
+      msa.reset_thr = 1e30;
+    }
+  }
+  const bool fused = !mixed && o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d);
   FusedArgs<real> fa;
   if (fused) {
     fa.dv = dv;
@@ -401,6 +437,10 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   }
 
   const bool lookback = use_diag_lookback(o, d);
+  // all sequences of equal length: round-robin tile order for the look-back scan
+  int64_t uniform_chunks = B > 0 ? chunk_first[1] - chunk_first[0] : 0;
+  for (int64_t b = 1; b < B && uniform_chunks > 0; ++b)
+    if (chunk_first[b + 1] - chunk_first[b] != uniform_chunks) uniform_chunks = 0;
   DiagLBArgs<real> lba;
   if (lookback) {
     lba.bt = bt;
@@ -449,6 +489,11 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
         gta.bt = bt;
         DEER_CK(launch_gru_lin_tiled(gta, st));
       }
+    } else if (mixed) {
+      if constexpr (sizeof(real) == 8) {
+        mla.bt = bt;
+        DEER_CK(launch_lin_ma_mixed(mla, st));
+      }
     } else {
       DEER_CK(launch_linearize<real>(la, st));
     }
@@ -475,11 +520,17 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     if (!stop && !fused) {
       const int64_t s0c = g_launches.load();
       pt.begin(PH_SCAN);
-      if (o->jac == DEER_JAC_FULL) {
+      if (mixed) {
+        if constexpr (sizeof(real) == 8) {
+          msa.bt = bt;
+          DEER_CK(launch_dense_scan_mixed(msa, st));
+        }
+      } else if (o->jac == DEER_JAC_FULL) {
         DEER_CK(launch_dense_scan<real>(dsa, st));
       } else if (lookback) {
         lba.bt = bt;
         lba.epoch += 1;
+        lba.cps = uniform_chunks;
         DEER_CK(launch_diag_lookback<real>(lba, st));
       } else {
         DEER_CK(launch_diag_scan<real>(gsa, st));
@@ -615,7 +666,7 @@ deer_status deer_rollout(const deer_dynamics* f, int64_t batch, int64_t T,
 
 size_t deer_grad_workspace_bytes(const deer_dynamics* f, int64_t batch, int64_t T,
                                  const deer_options* opt) {
-  if (!opt || batch < 0 || T < 0) return 0;
+  if (!opt || batch < 0 || T < 0 || opt->prec == DEER_MIXED_BF16) return 0;
   deer_options o = *opt;
   o.jac = DEER_JAC_FULL;
   o.damp = DEER_DAMP_NONE;
@@ -738,6 +789,7 @@ deer_status deer_grad(const deer_dynamics* f, int64_t batch, int64_t T, const vo
   deer_options o = *opt;
   o.jac = DEER_JAC_FULL;
   o.damp = DEER_DAMP_NONE;
+  if (o.prec == DEER_MIXED_BF16) return DEER_ERR_UNSUPPORTED;
   deer_status c = check_common(f, &o);
   if (c != DEER_OK) return c;
   if (batch < 0 || T < 0) return DEER_ERR_INVALID;
@@ -933,7 +985,8 @@ static deer_status solve_noalloc_impl(const deer_dynamics* f, int64_t B, int64_t
                        reinterpret_cast<unsigned*>(ws + ly.lb_ticket),
                        reinterpret_cast<unsigned*>(ws + ly.lb_flags),
                        reinterpret_cast<real*>(ws + ly.lb_agg),
-                       reinterpret_cast<real*>(ws + ly.lb_pre), 0u, flags, o->reset, reset_thr};
+                       reinterpret_cast<real*>(ws + ly.lb_pre), 0u, 0, flags, o->reset,
+                       reset_thr};
   if (lookback) DEER_CK(cudaMemsetAsync(lba.flags, 0, (size_t)ly.n_chunks_max * 4, st));
 
   deer_status status = DEER_OK;
@@ -988,6 +1041,7 @@ deer_status deer_solve_noalloc(const deer_dynamics* f, int64_t batch, int64_t T,
                                deer_info* info) {
   deer_status c = check_common(f, opt);
   if (c != DEER_OK) return c;
+  if (opt->prec == DEER_MIXED_BF16) return DEER_ERR_UNSUPPORTED;
   if (batch < 0 || T < 0) return DEER_ERR_INVALID;
   if (batch == 0 || T == 0) return DEER_OK;
   if (!s0 || !s_out) return DEER_ERR_INVALID;

@@ -66,8 +66,11 @@ __global__ void __launch_bounds__(256) k_diag_lb(DiagLBArgs<real> a) {
   __shared__ unsigned s_tile;
   if (threadIdx.x == 0) s_tile = atomicAdd(a.ticket, 1u);
   __syncthreads();
-  const int64_t ac = s_tile;
-  if (ac >= a.bt.act_chunks) return;  // uniform over the CTA
+  const int64_t tk = s_tile;
+  if (tk >= a.bt.act_chunks) return;  // uniform over the CTA
+  // ticket -> active chunk index: sequence-major, or round-robin over the sequences when
+  // they all have cps chunks (a predecessor tile always holds a smaller ticket either way)
+  const int64_t ac = a.cps > 0 ? (tk % a.bt.n_act) * a.cps + tk / a.bt.n_act : tk;
   int64_t seq, c, r0;
   int n;
   act_chunk(a.bt, ac, seq, c, r0, n);

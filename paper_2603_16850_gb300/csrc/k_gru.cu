@@ -17,8 +17,7 @@ constexpr int kGThreads = 256;
 
 struct GruSmem {
   float UT[4][kGD][kGD];      // Uz^T, Ur^T, Uh^T, M^T as [k][out]  (64 KB)
-  float HT[kGD][kGT];         // h transposed [k][row]
-  float QT[kGD][kGT];         // r*h transposed
+  float HT[kGD][kGT];         // h transposed [k][row]; reused for r*h after the first product
   float CT[kGD][kGT];         // h*r*(1-r) transposed
   float diag_z[kGD], diag_h[kGD];
   float rmx[kGT];
@@ -126,20 +125,24 @@ __global__ void __launch_bounds__(kGThreads) k_gru_lin_tiled(GruTileArgs a) {
           ar_[i][j] += hh[i] * rr[j];
         }
     }
-    float z[4][4], r[4][4];
+    float z[4][4], r[4][4], hreg[4][4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float4 h4 = lds4(&S.HT[4 * tx + j][4 * ty]);
-      const float hh[4] = {h4.x, h4.y, h4.z, h4.w};
+      hreg[0][j] = h4.x; hreg[1][j] = h4.y; hreg[2][j] = h4.z; hreg[3][j] = h4.w;
+    }
+    __syncthreads();  // every thread is done reading h: its space now takes r*h
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
       float q[4], cc[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         z[i][j] = fsig(az[i][j]);
         r[i][j] = fsig(ar_[i][j]);
-        q[i] = r[i][j] * hh[i];
-        cc[i] = hh[i] * r[i][j] * (1.f - r[i][j]);
+        q[i] = r[i][j] * hreg[i][j];
+        cc[i] = hreg[i][j] * r[i][j] * (1.f - r[i][j]);
       }
-      *reinterpret_cast<float4*>(&S.QT[4 * tx + j][4 * ty]) = make_float4(q[0], q[1], q[2], q[3]);
+      *reinterpret_cast<float4*>(&S.HT[4 * tx + j][4 * ty]) = make_float4(q[0], q[1], q[2], q[3]);
       *reinterpret_cast<float4*>(&S.CT[4 * tx + j][4 * ty]) = make_float4(cc[0], cc[1], cc[2], cc[3]);
     }
     __syncthreads();
@@ -155,7 +158,7 @@ __global__ void __launch_bounds__(kGThreads) k_gru_lin_tiled(GruTileArgs a) {
     }
 #pragma unroll 8
     for (int k = 0; k < kGD; ++k) {
-      const float4 q4 = lds4(&S.QT[k][4 * ty]);
+      const float4 q4 = lds4(&S.HT[k][4 * ty]);
       const float4 c4 = lds4(&S.CT[k][4 * ty]);
       const float4 uh = lds4(&S.UT[2][k][4 * tx]);
       const float4 mm = lds4(&S.UT[3][k][4 * tx]);
@@ -185,7 +188,7 @@ __global__ void __launch_bounds__(kGThreads) k_gru_lin_tiled(GruTileArgs a) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int o = 4 * tx + j;
-        const float h = S.HT[o][rl];
+        const float h = hreg[i][j];
         const float ht = tanhf(ah[i][j]);
         const float zi = z[i][j], ri = r[i][j];
         const float F = (1.f - zi) * h + zi * ht;

@@ -184,6 +184,9 @@ struct DiagLBArgs {
   real* agg;            // [n_chunks][d][2] tile aggregates (A, B)
   real* pre;            // [n_chunks][d] state at the end of the tile
   unsigned epoch;       // distinct per launch within one solve (starts at 1)
+  int64_t cps;          // > 0: every active sequence has this many chunks and tickets
+                        // are dealt round-robin over the sequences (tile k of every
+                        // sequence before tile k+1 of any), which keeps look-back short
   Flags* status;        // timeout reporting
   int reset;
   real reset_thr;
@@ -263,6 +266,49 @@ cudaError_t launch_gru_lin_tiled(const GruTileArgs& a, cudaStream_t st);
 inline bool gru_tiled_supported(int kind, int d, int d_in, int jac, int prec) {
   return kind == DEER_F_GRU && d == 64 && d_in == 64 && jac != DEER_JAC_FULL &&
          prec == DEER_FP32;
+}
+
+}  // namespace deer
+
+#include <cuda_bf16.h>
+
+namespace deer {
+
+// Mixed precision (DEER_MIXED_BF16), mass action with d = 16 / 32, full Jacobian:
+// float64 state, dynamics value and residual; float32 Jacobian arithmetic stored as
+// E_t = A_t - I in bfloat16; the correction-form scan Delta_t = (I + E_t) Delta_{t-1} - r_t
+// accumulates in float32 and the update s += Delta is applied in float64.
+struct MixedLinArgs {
+  DynView<double> dv;
+  Batch bt;
+  const double* s0;
+  const double* s;
+  __nv_bfloat16* E;   // [N][d][d]
+  float* b;           // [N][d]  (-r_t)
+  SeqAcc* acc;
+  int damp;
+  double dparam;
+};
+
+struct MixedScanArgs {
+  Batch bt;
+  int d;
+  const __nv_bfloat16* E;
+  const float* b;
+  double* s;
+  float* aggP;  // [n_chunks][d][d]
+  float* aggv;  // [n_chunks][d]
+  float* cin;   // [n_chunks][d]
+  int reset;
+  double reset_thr;
+};
+
+cudaError_t launch_lin_ma_mixed(const MixedLinArgs& a, cudaStream_t st);
+cudaError_t launch_dense_scan_mixed(const MixedScanArgs& a, cudaStream_t st);
+
+inline bool mixed_supported(int kind, int d, int jac) {
+  return (kind == DEER_F_MASSACTION_RK4 || kind == DEER_F_MASSACTION_EULER) &&
+         (d == 16 || d == 32) && jac == DEER_JAC_FULL;
 }
 
 }  // namespace deer

@@ -304,3 +304,25 @@ def test_gru_d64_quasi_elk_fp32(lam):
     roll = onewton.rollout(odyn.GRU(g["W"], g["U"], g["x"]), g["s0"], T)
     for b in range(B):
         assert _relerr(s.cpu().numpy()[b * T:(b + 1) * T], roll[b]) <= 1e-5
+
+
+@pytest.mark.parametrize("d,R", [(16, 24), (32, 48)])
+def test_mixed_bf16_ragged_matches_fp64_rollout(d, R):
+    """Mixed precision (bf16 Jacobians E = A - I, float32 scan accumulation, float64
+    state and residual) on a ragged batch: the fixed point is refined against the float64
+    residual, so it equals the float64 rollout to float64 accuracy."""
+    deer = _deer()
+    lengths = [300, 1000, 77, 2000, 1]
+    off = synth.offsets_from_lengths(lengths)
+    B = len(lengths)
+    p = _ma_problem(B, d, R, 1, seed=12)
+    dyn = _ma_dyn(p, torch.float64)
+    s, info = deer.deer_solve_batched(dyn, _t(p["s0"]), off, jac="full", tol=1e-10,
+                                      prec="mixed_bf16", init="s0", reset=True, max_iters=500)
+    assert bool(info.converged.all()), info
+    od = _ma_oracle(p)
+    sn = s.cpu().numpy()
+    for b, L in enumerate(lengths):
+        sub = odyn.MassAction(p["topology"][b:b + 1], p["params"][b:b + 1], p["dt"], "rk4", d=d)
+        roll = onewton.rollout(sub, p["s0"][b:b + 1], L)[0]
+        assert _relerr(sn[off[b]:off[b + 1]], roll) <= 1e-9
