@@ -203,6 +203,86 @@ def gru_diag_measurement(deer, N, lib, dev, stream, steps=3):
                           "flop_per_row": 4 * 2 * d * d}}
 
 
+def adjoint_measurement(deer, N, lib, dev, stream):
+    """Differentiation workload: d=32 kinetic networks (48 reactions), B=256, T=32768, RK4
+    dt=1e-3, FP32. Forward full-Jacobian solve, then the adjoint gradient of
+    sum_t ||s_t - y_t||^2 w.r.t. the rate constants (targets y: the sequential rollout with
+    rate constants k exp(0.1 eps), used for timing only)."""
+    import numpy as np
+    import torch
+    import synth
+    B, d, R, T = 256, 32, 48, 32768
+    p = synth.massaction(B, d, R, T, seed=3)
+    topo = torch.tensor(p["topology"], dtype=torch.int32, device=dev)
+    k = torch.tensor(p["params"], dtype=torch.float32, device=dev)
+    kp = torch.tensor(synth.perturbed_rates(p["params"], seed=4), dtype=torch.float32, device=dev)
+    s0 = torch.tensor(p["s0"], dtype=torch.float32, device=dev)
+    dyn = deer.Dynamics.massaction(topo, k, d, p["dt"])
+    y = deer.deer_rollout(deer.Dynamics.massaction(topo, kp, d, p["dt"]), s0, T, prec="fp32")
+    opts = dict(jac="full", tol=5e-7, confirm=2, prec="fp32", init="zeros", reset=True)
+    ws_ = torch.empty(deer.deer_workspace_bytes(dyn, B, B * T, **opts), dtype=torch.uint8,
+                      device=dev)
+    s, info = deer.deer_solve(dyn, s0, T, workspace=ws_, stream=stream, **opts)  # warm
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    s, info = deer.deer_solve(dyn, s0, T, workspace=ws_, stream=stream, **opts)
+    e1.record(stream)
+    g = 2.0 * (s - y)
+    dk, ds0 = deer.deer_grad(dyn, s0, T, s, g, prec="fp32")
+    e2.record(stream)
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1)
+    grad = e1.elapsed_time(e2)
+    return {"workload": "mass action d=32 R=48 B=256 T=32768 RK4, FP32, adjoint wrt rates",
+            "forward_ms": fwd, "grad_ms": grad,
+            "forward_value": B * T / (fwd / 1000.0), "grad_value": B * T / (grad / 1000.0),
+            "unit": UNIT, "newton_iters_max": int(info.iters.max()),
+            "converged": bool(info.converged.all()),
+            "grad_finite": bool(torch.isfinite(dk).all())}
+
+
+def ragged_mixed_measurement(deer, N, lib, dev, stream, groups=1):
+    """Ragged mixed-precision workload: d=16 kinetic networks (24 reactions), lengths
+    uniform on [1000, 100000], RK4 dt=1e-3, bf16 Jacobians with float32 scan accumulation,
+    float64 state and residual. One group of 1000 trajectories (the full 10000-trajectory
+    batch does not fit its Jacobians in HBM at once and runs as ten such groups)."""
+    import numpy as np
+    import torch
+    import synth
+    B, d, R = 1000, 16, 24
+    lengths = synth.ragged_lengths(B, 1000, 100000, seed=5)
+    off = synth.offsets_from_lengths(lengths)
+    p = synth.massaction(B, d, R, 1, seed=6)
+    topo = torch.tensor(p["topology"], dtype=torch.int32, device=dev)
+    k = torch.tensor(p["params"], dtype=torch.float64, device=dev)
+    s0 = torch.tensor(p["s0"], dtype=torch.float64, device=dev)
+    dyn = deer.Dynamics.massaction(topo, k, d, p["dt"])
+    opts = dict(jac="full", tol=1e-10, prec="mixed_bf16", init="zeros", reset=True)
+    ntot = int(off[-1])
+    ws_ = torch.empty(deer.deer_workspace_bytes(dyn, B, ntot, **opts), dtype=torch.uint8,
+                      device=dev)
+    torch.cuda.synchronize()
+    lib.deer_profile_reset()
+    lib.deer_profile_enable(1)
+    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    e0.record(stream)
+    s, info = deer.deer_solve_batched(dyn, s0, off, workspace=ws_, stream=stream, **opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lib.deer_profile_enable(0)
+    prof = N.deer_profile()
+    lib.deer_profile_read(prof)
+    ms = e0.elapsed_time(e1)
+    return {"workload": "ragged mass action d=16 R=24, T ~ U[1000,100000], B=1000 (one of "
+                        "ten groups), bf16 Jacobians / fp32 scan / fp64 residual",
+            "total_steps": ntot, "ms": ms, "value": ntot / (ms / 1000.0), "unit": UNIT,
+            "newton_iters_max": int(info.iters.max()),
+            "newton_iters_p50": float(np.percentile(info.iters.numpy(), 50)),
+            "converged": bool(info.converged.all()),
+            "phase_ms": {n: prof.ms[i] for i, n in enumerate(N.PHASES)}}
+
+
 def run(args):
     import numpy as np
     import torch
@@ -329,6 +409,8 @@ def run(args):
     extra = {}
     if rank == 0 and ws == 1 and not args.no_extra:
         extra["gru_quasi_deer"] = gru_diag_measurement(deer, N, lib, dev, stream)
+        extra["adjoint"] = adjoint_measurement(deer, N, lib, dev, stream)
+        extra["ragged_mixed"] = ragged_mixed_measurement(deer, N, lib, dev, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -87,7 +87,7 @@ static bool d_supported(int kind, int d, int jac) {
 struct Layout {
   size_t offsets, chunk_first, act_seq, act_row_off, act_chunk_off, acc, info, flags, ma, gru_M,
       A, b, aggP, aggv, cin, gam, mob, pin, sprev, lb_ticket, lb_flags, lb_agg, lb_pre, xproj,
-      total;
+      adj_off, adj_e, total;
   int64_t n_chunks_max;
   int64_t ma_stride, n_ma;
   int L;
@@ -165,6 +165,12 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
     ly.mob = take((size_t)C * d * 4 * rs);
     ly.pin = take((size_t)C * d * rs);
   }
+  ly.adj_off = ly.adj_e = p;
+  if (mixed) {
+    const int64_t nseq = f->topology_stride ? (B > 0 ? B : 1) : 1;
+    ly.adj_off = take((size_t)nseq * (d + 1) * 4);
+    ly.adj_e = take((size_t)nseq * 4 * f->n_reactions * 4);
+  }
   ly.xproj = p;
   if (gru_tiled_supported(f->kind, d, f->d_in, o->jac, o->prec))
     ly.xproj = take((size_t)N * 3 * d * rs);
@@ -211,7 +217,7 @@ static deer_status check_common(const deer_dynamics* f, const deer_options* o) {
   if (o->prec != DEER_FP64 && o->prec != DEER_FP32 && o->prec != DEER_MIXED_BF16)
     return DEER_ERR_INVALID;
   if (o->prec == DEER_MIXED_BF16 &&
-      (!mixed_supported(f->kind, f->d, o->jac) ||
+      (!mixed_supported(f->kind, f->d, o->jac) || f->n_reactions > 64 ||
        (o->damp != DEER_DAMP_NONE && o->damp != DEER_DAMP_SCALE)))
     return DEER_ERR_UNSUPPORTED;
   if (!d_supported(f->kind, f->d, o->jac)) return DEER_ERR_UNSUPPORTED;
@@ -394,6 +400,13 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   MixedScanArgs msa;
   if constexpr (sizeof(real) == 8) {
     if (mixed) {
+      const int64_t nseq = f->topology_stride ? B : 1;
+      DEER_CK(launch_ma_adjacency(nseq, d, f->n_reactions, f->topology, f->topology_stride,
+                                  reinterpret_cast<int32_t*>(ws + ly.adj_off),
+                                  reinterpret_cast<int32_t*>(ws + ly.adj_e), st));
+      mla.adj_off = reinterpret_cast<const int32_t*>(ws + ly.adj_off);
+      mla.adj_e = reinterpret_cast<const int32_t*>(ws + ly.adj_e);
+      mla.adj_stride = f->topology_stride ? 4 * (int64_t)f->n_reactions : 0;
       mla.dv = dv;
       mla.bt = bt;
       mla.s0 = s0;

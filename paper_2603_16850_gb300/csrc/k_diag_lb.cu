@@ -6,7 +6,8 @@
 // rows in registers and shared memory (Kogge-Stone over the row sub-ranges), publishes its
 // aggregate, resolves the state entering the tile by looking back over the published
 // aggregates / prefixes of the preceding tiles of the same sequence, and writes s. a, b are
-// read once and s written once: 12 bytes per coordinate-step in float32.
+// read from DRAM once (the second read hits L2) and s written once: 12 bytes of DRAM
+// traffic per coordinate-step in float32.
 #include "kernels.h"
 
 namespace deer {
@@ -77,38 +78,41 @@ __global__ void __launch_bounds__(256) k_diag_lb(DiagLBArgs<real> a) {
   const int g = threadIdx.x % G, q = threadIdx.x / G;
   const int k0 = 4 * g;
 
-  // load this thread's rows (identity elements past the end of a ragged tile)
-  real av[RPT][4], bv[RPT][4];
-#pragma unroll
-  for (int i = 0; i < RPT; ++i) {
+  // this thread's rows (identity elements past the end of a ragged tile); the values are
+  // read twice: here for the aggregate, and after the look-back (from L2) for the output,
+  // which keeps few registers live and many CTAs resident
+  auto load_row = [&](int i, real (&av)[4], real (&bv)[4]) {
     const int lr = q * RPT + i;
     if (lr < n) {
       const int64_t off = (r0 + lr) * D + k0;
       const V4<real> bb = ld4(a.b + off);
-      bv[i][0] = bb.x; bv[i][1] = bb.y; bv[i][2] = bb.z; bv[i][3] = bb.w;
+      bv[0] = bb.x; bv[1] = bb.y; bv[2] = bb.z; bv[3] = bb.w;
       if (a.amode == 0) {
         const V4<real> aa = ld4(a.a + off);
-        av[i][0] = aa.x; av[i][1] = aa.y; av[i][2] = aa.z; av[i][3] = aa.w;
+        av[0] = aa.x; av[1] = aa.y; av[2] = aa.z; av[3] = aa.w;
       } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) av[i][k] = a.aconst;
+        for (int k = 0; k < 4; ++k) av[k] = a.aconst;
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) { av[i][k] = real(1); bv[i][k] = real(0); }
+      for (int k = 0; k < 4; ++k) { av[k] = real(1); bv[k] = real(0); }
     }
-  }
+  };
   // thread aggregate (composition in row order)
   real A[4], Bv[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) { A[k] = real(1); Bv[k] = real(0); }
 #pragma unroll
-  for (int i = 0; i < RPT; ++i)
+  for (int i = 0; i < RPT; ++i) {
+    real av[4], bv[4];
+    load_row(i, av, bv);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      Bv[k] = av[i][k] * Bv[k] + bv[i][k];
-      A[k] = av[i][k] * A[k];
+      Bv[k] = av[k] * Bv[k] + bv[k];
+      A[k] = av[k] * A[k];
     }
+  }
 #pragma unroll
   for (int k = 0; k < 4; ++k) { sA[q][k0 + k] = A[k]; sB[q][k0 + k] = Bv[k]; }
   __syncthreads();
@@ -221,10 +225,11 @@ __global__ void __launch_bounds__(256) k_diag_lb(DiagLBArgs<real> a) {
   for (int i = 0; i < RPT; ++i) {
     const int lr = q * RPT + i;
     if (lr < n) {
-      real o[4];
+      real av[4], bv[4], o[4];
+      load_row(i, av, bv);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        x[k] = av[i][k] * x[k] + bv[i][k];
+        x[k] = av[k] * x[k] + bv[k];
         o[k] = (a.reset && !(x[k] <= a.reset_thr && x[k] >= -a.reset_thr)) ? real(0) : x[k];
       }
       st4(a.s + (r0 + lr) * D + k0, o);

@@ -11,11 +11,46 @@ __device__ __forceinline__ unsigned gmask_mixed() {
   return D == 32 ? 0xffffffffu : (0xffffu << (16 * ((threadIdx.x >> 4) & 1)));
 }
 
+// Species adjacency: for sequence b and species i, the reactions r that change species i
+// and the change nu_{r,i} (reactants -1 each, products +1 each).
+__global__ void k_ma_adjacency(int64_t n_seq, int d, int R, const int32_t* __restrict__ topo,
+                               int64_t tstride, int32_t* __restrict__ adj_off,
+                               int32_t* __restrict__ adj_e) {
+  const int64_t seq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (seq >= n_seq) return;
+  const int32_t* tt = topo + seq * tstride;
+  int32_t* off = adj_off + seq * (d + 1);
+  int32_t* e = adj_e + seq * (int64_t)(4 * R);
+  int pos = 0;
+  for (int i = 0; i < d; ++i) {
+    off[i] = pos;
+    for (int r = 0; r < R; ++r) {
+      const int i1 = tt[4 * r], i2 = tt[4 * r + 1], p1 = tt[4 * r + 2], p2 = tt[4 * r + 3];
+      const int nu = (i == p1) + (i == p2) - (i == i1) - (i == i2);
+      if (nu != 0 && pos < 4 * R) e[pos++] = r | ((nu + 4) << 16);
+    }
+  }
+  off[d] = pos;
+}
+
+cudaError_t launch_ma_adjacency(int64_t n_seq, int d, int R, const int32_t* topo,
+                                int64_t tstride, int32_t* adj_off, int32_t* adj_e,
+                                cudaStream_t st) {
+  if (n_seq == 0) return cudaSuccess;
+  k_ma_adjacency<<<grid_for(n_seq, 128), 128, 0, st>>>(n_seq, d, R, topo, tstride, adj_off,
+                                                     adj_e);
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <int D, bool RK4>
 __global__ void __launch_bounds__(128) k_lin_ma_mixed(MixedLinArgs a) {
   constexpr int GROUPS = 128 / D;
+  constexpr int RMAX = 64;  // reactions per network held in shared memory
   __shared__ float sG[GROUPS][D][D + 1];
   __shared__ float sK[GROUPS][D][D];
+  __shared__ double sRate[GROUPS][RMAX];
+  __shared__ float sD1[GROUPS][RMAX], sD2[GROUPS][RMAX];  // d rate / d c_i1, d c_i2 (no k)
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gm = gmask_mixed<D>();
   const int64_t ar = blockIdx.x * (int64_t)GROUPS + grp;
@@ -27,9 +62,12 @@ __global__ void __launch_bounds__(128) k_lin_ma_mixed(MixedLinArgs a) {
                               : 0.0;
   const double* kk = a.dv.params + seq * a.dv.pstride;
   const int4* tt = reinterpret_cast<const int4*>(a.dv.topo + seq * a.dv.tstride);
-  const int R = a.dv.R;
+  const int32_t* aoff = a.adj_off + (a.adj_stride ? seq : 0) * (D + 1);
+  const int32_t* ae = a.adj_e + (a.adj_stride ? seq : 0) * a.adj_stride;
+  const int e0 = __ldg(aoff + lane), e1 = __ldg(aoff + lane + 1);
+  const int R = a.dv.R < RMAX ? a.dv.R : RMAX;
   const double h = a.dv.dt;
-  double c = s_prev, acc = 0.0, g = 0.0;
+  double c = s_prev, acc = 0.0;
   float Kacc[D];
 #pragma unroll
   for (int j = 0; j < D; ++j) Kacc[j] = 0.f;
@@ -37,23 +75,33 @@ __global__ void __launch_bounds__(128) k_lin_ma_mixed(MixedLinArgs a) {
   for (int stage = 0; stage < nst; ++stage) {
     const float cK = stage == 0 ? 0.f : (stage == 3 ? (float)h : 0.5f * (float)h);
     const double w = (stage == 1 || stage == 2) ? 2.0 : 1.0;
+    // every reaction's rate once (lane r % D), in float64, and its two partial derivatives
+    for (int r0 = 0; r0 < R; r0 += D) {
+      const int r = r0 + lane;
+      const int4 q = __ldg(tt + (r < R ? r : 0));
+      const double c1 = __shfl_sync(gm, c, q.x, D);
+      const double c2 = __shfl_sync(gm, c, q.y < 0 ? 0 : q.y, D);
+      if (r < R) {
+        const double kr = __ldg(kk + r);
+        const double f2 = q.y < 0 ? 1.0 : c2;
+        sRate[grp][r] = kr * c1 * f2;
+        sD1[grp][r] = (float)(kr * f2);
+        sD2[grp][r] = (float)(kr * c1);
+      }
+    }
 #pragma unroll
     for (int j = 0; j < D; ++j) sG[grp][lane][j] = 0.f;
     __syncwarp(gm);
-    g = 0.0;
-    for (int r = 0; r < R; ++r) {
+    // this species' slope and its row of the rate Jacobian, from its own reactions
+    double g = 0.0;
+    for (int e = e0; e < e1; ++e) {
+      const int code = __ldg(ae + e);
+      const int r = code & 0xffff;
+      const int nu = (code >> 16) - 4;
+      g += (double)nu * sRate[grp][r];
       const int4 q = __ldg(tt + r);
-      const double kr = __ldg(kk + r);
-      const double c1 = __shfl_sync(gm, c, q.x, D);
-      const double c2 = __shfl_sync(gm, c, q.y < 0 ? 0 : q.y, D);
-      const double f2 = q.y < 0 ? 1.0 : c2;
-      const int nu = (lane == q.z) + (lane == q.w) - (lane == q.x) - (lane == q.y);
-      g += (double)nu * (kr * c1 * f2);
-      if (nu != 0) {
-        const float fk = (float)(nu * kr);
-        sG[grp][lane][q.x] += fk * (float)f2;
-        if (q.y >= 0) sG[grp][lane][q.y] += fk * (float)c1;
-      }
+      sG[grp][lane][q.x] += (float)nu * sD1[grp][r];
+      if (q.y >= 0) sG[grp][lane][q.y] += (float)nu * sD2[grp][r];
     }
     __syncwarp(gm);
     float Gi[D], Kn[D];
@@ -75,10 +123,10 @@ __global__ void __launch_bounds__(128) k_lin_ma_mixed(MixedLinArgs a) {
       sK[grp][lane][j] = Kn[j];
       Kacc[j] += (float)w * Kn[j];
     }
-    __syncwarp(gm);
     acc += w * g;
     const double cs = stage == 2 ? h : 0.5 * h;
     c = s_prev + cs * g;
+    __syncwarp(gm);
   }
   const double hw = RK4 ? h / 6.0 : h;
   const double F = s_prev + hw * acc;

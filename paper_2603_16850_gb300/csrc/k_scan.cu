@@ -589,6 +589,9 @@ static void adj_launch(const AdjScanArgs<real>& a, cudaStream_t st) {
   note_launch(3);
 }
 
+template <class real, int D>
+void adj_launch_wide(const AdjScanArgs<real>& a, cudaStream_t st);
+
 template <class real>
 cudaError_t launch_adjoint_scan(const AdjScanArgs<real>& a, cudaStream_t st) {
   if (a.bt.N == 0) return cudaSuccess;
@@ -597,8 +600,8 @@ cudaError_t launch_adjoint_scan(const AdjScanArgs<real>& a, cudaStream_t st) {
     case 2: adj_launch<real, 2>(a, st); break;
     case 4: adj_launch<real, 4>(a, st); break;
     case 8: adj_launch<real, 8>(a, st); break;
-    case 16: adj_launch<real, 16>(a, st); break;
-    case 32: adj_launch<real, 32>(a, st); break;
+    case 16: adj_launch_wide<real, 16>(a, st); break;
+    case 32: adj_launch_wide<real, 32>(a, st); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -725,5 +728,126 @@ template void dense_launch_wide<float, 16>(const DenseScanArgs<float>&, cudaStre
 template void dense_launch_wide<float, 32>(const DenseScanArgs<float>&, cudaStream_t);
 template void dense_launch_wide<double, 16>(const DenseScanArgs<double>&, cudaStream_t);
 template void dense_launch_wide<double, 32>(const DenseScanArgs<double>&, cudaStream_t);
+
+}  // namespace deer
+
+namespace deer {
+
+// ----------------------------------------------------------------------------
+// Reverse (adjoint) dense scan, d = 16 / 32: D lanes per chunk / sequence; lane i owns
+// entry i of the vectors and column i of the reversed chunk product. M_t = A_{t+1}^T is
+// read column-wise (entry (k, i) of A_{t+1} for lane i), i.e. coalesced across lanes.
+// ----------------------------------------------------------------------------
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_adj_chunk_wide(AdjScanArgs<real> a) {
+  constexpr int G = 128 / D;
+  const int grp = threadIdx.x / D, lane = threadIdx.x % D;
+  const unsigned gm = group_mask<D>();
+  const int64_t c = blockIdx.x * (int64_t)G + grp;
+  const bool valid = c < a.bt.n_chunks;
+  int64_t seq = 0, r0 = 0;
+  int n = 0;
+  if (valid) chunk_rows(a.bt, c, seq, r0, n);
+  const int64_t rend = valid ? __ldg(a.bt.offsets + seq + 1) : 0;
+  const bool need_P = valid && c != __ldg(a.bt.chunk_first + seq + 1) - 1;
+  real Pc[D];
+  real v = real(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) Pc[i] = i == lane ? real(1) : real(0);
+  for (int t = n - 1; t >= 0; --t) {
+    const int64_t row = r0 + t;
+    const real gt = __ldg(a.g + row * D + lane);
+    if (row + 1 < rend) {
+      const real* An = a.A + (row + 1) * (int64_t)(D * D);
+      real nv = gt;
+#pragma unroll
+      for (int k = 0; k < D; ++k) nv += __ldg(An + k * D + lane) * __shfl_sync(gm, v, k, D);
+      v = nv;
+      if (need_P) {
+        real np[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          real x = real(0);
+#pragma unroll
+          for (int k = 0; k < D; ++k) x += __ldg(An + k * D + i) * Pc[k];
+          np[i] = x;
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) Pc[i] = np[i];
+      }
+    } else {
+      v = gt;
+#pragma unroll
+      for (int i = 0; i < D; ++i) Pc[i] = real(0);
+    }
+  }
+  if (valid) {
+    real* Po = a.aggP + c * (int64_t)(D * D);
+#pragma unroll
+    for (int i = 0; i < D; ++i) Po[i * D + lane] = Pc[i];
+    a.aggv[c * D + lane] = v;
+  }
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_adj_carry_wide(AdjScanArgs<real> a) {
+  constexpr int G = 128 / D;
+  const int grp = threadIdx.x / D, lane = threadIdx.x % D;
+  const unsigned gm = group_mask<D>();
+  const int64_t seq = blockIdx.x * (int64_t)G + grp;
+  const bool valid = seq < a.bt.B;
+  const int64_t c0 = valid ? a.bt.chunk_first[seq] : 0;
+  const int64_t c1 = valid ? a.bt.chunk_first[seq + 1] : 0;
+  real x = real(0);
+  for (int64_t c = c1 - 1; c >= c0; --c) {
+    a.cin[c * D + lane] = x;
+    const real* P = a.aggP + c * (int64_t)(D * D);
+    real y = a.aggv[c * D + lane];
+#pragma unroll
+    for (int k = 0; k < D; ++k) y += P[lane * D + k] * __shfl_sync(gm, x, k, D);
+    x = y;
+  }
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_adj_apply_wide(AdjScanArgs<real> a) {
+  constexpr int G = 128 / D;
+  const int grp = threadIdx.x / D, lane = threadIdx.x % D;
+  const unsigned gm = group_mask<D>();
+  const int64_t c = blockIdx.x * (int64_t)G + grp;
+  const bool valid = c < a.bt.n_chunks;
+  int64_t seq = 0, r0 = 0;
+  int n = 0;
+  if (valid) chunk_rows(a.bt, c, seq, r0, n);
+  const int64_t rend = valid ? __ldg(a.bt.offsets + seq + 1) : 0;
+  real x = valid ? a.cin[c * D + lane] : real(0);
+  for (int t = n - 1; t >= 0; --t) {
+    const int64_t row = r0 + t;
+    real y = __ldg(a.g + row * D + lane);
+    if (row + 1 < rend) {
+      const real* An = a.A + (row + 1) * (int64_t)(D * D);
+#pragma unroll
+      for (int k = 0; k < D; ++k) y += __ldg(An + k * D + lane) * __shfl_sync(gm, x, k, D);
+    }
+    x = y;
+    a.lam[row * D + lane] = y;
+  }
+}
+
+template <class real, int D>
+void adj_launch_wide(const AdjScanArgs<real>& a, cudaStream_t st) {
+  constexpr int G = 128 / D;
+  const unsigned gc = grid_for(a.bt.n_chunks, G);
+  const unsigned gs = grid_for(a.bt.B, G);
+  k_adj_chunk_wide<real, D><<<gc, 128, 0, st>>>(a);
+  k_adj_carry_wide<real, D><<<gs, 128, 0, st>>>(a);
+  k_adj_apply_wide<real, D><<<gc, 128, 0, st>>>(a);
+  note_launch(3);
+}
+
+template void adj_launch_wide<float, 16>(const AdjScanArgs<float>&, cudaStream_t);
+template void adj_launch_wide<float, 32>(const AdjScanArgs<float>&, cudaStream_t);
+template void adj_launch_wide<double, 16>(const AdjScanArgs<double>&, cudaStream_t);
+template void adj_launch_wide<double, 32>(const AdjScanArgs<double>&, cudaStream_t);
 
 }  // namespace deer

@@ -281,6 +281,9 @@ namespace deer {
 struct MixedLinArgs {
   DynView<double> dv;
   Batch bt;
+  const int32_t* adj_off;  // [n_seq][d+1] per-species offsets into adj_e
+  const int32_t* adj_e;    // [n_seq][4R] (reaction | (nu + 4) << 16)
+  int64_t adj_stride;      // 0 when the topology is shared
   const double* s0;
   const double* s;
   __nv_bfloat16* E;   // [N][d][d]
@@ -304,6 +307,10 @@ struct MixedScanArgs {
 };
 
 cudaError_t launch_lin_ma_mixed(const MixedLinArgs& a, cudaStream_t st);
+// per-sequence species -> (reaction, stoichiometric coefficient) lists for the mixed kernel
+cudaError_t launch_ma_adjacency(int64_t n_seq, int d, int R, const int32_t* topo,
+                                int64_t tstride, int32_t* adj_off, int32_t* adj_e,
+                                cudaStream_t st);
 cudaError_t launch_dense_scan_mixed(const MixedScanArgs& a, cudaStream_t st);
 
 inline bool mixed_supported(int kind, int d, int jac) {

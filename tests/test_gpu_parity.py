@@ -317,7 +317,7 @@ def test_mixed_bf16_ragged_matches_fp64_rollout(d, R):
     B = len(lengths)
     p = _ma_problem(B, d, R, 1, seed=12)
     dyn = _ma_dyn(p, torch.float64)
-    s, info = deer.deer_solve_batched(dyn, _t(p["s0"]), off, jac="full", tol=1e-10,
+    s, info = deer.deer_solve_batched(dyn, _t(p["s0"]), off, jac="full", tol=1e-12,
                                       prec="mixed_bf16", init="s0", reset=True, max_iters=500)
     assert bool(info.converged.all()), info
     od = _ma_oracle(p)
