@@ -40,6 +40,10 @@ LIN_FLOP_PER_ROW = 3 * 2 * 8 ** 3 + 300 + 2 * 8 ** 3 + 2 * 8 ** 2 + 2 * 8 ** 2
 # offset read, the new ones written (d^2 + d each way) and the state read and written.
 FUSED_BYTES_PER_ROW = 2 * (8 * 8 + 8) * 4 + 2 * 8 * 4
 FP32_LANES_PER_SM, SMS = 128, 152
+# Mixed-precision d=16 mass-action linearise, per row: the RK4 step Jacobian chain in
+# float32 (3 products of 16x16 matrices, 3 * 2 d^3 flop); the float64 rate evaluations are
+# not counted.
+MIXED_LIN_FLOP_PER_ROW = 3 * 2 * 16 ** 3
 
 
 def _peaks():
@@ -151,7 +155,7 @@ def run_reference(args):
     return 0
 
 
-def gru_diag_measurement(deer, N, lib, dev, stream, steps=3):
+def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64):
     """GRU cell d=64, inputs 64, T=65536, B=64, weights N(0,1/d), inputs N(0,1), quasi-DEER
     (diagonal Jacobian), FP32: converged state-steps/s and the single-pass look-back
     diagonal scan in achieved HBM GB/s (algorithmic 12 bytes per coordinate-step: a, b read,
@@ -159,7 +163,7 @@ def gru_diag_measurement(deer, N, lib, dev, stream, steps=3):
     import numpy as np
     import torch
     import synth
-    B, T, d = 64, 65536, 64
+    T, d = 65536, 64
     g = synth.gru(B, T, d, d, seed=0, dtype=np.float32)
     dyn = deer.Dynamics.gru(torch.tensor(g["W"], dtype=torch.float32, device=dev),
                             torch.tensor(g["U"], dtype=torch.float32, device=dev))
@@ -191,7 +195,7 @@ def gru_diag_measurement(deer, N, lib, dev, stream, steps=3):
     peaks, _ = _peaks()
     gbs = scan_rows * d * 12 / (scan_ms / 1000.0) / 1e9
     lin_tf = lin_rows * 4 * 2 * d * d / (lin_ms / 1000.0) / 1e12
-    return {"workload": "GRU d=64 d_in=64 T=65536 B=64, quasi-DEER, FP32, tol 1e-5 x2",
+    return {"workload": f"GRU d=64 d_in=64 T=65536 B={B}, quasi-DEER, FP32, tol 1e-5 x2",
             "value": B * T / (ms / 1000.0), "unit": UNIT, "ms_per_solve": ms,
             "newton_iters_max": int(info.iters.max()), "converged": bool(info.converged.all()),
             "diag_scan": {"kernel": "k_diag_lb<float,64>", "bound": "hbm", "achieved": gbs,
@@ -242,7 +246,7 @@ def adjoint_measurement(deer, N, lib, dev, stream):
             "grad_finite": bool(torch.isfinite(dk).all())}
 
 
-def ragged_mixed_measurement(deer, N, lib, dev, stream, groups=1):
+def ragged_mixed_measurement(deer, N, lib, dev, stream, B=1000):
     """Ragged mixed-precision workload: d=16 kinetic networks (24 reactions), lengths
     uniform on [1000, 100000], RK4 dt=1e-3, bf16 Jacobians with float32 scan accumulation,
     float64 state and residual. One group of 1000 trajectories (the full 10000-trajectory
@@ -250,7 +254,7 @@ def ragged_mixed_measurement(deer, N, lib, dev, stream, groups=1):
     import numpy as np
     import torch
     import synth
-    B, d, R = 1000, 16, 24
+    d, R = 16, 24
     lengths = synth.ragged_lengths(B, 1000, 100000, seed=5)
     off = synth.offsets_from_lengths(lengths)
     p = synth.massaction(B, d, R, 1, seed=6)
@@ -274,13 +278,39 @@ def ragged_mixed_measurement(deer, N, lib, dev, stream, groups=1):
     prof = N.deer_profile()
     lib.deer_profile_read(prof)
     ms = e0.elapsed_time(e1)
-    return {"workload": "ragged mass action d=16 R=24, T ~ U[1000,100000], B=1000 (one of "
+    lin_rows = prof.rows[1]
+    lin_s = prof.ms[1] / 1000.0
+    return {"workload": f"ragged mass action d=16 R=24, T ~ U[1000,100000], B={B} (one of "
                         "ten groups), bf16 Jacobians / fp32 scan / fp64 residual",
+            "rows_linearized": int(lin_rows), "rows_scanned": int(prof.rows[3]),
+            "linearize_rows_per_s": lin_rows / max(lin_s, 1e-12),
+            "linearize_tflops": lin_rows * MIXED_LIN_FLOP_PER_ROW / max(lin_s, 1e-12) / 1e12,
             "total_steps": ntot, "ms": ms, "value": ntot / (ms / 1000.0), "unit": UNIT,
             "newton_iters_max": int(info.iters.max()),
             "newton_iters_p50": float(np.percentile(info.iters.numpy(), 50)),
             "converged": bool(info.converged.all()),
             "phase_ms": {n: prof.ms[i] for i, n in enumerate(N.PHASES)}}
+
+
+def run_only(args):
+    """One secondary workload alone, for profiler captures of its kernels."""
+    import torch
+
+    import paper_2603_16850_gb300 as deer
+    from paper_2603_16850_gb300 import _native as N
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    lib = N.load()
+    if args.only == "gru":
+        out = gru_diag_measurement(deer, N, lib, dev, stream, steps=max(args.steps, 1),
+                                   B=args.batch or 64)
+    elif args.only == "ragged_mixed":
+        out = ragged_mixed_measurement(deer, N, lib, dev, stream, B=args.batch or 1000)
+    else:
+        out = adjoint_measurement(deer, N, lib, dev, stream)
+    print(json.dumps({"only": args.only, **out}), flush=True)
+    return 0
 
 
 def run(args):
@@ -461,11 +491,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary GRU quasi-DEER measurement")
+    ap.add_argument("--only", default="", choices=["", "gru", "adjoint", "ragged_mixed"],
+                    help="run one secondary workload alone (with --batch) and print it")
     ap.add_argument("--batch", type=int, default=0,
                     help="trajectories per GPU (default 4096; smaller for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run(args)
 
 

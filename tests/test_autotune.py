@@ -1,0 +1,63 @@
+"""Chunk-length autotuner: host logic on the CPU (key, cache round trip, selection with
+failing candidates), and one GPU tuning run whose choice is then read back from the cache."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2603_16850_gb300 import autotune as at
+
+
+def test_key_rounds_T_up_to_power_of_two():
+    assert at.make_key("G", "massaction", 8, "full", "fp32", 16384).endswith("|T16384")
+    assert at.make_key("G", "massaction", 8, "full", "fp32", 16385).endswith("|T32768")
+    assert at.make_key("G", "gru", 64, "diag", "fp32", 1) == "G|gru|d64|diag|fp32|T1"
+
+
+def test_pick_best_skips_failures_and_takes_fastest():
+    times = {16: 3.0, 32: 1.5, 64: float("inf"), 128: 2.0}
+
+    def fn(L):
+        if L == 256:
+            raise ValueError("rejected")
+        return times[L]
+
+    res = at.pick_best([16, 32, 64, 128, 256], fn)
+    assert res["chunk"] == 32 and res["ms"] == 1.5
+    assert math.isinf(res["timings"]["256"]) and math.isinf(res["timings"]["64"])
+
+
+def test_pick_best_raises_when_nothing_ran():
+    with pytest.raises(RuntimeError):
+        at.pick_best([16, 32], lambda L: float("inf"))
+
+
+def test_cache_round_trip(tmp_path):
+    p = str(tmp_path / "sub" / "tune.json")
+    assert at.load_cache(p) == {}
+    at.store("k1", {"chunk": 64, "ms": 1.0}, p)
+    at.store("k2", {"chunk": 32, "ms": 2.0}, p)
+    c = at.load_cache(p)
+    assert c["k1"]["chunk"] == 64 and c["k2"]["chunk"] == 32
+
+
+@pytest.mark.gpu
+def test_tune_chunk_on_gpu(tmp_path):
+    import torch
+
+    import paper_2603_16850_gb300 as deer
+    import synth
+    p = synth.massaction(64, 8, 12, 2048, seed=4)
+    dyn = deer.Dynamics.massaction(torch.tensor(p["topology"], dtype=torch.int32, device="cuda"),
+                                   torch.tensor(p["params"], dtype=torch.float32, device="cuda"),
+                                   8, p["dt"])
+    s0 = torch.tensor(p["s0"], dtype=torch.float32, device="cuda")
+    path = str(tmp_path / "tune.json")
+    best = at.tune_chunk(dyn, s0, 2048, candidates=(32, 64, 128), path=path, jac="full",
+                         prec="fp32", tol=5e-7, confirm=2, init="s0", reset=True)
+    assert best in (32, 64, 128)
+    assert at.cached_chunk(dyn, 2048, "full", "fp32", path=path) == best
+    s, info = deer.deer_solve(dyn, s0, 2048, chunk=best, jac="full", prec="fp32", tol=5e-7,
+                              confirm=2, init="s0", reset=True)
+    assert bool(info.converged.all())
+    assert np.isfinite(s.cpu().numpy()).all()
