@@ -91,12 +91,19 @@ typedef enum {
 
 typedef enum {
   DEER_FP64 = 0,       /* everything float64 */
-  DEER_FP32 = 1,       /* everything float32; residual max/merit accumulated in float64 */
+  DEER_FP32 = 1,       /* everything float32; per-sequence residual max/merit reported in
+                          float64 */
   DEER_MIXED_BF16 = 2  /* float64 state, dynamics value and residual; the Jacobian is formed
                           in float32 and stored as bf16 E = A - I, and the dense scan composes
-                          (I + E) with float32 accumulation in correction form. Mass-action
-                          kinetics with d = 16 or 32 and DEER_JAC_FULL (no damping or
-                          scale-ELK); not available in deer_grad or deer_solve_noalloc. */
+                          (I + E) with float32 accumulation in correction form. While a
+                          sequence's scaled residual is above 1e-4 (and in the first
+                          iteration) its dynamics value is evaluated in float32, whose
+                          rounding is far below that residual; such an iterate reports at
+                          least 1e-6 and cannot pass the test, so convergence is always
+                          decided on a float64 residual. State entries beyond 1e18 count as
+                          overflow for the reset heuristic. Mass-action kinetics with d = 16
+                          or 32 and DEER_JAC_FULL (no damping or scale-ELK); not available
+                          in deer_grad or deer_solve_noalloc. */
 } deer_prec;
 
 typedef struct {

@@ -145,7 +145,8 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
     ly.A = take((size_t)N * d * d * 2);
     ly.b = take((size_t)N * d * 4);
   } else if (o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d)) {
-    // chunk-interleaved Jacobians / offsets of the fused path, padded to whole chunks
+    // pending Jacobians / offsets of the fused path (chunk-major or chunk-interleaved),
+    // padded to whole chunks and to groups of 32 chunks
     const size_t rows = (size_t)((C + 31) / 32 * 32) * L;
     ly.A = take(rows * d * d * rs);
     ly.b = take(rows * d * rs);
@@ -414,8 +415,12 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
       mla.E = reinterpret_cast<__nv_bfloat16*>(ws + ly.A);
       mla.b = reinterpret_cast<float*>(ws + ly.b);
       mla.acc = acc;
+      mla.info = info;
+      mla.it = 0;
       mla.damp = o->damp;
       mla.dparam = o->damp_param;
+      mla.scale_f = o->damp == DEER_DAMP_SCALE ? (float)(1.0 - o->damp_param) : 1.f;
+      mla.dt_f = (float)f->dt;
       msa.bt = bt;
       msa.d = d;
       msa.E = mla.E;
@@ -425,7 +430,7 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
       msa.aggv = reinterpret_cast<float*>(ws + ly.aggv);
       msa.cin = reinterpret_cast<float*>(ws + ly.cin);
       msa.reset = o->reset;
-      msa.reset_thr = 1e30;
+      msa.reset_thr = 1e18;  // the scan and the Jacobians are float32
     }
   }
   const bool fused = !mixed && o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d);
@@ -505,6 +510,7 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     } else if (mixed) {
       if constexpr (sizeof(real) == 8) {
         mla.bt = bt;
+        mla.it = it;
         DEER_CK(launch_lin_ma_mixed(mla, st));
       }
     } else {

@@ -163,6 +163,47 @@ __device__ __forceinline__ void acc_resid(SeqAcc* acc, int64_t seq, bool valid, 
   }
 }
 
+// Float32 statistics variant of acc_resid for the float32 paths: the warp reduction runs
+// in float32 and only the final atomics touch float64, since every float64 instruction
+// costs the FP64 pipe (a small fraction of the FP32 rate on this GPU).
+__device__ __forceinline__ float nanmaxf(float a, float b) {
+  return (b > a || b != b) ? b : a;
+}
+
+__device__ __forceinline__ void acc_resid_f(SeqAcc* acc, int64_t seq, bool valid, float mx,
+                                            float sq) {
+  const unsigned full = 0xffffffffu;
+  unsigned vm = __ballot_sync(full, valid);
+  if (vm == 0) return;
+  int src = __ffs(vm) - 1;
+  long long sseq = __shfl_sync(full, (long long)seq, src);
+  bool uniform = __all_sync(full, (!valid) || (seq == sseq));
+  if (uniform) {
+    if (!valid) { mx = 0.f; sq = 0.f; }
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = nanmaxf(mx, __shfl_xor_sync(full, mx, o));
+      sq += __shfl_xor_sync(full, sq, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(&acc[sseq].max_bits, dbits((double)mx));
+      atomicAdd(&acc[sseq].sumsq, (double)sq);
+    }
+  } else if (valid) {
+    atomicMax(&acc[seq].max_bits, dbits((double)mx));
+    atomicAdd(&acc[seq].sumsq, (double)sq);
+  }
+}
+
+// Dispatch on the precision of the per-thread statistics.
+__device__ __forceinline__ void acc_resid_t(SeqAcc* acc, int64_t seq, bool valid, float mx,
+                                            float sq) {
+  acc_resid_f(acc, seq, valid, mx, sq);
+}
+__device__ __forceinline__ void acc_resid_t(SeqAcc* acc, int64_t seq, bool valid, double mx,
+                                            double sq) {
+  acc_resid(acc, seq, valid, mx, sq);
+}
+
 // ---------------------------------------------------------------------------
 // Launch bookkeeping (counted for deer_kernel_launch_count).
 // ---------------------------------------------------------------------------

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kFusedBlock) k_dense_fused(FusedArgs<real> a) 
   const int64_t ac = blockIdx.x * (int64_t)blockDim.x + tid;
   const bool valid = ac < a.bt.act_chunks;
   int64_t seq = 0;
-  double mx = 0.0, sq = 0.0;
+  real mx = real(0), sq = real(0);  // residual statistics in the path's own precision
   if (valid) {
     int64_t c, r0;
     int n;
@@ -125,8 +125,9 @@ __global__ void __launch_bounds__(kFusedBlock) k_dense_fused(FusedArgs<real> a) 
         prev[i] = x;
         r[i] = x - F[i];
         const real sabs = rabs(x);
-        mx = nanmax(mx, (double)rabs(r[i]) / (double)(sabs > real(1) ? sabs : real(1)));
-        sq += (double)r[i] * (double)r[i];
+        const real sr = rabs(r[i]) / (sabs > real(1) ? sabs : real(1));
+        mx = (sr > mx || sr != sr) ? sr : mx;
+        sq += r[i] * r[i];
       }
 #pragma unroll
       for (int i = 0; i < D; ++i) {
@@ -179,7 +180,247 @@ __global__ void __launch_bounds__(kFusedBlock) k_dense_fused(FusedArgs<real> a) 
       for (int j = 0; j < D; ++j) Po[i * D + j] = sP[i * D + j][tid];
     }
   }
-  acc_resid(a.acc, seq, valid, mx, sq);
+  acc_resid_t(a.acc, seq, valid, mx, sq);
+}
+
+// Row loads / stores through plain (coherent) accesses, for shared memory and for global
+// data the same kernel also writes.
+template <class real, int D>
+__device__ __forceinline__ void ldrow_p(const real* p, real (&v)[D]) {
+  if constexpr (sizeof(real) == 4 && D % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < D / 4; ++k) {
+      const float4 q = reinterpret_cast<const float4*>(p)[k];
+      v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+    }
+  } else if constexpr (sizeof(real) == 8 && D % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < D / 2; ++k) {
+      const double2 q = reinterpret_cast<const double2*>(p)[k];
+      v[2 * k] = q.x; v[2 * k + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = p[k];
+  }
+}
+
+template <class real, int D>
+__device__ __forceinline__ void strow_p(real* p, const real (&v)[D]) {
+  if constexpr (sizeof(real) == 4 && D % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < D / 4; ++k)
+      reinterpret_cast<float4*>(p)[k] =
+          make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+  } else if constexpr (sizeof(real) == 8 && D % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < D / 2; ++k)
+      reinterpret_cast<double2*>(p)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) p[k] = v[k];
+  }
+}
+// Read-only row load (the per-sequence kinetics tensors) through the non-coherent path.
+template <class real, int D>
+__device__ __forceinline__ void ldrow_ro(const real* __restrict__ p, real (&v)[D]) {
+  if constexpr (sizeof(real) == 4 && D % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < D / 4; ++k) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(p) + k);
+      v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+    }
+  } else if constexpr (sizeof(real) == 8 && D % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < D / 2; ++k) {
+      const double2 q = __ldg(reinterpret_cast<const double2*>(p) + k);
+      v[2 * k] = q.x; v[2 * k + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = __ldg(p + k);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Lane-per-species variant for mass-action kinetics (d = 4, 8): a group of d lanes owns
+// one chunk and lane i owns species i, i.e. row i of every d x d matrix of the row being
+// processed (the rate Jacobian G, the stage Jacobian K, the accumulated sum of K, the new
+// A_t and the chunk aggregate P). Values a lane needs from other species travel by
+// shuffles (vectors) or through a small padded shared-memory buffer per group (matrix
+// rows: K of the previous stage, P of the previous row). The work per row is the same as
+// in the thread-per-chunk kernel, but each thread holds about a tenth of the registers,
+// so far more warps are resident to hide latency. The pending (A_t, b_t) of a chunk are
+// stored chunk-major: A at ((c L + t) d + i) d + j, b at (c L + t) d + i.
+// ---------------------------------------------------------------------------
+template <class real, int D, bool RK4, int MODE>
+__global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real> a) {
+  constexpr int GPB = kFusedBlock / D;                  // chunks per block
+  constexpr int E = D * D;
+  // Exchange buffers: row stride D + 16 B and group stride + 16 B, so that the d lanes of a
+  // group storing their rows, and the groups of a warp reading one row each, hit distinct
+  // banks.
+  constexpr int RS = D + 16 / (int)sizeof(real);
+  constexpr int GS = D * RS + 16 / (int)sizeof(real);
+  // B_m[i][:] for all m held in registers (float32), else re-read through L1 per stage
+  constexpr bool BREG = sizeof(real) == 4;
+  __shared__ __align__(16) real sK[GPB][GS];
+  __shared__ __align__(16) real sP[GPB][GS];
+  const int grp = threadIdx.x / D, i = threadIdx.x % D;
+  const unsigned gm = ((1u << D) - 1u) << ((threadIdx.x & 31) & ~(D - 1));
+  const int64_t ac = blockIdx.x * (int64_t)GPB + grp;
+  const bool valid = ac < a.bt.act_chunks;
+  int64_t seq = 0;
+  real mx = real(0), sq = real(0);  // residual statistics in the path's own precision
+  if (valid) {
+    int64_t c, r0;
+    int n;
+    act_chunk(a.bt, ac, seq, c, r0, n);
+    const int L = a.bt.L;
+    const bool first = c == __ldg(a.bt.chunk_first + seq);
+    const real scale = a.damp == DEER_DAMP_SCALE ? real(1) - a.dparam : real(1);
+    const real h = a.dv.dt;
+    const real hw = RK4 ? h / real(6) : h;
+    real* Kx = sK[grp];
+    real* Px = sP[grp];
+    const real* T = a.dv.ma + seq * a.dv.ma_stride;
+    real Lrow[D];
+    ldrow_ro<real, D>(T + i * D, Lrow);
+    const real* Brow = T + E + i * D;  // B_m[i][:] at Brow + m E
+    real Breg[BREG ? D : 1][BREG ? D : 1];
+    if constexpr (BREG) {
+#pragma unroll
+      for (int m = 0; m < D; ++m) ldrow_ro<real, D>(Brow + m * E, Breg[m]);
+    }
+    real prev;
+    if (first) prev = a.s0[seq * D + i];
+    else if (MODE == 0) prev = a.s[(r0 - 1) * D + i];
+    else prev = a.sprev[c * D + i];
+    real dl = MODE == 1 ? a.cin[c * D + i] : real(0);
+    real v = real(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) Px[i * RS + j] = i == j ? real(1) : real(0);
+    __syncwarp(gm);
+    for (int t = 0; t < n; ++t) {
+      const int64_t row = r0 + t;
+      const int64_t pr = (c * L + t);
+      real* Arow = a.Ai + pr * E + i * D;
+      real* bp = a.bi + pr * D + i;
+      real sn = a.s[row * D + i];
+      if constexpr (MODE == 1) {
+        // pending scan step: Delta_t = A_t Delta_{t-1} + b_t, s_t += Delta_t
+        real Ar[D];
+        ldrow_p<real, D>(Arow, Ar);
+        real nd = *bp;
+#pragma unroll
+        for (int j = 0; j < D; ++j) nd += Ar[j] * __shfl_sync(gm, dl, j, D);
+        dl = nd;
+        real x = sn + nd;
+        if (a.reset && !(x <= a.reset_thr && x >= -a.reset_thr)) x = real(0);
+        sn = x;
+        a.s[row * D + i] = sn;
+      }
+      // linearise at the new state of the previous row
+      real st = prev, accg = real(0);
+      real Kacc[D], Kown[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) Kacc[j] = real(0);
+      constexpr int NST = RK4 ? 4 : 1;
+#pragma unroll 1
+      for (int stage = 0; stage < NST; ++stage) {
+        // RK4 tableau: stage derivative weights (1, 2, 2, 1), stage offsets (h/2, h/2, h)
+        const real cK = stage == 0 ? real(0) : (stage == 3 ? h : real(0.5) * h);
+        const real w = (stage == 1 || stage == 2) ? real(2) : real(1);
+        real cj[D], Gr[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          cj[j] = __shfl_sync(gm, st, j, D);
+          Gr[j] = Lrow[j];
+        }
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+          real bm[D];
+          if constexpr (BREG) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) bm[j] = Breg[m][j];
+          } else {
+            ldrow_ro<real, D>(Brow + m * E, bm);
+          }
+#pragma unroll
+          for (int j = 0; j < D; ++j) Gr[j] += cj[m] * bm[j];
+        }
+        real g = real(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) g += (Lrow[j] + Gr[j]) * cj[j];
+        g *= real(0.5);
+        // K_s = G_s (I + cK K_{s-1}), row i; K_{s-1} rows come from the group buffer
+#pragma unroll
+        for (int j = 0; j < D; ++j) Kown[j] = Gr[j];
+        if (stage > 0) {
+#pragma unroll
+          for (int m = 0; m < D; ++m) {
+            real km[D];
+            ldrow_p<real, D>(Kx + m * RS, km);
+            const real gk = cK * Gr[m];
+#pragma unroll
+            for (int j = 0; j < D; ++j) Kown[j] += gk * km[j];
+          }
+        }
+        __syncwarp(gm);
+        strow_p<real, D>(Kx + i * RS, Kown);
+        __syncwarp(gm);
+#pragma unroll
+        for (int j = 0; j < D; ++j) Kacc[j] += w * Kown[j];
+        accg += w * g;
+        const real cs = stage == 2 ? h : real(0.5) * h;
+        st = prev + cs * g;
+      }
+      const real F = prev + hw * accg;
+      const real r = sn - F;
+      const real sabs = rabs(sn);
+      const real sr = rabs(r) / (sabs > real(1) ? sabs : real(1));
+      mx = (sr > mx || sr != sr) ? sr : mx;
+      sq += r * r;
+      real An[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) An[j] = scale * (hw * Kacc[j] + (j == i ? real(1) : real(0)));
+      strow_p<real, D>(Arow, An);
+      *bp = -r;
+      // chunk aggregate for the next scan: v <- A v - r, P <- A P
+      real nv = -r;
+#pragma unroll
+      for (int j = 0; j < D; ++j) nv += An[j] * __shfl_sync(gm, v, j, D);
+      v = nv;
+      if (!first) {
+        real np[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) np[j] = real(0);
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+          real pm[D];
+          ldrow_p<real, D>(Px + m * RS, pm);
+#pragma unroll
+          for (int j = 0; j < D; ++j) np[j] += An[m] * pm[j];
+        }
+        __syncwarp(gm);
+        strow_p<real, D>(Px + i * RS, np);
+        __syncwarp(gm);
+      }
+      prev = sn;
+    }
+    real pf[D];
+    ldrow_p<real, D>(Px + i * RS, pf);
+    strow_p<real, D>(a.aggP + c * (int64_t)E + i * D, pf);
+    a.aggv[c * D + i] = v;
+  }
+  // one accumulator update per chunk: reduce over the group's species first
+#pragma unroll
+  for (int o = D / 2; o > 0; o >>= 1) {
+    const real om = __shfl_xor_sync(0xffffffffu, mx, o, D);
+    mx = (om > mx || om != om) ? om : mx;
+    sq += __shfl_xor_sync(0xffffffffu, sq, o, D);
+  }
+  acc_resid_t(a.acc, seq, valid && i == 0, mx, sq);
 }
 
 // Per active sequence: compose the chunk aggregates in order; record the Delta entering
@@ -239,11 +480,65 @@ __global__ void __launch_bounds__(128) k_dense_fused_carry(FusedArgs<real> a) {
   }
 }
 
+// Lane-per-species carry pass (d = 4, 8): d lanes per sequence, lane i owns row i of every
+// chunk aggregate and entry i of the carried Delta; the other entries arrive by shuffles.
+// The next chunk's aggregate row is loaded before the current one is applied.
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_fused_carry_lps(FusedArgs<real> a) {
+  constexpr int E = D * D;
+  constexpr int GPB = 128 / D;
+  const int grp = threadIdx.x / D, i = threadIdx.x % D;
+  const unsigned gm = ((1u << D) - 1u) << ((threadIdx.x & 31) & ~(D - 1));
+  const int64_t kq = blockIdx.x * (int64_t)GPB + grp;
+  if (kq >= a.bt.n_act) return;  // whole groups
+  const int64_t seq = a.bt.act_seq[kq];
+  const int64_t c0 = a.bt.chunk_first[seq], c1 = a.bt.chunk_first[seq + 1];
+  const int64_t base = a.bt.offsets[seq];
+  real x = real(0);
+  real P[D], v = real(0);
+  if (c0 < c1) {
+    ldrow_p<real, D>(a.aggP + c0 * E + i * D, P);
+    v = a.aggv[c0 * D + i];
+  }
+  for (int64_t c = c0; c < c1; ++c) {
+    real Pc[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) Pc[j] = P[j];
+    const real vc = v;
+    real so = real(0);
+    if (c > c0) so = a.s[(base + ((c - c0) << a.bt.log2L) - 1) * D + i];
+    if (c + 1 < c1) {  // prefetch the next aggregate row
+      ldrow_p<real, D>(a.aggP + (c + 1) * E + i * D, P);
+      v = a.aggv[(c + 1) * D + i];
+    }
+    a.cin[c * D + i] = x;
+    if (c > c0) {
+      real y = so + x;
+      if (a.reset && !(y <= a.reset_thr && y >= -a.reset_thr)) y = real(0);
+      a.sprev[c * D + i] = y;
+    }
+    real nx = vc;
+    if (c > c0) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) nx += Pc[j] * __shfl_sync(gm, x, j, D);
+    }
+    x = nx;
+  }
+}
+
 template <class real, int D, int KIND>
 static void fused_launch(const FusedArgs<real>& a, cudaStream_t st) {
-  const unsigned g = grid_for(a.bt.act_chunks, kFusedBlock);
-  if (a.mode == 0) k_dense_fused<real, D, KIND, 0><<<g, kFusedBlock, 0, st>>>(a);
-  else k_dense_fused<real, D, KIND, 1><<<g, kFusedBlock, 0, st>>>(a);
+  constexpr bool MA = KIND == DEER_F_MASSACTION_EULER || KIND == DEER_F_MASSACTION_RK4;
+  if constexpr (MA && (D == 4 || D == 8)) {
+    constexpr bool RK4 = KIND == DEER_F_MASSACTION_RK4;
+    const unsigned g = grid_for(a.bt.act_chunks, kFusedBlock / D);
+    if (a.mode == 0) k_fused_ma_lps<real, D, RK4, 0><<<g, kFusedBlock, 0, st>>>(a);
+    else k_fused_ma_lps<real, D, RK4, 1><<<g, kFusedBlock, 0, st>>>(a);
+  } else {
+    const unsigned g = grid_for(a.bt.act_chunks, kFusedBlock);
+    if (a.mode == 0) k_dense_fused<real, D, KIND, 0><<<g, kFusedBlock, 0, st>>>(a);
+    else k_dense_fused<real, D, KIND, 1><<<g, kFusedBlock, 0, st>>>(a);
+  }
 }
 
 template <class real, int KIND>
@@ -277,6 +572,15 @@ cudaError_t launch_dense_fused(const FusedArgs<real>& a, cudaStream_t st) {
 template <class real>
 cudaError_t launch_dense_fused_carry(const FusedArgs<real>& a, cudaStream_t st) {
   if (a.bt.n_act == 0) return cudaSuccess;
+  const bool ma = a.dv.kind == DEER_F_MASSACTION_EULER || a.dv.kind == DEER_F_MASSACTION_RK4;
+  if (ma && (a.dv.d == 4 || a.dv.d == 8)) {
+    // same kernels as the fused pass selects (lane-per-species layout of the aggregates is
+    // row-major either way)
+    if (a.dv.d == 4) k_fused_carry_lps<real, 4><<<grid_for(a.bt.n_act, 32), 128, 0, st>>>(a);
+    else k_fused_carry_lps<real, 8><<<grid_for(a.bt.n_act, 16), 128, 0, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
+  }
   const unsigned g = grid_for(a.bt.n_act, 128);
   switch (a.dv.d) {
     case 1: k_dense_fused_carry<real, 1><<<g, 128, 0, st>>>(a); break;

@@ -58,7 +58,7 @@ struct LBShape {
 constexpr unsigned kSpinLimit = 1u << 22;  // bounded wait (about 0.3 s with backoff)
 
 template <class real, int D>
-__global__ void __launch_bounds__(256) k_diag_lb(DiagLBArgs<real> a) {
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 8 : 4) k_diag_lb(DiagLBArgs<real> a) {
   using S = LBShape<D>;
   constexpr int Q = S::Q, G = S::G, RPT = S::RPT;
   __shared__ real sA[Q][D];
@@ -162,45 +162,74 @@ __global__ void __launch_bounds__(256) k_diag_lb(DiagLBArgs<real> a) {
       __threadfence();
       __syncwarp();
       if (lane == 0) st_release(a.flags + c, ep | 1u);
-      // look back over the predecessors of this sequence
-      real XA[(D + 31) / 32], XB[(D + 31) / 32];
+      // look back over the predecessors of this sequence, 32 tiles per round: lane j
+      // reads the status of tile base - j; the run of published tiles nearest to this
+      // one is folded in (their aggregates are fetched together, so a round costs about
+      // two memory latencies however many tiles it folds), and the walk ends at the
+      // nearest tile whose inclusive prefix is published.
+      constexpr int NJ = (D + 31) / 32;
+      real XA[NJ], XB[NJ];
 #pragma unroll
-      for (int j = 0; j < (D + 31) / 32; ++j) { XA[j] = real(1); XB[j] = real(0); }
-      int64_t p = c - 1;
+      for (int j = 0; j < NJ; ++j) { XA[j] = real(1); XB[j] = real(0); }
+      const int64_t cfirst = __ldg(a.bt.chunk_first + seq);
+      int64_t base = c - 1;
       unsigned spins = 0;
       bool timed_out = false;
       while (true) {
-        unsigned f = 0;
-        if (lane == 0) {
-          while (true) {
-            f = ld_acquire(a.flags + p);
-            if ((f >> 2) == a.epoch && (f & 3u) != 0u) break;
-            if (++spins > kSpinLimit) { f = 0; break; }
-            __nanosleep(64);
-          }
+        const int64_t p = base - lane;
+        unsigned f = p >= cfirst ? ld_acquire(a.flags + p) : 0u;
+        const bool ok = (f >> 2) == a.epoch && (f & 3u) != 0u;
+        const unsigned ready = __ballot_sync(0xffffffffu, ok);
+        const unsigned haspre = __ballot_sync(0xffffffffu, ok && (f & 3u) == 2u);
+        const int run = ready == 0xffffffffu ? 32 : __ffs(~ready) - 1;  // ready from lane 0
+        const int kp = haspre ? __ffs(haspre) - 1 : 32;                   // nearest prefix
+        const int nfold = kp < run ? kp : run;  // aggregates to fold this round
+        if (nfold == 0 && kp != 0) {
+          if (++spins > kSpinLimit) { timed_out = true; break; }
+          __nanosleep(64);
+          continue;
         }
-        f = __shfl_sync(0xffffffffu, f, 0);
-        if (f == 0) { timed_out = true; break; }
-        if ((f & 3u) == 2u) {
-          const real* pp = a.pre + p * (int64_t)D;
+        // the statuses above were read by other lanes: order this lane's reads after them
+        __threadfence();
+        // fold the aggregates of tiles base .. base - nfold + 1 (nearest first), four
+        // tiles' loads in flight at a time
+        for (int j0 = 0; j0 < nfold; j0 += 4) {
+          real Ap[4][NJ], Bp[4][NJ];
 #pragma unroll
-          for (int j = 0; j < (D + 31) / 32; ++j) {
+          for (int u = 0; u < 4; ++u) {
+            const real* ap = a.agg + (base - j0 - u) * (int64_t)(2 * D);
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+              const int k = lane + 32 * j;
+              if (j0 + u < nfold && k < D) {
+                Ap[u][j] = __ldcg(ap + 2 * k);
+                Bp[u][j] = __ldcg(ap + 2 * k + 1);
+              } else {
+                Ap[u][j] = real(1);
+                Bp[u][j] = real(0);
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+              XB[j] = XA[j] * Bp[u][j] + XB[j];
+              XA[j] = XA[j] * Ap[u][j];
+            }
+        }
+        if (kp <= run && kp < 32) {
+          // the tile at base - kp has its inclusive prefix: the state entering this tile
+          const real* pp = a.pre + (base - kp) * (int64_t)D;
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) {
             const int k = lane + 32 * j;
             if (k < D) s_in[k] = XA[j] * __ldcg(pp + k) + XB[j];
           }
           break;
         }
-        const real* ap = a.agg + p * (int64_t)(2 * D);
-#pragma unroll
-        for (int j = 0; j < (D + 31) / 32; ++j) {
-          const int k = lane + 32 * j;
-          if (k < D) {
-            const real Ap = __ldcg(ap + 2 * k), Bp = __ldcg(ap + 2 * k + 1);
-            XB[j] = XA[j] * Bp + XB[j];
-            XA[j] = XA[j] * Ap;
-          }
-        }
-        --p;
+        base -= nfold;
+        spins = 0;
       }
       if (timed_out) {
         if (lane == 0) atomicExch(&a.status->timeout, 1);

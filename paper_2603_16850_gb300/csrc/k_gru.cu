@@ -21,7 +21,7 @@ struct GruSmem {
   float CT[kGD][kGT];         // h*r*(1-r) transposed
   float diag_z[kGD], diag_h[kGD];
   float rmx[kGT];
-  double rsq[kGT];
+  float rsq[kGT];
   long long rseq[kGT];
   int rvalid[kGT];
 };
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kGThreads) k_gru_lin_tiled(GruTileArgs a) {
       S.rseq[tid] = seq;
       S.rvalid[tid] = v;
       S.rmx[tid] = 0.f;
-      S.rsq[tid] = 0.0;
+      S.rsq[tid] = 0.f;
     }
     __syncthreads();
     for (int e = tid; e < kGT * (kGD / 4); e += kGThreads) {
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kGThreads) k_gru_lin_tiled(GruTileArgs a) {
       const int rl = 4 * ty + i;
       float bo[4], ao[4];
       float mx = 0.f;
-      double sq = 0.0;
+      float sq = 0.f;
       float4 sc4 = make_float4(0.f, 0.f, 0.f, 0.f);
       if (rv[i]) sc4 = *reinterpret_cast<const float4*>(a.s + rows[i] * kGD + 4 * tx);
       const float sc[4] = {sc4.x, sc4.y, sc4.z, sc4.w};
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kGThreads) k_gru_lin_tiled(GruTileArgs a) {
         const float sa = fabsf(sc[j]);
         const float m = fabsf(res) / (sa > 1.f ? sa : 1.f);
         mx = (m > mx || m != m) ? m : mx;
-        sq += (double)res * (double)res;
+        sq += res * res;
       }
       if (rv[i]) {
         *reinterpret_cast<float4*>(a.b + rows[i] * kGD + 4 * tx) = make_float4(bo[0], bo[1], bo[2], bo[3]);
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kGThreads) k_gru_lin_tiled(GruTileArgs a) {
     }
     __syncthreads();
     if (tid < kGT) {
-      acc_resid(a.acc, S.rseq[tid], S.rvalid[tid] != 0, (double)S.rmx[tid], S.rsq[tid]);
+      acc_resid_f(a.acc, S.rseq[tid], S.rvalid[tid] != 0, S.rmx[tid], S.rsq[tid]);
     }
     __syncthreads();
   }

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(128) k_linearize(LinArgs<real> a) {
   const int64_t ar = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool valid = ar < a.bt.act_rows;
   int64_t seq = 0, row = 0;
-  double mx = 0.0, sq = 0.0;
+  real mx = real(0), sq = real(0);
   if (valid) act_row(a.bt, ar, seq, row);
   if (valid) {
     const int64_t first = __ldg(a.bt.offsets + seq);
@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(128) k_linearize(LinArgs<real> a) {
         real r = sc[i] - F[i];
         b[i] = -r;
         const real sabs = rabs(sc[i]);
-        mx = nanmax(mx, (double)rabs(r) / (double)(sabs > real(1) ? sabs : real(1)));
-        sq += (double)r * (double)r;
+        { const real sr = rabs(r) / (sabs > real(1) ? sabs : real(1)); mx = (sr > mx || sr != sr) ? sr : mx; }
+        sq += r * r;
       }
       store_row<real, D>(a.b + row * D, b);
     } else {
@@ -173,14 +173,14 @@ __global__ void __launch_bounds__(128) k_linearize(LinArgs<real> a) {
         b[i] = F[i] - ai * sp[i];
         real r = sc[i] - F[i];
         const real sabs = rabs(sc[i]);
-        mx = nanmax(mx, (double)rabs(r) / (double)(sabs > real(1) ? sabs : real(1)));
-        sq += (double)r * (double)r;
+        { const real sr = rabs(r) / (sabs > real(1) ? sabs : real(1)); mx = (sr > mx || sr != sr) ? sr : mx; }
+        sq += r * r;
       }
       if constexpr (JAC == DEER_JAC_DIAG) store_row<real, D>(a.A + row * D, ad_);
       store_row<real, D>(a.b + row * D, b);
     }
   }
-  acc_resid(a.acc, seq, valid, mx, sq);
+  acc_resid_t(a.acc, seq, valid, mx, sq);
 }
 
 
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(128) k_lin_ma(LinArgs<real> a) {
   const bool valid = ar < a.bt.act_rows;
   int64_t seq = 0, row = 0;
   if (valid) act_row(a.bt, ar, seq, row);
-  double mx = 0.0, sq = 0.0;
+  real mx = real(0), sq = real(0);
   if (valid) {
     real sp[D], sc[JC];
     if (row == __ldg(a.bt.offsets + seq)) {
@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(128) k_lin_ma(LinArgs<real> a) {
       const real Fi = own_row<real, D, JC>(F, h, ii);
       const real r = sc[ii] - Fi;
       const real sabs = rabs(sc[ii]);
-      mx = nanmax(mx, (double)rabs(r) / (double)(sabs > real(1) ? sabs : real(1)));
-      sq += (double)r * (double)r;
+      { const real sr = rabs(r) / (sabs > real(1) ? sabs : real(1)); mx = (sr > mx || sr != sr) ? sr : mx; }
+      sq += r * r;
       b[ii] = -r;
     }
     if constexpr (JAC == DEER_JAC_FULL) {
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(128) k_lin_ma(LinArgs<real> a) {
     }
     store_row<real, JC>(a.b + row * D + h * JC, b);
   }
-  acc_resid(a.acc, seq, valid, mx, sq);
+  acc_resid_t(a.acc, seq, valid, mx, sq);
 }
 
 // ----------------------------------------------------------------------------
@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
   const bool valid = ar < a.bt.act_rows;
   int64_t seq = 0, row = 0;
   if (valid) act_row(a.bt, ar, seq, row);
-  double mx = 0.0, sq = 0.0;
+  real mx = real(0), sq = real(0);
   // all lanes run the loops (shuffles within a row group stay converged); invalid rows
   // compute on row 0 of sequence 0 and store nothing
   const real s_prev = valid ? (row == __ldg(a.bt.offsets + seq) ? a.s0[seq * D + lane]
@@ -773,9 +773,9 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
     const real sc = a.s[row * D + lane];
     const real rr = sc - F;
     const real sabs = rabs(sc);
-    mx = (double)rabs(rr) / (double)(sabs > real(1) ? sabs : real(1));
+    mx = rabs(rr) / (sabs > real(1) ? sabs : real(1));
     if (rr != rr) mx = rr;  // keep NaN
-    sq = (double)rr * (double)rr;
+    sq = rr * rr;
     const real k = a.dparam;
     if constexpr (JAC == DEER_JAC_FULL) {
       const real scale = a.damp == DEER_DAMP_SCALE ? real(1) - k : real(1);
@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
       a.b[row * D + lane] = F - ai * s_prev;
     }
   }
-  acc_resid(a.acc, seq, valid, mx, sq);
+  acc_resid_t(a.acc, seq, valid, mx, sq);
 }
 
 template <class real, int JAC>

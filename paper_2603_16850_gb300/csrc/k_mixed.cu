@@ -43,14 +43,156 @@ cudaError_t launch_ma_adjacency(int64_t n_seq, int d, int R, const int32_t* topo
   return cudaGetLastError();
 }
 
+// Float32 value of a float64 by truncating its mantissa with integer operations (no FP64
+// pipe, the scarce unit on this GPU). Used only where the float32 value steers the
+// Jacobian, or for a float32 evaluation far from convergence, so rounding toward zero
+// (relative error < 2^-23) is immaterial. Magnitudes below the float32 normal range give
+// zero, above it the largest float32; NaN stays NaN.
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u));
+  const int fe = e - 1023 + 127;
+  if (fe <= 0) return __uint_as_float(sign);
+  if (fe >= 255) return __uint_as_float(sign | 0x7f7fffffu);
+  return __uint_as_float(sign | ((unsigned)fe << 23) | m);
+}
+
+// Stoichiometric change nu in {-2, -1, 1, 2} as a float64 assembled from its bit pattern.
+__device__ __forceinline__ double nu_f64(int nu) {
+  const unsigned m = (unsigned)(nu < 0 ? -nu : nu);
+  const unsigned hi = (nu < 0 ? 0x80000000u : 0u) | (m == 2u ? 0x40000000u : 0x3ff00000u);
+  return __hiloint2double((int)hi, 0);
+}
+
+// Scaled residual above which a sequence's rows are evaluated in float32: the float32
+// rounding error (~1e-7 relative) is then far below the residual being removed. A float32
+// evaluation never reports less than kMixedFloor, so only float64 evaluations can pass the
+// convergence test.
+constexpr double kMixedFastAbove = 1e-4;
+constexpr float kMixedFloor = 1e-6f;
+
+// One row of the mixed linearisation with the dynamics' value path (stage states, reaction
+// rates, slopes, F, residual) in V = float or double; the Jacobian path is float32 either
+// way. Writes E and b for the row and returns its scaled residual and squared residual.
+template <class V, int D, bool RK4, int RPL>
+__device__ __forceinline__ void mixed_row(const MixedLinArgs& a, bool valid, int64_t row,
+                                          int lane, unsigned gm, double s_prev_d,
+                                          const int4 (&q)[RPL], const double (&kd)[RPL],
+                                          const float (&kf)[RPL], int R, const int4* tt,
+                                          const int32_t* ae, int e0, int e1,
+                                          float (*sG)[D + 1], float (*sK)[D], V* sRate,
+                                          float* sD1, float* sD2, float& mx, float& sq) {
+  constexpr bool F64 = sizeof(V) == 8;
+  const V s_prev = F64 ? (V)s_prev_d : (V)d2f_trunc(s_prev_d);
+  const V h = F64 ? (V)a.dv.dt : (V)a.dt_f;
+  const float hf = a.dt_f;
+  V c = s_prev, acc = V(0);
+  float Kacc[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) Kacc[j] = 0.f;
+  const int nst = RK4 ? 4 : 1;
+  for (int stage = 0; stage < nst; ++stage) {
+    // RK4 tableau: stage derivative weights (1, 2, 2, 1), stage offsets (h/2, h/2, h)
+    const float cK = stage == 0 ? 0.f : (stage == 3 ? hf : 0.5f * hf);
+    const V w = (stage == 1 || stage == 2) ? V(2) : V(1);
+    const float cf = F64 ? d2f_trunc((double)c) : (float)c;
+    // every reaction's rate once (reaction r on lane r mod d) and its two partials
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      const int r = k * D + lane;
+      const int j2 = q[k].y < 0 ? 0 : q[k].y;
+      const V c1 = __shfl_sync(gm, c, q[k].x, D);
+      const V c2 = __shfl_sync(gm, c, j2, D);
+      const float c1f = __shfl_sync(gm, cf, q[k].x, D);
+      const float c2f = __shfl_sync(gm, cf, j2, D);
+      if (r < R) {
+        const bool bi = q[k].y >= 0;
+        const V kr = F64 ? (V)kd[k] : (V)kf[k];
+        sRate[r] = bi ? kr * c1 * c2 : kr * c1;
+        sD1[r] = bi ? kf[k] * c2f : kf[k];
+        sD2[r] = kf[k] * c1f;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) sG[lane][j] = 0.f;
+    __syncwarp(gm);
+    // this species' slope and its row of the rate Jacobian, from its own reactions
+    V g = V(0);
+    for (int e = e0; e < e1; ++e) {
+      const int code = __ldg(ae + e);
+      const int r = code & 0xffff;
+      const int nu = (code >> 16) - 4;
+      g += (F64 ? (V)nu_f64(nu) : (V)nu) * sRate[r];
+      const int4 qq = __ldg(tt + r);
+      const float nuf = (float)nu;
+      sG[lane][qq.x] += nuf * sD1[r];
+      if (qq.y >= 0) sG[lane][qq.y] += nuf * sD2[r];
+    }
+    __syncwarp(gm);
+    float Gi[D], Kn[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) Gi[j] = sG[lane][j];
+#pragma unroll
+    for (int j = 0; j < D; ++j) Kn[j] = Gi[j];
+    if (stage > 0) {
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        const float gmv = cK * Gi[m];
+#pragma unroll
+        for (int j = 0; j < D; ++j) Kn[j] += gmv * sK[m][j];
+      }
+    }
+    __syncwarp(gm);
+    const float wf = (stage == 1 || stage == 2) ? 2.f : 1.f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      sK[lane][j] = Kn[j];
+      Kacc[j] += wf * Kn[j];
+    }
+    acc += w * g;
+    const V cs = stage == 2 ? h : V(0.5) * h;
+    c = s_prev + cs * g;
+    __syncwarp(gm);
+  }
+  const V hw = RK4 ? h / V(6) : h;
+  const V F = s_prev + hw * acc;
+  if (valid) {
+    const double sc = a.s[row * D + lane];
+    const float scf = d2f_trunc(sc);
+    float rf;
+    if constexpr (F64) rf = d2f_trunc(sc - (double)F);
+    else rf = scf - (float)F;
+    const float sabs = fabsf(scf);
+    float m = fabsf(rf) / (sabs > 1.f ? sabs : 1.f);
+    if (!F64 && !(m != m)) m = m > kMixedFloor ? m : kMixedFloor;
+    mx = m;
+    sq = rf * rf;
+    const float scale = a.scale_f;
+    const float hwf = RK4 ? hf / 6.f : hf;
+    __nv_bfloat16* Eo = a.E + row * (int64_t)(D * D) + lane * D;
+    // E = A - I with A = I + hw Kacc (scaled by (1 - k) under scale-ELK: E = s A - I)
+#pragma unroll
+    for (int j = 0; j < D; j += 2) {
+      const float x0 = scale * hwf * Kacc[j] + (j == lane ? scale - 1.f : 0.f);
+      const float x1 = scale * hwf * Kacc[j + 1] + (j + 1 == lane ? scale - 1.f : 0.f);
+      *reinterpret_cast<__nv_bfloat162*>(Eo + j) = __floats2bfloat162_rn(x0, x1);
+    }
+    a.b[row * D + lane] = -rf;
+  }
+}
+
 template <int D, bool RK4>
 __global__ void __launch_bounds__(128) k_lin_ma_mixed(MixedLinArgs a) {
   constexpr int GROUPS = 128 / D;
-  constexpr int RMAX = 64;  // reactions per network held in shared memory
+  constexpr int RMAX = 64;         // reactions per network held in shared memory
+  constexpr int RPL = RMAX / D;    // reactions per lane
   __shared__ float sG[GROUPS][D][D + 1];
   __shared__ float sK[GROUPS][D][D];
-  __shared__ double sRate[GROUPS][RMAX];
-  __shared__ float sD1[GROUPS][RMAX], sD2[GROUPS][RMAX];  // d rate / d c_i1, d c_i2 (no k)
+  __shared__ double sRate[GROUPS][RMAX];  // float rates use the first half in float32 mode
+  __shared__ float sD1[GROUPS][RMAX], sD2[GROUPS][RMAX];  // d rate / d c_i1, d c_i2
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gm = gmask_mixed<D>();
   const int64_t ar = blockIdx.x * (int64_t)GROUPS + grp;
@@ -66,90 +208,28 @@ __global__ void __launch_bounds__(128) k_lin_ma_mixed(MixedLinArgs a) {
   const int32_t* ae = a.adj_e + (a.adj_stride ? seq : 0) * a.adj_stride;
   const int e0 = __ldg(aoff + lane), e1 = __ldg(aoff + lane + 1);
   const int R = a.dv.R < RMAX ? a.dv.R : RMAX;
-  const double h = a.dv.dt;
-  double c = s_prev, acc = 0.0;
-  float Kacc[D];
+  int4 q[RPL];
+  double kd[RPL];
+  float kf[RPL];
 #pragma unroll
-  for (int j = 0; j < D; ++j) Kacc[j] = 0.f;
-  const int nst = RK4 ? 4 : 1;
-  for (int stage = 0; stage < nst; ++stage) {
-    const float cK = stage == 0 ? 0.f : (stage == 3 ? (float)h : 0.5f * (float)h);
-    const double w = (stage == 1 || stage == 2) ? 2.0 : 1.0;
-    // every reaction's rate once (lane r % D), in float64, and its two partial derivatives
-    for (int r0 = 0; r0 < R; r0 += D) {
-      const int r = r0 + lane;
-      const int4 q = __ldg(tt + (r < R ? r : 0));
-      const double c1 = __shfl_sync(gm, c, q.x, D);
-      const double c2 = __shfl_sync(gm, c, q.y < 0 ? 0 : q.y, D);
-      if (r < R) {
-        const double kr = __ldg(kk + r);
-        const double f2 = q.y < 0 ? 1.0 : c2;
-        sRate[grp][r] = kr * c1 * f2;
-        sD1[grp][r] = (float)(kr * f2);
-        sD2[grp][r] = (float)(kr * c1);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < D; ++j) sG[grp][lane][j] = 0.f;
-    __syncwarp(gm);
-    // this species' slope and its row of the rate Jacobian, from its own reactions
-    double g = 0.0;
-    for (int e = e0; e < e1; ++e) {
-      const int code = __ldg(ae + e);
-      const int r = code & 0xffff;
-      const int nu = (code >> 16) - 4;
-      g += (double)nu * sRate[grp][r];
-      const int4 q = __ldg(tt + r);
-      sG[grp][lane][q.x] += (float)nu * sD1[grp][r];
-      if (q.y >= 0) sG[grp][lane][q.y] += (float)nu * sD2[grp][r];
-    }
-    __syncwarp(gm);
-    float Gi[D], Kn[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) Gi[j] = sG[grp][lane][j];
-#pragma unroll
-    for (int j = 0; j < D; ++j) Kn[j] = Gi[j];
-    if (stage > 0) {
-#pragma unroll
-      for (int m = 0; m < D; ++m) {
-        const float gmv = cK * Gi[m];
-#pragma unroll
-        for (int j = 0; j < D; ++j) Kn[j] += gmv * sK[grp][m][j];
-      }
-    }
-    __syncwarp(gm);
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      sK[grp][lane][j] = Kn[j];
-      Kacc[j] += (float)w * Kn[j];
-    }
-    acc += w * g;
-    const double cs = stage == 2 ? h : 0.5 * h;
-    c = s_prev + cs * g;
-    __syncwarp(gm);
+  for (int k = 0; k < RPL; ++k) {
+    const int r = k * D + lane;
+    q[k] = __ldg(tt + (r < R ? r : 0));
+    kd[k] = r < R ? __ldg(kk + r) : 0.0;
+    kf[k] = d2f_trunc(kd[k]);
   }
-  const double hw = RK4 ? h / 6.0 : h;
-  const double F = s_prev + hw * acc;
-  double mx = 0.0, sq = 0.0;
-  if (valid) {
-    const double sc = a.s[row * D + lane];
-    const double rr = sc - F;
-    const double sabs = fabs(sc);
-    mx = fabs(rr) / (sabs > 1.0 ? sabs : 1.0);
-    if (rr != rr) mx = rr;
-    sq = rr * rr;
-    const float scale = a.damp == DEER_DAMP_SCALE ? (float)(1.0 - a.dparam) : 1.f;
-    __nv_bfloat16* Eo = a.E + row * (int64_t)(D * D) + lane * D;
-    // E = A - I with A = I + hw Kacc (scaled by (1 - k) under scale-ELK: E = s A - I)
-#pragma unroll
-    for (int j = 0; j < D; j += 2) {
-      const float e0 = scale * (float)hw * Kacc[j] + (j == lane ? scale - 1.f : 0.f);
-      const float e1 = scale * (float)hw * Kacc[j + 1] + (j + 1 == lane ? scale - 1.f : 0.f);
-      *reinterpret_cast<__nv_bfloat162*>(Eo + j) = __floats2bfloat162_rn(e0, e1);
-    }
-    a.b[row * D + lane] = (float)(-rr);
-  }
-  acc_resid(a.acc, seq, valid, mx, sq);
+  const bool fast = !valid || a.it == 0 || a.info[seq].max_resid > kMixedFastAbove;
+  float mx = 0.f, sq = 0.f;
+  if (fast)
+    mixed_row<float, D, RK4, RPL>(a, valid, row, lane, gm, s_prev, q, kd, kf, R, tt, ae, e0,
+                                  e1, sG[grp], sK[grp],
+                                  reinterpret_cast<float*>(sRate[grp]), sD1[grp], sD2[grp],
+                                  mx, sq);
+  else
+    mixed_row<double, D, RK4, RPL>(a, valid, row, lane, gm, s_prev, q, kd, kf, R, tt, ae, e0,
+                                   e1, sG[grp], sK[grp], sRate[grp], sD1[grp], sD2[grp], mx,
+                                   sq);
+  acc_resid_f(a.acc, seq, valid, mx, sq);
 }
 
 // ---- mixed dense scan: lane j owns column j of P and entry j of the vectors ----------
@@ -244,6 +324,128 @@ __global__ void __launch_bounds__(128) k_mixed_apply(MixedScanArgs a) {
   }
 }
 
+// ---- d = 16 on the tensor cores: one warp per chunk --------------------------------
+// The chunk aggregate P <- (I + E_t) P is carried transposed, P^T <- P^T + P^T E_t^T, as
+// one warp-level bf16 MMA pair (m16n8k16, float32 accumulate) per row: the float32
+// accumulator fragment of P^T is exactly the A-operand fragment of the next product once
+// rounded to bf16, and the B operand E_t^T is read straight from the row-major bf16 E_t
+// (lane (g, t) of the warp, g = lane / 4, t = lane % 4, holds E[g][2t..2t+1],
+// E[g][2t+8..2t+9] for columns 0-7 and the same entries of row g + 8 for columns 8-15).
+// The vector part v <- v + E_t v + b_t stays in float32 on the same fragments: lane (g, t)
+// forms the partial dot products of rows g and g + 8 over its four columns, a two-step
+// shuffle sums the four lanes of row g, and each lane then fetches the four entries
+// (2t, 2t+1, 2t+8, 2t+9) it needs for the next row.
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4],
+                                               uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One row of the vector recurrence x <- x + E x + b on the fragments described above.
+// lo / hi: x[g], x[g + 8] (same in the four lanes of row g); q[0..3]: x[2t], x[2t+1],
+// x[2t+8], x[2t+9]. e0..e3: the lane's four words of E (rows g and g + 8).
+__device__ __forceinline__ void frag_matvec16(uint32_t e0, uint32_t e1, uint32_t e2,
+                                              uint32_t e3, float b_lo, float b_hi, float& lo,
+                                              float& hi, float (&q)[4], int t) {
+  float pl = bf_lo(e0) * q[0] + bf_hi(e0) * q[1] + bf_lo(e1) * q[2] + bf_hi(e1) * q[3];
+  float ph = bf_lo(e2) * q[0] + bf_hi(e2) * q[1] + bf_lo(e3) * q[2] + bf_hi(e3) * q[3];
+  pl += __shfl_xor_sync(0xffffffffu, pl, 1);
+  ph += __shfl_xor_sync(0xffffffffu, ph, 1);
+  pl += __shfl_xor_sync(0xffffffffu, pl, 2);
+  ph += __shfl_xor_sync(0xffffffffu, ph, 2);
+  lo = lo + pl + b_lo;
+  hi = hi + ph + b_hi;
+  q[0] = __shfl_sync(0xffffffffu, lo, 8 * t);
+  q[1] = __shfl_sync(0xffffffffu, lo, 8 * t + 4);
+  q[2] = __shfl_sync(0xffffffffu, hi, 8 * t);
+  q[3] = __shfl_sync(0xffffffffu, hi, 8 * t + 4);
+}
+
+__global__ void __launch_bounds__(128) k_mixed_chunk_tc16(MixedScanArgs a) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int64_t ac = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (ac >= a.bt.act_chunks) return;  // whole warps
+  int64_t seq, c, r0;
+  int n;
+  act_chunk(a.bt, ac, seq, c, r0, n);
+  const bool need_P = c != __ldg(a.bt.chunk_first + seq);
+  // P^T = I: fragment entries (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1) of the two tiles
+  float p0[4] = {g == 2 * t ? 1.f : 0.f, g == 2 * t + 1 ? 1.f : 0.f, 0.f, 0.f};
+  float p1[4] = {0.f, 0.f, g == 2 * t ? 1.f : 0.f, g == 2 * t + 1 ? 1.f : 0.f};
+  float lo = 0.f, hi = 0.f, q[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k = 0; k < n; ++k) {
+    const int64_t row = r0 + k;
+    const uint32_t* Ew = reinterpret_cast<const uint32_t*>(a.E + row * 256);
+    const uint32_t e0 = __ldg(Ew + g * 8 + t), e1 = __ldg(Ew + g * 8 + t + 4);
+    const uint32_t e2 = __ldg(Ew + (g + 8) * 8 + t), e3 = __ldg(Ew + (g + 8) * 8 + t + 4);
+    const float b_lo = __ldg(a.b + row * 16 + g), b_hi = __ldg(a.b + row * 16 + g + 8);
+    if (need_P) {
+      const uint32_t A[4] = {pack_bf16x2(p0[0], p0[1]), pack_bf16x2(p0[2], p0[3]),
+                             pack_bf16x2(p1[0], p1[1]), pack_bf16x2(p1[2], p1[3])};
+      mma_bf16_16816(p0, A, e0, e1);
+      mma_bf16_16816(p1, A, e2, e3);
+    }
+    frag_matvec16(e0, e1, e2, e3, b_lo, b_hi, lo, hi, q, t);
+  }
+  // P[i][j] = P^T[j][i]: tile 0 holds P^T[g][2t], P^T[g][2t+1], P^T[g+8][2t], P^T[g+8][2t+1]
+  float* Po = a.aggP + c * 256;
+  Po[(2 * t) * 16 + g] = p0[0];
+  Po[(2 * t + 1) * 16 + g] = p0[1];
+  Po[(2 * t) * 16 + g + 8] = p0[2];
+  Po[(2 * t + 1) * 16 + g + 8] = p0[3];
+  Po[(2 * t + 8) * 16 + g] = p1[0];
+  Po[(2 * t + 9) * 16 + g] = p1[1];
+  Po[(2 * t + 8) * 16 + g + 8] = p1[2];
+  Po[(2 * t + 9) * 16 + g + 8] = p1[3];
+  if (t == 0) {
+    a.aggv[c * 16 + g] = lo;
+    a.aggv[c * 16 + g + 8] = hi;
+  }
+}
+
+// |x| >= 2^60 (about 1.15e18), Inf or NaN, from the exponent bits (no FP64 pipe)
+__device__ __forceinline__ bool overflowed(double x) {
+  return ((((unsigned)__double2hiint(x)) >> 20) & 0x7ffu) >= 1023u + 60u;
+}
+
+__global__ void __launch_bounds__(128) k_mixed_apply_tc16(MixedScanArgs a) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int64_t ac = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (ac >= a.bt.act_chunks) return;  // whole warps
+  int64_t seq, c, r0;
+  int n;
+  act_chunk(a.bt, ac, seq, c, r0, n);
+  const float* ci = a.cin + c * 16;
+  float lo = ci[g], hi = ci[g + 8];
+  float q[4] = {ci[2 * t], ci[2 * t + 1], ci[2 * t + 8], ci[2 * t + 9]};
+  for (int k = 0; k < n; ++k) {
+    const int64_t row = r0 + k;
+    const uint32_t* Ew = reinterpret_cast<const uint32_t*>(a.E + row * 256);
+    const uint32_t e0 = __ldg(Ew + g * 8 + t), e1 = __ldg(Ew + g * 8 + t + 4);
+    const uint32_t e2 = __ldg(Ew + (g + 8) * 8 + t), e3 = __ldg(Ew + (g + 8) * 8 + t + 4);
+    const float b_lo = __ldg(a.b + row * 16 + g), b_hi = __ldg(a.b + row * 16 + g + 8);
+    frag_matvec16(e0, e1, e2, e3, b_lo, b_hi, lo, hi, q, t);
+    // s += Delta in float64; lanes t = 0 (row g) and t = 1 (row g + 8) write
+    if (t < 2) {
+      double* sp = a.s + row * 16 + g + 8 * t;
+      double v = *sp + (double)(t == 0 ? lo : hi);
+      if (a.reset && overflowed(v)) v = 0.0;
+      *sp = v;
+    }
+  }
+}
+
 cudaError_t launch_lin_ma_mixed(const MixedLinArgs& a, cudaStream_t st) {
   if (a.bt.act_rows == 0) return cudaSuccess;
   const bool rk4 = a.dv.kind == DEER_F_MASSACTION_RK4;
@@ -265,11 +467,18 @@ cudaError_t launch_lin_ma_mixed(const MixedLinArgs& a, cudaStream_t st) {
 template <int D>
 static void mixed_launch(const MixedScanArgs& a, cudaStream_t st) {
   constexpr int G = 128 / D;
-  const unsigned gc = grid_for(a.bt.act_chunks, G);
   const unsigned gs = grid_for(a.bt.n_act, G);
-  k_mixed_chunk<D><<<gc, 128, 0, st>>>(a);
-  k_mixed_carry<D><<<gs, 128, 0, st>>>(a);
-  k_mixed_apply<D><<<gc, 128, 0, st>>>(a);
+  if constexpr (D == 16) {
+    const unsigned gw = grid_for(a.bt.act_chunks, 4);  // one warp per chunk
+    k_mixed_chunk_tc16<<<gw, 128, 0, st>>>(a);
+    k_mixed_carry<D><<<gs, 128, 0, st>>>(a);
+    k_mixed_apply_tc16<<<gw, 128, 0, st>>>(a);
+  } else {
+    const unsigned gc = grid_for(a.bt.act_chunks, G);
+    k_mixed_chunk<D><<<gc, 128, 0, st>>>(a);
+    k_mixed_carry<D><<<gs, 128, 0, st>>>(a);
+    k_mixed_apply<D><<<gc, 128, 0, st>>>(a);
+  }
   note_launch(3);
 }
 

@@ -202,11 +202,14 @@ cudaError_t launch_diag_lookback(const DiagLBArgs<real>& a, cudaStream_t st);
 
 namespace deer {
 
-// Fused dense (full-Jacobian) iteration for d <= 8, one thread per chunk of L rows:
+// Fused dense (full-Jacobian) iteration for d <= 8:
 //   mode 0: linearise at the current iterate and reduce every chunk to its aggregate;
 //   mode 1: first apply the pending scan (Delta_t = A_t Delta_{t-1} - r_t from the chunk's
 //           carry, s_t += Delta_t), then linearise at the new iterate in the same pass.
-// A_t and b_t = -r_t live in a chunk-interleaved layout (element e of row t of chunk c at
+// Mass-action kinetics with d = 4, 8 run lane-per-species (d lanes per chunk) and keep
+// A_t, b_t = -r_t chunk-major: A at ((c L + t) d + i) d + j, b at (c L + t) d + i, so a
+// group's d lanes touch d*d contiguous values per row. The other dynamics run one thread
+// per chunk with a chunk-interleaved layout (element e of row t of chunk c at
 // ((c/32 * L + t) * E + e) * 32 + c%32, E = d*d or d) so that the 32 lanes of a warp, which
 // walk 32 chunks in step, touch 128 contiguous bytes per access.
 template <class real>
@@ -215,8 +218,8 @@ struct FusedArgs {
   Batch bt;
   const real* s0;
   real* s;
-  real* Ai;          // interleaved Jacobians
-  real* bi;          // interleaved offsets -r_t
+  real* Ai;          // pending Jacobians (layout above)
+  real* bi;          // pending offsets -r_t
   real* aggP;        // [n_chunks][d][d]
   real* aggv;        // [n_chunks][d]
   real* cin;         // [n_chunks][d]  Delta entering each chunk
@@ -289,8 +292,12 @@ struct MixedLinArgs {
   __nv_bfloat16* E;   // [N][d][d]
   float* b;           // [N][d]  (-r_t)
   SeqAcc* acc;
+  const SeqInfo* info;  // previous check's max scaled residual selects the value path
+  int it;               // iteration (0: no previous residual yet)
   int damp;
   double dparam;
+  float scale_f;        // (1 - k) under scale damping, else 1
+  float dt_f;
 };
 
 struct MixedScanArgs {
