@@ -15,6 +15,57 @@ namespace deer {
 template <class real>
 struct V4 { real x, y, z, w; };
 
+// L2 eviction-priority policies: a and b are read twice (for the tile aggregate, then after
+// the look-back for the output); the first read marks them evict-last so that the second
+// read finds them in L2, and the second read and the stores of s mark their lines
+// evict-first so that streaming data does not push the pending tiles out.
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+template <class real>
+__device__ __forceinline__ V4<real> ld4_hint(const real* p, uint64_t pol) {
+  if constexpr (sizeof(real) == 4) {
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol));
+    return {v.x, v.y, v.z, v.w};
+  } else {
+    double2 u, v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+                 : "=d"(u.x), "=d"(u.y)
+                 : "l"(p), "l"(pol));
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+                 : "=d"(v.x), "=d"(v.y)
+                 : "l"(p + 2), "l"(pol));
+    return {u.x, u.y, v.x, v.y};
+  }
+}
+
+template <class real>
+__device__ __forceinline__ void st4_hint(real* p, const real (&v)[4], uint64_t pol) {
+  if constexpr (sizeof(real) == 4) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(p),
+                 "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "l"(pol)
+                 : "memory");
+  } else {
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1,%2}, %3;" ::"l"(p), "d"(v[0]),
+                 "d"(v[1]), "l"(pol)
+                 : "memory");
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1,%2}, %3;" ::"l"(p + 2),
+                 "d"(v[2]), "d"(v[3]), "l"(pol)
+                 : "memory");
+  }
+}
+
 template <class real>
 __device__ __forceinline__ V4<real> ld4(const real* p) {
   if constexpr (sizeof(real) == 4) {
@@ -57,62 +108,17 @@ struct LBShape {
 
 constexpr unsigned kSpinLimit = 1u << 22;  // bounded wait (about 0.3 s with backoff)
 
+// Tile-level part shared by both variants: the inclusive scan over the row sub-ranges of
+// the tile (per coordinate, Kogge-Stone through shared memory), publication of the tile's
+// aggregate, and the look-back that resolves the state entering the tile into s_in. On
+// return sA[q] / sB[q] hold the composition of sub-ranges 0..q and s_in the incoming state.
 template <class real, int D>
-__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 8 : 4) k_diag_lb(DiagLBArgs<real> a) {
-  using S = LBShape<D>;
-  constexpr int Q = S::Q, G = S::G, RPT = S::RPT;
-  __shared__ real sA[Q][D];
-  __shared__ real sB[Q][D];
-  __shared__ real s_in[D];
-  __shared__ unsigned s_tile;
-  if (threadIdx.x == 0) s_tile = atomicAdd(a.ticket, 1u);
-  __syncthreads();
-  const int64_t tk = s_tile;
-  if (tk >= a.bt.act_chunks) return;  // uniform over the CTA
-  // ticket -> active chunk index: sequence-major, or round-robin over the sequences when
-  // they all have cps chunks (a predecessor tile always holds a smaller ticket either way)
-  const int64_t ac = a.cps > 0 ? (tk % a.bt.n_act) * a.cps + tk / a.bt.n_act : tk;
-  int64_t seq, c, r0;
-  int n;
-  act_chunk(a.bt, ac, seq, c, r0, n);
-  const int g = threadIdx.x % G, q = threadIdx.x / G;
-  const int k0 = 4 * g;
-
-  // this thread's rows (identity elements past the end of a ragged tile); the values are
-  // read twice: here for the aggregate, and after the look-back (from L2) for the output,
-  // which keeps few registers live and many CTAs resident
-  auto load_row = [&](int i, real (&av)[4], real (&bv)[4]) {
-    const int lr = q * RPT + i;
-    if (lr < n) {
-      const int64_t off = (r0 + lr) * D + k0;
-      const V4<real> bb = ld4(a.b + off);
-      bv[0] = bb.x; bv[1] = bb.y; bv[2] = bb.z; bv[3] = bb.w;
-      if (a.amode == 0) {
-        const V4<real> aa = ld4(a.a + off);
-        av[0] = aa.x; av[1] = aa.y; av[2] = aa.z; av[3] = aa.w;
-      } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) av[k] = a.aconst;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) { av[k] = real(1); bv[k] = real(0); }
-    }
-  };
-  // thread aggregate (composition in row order)
-  real A[4], Bv[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) { A[k] = real(1); Bv[k] = real(0); }
-#pragma unroll
-  for (int i = 0; i < RPT; ++i) {
-    real av[4], bv[4];
-    load_row(i, av, bv);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      Bv[k] = av[k] * Bv[k] + bv[k];
-      A[k] = av[k] * A[k];
-    }
-  }
+__device__ __forceinline__ void block_scan_and_lookback(const DiagLBArgs<real>& a,
+                                                        int64_t seq, int64_t c, real (&A)[4],
+                                                        real (&Bv)[4], int q, int k0,
+                                                        real (*sA)[D], real (*sB)[D],
+                                                        real* s_in) {
+  constexpr int Q = LBShape<D>::Q;
 #pragma unroll
   for (int k = 0; k < 4; ++k) { sA[q][k0 + k] = A[k]; sB[q][k0 + k] = Bv[k]; }
   __syncthreads();
@@ -242,6 +248,66 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 8 : 4) k_diag_lb(Diag
     }
   }
   __syncthreads();
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 8 : 4) k_diag_lb(DiagLBArgs<real> a) {
+  using S = LBShape<D>;
+  constexpr int Q = S::Q, G = S::G, RPT = S::RPT;
+  __shared__ real sA[Q][D];
+  __shared__ real sB[Q][D];
+  __shared__ real s_in[D];
+  __shared__ unsigned s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(a.ticket, 1u);
+  __syncthreads();
+  const int64_t tk = s_tile;
+  if (tk >= a.bt.act_chunks) return;  // uniform over the CTA
+  // ticket -> active chunk index: sequence-major, or round-robin over the sequences when
+  // they all have cps chunks (a predecessor tile always holds a smaller ticket either way)
+  const int64_t ac = a.cps > 0 ? (tk % a.bt.n_act) * a.cps + tk / a.bt.n_act : tk;
+  int64_t seq, c, r0;
+  int n;
+  act_chunk(a.bt, ac, seq, c, r0, n);
+  const int g = threadIdx.x % G, q = threadIdx.x / G;
+  const int k0 = 4 * g;
+
+  // this thread's rows (identity elements past the end of a ragged tile); the values are
+  // read twice: here for the aggregate, and after the look-back (from L2) for the output,
+  // which keeps few registers live and many CTAs resident
+  const uint64_t keep = l2_policy_evict_last(), stream = l2_policy_evict_first();
+  auto load_row = [&](int i, real (&av)[4], real (&bv)[4], uint64_t pol) {
+    const int lr = q * RPT + i;
+    if (lr < n) {
+      const int64_t off = (r0 + lr) * D + k0;
+      const V4<real> bb = ld4_hint(a.b + off, pol);
+      bv[0] = bb.x; bv[1] = bb.y; bv[2] = bb.z; bv[3] = bb.w;
+      if (a.amode == 0) {
+        const V4<real> aa = ld4_hint(a.a + off, pol);
+        av[0] = aa.x; av[1] = aa.y; av[2] = aa.z; av[3] = aa.w;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) av[k] = a.aconst;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) { av[k] = real(1); bv[k] = real(0); }
+    }
+  };
+  // thread aggregate (composition in row order)
+  real A[4], Bv[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) { A[k] = real(1); Bv[k] = real(0); }
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    real av[4], bv[4];
+    load_row(i, av, bv, keep);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Bv[k] = av[k] * Bv[k] + bv[k];
+      A[k] = av[k] * A[k];
+    }
+  }
+  block_scan_and_lookback<real, D>(a, seq, c, A, Bv, q, k0, sA, sB, s_in);
 
   // state entering this thread's rows = exclusive prefix applied to the tile's input
   real x[4];
@@ -255,13 +321,13 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 8 : 4) k_diag_lb(Diag
     const int lr = q * RPT + i;
     if (lr < n) {
       real av[4], bv[4], o[4];
-      load_row(i, av, bv);
+      load_row(i, av, bv, stream);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         x[k] = av[k] * x[k] + bv[k];
         o[k] = (a.reset && !(x[k] <= a.reset_thr && x[k] >= -a.reset_thr)) ? real(0) : x[k];
       }
-      st4(a.s + (r0 + lr) * D + k0, o);
+      st4_hint(a.s + (r0 + lr) * D + k0, o, stream);
     }
   }
 }

@@ -221,6 +221,35 @@ def test_ragged_batch_matches_per_sequence_rollouts():
         assert _relerr(sn[off[b]:off[b + 1]], roll) <= 1e-10
 
 
+@pytest.mark.parametrize("d,R,jac,prec", [(8, 12, "diag", "fp32"), (16, 24, "diag", "fp32"),
+                                          (32, 48, "diag", "fp32"), (8, 12, "identity", "fp32"),
+                                          (4, 6, "diag", "fp64"), (64, 96, "diag", "fp64")])
+def test_diag_lookback_ragged(d, R, jac, prec):
+    """Single-pass look-back diagonal scans (tiles of 8192 / d rows, 1024 for d = 4; Picard
+    reads no a) on a ragged batch whose lengths are below, at and above the tile length:
+    every sequence equals its float64 rollout within 1e-5 (float32) or 1e-10 (float64).
+    float32 uses d >= 8: the standard-form diagonal update has a float32 residual floor
+    near 5e-7 on the longer d = 4 sequences, where the float32 test cannot be met."""
+    deer = _deer()
+    L = 8192 // d if d >= 8 else 1024
+    lengths = [L - 1, 1, L + 3, L, 37]
+    off = synth.offsets_from_lengths(lengths)
+    B = len(lengths)
+    p = _ma_problem(B, d, R, 1, seed=21)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    dyn = _ma_dyn(p, dt)
+    extra = FP32 if prec == "fp32" else dict(tol=1e-12, prec="fp64")
+    s, info = deer.deer_solve_batched(dyn, _t(p["s0"], dt), off, jac=jac, init="s0",
+                                      reset=True, max_iters=4000, **extra)
+    assert bool(info.converged.all()), (info.iters.max(), info.max_resid.max())
+    sn = s.cpu().numpy()
+    lim = 1e-5 if prec == "fp32" else 1e-10
+    for b, n in enumerate(lengths):
+        sub = odyn.MassAction(p["topology"][b:b + 1], p["params"][b:b + 1], p["dt"], "rk4", d=d)
+        roll = onewton.rollout(sub, p["s0"][b:b + 1], n)[0]
+        assert _relerr(sn[off[b]:off[b + 1]], roll) <= lim
+
+
 @pytest.mark.parametrize("kind", ["massaction_rk4", "gru", "brusselator"])
 def test_sequential_rollout_parity(kind):
     deer = _deer()
