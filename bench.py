@@ -195,6 +195,19 @@ def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64):
     peaks, _ = _peaks()
     gbs = scan_rows * d * 12 / (scan_ms / 1000.0) / 1e9
     lin_tf = lin_rows * 4 * 2 * d * d / (lin_ms / 1000.0) / 1e12
+    if int(lib.deer_get_tensor_cores()):
+        # three products per row on tcgen05 kind::tf32, each as three split MMAs: the
+        # tensor pipe executes 3x the useful flops; its peak is the measured bf16 peak x the
+        # nominal tf32 / bf16 ratio (1.1 / 2.25 PFLOP/s dense)
+        tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25
+        lin_entry = {"kernel": "k_gru_lin_tc (tcgen05 kind::tf32, 3-term split)",
+                     "avg_launch_ms": lin_ms, "achieved_tflops": lin_tf,
+                     "flop_per_row": 4 * 2 * d * d,
+                     "tensor_pipe_tflops": 3 * lin_tf, "tf32_peak_tflops": tf32_peak,
+                     "tensor_frac": 3 * lin_tf / tf32_peak}
+    else:
+        lin_entry = {"kernel": "k_gru_lin_tiled", "avg_launch_ms": lin_ms,
+                     "achieved_tflops": lin_tf, "flop_per_row": 4 * 2 * d * d}
     return {"workload": f"GRU d=64 d_in=64 T=65536 B={B}, quasi-DEER, FP32, tol 1e-5 x2",
             "value": B * T / (ms / 1000.0), "unit": UNIT, "ms_per_solve": ms,
             "newton_iters_max": int(info.iters.max()), "converged": bool(info.converged.all()),
@@ -202,9 +215,7 @@ def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64):
                           "peak": peaks["hbm_gbs"], "unit": "GB/s",
                           "frac": gbs / peaks["hbm_gbs"], "avg_launch_ms": scan_ms,
                           "avg_rows_per_launch": scan_rows},
-            "linearize": {"kernel": "k_gru_lin_tiled", "avg_launch_ms": lin_ms,
-                          "achieved_tflops": lin_tf,
-                          "flop_per_row": 4 * 2 * d * d}}
+            "linearize": lin_entry}
 
 
 def adjoint_measurement(deer, N, lib, dev, stream):

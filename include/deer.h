@@ -210,6 +210,14 @@ deer_status deer_solve_noalloc(const deer_dynamics* f, int64_t batch, int64_t T,
                                deer_info* info);
 size_t deer_noalloc_scratch_bytes(void);
 
+/* Tensor-core kernels (on by default): where a step of the path has a tensor-core kernel
+   and a SIMT one with the same results up to rounding, the tensor-core one runs when this
+   is on (today: the GRU d = 64 float32 linearisation, whose three products per step run
+   as tcgen05 MMAs split to float32 accuracy). Process-wide, thread-safe; affects calls
+   made after it returns. */
+void deer_set_tensor_cores(int32_t on);
+int32_t deer_get_tensor_cores(void);
+
 /* Number of kernels this library enqueued since load (all entry points, all threads). */
 int64_t deer_kernel_launch_count(void);
 

@@ -132,6 +132,15 @@ def kernel_launch_count() -> int:
     return int(N.load().deer_kernel_launch_count())
 
 
+def set_tensor_cores(on: bool) -> None:
+    """Select the tensor-core kernels where a step has one (deer_set_tensor_cores)."""
+    N.load().deer_set_tensor_cores(1 if on else 0)
+
+
+def tensor_cores() -> bool:
+    return bool(N.load().deer_get_tensor_cores())
+
+
 def deer_workspace_bytes(dyn: Dynamics, batch: int, total_steps: int, **opts) -> int:
     o = _options(**_opt_defaults(opts))
     return int(N.load().deer_workspace_bytes(C.byref(dyn.c_struct()), batch, total_steps,

@@ -76,6 +76,8 @@ SIGNATURES = {
     "deer_noalloc_scratch_bytes": (C.c_size_t, []),
     "deer_kernel_launch_count": (C.c_int64, []),
     "deer_profile_enable": (None, [C.c_int32]),
+    "deer_set_tensor_cores": (None, [C.c_int32]),
+    "deer_get_tensor_cores": (C.c_int32, []),
     "deer_profile_reset": (None, []),
     "deer_profile_read": (None, [C.POINTER(deer_profile)]),
     "deer_status_string": (C.c_char_p, [C.c_int32]),

@@ -18,6 +18,7 @@ void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 // Optional per-phase timing with CUDA events on the solver's stream (deer_profile_*).
 enum { PH_SETUP = 0, PH_LIN = 1, PH_CHECK = 2, PH_SCAN = 3, PH_N = 4 };
 static std::atomic<int> g_prof_on{0};
+static std::atomic<int> g_tensor_cores{1};
 static std::mutex g_prof_mu;
 static deer_profile g_prof{};
 
@@ -320,6 +321,7 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
       gta.A = reinterpret_cast<float*>(ws + ly.A);
       gta.b = reinterpret_cast<float*>(ws + ly.b);
       gta.acc = acc;
+      gta.status = flags;
       gta.jac = o->jac;
       gta.damp = o->damp;
       gta.dparam = (float)o->damp_param;
@@ -505,7 +507,8 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     } else if (gru_tiled) {
       if constexpr (sizeof(real) == 4) {
         gta.bt = bt;
-        DEER_CK(launch_gru_lin_tiled(gta, st));
+        if (g_tensor_cores.load() != 0) DEER_CK(launch_gru_lin_tc(gta, st));
+        else DEER_CK(launch_gru_lin_tiled(gta, st));
       }
     } else if (mixed) {
       if constexpr (sizeof(real) == 8) {
@@ -830,6 +833,8 @@ deer_status deer_grad(const deer_dynamics* f, int64_t batch, int64_t T, const vo
 int64_t deer_kernel_launch_count(void) { return g_launches.load(); }
 
 void deer_profile_enable(int32_t on) { g_prof_on.store(on ? 1 : 0); }
+void deer_set_tensor_cores(int32_t on) { g_tensor_cores.store(on ? 1 : 0); }
+int32_t deer_get_tensor_cores(void) { return g_tensor_cores.load(); }
 
 void deer_profile_reset(void) {
   std::lock_guard<std::mutex> g(g_prof_mu);

@@ -258,6 +258,7 @@ struct GruTileArgs {
   float* A;             // [N][64] diag A~_t (DIAG only)
   float* b;             // [N][64]
   SeqAcc* acc;
+  Flags* status;        // timeout flag of the bounded waits (tensor-core variant)
   int jac, damp;
   float dparam;
 };
@@ -265,6 +266,9 @@ struct GruTileArgs {
 cudaError_t launch_gru_xproj(const float* W, const float* x, int64_t N, float* out,
                              cudaStream_t st);
 cudaError_t launch_gru_lin_tiled(const GruTileArgs& a, cudaStream_t st);
+// the same linearisation with the three products on tcgen05 (kind::tf32, split to float32
+// accuracy); one persistent CTA per SM
+cudaError_t launch_gru_lin_tc(const GruTileArgs& a, cudaStream_t st);
 
 inline bool gru_tiled_supported(int kind, int d, int d_in, int jac, int prec) {
   return kind == DEER_F_GRU && d == 64 && d_in == 64 && jac != DEER_JAC_FULL &&

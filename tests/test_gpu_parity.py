@@ -167,6 +167,36 @@ def test_gru_quasi_deer(d, prec):
         assert _relerr(s.cpu().numpy()[b * T:(b + 1) * T], roll[b]) <= lim
 
 
+@pytest.mark.parametrize("jac", ["diag", "zero"])
+def test_gru_tensor_core_linearisation_matches_simt(jac):
+    """GRU d = 64 float32: the tcgen05 linearisation (three products per step as tf32 MMAs
+    split to float32 accuracy) and the SIMT one give the same iterates up to float32
+    rounding, and both converge to the float64 rollout within 1e-5."""
+    deer = _deer()
+    B, T, d = 3, 1000, 64  # 3000 rows: 23 tiles of 128 and a ragged last tile
+    g = synth.gru(B, T, d, d, seed=5)
+    dyn = deer.Dynamics.gru(_t(g["W"], torch.float32), _t(g["U"], torch.float32))
+    x = _t(g["x"].reshape(-1, d), torch.float32)
+    s0 = _t(g["s0"], torch.float32)
+    out = {}
+    try:
+        for tc in (True, False):
+            deer.set_tensor_cores(tc)
+            s2, _ = deer.deer_solve(dyn, s0, T, x, jac=jac, tol=0.0, max_iters=2,
+                                    init="zeros", prec="fp32")
+            s, info = deer.deer_solve(dyn, s0, T, x, jac=jac, init="zeros", max_iters=T,
+                                      **FP32)
+            assert bool(info.converged.all()), (tc, info.iters.max())
+            out[tc] = (s2.cpu().numpy(), s.cpu().numpy())
+    finally:
+        deer.set_tensor_cores(True)
+    assert _relerr(out[True][0], out[False][0]) <= 2e-6
+    roll = onewton.rollout(odyn.GRU(g["W"], g["U"], g["x"]), g["s0"], T)
+    for tc in (True, False):
+        for b in range(B):
+            assert _relerr(out[tc][1][b * T:(b + 1) * T], roll[b]) <= 1e-5
+
+
 @pytest.mark.parametrize("lam", [0.5, 10.0])
 def test_gru_quasi_elk_iterates(lam):
     """Kalman-filter damped quasi-DEER (quasi-ELK): each iterate equals the oracle's
