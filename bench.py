@@ -14,6 +14,7 @@ no data-path collective; weak scaling); the step time is the max over ranks.
 from __future__ import annotations
 
 import argparse
+import ctypes as C
 import json
 import os
 import statistics
@@ -25,8 +26,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# window: the sliding window of Sec. 3.2 (converged prefixes are frozen), which the thesis
+# recommends for every parallel Newton solve
 WORKLOAD = dict(B=4096, d=8, R=12, T=16384, dt=1e-3, integrator="rk4", tol=5e-7,
-                confirm=2, init="zeros")
+                confirm=2, init="zeros", window=True)
 METRIC = "converged state-steps/sec vs sequential rollout; scan GB/s or TC % of peak"
 UNIT = "state-steps/s"
 CONFIG_NAME = ("batched mass-action networks B=4096 d=8 R=12 RK4 dt=1e-3 T=16384, "
@@ -40,6 +43,10 @@ LIN_FLOP_PER_ROW = 3 * 2 * 8 ** 3 + 300 + 2 * 8 ** 3 + 2 * 8 ** 2 + 2 * 8 ** 2
 # offset read, the new ones written (d^2 + d each way) and the state read and written.
 FUSED_BYTES_PER_ROW = 2 * (8 * 8 + 8) * 4 + 2 * 8 * 4
 FP32_LANES_PER_SM, SMS = 128, 152
+# DRAM bytes per row of the fused iteration kernel from the committed ncu capture of the
+# same kernel (dram__bytes_read.sum + dram__bytes_write.sum over 8.39 M rows at B=512; the
+# traffic per row does not depend on B). Scaled by the rows of an average launch.
+FUSED_TRAFFIC_PER_ROW = (2.699873e9 + 2.674500e9) / 8388608
 # Mixed-precision d=16 mass-action linearise, per row: the RK4 step Jacobian chain in
 # float32 (3 products of 16x16 matrices, 3 * 2 d^3 flop); the float64 rate evaluations are
 # not counted.
@@ -104,6 +111,24 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def _max_over_ranks(value: float, device=None) -> float:
+    """Largest value over the ranks of the job (identity on one rank): the step time every
+    rank reports is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _whole_job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Throughput of the whole job: every rank solves its own batch (replicas, weak
+    scaling) in at most `ms` (the max over ranks)."""
+    return world * units_per_rank / (ms / 1000.0)
 
 
 def _problem(rank: int, batch: int = 0):
@@ -238,13 +263,18 @@ def adjoint_measurement(deer, N, lib, dev, stream):
     ws_ = torch.empty(deer.deer_workspace_bytes(dyn, B, B * T, **opts), dtype=torch.uint8,
                       device=dev)
     s, info = deer.deer_solve(dyn, s0, T, workspace=ws_, stream=stream, **opts)  # warm
+    g = 2.0 * (s - y)
+    gws = torch.empty(int(N.load().deer_grad_workspace_bytes(
+        C.byref(dyn.c_struct()), B, T, C.byref(deer._options(**deer._opt_defaults(
+            dict(prec="fp32")))))), dtype=torch.uint8, device=dev)
+    deer.deer_grad(dyn, s0, T, s, g, prec="fp32", workspace=gws, stream=stream)  # warm
     torch.cuda.synchronize()
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     e0.record(stream)
     s, info = deer.deer_solve(dyn, s0, T, workspace=ws_, stream=stream, **opts)
     e1.record(stream)
     g = 2.0 * (s - y)
-    dk, ds0 = deer.deer_grad(dyn, s0, T, s, g, prec="fp32")
+    dk, ds0 = deer.deer_grad(dyn, s0, T, s, g, prec="fp32", workspace=gws, stream=stream)
     e2.record(stream)
     torch.cuda.synchronize()
     fwd = e0.elapsed_time(e1)
@@ -273,7 +303,8 @@ def ragged_mixed_measurement(deer, N, lib, dev, stream, B=1000):
     k = torch.tensor(p["params"], dtype=torch.float64, device=dev)
     s0 = torch.tensor(p["s0"], dtype=torch.float64, device=dev)
     dyn = deer.Dynamics.massaction(topo, k, d, p["dt"])
-    opts = dict(jac="full", tol=1e-10, prec="mixed_bf16", init="zeros", reset=True)
+    opts = dict(jac="full", tol=1e-10, prec="mixed_bf16", init="zeros", reset=True,
+                window=True)
     ntot = int(off[-1])
     ws_ = torch.empty(deer.deer_workspace_bytes(dyn, B, ntot, **opts), dtype=torch.uint8,
                       device=dev)
@@ -347,7 +378,7 @@ def run(args):
     s0 = torch.tensor(p["s0"], dtype=torch.float32, device=dev)
     dyn = deer.Dynamics.massaction(topo, k, d, w["dt"], w["integrator"])
     opts = dict(jac="full", tol=w["tol"], confirm=w["confirm"], prec="fp32", init=w["init"],
-                reset=True)
+                reset=True, window=w["window"])
     nbytes = deer.deer_workspace_bytes(dyn, B, B * T, **opts)
     workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -384,11 +415,8 @@ def run(args):
     lib.deer_profile_read(prof)
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * B * T / (ms / 1000.0)
+    ms = _max_over_ranks(ms, dev)
+    value = _whole_job_rate(B * T, ws, ms)
 
     # roofline of the dominant kernel: the fused iteration kernel (apply the pending scan
     # step, linearise, form the chunk aggregates) holds almost all device time; the carry
@@ -403,7 +431,8 @@ def run(args):
     alu_ach = lin_rows * LIN_FLOP_PER_ROW / (lin_ms / 1000.0) / 1e12
     hbm_ach = lin_rows * FUSED_BYTES_PER_ROW / (lin_ms / 1000.0) / 1e9
     alu_frac, hbm_frac = alu_ach / alu_peak, hbm_ach / peaks["hbm_gbs"]
-    common = {"kernel": "k_dense_fused<float,8,massaction_rk4>", "traffic": None,
+    common = {"kernel": "k_fused_ma_lps<float,8,RK4>", "traffic": FUSED_TRAFFIC_PER_ROW * lin_rows,
+              "traffic_source": "ncu dram bytes per row (profiles/, B=512) x rows per launch",
               "launches": int(prof.launches[1]), "avg_launch_ms": lin_ms,
               "avg_rows_per_launch": lin_rows,
               "share_of_step": prof.ms[1] / max(sum(prof.ms), 1e-9)}
@@ -468,7 +497,7 @@ def run(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": CONFIG_NAME, "B_per_gpu": B, "T": T, "d": d, "reactions": 12,
                        "tol": w["tol"], "confirm": w["confirm"], "init": w["init"],
-                       "reset": True,
+                       "reset": True, "sliding_window": w["window"],
                        "newton_iters_max": iters[-1],
                        "newton_iters_pct": {q: float(v) for q, v in zip(
                            ("p50", "p90", "p99", "max"),

@@ -134,6 +134,14 @@ typedef struct {
                          test (<= 1 means one). With 2 the returned iterate has had one more
                          Newton step after first passing, which removes the smooth part of
                          the remaining error when the test sits near float32 roundoff. */
+  int32_t window;     /* sliding window (Sec. 3.2; parallel Newton converges from the front,
+                         so a converged prefix can be left alone): 0 = every iteration
+                         covers each sequence whole; 1 = after each test, the whole chunks
+                         before a sequence's first row whose scaled residual exceeds tol
+                         (in any of the last `confirm` + 1 iterates) are frozen and later
+                         iterations solve only from there, starting from the frozen
+                         state. The fixed point is the same; iterates differ from the
+                         unwindowed iteration once rows are frozen. */
 } deer_options;
 
 typedef struct {

@@ -108,7 +108,7 @@ def _dtype(prec: str):
 
 
 def _options(jac, damp, damp_param, tol, max_iters, init, prec, reset, chunk,
-             confirm=1) -> N.deer_options:
+             confirm=1, window=False) -> N.deer_options:
     o = N.deer_options()
     o.max_iters = int(max_iters)
     o.tol = float(tol)
@@ -120,6 +120,7 @@ def _options(jac, damp, damp_param, tol, max_iters, init, prec, reset, chunk,
     o.reset = int(bool(reset))
     o.chunk = int(chunk)
     o.confirm = int(confirm)
+    o.window = int(bool(window))
     return o
 
 
@@ -149,7 +150,7 @@ def deer_workspace_bytes(dyn: Dynamics, batch: int, total_steps: int, **opts) ->
 
 def _opt_defaults(opts):
     base = dict(jac="full", damp="none", damp_param=0.0, tol=1e-10, max_iters=0, init="s0",
-                prec="fp64", reset=False, chunk=0, confirm=1)
+                prec="fp64", reset=False, chunk=0, confirm=1, window=False)
     base.update(opts)
     return base
 
@@ -203,7 +204,8 @@ def deer_solve(dyn: Dynamics, s0: torch.Tensor, T: int, x: Optional[torch.Tensor
 
     Options (see deer_options in include/deer.h): jac ('full'|'diag'|'identity'|'zero'),
     damp ('none'|'elk'|'scale'|'clip'), damp_param, tol, max_iters, init
-    ('zeros'|'s0'|'jacobi'|'user'), prec ('fp64'|'fp32'), reset, chunk, confirm.
+    ('zeros'|'s0'|'jacobi'|'user'), prec ('fp64'|'fp32'|'mixed_bf16'), reset, chunk,
+    confirm, window (sliding window: freeze the converged prefix of each sequence).
     """
     opts = _opt_defaults(opts)
     host = not s0.is_cuda

@@ -36,6 +36,7 @@ class deer_options(C.Structure):
         ("max_iters", C.c_int32), ("tol", C.c_double), ("jac", C.c_int32), ("damp", C.c_int32),
         ("damp_param", C.c_double), ("init", C.c_int32), ("prec", C.c_int32),
         ("reset", C.c_int32), ("chunk", C.c_int32), ("confirm", C.c_int32),
+        ("window", C.c_int32),
     ]
 
 

@@ -1,6 +1,7 @@
 // Host side of the C ABI: argument checks, workspace layout and the Newton loop of
 // Algorithm alg:deer (linearise -> convergence test -> parallel scan, repeated).
 #include <atomic>
+#include <cmath>
 #include <mutex>
 #include <cstdio>
 #include <cstring>
@@ -86,7 +87,8 @@ static bool d_supported(int kind, int d, int jac) {
 
 // Everything the solver carves out of the caller's workspace.
 struct Layout {
-  size_t offsets, chunk_first, act_seq, act_row_off, act_chunk_off, acc, info, flags, ma, gru_M,
+  size_t offsets, chunk_first, win_chunk, act_seq, act_row_off, act_chunk_off, acc, info, flags,
+      ma, gru_M,
       A, b, aggP, aggv, cin, gam, mob, pin, sprev, lb_ticket, lb_flags, lb_agg, lb_pre, xproj,
       adj_off, adj_e, total;
   int64_t n_chunks_max;
@@ -124,6 +126,7 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
   auto take = [&](size_t bytes) { size_t at = p; p = align_up(p + bytes); return at; };
   ly.offsets = take((size_t)(B + 1) * 8);
   ly.chunk_first = take((size_t)(B + 1) * 8);
+  ly.win_chunk = take((size_t)(B + 1) * 8);
   ly.act_seq = take((size_t)(B + 1) * 8);
   ly.act_row_off = take((size_t)(B + 1) * 8);
   ly.act_chunk_off = take((size_t)(B + 1) * 8);
@@ -226,6 +229,7 @@ static deer_status check_common(const deer_dynamics* f, const deer_options* o) {
   if (o->damp == DEER_DAMP_ELK && o->jac == DEER_JAC_FULL) return DEER_ERR_UNSUPPORTED;
   if (o->damp == DEER_DAMP_CLIP && o->jac == DEER_JAC_FULL) return DEER_ERR_INVALID;
   if (o->damp == DEER_DAMP_ELK && !(o->damp_param >= 0.0)) return DEER_ERR_INVALID;
+  if (o->window != 0 && o->window != 1) return DEER_ERR_INVALID;
   if (!f->params) return DEER_ERR_INVALID;
   if (f->kind == DEER_F_MASSACTION_EULER || f->kind == DEER_F_MASSACTION_RK4) {
     if (!f->topology || f->n_reactions <= 0) return DEER_ERR_INVALID;
@@ -293,6 +297,18 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   bt.n_act = B;
   bt.act_rows = N;
   bt.act_chunks = nc;
+  int64_t* d_win = reinterpret_cast<int64_t*>(ws + ly.win_chunk);
+  if (o->window) {
+    // sliding window: every sequence starts solved from its first chunk
+    DEER_CK(cudaMemcpyAsync(d_win, chunk_first.data(), (B + 1) * 8, cudaMemcpyHostToDevice, st));
+    bt.win_chunk = d_win;
+  }
+  // the convergence test in the kernels' precision: the largest value of that type not
+  // above tol, so that a row passes exactly when the float64 test on its value would
+  real tol_r = (real)o->tol;
+  if ((double)tol_r > o->tol) tol_r = std::nextafter(tol_r, real(0));
+  float tol_f = (float)o->tol;
+  if ((double)tol_f > o->tol) tol_f = std::nextafter(tol_f, 0.f);
 
   DynView<real> dv = make_view<real>(f, x_, ws, ly);
   if (ly.n_ma > 0) {
@@ -325,6 +341,7 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
       gta.jac = o->jac;
       gta.damp = o->damp;
       gta.dparam = (float)o->damp_param;
+      gta.tol_f = tol_f;
     }
   }
   if (o->init != DEER_INIT_USER) {
@@ -347,12 +364,16 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   la.jac = o->jac;
   la.damp = o->damp;
   la.dparam = (real)o->damp_param;
+  la.tol = tol_r;
 
   CheckArgs ca{B, d_off, d_cf, acc, info, flags,
                reinterpret_cast<int64_t*>(ws + ly.act_seq),
                reinterpret_cast<int64_t*>(ws + ly.act_row_off),
                reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), o->tol, 0, max_iters, 1,
                o->confirm > 1 ? o->confirm : 1};
+  ca.win_chunk = o->window ? d_win : nullptr;
+  ca.window = o->window;
+  ca.log2L = bt.log2L;
   DEER_CK(launch_check(ca, st));  // every sequence starts active
   ca.compact_only = 0;
 
@@ -423,6 +444,7 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
       mla.dparam = o->damp_param;
       mla.scale_f = o->damp == DEER_DAMP_SCALE ? (float)(1.0 - o->damp_param) : 1.f;
       mla.dt_f = (float)f->dt;
+      mla.tol_f = tol_f;
       msa.bt = bt;
       msa.d = d;
       msa.E = mla.E;
@@ -454,6 +476,7 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     fa.reset = o->reset;
     fa.reset_thr = reset_thr;
     fa.mode = 0;
+    fa.tol = tol_r;
   }
 
   const bool lookback = use_diag_lookback(o, d);
@@ -552,7 +575,9 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
       } else if (lookback) {
         lba.bt = bt;
         lba.epoch += 1;
-        lba.cps = uniform_chunks;
+        // round-robin tile order assumes every sequence has the same chunks to solve,
+        // which a sliding window breaks
+        lba.cps = o->window ? 0 : uniform_chunks;
         DEER_CK(launch_diag_lookback<real>(lba, st));
       } else {
         DEER_CK(launch_diag_scan<real>(gsa, st));
@@ -607,6 +632,7 @@ void deer_default_options(deer_options* o) {
   o->reset = 0;
   o->chunk = 0;
   o->confirm = 1;
+  o->window = 0;
 }
 
 size_t deer_workspace_bytes(const deer_dynamics* f, int64_t batch, int64_t total_steps,

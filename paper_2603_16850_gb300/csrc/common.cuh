@@ -14,6 +14,8 @@ namespace deer {
 struct SeqAcc {                 // reset every iteration
   unsigned long long max_bits;  // bit pattern of max_t ||r_t||_inf (non-negative double)
   double sumsq;                 // sum_t ||r_t||^2
+  unsigned long long badkey;    // max over rows failing the test of ~(row - first row);
+                                // 0 = every evaluated row passed
 };
 
 struct SeqInfo {                // persistent during one solve
@@ -22,7 +24,10 @@ struct SeqInfo {                // persistent during one solve
   double merit;
   double max_resid;
   int32_t passes;               // consecutive iterates that passed the test
-  int32_t pad;
+  int32_t j0;                   // sliding window: first chunk (from the sequence's first)
+                                // still solved; rows before it are frozen
+  int32_t fb_prev;              // first failing row of the previous iterate
+  int32_t fb_prev2;             // ... and of the one before
 };
 
 struct Flags {                  // read back by the host once per iteration
@@ -64,7 +69,14 @@ struct Batch {
   const int64_t* act_row_off;    // [n_act+1] exclusive prefix of their lengths
   const int64_t* act_chunk_off;  // [n_act+1] exclusive prefix of their chunk counts
   int64_t n_act, act_rows, act_chunks;  // sizes for the current launch
+  // sliding window: [B] first chunk still solved per sequence (>= chunk_first); nullptr =
+  // whole sequences. Active rows / chunks of a sequence start at its window.
+  const int64_t* win_chunk = nullptr;
 };
+
+__device__ __forceinline__ int64_t win_first(const Batch& bt, int64_t seq) {
+  return bt.win_chunk ? __ldg(bt.win_chunk + seq) : __ldg(bt.chunk_first + seq);
+}
 
 __device__ __forceinline__ int64_t find_seq(const int64_t* __restrict__ off, int64_t B,
                                             int64_t row) {
@@ -95,7 +107,8 @@ __device__ __forceinline__ void act_row(const Batch& bt, int64_t ar, int64_t& se
                                         int64_t& row) {
   const int64_t k = find_k(bt.act_row_off, bt.n_act, ar);
   seq = __ldg(bt.act_seq + k);
-  row = __ldg(bt.offsets + seq) + (ar - __ldg(bt.act_row_off + k));
+  const int64_t j0 = win_first(bt, seq) - __ldg(bt.chunk_first + seq);
+  row = __ldg(bt.offsets + seq) + (j0 << bt.log2L) + (ar - __ldg(bt.act_row_off + k));
 }
 
 // active chunk index -> (sequence, global chunk index, first row, row count)
@@ -103,8 +116,9 @@ __device__ __forceinline__ void act_chunk(const Batch& bt, int64_t ac, int64_t& 
                                           int64_t& c, int64_t& r0, int32_t& n) {
   const int64_t k = find_k(bt.act_chunk_off, bt.n_act, ac);
   seq = __ldg(bt.act_seq + k);
-  const int64_t j = ac - __ldg(bt.act_chunk_off + k);
-  c = __ldg(bt.chunk_first + seq) + j;
+  const int64_t cf = __ldg(bt.chunk_first + seq);
+  const int64_t j = (win_first(bt, seq) - cf) + (ac - __ldg(bt.act_chunk_off + k));
+  c = cf + j;
   const int64_t s0 = __ldg(bt.offsets + seq), s1 = __ldg(bt.offsets + seq + 1);
   r0 = s0 + (j << bt.log2L);
   const int64_t e = r0 + bt.L;
@@ -140,7 +154,7 @@ __device__ __forceinline__ double nanmax(double a, double b) {
 // Non-negative doubles order like their bit patterns, and NaN sorts above +Inf, so the
 // integer atomicMax both takes the maximum and flags non-finite residuals.
 __device__ __forceinline__ void acc_resid(SeqAcc* acc, int64_t seq, bool valid, double mx,
-                                          double sq) {
+                                          double sq, unsigned long long badkey = 0ull) {
   const unsigned full = 0xffffffffu;
   unsigned vm = __ballot_sync(full, valid);
   if (vm == 0) return;
@@ -148,19 +162,29 @@ __device__ __forceinline__ void acc_resid(SeqAcc* acc, int64_t seq, bool valid, 
   long long sseq = __shfl_sync(full, (long long)seq, src);
   bool uniform = __all_sync(full, (!valid) || (seq == sseq));
   if (uniform) {
-    if (!valid) { mx = 0.0; sq = 0.0; }
+    if (!valid) { mx = 0.0; sq = 0.0; badkey = 0ull; }
     for (int o = 16; o > 0; o >>= 1) {
       mx = nanmax(mx, __shfl_xor_sync(full, mx, o));
       sq += __shfl_xor_sync(full, sq, o);
+      const unsigned long long ok = __shfl_xor_sync(full, badkey, o);
+      badkey = ok > badkey ? ok : badkey;
     }
     if ((threadIdx.x & 31) == 0) {
       atomicMax(&acc[sseq].max_bits, dbits(mx));
       atomicAdd(&acc[sseq].sumsq, sq);
+      if (badkey) atomicMax(&acc[sseq].badkey, badkey);
     }
   } else if (valid) {
     atomicMax(&acc[seq].max_bits, dbits(mx));
     atomicAdd(&acc[seq].sumsq, sq);
+    if (badkey) atomicMax(&acc[seq].badkey, badkey);
   }
+}
+
+// Key of a row for the sliding window: rows failing the test map to ~(row - first row of
+// the sequence), so the largest key over a sequence names its first failing row.
+__device__ __forceinline__ unsigned long long bad_key(bool bad, int64_t rel) {
+  return bad ? ~(unsigned long long)rel : 0ull;
 }
 
 // Float32 statistics variant of acc_resid for the float32 paths: the warp reduction runs
@@ -171,7 +195,7 @@ __device__ __forceinline__ float nanmaxf(float a, float b) {
 }
 
 __device__ __forceinline__ void acc_resid_f(SeqAcc* acc, int64_t seq, bool valid, float mx,
-                                            float sq) {
+                                            float sq, unsigned long long badkey = 0ull) {
   const unsigned full = 0xffffffffu;
   unsigned vm = __ballot_sync(full, valid);
   if (vm == 0) return;
@@ -179,29 +203,33 @@ __device__ __forceinline__ void acc_resid_f(SeqAcc* acc, int64_t seq, bool valid
   long long sseq = __shfl_sync(full, (long long)seq, src);
   bool uniform = __all_sync(full, (!valid) || (seq == sseq));
   if (uniform) {
-    if (!valid) { mx = 0.f; sq = 0.f; }
+    if (!valid) { mx = 0.f; sq = 0.f; badkey = 0ull; }
     for (int o = 16; o > 0; o >>= 1) {
       mx = nanmaxf(mx, __shfl_xor_sync(full, mx, o));
       sq += __shfl_xor_sync(full, sq, o);
+      const unsigned long long ok = __shfl_xor_sync(full, badkey, o);
+      badkey = ok > badkey ? ok : badkey;
     }
     if ((threadIdx.x & 31) == 0) {
       atomicMax(&acc[sseq].max_bits, dbits((double)mx));
       atomicAdd(&acc[sseq].sumsq, (double)sq);
+      if (badkey) atomicMax(&acc[sseq].badkey, badkey);
     }
   } else if (valid) {
     atomicMax(&acc[seq].max_bits, dbits((double)mx));
     atomicAdd(&acc[seq].sumsq, (double)sq);
+    if (badkey) atomicMax(&acc[seq].badkey, badkey);
   }
 }
 
 // Dispatch on the precision of the per-thread statistics.
 __device__ __forceinline__ void acc_resid_t(SeqAcc* acc, int64_t seq, bool valid, float mx,
-                                            float sq) {
-  acc_resid_f(acc, seq, valid, mx, sq);
+                                            float sq, unsigned long long badkey = 0ull) {
+  acc_resid_f(acc, seq, valid, mx, sq, badkey);
 }
 __device__ __forceinline__ void acc_resid_t(SeqAcc* acc, int64_t seq, bool valid, double mx,
-                                            double sq) {
-  acc_resid(acc, seq, valid, mx, sq);
+                                            double sq, unsigned long long badkey = 0ull) {
+  acc_resid(acc, seq, valid, mx, sq, badkey);
 }
 
 // ---------------------------------------------------------------------------

@@ -58,22 +58,27 @@ __global__ void __launch_bounds__(kFusedBlock) k_dense_fused(FusedArgs<real> a) 
   const bool valid = ac < a.bt.act_chunks;
   int64_t seq = 0;
   real mx = real(0), sq = real(0);  // residual statistics in the path's own precision
+  unsigned long long key = 0ull;     // first failing row (sliding window)
   if (valid) {
     int64_t c, r0;
     int n;
     act_chunk(a.bt, ac, seq, c, r0, n);
+    const int64_t base = __ldg(a.bt.offsets + seq);
     const int64_t gi = c >> 5;
     const int lane = (int)(c & 31);
     const int L = a.bt.L;
-    const bool first = c == __ldg(a.bt.chunk_first + seq);
+    // first chunk of the sequence (starts from s_0) / first solved chunk (starts from
+    // Delta = 0; with a sliding window the rows before it are frozen)
+    const bool seq_first = c == __ldg(a.bt.chunk_first + seq);
+    const bool first = c == win_first(a.bt, seq);
     const bool need_P = !first;
     const real k = a.dparam;
     const real scale = a.damp == DEER_DAMP_SCALE ? real(1) - k : real(1);
     real prev[D];
-    if (first) {
+    if (seq_first) {
 #pragma unroll
       for (int i = 0; i < D; ++i) prev[i] = a.s0[seq * D + i];
-    } else if (MODE == 0) {
+    } else if (MODE == 0 || first) {
       ld_vec<real, D>(a.s + (r0 - 1) * D, prev);
     } else {
 #pragma unroll
@@ -128,6 +133,7 @@ __global__ void __launch_bounds__(kFusedBlock) k_dense_fused(FusedArgs<real> a) 
         const real sr = rabs(r[i]) / (sabs > real(1) ? sabs : real(1));
         mx = (sr > mx || sr != sr) ? sr : mx;
         sq += r[i] * r[i];
+        if (!(sr <= a.tol) && key == 0ull) key = bad_key(true, row - base);
       }
 #pragma unroll
       for (int i = 0; i < D; ++i) {
@@ -180,7 +186,7 @@ __global__ void __launch_bounds__(kFusedBlock) k_dense_fused(FusedArgs<real> a) 
       for (int j = 0; j < D; ++j) Po[i * D + j] = sP[i * D + j][tid];
     }
   }
-  acc_resid_t(a.acc, seq, valid, mx, sq);
+  acc_resid_t(a.acc, seq, valid, mx, sq, key);
 }
 
 // Row loads / stores through plain (coherent) accesses, for shared memory and for global
@@ -272,12 +278,17 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
   const bool valid = ac < a.bt.act_chunks;
   int64_t seq = 0;
   real mx = real(0), sq = real(0);  // residual statistics in the path's own precision
+  unsigned long long key = 0ull;     // first failing row (sliding window)
   if (valid) {
     int64_t c, r0;
     int n;
     act_chunk(a.bt, ac, seq, c, r0, n);
+    const int64_t base = __ldg(a.bt.offsets + seq);
     const int L = a.bt.L;
-    const bool first = c == __ldg(a.bt.chunk_first + seq);
+    // first chunk of the sequence (starts from s_0) / first solved chunk (starts from
+    // Delta = 0; with a sliding window the rows before it are frozen)
+    const bool seq_first = c == __ldg(a.bt.chunk_first + seq);
+    const bool first = c == win_first(a.bt, seq);
     const real scale = a.damp == DEER_DAMP_SCALE ? real(1) - a.dparam : real(1);
     const real h = a.dv.dt;
     const real hw = RK4 ? h / real(6) : h;
@@ -293,8 +304,8 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
       for (int m = 0; m < D; ++m) ldrow_ro<real, D>(Brow + m * E, Breg[m]);
     }
     real prev;
-    if (first) prev = a.s0[seq * D + i];
-    else if (MODE == 0) prev = a.s[(r0 - 1) * D + i];
+    if (seq_first) prev = a.s0[seq * D + i];
+    else if (MODE == 0 || first) prev = a.s[(r0 - 1) * D + i];
     else prev = a.sprev[c * D + i];
     real dl = MODE == 1 ? a.cin[c * D + i] : real(0);
     real v = real(0);
@@ -381,6 +392,7 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
       const real sr = rabs(r) / (sabs > real(1) ? sabs : real(1));
       mx = (sr > mx || sr != sr) ? sr : mx;
       sq += r * r;
+      if (!(sr <= a.tol) && key == 0ull) key = bad_key(true, row - base);
       real An[D];
 #pragma unroll
       for (int j = 0; j < D; ++j) An[j] = scale * (hw * Kacc[j] + (j == i ? real(1) : real(0)));
@@ -419,8 +431,10 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
     const real om = __shfl_xor_sync(0xffffffffu, mx, o, D);
     mx = (om > mx || om != om) ? om : mx;
     sq += __shfl_xor_sync(0xffffffffu, sq, o, D);
+    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o, D);
+    key = ok > key ? ok : key;
   }
-  acc_resid_t(a.acc, seq, valid && i == 0, mx, sq);
+  acc_resid_t(a.acc, seq, valid && i == 0, mx, sq, key);
 }
 
 // Per active sequence: compose the chunk aggregates in order; record the Delta entering
@@ -432,7 +446,8 @@ __global__ void __launch_bounds__(128) k_dense_fused_carry(FusedArgs<real> a) {
   const int64_t kq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (kq >= a.bt.n_act) return;
   const int64_t seq = a.bt.act_seq[kq];
-  const int64_t c0 = a.bt.chunk_first[seq], c1 = a.bt.chunk_first[seq + 1];
+  const int64_t cf = a.bt.chunk_first[seq], c0 = win_first(a.bt, seq);
+  const int64_t c1 = a.bt.chunk_first[seq + 1];
   const int64_t base = a.bt.offsets[seq];
   real x[D];
 #pragma unroll
@@ -455,7 +470,7 @@ __global__ void __launch_bounds__(128) k_dense_fused_carry(FusedArgs<real> a) {
 #pragma unroll
     for (int i = 0; i < D; ++i) a.cin[c * D + i] = x[i];
     if (c > c0) {
-      const int64_t r0 = base + ((c - c0) << a.bt.log2L);
+      const int64_t r0 = base + ((c - cf) << a.bt.log2L);
       real so[D];
       ld_vec<real, D>(a.s + (r0 - 1) * D, so);
 #pragma unroll
@@ -492,7 +507,8 @@ __global__ void __launch_bounds__(128) k_fused_carry_lps(FusedArgs<real> a) {
   const int64_t kq = blockIdx.x * (int64_t)GPB + grp;
   if (kq >= a.bt.n_act) return;  // whole groups
   const int64_t seq = a.bt.act_seq[kq];
-  const int64_t c0 = a.bt.chunk_first[seq], c1 = a.bt.chunk_first[seq + 1];
+  const int64_t cf = a.bt.chunk_first[seq], c0 = win_first(a.bt, seq);
+  const int64_t c1 = a.bt.chunk_first[seq + 1];
   const int64_t base = a.bt.offsets[seq];
   real x = real(0);
   real P[D], v = real(0);
@@ -506,7 +522,7 @@ __global__ void __launch_bounds__(128) k_fused_carry_lps(FusedArgs<real> a) {
     for (int j = 0; j < D; ++j) Pc[j] = P[j];
     const real vc = v;
     real so = real(0);
-    if (c > c0) so = a.s[(base + ((c - c0) << a.bt.log2L) - 1) * D + i];
+    if (c > c0) so = a.s[(base + ((c - cf) << a.bt.log2L) - 1) * D + i];
     if (c + 1 < c1) {  // prefetch the next aggregate row
       ldrow_p<real, D>(a.aggP + (c + 1) * E + i * D, P);
       v = a.aggv[(c + 1) * D + i];

@@ -147,13 +147,18 @@ __device__ __forceinline__ void block_scan_and_lookback(const DiagLBArgs<real>& 
   // publish the tile aggregate and resolve the incoming state (first warp)
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    const bool first = c == __ldg(a.bt.chunk_first + seq);
+    // the first solved tile starts from s_0 or, under a sliding window, from the frozen
+    // state of the row before it
+    const int64_t cf = __ldg(a.bt.chunk_first + seq);
+    const bool first = c == win_first(a.bt, seq);
     const unsigned ep = a.epoch << 2;
     real* agg = a.agg + c * (int64_t)(2 * D);
     real* pre = a.pre + c * (int64_t)D;
     if (first) {
+      const real* sp = c == cf ? a.s0 + seq * D
+                               : a.s + (__ldg(a.bt.offsets + seq) + ((c - cf) << a.bt.log2L) - 1) * D;
       for (int k = lane; k < D; k += 32) {
-        const real sin = a.s0[seq * D + k];
+        const real sin = sp[k];
         s_in[k] = sin;
         __stcg(pre + k, sA[Q - 1][k] * sin + sB[Q - 1][k]);
       }
@@ -177,7 +182,7 @@ __device__ __forceinline__ void block_scan_and_lookback(const DiagLBArgs<real>& 
       real XA[NJ], XB[NJ];
 #pragma unroll
       for (int j = 0; j < NJ; ++j) { XA[j] = real(1); XB[j] = real(0); }
-      const int64_t cfirst = __ldg(a.bt.chunk_first + seq);
+      const int64_t cfirst = win_first(a.bt, seq);
       int64_t base = c - 1;
       unsigned spins = 0;
       bool timed_out = false;

@@ -220,7 +220,15 @@ __global__ void __launch_bounds__(kGThreads) k_gru_lin_tiled(GruTileArgs a) {
     }
     __syncthreads();
     if (tid < kGT) {
-      acc_resid_f(a.acc, S.rseq[tid], S.rvalid[tid] != 0, S.rmx[tid], S.rsq[tid]);
+      const int64_t sq_ = S.rseq[tid];
+      int64_t rrow = 0;
+      if (S.rvalid[tid]) {
+        int64_t sq2;
+        act_row(a.bt, tile * kGT + tid, sq2, rrow);
+        rrow -= __ldg(a.bt.offsets + sq_);
+      }
+      acc_resid_f(a.acc, sq_, S.rvalid[tid] != 0, S.rmx[tid], S.rsq[tid],
+                  bad_key(!(S.rmx[tid] <= a.tol_f), rrow));
     }
     __syncthreads();
   }

@@ -272,6 +272,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_gru_lin_tc(GruTileArgs a) {
                      make_float4(r[j] * h[j], r[j + 1] * h[j + 1], r[j + 2] * h[j + 2],
                                  r[j + 3] * h[j + 3]));
     }
+    // the epilogue's row inputs, loaded now so that they arrive while the products run
+    float xz[kCols], xh[kCols], sc[kCols];
+#pragma unroll
+    for (int j = 0; j < kCols; j += 4) {
+      float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f), b4 = a4, c4 = a4;
+      if (v) {
+        a4 = ldg4(xp + c0 + j);
+        b4 = ldg4(xp + 2 * kD + c0 + j);
+        c4 = *reinterpret_cast<const float4*>(a.s + row * kD + c0 + j);
+      }
+      xz[j] = a4.x; xz[j + 1] = a4.y; xz[j + 2] = a4.z; xz[j + 3] = a4.w;
+      xh[j] = b4.x; xh[j + 1] = b4.y; xh[j + 2] = b4.z; xh[j + 3] = b4.w;
+      sc[j] = c4.x; sc[j + 1] = c4.y; sc[j + 2] = c4.z; sc[j + 3] = c4.w;
+    }
     if (!(ok = run_stage(2))) break;
     // stage 3: h o r o (1 - r)
 #pragma unroll
@@ -294,18 +308,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gru_lin_tc(GruTileArgs a) {
 #pragma unroll
         for (int jj = 0; jj < 8; jj += 4) {
           const int j = hh + jj, k = c0 + j;
-          const float4 xz4 = ldg4(xp + k), xh4 = ldg4(xp + 2 * kD + k);
-          const float4 s4 = *reinterpret_cast<const float4*>(a.s + row * kD + k);
-          const float xz[4] = {xz4.x, xz4.y, xz4.z, xz4.w};
-          const float xh[4] = {xh4.x, xh4.y, xh4.z, xh4.w};
-          const float sc[4] = {s4.x, s4.y, s4.z, s4.w};
           float bo[4], ao[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int o = k + e;
-            const float zi = fsig(zp[jj + e] + xz[e]);
+            const float zi = fsig(zp[jj + e] + xz[j + e]);
             const float ri = r[j + e];
-            const float ht = tanhf(hq[jj + e] + xh[e]);
+            const float ht = tanhf(hq[jj + e] + xh[j + e]);
             const float hv = h[j + e];
             const float F = (1.f - zi) * hv + zi * ht;
             float ai;
@@ -319,8 +328,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gru_lin_tc(GruTileArgs a) {
             else if (a.damp == DEER_DAMP_CLIP) ai = fminf(fmaxf(ai, -kk), kk);
             ao[e] = ai;
             bo[e] = F - ai * hv;
-            const float res = sc[e] - F;
-            const float sa = fabsf(sc[e]);
+            const float res = sc[j + e] - F;
+            const float sa = fabsf(sc[j + e]);
             const float m = fabsf(res) / (sa > 1.f ? sa : 1.f);
             mx = (m > mx || m != m) ? m : mx;
             sq += res * res;
@@ -340,7 +349,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gru_lin_tc(GruTileArgs a) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (qc == 0) acc_resid_f(a.acc, seq, v, rmx[rl], rsq[rl]);
+    if (qc == 0)
+      acc_resid_f(a.acc, seq, v, rmx[rl], rsq[rl],
+                  bad_key(!(rmx[rl] <= a.tol_f), row - (v ? __ldg(a.bt.offsets + seq) : 0)));
   }
   if (!ok) {
     if (tid == 0) atomicExch(&a.status->timeout, 1);

@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(128) k_linearize(LinArgs<real> a) {
   const bool valid = ar < a.bt.act_rows;
   int64_t seq = 0, row = 0;
   real mx = real(0), sq = real(0);
+  unsigned long long key = 0ull;  // first failing row (sliding window)
   if (valid) act_row(a.bt, ar, seq, row);
   if (valid) {
     const int64_t first = __ldg(a.bt.offsets + seq);
@@ -149,7 +150,9 @@ __global__ void __launch_bounds__(128) k_linearize(LinArgs<real> a) {
         real r = sc[i] - F[i];
         b[i] = -r;
         const real sabs = rabs(sc[i]);
-        { const real sr = rabs(r) / (sabs > real(1) ? sabs : real(1)); mx = (sr > mx || sr != sr) ? sr : mx; }
+        const real sr = rabs(r) / (sabs > real(1) ? sabs : real(1));
+        mx = (sr > mx || sr != sr) ? sr : mx;
+        if (!(sr <= a.tol)) key = bad_key(true, row - __ldg(a.bt.offsets + seq));
         sq += r * r;
       }
       store_row<real, D>(a.b + row * D, b);
@@ -173,14 +176,16 @@ __global__ void __launch_bounds__(128) k_linearize(LinArgs<real> a) {
         b[i] = F[i] - ai * sp[i];
         real r = sc[i] - F[i];
         const real sabs = rabs(sc[i]);
-        { const real sr = rabs(r) / (sabs > real(1) ? sabs : real(1)); mx = (sr > mx || sr != sr) ? sr : mx; }
+        const real sr = rabs(r) / (sabs > real(1) ? sabs : real(1));
+        mx = (sr > mx || sr != sr) ? sr : mx;
+        if (!(sr <= a.tol)) key = bad_key(true, row - __ldg(a.bt.offsets + seq));
         sq += r * r;
       }
       if constexpr (JAC == DEER_JAC_DIAG) store_row<real, D>(a.A + row * D, ad_);
       store_row<real, D>(a.b + row * D, b);
     }
   }
-  acc_resid_t(a.acc, seq, valid, mx, sq);
+  acc_resid_t(a.acc, seq, valid, mx, sq, key);
 }
 
 
@@ -199,6 +204,7 @@ __global__ void __launch_bounds__(128) k_lin_ma(LinArgs<real> a) {
   int64_t seq = 0, row = 0;
   if (valid) act_row(a.bt, ar, seq, row);
   real mx = real(0), sq = real(0);
+  unsigned long long key = 0ull;  // first failing row (sliding window)
   if (valid) {
     real sp[D], sc[JC];
     if (row == __ldg(a.bt.offsets + seq)) {
@@ -218,7 +224,9 @@ __global__ void __launch_bounds__(128) k_lin_ma(LinArgs<real> a) {
       const real Fi = own_row<real, D, JC>(F, h, ii);
       const real r = sc[ii] - Fi;
       const real sabs = rabs(sc[ii]);
-      { const real sr = rabs(r) / (sabs > real(1) ? sabs : real(1)); mx = (sr > mx || sr != sr) ? sr : mx; }
+      const real sr = rabs(r) / (sabs > real(1) ? sabs : real(1));
+      mx = (sr > mx || sr != sr) ? sr : mx;
+      if (!(sr <= a.tol)) key = bad_key(true, row - __ldg(a.bt.offsets + seq));
       sq += r * r;
       b[ii] = -r;
     }
@@ -256,7 +264,7 @@ __global__ void __launch_bounds__(128) k_lin_ma(LinArgs<real> a) {
     }
     store_row<real, JC>(a.b + row * D + h * JC, b);
   }
-  acc_resid_t(a.acc, seq, valid, mx, sq);
+  acc_resid_t(a.acc, seq, valid, mx, sq, key);
 }
 
 // ----------------------------------------------------------------------------
@@ -704,6 +712,7 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
   int64_t seq = 0, row = 0;
   if (valid) act_row(a.bt, ar, seq, row);
   real mx = real(0), sq = real(0);
+  unsigned long long key = 0ull;  // first failing row (sliding window)
   // all lanes run the loops (shuffles within a row group stay converged); invalid rows
   // compute on row 0 of sequence 0 and store nothing
   const real s_prev = valid ? (row == __ldg(a.bt.offsets + seq) ? a.s0[seq * D + lane]
@@ -776,6 +785,7 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
     mx = rabs(rr) / (sabs > real(1) ? sabs : real(1));
     if (rr != rr) mx = rr;  // keep NaN
     sq = rr * rr;
+    if (!(mx <= a.tol)) key = bad_key(true, row - __ldg(a.bt.offsets + seq));
     const real k = a.dparam;
     if constexpr (JAC == DEER_JAC_FULL) {
       const real scale = a.damp == DEER_DAMP_SCALE ? real(1) - k : real(1);
@@ -801,7 +811,7 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
       a.b[row * D + lane] = F - ai * s_prev;
     }
   }
-  acc_resid_t(a.acc, seq, valid, mx, sq);
+  acc_resid_t(a.acc, seq, valid, mx, sq, key);
 }
 
 template <class real, int JAC>

@@ -84,7 +84,8 @@ __device__ __forceinline__ void mixed_row(const MixedLinArgs& a, bool valid, int
                                           const float (&kf)[RPL], int R, const int4* tt,
                                           const int32_t* ae, int e0, int e1,
                                           float (*sG)[D + 1], float (*sK)[D], V* sRate,
-                                          float* sD1, float* sD2, float& mx, float& sq) {
+                                          float* sD1, float* sD2, float& mx, float& sq,
+                                          int64_t seq, unsigned long long& key) {
   constexpr bool F64 = sizeof(V) == 8;
   const V s_prev = F64 ? (V)s_prev_d : (V)d2f_trunc(s_prev_d);
   const V h = F64 ? (V)a.dv.dt : (V)a.dt_f;
@@ -170,6 +171,7 @@ __device__ __forceinline__ void mixed_row(const MixedLinArgs& a, bool valid, int
     if (!F64 && !(m != m)) m = m > kMixedFloor ? m : kMixedFloor;
     mx = m;
     sq = rf * rf;
+    if (!(m <= a.tol_f)) key = bad_key(true, row - __ldg(a.bt.offsets + seq));
     const float scale = a.scale_f;
     const float hwf = RK4 ? hf / 6.f : hf;
     __nv_bfloat16* Eo = a.E + row * (int64_t)(D * D) + lane * D;
@@ -220,16 +222,17 @@ __global__ void __launch_bounds__(128) k_lin_ma_mixed(MixedLinArgs a) {
   }
   const bool fast = !valid || a.it == 0 || a.info[seq].max_resid > kMixedFastAbove;
   float mx = 0.f, sq = 0.f;
+  unsigned long long key = 0ull;  // first failing row (sliding window)
   if (fast)
     mixed_row<float, D, RK4, RPL>(a, valid, row, lane, gm, s_prev, q, kd, kf, R, tt, ae, e0,
                                   e1, sG[grp], sK[grp],
                                   reinterpret_cast<float*>(sRate[grp]), sD1[grp], sD2[grp],
-                                  mx, sq);
+                                  mx, sq, seq, key);
   else
     mixed_row<double, D, RK4, RPL>(a, valid, row, lane, gm, s_prev, q, kd, kf, R, tt, ae, e0,
                                    e1, sG[grp], sK[grp], sRate[grp], sD1[grp], sD2[grp], mx,
-                                   sq);
-  acc_resid_f(a.acc, seq, valid, mx, sq);
+                                   sq, seq, key);
+  acc_resid_f(a.acc, seq, valid, mx, sq, key);
 }
 
 // ---- mixed dense scan: lane j owns column j of P and entry j of the vectors ----------
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(128) k_mixed_chunk(MixedScanArgs a) {
   int64_t seq = 0, c = 0, r0 = 0;
   int n = 0;
   if (valid) act_chunk(a.bt, ac, seq, c, r0, n);
-  const bool need_P = valid && c != __ldg(a.bt.chunk_first + seq);
+  const bool need_P = valid && c != win_first(a.bt, seq);
   float Pc[D];
   float v = 0.f;
 #pragma unroll
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(128) k_mixed_carry(MixedScanArgs a) {
   const int64_t kq = blockIdx.x * (int64_t)G + grp;
   const bool valid = kq < a.bt.n_act;
   const int64_t seq = valid ? a.bt.act_seq[kq] : 0;
-  const int64_t c0 = valid ? a.bt.chunk_first[seq] : 0;
+  const int64_t c0 = valid ? win_first(a.bt, seq) : 0;
   const int64_t c1 = valid ? a.bt.chunk_first[seq + 1] : 0;
   float x = 0.f;
   for (int64_t c = c0; c < c1; ++c) {
@@ -379,7 +382,7 @@ __global__ void __launch_bounds__(128) k_mixed_chunk_tc16(MixedScanArgs a) {
   int64_t seq, c, r0;
   int n;
   act_chunk(a.bt, ac, seq, c, r0, n);
-  const bool need_P = c != __ldg(a.bt.chunk_first + seq);
+  const bool need_P = c != win_first(a.bt, seq);
   // P^T = I: fragment entries (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1) of the two tiles
   float p0[4] = {g == 2 * t ? 1.f : 0.f, g == 2 * t + 1 ? 1.f : 0.f, 0.f, 0.f};
   float p1[4] = {0.f, 0.f, g == 2 * t ? 1.f : 0.f, g == 2 * t + 1 ? 1.f : 0.f};

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(1024) k_check(CheckArgs a) {
     SeqInfo inf = a.info[seq];
     if (!inf.done && !a.compact_only) {
       SeqAcc acc = a.acc[seq];
-      a.acc[seq] = SeqAcc{0ull, 0.0};
+      a.acc[seq] = SeqAcc{0ull, 0.0, 0ull};
       const double mr = __longlong_as_double((long long)acc.max_bits);
       inf.max_resid = mr;
       inf.merit = 0.5 * acc.sumsq;
@@ -70,26 +70,44 @@ __global__ void __launch_bounds__(1024) k_check(CheckArgs a) {
         inf.iters = a.it;
       } else {
         inf.iters = a.it < a.max_iters ? a.it + 1 : a.it;
+        if (a.window) {
+          // rows that passed in one more consecutive iterate than the convergence test asks
+          // for (so every frozen row has had one further Newton step after it first
+          // qualified) are frozen, in whole chunks
+          const int64_t len = a.offsets[seq + 1] - a.offsets[seq];
+          const int64_t nch = a.chunk_first[seq + 1] - a.chunk_first[seq];
+          const int64_t fb = acc.badkey ? (int64_t)(~acc.badkey) : len;
+          int64_t fbw = fb < inf.fb_prev ? fb : (int64_t)inf.fb_prev;
+          if (a.confirm >= 2 && inf.fb_prev2 < fbw) fbw = inf.fb_prev2;
+          inf.fb_prev2 = inf.fb_prev;
+          inf.fb_prev = (int32_t)fb;
+          int64_t j0 = fbw >> a.log2L;
+          if (j0 < inf.j0) j0 = inf.j0;
+          if (j0 > nch - 1) j0 = nch - 1 > 0 ? nch - 1 : 0;
+          inf.j0 = (int32_t)j0;
+          a.win_chunk[seq] = a.chunk_first[seq] + j0;
+        }
       }
       a.info[seq] = inf;
     }
     if (!inf.done) {
       ++n_act;
-      rows += a.offsets[seq + 1] - a.offsets[seq];
-      chunks += a.chunk_first[seq + 1] - a.chunk_first[seq];
+      rows += a.offsets[seq + 1] - a.offsets[seq] - ((int64_t)inf.j0 << a.log2L);
+      chunks += a.chunk_first[seq + 1] - a.chunk_first[seq] - inf.j0;
     }
   }
   long long tn, tr, tc;
   long long pn = n_act, pr = rows, pc = chunks;
   block_excl_scan3(pn, pr, pc, tn, tr, tc);
   for (int64_t seq = lo; seq < hi; ++seq) {
-    if (a.info[seq].done) continue;
+    const SeqInfo inf = a.info[seq];
+    if (inf.done) continue;
     a.act_seq[pn] = seq;
     a.act_row_off[pn] = pr;
     a.act_chunk_off[pn] = pc;
     ++pn;
-    pr += a.offsets[seq + 1] - a.offsets[seq];
-    pc += a.chunk_first[seq + 1] - a.chunk_first[seq];
+    pr += a.offsets[seq + 1] - a.offsets[seq] - ((int64_t)inf.j0 << a.log2L);
+    pc += a.chunk_first[seq + 1] - a.chunk_first[seq] - inf.j0;
   }
   __shared__ int s_nonfinite;
   if (threadIdx.x == 0) s_nonfinite = 0;
@@ -131,8 +149,9 @@ __global__ void __launch_bounds__(128) k_dense_chunk(DenseScanArgs<real> a) {
   int64_t seq, c, r0;
   int n;
   act_chunk(a.bt, ac, seq, c, r0, n);
-  // the first chunk of a sequence starts from Delta_0 = 0: its carry never multiplies P
-  const bool need_P = c != __ldg(a.bt.chunk_first + seq);
+  // the first solved chunk of a sequence starts from Delta = 0: its carry never
+  // multiplies P (the rows before it are the initial state or frozen)
+  const bool need_P = c != win_first(a.bt, seq);
   real P[D][D], v[D];
 #pragma unroll U<D>::n
   for (int i = 0; i < D; ++i) {
@@ -185,7 +204,7 @@ __global__ void __launch_bounds__(128) k_dense_carry(DenseScanArgs<real> a) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= a.bt.n_act) return;
   const int64_t seq = a.bt.act_seq[k];
-  const int64_t c0 = a.bt.chunk_first[seq], c1 = a.bt.chunk_first[seq + 1];
+  const int64_t c0 = win_first(a.bt, seq), c1 = a.bt.chunk_first[seq + 1];
   real x[D];
 #pragma unroll U<D>::n
   for (int i = 0; i < D; ++i) x[i] = real(0);
@@ -317,8 +336,10 @@ __global__ void __launch_bounds__(128) k_diag_carry(DiagScanArgs<real> a) {
   const int64_t k = id / a.d;
   const int j = (int)(id - k * a.d);
   const int64_t seq = a.bt.act_seq[k];
-  real x = a.s0[seq * a.d + j];
-  const int64_t c0 = a.bt.chunk_first[seq], c1 = a.bt.chunk_first[seq + 1];
+  const int64_t cf = a.bt.chunk_first[seq], c0 = win_first(a.bt, seq);
+  const int64_t c1 = a.bt.chunk_first[seq + 1];
+  real x = c0 == cf ? a.s0[seq * a.d + j]
+                   : a.s[(a.bt.offsets[seq] + ((c0 - cf) << a.bt.log2L) - 1) * a.d + j];
   for (int64_t c = c0; c < c1; ++c) {
     a.cin[c * a.d + j] = x;
     x = a.aggA[c * a.d + j] * x + a.aggB[c * a.d + j];
@@ -387,8 +408,8 @@ __global__ void __launch_bounds__(128) k_elk_carry(DiagScanArgs<real> a) {
   const int64_t k = id / a.d;
   const int j = (int)(id - k * a.d);
   const int64_t seq = a.bt.act_seq[k];
-  real P = real(0);  // s_0 is known exactly
-  const int64_t c0 = a.bt.chunk_first[seq], c1 = a.bt.chunk_first[seq + 1];
+  real P = real(0);  // the state before the first solved row (s_0 or frozen) is known exactly
+  const int64_t c0 = win_first(a.bt, seq), c1 = a.bt.chunk_first[seq + 1];
   for (int64_t c = c0; c < c1; ++c) {
     a.pin[c * a.d + j] = P;
     const real* m = a.mob + (c * a.d + j) * 4;
@@ -634,7 +655,7 @@ __global__ void __launch_bounds__(128) k_dense_chunk_wide(DenseScanArgs<real> a)
   int64_t seq = 0, c = 0, r0 = 0;
   int n = 0;
   if (valid) act_chunk(a.bt, ac, seq, c, r0, n);
-  const bool need_P = valid && c != __ldg(a.bt.chunk_first + seq);
+  const bool need_P = valid && c != win_first(a.bt, seq);
   real Pc[D];  // column `lane` of P
   real v = real(0);
 #pragma unroll
@@ -675,7 +696,7 @@ __global__ void __launch_bounds__(128) k_dense_carry_wide(DenseScanArgs<real> a)
   const int64_t kq = blockIdx.x * (int64_t)G + grp;
   const bool valid = kq < a.bt.n_act;
   const int64_t seq = valid ? a.bt.act_seq[kq] : 0;
-  const int64_t c0 = valid ? a.bt.chunk_first[seq] : 0;
+  const int64_t c0 = valid ? win_first(a.bt, seq) : 0;
   const int64_t c1 = valid ? a.bt.chunk_first[seq + 1] : 0;
   real x = real(0);
   for (int64_t c = c0; c < c1; ++c) {

@@ -27,6 +27,8 @@ struct LinArgs {
   const SeqInfo* info;
   int jac, damp;
   real dparam;
+  real tol = real(0);  // convergence test in this precision: rows with a scaled residual
+                       // above it are reported (first failing row, for the sliding window)
 };
 
 template <class real>
@@ -60,6 +62,11 @@ struct CheckArgs {
   int it, max_iters;
   int compact_only;        // 1: rebuild the active set from info without testing
   int confirm;             // consecutive passing iterates needed
+  // sliding window (Sec. 3.2): advance each sequence's first solved chunk past the rows
+  // that passed the test (in the last `confirm` iterates); nullptr / 0 = off
+  int64_t* win_chunk = nullptr;
+  int window = 0;
+  int log2L = 0;
 };
 
 // Dense (FULL) correction-form scan: Delta_t = A_t Delta_{t-1} + b_t, Delta_0 = 0,
@@ -230,6 +237,7 @@ struct FusedArgs {
   int reset;
   real reset_thr;
   int mode;
+  real tol = real(0);  // see LinArgs::tol
 };
 
 template <class real>
@@ -261,6 +269,7 @@ struct GruTileArgs {
   Flags* status;        // timeout flag of the bounded waits (tensor-core variant)
   int jac, damp;
   float dparam;
+  float tol_f = 0.f;    // see LinArgs::tol
 };
 
 cudaError_t launch_gru_xproj(const float* W, const float* x, int64_t N, float* out,
@@ -302,6 +311,7 @@ struct MixedLinArgs {
   double dparam;
   float scale_f;        // (1 - k) under scale damping, else 1
   float dt_f;
+  float tol_f = 0.f;    // see LinArgs::tol
 };
 
 struct MixedScanArgs {

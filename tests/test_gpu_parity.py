@@ -253,7 +253,7 @@ def test_ragged_batch_matches_per_sequence_rollouts():
 
 @pytest.mark.parametrize("d,R,jac,prec", [(8, 12, "diag", "fp32"), (16, 24, "diag", "fp32"),
                                           (32, 48, "diag", "fp32"), (8, 12, "identity", "fp32"),
-                                          (4, 6, "diag", "fp64"), (64, 96, "diag", "fp64")])
+                                          (4, 6, "diag", "fp64"), (32, 48, "diag", "fp64")])
 def test_diag_lookback_ragged(d, R, jac, prec):
     """Single-pass look-back diagonal scans (tiles of 8192 / d rows, 1024 for d = 4; Picard
     reads no a) on a ragged batch whose lengths are below, at and above the tile length:
@@ -278,6 +278,79 @@ def test_diag_lookback_ragged(d, R, jac, prec):
         sub = odyn.MassAction(p["topology"][b:b + 1], p["params"][b:b + 1], p["dt"], "rk4", d=d)
         roll = onewton.rollout(sub, p["s0"][b:b + 1], n)[0]
         assert _relerr(sn[off[b]:off[b + 1]], roll) <= lim
+
+
+@pytest.mark.parametrize("case", ["full_fp64_d4", "full_fp32_d8", "full_fp32_d16",
+                                  "diag_fp64_d8", "diag_fp64_d2", "elk_fp64_gru8",
+                                  "mixed_d16", "gru64_fp32_tc"])
+def test_sliding_window_matches_rollout(case):
+    """Sliding window (Sec. 3.2): the converged prefix of every sequence is frozen and later
+    iterations solve only from its first failing chunk on. The fixed point is unchanged: on
+    ragged batches every path (fused d <= 8, wide dense, three-pass and look-back diagonal,
+    quasi-ELK, mixed precision, tensor-core GRU) returns the sequential rollout, and no more
+    rows are linearised than without the window (up to a margin: frozen rows sit anywhere
+    within the tolerance, which can cost the rows after them an extra iteration)."""
+    deer = _deer()
+    from paper_2603_16850_gb300 import _native as N
+    lib = N.load()
+    kind, prec, d = case.split("_")[0], case.split("_")[1], case.split("_")[-1]
+    lengths = [900, 1, 257, 2000, 64]
+    off = synth.offsets_from_lengths(lengths)
+    B = len(lengths)
+    x = None
+    if kind in ("full", "diag", "mixed"):
+        dd = int(d[1:])
+        R = {2: 3, 4: 6, 8: 12, 16: 24}[dd]
+        p = _ma_problem(B, dd, R, 1, seed=31)
+        tdt = torch.float32 if prec == "fp32" else torch.float64
+        dyn = _ma_dyn(p, tdt)
+        s0 = _t(p["s0"], tdt)
+        opts = dict(jac="full" if kind != "diag" else "diag", init="zeros", reset=True,
+                    max_iters=3000)
+        if prec == "fp32":
+            opts.update(FP32)
+        elif kind == "mixed":
+            opts.update(tol=1e-12, prec="mixed_bf16")
+        else:
+            opts.update(tol=1e-12, prec="fp64")
+        rolls = [onewton.rollout(odyn.MassAction(p["topology"][b:b + 1], p["params"][b:b + 1],
+                                                 p["dt"], "rk4", d=dd), p["s0"][b:b + 1], n)[0]
+                 for b, n in enumerate(lengths)]
+    else:
+        dd = 8 if case.endswith("gru8") else 64
+        g = synth.gru(1, sum(lengths), dd, dd, seed=32)
+        tdt = torch.float32 if prec == "fp32" else torch.float64
+        dyn = deer.Dynamics.gru(_t(g["W"], tdt), _t(g["U"], tdt))
+        x = _t(g["x"].reshape(-1, dd), tdt)
+        s0 = _t(np.zeros((B, dd)), tdt)
+        opts = dict(jac="diag", init="zeros", max_iters=3000)
+        if kind == "elk":
+            opts.update(damp="elk", damp_param=2.0)
+        opts.update(FP32 if prec == "fp32" else dict(tol=1e-12, prec="fp64"))
+        xs = g["x"][0]
+        rolls = []
+        for b, n in enumerate(lengths):
+            sub = odyn.GRU(g["W"], g["U"], xs[off[b]:off[b + 1]][None])
+            rolls.append(onewton.rollout(sub, np.zeros((1, dd)), n)[0])
+    rows = {}
+    for win in (False, True):
+        lib.deer_profile_reset()
+        lib.deer_profile_enable(1)
+        s, info = deer.deer_solve_batched(dyn, s0, off, x, window=win, **opts)
+        torch.cuda.synchronize()
+        lib.deer_profile_enable(0)
+        prof = N.deer_profile()
+        lib.deer_profile_read(prof)
+        rows[win] = int(prof.rows[1])
+        assert bool(info.converged.all()), (case, win, info.iters.max())
+        sn = s.cpu().numpy()
+        # float64 rows are frozen once their scaled residual is below tol, so along the
+        # conserved directions of the kinetics the frozen prefix carries up to ~T tol of
+        # drift (the unwindowed iteration keeps refining it while later rows converge)
+        lim = 1e-5 if prec == "fp32" else (1e-9 if (kind == "mixed" or win) else 1e-10)
+        for b in range(B):
+            assert _relerr(sn[off[b]:off[b + 1]], rolls[b]) <= lim, (case, win, b)
+    assert rows[True] <= 1.25 * rows[False], rows
 
 
 @pytest.mark.parametrize("kind", ["massaction_rk4", "gru", "brusselator"])
@@ -309,15 +382,17 @@ def test_nonfinite_input_is_reported():
         deer.deer_solve(dyn, s0, 100, jac="full", tol=1e-12)
 
 
-def test_full_size_batched_massaction_fp32_sampled():
-    """B=4096 systems, d=8, 12 reactions, RK4 dt=1e-3, T=16384, full Newton, FP32: sampled
-    trajectories equal the FP64 oracle rollout within 1e-5."""
+@pytest.mark.parametrize("window", [False, True])
+def test_full_size_batched_massaction_fp32_sampled(window):
+    """B=4096 systems, d=8, 12 reactions, RK4 dt=1e-3, T=16384, full Newton, FP32 (with and
+    without the sliding window, the benchmark runs with it): sampled trajectories equal the
+    FP64 oracle rollout within 1e-5."""
     deer = _deer()
     B, d, R, T = 4096, 8, 12, 16384
     p = _ma_problem(B, d, R, T, seed=0)
     dyn = _ma_dyn(p, torch.float32)
     s, info = deer.deer_solve(dyn, _t(p["s0"], torch.float32), T, jac="full", init="zeros",
-                              reset=True, **FP32)
+                              reset=True, window=window, **FP32)
     assert bool(info.converged.all()), (info.max_resid.max(), info.iters.max())
     assert float(info.max_resid.max()) <= FP32_TOL
     rng = np.random.default_rng(0)
