@@ -22,6 +22,8 @@ Contents (each function cites the passage of the paper it follows):
 * ``adjoint``   - the loss sum_t ||s_t - y_t||^2, its gradient by the
   reverse recursion of Eq. bptt / bptt_lds, by forward sensitivities and by
   central finite differences.
+* ``lle``       - the largest Lyapunov exponent along a trajectory by the
+  renormalised tangent recursion of Algorithm alg:LLE_estimate.
 
 Every function runs in float64. Parity unpinned: the iteration counts of the
 synthetic workloads (the paper reports none for them).

@@ -402,3 +402,60 @@ def test_adjoint_equals_forward_sensitivity_and_fd():
     fd = adjoint.fd_grad(mk, p["params"], s0, T, y, idx, h=1e-6)
     got = np.array([dth[b, j] for b, j in idx])
     assert np.allclose(got, fd, rtol=1e-5, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Largest Lyapunov exponent (Algorithm alg:LLE_estimate)
+# ---------------------------------------------------------------------------
+def test_lle_diagonal_linear_closed_form():
+    """For a constant diagonal Jacobian the renormalised products telescope:
+    the estimate is (1/T) log ||A^T u0|| = (1/(2T)) log sum_i a_i^(2T) u0_i^2."""
+    from oracle import lle
+    rng = np.random.default_rng(3)
+    d, T, B = 5, 60, 3
+    a = rng.uniform(0.4, 1.6, size=d) * rng.choice([-1.0, 1.0], size=d)
+    u0 = rng.standard_normal((B, d))
+    u0 /= np.linalg.norm(u0, axis=1, keepdims=True)
+    dyn = dynamics.Linear(np.diag(a))
+    s = newton.rollout(dyn, np.zeros((B, d)), T)
+    got = lle.lle_estimate(dyn, np.zeros((B, d)), s, u0)
+    want = 0.5 * np.log((a[None, :] ** (2 * T) * u0 ** 2).sum(axis=1)) / T
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-14)
+
+
+def test_lle_linear_tends_to_log_spectral_radius():
+    """A constant non-normal Jacobian with known eigenvalues: the estimate approaches
+    log of the spectral radius at the rate 1/T."""
+    from oracle import lle
+    rng = np.random.default_rng(4)
+    d = 4
+    lam = np.array([0.9, -1.3, 0.5, 0.2])
+    Q = rng.standard_normal((d, d)) + 2 * np.eye(d)
+    A = Q @ np.diag(lam) @ np.linalg.inv(Q)
+    dyn = dynamics.Linear(A)
+    u0 = rng.standard_normal((2, d))
+    u0 /= np.linalg.norm(u0, axis=1, keepdims=True)
+    errs = []
+    for T in (250, 2000):
+        s = newton.rollout(dyn, np.zeros((2, d)), T)
+        errs.append(np.abs(lle.lle_estimate(dyn, np.zeros((2, d)), s, u0) - np.log(1.3)).max())
+    assert errs[1] < 2e-3 and errs[1] < errs[0] / 4
+
+
+def test_lle_mass_action_bounded_below_by_conservation():
+    """A mass-conserving network: m^T J_t = m^T for every step Jacobian, so
+    ||J_T..J_1 u0|| >= |m^T u0| / ||m|| and the estimate is at least
+    (1/T) log(|m^T u0| / ||m||); it is also at most 0 up to O(1/T) for these relaxing
+    networks (the mass direction is neutral, every other mode decays)."""
+    from oracle import lle
+    p = synth.massaction(3, 6, 9, 800, seed=5)
+    dyn = dynamics.MassAction(p["topology"], p["params"], p["dt"], "rk4", d=6)
+    s = newton.rollout(dyn, p["s0"], 800)
+    rng = np.random.default_rng(6)
+    u0 = rng.standard_normal((3, 6))
+    u0 /= np.linalg.norm(u0, axis=1, keepdims=True)
+    got = lle.lle_estimate(dyn, p["s0"], s, u0)
+    m = p["masses"].astype(np.float64)  # per system
+    lower = np.log(np.abs((u0 * m).sum(axis=1)) / np.linalg.norm(m, axis=1)) / 800
+    assert np.all(got >= lower - 1e-12)
+    assert np.all(got <= 0.05)
