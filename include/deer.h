@@ -191,6 +191,22 @@ deer_status deer_grad(const deer_dynamics* f, int64_t batch, int64_t T, const vo
                       void* dl_ds0, const deer_options* opt, void* workspace,
                       size_t workspace_bytes, deer_stream_t stream);
 
+/* Largest Lyapunov exponent along trajectories (Ch. 5, Algorithm alg:LLE_estimate): for
+   each of `batch` sequences of T steps, the unit vector u_0 = u0[b] is pushed through the
+   step Jacobians J_t = df_t/ds evaluated at s_{t-1} (s_0 for t = 1) and renormalised
+   every step, u_t = J_t u_{t-1} / ||J_t u_{t-1}||, and lle_out[b] = (1/T) sum_t
+   log ||J_t u_{t-1}||. A positive value predicts slow parallel-Newton convergence over
+   long horizons (Ch. 5). s: DEVICE trajectory [batch*T][d] (a rollout or a converged
+   solve); u0: DEVICE [batch][d], unit vectors; lle_out: DEVICE float64 [batch]; buffers in
+   float64 for DEER_FP64, float32 for DEER_FP32 (lle_out always float64); d <= 32. The
+   Jacobians are materialised in the workspace (size from deer_lle_workspace_bytes). */
+size_t deer_lle_workspace_bytes(const deer_dynamics* f, int64_t batch, int64_t T,
+                                int32_t prec);
+deer_status deer_lle(const deer_dynamics* f, int64_t batch, int64_t T, const void* s0,
+                     const void* x, const void* s, const void* u0, double* lle_out,
+                     int32_t prec, void* workspace, size_t workspace_bytes,
+                     deer_stream_t stream);
+
 /* Sequential rollout s_t = f_t(s_{t-1}) on the GPU (the comparison baseline: one
    trajectory per thread or thread group, no parallelism over t). offsets: DEVICE array
    [batch+1] for a ragged batch, or NULL for `batch` sequences of length T. Needs no

@@ -270,6 +270,36 @@ def deer_grad(dyn: Dynamics, s0, T, s_star, dl_ds, x=None, *, prec="fp64", chunk
     return dparams, ds0
 
 
+def deer_lle(dyn: Dynamics, s0, T: int, s, u0=None, x=None, *, prec="fp64", stream=None,
+             workspace=None):
+    """Largest Lyapunov exponent estimate along trajectories (deer_lle): s [B*T][d] (a
+    rollout or a converged solve), u0 [B][d] unit start vectors (default: the normalised
+    all-ones vector). Returns a float64 tensor [B]."""
+    lib = N.load()
+    B = s0.shape[0]
+    dt = _dtype(prec)
+    if u0 is None:
+        u0 = torch.full((B, dyn.d), dyn.d ** -0.5, dtype=dt, device=s0.device)
+    for name, t in (("s0", s0), ("s", s), ("u0", u0), ("x", x)):
+        if t is not None:
+            _check_dev(t, name)
+            if t.dtype != dt:
+                raise ValueError(f"{name} must be {dt} for prec={prec}")
+    out = torch.empty(B, dtype=torch.float64, device=s0.device)
+    cdyn = dyn.c_struct()
+    need = lib.deer_lle_workspace_bytes(C.byref(cdyn), B, int(T), N.PREC[prec])
+    if need == 0 and B > 0:
+        raise N.DeerError(N.DEER_ERR_UNSUPPORTED, "deer_lle_workspace_bytes")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=s0.device)
+    st = lib.deer_lle(C.byref(cdyn), B, int(T), _ptr(s0), _ptr(x), _ptr(s), _ptr(u0),
+                      _ptr(out), N.PREC[prec], _ptr(workspace), workspace.numel(),
+                      _stream_handle(stream))
+    if st != N.DEER_OK:
+        raise N.DeerError(st, "deer_lle")
+    return out
+
+
 def _to_device(dyn, s0, x, device):
     nb = True
     dyn = Dynamics(dyn.kind, dyn.d, dyn.params.to(device, non_blocking=nb), dyn.d_in,

@@ -78,6 +78,11 @@ SIGNATURES = {
     "deer_kernel_launch_count": (C.c_int64, []),
     "deer_profile_enable": (None, [C.c_int32]),
     "deer_set_tensor_cores": (None, [C.c_int32]),
+    "deer_lle_workspace_bytes": (C.c_size_t, [C.POINTER(deer_dynamics), C.c_int64, C.c_int64,
+                                              C.c_int32]),
+    "deer_lle": (C.c_int32, [C.POINTER(deer_dynamics), C.c_int64, C.c_int64, C.c_void_p,
+                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                             C.c_void_p, C.c_size_t, C.c_void_p]),
     "deer_get_tensor_cores": (C.c_int32, []),
     "deer_profile_reset": (None, []),
     "deer_profile_read": (None, [C.POINTER(deer_profile)]),

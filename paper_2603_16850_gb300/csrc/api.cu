@@ -728,6 +728,70 @@ size_t deer_grad_workspace_bytes(const deer_dynamics* f, int64_t batch, int64_t 
 }  // extern "C"
 
 namespace deer {
+// Step Jacobians A_t = df_t/ds at s_{t-1} (Eq. lil_j) for every row of B sequences of T
+// steps of the trajectory s, written row-major to ws + ly.A (shared by the adjoint and the
+// Lyapunov-exponent entry points).
+template <class real>
+static deer_status jacobians_at(const deer_dynamics* f, int64_t B, int64_t T, const void* s0_,
+                                const void* x_, const void* s_, const Layout& ly, char* ws,
+                                cudaStream_t st, Batch& bt, DynView<real>& dv, Flags*& flags,
+                                LinArgs<real>& la) {
+  const int64_t N = B * T;
+  const int d = f->d;
+  std::vector<int64_t> off(B + 1), cf(B + 1);
+  int64_t nc = 0;
+  for (int64_t b = 0; b <= B; ++b) {
+    off[b] = b * T;
+    cf[b] = nc;
+    if (b < B) nc += (T + ly.L - 1) / ly.L;
+  }
+  int64_t* d_off = reinterpret_cast<int64_t*>(ws + ly.offsets);
+  int64_t* d_cf = reinterpret_cast<int64_t*>(ws + ly.chunk_first);
+  DEER_CK(cudaMemcpyAsync(d_off, off.data(), (B + 1) * 8, cudaMemcpyHostToDevice, st));
+  DEER_CK(cudaMemcpyAsync(d_cf, cf.data(), (B + 1) * 8, cudaMemcpyHostToDevice, st));
+  SeqAcc* acc = reinterpret_cast<SeqAcc*>(ws + ly.acc);
+  SeqInfo* info = reinterpret_cast<SeqInfo*>(ws + ly.info);
+  flags = reinterpret_cast<Flags*>(ws + ly.flags);
+  DEER_CK(cudaMemsetAsync(acc, 0, B * sizeof(SeqAcc), st));
+  DEER_CK(cudaMemsetAsync(info, 0, B * sizeof(SeqInfo), st));
+  DEER_CK(cudaMemsetAsync(flags, 0, sizeof(Flags), st));
+  bt = Batch{B, N, d_off, d_cf, nc, ly.L, ilog2(ly.L),
+             reinterpret_cast<int64_t*>(ws + ly.act_seq),
+             reinterpret_cast<int64_t*>(ws + ly.act_row_off),
+             reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), B, N, nc};
+  {
+    CheckArgs ca{B, d_off, d_cf, acc, info, flags,
+                 reinterpret_cast<int64_t*>(ws + ly.act_seq),
+                 reinterpret_cast<int64_t*>(ws + ly.act_row_off),
+                 reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), 0.0, 0, 0, 1, 1};
+    DEER_CK(launch_check(ca, st));
+  }
+  dv = make_view<real>(f, x_, ws, ly);
+  if (ly.n_ma > 0) {
+    DEER_CK(launch_ma_setup<real>(ly.n_ma, d, f->n_reactions, static_cast<const real*>(f->params),
+                                  f->params_stride, f->topology, f->topology_stride,
+                                  reinterpret_cast<real*>(ws + ly.ma), ly.ma_stride,
+                                  &flags->bad_input, st));
+  }
+  if (f->kind == DEER_F_GRU) {
+    DEER_CK(launch_gru_setup<real>(d, static_cast<const real*>(f->params), f->d_in,
+                                   reinterpret_cast<real*>(ws + ly.gru_M), st));
+  }
+  la.dv = dv;
+  la.bt = bt;
+  la.s0 = static_cast<const real*>(s0_);
+  la.s = static_cast<const real*>(s_);
+  la.A = reinterpret_cast<real*>(ws + ly.A);
+  la.b = reinterpret_cast<real*>(ws + ly.b);
+  la.acc = acc;
+  la.info = info;
+  la.jac = DEER_JAC_FULL;
+  la.damp = DEER_DAMP_NONE;
+  la.dparam = real(0);
+  DEER_CK(launch_linearize<real>(la, st));
+  return DEER_OK;
+}
+
 template <class real>
 static deer_status grad_impl(const deer_dynamics* f, int64_t B, int64_t T, const void* s0_,
                              const void* x_, const void* sstar_, const void* g_, void* dp_,
@@ -743,59 +807,12 @@ static deer_status grad_impl(const deer_dynamics* f, int64_t B, int64_t T, const
     return DEER_ERR_WORKSPACE;
   char* ws = static_cast<char*>(ws_);
   const int d = f->d;
-  std::vector<int64_t> off(B + 1), cf(B + 1);
-  int64_t nc = 0;
-  for (int64_t b = 0; b <= B; ++b) {
-    off[b] = b * T;
-    cf[b] = nc;
-    if (b < B) nc += (T + ly.L - 1) / ly.L;
-  }
-  int64_t* d_off = reinterpret_cast<int64_t*>(ws + ly.offsets);
-  int64_t* d_cf = reinterpret_cast<int64_t*>(ws + ly.chunk_first);
-  DEER_CK(cudaMemcpyAsync(d_off, off.data(), (B + 1) * 8, cudaMemcpyHostToDevice, st));
-  DEER_CK(cudaMemcpyAsync(d_cf, cf.data(), (B + 1) * 8, cudaMemcpyHostToDevice, st));
-  SeqAcc* acc = reinterpret_cast<SeqAcc*>(ws + ly.acc);
-  SeqInfo* info = reinterpret_cast<SeqInfo*>(ws + ly.info);
-  Flags* flags = reinterpret_cast<Flags*>(ws + ly.flags);
-  DEER_CK(cudaMemsetAsync(acc, 0, B * sizeof(SeqAcc), st));
-  DEER_CK(cudaMemsetAsync(info, 0, B * sizeof(SeqInfo), st));
-  DEER_CK(cudaMemsetAsync(flags, 0, sizeof(Flags), st));
-  Batch bt{B, N, d_off, d_cf, nc, ly.L, ilog2(ly.L),
-           reinterpret_cast<int64_t*>(ws + ly.act_seq),
-           reinterpret_cast<int64_t*>(ws + ly.act_row_off),
-           reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), B, N, nc};
-  {
-    CheckArgs ca{B, d_off, d_cf, acc, info, flags,
-                 reinterpret_cast<int64_t*>(ws + ly.act_seq),
-                 reinterpret_cast<int64_t*>(ws + ly.act_row_off),
-                 reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), 0.0, 0, 0, 1, 1};
-    DEER_CK(launch_check(ca, st));
-  }
-  DynView<real> dv = make_view<real>(f, x_, ws, ly);
-  if (ly.n_ma > 0) {
-    DEER_CK(launch_ma_setup<real>(ly.n_ma, d, f->n_reactions, static_cast<const real*>(f->params),
-                                  f->params_stride, f->topology, f->topology_stride,
-                                  reinterpret_cast<real*>(ws + ly.ma), ly.ma_stride,
-                                  &flags->bad_input, st));
-  }
-  if (f->kind == DEER_F_GRU) {
-    DEER_CK(launch_gru_setup<real>(d, static_cast<const real*>(f->params), f->d_in,
-                                   reinterpret_cast<real*>(ws + ly.gru_M), st));
-  }
-  // A_t at the fixed point (Eq. lil_j) for every row
+  Batch bt;
+  DynView<real> dv;
+  Flags* flags = nullptr;
   LinArgs<real> la;
-  la.dv = dv;
-  la.bt = bt;
-  la.s0 = static_cast<const real*>(s0_);
-  la.s = static_cast<const real*>(sstar_);
-  la.A = reinterpret_cast<real*>(ws + ly.A);
-  la.b = reinterpret_cast<real*>(ws + ly.b);
-  la.acc = acc;
-  la.info = info;
-  la.jac = DEER_JAC_FULL;
-  la.damp = DEER_DAMP_NONE;
-  la.dparam = real(0);
-  DEER_CK(launch_linearize<real>(la, st));
+  deer_status js = jacobians_at<real>(f, B, T, s0_, x_, sstar_, ly, ws, st, bt, dv, flags, la);
+  if (js != DEER_OK) return js;
   // reverse scan lambda_t = A_{t+1}^T lambda_{t+1} + g_t
   AdjScanArgs<real> sa;
   sa.bt = bt;
@@ -825,9 +842,69 @@ static deer_status grad_impl(const deer_dynamics* f, int64_t B, int64_t T, const
   if (hf.bad_input) return DEER_ERR_INVALID;
   return DEER_OK;
 }
+template <class real>
+static deer_status lle_impl(const deer_dynamics* f, int64_t B, int64_t T, const void* s0_,
+                            const void* x_, const void* s_, const void* u0_, double* out,
+                            const deer_options* o, void* ws_, size_t ws_bytes,
+                            cudaStream_t st) {
+  Layout ly;
+  if (!make_layout(f, B, B * T, o, ly)) return DEER_ERR_INVALID;
+  if (!ws_ || ws_bytes < ly.total || (reinterpret_cast<uintptr_t>(ws_) & 255u))
+    return DEER_ERR_WORKSPACE;
+  char* ws = static_cast<char*>(ws_);
+  Batch bt;
+  DynView<real> dv;
+  Flags* flags = nullptr;
+  LinArgs<real> la;
+  deer_status js = jacobians_at<real>(f, B, T, s0_, x_, s_, ly, ws, st, bt, dv, flags, la);
+  if (js != DEER_OK) return js;
+  LleArgs<real> a{B, T, f->d, la.A, static_cast<const real*>(u0_), out};
+  DEER_CK(launch_lle<real>(a, st));
+  Flags hf;
+  DEER_CK(cudaMemcpyAsync(&hf, flags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
+  DEER_CK(cudaStreamSynchronize(st));
+  if (hf.bad_input) return DEER_ERR_INVALID;
+  return DEER_OK;
+}
 }  // namespace deer
 
 extern "C" {
+
+size_t deer_lle_workspace_bytes(const deer_dynamics* f, int64_t batch, int64_t T,
+                                int32_t prec) {
+  if (batch < 0 || T < 0 || (prec != DEER_FP64 && prec != DEER_FP32) || !f || f->d > 32)
+    return 0;
+  deer_options o;
+  deer_default_options(&o);
+  o.prec = prec;
+  if (check_common(f, &o) != DEER_OK) return 0;
+  Layout ly;
+  if (!make_layout(f, batch, batch * T, &o, ly)) return 0;
+  return ly.total;
+}
+
+deer_status deer_lle(const deer_dynamics* f, int64_t batch, int64_t T, const void* s0,
+                     const void* x, const void* s, const void* u0, double* lle_out,
+                     int32_t prec, void* workspace, size_t workspace_bytes,
+                     deer_stream_t stream) {
+  if (!f || batch < 0 || T < 0) return DEER_ERR_INVALID;
+  if (prec != DEER_FP64 && prec != DEER_FP32) return DEER_ERR_UNSUPPORTED;
+  if (f->d > 32) return DEER_ERR_UNSUPPORTED;
+  deer_options o;
+  deer_default_options(&o);
+  o.prec = prec;
+  deer_status c = check_common(f, &o);
+  if (c != DEER_OK) return c;
+  if (batch == 0 || T == 0) return DEER_OK;
+  if (!s0 || !s || !u0 || !lle_out) return DEER_ERR_INVALID;
+  if (f->kind == DEER_F_GRU && !x) return DEER_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (prec == DEER_FP32)
+    return lle_impl<float>(f, batch, T, s0, x, s, u0, lle_out, &o, workspace, workspace_bytes,
+                           st);
+  return lle_impl<double>(f, batch, T, s0, x, s, u0, lle_out, &o, workspace, workspace_bytes,
+                          st);
+}
 
 deer_status deer_grad(const deer_dynamics* f, int64_t batch, int64_t T, const void* s0,
                       const void* x, const void* s_star, const void* dl_ds, void* dl_dparams,

@@ -340,3 +340,22 @@ inline bool mixed_supported(int kind, int d, int jac) {
 }
 
 }  // namespace deer
+
+namespace deer {
+
+// Largest Lyapunov exponent of each of B sequences of T steps from the stored step
+// Jacobians (A [B*T][d][d], row-major, J_t at row b*T + t - 1) and unit start vectors
+// u0 [B][d]; out [B] (float64).
+template <class real>
+struct LleArgs {
+  int64_t B, T;
+  int d;
+  const real* A;
+  const real* u0;
+  double* out;
+};
+
+template <class real>
+cudaError_t launch_lle(const LleArgs<real>& a, cudaStream_t st);
+
+}  // namespace deer
