@@ -243,6 +243,27 @@ def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64):
             "linearize": lin_entry}
 
 
+def lle_measurement(deer, dyn, s0, s, T, d, stream, n_sys=64):
+    """Largest Lyapunov exponent (Ch. 5) along the converged trajectories of the first
+    n_sys systems of the headline workload: the thesis's predictor of parallel-Newton
+    convergence (negative: predictable, fast; positive: chaotic, slow)."""
+    import torch
+    sub = deer.Dynamics.massaction(dyn.topology[:n_sys].contiguous(),
+                                   dyn.params[:n_sys].contiguous(), d, dyn.dt)
+    u0 = torch.full((n_sys, d), d ** -0.5, dtype=s.dtype, device=s.device)
+    traj = s.view(-1, T, d)[:n_sys].reshape(-1, d)
+    torch.cuda.synchronize()
+    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    e0.record(stream)
+    lle = deer.deer_lle(sub, s0[:n_sys].contiguous(), T, traj, u0, prec="fp32", stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    v = lle.cpu().numpy()
+    return {"what": f"LLE estimate along the converged trajectories of {n_sys} systems",
+            "min": float(v.min()), "median": float(sorted(v)[len(v) // 2]),
+            "max": float(v.max()), "ms": e0.elapsed_time(e1)}
+
+
 def adjoint_measurement(deer, N, lib, dev, stream):
     """Differentiation workload: d=32 kinetic networks (48 reactions), B=256, T=32768, RK4
     dt=1e-3, FP32. Forward full-Jacobian solve, then the adjoint gradient of
@@ -478,6 +499,7 @@ def run(args):
 
     extra = {}
     if rank == 0 and ws == 1 and not args.no_extra:
+        extra["lle"] = lle_measurement(deer, dyn, s0, s, T, d, stream)
         extra["gru_quasi_deer"] = gru_diag_measurement(deer, N, lib, dev, stream)
         extra["adjoint"] = adjoint_measurement(deer, N, lib, dev, stream)
         extra["ragged_mixed"] = ragged_mixed_measurement(deer, N, lib, dev, stream)
