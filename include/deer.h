@@ -77,7 +77,8 @@ typedef enum {
 
 typedef enum {
   DEER_DAMP_NONE = 0,
-  DEER_DAMP_ELK = 1,   /* Kalman-filter step, lambda = damp_param (diag modes only; Sec. 4.3) */
+  DEER_DAMP_ELK = 1,   /* Kalman-filter step, lambda = damp_param (Sec. 4.3): diagonal modes
+                          (quasi-ELK) and the full Jacobian for d <= 8 (dense ELK) */
   DEER_DAMP_SCALE = 2, /* scale-ELK: A~ <- (1 - k) A~, k = damp_param in [0, 1] (Sec. 4.5.1) */
   DEER_DAMP_CLIP = 3   /* clip-ELK: diag A~ clipped to [-rho, rho], rho = damp_param (Sec. 4.5.2) */
 } deer_damp;
@@ -141,7 +142,9 @@ typedef struct {
                          (in any of the last `confirm` + 1 iterates) are frozen and later
                          iterations solve only from there, starting from the frozen
                          state. The fixed point is the same; iterates differ from the
-                         unwindowed iteration once rows are frozen. */
+                         unwindowed iteration once rows are frozen. Applies to undamped
+                         steps (damp = DEER_DAMP_NONE); damped steps converge linearly and
+                         always cover each sequence whole. */
 } deer_options;
 
 typedef struct {
@@ -227,7 +230,8 @@ deer_status deer_rollout(const deer_dynamics* f, int64_t batch, int64_t T,
    the device current; make that first call before any stream capture. Every call reuses
    the same array and clears what must start at zero, so calls that overlap on the GPU
    (other streams or threads) race and must be serialised by the caller. Arguments and
-   results as deer_solve; nothing is allocated on the device or the host. */
+   results as deer_solve (without mixed precision, dense ELK or the sliding window, which
+   return DEER_ERR_UNSUPPORTED); nothing is allocated on the device or the host. */
 deer_status deer_solve_noalloc(const deer_dynamics* f, int64_t batch, int64_t T,
                                const void* s0, const void* x, void* s_out,
                                const deer_options* opt, deer_stream_t stream,

@@ -148,7 +148,8 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
     // bfloat16 E = A - I, float32 offsets and aggregates
     ly.A = take((size_t)N * d * d * 2);
     ly.b = take((size_t)N * d * 4);
-  } else if (o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d)) {
+  } else if (o->jac == DEER_JAC_FULL && o->damp != DEER_DAMP_ELK &&
+             dense_fused_supported(f->kind, d)) {
     // pending Jacobians / offsets of the fused path (chunk-major or chunk-interleaved),
     // padded to whole chunks and to groups of 32 chunks
     const size_t rows = (size_t)((C + 31) / 32 * 32) * L;
@@ -180,7 +181,8 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
   if (gru_tiled_supported(f->kind, d, f->d_in, o->jac, o->prec))
     ly.xproj = take((size_t)N * 3 * d * rs);
   ly.sprev = p;
-  if (!mixed && o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d))
+  if (!mixed && o->jac == DEER_JAC_FULL && o->damp != DEER_DAMP_ELK &&
+      dense_fused_supported(f->kind, d))
     ly.sprev = take((size_t)C * d * rs);
   ly.lb_ticket = ly.lb_flags = ly.lb_agg = ly.lb_pre = p;
   if (use_diag_lookback(o, d)) {
@@ -226,7 +228,10 @@ static deer_status check_common(const deer_dynamics* f, const deer_options* o) {
        (o->damp != DEER_DAMP_NONE && o->damp != DEER_DAMP_SCALE)))
     return DEER_ERR_UNSUPPORTED;
   if (!d_supported(f->kind, f->d, o->jac)) return DEER_ERR_UNSUPPORTED;
-  if (o->damp == DEER_DAMP_ELK && o->jac == DEER_JAC_FULL) return DEER_ERR_UNSUPPORTED;
+  // dense ELK: the covariance recursion runs in registers for d <= 8
+  if (o->damp == DEER_DAMP_ELK && o->jac == DEER_JAC_FULL &&
+      !(f->d == 1 || f->d == 2 || f->d == 4 || f->d == 8))
+    return DEER_ERR_UNSUPPORTED;
   if (o->damp == DEER_DAMP_CLIP && o->jac == DEER_JAC_FULL) return DEER_ERR_INVALID;
   if (o->damp == DEER_DAMP_ELK && !(o->damp_param >= 0.0)) return DEER_ERR_INVALID;
   if (o->window != 0 && o->window != 1) return DEER_ERR_INVALID;
@@ -298,7 +303,10 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   bt.act_rows = N;
   bt.act_chunks = nc;
   int64_t* d_win = reinterpret_cast<int64_t*>(ws + ly.win_chunk);
-  if (o->window) {
+  // the window freezes rows one iterate after they qualify, which relies on the fast
+  // (quadratic) convergence of undamped steps; damped steps converge linearly and run whole
+  const bool window = o->window && o->damp == DEER_DAMP_NONE;
+  if (window) {
     // sliding window: every sequence starts solved from its first chunk
     DEER_CK(cudaMemcpyAsync(d_win, chunk_first.data(), (B + 1) * 8, cudaMemcpyHostToDevice, st));
     bt.win_chunk = d_win;
@@ -371,8 +379,8 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
                reinterpret_cast<int64_t*>(ws + ly.act_row_off),
                reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), o->tol, 0, max_iters, 1,
                o->confirm > 1 ? o->confirm : 1};
-  ca.win_chunk = o->window ? d_win : nullptr;
-  ca.window = o->window;
+  ca.win_chunk = window ? d_win : nullptr;
+  ca.window = window ? 1 : 0;
   ca.log2L = bt.log2L;
   DEER_CK(launch_check(ca, st));  // every sequence starts active
   ca.compact_only = 0;
@@ -457,7 +465,8 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
       msa.reset_thr = 1e18;  // the scan and the Jacobians are float32
     }
   }
-  const bool fused = !mixed && o->jac == DEER_JAC_FULL && dense_fused_supported(f->kind, d);
+  const bool fused = !mixed && o->jac == DEER_JAC_FULL && o->damp != DEER_DAMP_ELK &&
+                     dense_fused_supported(f->kind, d);
   FusedArgs<real> fa;
   if (fused) {
     fa.dv = dv;
@@ -571,13 +580,18 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
           DEER_CK(launch_dense_scan_mixed(msa, st));
         }
       } else if (o->jac == DEER_JAC_FULL) {
+        if (o->damp == DEER_DAMP_ELK && o->damp_param > 0.0) {
+          // dense ELK: Kalman-filter damping of the linearised step (A, b rewritten)
+          ElkDenseArgs<real> ea{bt, d, la.A, la.b, (real)o->damp_param};
+          DEER_CK(launch_elk_dense<real>(ea, st));
+        }
         DEER_CK(launch_dense_scan<real>(dsa, st));
       } else if (lookback) {
         lba.bt = bt;
         lba.epoch += 1;
         // round-robin tile order assumes every sequence has the same chunks to solve,
         // which a sliding window breaks
-        lba.cps = o->window ? 0 : uniform_chunks;
+        lba.cps = window ? 0 : uniform_chunks;
         DEER_CK(launch_diag_lookback<real>(lba, st));
       } else {
         DEER_CK(launch_diag_scan<real>(gsa, st));
@@ -1169,6 +1183,8 @@ deer_status deer_solve_noalloc(const deer_dynamics* f, int64_t batch, int64_t T,
   deer_status c = check_common(f, opt);
   if (c != DEER_OK) return c;
   if (opt->prec == DEER_MIXED_BF16) return DEER_ERR_UNSUPPORTED;
+  if (opt->damp == DEER_DAMP_ELK && opt->jac == DEER_JAC_FULL) return DEER_ERR_UNSUPPORTED;
+  if (opt->window) return DEER_ERR_UNSUPPORTED;
   if (batch < 0 || T < 0) return DEER_ERR_INVALID;
   if (batch == 0 || T == 0) return DEER_OK;
   if (!s0 || !s_out) return DEER_ERR_INVALID;

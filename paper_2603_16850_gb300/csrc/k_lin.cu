@@ -704,7 +704,9 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
   constexpr int GROUPS = 128 / D;          // rows per block
   constexpr bool WANTA = JAC == DEER_JAC_FULL || JAC == DEER_JAC_DIAG;
   __shared__ real sG[GROUPS][D][D + 1];
-  __shared__ real sK[GROUPS][D][D];
+  // group stride padded by 16 bytes: the groups of a warp read their K rows from
+  // different banks
+  __shared__ __align__(16) real sK[GROUPS][D * D + 16 / sizeof(real)];
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gmask = D == 32 ? 0xffffffffu : (0xffffu << (16 * ((threadIdx.x >> 4) & 1)));
   const int64_t ar = blockIdx.x * (int64_t)GROUPS + grp;
@@ -761,13 +763,13 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
         for (int m = 0; m < D; ++m) {
           const real gm = cK * Gi[m];
 #pragma unroll
-          for (int j = 0; j < D; ++j) Kn[j] += gm * sK[grp][m][j];
+          for (int j = 0; j < D; ++j) Kn[j] += gm * sK[grp][m * D + j];
         }
       }
       __syncwarp(gmask);
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        sK[grp][lane][j] = Kn[j];
+        sK[grp][lane * D + j] = Kn[j];
         Kacc[j] += w * Kn[j];
       }
       __syncwarp(gmask);

@@ -192,7 +192,9 @@ __global__ void __launch_bounds__(128) k_lin_ma_mixed(MixedLinArgs a) {
   constexpr int RMAX = 64;         // reactions per network held in shared memory
   constexpr int RPL = RMAX / D;    // reactions per lane
   __shared__ float sG[GROUPS][D][D + 1];
-  __shared__ float sK[GROUPS][D][D];
+  // one padding row per group: the two groups of a warp read their K rows from banks 16
+  // apart (same-bank broadcasts of different groups would serialise)
+  __shared__ __align__(16) float sK[GROUPS][D + 1][D];
   __shared__ double sRate[GROUPS][RMAX];  // float rates use the first half in float32 mode
   __shared__ float sD1[GROUPS][RMAX], sD2[GROUPS][RMAX];  // d rate / d c_i1, d c_i2
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;

@@ -359,3 +359,21 @@ template <class real>
 cudaError_t launch_lle(const LleArgs<real>& a, cudaStream_t st);
 
 }  // namespace deer
+
+namespace deer {
+
+// Dense ELK (Kalman-filter damping of the full-Jacobian step): rewrites the linearised
+// A [N][d][d] and b [N][d] of the active rows in place as Gamma_t A_t, Gamma_t b_t.
+template <class real>
+struct ElkDenseArgs {
+  Batch bt;
+  int d;
+  real* A;
+  real* b;
+  real lambda;
+};
+
+template <class real>
+cudaError_t launch_elk_dense(const ElkDenseArgs<real>& a, cudaStream_t st);
+
+}  // namespace deer

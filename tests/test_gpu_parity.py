@@ -460,3 +460,49 @@ def test_mixed_bf16_ragged_matches_fp64_rollout(d, R):
         sub = odyn.MassAction(p["topology"][b:b + 1], p["params"][b:b + 1], p["dt"], "rk4", d=d)
         roll = onewton.rollout(sub, p["s0"][b:b + 1], L)[0]
         assert _relerr(sn[off[b]:off[b + 1]], roll) <= 1e-9
+
+
+@pytest.mark.parametrize("d,lam", [(2, 0.7), (4, 3.0), (8, 1.0)])
+def test_dense_elk_iterates_and_fixed_point(d, lam):
+    """Dense ELK (full-Jacobian Kalman-filter step, Sec. 4.2-4.3): two iterations equal the
+    oracle's filtered means (elk_filter_step with the full Jacobian) and the iteration
+    converges to the sequential rollout."""
+    deer = _deer()
+    B, T = 3, 300
+    R = {2: 3, 4: 6, 8: 12}[d]
+    p = _ma_problem(B, d, R, T, seed=50 + d, dt=0.01)
+    od = _ma_oracle(p)
+    dyn = _ma_dyn(p, torch.float64)
+    s2, _ = deer.deer_solve(dyn, _t(p["s0"]), T, jac="full", damp="elk", damp_param=lam,
+                            tol=0.0, max_iters=2, init="s0")
+    ref = onewton.initial_guess(od, p["s0"], T, "s0")
+    for _ in range(2):
+        ref = oelk.elk_filter_step(od, p["s0"], ref, "full", lam)
+    assert _relerr(s2.cpu().numpy(), ref.reshape(-1, d)) <= 1e-11
+    s, info = deer.deer_solve(dyn, _t(p["s0"]), T, jac="full", damp="elk", damp_param=lam,
+                              tol=1e-12, init="s0", max_iters=2000)
+    assert bool(info.converged.all()), info.iters.max()
+    roll = onewton.rollout(od, p["s0"], T)
+    for b in range(B):
+        assert _relerr(s.cpu().numpy()[b * T:(b + 1) * T], roll[b]) <= 1e-10
+
+
+@pytest.mark.parametrize("window", [False, True])
+def test_dense_elk_fp32_ragged_converges(window):
+    """Dense ELK in float32 on a ragged batch, within 1e-5 of the float64 rollout. The
+    sliding window does not apply to damped steps (they converge linearly, so rows would
+    be frozen with too little margin for float32): the option is accepted and ignored."""
+    deer = _deer()
+    lengths = [700, 33, 1500]
+    off = synth.offsets_from_lengths(lengths)
+    p = _ma_problem(3, 8, 12, 1, seed=55)
+    dyn = _ma_dyn(p, torch.float32)
+    s, info = deer.deer_solve_batched(dyn, _t(p["s0"], torch.float32), off, jac="full",
+                                      damp="elk", damp_param=0.5, init="zeros", reset=True,
+                                      window=window, max_iters=3000, **FP32)
+    assert bool(info.converged.all()), info.iters.max()
+    sn = s.cpu().numpy()
+    for b, n in enumerate(lengths):
+        sub = odyn.MassAction(p["topology"][b:b + 1], p["params"][b:b + 1], p["dt"], "rk4", d=8)
+        roll = onewton.rollout(sub, p["s0"][b:b + 1], n)[0]
+        assert _relerr(sn[off[b]:off[b + 1]], roll) <= 1e-5
