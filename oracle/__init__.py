@@ -9,8 +9,10 @@ sides receive their inputs from ``synth`` only.
 Contents (each function cites the passage of the paper it follows):
 
 * ``dynamics``  - the recurrences f_t (Brusselator-Euler, mass-action
-  Euler/RK4, GRU, linear), their Jacobians and parameter derivatives,
-  written as plain per-reaction / per-gate loops.
+  Euler/RK4, GRU, linear; the mean-field RNN, two-well Langevin,
+  Lorenz-96 with Dormand-Prince steps and the word-problem permutation
+  of the thesis's second workloads), their Jacobians and parameter
+  derivatives, written as plain per-reaction / per-gate loops.
 * ``newton``    - the sequential rollout (the plain definition of the
   answer, Sec. 2.1), the residual (Eq. r_def), the generalised
   quasi-Newton step in correction form (Eq. qdeer_lds, forward

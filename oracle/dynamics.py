@@ -235,6 +235,182 @@ class Linear:
         return np.broadcast_to(self.A, (s.shape[0], self.d, self.d)).copy()
 
 
+class MeanFieldRNN:
+    """Mean-field RNN of the predictability-threshold experiment (Sec. ssc:exp_thresh):
+        s_t = W tanh(s_{t-1}) + u_t,   A_t = W diag(1 - tanh(s_{t-1})^2).
+    W [d][d] shared or [B][d][d] per sequence; u [B][T][d] (None for u = 0)."""
+
+    def __init__(self, W, u=None):
+        self.W = np.asarray(W, dtype=np.float64)
+        self.d = self.W.shape[-1]
+        self.u = None if u is None else np.asarray(u, dtype=np.float64)
+        self.n_params = 0
+
+    def f(self, t, s):
+        th = np.tanh(s)
+        if self.W.ndim == 2:
+            out = th @ self.W.T
+        else:
+            out = np.einsum("bij,bj->bi", self.W, th)
+        if self.u is not None:
+            out = out + self.u[:, t - 1]
+        return out
+
+    def jac(self, t, s):
+        sech2 = 1.0 - np.tanh(s) ** 2
+        W = np.broadcast_to(self.W, (s.shape[0], self.d, self.d))
+        return W * sech2[:, None, :]
+
+
+class TwoWellLangevin:
+    """Discretised Langevin dynamics (Eq. langevin) for the potential
+        phi(s) = -log( w1 N(s; m1, diag v1) + w2 N(s; m2, diag v2) ),
+        s_t = s_{t-1} - eps grad phi(s_{t-1}) + sqrt(2 eps) xi_t,
+    with xi_t the standard normal draws in ``noise`` [B][T][d] (None: no noise).
+    The Jacobian is I - eps Hess phi (Sec. ssc:2well).
+    params [4d+2] shared or [B][4d+2]: m1 | m2 | v1 | v2 | w1 | w2."""
+
+    def __init__(self, params, eps, noise=None, d=None):
+        p = np.atleast_2d(np.asarray(params, dtype=np.float64))
+        self.d = (p.shape[1] - 2) // 4 if d is None else d
+        d = self.d
+        self.m1, self.m2 = p[:, :d], p[:, d:2 * d]
+        self.v1, self.v2 = p[:, 2 * d:3 * d], p[:, 3 * d:4 * d]
+        self.w1, self.w2 = p[:, 4 * d], p[:, 4 * d + 1]
+        self.eps = float(eps)
+        self.noise = None if noise is None else np.asarray(noise, dtype=np.float64)
+        self.n_params = 0
+
+    def _resp(self, s):
+        """Responsibilities of the two components at s (posterior weights)."""
+        with np.errstate(divide="ignore", over="ignore"):  # w_k = 0 or far from a well
+            l1 = np.log(self.w1) - 0.5 * np.sum(np.log(self.v1) + (s - self.m1) ** 2 / self.v1,
+                                                axis=1)
+            l2 = np.log(self.w2) - 0.5 * np.sum(np.log(self.v2) + (s - self.m2) ** 2 / self.v2,
+                                                axis=1)
+            g1 = 1.0 / (1.0 + np.exp(l2 - l1))
+            g2 = 1.0 / (1.0 + np.exp(l1 - l2))
+        return g1, g2
+
+    def grad_phi(self, s):
+        g1, g2 = self._resp(s)
+        return g1[:, None] * (s - self.m1) / self.v1 + g2[:, None] * (s - self.m2) / self.v2
+
+    def hess_phi(self, s):
+        """sum_k g_k diag(1/v_k) minus the covariance of the component scores."""
+        g1, g2 = self._resp(s)
+        sc1 = -(s - self.m1) / self.v1          # score of component 1
+        sc2 = -(s - self.m2) / self.v2
+        H = np.zeros((s.shape[0], self.d, self.d))
+        idx = np.arange(self.d)
+        H[:, idx, idx] = g1[:, None] / self.v1 + g2[:, None] / self.v2
+        diff = sc1 - sc2
+        H -= (g1 * g2)[:, None, None] * diff[:, :, None] * diff[:, None, :]
+        return H
+
+    def f(self, t, s):
+        out = s - self.eps * self.grad_phi(s)
+        if self.noise is not None:
+            out = out + np.sqrt(2.0 * self.eps) * self.noise[:, t - 1]
+        return out
+
+    def jac(self, t, s):
+        return np.eye(self.d)[None] - self.eps * self.hess_phi(s)
+
+
+# Dormand-Prince 5(4) pair (Dormand & Prince, 1980): nodes, stage matrix and the weights
+# of the fifth-order solution; the seventh (FSAL) stage has zero weight there.
+DP5_C = np.array([0.0, 1 / 5, 3 / 10, 4 / 5, 8 / 9, 1.0])
+DP5_A = np.array([
+    [0, 0, 0, 0, 0, 0],
+    [1 / 5, 0, 0, 0, 0, 0],
+    [3 / 40, 9 / 40, 0, 0, 0, 0],
+    [44 / 45, -56 / 15, 32 / 9, 0, 0, 0],
+    [19372 / 6561, -25360 / 2187, 64448 / 6561, -212 / 729, 0, 0],
+    [9017 / 3168, -355 / 33, 46732 / 5247, 49 / 176, -5103 / 18656, 0],
+])
+DP5_B = np.array([35 / 384, 0.0, 500 / 1113, 125 / 192, -2187 / 6784, 11 / 84])
+
+
+class Lorenz96:
+    """Lorenz-96, dx_i/dt = (x_{i+1} - x_{i-2}) x_{i-1} - x_i + F (cyclic indices), one
+    fixed step h of an explicit Runge-Kutta method (default: the fifth-order
+    Dormand-Prince solution) per time step (the Lorenz-96 experiment of Sec. elk_exps
+    evaluates it with the Dormand-Prince solver).
+    F scalar or [B]."""
+
+    def __init__(self, F, dt, d, tableau=None):
+        self.F = np.asarray(F, dtype=np.float64).reshape(-1, 1)
+        self.dt = float(dt)
+        self.d = d
+        self.A, self.b = (DP5_A, DP5_B) if tableau is None else tableau
+        self.n_params = 0
+
+    def rhs(self, x):
+        return (np.roll(x, -1, axis=1) - np.roll(x, 2, axis=1)) * np.roll(x, 1, axis=1) - x + self.F
+
+    def rhs_jac(self, x):
+        B, d = x.shape
+        G = np.zeros((B, d, d))
+        for i in range(d):
+            ip, im, im2 = (i + 1) % d, (i - 1) % d, (i - 2) % d
+            G[:, i, ip] += x[:, im]
+            G[:, i, im2] -= x[:, im]
+            G[:, i, im] += x[:, ip] - x[:, im2]
+            G[:, i, i] -= 1.0
+        return G
+
+    def _stages(self, s):
+        h = self.dt
+        Y, K = [], []
+        for k in range(len(self.b)):
+            y = s.copy()
+            for j in range(k):
+                y = y + h * self.A[k, j] * K[j]
+            Y.append(y)
+            K.append(self.rhs(y))
+        return Y, K
+
+    def f(self, t, s):
+        Y, K = self._stages(s)
+        return s + self.dt * sum(bk * kk for bk, kk in zip(self.b, K))
+
+    def jac(self, t, s):
+        """Chain rule through the stages: dK_k = G(Y_k) (I + h sum_j a_kj dK_j)."""
+        h = self.dt
+        Y, _ = self._stages(s)
+        I = np.eye(self.d)[None]
+        dK = []
+        for k in range(len(self.b)):
+            M = I.copy()
+            for j in range(k):
+                M = M + h * self.A[k, j] * dK[j]
+            dK.append(self.rhs_jac(Y[k]) @ M)
+        return I + h * sum(bk * dk for bk, dk in zip(self.b, dK))
+
+
+class Permute:
+    """The group word problem as a time-varying LDS (Prop. cayley):
+        s_t[i] = s_{t-1}[p_t[i]],  A_t = the permutation matrix with A_t[i, p_t[i]] = 1,
+    p [B][T][d] integer source indices (one permutation per step)."""
+
+    def __init__(self, perms):
+        self.p = np.asarray(perms).astype(np.int64)
+        self.d = self.p.shape[2]
+        self.n_params = 0
+
+    def f(self, t, s):
+        return np.take_along_axis(s, self.p[:, t - 1], axis=1)
+
+    def jac(self, t, s):
+        B = s.shape[0]
+        J = np.zeros((B, self.d, self.d))
+        rows = np.arange(self.d)
+        for b in range(B):
+            J[b, rows, self.p[b, t - 1]] = 1.0
+        return J
+
+
 def from_problem(prob: dict):
     """Build the oracle dynamics for a problem dict made by ``synth``."""
     kind = prob["kind"]
@@ -247,4 +423,12 @@ def from_problem(prob: dict):
         return GRU(prob["W"], prob["U"], prob["x"])
     if kind == "linear":
         return Linear(prob["A"], prob["x"])
+    if kind == "rnn_tanh":
+        return MeanFieldRNN(prob["W"], prob["x"])
+    if kind == "langevin_2well":
+        return TwoWellLangevin(prob["params"], prob["dt"], prob["x"], d=prob["d"])
+    if kind == "lorenz96_dp5":
+        return Lorenz96(prob["params"], prob["dt"], prob["d"])
+    if kind == "permute":
+        return Permute(prob["x"])
     raise ValueError(kind)

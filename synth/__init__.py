@@ -18,6 +18,10 @@ none of them; they are stand-ins for its kinetic-ODE and GRU settings):
 * Untrained GRU cells with weights N(0, 1/d) and inputs N(0, 1)
   (Sec. 3.3 of the paper evaluates untrained GRUs the same way).
 * Ragged batches with lengths uniform on an integer range.
+* The second workloads of the thesis (its experiments' settings, synthetic):
+  mean-field RNN weights N(0, g^2/d) with zero diagonal and sinusoidal inputs,
+  a two-well Gaussian-mixture potential with Langevin noise draws, Lorenz-96
+  initial points, and uniformly random permutations for the S_d word problem.
 """
 from __future__ import annotations
 
@@ -172,6 +176,58 @@ def linear_lds(B: int, T: int, d: int, seed: int, spectral_radius: float = 0.9,
     x = rng.standard_normal((B, T, d))
     s0 = rng.standard_normal((B, d))
     return {"kind": "linear", "d": d, "d_in": d, "T": int(T), "A": A, "x": x, "s0": s0}
+
+
+def mean_field_rnn(B: int, T: int, d: int, g: float, seed: int, amp: float = 0.1,
+                   period: float = 50.0) -> dict:
+    """Mean-field RNN of the threshold experiment: W_ij iid N(0, g^2/d) with W_ii = 0
+    (shared by the batch), mild sinusoidal inputs u[b, t, i] = amp sin(2 pi t / period +
+    phase[b, i]) with uniform phases, and s0 ~ N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    W = rng.standard_normal((d, d)) * (g / np.sqrt(d))
+    np.fill_diagonal(W, 0.0)
+    phase = rng.uniform(0.0, 2.0 * np.pi, size=(B, 1, d))
+    t = np.arange(1, T + 1, dtype=np.float64).reshape(1, T, 1)
+    x = amp * np.sin(2.0 * np.pi * t / period + phase)
+    s0 = rng.standard_normal((B, d))
+    return {"kind": "rnn_tanh", "d": d, "T": int(T), "W": W, "x": x, "s0": s0, "g": g}
+
+
+def two_well(B: int, T: int, d: int, seed: int, eps: float = 0.01) -> dict:
+    """Two-well potential of the Langevin experiment: a mixture of two diagonal
+    Gaussians with equal weights centred at -1.4 and +1.6 on the separating axis
+    (coordinate 1, or 0 when d = 1) and 0 elsewhere; variances 0.5 on that axis and 1.0
+    on the others (anisotropic). Standard normal noise draws x [B][T][d], s0 ~ N(0, 1).
+    params [4d+2] = m1 | m2 | v1 | v2 | w1 | w2."""
+    rng = np.random.default_rng(seed)
+    ax = 1 if d >= 2 else 0
+    m1 = np.zeros(d)
+    m2 = np.zeros(d)
+    m1[ax], m2[ax] = -1.4, 1.6
+    v = np.ones(d)
+    v[ax] = 0.5
+    params = np.concatenate([m1, m2, v, v, [0.5, 0.5]])
+    x = rng.standard_normal((B, T, d))
+    s0 = rng.standard_normal((B, d))
+    return {"kind": "langevin_2well", "d": d, "T": int(T), "params": params, "dt": eps,
+            "x": x, "s0": s0}
+
+
+def lorenz96(B: int, d: int, seed: int, F: float = 8.0, dt: float = 0.01,
+             spread: float = 1.0) -> dict:
+    """Lorenz-96 with forcing F: initial points F + spread * N(0, 1) per coordinate."""
+    rng = np.random.default_rng(seed)
+    s0 = F + spread * rng.standard_normal((B, d))
+    return {"kind": "lorenz96_dp5", "d": d, "params": np.full(B, F), "dt": dt, "s0": s0}
+
+
+def word_problem(B: int, T: int, seed: int, d: int = 5) -> dict:
+    """Group word problem in S_d: one uniformly random permutation of range(d) per step
+    (as source indices, x [B][T][d]) and the distinct vocabulary s0 = (1, ..., d)."""
+    rng = np.random.default_rng(seed)
+    x = rng.permuted(np.broadcast_to(np.arange(d), (B, T, d)), axis=2).astype(np.float64)
+    s0 = np.broadcast_to(np.arange(1, d + 1, dtype=np.float64), (B, d)).copy()
+    return {"kind": "permute", "d": d, "T": int(T), "x": x, "s0": s0}
 
 
 def ragged_lengths(B: int, lo: int, hi: int, seed: int) -> np.ndarray:

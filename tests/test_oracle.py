@@ -459,3 +459,181 @@ def test_lle_mass_action_bounded_below_by_conservation():
     lower = np.log(np.abs((u0 * m).sum(axis=1)) / np.linalg.norm(m, axis=1)) / 800
     assert np.all(got >= lower - 1e-12)
     assert np.all(got <= 0.05)
+
+
+# --- second workloads: mean-field RNN, two-well Langevin, Lorenz-96, word problem ------
+
+def test_rnn_jacobian_matches_fd_and_has_zero_diagonal():
+    """A = W diag(1 - tanh^2) against central differences; with W_ii = 0 (no
+    self-coupling, Sec. ssc:exp_thresh) the diagonal of every step Jacobian is zero, so
+    quasi-DEER coincides with Jacobi on this family."""
+    p = synth.mean_field_rnn(3, 4, 6, 1.5, seed=2)
+    dyn = dynamics.MeanFieldRNN(p["W"], p["x"])
+    s = np.random.default_rng(3).standard_normal((3, 6))
+    J = dyn.jac(2, s)
+    assert np.abs(J - _fd_jac(lambda v: dyn.f(2, v), s)).max() < 1e-8
+    assert np.all(np.diagonal(J, axis1=1, axis2=2) == 0.0)
+
+
+def test_rnn_without_coupling_returns_its_input():
+    """g = 0 gives W = 0: s_t = u_t exactly."""
+    p = synth.mean_field_rnn(2, 20, 4, 0.0, seed=0)
+    s = newton.rollout(dynamics.MeanFieldRNN(p["W"], p["x"]), p["s0"], 20)
+    assert np.array_equal(s, p["x"])
+
+
+def test_rnn_threshold_between_predictable_and_chaotic():
+    """Sec. ssc:exp_thresh: the LLE rises with the gain g and changes sign; DEER needs a
+    handful of iterations for the predictable network and an order of magnitude more
+    for the chaotic one (Theorem PL-LLE)."""
+    from oracle import lle
+    u0 = np.ones((1, 16)) / 4.0
+    lles, its = [], []
+    for g in (0.5, 1.0, 2.0, 3.0):
+        p = synth.mean_field_rnn(1, 200, 16, g, seed=1)
+        dyn = dynamics.MeanFieldRNN(p["W"], p["x"])
+        s = newton.rollout(dyn, p["s0"], 200)
+        lles.append(float(lle.lle_estimate(dyn, p["s0"], s, u0)[0]))
+        if g in (0.5, 2.0):
+            its.append(int(newton.solve(dyn, p["s0"], 200, mode="full", tol=1e-10,
+                                        init="zeros")["iters"][0]))
+    assert all(a < b for a, b in zip(lles, lles[1:]))
+    assert lles[0] < 0.0 < lles[2]
+    assert its[0] <= 5 and its[1] >= 10 * its[0]
+
+
+def _mixture_potential(dyn, s):
+    """-log(w1 N(s; m1, v1) + w2 N(s; m2, v2)) straight from the Gaussian densities."""
+    def dens(m, v):
+        return np.exp(-0.5 * np.sum(np.log(2 * np.pi * v) + (s - m) ** 2 / v, axis=1))
+    return -np.log(dyn.w1 * dens(dyn.m1, dyn.v1) + dyn.w2 * dens(dyn.m2, dyn.v2))
+
+
+def test_langevin_gradient_and_jacobian_match_fd():
+    """grad phi against central differences of the potential written from the densities,
+    and A = I - eps Hess phi against central differences of f."""
+    p = synth.two_well(4, 3, 3, seed=1)
+    dyn = dynamics.TwoWellLangevin(p["params"], p["dt"], p["x"], d=3)
+    s = np.random.default_rng(2).standard_normal((4, 3)) * 1.5
+    h = 1e-5
+    fd = np.stack([(_mixture_potential(dyn, s + h * e) - _mixture_potential(dyn, s - h * e))
+                   / (2 * h) for e in np.eye(3)], axis=1)
+    assert np.abs(dyn.grad_phi(s) - fd).max() < 1e-8
+    J = dyn.jac(1, s)
+    assert np.abs(J - _fd_jac(lambda v: dyn.f(1, v), s)).max() < 1e-9
+    assert np.allclose(J, np.transpose(J, (0, 2, 1)))  # I - eps Hess is symmetric
+
+
+def test_langevin_one_component_is_ornstein_uhlenbeck():
+    """With w2 = 0 the potential is one Gaussian: f is affine with the constant Jacobian
+    I - eps diag(1/v1), so DEER converges in one iteration and Jacobi needs T."""
+    p = synth.two_well(2, 40, 2, seed=3)
+    prm = p["params"].copy()
+    prm[-1] = 0.0
+    dyn = dynamics.TwoWellLangevin(prm, p["dt"], p["x"], d=2)
+    s = np.random.default_rng(4).standard_normal((2, 2)) * 3.0
+    assert np.allclose(dyn.jac(1, s), np.diag(1.0 - p["dt"] / prm[4:6])[None], atol=1e-15)
+    exp = s - p["dt"] * (s - prm[0:2]) / prm[4:6] + np.sqrt(2 * p["dt"]) * p["x"][:, 0]
+    assert np.allclose(dyn.f(1, s), exp, rtol=1e-14, atol=1e-14)
+    r = newton.solve(dyn, p["s0"], 40, mode="full", tol=1e-12, init="zeros")
+    assert list(r["iters"]) == [1, 1]
+    rj = newton.solve(dyn, p["s0"], 40, mode="zero", tol=1e-12, init="zeros")
+    assert list(rj["iters"]) == [40, 40]
+
+
+def test_langevin_unstable_between_wells_contracting_inside():
+    """Sec. ssc:2well: the step is expanding between the wells (negative curvature of
+    phi) and contracting at the bottom of a well."""
+    p = synth.two_well(1, 1, 2, seed=0)
+    dyn = dynamics.TwoWellLangevin(p["params"], p["dt"], d=2)
+    mid = np.array([[0.0, 0.1]])
+    well = np.array([[0.0, 1.6]])
+    assert np.linalg.norm(dyn.jac(1, mid)[0], 2) > 1.0
+    assert np.linalg.norm(dyn.jac(1, well)[0], 2) < 1.0
+
+
+def test_langevin_deer_converges_fast_jacobi_needs_T():
+    """Sec. ssc:2well / sec:WellExp: from a random initial guess DEER converges in a few
+    iterations, growing sublinearly in T; Picard takes far fewer than T and Jacobi
+    exactly T."""
+    its = {}
+    for T in (100, 400):
+        p = synth.two_well(1, T, 2, seed=0)
+        dyn = dynamics.TwoWellLangevin(p["params"], p["dt"], p["x"], d=2)
+        guess = synth.targets_noise((1, T, 2), seed=5)
+        its[T] = {m: int(newton.solve(dyn, p["s0"], T, mode=m, tol=1e-10, init="user",
+                                      user=guess)["iters"][0])
+                  for m in ("full", "identity", "zero")}
+    assert its[100]["full"] <= 10 and its[400]["full"] <= 2 * its[100]["full"]
+    assert its[400]["identity"] < 400 // 2
+    assert its[100]["zero"] == 100 and its[400]["zero"] == 400
+
+
+def test_dp5_tableau_satisfies_the_order_conditions():
+    """Every coefficient of the Dormand-Prince tableau is pinned by the row-sum condition
+    c = A 1 and by the 17 Butcher order conditions up to order five (rooted trees)."""
+    A, b, c = dynamics.DP5_A, dynamics.DP5_B, dynamics.DP5_C
+    assert np.allclose(A.sum(axis=1), c, atol=1e-15)
+    Ac, Ac2, Ac3 = A @ c, A @ c ** 2, A @ c ** 3
+    conds = [
+        (b.sum(), 1.0), (b @ c, 1 / 2),
+        (b @ c ** 2, 1 / 3), (b @ Ac, 1 / 6),
+        (b @ c ** 3, 1 / 4), (b @ (c * Ac), 1 / 8), (b @ Ac2, 1 / 12), (b @ (A @ Ac), 1 / 24),
+        (b @ c ** 4, 1 / 5), (b @ (c ** 2 * Ac), 1 / 10), (b @ (c * Ac2), 1 / 15),
+        (b @ (c * (A @ Ac)), 1 / 30), (b @ (Ac * Ac), 1 / 20), (b @ Ac3, 1 / 20),
+        (b @ (A @ (c * Ac)), 1 / 40), (b @ (A @ Ac2), 1 / 60), (b @ (A @ (A @ Ac)), 1 / 120),
+    ]
+    for got, want in conds:
+        assert abs(got - want) < 1e-14
+
+
+def test_lorenz96_step_order_equilibrium_and_jacobian():
+    """One DP5 step has local error O(h^6) against a tight reference integration (the
+    ratio for h and h/2 approaches 64); x = F 1 is an equilibrium (f leaves it
+    unchanged); the stage chain-rule Jacobian matches central differences."""
+    from scipy.integrate import solve_ivp
+    p = synth.lorenz96(1, 5, seed=0)
+    errs = []
+    for h in (0.02, 0.01):
+        dyn = dynamics.Lorenz96(p["params"], h, 5)
+        ref = solve_ivp(lambda t, x: dyn.rhs(x[None])[0], (0.0, h), p["s0"][0], method="DOP853",
+                        rtol=1e-13, atol=1e-13).y[:, -1]
+        errs.append(np.abs(dyn.f(1, p["s0"]) - ref).max())
+    assert errs[0] / errs[1] > 40.0
+    dyn = dynamics.Lorenz96(p["params"], 0.01, 5)
+    eq = np.full((1, 5), 8.0)
+    assert np.array_equal(dyn.f(1, eq), eq)
+    s = p["s0"] + np.random.default_rng(1).standard_normal((1, 5))
+    assert np.abs(dyn.jac(1, s) - _fd_jac(lambda v: dyn.f(1, v), s)).max() < 1e-8
+
+
+def test_word_problem_rollout_is_the_group_product():
+    """Prop. cayley: s_t is s_0 permuted by the running product of the step
+    permutations (composed here as index arrays, not through f), so s_T is a
+    permutation of s_0; every step Jacobian is the permutation matrix of its input."""
+    p = synth.word_problem(3, 50, seed=0)
+    dyn = dynamics.Permute(p["x"])
+    s = newton.rollout(dyn, p["s0"], 50)
+    for b in range(3):
+        idx = np.arange(5)
+        for t in range(50):
+            idx = idx[p["x"][b, t].astype(int)]
+            assert np.array_equal(s[b, t], p["s0"][b, idx])
+        assert np.array_equal(np.sort(s[b, -1]), np.sort(p["s0"][b]))
+    J = dyn.jac(7, s[:, 5])
+    assert np.array_equal(J.sum(axis=1), np.ones((3, 5)))
+    assert np.array_equal(J.sum(axis=2), np.ones((3, 5)))
+    assert np.array_equal(np.einsum("bij,bj->bi", J, s[:, 5]), dyn.f(7, s[:, 5]))
+
+
+def test_word_problem_newton_one_iteration_others_near_T():
+    """Sec. sec:GrpWordProb: the recursion is linear, so one Newton iteration solves it;
+    quasi-Newton, Picard and Jacobi need a number of iterations close to T."""
+    T = 32
+    p = synth.word_problem(2, T, seed=1)
+    dyn = dynamics.Permute(p["x"])
+    its = {m: newton.solve(dyn, p["s0"], T, mode=m, tol=1e-12, init="zeros")["iters"]
+           for m in ("full", "diag", "identity", "zero")}
+    assert list(its["full"]) == [1, 1]
+    for m in ("diag", "identity", "zero"):
+        assert np.all(its[m] >= T // 2)
