@@ -308,6 +308,27 @@ def adjoint_measurement(deer, N, lib, dev, stream):
             "grad_finite": bool(torch.isfinite(dk).all())}
 
 
+def dyn_sub(deer, p, d, dev, n=32):
+    """Kinetics of the first n systems of a problem (autotuning subset)."""
+    import torch
+    return deer.Dynamics.massaction(
+        torch.tensor(p["topology"][:n], dtype=torch.int32, device=dev),
+        torch.tensor(p["params"][:n], dtype=torch.float64, device=dev), d, p["dt"])
+
+
+def _time_solve(deer, dyn, s0, offsets, opts, stream):
+    """Milliseconds of one batched solve (after one warm-up), CUDA events."""
+    import torch
+    deer.deer_solve_batched(dyn, s0, offsets, stream=stream, **opts)
+    torch.cuda.synchronize()
+    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    e0.record(stream)
+    deer.deer_solve_batched(dyn, s0, offsets, stream=stream, **opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
 def ragged_mixed_measurement(deer, N, lib, dev, stream, B=1000):
     """Ragged mixed-precision workload: d=16 kinetic networks (24 reactions), lengths
     uniform on [1000, 100000], RK4 dt=1e-3, bf16 Jacobians with float32 scan accumulation,
@@ -326,6 +347,17 @@ def ragged_mixed_measurement(deer, N, lib, dev, stream, B=1000):
     dyn = deer.Dynamics.massaction(topo, k, d, p["dt"])
     opts = dict(jac="full", tol=1e-10, prec="mixed_bf16", init="zeros", reset=True,
                 window=True)
+    # chunk length chosen by the autotuner on a 32-trajectory subset of the same
+    # distribution (not timed), then used for the whole group
+    from paper_2603_16850_gb300 import autotune
+    sub_off = off[:33] - off[0]
+    t0 = time.perf_counter()
+    timings = autotune.pick_best(
+        (32, 64, 128, 256),
+        lambda L: _time_solve(deer, dyn_sub(deer, p, d, dev), s0[:32].contiguous(), sub_off,
+                              dict(opts, chunk=L), stream))
+    tune_s = time.perf_counter() - t0
+    opts["chunk"] = timings["chunk"]
     ntot = int(off[-1])
     ws_ = torch.empty(deer.deer_workspace_bytes(dyn, B, ntot, **opts), dtype=torch.uint8,
                       device=dev)
@@ -345,6 +377,8 @@ def ragged_mixed_measurement(deer, N, lib, dev, stream, B=1000):
     lin_s = prof.ms[1] / 1000.0
     return {"workload": f"ragged mass action d=16 R=24, T ~ U[1000,100000], B={B} (one of "
                         "ten groups), bf16 Jacobians / fp32 scan / fp64 residual",
+            "chunk": {"chosen": timings["chunk"], "tuning_ms": timings["timings"],
+                      "tuning_s": tune_s, "how": "autotune.pick_best on 32 trajectories"},
             "rows_linearized": int(lin_rows), "rows_scanned": int(prof.rows[3]),
             "linearize_rows_per_s": lin_rows / max(lin_s, 1e-12),
             "linearize_tflops": lin_rows * MIXED_LIN_FLOP_PER_ROW / max(lin_s, 1e-12) / 1e12,
