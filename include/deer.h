@@ -63,7 +63,32 @@ typedef enum {
      [Wz, Wr, Wh] each [d][d_in], then [Uz, Ur, Uh] each [d][d]. */
   DEER_F_GRU = 3,
   /* Affine recurrence s_t = A s_{t-1} + x_t (x may be NULL). params (shared): A [d][d]. */
-  DEER_F_LINEAR = 4
+  DEER_F_LINEAR = 4,
+  /* Mean-field RNN of the predictability threshold experiment (Sec. ssc:exp_thresh):
+     s_t = W tanh(s_{t-1}) + u_t with u_t the row of x (input size d; x may be NULL for
+     u = 0). params: W [d][d], per sequence (params_stride >= d*d) or shared. The thesis
+     draws W_ij ~ N(0, g^2/d) with W_ii = 0; any W is accepted. d in {1,2,4,8,16,32}. */
+  DEER_F_RNN_TANH = 5,
+  /* Discretised Langevin dynamics (Eq. langevin) in a two-component Gaussian-mixture
+     potential phi(s) = -log(w1 N(s; m1, diag v1) + w2 N(s; m2, diag v2)):
+     s_t = s_{t-1} - dt grad phi(s_{t-1}) + sqrt(2 dt) w_t, with w_t the row of x (input
+     size d; standard normal draws; x may be NULL for the noise-free drift). Its Jacobian is
+     I - dt Hess phi. params per sequence (params_stride >= 4d+2) or shared:
+     [m1 (d) | m2 (d) | v1 (d) | v2 (d) | w1 | w2] with v > 0, w >= 0, w1 + w2 > 0.
+     d in {1,2,4,8,16,32}. */
+  DEER_F_LANGEVIN_2WELL = 6,
+  /* Lorenz-96 dx_i/dt = (x_{i+1} - x_{i-2}) x_{i-1} - x_i + F (indices modulo d), one fixed
+     step dt of the fifth-order solution of the Dormand-Prince 5(4) pair (no step-size
+     control: f_t must be one fixed map). params: [F], per sequence (params_stride >= 1) or
+     shared. d in {4, 5, 8}. */
+  DEER_F_LORENZ96_DP5 = 7,
+  /* Input-selected permutation, the group word problem as a linear recurrence
+     (Prop. cayley): s_t[i] = s_{t-1}[x_t[i]] with x_t the row of x holding d source
+     indices stored as exact integers in [0, d) (input size d; x required). A_t is the
+     corresponding permutation (selection) matrix. An index that is not an integer in
+     [0, d) makes that entry NaN, which the solver reports as DEER_ERR_NONFINITE.
+     params: unused (any non-NULL pointer). d in {2,4,5,8,16,32}. */
+  DEER_F_PERMUTE = 8
 } deer_fkind;
 
 /* Transition matrix A~_t of the linear recurrence solved per iteration

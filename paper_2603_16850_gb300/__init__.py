@@ -65,6 +65,36 @@ class Dynamics:
         """s_t = A s_{t-1} + x_t with A [d][d] shared by the batch."""
         return Dynamics("linear", A.shape[0], A.contiguous(), d_in=A.shape[0])
 
+    @staticmethod
+    def rnn_tanh(W: torch.Tensor) -> "Dynamics":
+        """Mean-field RNN s_t = W tanh(s_{t-1}) + u_t; W [d][d] shared or [B][d][d] per
+        sequence; the inputs u_t are the rows of x (or none)."""
+        d = W.shape[-1]
+        stride = d * d if W.dim() == 3 and W.shape[0] > 1 else 0
+        return Dynamics("rnn_tanh", d, W.reshape(-1).contiguous(), d_in=d, params_stride=stride)
+
+    @staticmethod
+    def langevin_2well(params: torch.Tensor, eps: float) -> "Dynamics":
+        """Langevin step of size eps in the two-Gaussian potential; params [4d+2] shared or
+        [B][4d+2] = m1 | m2 | v1 | v2 | w1 | w2; the noise draws are the rows of x."""
+        n = params.shape[-1]
+        d = (n - 2) // 4
+        stride = n if params.dim() == 2 and params.shape[0] > 1 else 0
+        return Dynamics("langevin_2well", d, params.reshape(-1).contiguous(), d_in=d, dt=eps,
+                        params_stride=stride)
+
+    @staticmethod
+    def lorenz96(F: torch.Tensor, d: int, dt: float) -> "Dynamics":
+        """Lorenz-96 with forcing F ([1] shared or [B]), one Dormand-Prince step dt per step."""
+        stride = 1 if F.numel() > 1 else 0
+        return Dynamics("lorenz96_dp5", d, F.reshape(-1).contiguous(), dt=dt,
+                        params_stride=stride)
+
+    @staticmethod
+    def permute(d: int, dtype=torch.float64, device="cuda") -> "Dynamics":
+        """Input-selected permutation s_t[i] = s_{t-1}[x_t[i]] (x holds the indices)."""
+        return Dynamics("permute", d, torch.zeros(1, dtype=dtype, device=device), d_in=d)
+
     def to(self, device) -> "Dynamics":
         return Dynamics(self.kind, self.d, self.params.to(device), self.d_in, self.n_reactions,
                         self.dt, self.params_stride,
@@ -250,14 +280,17 @@ def deer_rollout(dyn: Dynamics, s0: torch.Tensor, T: int = 0, x=None, *, offsets
 
 def deer_grad(dyn: Dynamics, s0, T, s_star, dl_ds, x=None, *, prec="fp64", chunk=0,
               stream=None, workspace=None, want_ds0=True):
-    """Adjoint gradient at the converged trajectory. Returns (dl/dparams [B][P], dl/ds0)."""
+    """Adjoint gradient at the converged trajectory. Returns (dl/dparams [B][P], dl/ds0);
+    dl/dparams is None for kinds without per-sequence trainable parameters (only the
+    Brusselator's (a, b) and the mass-action rate constants are differentiated)."""
     lib = N.load()
     B = s0.shape[0]
     dt = _dtype(prec)
     o = _options(**_opt_defaults(dict(prec=prec, chunk=chunk)))
     cdyn = dyn.c_struct()
     P = dyn.params_stride if dyn.params_stride else dyn.params.numel()
-    dparams = torch.zeros((B, P), dtype=dt, device=s0.device)
+    trainable = dyn.kind in ("brusselator_euler", "massaction_euler", "massaction_rk4")
+    dparams = torch.zeros((B, P), dtype=dt, device=s0.device) if trainable else None
     ds0 = torch.zeros((B, dyn.d), dtype=dt, device=s0.device) if want_ds0 else None
     need = lib.deer_grad_workspace_bytes(C.byref(cdyn), B, int(T), C.byref(o))
     if workspace is None or workspace.numel() < need:
@@ -337,4 +370,5 @@ class DeerFunction(torch.autograd.Function):
     def backward(ctx, g):
         s0, s = ctx.saved_tensors
         dp, ds0 = deer_grad(ctx.dyn, s0, ctx.T, s, g.contiguous(), ctx.x, prec=ctx.prec)
-        return dp.reshape(ctx.dyn.params.shape), ds0, None, None, None, None
+        return (None if dp is None else dp.reshape(ctx.dyn.params.shape)), ds0, None, None, \
+            None, None

@@ -16,7 +16,8 @@ DEER_OK, DEER_NOT_CONVERGED = 0, 1
 DEER_ERR_INVALID, DEER_ERR_CUDA, DEER_ERR_NONFINITE = -1, -2, -3
 DEER_ERR_WORKSPACE, DEER_ERR_TIMEOUT, DEER_ERR_UNSUPPORTED = -4, -5, -6
 
-KIND = {"brusselator_euler": 0, "massaction_euler": 1, "massaction_rk4": 2, "gru": 3, "linear": 4}
+KIND = {"brusselator_euler": 0, "massaction_euler": 1, "massaction_rk4": 2, "gru": 3, "linear": 4,
+        "rnn_tanh": 5, "langevin_2well": 6, "lorenz96_dp5": 7, "permute": 8}
 JAC = {"full": 0, "diag": 1, "identity": 2, "zero": 3}
 DAMP = {"none": 0, "elk": 1, "scale": 2, "clip": 3}
 INIT = {"zeros": 0, "s0": 1, "jacobi": 2, "user": 3}

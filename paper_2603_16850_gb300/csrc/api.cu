@@ -82,7 +82,31 @@ static bool d_supported(int kind, int d, int jac) {
   const bool p2 = d == 1 || d == 2 || d == 4 || d == 8 || d == 16 || d == 32;
   if (kind == DEER_F_GRU) return p2 || (d == 64 && jac != DEER_JAC_FULL);
   if (kind == DEER_F_MASSACTION_EULER || kind == DEER_F_MASSACTION_RK4) return p2 && d >= 2;
+  if (kind == DEER_F_LORENZ96_DP5) return d == 4 || d == 5 || d == 8;
+  if (kind == DEER_F_PERMUTE) return (p2 && d >= 2) || d == 5;
   return p2;
+}
+
+// Kinds whose input rows have d entries (the GRU's have d_in).
+static bool input_is_d(int kind) {
+  return kind == DEER_F_LINEAR || kind == DEER_F_RNN_TANH || kind == DEER_F_LANGEVIN_2WELL ||
+         kind == DEER_F_PERMUTE;
+}
+
+// Kinds whose f_t cannot be evaluated without inputs.
+static bool needs_x(int kind) { return kind == DEER_F_GRU || kind == DEER_F_PERMUTE; }
+
+// Smallest per-sequence parameter stride of a kind (0: no parameters read).
+static int64_t min_param_stride(const deer_dynamics* f) {
+  switch (f->kind) {
+    case DEER_F_BRUSSELATOR_EULER: return 2;
+    case DEER_F_MASSACTION_EULER:
+    case DEER_F_MASSACTION_RK4: return f->n_reactions;
+    case DEER_F_RNN_TANH: return (int64_t)f->d * f->d;
+    case DEER_F_LANGEVIN_2WELL: return 4 * (int64_t)f->d + 2;
+    case DEER_F_LORENZ96_DP5: return 1;
+    default: return 0;
+  }
 }
 
 // Everything the solver carves out of the caller's workspace.
@@ -201,7 +225,7 @@ static DynView<real> make_view(const deer_dynamics* f, const void* x, char* ws,
   DynView<real> v;
   v.kind = f->kind;
   v.d = f->d;
-  v.d_in = f->kind == DEER_F_LINEAR ? f->d : f->d_in;
+  v.d_in = input_is_d(f->kind) ? f->d : f->d_in;
   v.R = f->n_reactions;
   v.dt = (real)f->dt;
   v.params = static_cast<const real*>(f->params);
@@ -217,7 +241,7 @@ static DynView<real> make_view(const deer_dynamics* f, const void* x, char* ws,
 
 static deer_status check_common(const deer_dynamics* f, const deer_options* o) {
   if (!f || !o) return DEER_ERR_INVALID;
-  if (f->kind < 0 || f->kind > DEER_F_LINEAR) return DEER_ERR_INVALID;
+  if (f->kind < 0 || f->kind > DEER_F_PERMUTE) return DEER_ERR_INVALID;
   if (o->jac < 0 || o->jac > DEER_JAC_ZERO) return DEER_ERR_INVALID;
   if (o->damp < 0 || o->damp > DEER_DAMP_CLIP) return DEER_ERR_INVALID;
   if (o->init < 0 || o->init > DEER_INIT_USER) return DEER_ERR_INVALID;
@@ -244,7 +268,9 @@ static deer_status check_common(const deer_dynamics* f, const deer_options* o) {
     if (f->topology_stride % 4 != 0) return DEER_ERR_INVALID;
   }
   if (f->kind == DEER_F_GRU && f->d_in <= 0) return DEER_ERR_INVALID;
-  if (f->kind == DEER_F_BRUSSELATOR_EULER && f->params_stride != 0 && f->params_stride < 2)
+  if (f->params_stride < 0 || (f->params_stride != 0 && f->params_stride < min_param_stride(f)))
+    return DEER_ERR_INVALID;
+  if ((f->kind == DEER_F_LANGEVIN_2WELL || f->kind == DEER_F_LORENZ96_DP5) && !(f->dt > 0.0))
     return DEER_ERR_INVALID;
   return DEER_OK;
 }
@@ -666,7 +692,7 @@ static deer_status solve_dispatch(const deer_dynamics* f, int64_t batch, const i
   if (batch < 0) return DEER_ERR_INVALID;
   if (batch == 0) return DEER_OK;
   if (!s0 || !s_out) return DEER_ERR_INVALID;
-  if ((f->kind == DEER_F_GRU) && !x) return DEER_ERR_INVALID;
+  if (needs_x(f->kind) && !x) return DEER_ERR_INVALID;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (opt->prec == DEER_FP32)
     return solve_impl<float>(f, batch, off, s0, x, s_out, opt, ws, wsb, st, info);
@@ -707,7 +733,7 @@ deer_status deer_rollout(const deer_dynamics* f, int64_t batch, int64_t T,
   if (batch < 0 || (!offsets && T < 0)) return DEER_ERR_INVALID;
   if (batch == 0) return DEER_OK;
   if (!s0 || !s_out) return DEER_ERR_INVALID;
-  if (f->kind == DEER_F_GRU && !x) return DEER_ERR_INVALID;
+  if (needs_x(f->kind) && !x) return DEER_ERR_INVALID;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   Layout ly{};
   cudaError_t e;
@@ -911,7 +937,7 @@ deer_status deer_lle(const deer_dynamics* f, int64_t batch, int64_t T, const voi
   if (c != DEER_OK) return c;
   if (batch == 0 || T == 0) return DEER_OK;
   if (!s0 || !s || !u0 || !lle_out) return DEER_ERR_INVALID;
-  if (f->kind == DEER_F_GRU && !x) return DEER_ERR_INVALID;
+  if (needs_x(f->kind) && !x) return DEER_ERR_INVALID;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (prec == DEER_FP32)
     return lle_impl<float>(f, batch, T, s0, x, s, u0, lle_out, &o, workspace, workspace_bytes,
@@ -934,7 +960,7 @@ deer_status deer_grad(const deer_dynamics* f, int64_t batch, int64_t T, const vo
   if (batch < 0 || T < 0) return DEER_ERR_INVALID;
   if (batch == 0 || T == 0) return DEER_OK;
   if (!s0 || !s_star || !dl_ds) return DEER_ERR_INVALID;
-  if (f->kind == DEER_F_GRU && !x) return DEER_ERR_INVALID;
+  if (needs_x(f->kind) && !x) return DEER_ERR_INVALID;
   const bool per_seq = f->kind == DEER_F_BRUSSELATOR_EULER ||
                        f->kind == DEER_F_MASSACTION_EULER || f->kind == DEER_F_MASSACTION_RK4;
   if (dl_dparams && !per_seq) return DEER_ERR_UNSUPPORTED;
@@ -1188,7 +1214,7 @@ deer_status deer_solve_noalloc(const deer_dynamics* f, int64_t batch, int64_t T,
   if (batch < 0 || T < 0) return DEER_ERR_INVALID;
   if (batch == 0 || T == 0) return DEER_OK;
   if (!s0 || !s_out) return DEER_ERR_INVALID;
-  if (f->kind == DEER_F_GRU && !x) return DEER_ERR_INVALID;
+  if (needs_x(f->kind) && !x) return DEER_ERR_INVALID;
   void* scratch = nullptr;
   cudaError_t e = noalloc_scratch(&scratch);
   if (e != cudaSuccess) return cuda_fail(e, "deer_solve_noalloc scratch lookup");

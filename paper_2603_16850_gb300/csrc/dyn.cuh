@@ -239,6 +239,211 @@ __device__ __forceinline__ void lin_eval(const DynView<real>& dv, int64_t row, c
   }
 }
 
+// ----------------------------------------------------------------------------
+// Mean-field RNN: f(s) = W tanh(s) + u_t, A = W diag(1 - tanh(s)^2) (Sec. ssc:exp_thresh).
+// JM: 0 = value, 1 = full Jacobian into A, 2 = diagonal into Ad.
+// ----------------------------------------------------------------------------
+template <class real, int D, int JM>
+__device__ __forceinline__ void rnn_eval(const DynView<real>& dv, int64_t seq, int64_t row,
+                                         const real* s, real* F, real (*A)[D], real* Ad) {
+  const real* W = dv.params + seq * dv.pstride;
+  real th[D];
+#pragma unroll Unroll<D>::n
+  for (int j = 0; j < D; ++j) th[j] = tanh(s[j]);
+#pragma unroll Unroll<D>::n
+  for (int i = 0; i < D; ++i) {
+    real v = dv.x ? __ldg(dv.x + row * D + i) : real(0);
+#pragma unroll Unroll<D>::n
+    for (int j = 0; j < D; ++j) {
+      const real w = __ldg(W + i * D + j);
+      v += w * th[j];
+      if constexpr (JM == 1) A[i][j] = w * (real(1) - th[j] * th[j]);
+    }
+    F[i] = v;
+    if constexpr (JM == 2) Ad[i] = __ldg(W + i * D + i) * (real(1) - th[i] * th[i]);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Langevin step in a two-component Gaussian-mixture potential (Eq. langevin):
+//   f(s) = s - dt grad phi(s) + sqrt(2 dt) w_t,  phi = -log(w1 N1 + w2 N2),
+// with responsibilities g_k = w_k N_k / (w1 N1 + w2 N2) taken from the log-densities
+// l_k = log w_k - (1/2) sum_i [log v_ki + (s_i - m_ki)^2 / v_ki] (the 2 pi terms cancel).
+//   grad phi = g1 (s - m1)/v1 + g2 (s - m2)/v2
+//   Hess phi = diag(g1/v1 + g2/v2) - g1 g2 e e^T,  e = (s - m2)/v2 - (s - m1)/v1
+// (the covariance of the component scores under the responsibilities), A = I - dt Hess.
+// ----------------------------------------------------------------------------
+template <class real, int D, int JM>
+__device__ __forceinline__ void langevin_eval(const DynView<real>& dv, int64_t seq,
+                                              int64_t row, const real* s, real* F,
+                                              real (*A)[D], real* Ad) {
+  const real* p = dv.params + seq * dv.pstride;
+  const real* m1 = p;
+  const real* m2 = p + D;
+  const real* v1 = p + 2 * D;
+  const real* v2 = p + 3 * D;
+  real q1 = real(0), q2 = real(0);
+  real z1[D], z2[D];  // (s - m_k) / v_k
+#pragma unroll Unroll<D>::n
+  for (int i = 0; i < D; ++i) {
+    const real a1 = s[i] - __ldg(m1 + i), a2 = s[i] - __ldg(m2 + i);
+    const real iv1 = real(1) / __ldg(v1 + i), iv2 = real(1) / __ldg(v2 + i);
+    z1[i] = a1 * iv1;
+    z2[i] = a2 * iv2;
+    q1 += log(__ldg(v1 + i)) + a1 * z1[i];
+    q2 += log(__ldg(v2 + i)) + a2 * z2[i];
+  }
+  const real l1 = log(__ldg(p + 4 * D)) - real(0.5) * q1;
+  const real l2 = log(__ldg(p + 4 * D + 1)) - real(0.5) * q2;
+  const real g1 = real(1) / (real(1) + exp(l2 - l1));
+  const real g2 = real(1) / (real(1) + exp(l1 - l2));
+  const real dt = dv.dt;
+  const real amp = sqrt(real(2) * dt);
+#pragma unroll Unroll<D>::n
+  for (int i = 0; i < D; ++i) {
+    const real grad = g1 * z1[i] + g2 * z2[i];
+    const real w = dv.x ? __ldg(dv.x + row * D + i) : real(0);
+    F[i] = s[i] - dt * grad + amp * w;
+  }
+  if constexpr (JM != 0) {
+    const real g12 = g1 * g2;
+#pragma unroll Unroll<D>::n
+    for (int i = 0; i < D; ++i) {
+      const real ei = z2[i] - z1[i];
+      const real hii = g1 / __ldg(v1 + i) + g2 / __ldg(v2 + i);
+      if constexpr (JM == 2) {
+        Ad[i] = real(1) - dt * (hii - g12 * ei * ei);
+      } else {
+#pragma unroll Unroll<D>::n
+        for (int j = 0; j < D; ++j) {
+          const real h = (i == j ? hii : real(0)) - g12 * ei * (z2[j] - z1[j]);
+          A[i][j] = (i == j ? real(1) : real(0)) - dt * h;
+        }
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Lorenz-96, one fixed step of the fifth-order Dormand-Prince solution. Stages
+//   Y_k = s + h sum_{j<k} a_kj k_j,  k_k = g(Y_k),  f(s) = s + h sum_k b_k k_k,
+// and the step Jacobian column by column in forward mode: for the tangent e_c,
+//   dY_k = e_c + h sum_{j<k} a_kj dk_j,  dk_k = g'(Y_k) dY_k,  A e_c = e_c + h sum_k b_k dk_k,
+// where g'(x) v = (v_{i+1} - v_{i-2}) x_{i-1} + (x_{i+1} - x_{i-2}) v_{i-1} - v_i.
+// Coefficients: the published Dormand-Prince (1980) tableau; the seventh stage carries no
+// weight in the fifth-order solution and is not evaluated.
+// ----------------------------------------------------------------------------
+struct DP5 {
+  static constexpr int S = 6;
+  __device__ static constexpr double a(int k, int j) {
+    return k == 1 ? (j == 0 ? 1.0 / 5 : 0.0)
+         : k == 2 ? (j == 0 ? 3.0 / 40 : j == 1 ? 9.0 / 40 : 0.0)
+         : k == 3 ? (j == 0 ? 44.0 / 45 : j == 1 ? -56.0 / 15 : j == 2 ? 32.0 / 9 : 0.0)
+         : k == 4 ? (j == 0 ? 19372.0 / 6561 : j == 1 ? -25360.0 / 2187
+                    : j == 2 ? 64448.0 / 6561 : j == 3 ? -212.0 / 729 : 0.0)
+         : k == 5 ? (j == 0 ? 9017.0 / 3168 : j == 1 ? -355.0 / 33 : j == 2 ? 46732.0 / 5247
+                    : j == 3 ? 49.0 / 176 : j == 4 ? -5103.0 / 18656 : 0.0)
+         : 0.0;
+  }
+  __device__ static constexpr double b(int k) {
+    return k == 0 ? 35.0 / 384 : k == 1 ? 0.0 : k == 2 ? 500.0 / 1113 : k == 3 ? 125.0 / 192
+         : k == 4 ? -2187.0 / 6784 : k == 5 ? 11.0 / 84 : 0.0;
+  }
+};
+
+template <class real, int D>
+__device__ __forceinline__ void l96_rhs(const real* x, real F, real* g) {
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+    g[i] = (x[(i + 1) % D] - x[(i + D - 2) % D]) * x[(i + D - 1) % D] - x[i] + F;
+}
+
+template <class real, int D>
+__device__ __forceinline__ void l96_jvp(const real* x, const real* v, real* out) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const int ip = (i + 1) % D, im = (i + D - 1) % D, im2 = (i + D - 2) % D;
+    out[i] = (v[ip] - v[im2]) * x[im] + (x[ip] - x[im2]) * v[im] - v[i];
+  }
+}
+
+template <class real, int D, int JM>
+__device__ __forceinline__ void l96_eval(const DynView<real>& dv, int64_t seq, const real* s,
+                                         real* F, real (*A)[D], real* Ad) {
+  static_assert(D >= 4, "Lorenz-96 needs at least four coordinates");
+  const real Fc = __ldg(dv.params + seq * dv.pstride);
+  const real h = dv.dt;
+  real Y[DP5::S][D], k[DP5::S][D];
+#pragma unroll
+  for (int st = 0; st < DP5::S; ++st) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      real y = s[i];
+#pragma unroll
+      for (int j = 0; j < st; ++j) y += h * real(DP5::a(st, j)) * k[j][i];
+      Y[st][i] = y;
+    }
+    l96_rhs<real, D>(Y[st], Fc, k[st]);
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    real acc = real(0);
+#pragma unroll
+    for (int st = 0; st < DP5::S; ++st) acc += real(DP5::b(st)) * k[st][i];
+    F[i] = s[i] + h * acc;
+  }
+  if constexpr (JM != 0) {
+#pragma unroll 1
+    for (int c = 0; c < D; ++c) {
+      real dk[DP5::S][D];
+#pragma unroll
+      for (int st = 0; st < DP5::S; ++st) {
+        real dy[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          real v = i == c ? real(1) : real(0);
+#pragma unroll
+          for (int j = 0; j < st; ++j) v += h * real(DP5::a(st, j)) * dk[j][i];
+          dy[i] = v;
+        }
+        l96_jvp<real, D>(Y[st], dy, dk[st]);
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        real acc = real(0);
+#pragma unroll
+        for (int st = 0; st < DP5::S; ++st) acc += real(DP5::b(st)) * dk[st][i];
+        const real v = (i == c ? real(1) : real(0)) + h * acc;
+        if constexpr (JM == 1) A[i][c] = v;
+        if constexpr (JM == 2) if (i == c) Ad[c] = v;
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Input-selected permutation (Prop. cayley): F_i = s[x_t[i]], A_t[i][j] = [j == x_t[i]].
+// An index that is not an integer in [0, D) yields NaN for that entry.
+// ----------------------------------------------------------------------------
+template <class real, int D, int JM>
+__device__ __forceinline__ void perm_eval(const DynView<real>& dv, int64_t row, const real* s,
+                                          real* F, real (*A)[D], real* Ad) {
+#pragma unroll Unroll<D>::n
+  for (int i = 0; i < D; ++i) {
+    const real xv = __ldg(dv.x + row * D + i);
+    const bool ok = xv >= real(0) && xv < real(D) && xv == real((int)xv);
+    const int src = ok ? (int)xv : -1;
+    real v = ok ? real(0) : real(NAN);
+#pragma unroll Unroll<D>::n
+    for (int j = 0; j < D; ++j) {
+      if (j == src) v = s[j];
+      if constexpr (JM == 1) A[i][j] = j == src ? real(1) : real(0);
+    }
+    F[i] = v;
+    if constexpr (JM == 2) Ad[i] = src == i ? real(1) : real(0);
+  }
+}
+
 // Dispatch on the dynamics kind (compile time). JM: 0 = value only, 1 = full Jacobian
 // into A, 2 = diagonal of the Jacobian into Ad.
 template <class real, int D, int KIND, int JM>
@@ -246,6 +451,14 @@ __device__ __forceinline__ void eval_f(const DynView<real>& dv, int64_t seq, int
                                        const real* s, real* F, real (*A)[D], real* Ad) {
   if constexpr (KIND == DEER_F_GRU) {
     gru_eval<real, D>(dv, row, s, F, A, Ad, JM);
+  } else if constexpr (KIND == DEER_F_RNN_TANH) {
+    rnn_eval<real, D, JM>(dv, seq, row, s, F, A, Ad);
+  } else if constexpr (KIND == DEER_F_LANGEVIN_2WELL) {
+    langevin_eval<real, D, JM>(dv, seq, row, s, F, A, Ad);
+  } else if constexpr (KIND == DEER_F_LORENZ96_DP5) {
+    if constexpr (D >= 4) l96_eval<real, D, JM>(dv, seq, s, F, A, Ad);
+  } else if constexpr (KIND == DEER_F_PERMUTE) {
+    perm_eval<real, D, JM>(dv, row, s, F, A, Ad);
   } else {
     real Af[JM == 2 ? D : 1][JM == 2 ? D : 1];
     real (*Aw)[D] = nullptr;

@@ -284,6 +284,7 @@ cudaError_t launch_dense_scan(const DenseScanArgs<real>& a, cudaStream_t st) {
     case 1: dense_launch<real, 1>(a, st); break;
     case 2: dense_launch<real, 2>(a, st); break;
     case 4: dense_launch<real, 4>(a, st); break;
+    case 5: dense_launch<real, 5>(a, st); break;
     case 8: dense_launch<real, 8>(a, st); break;
     case 16: dense_launch_wide<real, 16>(a, st); break;
     case 32: dense_launch_wide<real, 32>(a, st); break;
@@ -620,6 +621,7 @@ cudaError_t launch_adjoint_scan(const AdjScanArgs<real>& a, cudaStream_t st) {
     case 1: adj_launch<real, 1>(a, st); break;
     case 2: adj_launch<real, 2>(a, st); break;
     case 4: adj_launch<real, 4>(a, st); break;
+    case 5: adj_launch<real, 5>(a, st); break;
     case 8: adj_launch<real, 8>(a, st); break;
     case 16: adj_launch_wide<real, 16>(a, st); break;
     case 32: adj_launch_wide<real, 32>(a, st); break;

@@ -124,6 +124,21 @@ template <class real>
 cudaError_t launch_rollout(const RolloutArgs<real>& a, cudaStream_t st);
 template <class real>
 cudaError_t launch_gru_setup(int d, const real* params, int d_in, real* M, cudaStream_t st);
+// Generic-kernel launchers per group of kinds (each group in its own translation unit):
+// Brusselator, GRU and affine ("basic"); mean-field RNN, Langevin, Lorenz-96 and
+// permutation ("models").
+template <class real>
+cudaError_t launch_init_basic(const InitArgs<real>& a, cudaStream_t st);
+template <class real>
+cudaError_t launch_linearize_basic(const LinArgs<real>& a, cudaStream_t st);
+template <class real>
+cudaError_t launch_rollout_basic(const RolloutArgs<real>& a, cudaStream_t st);
+template <class real>
+cudaError_t launch_init_models(const InitArgs<real>& a, cudaStream_t st);
+template <class real>
+cudaError_t launch_linearize_models(const LinArgs<real>& a, cudaStream_t st);
+template <class real>
+cudaError_t launch_rollout_models(const RolloutArgs<real>& a, cudaStream_t st);
 
 cudaError_t launch_check(const CheckArgs& a, cudaStream_t st);
 
@@ -246,8 +261,9 @@ template <class real>
 cudaError_t launch_dense_fused_carry(const FusedArgs<real>& a, cudaStream_t st);
 
 inline bool dense_fused_supported(int kind, int d) {
-  (void)kind;
-  return d == 1 || d == 2 || d == 4 || d == 8;
+  // the kinds of the thesis's second workloads (RNN, Langevin, Lorenz-96, permutation)
+  // take the unfused linearise + dense scan path
+  return kind <= DEER_F_LINEAR && (d == 1 || d == 2 || d == 4 || d == 8);
 }
 
 }  // namespace deer

@@ -103,3 +103,36 @@ def test_invalid_arguments_fail_without_device_work(lib):
     # workspace too small (checked before any device call)
     assert lib.deer_solve(C.byref(dyn), 1, 10, 8, None, 8, C.byref(o), 256, 16, None,
                           info) == N.DEER_ERR_WORKSPACE
+
+
+def test_second_workload_kinds_sizes_and_checks(lib):
+    """Supported sizes of the mean-field RNN, two-well Langevin, Lorenz-96 and permutation
+    kinds, and their argument checks (all host-side: no device work)."""
+    from paper_2603_16850_gb300 import _native as N
+    o = N.deer_options()
+    lib.deer_default_options(C.byref(o))
+
+    def ws(kind, d, dt=0.01, stride=0, jac="full", damp="none"):
+        o.jac, o.damp = N.JAC[jac], N.DAMP[damp]
+        dyn = N.deer_dynamics(N.KIND[kind], d, d, 0, dt, 8, stride, 0, 0)
+        return lib.deer_workspace_bytes(C.byref(dyn), 2, 200, C.byref(o))
+
+    assert ws("rnn_tanh", 32) > 0 and ws("rnn_tanh", 64) == 0 and ws("rnn_tanh", 5) == 0
+    assert ws("langevin_2well", 2) > 0 and ws("langevin_2well", 16, jac="diag") > 0
+    assert ws("lorenz96_dp5", 5) > 0 and ws("lorenz96_dp5", 8) > 0
+    assert ws("lorenz96_dp5", 2) == 0 and ws("lorenz96_dp5", 16) == 0
+    assert ws("permute", 5) > 0 and ws("permute", 32) > 0 and ws("permute", 1) == 0
+    # dense ELK keeps its register sizes (1, 2, 4, 8); quasi-ELK takes any size
+    assert ws("lorenz96_dp5", 8, damp="elk") > 0 and ws("lorenz96_dp5", 5, damp="elk") == 0
+    assert ws("lorenz96_dp5", 5, jac="diag", damp="elk") > 0
+    # a time step is required where f integrates an ODE or scales the noise
+    assert ws("lorenz96_dp5", 5, dt=0.0) == 0 and ws("langevin_2well", 2, dt=-1.0) == 0
+    # per-sequence parameter strides below one block of parameters are rejected
+    assert ws("langevin_2well", 2, stride=9) == 0 and ws("langevin_2well", 2, stride=10) > 0
+    assert ws("rnn_tanh", 4, stride=15) == 0 and ws("rnn_tanh", 4, stride=16) > 0
+    # the permutation needs its inputs: a solve without x fails before any device work
+    lib.deer_default_options(C.byref(o))
+    info = (N.deer_info * 1)()
+    pd = N.deer_dynamics(N.KIND["permute"], 5, 5, 0, 0.0, 8, 0, 0, 0)
+    assert lib.deer_solve(C.byref(pd), 1, 10, 8, None, 8, C.byref(o), 256, 1 << 20, None,
+                          info) == N.DEER_ERR_INVALID
