@@ -308,6 +308,84 @@ def adjoint_measurement(deer, N, lib, dev, stream):
             "grad_finite": bool(torch.isfinite(dk).all())}
 
 
+def threshold_measurement(deer, N, lib, dev, stream, T=100000, d=32, gains=(0.5, 1.0, 2.0),
+                          cap=300):
+    """The wall-clock side of the predictability threshold (Sec. ssc:exp_thresh): one
+    mean-field RNN trajectory (B = 1, d = 32, W_ij ~ N(0, g^2/d), W_ii = 0, sinusoidal
+    inputs) of length T, full-Jacobian DEER in FP32 (scaled residual 1e-5, sliding window,
+    at most ``cap`` iterations) against the sequential GPU rollout (a warp walking the
+    trajectory). Parallelising over time pays below the threshold (negative LLE, a few
+    Newton iterations) and loses above it (positive LLE, iterations grow toward T)."""
+    import numpy as np
+    import torch
+    import synth
+    rows = []
+    tuned = None
+    for g in gains:
+        p = synth.mean_field_rnn(1, T, d, g, seed=0)
+        W = torch.tensor(p["W"], dtype=torch.float32, device=dev)
+        dyn = deer.Dynamics.rnn_tanh(W)
+        x = torch.tensor(p["x"].reshape(-1, d), dtype=torch.float32, device=dev)
+        s0 = torch.tensor(p["s0"], dtype=torch.float32, device=dev)
+        opts = dict(jac="full", tol=1e-5, prec="fp32", init="zeros", reset=True, window=True,
+                    max_iters=cap)
+        if tuned is None:
+            # chunk length for a single long sequence, tuned once on the predictable case
+            # (untimed): the per-sequence carry walks T / L chunk aggregates in order
+            from paper_2603_16850_gb300 import autotune
+            tuned = autotune.pick_best(
+                (32, 64, 128, 256, 512),
+                lambda L: _time_solve1(deer, dyn, s0, T, x, dict(opts, chunk=L), stream))
+        opts["chunk"] = tuned["chunk"]
+        ws_ = torch.empty(deer.deer_workspace_bytes(dyn, 1, T, **opts), dtype=torch.uint8,
+                          device=dev)
+        deer.deer_solve(dyn, s0, T, x, workspace=ws_, stream=stream, **opts)  # warm
+        deer.deer_rollout(dyn, s0, T, x, prec="fp32", stream=stream)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        s, info = deer.deer_solve(dyn, s0, T, x, workspace=ws_, stream=stream, **opts)
+        e[1].record(stream)
+        e[2].record(stream)
+        ref = deer.deer_rollout(dyn, s0, T, x, prec="fp32", stream=stream)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        deer_ms, seq_ms = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+        # one more solve with the library's per-phase events (not the timed one)
+        lib.deer_profile_reset()
+        lib.deer_profile_enable(1)
+        deer.deer_solve(dyn, s0, T, x, workspace=ws_, stream=stream, **opts)
+        torch.cuda.synchronize()
+        lib.deer_profile_enable(0)
+        prof = N.deer_profile()
+        lib.deer_profile_read(prof)
+        lle = float(deer.deer_lle(dyn, s0, T, ref, x=x, prec="fp32", stream=stream)[0])
+        err = float((s - ref).abs().max() / ref.abs().max())
+        rows.append({"g": g, "lle": lle, "newton_iters": int(info.iters[0]),
+                     "converged": bool(info.converged[0]), "deer_ms": deer_ms,
+                     "sequential_ms": seq_ms, "speedup": seq_ms / deer_ms,
+                     "max_rel_diff_vs_rollout": err,
+                     "phase_ms": {n: prof.ms[i] for i, n in enumerate(N.PHASES)}})
+    return {"workload": f"mean-field RNN d={d}, B=1, T={T}, FP32 DEER (cap {cap} "
+                        "iterations) vs sequential GPU rollout",
+            "chunk": {"chosen": tuned["chunk"], "tuning_ms": tuned["timings"],
+                      "how": "autotune.pick_best on the g=%.1f problem" % gains[0]},
+            "rows": rows}
+
+
+def _time_solve1(deer, dyn, s0, T, x, opts, stream):
+    """Milliseconds of one solve of B sequences of length T (after one warm-up)."""
+    import torch
+    deer.deer_solve(dyn, s0, T, x, stream=stream, **opts)
+    torch.cuda.synchronize()
+    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    e0.record(stream)
+    deer.deer_solve(dyn, s0, T, x, stream=stream, **opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
 def dyn_sub(deer, p, d, dev, n=32):
     """Kinetics of the first n systems of a problem (autotuning subset)."""
     import torch
@@ -404,6 +482,9 @@ def run_only(args):
                                    B=args.batch or 64)
     elif args.only == "ragged_mixed":
         out = ragged_mixed_measurement(deer, N, lib, dev, stream, B=args.batch or 1000)
+    elif args.only == "threshold":
+        gains = tuple(float(v) for v in args.gains.split(",")) if args.gains else (0.5, 1.0, 2.0)
+        out = threshold_measurement(deer, N, lib, dev, stream, gains=gains)
     else:
         out = adjoint_measurement(deer, N, lib, dev, stream)
     print(json.dumps({"only": args.only, **out}), flush=True)
@@ -587,8 +668,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary GRU quasi-DEER measurement")
-    ap.add_argument("--only", default="", choices=["", "gru", "adjoint", "ragged_mixed"],
+    ap.add_argument("--only", default="", choices=["", "gru", "adjoint", "ragged_mixed",
+                                                   "threshold"],
                     help="run one secondary workload alone (with --batch) and print it")
+    ap.add_argument("--gains", default="",
+                    help="--only threshold: comma-separated RNN gains g (default 0.5,1.0,2.0)")
     ap.add_argument("--batch", type=int, default=0,
                     help="trajectories per GPU (default 4096; smaller for profiler captures)")
     args = ap.parse_args()

@@ -642,108 +642,259 @@ namespace deer {
 // owns column j of the chunk product P and entry j of the vectors; the Jacobian rows are
 // read as warp-wide broadcasts, vector entries travel by shuffles.
 // ----------------------------------------------------------------------------
+// 16 bytes (four floats or two doubles) from a 16-byte aligned address. Plain (coherent)
+// load: used for data the same launch never writes, and for data written by earlier
+// launches.
+template <class real>
+__device__ __forceinline__ void ld16(const real* p, real* v) {
+  if constexpr (sizeof(real) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  }
+}
+
 template <int D>
 __device__ __forceinline__ unsigned group_mask() {
   return D == 32 ? 0xffffffffu : (0xffffu << (16 * ((threadIdx.x >> 4) & 1)));
 }
 
+// ----------------------------------------------------------------------------
+// Asynchronous row staging for the wide dense scans. Lane i of a group copies its own row
+// (D values, 16-byte pieces) of a d x d block, and one entry of a vector, from global
+// memory into a slot of a shared-memory ring with cp.async; the ring runs kRing slots
+// ahead of the rows being consumed, so the DRAM latency of a row is hidden behind the
+// dependent work on the rows before it. Rows are padded to D + 16 B so that 128-bit
+// reads of eight lanes' rows hit distinct banks. Every stage commits one (possibly empty)
+// group, and cp.async.wait_group(kRing - 1) before a slot is read guarantees that the
+// slot's copies (issued kRing commits earlier) have landed: the wait ends when the copies
+// do, with no spin loop of our own.
+// ----------------------------------------------------------------------------
+template <class real>
+constexpr int ring_depth() { return sizeof(real) == 4 ? 8 : 4; }
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
+  static_assert(BYTES == 4 || BYTES == 8, "cp.async.ca copies 4, 8 or 16 bytes");
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 template <class real, int D>
-__global__ void __launch_bounds__(128) k_dense_chunk_wide(DenseScanArgs<real> a) {
-  constexpr int G = 128 / D;
+struct RowRing {
+  static constexpr int K = ring_depth<real>();
+  static constexpr int RS = D + 16 / (int)sizeof(real);
+  real m[K][D][RS];  // row `lane` of a d x d block per slot
+  real v[K][D];      // one vector entry per lane per slot
+
+  // copy row `lane` of the block at `blk` (16-byte aligned) and vec[lane] into `slot`
+  __device__ __forceinline__ void issue(int slot, int lane, const real* blk, const real* vec) {
+    constexpr int PIECES = D * (int)sizeof(real) / 16;
+#pragma unroll
+    for (int q = 0; q < PIECES; ++q)
+      cp_async16(&m[slot][lane][q * 16 / (int)sizeof(real)],
+                 blk + lane * D + q * 16 / (int)sizeof(real));
+    cp_async_small<sizeof(real)>(&v[slot][lane], vec + lane);
+  }
+  __device__ __forceinline__ void row(int slot, int r, real (&out)[D]) const {
+#pragma unroll
+    for (int k = 0; k < D; k += 16 / (int)sizeof(real)) {
+      if constexpr (sizeof(real) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(&m[slot][r][k]);
+        out[k] = q.x; out[k + 1] = q.y; out[k + 2] = q.z; out[k + 3] = q.w;
+      } else {
+        const double2 q = *reinterpret_cast<const double2*>(&m[slot][r][k]);
+        out[k] = q.x; out[k + 1] = q.y;
+      }
+    }
+  }
+};
+
+// Chunk pass, d = 16 / 32: one group of D lanes per chunk (one warp per block), lane j owns
+// column j of the chunk product P and entry j of the vector part. Row t's Jacobian is
+// staged in the ring; every lane reads all of its rows (broadcast) for P <- A_t P and
+// its own row for v <- A_t v + b_t.
+template <class real, int D>
+__global__ void __launch_bounds__(32) k_dense_chunk_ring(DenseScanArgs<real> a) {
+  constexpr int G = 32 / D;
+  using Ring = RowRing<real, D>;
+  constexpr int K = Ring::K;
+  __shared__ __align__(16) Ring ring[G];
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gm = group_mask<D>();
   const int64_t ac = blockIdx.x * (int64_t)G + grp;
-  const bool valid = ac < a.bt.act_chunks;
-  int64_t seq = 0, c = 0, r0 = 0;
-  int n = 0;
-  if (valid) act_chunk(a.bt, ac, seq, c, r0, n);
-  const bool need_P = valid && c != win_first(a.bt, seq);
+  if (ac >= a.bt.act_chunks) return;  // whole groups; groups never synchronise with each other
+  int64_t seq, c, r0;
+  int n;
+  act_chunk(a.bt, ac, seq, c, r0, n);
+  const bool need_P = c != win_first(a.bt, seq);
+  Ring& R = ring[grp];
+  const real* A0 = a.A + r0 * (int64_t)(D * D);
+  const real* b0 = a.b + r0 * D;
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    if (s < n) R.issue(s, lane, A0 + s * (int64_t)(D * D), b0 + s * D);
+    cp_async_commit();
+  }
   real Pc[D];  // column `lane` of P
   real v = real(0);
 #pragma unroll
   for (int i = 0; i < D; ++i) Pc[i] = i == lane ? real(1) : real(0);
-  for (int t = 0; t < n; ++t) {
-    const real* At = a.A + (r0 + t) * (int64_t)(D * D);
-    // v <- A v + b: lane i forms row i, v entries by shuffle
-    real nv = __ldg(a.b + (r0 + t) * D + lane);
+  for (int t0 = 0; t0 < n; t0 += K) {
 #pragma unroll
-    for (int k = 0; k < D; ++k) nv += __ldg(At + lane * D + k) * __shfl_sync(gm, v, k, D);
-    v = nv;
-    if (need_P) {
-      real np[D];
+    for (int s = 0; s < K; ++s) {
+      const int t = t0 + s;
+      cp_async_wait<K - 1>();
+      __syncwarp(gm);  // the other lanes' rows of this slot have landed
+      if (t < n) {
+        real own[D];
+        R.row(s, lane, own);
+        real nv = R.v[s][lane];
 #pragma unroll
-      for (int i = 0; i < D; ++i) {
-        real x = real(0);
+        for (int k = 0; k < D; ++k) nv += own[k] * __shfl_sync(gm, v, k, D);
+        v = nv;
+        if (need_P) {
+          real np[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) x += __ldg(At + i * D + k) * Pc[k];
-        np[i] = x;
+          for (int i = 0; i < D; ++i) {
+            real ar[D];
+            R.row(s, i, ar);
+            real x = real(0);
+#pragma unroll
+            for (int k = 0; k < D; ++k) x += ar[k] * Pc[k];
+            np[i] = x;
+          }
+#pragma unroll
+          for (int i = 0; i < D; ++i) Pc[i] = np[i];
+        }
       }
-#pragma unroll
-      for (int i = 0; i < D; ++i) Pc[i] = np[i];
+      __syncwarp(gm);  // every lane is done with the slot before it is refilled
+      if (t + K < n) R.issue(s, lane, A0 + (t + K) * (int64_t)(D * D), b0 + (t + K) * D);
+      cp_async_commit();
     }
   }
-  if (valid) {
-    real* Po = a.aggP + c * (int64_t)(D * D);
+  cp_async_wait<0>();
+  real* Po = a.aggP + c * (int64_t)(D * D);
 #pragma unroll
-    for (int i = 0; i < D; ++i) Po[i * D + lane] = Pc[i];
-    a.aggv[c * D + lane] = v;
-  }
+  for (int i = 0; i < D; ++i) Po[i * D + lane] = Pc[i];
+  a.aggv[c * D + lane] = v;
 }
 
+// Carry pass: x_c = P_c x_{c-1} + v_c along each active sequence's chunks (one group per
+// sequence); the aggregates do not depend on x and stream through the ring.
 template <class real, int D>
-__global__ void __launch_bounds__(128) k_dense_carry_wide(DenseScanArgs<real> a) {
-  constexpr int G = 128 / D;
+__global__ void __launch_bounds__(32) k_dense_carry_ring(DenseScanArgs<real> a) {
+  constexpr int G = 32 / D;
+  using Ring = RowRing<real, D>;
+  constexpr int K = Ring::K;
+  __shared__ __align__(16) Ring ring[G];
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gm = group_mask<D>();
   const int64_t kq = blockIdx.x * (int64_t)G + grp;
-  const bool valid = kq < a.bt.n_act;
-  const int64_t seq = valid ? a.bt.act_seq[kq] : 0;
-  const int64_t c0 = valid ? win_first(a.bt, seq) : 0;
-  const int64_t c1 = valid ? a.bt.chunk_first[seq + 1] : 0;
-  real x = real(0);
-  for (int64_t c = c0; c < c1; ++c) {
-    a.cin[c * D + lane] = x;
-    const real* P = a.aggP + c * (int64_t)(D * D);
-    real y = a.aggv[c * D + lane];
-    if (c > c0) {
+  if (kq >= a.bt.n_act) return;
+  const int64_t seq = a.bt.act_seq[kq];
+  const int64_t c0 = win_first(a.bt, seq), c1 = a.bt.chunk_first[seq + 1];
+  Ring& R = ring[grp];
 #pragma unroll
-      for (int k = 0; k < D; ++k) y += P[lane * D + k] * __shfl_sync(gm, x, k, D);
-    }
-    x = y;
+  for (int s = 0; s < K; ++s) {
+    if (c0 + s < c1) R.issue(s, lane, a.aggP + (c0 + s) * (int64_t)(D * D), a.aggv + (c0 + s) * D);
+    cp_async_commit();
   }
+  real x = real(0);
+  for (int64_t cb = c0; cb < c1; cb += K) {
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      const int64_t c = cb + s;
+      cp_async_wait<K - 1>();  // each lane reads only its own row: no exchange needed
+      if (c < c1) {
+        a.cin[c * D + lane] = x;
+        real y = R.v[s][lane];
+        if (c > c0) {
+          real pr[D];
+          R.row(s, lane, pr);
+#pragma unroll
+          for (int k = 0; k < D; ++k) y += pr[k] * __shfl_sync(gm, x, k, D);
+        }
+        x = y;
+      }
+      if (c + K < c1) R.issue(s, lane, a.aggP + (c + K) * (int64_t)(D * D), a.aggv + (c + K) * D);
+      cp_async_commit();
+    }
+  }
+  cp_async_wait<0>();
 }
 
+// Apply pass: Delta_t = A_t Delta_{t-1} + b_t from the chunk's carry, s_t += Delta_t; lane
+// i reads its own row of each staged A_t.
 template <class real, int D>
-__global__ void __launch_bounds__(128) k_dense_apply_wide(DenseScanArgs<real> a) {
-  constexpr int G = 128 / D;
+__global__ void __launch_bounds__(32) k_dense_apply_ring(DenseScanArgs<real> a) {
+  constexpr int G = 32 / D;
+  using Ring = RowRing<real, D>;
+  constexpr int K = Ring::K;
+  __shared__ __align__(16) Ring ring[G];
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gm = group_mask<D>();
   const int64_t ac = blockIdx.x * (int64_t)G + grp;
-  const bool valid = ac < a.bt.act_chunks;
-  int64_t seq = 0, c = 0, r0 = 0;
-  int n = 0;
-  if (valid) act_chunk(a.bt, ac, seq, c, r0, n);
-  real x = valid ? a.cin[c * D + lane] : real(0);
-  for (int t = 0; t < n; ++t) {
-    const int64_t row = r0 + t;
-    const real* At = a.A + row * (int64_t)(D * D) + lane * D;
-    real y = __ldg(a.b + row * D + lane);
+  if (ac >= a.bt.act_chunks) return;
+  int64_t seq, c, r0;
+  int n;
+  act_chunk(a.bt, ac, seq, c, r0, n);
+  const real* A0 = a.A + r0 * (int64_t)(D * D);
+  const real* b0 = a.b + r0 * D;
+  Ring& R = ring[grp];
 #pragma unroll
-    for (int k = 0; k < D; ++k) y += __ldg(At + k) * __shfl_sync(gm, x, k, D);
-    x = y;
-    real* sp = a.s + row * D + lane;
-    *sp = reset_val(*sp + y, a.reset_thr, a.reset);
+  for (int s = 0; s < K; ++s) {
+    if (s < n) R.issue(s, lane, A0 + s * (int64_t)(D * D), b0 + s * D);
+    cp_async_commit();
   }
+  real x = a.cin[c * D + lane];
+  for (int t0 = 0; t0 < n; t0 += K) {
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      const int t = t0 + s;
+      cp_async_wait<K - 1>();
+      if (t < n) {
+        real ar[D];
+        R.row(s, lane, ar);
+        real y = R.v[s][lane];
+#pragma unroll
+        for (int k = 0; k < D; ++k) y += ar[k] * __shfl_sync(gm, x, k, D);
+        x = y;
+        real* sp = a.s + (r0 + t) * D + lane;
+        *sp = reset_val(*sp + y, a.reset_thr, a.reset);
+      }
+      if (t + K < n) R.issue(s, lane, A0 + (t + K) * (int64_t)(D * D), b0 + (t + K) * D);
+      cp_async_commit();
+    }
+  }
+  cp_async_wait<0>();
 }
 
 template <class real, int D>
 void dense_launch_wide(const DenseScanArgs<real>& a, cudaStream_t st) {
-  constexpr int G = 128 / D;
+  constexpr int G = 32 / D;
   const unsigned gc = grid_for(a.bt.act_chunks, G);
   const unsigned gs = grid_for(a.bt.n_act, G);
-  k_dense_chunk_wide<real, D><<<gc, 128, 0, st>>>(a);
-  k_dense_carry_wide<real, D><<<gs, 128, 0, st>>>(a);
-  k_dense_apply_wide<real, D><<<gc, 128, 0, st>>>(a);
+  k_dense_chunk_ring<real, D><<<gc, 32, 0, st>>>(a);
+  k_dense_carry_ring<real, D><<<gs, 32, 0, st>>>(a);
+  k_dense_apply_ring<real, D><<<gc, 32, 0, st>>>(a);
   note_launch(3);
 }
 

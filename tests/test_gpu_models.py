@@ -242,3 +242,23 @@ def test_bad_permutation_index_is_reported():
     with pytest.raises(RuntimeError, match="non-finite"):
         deer.deer_solve(dyn, _t(p["s0"]), T, _t(xb.reshape(-1, d)), jac="full", tol=1e-12,
                         init="zeros")
+
+
+@pytest.mark.parametrize("kind,d", [("rnn", 32), ("rnn", 8), ("langevin", 2), ("lorenz", 5),
+                                    ("permute", 5)])
+def test_sequential_rollout_matches_oracle(kind, d):
+    """The GPU sequential baseline (warp per trajectory for the RNN, a thread per
+    trajectory otherwise) on a ragged batch whose groups share warps."""
+    deer = _deer()
+    lengths = [300, 1, 77, 250, 5]
+    off = synth.offsets_from_lengths(lengths)
+    B, T = len(lengths), max(lengths)
+    p, od, dyn, _ = _case(kind, B, T, d, seed=13)
+    x = None
+    if "x" in p:
+        x = _t(np.concatenate([p["x"][b, :n] for b, n in enumerate(lengths)]).reshape(-1, d))
+    s = deer.deer_rollout(dyn, _t(p["s0"]), 0, x, offsets=_t(off, torch.int64))
+    roll = onewton.rollout(od, p["s0"], T)
+    sn = s.cpu().numpy()
+    for b, n in enumerate(lengths):
+        assert _relerr(sn[off[b]:off[b + 1]], roll[b, :n]) <= 1e-12
