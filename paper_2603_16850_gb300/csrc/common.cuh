@@ -232,6 +232,53 @@ __device__ __forceinline__ void acc_resid_t(SeqAcc* acc, int64_t seq, bool valid
   acc_resid(acc, seq, valid, mx, sq, badkey);
 }
 
+// Group-local variant for kernels whose D-lane groups walk several rows each: the lanes of
+// one group reduce their per-lane statistics (shuffles within the group mask only, so
+// the groups of a warp need not flush together) and lane 0 issues the atomics.
+template <int D, class real>
+__device__ __forceinline__ void acc_resid_group(SeqAcc* acc, int64_t seq, real mx, real sq,
+                                                unsigned long long badkey, int lane,
+                                                unsigned gm) {
+#pragma unroll
+  for (int o = D / 2; o > 0; o >>= 1) {
+    const real om = __shfl_xor_sync(gm, mx, o, D);
+    mx = (om > mx || om != om) ? om : mx;
+    sq += __shfl_xor_sync(gm, sq, o, D);
+    const unsigned long long ok = __shfl_xor_sync(gm, badkey, o, D);
+    badkey = ok > badkey ? ok : badkey;
+  }
+  if (lane == 0) {
+    atomicMax(&acc[seq].max_bits, dbits((double)mx));
+    atomicAdd(&acc[seq].sumsq, (double)sq);
+    if (badkey) atomicMax(&acc[seq].badkey, badkey);
+  }
+}
+
+// Writes a D x D block held one row per lane of a D-lane group (row `lane` in registers)
+// to `dst` (16-byte aligned) with contiguous 16-byte stores across the group: the rows go
+// through `tile` ([D][D + 1] per group; the odd stride keeps both the row writes and the
+// strided reads free of bank conflicts for float).
+template <class real, int D>
+__device__ __forceinline__ void store_block_rows(real* tile, real* dst, const real (&row)[D],
+                                                 int lane, unsigned gm) {
+  constexpr int VW = 16 / (int)sizeof(real);
+  static_assert(D % VW == 0, "rows of whole 16-byte pieces");
+#pragma unroll
+  for (int j = 0; j < D; ++j) tile[lane * (D + 1) + j] = row[j];
+  __syncwarp(gm);
+#pragma unroll
+  for (int q = 0; q < D / VW; ++q) {
+    const int e = (q * D + lane) * VW;
+    const real* src = tile + (e / D) * (D + 1) + e % D;
+    if constexpr (sizeof(real) == 4) {
+      reinterpret_cast<float4*>(dst)[q * D + lane] = make_float4(src[0], src[1], src[2], src[3]);
+    } else {
+      reinterpret_cast<double2*>(dst)[q * D + lane] = make_double2(src[0], src[1]);
+    }
+  }
+  __syncwarp(gm);
+}
+
 // ---------------------------------------------------------------------------
 // Launch bookkeeping (counted for deer_kernel_launch_count).
 // ---------------------------------------------------------------------------

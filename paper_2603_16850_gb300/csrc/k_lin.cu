@@ -468,6 +468,8 @@ DEER_INST(double)
 
 namespace deer {
 
+constexpr int kMaRows = 4;  // consecutive rows per lane group in k_lin_ma_wide
+
 // ----------------------------------------------------------------------------
 // Mass action, d = 16 / 32: D lanes per row, lane i owns species i (its state, slope and
 // row i of the stage Jacobians). Rates come from one pass over the reactions with
@@ -485,118 +487,133 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
   __shared__ __align__(16) real sK[GROUPS][D * D + 16 / sizeof(real)];
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gmask = D == 32 ? 0xffffffffu : (0xffffu << (16 * ((threadIdx.x >> 4) & 1)));
-  const int64_t ar = blockIdx.x * (int64_t)GROUPS + grp;
-  const bool valid = ar < a.bt.act_rows;
-  int64_t seq = 0, row = 0;
-  if (valid) act_row(a.bt, ar, seq, row);
+  // each group walks kMaRows consecutive active rows and flushes the residual statistics
+  // once per sequence it meets (not once per row): fewer atomics on the accumulator of a
+  // long sequence
+  const int64_t ar0 = (blockIdx.x * (int64_t)GROUPS + grp) * kMaRows;
+  int64_t cur = -1;
   real mx = real(0), sq = real(0);
   unsigned long long key = 0ull;  // first failing row (sliding window)
-  // all lanes run the loops (shuffles within a row group stay converged); invalid rows
-  // compute on row 0 of sequence 0 and store nothing
-  const real s_prev = valid ? (row == __ldg(a.bt.offsets + seq) ? a.s0[seq * D + lane]
-                                                              : a.s[(row - 1) * D + lane])
-                            : real(0);
-  const real* kk = a.dv.params + seq * a.dv.pstride;
-  const int4* tt = reinterpret_cast<const int4*>(a.dv.topo + seq * a.dv.tstride);
-  const int R = a.dv.R;
-  const real h = a.dv.dt;
-  real c = s_prev, acc = real(0), g = real(0);
-  real Kacc[D];
-#pragma unroll
-  for (int j = 0; j < D; ++j) Kacc[j] = real(0);
-  const int nst = RK4 ? 4 : 1;
-  for (int stage = 0; stage < nst; ++stage) {
-    const real cK = stage == 0 ? real(0) : (stage == 3 ? h : real(0.5) * h);
-    const real w = (stage == 1 || stage == 2) ? real(2) : real(1);
-    if (WANTA) {
-#pragma unroll
-      for (int j = 0; j < D; ++j) sG[grp][lane][j] = real(0);
+  for (int ri = 0; ri < kMaRows; ++ri) {
+    const int64_t ar = ar0 + ri;
+    if (ar >= a.bt.act_rows) break;  // uniform over the group
+    int64_t seq, row;
+    act_row(a.bt, ar, seq, row);
+    if (seq != cur) {
+      if (cur >= 0) acc_resid_group<D>(a.acc, cur, mx, sq, key, lane, gmask);
+      cur = seq;
+      mx = real(0);
+      sq = real(0);
+      key = 0ull;
     }
-    __syncwarp(gmask);
-    g = real(0);
-    for (int r = 0; r < R; ++r) {
-      const int4 q = __ldg(tt + r);
-      const real kr = __ldg(kk + r);
-      const real c1 = __shfl_sync(gmask, c, q.x, D);
-      const real c2 = __shfl_sync(gmask, c, q.y < 0 ? 0 : q.y, D);
-      const real f2 = q.y < 0 ? real(1) : c2;
-      const real nu = real((lane == q.z) + (lane == q.w) - (lane == q.x) - (lane == q.y));
-      g += nu * (kr * c1 * f2);
-      if (WANTA && nu != real(0)) {
-        sG[grp][lane][q.x] += nu * kr * f2;                  // d rate / d c_i1
-        if (q.y >= 0) sG[grp][lane][q.y] += nu * kr * c1;    // d rate / d c_i2
+    const real s_prev = row == __ldg(a.bt.offsets + seq) ? a.s0[seq * D + lane]
+                                                        : a.s[(row - 1) * D + lane];
+    const real* kk = a.dv.params + seq * a.dv.pstride;
+    const int4* tt = reinterpret_cast<const int4*>(a.dv.topo + seq * a.dv.tstride);
+    const int R = a.dv.R;
+    const real h = a.dv.dt;
+    real c = s_prev, acc = real(0), g = real(0);
+    real Kacc[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) Kacc[j] = real(0);
+    const int nst = RK4 ? 4 : 1;
+    for (int stage = 0; stage < nst; ++stage) {
+      const real cK = stage == 0 ? real(0) : (stage == 3 ? h : real(0.5) * h);
+      const real w = (stage == 1 || stage == 2) ? real(2) : real(1);
+      if (WANTA) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) sG[grp][lane][j] = real(0);
       }
-    }
-    if (WANTA) {
       __syncwarp(gmask);
-      real Gi[D], Kn[D];
-#pragma unroll
-      for (int j = 0; j < D; ++j) Gi[j] = sG[grp][lane][j];
-#pragma unroll
-      for (int j = 0; j < D; ++j) Kn[j] = Gi[j];
-      if (stage > 0) {
-#pragma unroll
-        for (int m = 0; m < D; ++m) {
-          const real gm = cK * Gi[m];
-#pragma unroll
-          for (int j = 0; j < D; ++j) Kn[j] += gm * sK[grp][m * D + j];
+      g = real(0);
+      for (int r = 0; r < R; ++r) {
+        const int4 q = __ldg(tt + r);
+        const real kr = __ldg(kk + r);
+        const real c1 = __shfl_sync(gmask, c, q.x, D);
+        const real c2 = __shfl_sync(gmask, c, q.y < 0 ? 0 : q.y, D);
+        const real f2 = q.y < 0 ? real(1) : c2;
+        const real nu = real((lane == q.z) + (lane == q.w) - (lane == q.x) - (lane == q.y));
+        g += nu * (kr * c1 * f2);
+        if (WANTA && nu != real(0)) {
+          sG[grp][lane][q.x] += nu * kr * f2;                  // d rate / d c_i1
+          if (q.y >= 0) sG[grp][lane][q.y] += nu * kr * c1;    // d rate / d c_i2
         }
       }
-      __syncwarp(gmask);
+      if (WANTA) {
+        __syncwarp(gmask);
+        real Gi[D], Kn[D];
 #pragma unroll
-      for (int j = 0; j < D; ++j) {
-        sK[grp][lane * D + j] = Kn[j];
-        Kacc[j] += w * Kn[j];
+        for (int j = 0; j < D; ++j) Gi[j] = sG[grp][lane][j];
+#pragma unroll
+        for (int j = 0; j < D; ++j) Kn[j] = Gi[j];
+        if (stage > 0) {
+#pragma unroll
+          for (int m = 0; m < D; ++m) {
+            const real gm = cK * Gi[m];
+#pragma unroll
+            for (int j = 0; j < D; ++j) Kn[j] += gm * sK[grp][m * D + j];
+          }
+        }
+        __syncwarp(gmask);
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          sK[grp][lane * D + j] = Kn[j];
+          Kacc[j] += w * Kn[j];
+        }
+        __syncwarp(gmask);
       }
-      __syncwarp(gmask);
+      acc += w * g;
+      const real cs = stage == 2 ? h : real(0.5) * h;
+      c = s_prev + cs * g;
     }
-    acc += w * g;
-    const real cs = stage == 2 ? h : real(0.5) * h;
-    c = s_prev + cs * g;
-  }
-  const real hw = RK4 ? h / real(6) : h;
-  const real F = s_prev + hw * acc;
-  if (valid) {
-    const real sc = a.s[row * D + lane];
-    const real rr = sc - F;
-    const real sabs = rabs(sc);
-    mx = rabs(rr) / (sabs > real(1) ? sabs : real(1));
-    if (rr != rr) mx = rr;  // keep NaN
-    sq = rr * rr;
-    if (!(mx <= a.tol)) key = bad_key(true, row - __ldg(a.bt.offsets + seq));
-    const real k = a.dparam;
-    if constexpr (JAC == DEER_JAC_FULL) {
-      const real scale = a.damp == DEER_DAMP_SCALE ? real(1) - k : real(1);
-      real* Ao = a.A + row * (int64_t)(D * D) + lane * D;
+    const real hw = RK4 ? h / real(6) : h;
+    const real F = s_prev + hw * acc;
+    {
+      const real sc = a.s[row * D + lane];
+      const real rr = sc - F;
+      const real sabs = rabs(sc);
+      real m1 = rabs(rr) / (sabs > real(1) ? sabs : real(1));
+      if (rr != rr) m1 = rr;  // keep NaN
+      mx = (m1 > mx || m1 != m1) ? m1 : mx;
+      sq += rr * rr;
+      if (!(m1 <= a.tol) && key == 0ull) key = bad_key(true, row - __ldg(a.bt.offsets + seq));
+      const real k = a.dparam;
+      if constexpr (JAC == DEER_JAC_FULL) {
+        const real scale = a.damp == DEER_DAMP_SCALE ? real(1) - k : real(1);
+        real An[D];
 #pragma unroll
-      for (int j = 0; j < D; ++j) Ao[j] = scale * (hw * Kacc[j] + (j == lane ? real(1) : real(0)));
-      a.b[row * D + lane] = -rr;
-    } else {
-      real ai;
-      if constexpr (JAC == DEER_JAC_DIAG) {
-        ai = real(0);
-#pragma unroll
-        for (int j = 0; j < D; ++j)
-          if (j == lane) ai = real(1) + hw * Kacc[j];
-      } else if constexpr (JAC == DEER_JAC_IDENTITY) {
-        ai = real(1);
+        for (int j = 0; j < D; ++j) An[j] = scale * (hw * Kacc[j] + (j == lane ? real(1) : real(0)));
+        // the rate-Jacobian buffer is free after the last stage
+        __syncwarp(gmask);
+        store_block_rows<real, D>(&sG[grp][0][0], a.A + row * (int64_t)(D * D), An, lane, gmask);
+        a.b[row * D + lane] = -rr;
       } else {
-        ai = real(0);
+        real ai;
+        if constexpr (JAC == DEER_JAC_DIAG) {
+          ai = real(0);
+#pragma unroll
+          for (int j = 0; j < D; ++j)
+            if (j == lane) ai = real(1) + hw * Kacc[j];
+        } else if constexpr (JAC == DEER_JAC_IDENTITY) {
+          ai = real(1);
+        } else {
+          ai = real(0);
+        }
+        if (a.damp == DEER_DAMP_SCALE) ai *= (real(1) - k);
+        else if (a.damp == DEER_DAMP_CLIP) ai = ai > k ? k : (ai < -k ? -k : ai);
+        if constexpr (JAC == DEER_JAC_DIAG) a.A[row * D + lane] = ai;
+        a.b[row * D + lane] = F - ai * s_prev;
       }
-      if (a.damp == DEER_DAMP_SCALE) ai *= (real(1) - k);
-      else if (a.damp == DEER_DAMP_CLIP) ai = ai > k ? k : (ai < -k ? -k : ai);
-      if constexpr (JAC == DEER_JAC_DIAG) a.A[row * D + lane] = ai;
-      a.b[row * D + lane] = F - ai * s_prev;
     }
   }
-  acc_resid_t(a.acc, seq, valid, mx, sq, key);
+  if (cur >= 0) acc_resid_group<D>(a.acc, cur, mx, sq, key, lane, gmask);
 }
 
 template <class real, int JAC>
 cudaError_t launch_lin_ma_wide(const LinArgs<real>& a, cudaStream_t st) {
   const bool rk4 = a.dv.kind == DEER_F_MASSACTION_RK4;
   const int d = a.dv.d;
-  const int64_t rows_per_block = 128 / d;
+  const int64_t rows_per_block = 128 / d * kMaRows;
   const unsigned g = grid_for(a.bt.act_rows, (int)rows_per_block);
   if (d == 16) {
     if (rk4) k_lin_ma_wide<real, 16, true, JAC><<<g, 128, 0, st>>>(a);

@@ -16,6 +16,8 @@ cudaError_t launch_init_models(const InitArgs<real>& a, cudaStream_t st) {
   }
 }
 
+constexpr int kRnnRows = 16;  // consecutive rows per lane group in k_lin_rnn_wide
+
 // ----------------------------------------------------------------------------
 // Mean-field RNN, d = 16 / 32: D lanes per row, lane i owns row i of W (registers) and
 // entry i of s_{t-1}, F_t, r_t, b_t; tanh(s_j) and its derivative arrive by shuffles and
@@ -25,62 +27,62 @@ template <class real, int D, int JAC>
 __global__ void __launch_bounds__(128) k_lin_rnn_wide(LinArgs<real> a) {
   constexpr int GROUPS = 128 / D;
   constexpr int VW = 16 / (int)sizeof(real);
+  __shared__ __align__(16) real sT[GROUPS][D * (D + 1)];  // transpose tile of A_t
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gmask = D == 32 ? 0xffffffffu : (0xffffu << (16 * ((threadIdx.x >> 4) & 1)));
-  const int64_t ar = blockIdx.x * (int64_t)GROUPS + grp;
-  const bool valid = ar < a.bt.act_rows;
-  int64_t seq = 0, row = 0;
-  if (valid) act_row(a.bt, ar, seq, row);
+  // each group walks kRnnRows consecutive active rows; the residual statistics of a
+  // sequence are flushed once per group (one sequence usually spans all of them) instead
+  // of once per row, which keeps the accumulator atomics of a long sequence uncontended
+  const int64_t ar0 = (blockIdx.x * (int64_t)GROUPS + grp) * kRnnRows;
+  int64_t cur = -1;
   real mx = real(0), sq = real(0);
   unsigned long long key = 0ull;  // first failing row (sliding window)
-  // all lanes run the shuffles; invalid rows compute on sequence 0 and store nothing
-  const real sp = valid ? (row == __ldg(a.bt.offsets + seq) ? a.s0[seq * D + lane]
-                                                          : a.s[(row - 1) * D + lane])
-                        : real(0);
-  const real th = tanh(sp);
-  const real dth = real(1) - th * th;
-  const real* Wr = a.dv.params + seq * a.dv.pstride + lane * D;
-  real w[D];
-#pragma unroll
-  for (int k = 0; k < D; k += VW) {
-    if constexpr (sizeof(real) == 4) {
-      const float4 q = __ldg(reinterpret_cast<const float4*>(Wr + k));
-      w[k] = q.x; w[k + 1] = q.y; w[k + 2] = q.z; w[k + 3] = q.w;
-    } else {
-      const double2 q = __ldg(reinterpret_cast<const double2*>(Wr + k));
-      w[k] = q.x; w[k + 1] = q.y;
+  for (int rr_i = 0; rr_i < kRnnRows; ++rr_i) {
+    const int64_t ar = ar0 + rr_i;
+    if (ar >= a.bt.act_rows) break;  // uniform over the group
+    int64_t seq, row;
+    act_row(a.bt, ar, seq, row);
+    if (seq != cur) {
+      if (cur >= 0) acc_resid_group<D>(a.acc, cur, mx, sq, key, lane, gmask);
+      cur = seq;
+      mx = real(0);
+      sq = real(0);
+      key = 0ull;
     }
-  }
-  real F = (valid && a.dv.x) ? __ldg(a.dv.x + row * D + lane) : real(0);
+    const int64_t first = __ldg(a.bt.offsets + seq);
+    const real sp = row == first ? a.s0[seq * D + lane] : a.s[(row - 1) * D + lane];
+    const real th = tanh(sp);
+    const real dth = real(1) - th * th;
+    const real* Wr = a.dv.params + seq * a.dv.pstride + lane * D;
+    real w[D];
 #pragma unroll
-  for (int j = 0; j < D; ++j) F += w[j] * __shfl_sync(gmask, th, j, D);
-  real Arow[JAC == DEER_JAC_FULL ? D : 1];
-  if constexpr (JAC == DEER_JAC_FULL) {
+    for (int k = 0; k < D; k += VW) {
+      if constexpr (sizeof(real) == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(Wr + k));
+        w[k] = q.x; w[k + 1] = q.y; w[k + 2] = q.z; w[k + 3] = q.w;
+      } else {
+        const double2 q = __ldg(reinterpret_cast<const double2*>(Wr + k));
+        w[k] = q.x; w[k + 1] = q.y;
+      }
+    }
+    real F = a.dv.x ? __ldg(a.dv.x + row * D + lane) : real(0);
 #pragma unroll
-    for (int j = 0; j < D; ++j) Arow[j] = w[j] * __shfl_sync(gmask, dth, j, D);
-  }
-  if (valid) {
+    for (int j = 0; j < D; ++j) F += w[j] * __shfl_sync(gmask, th, j, D);
     const real sc = a.s[row * D + lane];
     const real rr = sc - F;
     const real sabs = rabs(sc);
-    mx = rabs(rr) / (sabs > real(1) ? sabs : real(1));
-    if (rr != rr) mx = rr;  // keep NaN
-    sq = rr * rr;
-    if (!(mx <= a.tol)) key = bad_key(true, row - __ldg(a.bt.offsets + seq));
+    real m1 = rabs(rr) / (sabs > real(1) ? sabs : real(1));
+    if (rr != rr) m1 = rr;  // keep NaN
+    mx = (m1 > mx || m1 != m1) ? m1 : mx;
+    sq += rr * rr;
+    if (!(m1 <= a.tol) && key == 0ull) key = bad_key(true, row - first);
     const real k = a.dparam;
     if constexpr (JAC == DEER_JAC_FULL) {
       const real scale = a.damp == DEER_DAMP_SCALE ? real(1) - k : real(1);
-      real* Ao = a.A + row * (int64_t)(D * D) + lane * D;
+      real Arow[D];
 #pragma unroll
-      for (int j = 0; j < D; j += VW) {
-        if constexpr (sizeof(real) == 4) {
-          reinterpret_cast<float4*>(Ao + j)[0] = make_float4(
-              scale * Arow[j], scale * Arow[j + 1], scale * Arow[j + 2], scale * Arow[j + 3]);
-        } else {
-          reinterpret_cast<double2*>(Ao + j)[0] = make_double2(scale * Arow[j],
-                                                               scale * Arow[j + 1]);
-        }
-      }
+      for (int j = 0; j < D; ++j) Arow[j] = scale * w[j] * __shfl_sync(gmask, dth, j, D);
+      store_block_rows<real, D>(sT[grp], a.A + row * (int64_t)(D * D), Arow, lane, gmask);
       a.b[row * D + lane] = -rr;
     } else {
       real ai;
@@ -101,13 +103,13 @@ __global__ void __launch_bounds__(128) k_lin_rnn_wide(LinArgs<real> a) {
       a.b[row * D + lane] = F - ai * sp;
     }
   }
-  acc_resid_t(a.acc, seq, valid, mx, sq, key);
+  if (cur >= 0) acc_resid_group<D>(a.acc, cur, mx, sq, key, lane, gmask);
 }
 
 template <class real, int JAC>
 static cudaError_t lin_rnn_wide(const LinArgs<real>& a, cudaStream_t st) {
   const int d = a.dv.d;
-  const unsigned g = grid_for(a.bt.act_rows, 128 / d);
+  const unsigned g = grid_for(a.bt.act_rows, 128 / d * kRnnRows);
   if (d == 16) k_lin_rnn_wide<real, 16, JAC><<<g, 128, 0, st>>>(a);
   else k_lin_rnn_wide<real, 32, JAC><<<g, 128, 0, st>>>(a);
   note_launch();
