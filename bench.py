@@ -618,6 +618,7 @@ def run(args):
         extra["gru_quasi_deer"] = gru_diag_measurement(deer, N, lib, dev, stream)
         extra["adjoint"] = adjoint_measurement(deer, N, lib, dev, stream)
         extra["ragged_mixed"] = ragged_mixed_measurement(deer, N, lib, dev, stream)
+        extra["threshold"] = threshold_measurement(deer, N, lib, dev, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
