@@ -797,6 +797,96 @@ __global__ void __launch_bounds__(32) k_dense_chunk_ring(DenseScanArgs<real> a) 
   a.aggv[c * D + lane] = v;
 }
 
+// Chunk pass, d = 32: one chunk per block of four warps. The staged rows of A_t are shared
+// by the block (its 128 threads copy the 4 KB block together); warp w forms rows
+// 8w .. 8w+7 of P <- A_t P for all 32 columns (lane j owns column j), the new rows meet
+// in shared memory and every warp reloads its full column. The vector part
+// v <- A_t v + b_t is formed redundantly by every warp (lane i, row i). A quarter of the
+// dependent work per warp compared with one warp per chunk, and four times the warps:
+// the single long sequences that leave few chunks stay busy.
+template <class real>
+__global__ void __launch_bounds__(128) k_dense_chunk_ring4(DenseScanArgs<real> a) {
+  constexpr int D = 32;
+  constexpr int W = 4;                       // warps per chunk
+  constexpr int RW = D / W;                  // rows of P per warp
+  constexpr int K = ring_depth<real>();
+  constexpr int RS = D + 16 / (int)sizeof(real);
+  constexpr int VW = 16 / (int)sizeof(real);
+  constexpr int PIECES = D * D / VW;         // 16-byte pieces of one A_t
+  __shared__ __align__(16) real sA[K][D][RS];
+  __shared__ __align__(16) real sB[K][D];
+  __shared__ real sP[D][D + 1];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ac = blockIdx.x;
+  if (ac >= a.bt.act_chunks) return;  // uniform over the block
+  int64_t seq, c, r0;
+  int n;
+  act_chunk(a.bt, ac, seq, c, r0, n);
+  const bool need_P = c != win_first(a.bt, seq);
+  const real* A0 = a.A + r0 * (int64_t)(D * D);
+  const real* b0 = a.b + r0 * D;
+  auto issue = [&](int slot, int t) {
+    if (t < n) {
+      const real* src = A0 + t * (int64_t)(D * D);
+      for (int p = tid; p < PIECES; p += 128)
+        cp_async16(&sA[slot][p / (D / VW)][(p % (D / VW)) * VW], src + p * VW);
+      if (tid < D / VW) cp_async16(&sB[slot][tid * VW], b0 + t * D + tid * VW);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int s = 0; s < K; ++s) issue(s, s);
+  real Pc[D];  // column `lane` of P (the same in every warp)
+  real v = real(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) Pc[i] = i == lane ? real(1) : real(0);
+  for (int t0 = 0; t0 < n; t0 += K) {
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      const int t = t0 + s;
+      cp_async_wait<K - 1>();
+      __syncthreads();  // slot s complete for the block; last row's column reloads done
+      if (t < n) {
+        real own[D];
+#pragma unroll
+        for (int k = 0; k < D; k += VW) ld16<real>(&sA[s][lane][k], own + k);
+        real nv = sB[s][lane];
+#pragma unroll
+        for (int k = 0; k < D; ++k) nv += own[k] * __shfl_sync(0xffffffffu, v, k);
+        v = nv;
+        if (need_P) {
+#pragma unroll
+          for (int ii = 0; ii < RW; ++ii) {
+            const int i = warp * RW + ii;
+            real x = real(0);
+#pragma unroll
+            for (int k = 0; k < D; k += VW) {
+              real ar[VW];
+              ld16<real>(&sA[s][i][k], ar);
+#pragma unroll
+              for (int q = 0; q < VW; ++q) x += ar[q] * Pc[k + q];
+            }
+            sP[i][lane] = x;
+          }
+        }
+      }
+      __syncthreads();  // new rows of P complete; every read of slot s done
+      if (need_P && t < n) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) Pc[k] = sP[k][lane];
+      }
+      issue(s, t + K);
+    }
+  }
+  cp_async_wait<0>();
+  if (warp == 0) {
+    real* Po = a.aggP + c * (int64_t)(D * D);
+#pragma unroll
+    for (int i = 0; i < D; ++i) Po[i * D + lane] = Pc[i];
+    a.aggv[c * D + lane] = v;
+  }
+}
+
 // Carry pass: x_c = P_c x_{c-1} + v_c along each active sequence's chunks (one group per
 // sequence); the aggregates do not depend on x and stream through the ring.
 template <class real, int D>
@@ -892,7 +982,8 @@ void dense_launch_wide(const DenseScanArgs<real>& a, cudaStream_t st) {
   constexpr int G = 32 / D;
   const unsigned gc = grid_for(a.bt.act_chunks, G);
   const unsigned gs = grid_for(a.bt.n_act, G);
-  k_dense_chunk_ring<real, D><<<gc, 32, 0, st>>>(a);
+  if constexpr (D == 32) k_dense_chunk_ring4<real><<<grid_for(a.bt.act_chunks, 1), 128, 0, st>>>(a);
+  else k_dense_chunk_ring<real, D><<<gc, 32, 0, st>>>(a);
   k_dense_carry_ring<real, D><<<gs, 32, 0, st>>>(a);
   k_dense_apply_ring<real, D><<<gc, 32, 0, st>>>(a);
   note_launch(3);

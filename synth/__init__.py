@@ -225,7 +225,8 @@ def word_problem(B: int, T: int, seed: int, d: int = 5) -> dict:
     """Group word problem in S_d: one uniformly random permutation of range(d) per step
     (as source indices, x [B][T][d]) and the distinct vocabulary s0 = (1, ..., d)."""
     rng = np.random.default_rng(seed)
-    x = rng.permuted(np.broadcast_to(np.arange(d), (B, T, d)), axis=2).astype(np.float64)
+    x = np.ascontiguousarray(
+        rng.permuted(np.broadcast_to(np.arange(d), (B, T, d)), axis=2).astype(np.float64))
     s0 = np.broadcast_to(np.arange(1, d + 1, dtype=np.float64), (B, d)).copy()
     return {"kind": "permute", "d": d, "T": int(T), "x": x, "s0": s0}
 
