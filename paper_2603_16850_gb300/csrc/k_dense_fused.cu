@@ -248,6 +248,33 @@ __device__ __forceinline__ void ldrow_ro(const real* __restrict__ p, real (&v)[D
   }
 }
 
+// y += a x for a register row. Float32 rows go through the packed two-wide FMA (one
+// instruction for two lanes of the FP32 pipe; each half rounds like a scalar FMA, so the
+// results are the same as the scalar loop's): the kinetics kernel below is bound by
+// instruction issue, not by the FMA pipe.
+template <int D>
+__device__ __forceinline__ void axpy_row(double a, const double (&x)[D], double (&y)[D]) {
+#pragma unroll
+  for (int j = 0; j < D; ++j) y[j] += a * x[j];
+}
+
+template <int D>
+__device__ __forceinline__ void axpy_row(float a, const float (&x)[D], float (&y)[D]) {
+  if constexpr (D % 2 == 0) {
+    const float2 a2 = make_float2(a, a);
+#pragma unroll
+    for (int q = 0; q < D / 2; ++q) {
+      const float2 r = __ffma2_rn(a2, make_float2(x[2 * q], x[2 * q + 1]),
+                                  make_float2(y[2 * q], y[2 * q + 1]));
+      y[2 * q] = r.x;
+      y[2 * q + 1] = r.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < D; ++j) y[j] += a * x[j];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Lane-per-species variant for mass-action kinetics (d = 4, 8): a group of d lanes owns
 // one chunk and lane i owns species i, i.e. row i of every d x d matrix of the row being
@@ -350,15 +377,13 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
         }
 #pragma unroll
         for (int m = 0; m < D; ++m) {
-          real bm[D];
           if constexpr (BREG) {
-#pragma unroll
-            for (int j = 0; j < D; ++j) bm[j] = Breg[m][j];
+            axpy_row<D>(cj[m], Breg[m], Gr);
           } else {
+            real bm[D];
             ldrow_ro<real, D>(Brow + m * E, bm);
+            axpy_row<D>(cj[m], bm, Gr);
           }
-#pragma unroll
-          for (int j = 0; j < D; ++j) Gr[j] += cj[m] * bm[j];
         }
         real g = real(0);
 #pragma unroll
@@ -372,16 +397,13 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
           for (int m = 0; m < D; ++m) {
             real km[D];
             ldrow_p<real, D>(Kx + m * RS, km);
-            const real gk = cK * Gr[m];
-#pragma unroll
-            for (int j = 0; j < D; ++j) Kown[j] += gk * km[j];
+            axpy_row<D>(cK * Gr[m], km, Kown);
           }
         }
         __syncwarp(gm);
         strow_p<real, D>(Kx + i * RS, Kown);
         __syncwarp(gm);
-#pragma unroll
-        for (int j = 0; j < D; ++j) Kacc[j] += w * Kown[j];
+        axpy_row<D>(w, Kown, Kacc);
         accg += w * g;
         const real cs = stage == 2 ? h : real(0.5) * h;
         st = prev + cs * g;
@@ -411,8 +433,7 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
         for (int m = 0; m < D; ++m) {
           real pm[D];
           ldrow_p<real, D>(Px + m * RS, pm);
-#pragma unroll
-          for (int j = 0; j < D; ++j) np[j] += An[m] * pm[j];
+          axpy_row<D>(An[m], pm, np);
         }
         __syncwarp(gm);
         strow_p<real, D>(Px + i * RS, np);
