@@ -46,7 +46,7 @@ FP32_LANES_PER_SM, SMS = 128, 152
 # DRAM bytes per row of the fused iteration kernel from the committed ncu capture of the
 # same kernel (dram__bytes_read.sum + dram__bytes_write.sum over 8.39 M rows at B=512; the
 # traffic per row does not depend on B). Scaled by the rows of an average launch.
-FUSED_TRAFFIC_PER_ROW = (2.699873e9 + 2.674500e9) / 8388608
+FUSED_TRAFFIC_PER_ROW = (2.710245e9 + 2.687720e9) / 8388608
 # Mixed-precision d=16 mass-action linearise, per row: the RK4 step Jacobian chain in
 # float32 (3 products of 16x16 matrices, 3 * 2 d^3 flop); the float64 rate evaluations are
 # not counted.
