@@ -254,6 +254,33 @@ __device__ __forceinline__ void acc_resid_group(SeqAcc* acc, int64_t seq, real m
   }
 }
 
+// y += a x for a register row. Float32 rows go through the packed two-wide FMA (one
+// instruction for two lanes of the FP32 pipe; each half rounds like a scalar FMA, so the
+// results are the same as the scalar loop's): the kinetics kernel below is bound by
+// instruction issue, not by the FMA pipe.
+template <int D>
+__device__ __forceinline__ void axpy_row(double a, const double (&x)[D], double (&y)[D]) {
+#pragma unroll
+  for (int j = 0; j < D; ++j) y[j] += a * x[j];
+}
+
+template <int D>
+__device__ __forceinline__ void axpy_row(float a, const float (&x)[D], float (&y)[D]) {
+  if constexpr (D % 2 == 0) {
+    const float2 a2 = make_float2(a, a);
+#pragma unroll
+    for (int q = 0; q < D / 2; ++q) {
+      const float2 r = __ffma2_rn(a2, make_float2(x[2 * q], x[2 * q + 1]),
+                                  make_float2(y[2 * q], y[2 * q + 1]));
+      y[2 * q] = r.x;
+      y[2 * q + 1] = r.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < D; ++j) y[j] += a * x[j];
+  }
+}
+
 // Writes a D x D block held one row per lane of a D-lane group (row `lane` in registers)
 // to `dst` (16-byte aligned) with contiguous 16-byte stores across the group: the rows go
 // through `tile` ([D][D + 1] per group; the odd stride keeps both the row writes and the

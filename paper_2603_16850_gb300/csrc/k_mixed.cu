@@ -77,13 +77,23 @@ constexpr float kMixedFloor = 1e-6f;
 // One row of the mixed linearisation with the dynamics' value path (stage states, reaction
 // rates, slopes, F, residual) in V = float or double; the Jacobian path is float32 either
 // way. Writes E and b for the row and returns its scaled residual and squared residual.
+// A row of D floats from shared memory in 16-byte pieces (16-byte aligned).
+template <int D>
+__device__ __forceinline__ void ld_row4(const float* p, float (&v)[D]) {
+#pragma unroll
+  for (int j = 0; j < D; j += 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p + j);
+    v[j] = q.x; v[j + 1] = q.y; v[j + 2] = q.z; v[j + 3] = q.w;
+  }
+}
+
 template <class V, int D, bool RK4, int RPL>
 __device__ __forceinline__ void mixed_row(const MixedLinArgs& a, bool valid, int64_t row,
                                           int lane, unsigned gm, double s_prev_d,
                                           const int4 (&q)[RPL], const double (&kd)[RPL],
                                           const float (&kf)[RPL], int R, const int4* tt,
                                           const int32_t* ae, int e0, int e1,
-                                          float (*sG)[D + 1], float (*sK)[D], V* sRate,
+                                          float (*sG)[D + 4], float (*sK)[D + 4], V* sRate,
                                           float* sD1, float* sD2, float& mx, float& sq,
                                           int64_t seq, unsigned long long& key) {
   constexpr bool F64 = sizeof(V) == 8;
@@ -118,7 +128,8 @@ __device__ __forceinline__ void mixed_row(const MixedLinArgs& a, bool valid, int
       }
     }
 #pragma unroll
-    for (int j = 0; j < D; ++j) sG[lane][j] = 0.f;
+    for (int j = 0; j < D; j += 4)
+      *reinterpret_cast<float4*>(&sG[lane][j]) = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncwarp(gm);
     // this species' slope and its row of the rate Jacobian, from its own reactions
     V g = V(0);
@@ -134,25 +145,23 @@ __device__ __forceinline__ void mixed_row(const MixedLinArgs& a, bool valid, int
     }
     __syncwarp(gm);
     float Gi[D], Kn[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) Gi[j] = sG[lane][j];
+    ld_row4<D>(&sG[lane][0], Gi);
 #pragma unroll
     for (int j = 0; j < D; ++j) Kn[j] = Gi[j];
     if (stage > 0) {
 #pragma unroll
       for (int m = 0; m < D; ++m) {
-        const float gmv = cK * Gi[m];
-#pragma unroll
-        for (int j = 0; j < D; ++j) Kn[j] += gmv * sK[m][j];
+        float km[D];
+        ld_row4<D>(&sK[m][0], km);  // the same row for every lane of the group
+        axpy_row<D>(cK * Gi[m], km, Kn);
       }
     }
     __syncwarp(gm);
     const float wf = (stage == 1 || stage == 2) ? 2.f : 1.f;
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
-      sK[lane][j] = Kn[j];
-      Kacc[j] += wf * Kn[j];
-    }
+    for (int j = 0; j < D; j += 4)
+      *reinterpret_cast<float4*>(&sK[lane][j]) = make_float4(Kn[j], Kn[j + 1], Kn[j + 2], Kn[j + 3]);
+    axpy_row<D>(wf, Kn, Kacc);
     acc += w * g;
     const V cs = stage == 2 ? h : V(0.5) * h;
     c = s_prev + cs * g;
@@ -191,10 +200,11 @@ __global__ void __launch_bounds__(128) k_lin_ma_mixed(MixedLinArgs a) {
   constexpr int GROUPS = 128 / D;
   constexpr int RMAX = 64;         // reactions per network held in shared memory
   constexpr int RPL = RMAX / D;    // reactions per lane
-  __shared__ float sG[GROUPS][D][D + 1];
-  // one padding row per group: the two groups of a warp read their K rows from banks 16
-  // apart (same-bank broadcasts of different groups would serialise)
-  __shared__ __align__(16) float sK[GROUPS][D + 1][D];
+  // rows padded to D + 4 floats: 16-byte row accesses of eight lanes fall in distinct
+  // banks; one padding row per group of sK: the two groups of a warp read their (common)
+  // K rows from banks 20 apart (same-bank reads of different groups would serialise)
+  __shared__ __align__(16) float sG[GROUPS][D][D + 4];
+  __shared__ __align__(16) float sK[GROUPS][D + 1][D + 4];
   __shared__ double sRate[GROUPS][RMAX];  // float rates use the first half in float32 mode
   __shared__ float sD1[GROUPS][RMAX], sD2[GROUPS][RMAX];  // d rate / d c_i1, d c_i2
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
