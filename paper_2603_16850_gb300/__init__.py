@@ -229,36 +229,41 @@ def _run_solve(dyn, B, T, offsets, s0, x, s_init, opts, stream, workspace, devic
 
 
 def deer_solve(dyn: Dynamics, s0: torch.Tensor, T: int, x: Optional[torch.Tensor] = None, *,
-               s_init: Optional[torch.Tensor] = None, stream=None, workspace=None, **opts):
+               s_init: Optional[torch.Tensor] = None, stream=None, workspace=None, out=None,
+               **opts):
     """Solve ``B = s0.shape[0]`` sequences of length T. Returns (s [B*T][d], SolveInfo).
 
     Options (see deer_options in include/deer.h): jac ('full'|'diag'|'identity'|'zero'),
     damp ('none'|'elk'|'scale'|'clip'), damp_param, tol, max_iters, init
     ('zeros'|'s0'|'jacobi'|'user'), prec ('fp64'|'fp32'|'mixed_bf16'), reset, chunk,
     confirm, window (sliding window: freeze the converged prefix of each sequence).
+    Host inputs are copied to the GPU and the result back to the host, into ``out`` when
+    given (a preallocated, ideally pinned, host tensor [B*T][d]).
     """
     opts = _opt_defaults(opts)
     host = not s0.is_cuda
     device = torch.device("cuda") if host else s0.device
     if host:
+        _check_out(out, (s0.shape[0] * int(T), dyn.d), _dtype(opts["prec"]))
         dyn, s0, x = _to_device(dyn, s0, x, device)
     s, info = _run_solve(dyn, s0.shape[0], int(T), None, s0, x, s_init, opts, stream,
                          workspace, device)
-    return (_to_host(s) if host else s), info
+    return (_to_host(s, out) if host else s), info
 
 
 def deer_solve_batched(dyn: Dynamics, s0: torch.Tensor, offsets, x: Optional[torch.Tensor] = None,
-                       *, s_init=None, stream=None, workspace=None, **opts):
+                       *, s_init=None, stream=None, workspace=None, out=None, **opts):
     """Ragged batch: sequence b owns rows offsets[b]..offsets[b+1]-1 of the packed output."""
     opts = _opt_defaults(opts)
     offsets = [int(v) for v in (offsets.tolist() if hasattr(offsets, "tolist") else offsets)]
     host = not s0.is_cuda
     device = torch.device("cuda") if host else s0.device
     if host:
+        _check_out(out, (int(offsets[-1]), dyn.d), _dtype(opts["prec"]))
         dyn, s0, x = _to_device(dyn, s0, x, device)
     s, info = _run_solve(dyn, s0.shape[0], 0, offsets, s0, x, s_init, opts, stream, workspace,
                          device)
-    return (_to_host(s) if host else s), info
+    return (_to_host(s, out) if host else s), info
 
 
 def deer_rollout(dyn: Dynamics, s0: torch.Tensor, T: int = 0, x=None, *, offsets=None,
@@ -344,10 +349,21 @@ def _to_device(dyn, s0, x, device):
     return dyn, s0, x
 
 
-def _to_host(s):
-    out = torch.empty(s.shape, dtype=s.dtype, pin_memory=True)
+def _to_host(s, out=None):
+    """Copy a device result to the host: into ``out`` (a host tensor of the same shape and
+    dtype; pinned for full copy bandwidth) or into a newly pinned buffer. Pinning gigabytes
+    takes longer than the copy itself, so callers that solve repeatedly pass ``out``."""
+    if out is None:
+        out = torch.empty(s.shape, dtype=s.dtype, pin_memory=True)
+    _check_out(out, tuple(s.shape), s.dtype)
     out.copy_(s)
     return out
+
+
+def _check_out(out, shape, dtype):
+    if out is not None and (out.is_cuda or tuple(out.shape) != tuple(shape) or
+                            out.dtype != dtype or not out.is_contiguous()):
+        raise ValueError(f"out must be a contiguous host tensor {tuple(shape)} {dtype}")
 
 
 class DeerFunction(torch.autograd.Function):

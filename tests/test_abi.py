@@ -136,3 +136,18 @@ def test_second_workload_kinds_sizes_and_checks(lib):
     pd = N.deer_dynamics(N.KIND["permute"], 5, 5, 0, 0.0, 8, 0, 0, 0)
     assert lib.deer_solve(C.byref(pd), 1, 10, 8, None, 8, C.byref(o), 256, 1 << 20, None,
                           info) == N.DEER_ERR_INVALID
+
+
+def test_host_output_buffer_checked_before_any_work():
+    """deer_solve with host inputs validates the caller's output buffer (shape, dtype,
+    host residency) before touching the device."""
+    import torch
+
+    import paper_2603_16850_gb300 as deer
+    dyn = deer.Dynamics.lorenz96(torch.full((1,), 8.0), 5, 0.01)
+    s0 = torch.full((2, 5), 8.0, dtype=torch.float64)
+    for bad in (torch.empty((2 * 7, 5)),                         # wrong dtype
+                torch.empty((2 * 6, 5), dtype=torch.float64),    # wrong shape
+                torch.empty((5, 2 * 7), dtype=torch.float64).t()):  # not contiguous
+        with pytest.raises(ValueError, match="out must be"):
+            deer.deer_solve(dyn, s0, 7, out=bad, jac="full")

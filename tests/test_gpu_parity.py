@@ -506,3 +506,23 @@ def test_dense_elk_fp32_ragged_converges(window):
         sub = odyn.MassAction(p["topology"][b:b + 1], p["params"][b:b + 1], p["dt"], "rk4", d=8)
         roll = onewton.rollout(sub, p["s0"][b:b + 1], n)[0]
         assert _relerr(sn[off[b]:off[b + 1]], roll) <= 1e-5
+
+
+def test_host_inputs_round_trip_into_preallocated_output():
+    """The end-to-end form of the API: host (pinned) inputs are copied to the GPU, the
+    trajectory comes back into the caller's pinned buffer, and equals the device-resident
+    solve bit for bit; a mismatched output buffer is rejected before any work."""
+    deer = _deer()
+    p = _ma_problem(4, 8, 12, 300, seed=21)
+    dyn_d = _ma_dyn(p, torch.float32)
+    s0_d = _t(p["s0"], torch.float32)
+    opts = dict(jac="full", init="zeros", reset=True, window=True, **FP32)
+    s_dev, info_d = deer.deer_solve(dyn_d, s0_d, 300, **opts)
+    dyn_h = deer.Dynamics.massaction(dyn_d.topology.cpu().pin_memory(),
+                                     dyn_d.params.cpu().pin_memory(), 8, p["dt"])
+    out = torch.empty((4 * 300, 8), dtype=torch.float32, pin_memory=True)
+    s_h, info_h = deer.deer_solve(dyn_h, s0_d.cpu().pin_memory(), 300, out=out, **opts)
+    assert s_h.data_ptr() == out.data_ptr() and not s_h.is_cuda
+    assert torch.equal(s_h, s_dev.cpu()) and info_h.iters.tolist() == info_d.iters.tolist()
+    with pytest.raises(ValueError):
+        deer.deer_solve(dyn_h, s0_d.cpu(), 300, out=torch.empty((10, 8)), **opts)
