@@ -243,6 +243,44 @@ def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64):
             "linearize": lin_entry}
 
 
+def gru_elk_measurement(deer, dev, stream, B=64, lams=(0.01, 0.1, 1.0, 10.0)):
+    """The damped variant of the GRU workload (quasi-ELK, Sec. 4.3 with the diagonal
+    Jacobian): the same d=64, T=65536, B=64 problem, FP32, tol 1e-5 x2, for a sweep of the
+    damping lambda = 1/sigma^2 (lambda -> 0 is quasi-DEER; larger lambda damps more, and
+    the untrained GRU is contracting, so damping only slows it down: lambda = 100 and 1000
+    did not converge within 2000 iterations). Converged state-steps/s and Newton
+    iterations per lambda."""
+    import numpy as np
+    import torch
+    import synth
+    T, d = 65536, 64
+    g = synth.gru(B, T, d, d, seed=0, dtype=np.float32)
+    dyn = deer.Dynamics.gru(torch.tensor(g["W"], dtype=torch.float32, device=dev),
+                            torch.tensor(g["U"], dtype=torch.float32, device=dev))
+    x = torch.tensor(g["x"].reshape(-1, d), device=dev)
+    s0 = torch.zeros((B, d), dtype=torch.float32, device=dev)
+    rows = []
+    for lam in lams:
+        opts = dict(jac="diag", damp="elk", damp_param=lam, tol=1e-5, confirm=2, prec="fp32",
+                    init="zeros", max_iters=1000)
+        ws_ = torch.empty(deer.deer_workspace_bytes(dyn, B, B * T, **opts), dtype=torch.uint8,
+                          device=dev)
+        deer.deer_solve(dyn, s0, T, x, workspace=ws_, stream=stream, **opts)  # warm
+        torch.cuda.synchronize()
+        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        e0.record(stream)
+        s, info = deer.deer_solve(dyn, s0, T, x, workspace=ws_, stream=stream, **opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        rows.append({"lambda": lam, "value": B * T / (ms / 1000.0), "unit": UNIT, "ms": ms,
+                     "newton_iters_max": int(info.iters.max()),
+                     "converged": bool(info.converged.all())})
+        del ws_
+    return {"workload": f"GRU d=64 d_in=64 T=65536 B={B}, quasi-ELK (diagonal Kalman-filter "
+                        "step), FP32, tol 1e-5 x2", "sweep": rows}
+
+
 def lle_measurement(deer, dyn, s0, s, T, d, stream, n_sys=64):
     """Largest Lyapunov exponent (Ch. 5) along the converged trajectories of the first
     n_sys systems of the headline workload: the thesis's predictor of parallel-Newton
@@ -482,6 +520,8 @@ def run_only(args):
                                    B=args.batch or 64)
     elif args.only == "ragged_mixed":
         out = ragged_mixed_measurement(deer, N, lib, dev, stream, B=args.batch or 1000)
+    elif args.only == "gru_elk":
+        out = gru_elk_measurement(deer, dev, stream, B=args.batch or 64)
     elif args.only == "threshold":
         gains = tuple(float(v) for v in args.gains.split(",")) if args.gains else (0.5, 1.0, 2.0)
         out = threshold_measurement(deer, N, lib, dev, stream, gains=gains)
@@ -619,6 +659,7 @@ def run(args):
     if rank == 0 and ws == 1 and not args.no_extra:
         extra["lle"] = lle_measurement(deer, dyn, s0, s, T, d, stream)
         extra["gru_quasi_deer"] = gru_diag_measurement(deer, N, lib, dev, stream)
+        extra["gru_quasi_elk"] = gru_elk_measurement(deer, dev, stream)
         extra["adjoint"] = adjoint_measurement(deer, N, lib, dev, stream)
         extra["ragged_mixed"] = ragged_mixed_measurement(deer, N, lib, dev, stream)
         extra["threshold"] = threshold_measurement(deer, N, lib, dev, stream)
@@ -672,8 +713,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary GRU quasi-DEER measurement")
-    ap.add_argument("--only", default="", choices=["", "gru", "adjoint", "ragged_mixed",
-                                                   "threshold"],
+    ap.add_argument("--only", default="", choices=["", "gru", "gru_elk", "adjoint",
+                                                   "ragged_mixed", "threshold"],
                     help="run one secondary workload alone (with --batch) and print it")
     ap.add_argument("--gains", default="",
                     help="--only threshold: comma-separated RNN gains g (default 0.5,1.0,2.0)")
