@@ -274,6 +274,15 @@ int32_t deer_get_tensor_cores(void);
 /* Number of kernels this library enqueued since load (all entry points, all threads). */
 int64_t deer_kernel_launch_count(void);
 
+/* Self-test of the bounded device waits (the failure path behind DEER_ERR_TIMEOUT): runs
+   the single-pass look-back scan over one sequence of two tiles whose first tile is never
+   scanned, so the second tile's wait for its predecessor's flag runs out at the spin limit
+   (a fraction of a second); the kernel then records the timeout and finishes, leaving the
+   context usable. Allocates and frees about 100 KB of device memory; synchronises the
+   stream. Returns DEER_ERR_TIMEOUT when the wait gave up as designed (the expected
+   result), DEER_OK if it did not, DEER_ERR_CUDA on a CUDA error. */
+deer_status deer_selftest_wait_timeout(deer_stream_t stream);
+
 /* Per-phase device time of deer_solve / deer_solve_batched, measured with CUDA events on
    the solver's stream while profiling is enabled (off by default; costs one extra stream
    synchronisation per iteration). Phase p: 0 set-up, 1 linearise + residual, 2

@@ -308,6 +308,13 @@ def deer_grad(dyn: Dynamics, s0, T, s_star, dl_ds, x=None, *, prec="fp64", chunk
     return dparams, ds0
 
 
+def selftest_wait_timeout(stream=None) -> int:
+    """Run the library's bounded-wait self-test (deer_selftest_wait_timeout): a look-back
+    scan whose predecessor tile never publishes. Returns the status: DEER_ERR_TIMEOUT (-5)
+    is the designed outcome."""
+    return int(N.load().deer_selftest_wait_timeout(_stream_handle(stream)))
+
+
 def deer_lle(dyn: Dynamics, s0, T: int, s, u0=None, x=None, *, prec="fp64", stream=None,
              workspace=None):
     """Largest Lyapunov exponent estimate along trajectories (deer_lle): s [B*T][d] (a

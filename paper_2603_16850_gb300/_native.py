@@ -77,6 +77,7 @@ SIGNATURES = {
                                        C.POINTER(deer_info)]),
     "deer_noalloc_scratch_bytes": (C.c_size_t, []),
     "deer_kernel_launch_count": (C.c_int64, []),
+    "deer_selftest_wait_timeout": (C.c_int32, [C.c_void_p]),
     "deer_profile_enable": (None, [C.c_int32]),
     "deer_set_tensor_cores": (None, [C.c_int32]),
     "deer_lle_workspace_bytes": (C.c_size_t, [C.POINTER(deer_dynamics), C.c_int64, C.c_int64,

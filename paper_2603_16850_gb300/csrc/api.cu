@@ -973,6 +973,63 @@ deer_status deer_grad(const deer_dynamics* f, int64_t batch, int64_t T, const vo
                            workspace_bytes, st);
 }
 
+deer_status deer_selftest_wait_timeout(deer_stream_t stream) {
+  // one sequence of two look-back tiles (d = 4, 1024 rows each) whose first tile is never
+  // dealt: the CTA scanning tile 1 waits for tile 0's flag, which nothing sets, until its
+  // spin limit, then reports through the status word and finishes
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  constexpr int D = 4;
+  const int L = diag_lb_chunk(D);
+  const int64_t N = 2 * (int64_t)L;
+  struct Host {
+    int64_t offsets[2], chunk_first[2], act_seq[1], act_row_off[2], act_chunk_off[2];
+  } h{{0, N}, {0, 2}, {0}, {0, N}, {0, 2}};
+  size_t p = 0;
+  auto take = [&](size_t bytes) { size_t at = p; p = align_up(p + bytes); return at; };
+  const size_t o_host = take(sizeof(Host)), o_b = take(N * D * 4),
+               o_s = take(N * D * 4), o_s0 = take(D * 4), o_ticket = take(4),
+               o_flags = take(2 * 4), o_agg = take(2 * 2 * D * 4), o_pre = take(2 * D * 4),
+               o_status = take(sizeof(Flags));
+  char* ws = nullptr;
+  DEER_CK(cudaMalloc(&ws, p));
+  deer_status ret = DEER_OK;
+  do {
+    if (cudaMemsetAsync(ws, 0, p, st) != cudaSuccess ||
+        cudaMemcpyAsync(ws + o_host, &h, sizeof(Host), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess) {
+      ret = DEER_ERR_CUDA;
+      break;
+    }
+    const Host* dh = reinterpret_cast<const Host*>(ws + o_host);
+    Batch bt{1, N, dh->offsets, dh->chunk_first, 2, L, ilog2(L), dh->act_seq, dh->act_row_off,
+             dh->act_chunk_off, 1, N, 2};
+    // constant transition 0.5 (a is not read), offsets b and s0 zero
+    DiagLBArgs<float> la{bt, D, 1, 0.5f, nullptr, reinterpret_cast<const float*>(ws + o_b),
+                         reinterpret_cast<const float*>(ws + o_s0),
+                         reinterpret_cast<float*>(ws + o_s),
+                         reinterpret_cast<unsigned*>(ws + o_ticket),
+                         reinterpret_cast<unsigned*>(ws + o_flags),
+                         reinterpret_cast<float*>(ws + o_agg),
+                         reinterpret_cast<float*>(ws + o_pre), 1u, 0,
+                         reinterpret_cast<Flags*>(ws + o_status), 0, 0.f};
+    if (launch_diag_lookback<float>(la, st, 1u) != cudaSuccess) {
+      ret = DEER_ERR_CUDA;
+      break;
+    }
+    Flags hf{};
+    if (cudaMemcpyAsync(&hf, ws + o_status, sizeof(Flags), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      ret = DEER_ERR_CUDA;
+      break;
+    }
+    ret = hf.timeout ? DEER_ERR_TIMEOUT : DEER_OK;
+  } while (false);
+  if (cudaStreamSynchronize(st) != cudaSuccess) ret = DEER_ERR_CUDA;
+  if (cudaFree(ws) != cudaSuccess) ret = DEER_ERR_CUDA;
+  return ret;
+}
+
 int64_t deer_kernel_launch_count(void) { return g_launches.load(); }
 
 void deer_profile_enable(int32_t on) { g_prof_on.store(on ? 1 : 0); }

@@ -338,11 +338,20 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 8 : 4) k_diag_lb(Diag
 }
 
 template <class real>
-cudaError_t launch_diag_lookback(const DiagLBArgs<real>& a, cudaStream_t st) {
+cudaError_t launch_diag_lookback(const DiagLBArgs<real>& a, cudaStream_t st,
+                                 unsigned first_ticket) {
   if (a.bt.act_chunks == 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), st);
+  // tiles are dealt from first_ticket on (0 in every solve; the wait self-test starts at 1,
+  // so that no CTA ever publishes tile 0)
+  static const unsigned kOne = 1u;
+  cudaError_t e = first_ticket == 0
+                      ? cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), st)
+                      : (first_ticket == 1 ? cudaMemcpyAsync(a.ticket, &kOne, sizeof(unsigned),
+                                                             cudaMemcpyHostToDevice, st)
+                                           : cudaErrorInvalidValue);
   if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)a.bt.act_chunks;
+  if ((int64_t)first_ticket >= a.bt.act_chunks) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)(a.bt.act_chunks - first_ticket);
   switch (a.d) {
     case 4: k_diag_lb<real, 4><<<grid, 256, 0, st>>>(a); break;
     case 8: k_diag_lb<real, 8><<<grid, 256, 0, st>>>(a); break;
@@ -355,7 +364,9 @@ cudaError_t launch_diag_lookback(const DiagLBArgs<real>& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template cudaError_t launch_diag_lookback<float>(const DiagLBArgs<float>&, cudaStream_t);
-template cudaError_t launch_diag_lookback<double>(const DiagLBArgs<double>&, cudaStream_t);
+template cudaError_t launch_diag_lookback<float>(const DiagLBArgs<float>&, cudaStream_t,
+                                                 unsigned);
+template cudaError_t launch_diag_lookback<double>(const DiagLBArgs<double>&, cudaStream_t,
+                                                  unsigned);
 
 }  // namespace deer

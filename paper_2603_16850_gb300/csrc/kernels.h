@@ -218,7 +218,8 @@ struct DiagLBArgs {
 inline int diag_lb_chunk(int d) { return d >= 8 ? 8192 / d : 1024; }
 
 template <class real>
-cudaError_t launch_diag_lookback(const DiagLBArgs<real>& a, cudaStream_t st);
+cudaError_t launch_diag_lookback(const DiagLBArgs<real>& a, cudaStream_t st,
+                                 unsigned first_ticket = 0);
 
 }  // namespace deer
 

@@ -526,3 +526,20 @@ def test_host_inputs_round_trip_into_preallocated_output():
     assert torch.equal(s_h, s_dev.cpu()) and info_h.iters.tolist() == info_d.iters.tolist()
     with pytest.raises(ValueError):
         deer.deer_solve(dyn_h, s0_d.cpu(), 300, out=torch.empty((10, 8)), **opts)
+
+
+def test_bounded_wait_times_out_and_context_stays_usable():
+    """The failure path of the device waits, made on the GPU without a fault: the look-back
+    scan's wait for a predecessor flag that nothing sets runs out at its spin limit, the
+    kernel records DEER_ERR_TIMEOUT and finishes, and the next solve runs normally."""
+    import time
+    deer = _deer()
+    t0 = time.perf_counter()
+    st = deer.selftest_wait_timeout()
+    torch.cuda.synchronize()
+    assert st == -5 and time.perf_counter() - t0 < 30.0
+    p = synth.brusselator(T=200)
+    dyn = deer.Dynamics.brusselator(_t(p["params"]), p["dt"])
+    s, info = deer.deer_solve(dyn, _t(p["s0"]), 200, jac="full", tol=1e-12, init="s0")
+    ref = onewton.rollout(odyn.Brusselator(p["params"], p["dt"]), p["s0"], 200)[0]
+    assert bool(info.converged[0]) and _relerr(s.cpu().numpy(), ref) <= 1e-10
