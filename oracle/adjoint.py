@@ -8,6 +8,8 @@ Test infrastructure only. For a loss l(s_{1:T}) with cotangents g_t = dl/ds_t:
 * ``forward_sensitivity_grad`` - Eq. bptt_lds run forward: S_t = A_t S_{t-1} +
   df_t/dtheta, dl/dtheta = sum_t g_t^T S_t (an independent route to the same number).
 * ``fd_grad`` - central finite differences of the loss of the rollout.
+* ``input_grad`` - dl/dx_t = lambda_t^T df_t/dx_t for inputs curried into f_t, pinned by
+  ``fd_input_grad`` (central differences with respect to single input entries).
 """
 from __future__ import annotations
 
@@ -42,6 +44,33 @@ def adjoint_grad(dyn, s0, s, g):
         cur = back + (g[:, t - 2] if t >= 2 else 0.0)
     ds0 = back
     return dtheta, ds0, lam
+
+
+def input_grad(dyn, s0, s, lam):
+    """dl/dx_t = lambda_t^T d f_t / d x_t (s_{t-1}) for every step, from the adjoint
+    states lambda [B, T, d] of ``adjoint_grad`` (the inputs are curried into f_t,
+    Sec. 2.1). Returns [B, T, d_in]."""
+    B, T, d = s.shape
+    out = []
+    for t in range(1, T + 1):
+        prev = s[:, t - 2] if t >= 2 else s0
+        out.append(np.einsum("bi,bik->bk", lam[:, t - 1], dyn.dinputs(t, prev)))
+    return np.stack(out, axis=1)
+
+
+def fd_input_grad(make_dyn, x, s0, T, y, indices, h=1e-6):
+    """Central differences of the rollout loss with respect to single input entries
+    x[b, t, k] (indices (b, t, k)); make_dyn(x) -> dynamics."""
+    out = []
+    for (b, t, k) in indices:
+        xp = np.array(x, dtype=np.float64, copy=True)
+        xm = np.array(x, dtype=np.float64, copy=True)
+        xp[b, t, k] += h
+        xm[b, t, k] -= h
+        lp = sq_loss(rollout(make_dyn(xp), s0, T), y)[b]
+        lm = sq_loss(rollout(make_dyn(xm), s0, T), y)[b]
+        out.append((lp - lm) / (2.0 * h))
+    return np.array(out)
 
 
 def forward_sensitivity_grad(dyn, s0, s, g):

@@ -215,6 +215,18 @@ class GRU:
         return J
 
 
+    def dinputs(self, t, h):
+        """d h' / d x_t [B, d, d_in] at h, through the three gates (chain rule)."""
+        z, r, ht = self._gates(t, h)
+        Wz, Wr, Wh = self.W
+        Uz, Ur, Uh = self.U
+        dz = (z * (1.0 - z))[:, :, None] * Wz[None]                       # dz_i/dx_k
+        dr = (r * (1.0 - r))[:, :, None] * Wr[None]                       # dr_m/dx_k
+        # a = W_h x + U_h (r * h): da_i/dx_k = W_h[i,k] + sum_m U_h[i,m] h_m dr_m/dx_k
+        da = Wh[None] + np.einsum("im,bm,bmk->bik", Uh, h, dr)
+        return (ht - h)[:, :, None] * dz + (z * (1.0 - ht * ht))[:, :, None] * da
+
+
 class Linear:
     """Affine recurrence s_t = A s_{t-1} + x_t (an LDS, Eq. lds), A [d][d] shared,
     x [B][T][d] (x may be None for s_t = A s_{t-1})."""
@@ -233,6 +245,10 @@ class Linear:
 
     def jac(self, t, s):
         return np.broadcast_to(self.A, (s.shape[0], self.d, self.d)).copy()
+
+    def dinputs(self, t, s):
+        """d f / d x_t = I."""
+        return np.broadcast_to(np.eye(self.d), (s.shape[0], self.d, self.d)).copy()
 
 
 class MeanFieldRNN:
@@ -260,6 +276,10 @@ class MeanFieldRNN:
         sech2 = 1.0 - np.tanh(s) ** 2
         W = np.broadcast_to(self.W, (s.shape[0], self.d, self.d))
         return W * sech2[:, None, :]
+
+    def dinputs(self, t, s):
+        """d f / d u_t = I (the input enters additively)."""
+        return np.broadcast_to(np.eye(self.d), (s.shape[0], self.d, self.d)).copy()
 
 
 class TwoWellLangevin:
@@ -316,6 +336,11 @@ class TwoWellLangevin:
 
     def jac(self, t, s):
         return np.eye(self.d)[None] - self.eps * self.hess_phi(s)
+
+    def dinputs(self, t, s):
+        """d f / d xi_t = sqrt(2 eps) I (the noise draws are the inputs)."""
+        return np.broadcast_to(np.sqrt(2.0 * self.eps) * np.eye(self.d),
+                               (s.shape[0], self.d, self.d)).copy()
 
 
 # Dormand-Prince 5(4) pair (Dormand & Prince, 1980): nodes, stage matrix and the weights

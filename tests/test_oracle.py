@@ -637,3 +637,41 @@ def test_word_problem_newton_one_iteration_others_near_T():
     assert list(its["full"]) == [1, 1]
     for m in ("diag", "identity", "zero"):
         assert np.all(its[m] >= T // 2)
+
+
+@pytest.mark.parametrize("kind", ["gru", "rnn", "langevin", "linear"])
+def test_input_gradient_matches_finite_differences(kind):
+    """dl/dx_t from the adjoint states (lambda_t^T df_t/dx_t) against central differences
+    of the rollout loss in single input entries; the GRU's input derivative goes through
+    all three gates."""
+    B, T, d = 2, 12, 4
+    if kind == "gru":
+        p = synth.gru(B, T, d, d, seed=3)
+        x = p["x"]
+        mk = lambda xx: dynamics.GRU(p["W"], p["U"], xx)  # noqa: E731
+        s0 = np.random.default_rng(1).standard_normal((B, d)) * 0.5
+    elif kind == "rnn":
+        p = synth.mean_field_rnn(B, T, d, 1.2, seed=3)
+        x = p["x"]
+        mk = lambda xx: dynamics.MeanFieldRNN(p["W"], xx)  # noqa: E731
+        s0 = p["s0"]
+    elif kind == "langevin":
+        p = synth.two_well(B, T, d, seed=3)
+        x = p["x"]
+        mk = lambda xx: dynamics.TwoWellLangevin(p["params"], p["dt"], xx, d=d)  # noqa: E731
+        s0 = p["s0"]
+    else:
+        p = synth.linear_lds(B, T, d, seed=3)
+        x = p["x"]
+        mk = lambda xx: dynamics.Linear(p["A"], xx)  # noqa: E731
+        s0 = p["s0"]
+    dyn = mk(x)
+    s = newton.rollout(dyn, s0, T)
+    y = s + 0.3 * synth.targets_noise(s.shape, seed=4)
+    g = adjoint.sq_loss_cotangent(s, y)
+    _, _, lam = adjoint.adjoint_grad(dyn, s0, s, g)
+    gx = adjoint.input_grad(dyn, s0, s, lam)
+    idx = [(0, 0, 1), (1, 5, 0), (0, 11, 3), (1, 7, 2)]
+    fd = adjoint.fd_input_grad(mk, x, s0, T, y, idx, h=1e-6)
+    got = np.array([gx[b, t, k] for (b, t, k) in idx])
+    assert np.allclose(got, fd, rtol=1e-6, atol=1e-7)
