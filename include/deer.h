@@ -219,6 +219,18 @@ deer_status deer_grad(const deer_dynamics* f, int64_t batch, int64_t T, const vo
                       void* dl_ds0, const deer_options* opt, void* workspace,
                       size_t workspace_bytes, deer_stream_t stream);
 
+/* deer_grad plus the gradient with respect to the inputs curried into f_t (Sec. 2.1):
+   dl_dx [batch*T][d_in] (the layout of x) receives lambda_t^T df_t/dx_t evaluated at
+   s_{t-1}, or NULL. Available for the kinds with differentiable inputs: the GRU (through
+   its three gates), the affine recurrence and the mean-field RNN (additive inputs), and
+   the Langevin kind (noise draws, scaled by sqrt(2 dt)); DEER_ERR_UNSUPPORTED for the
+   others or when x is NULL. Same workspace as deer_grad. */
+deer_status deer_grad_ex(const deer_dynamics* f, int64_t batch, int64_t T, const void* s0,
+                         const void* x, const void* s_star, const void* dl_ds,
+                         void* dl_dparams, void* dl_ds0, void* dl_dx,
+                         const deer_options* opt, void* workspace, size_t workspace_bytes,
+                         deer_stream_t stream);
+
 /* Largest Lyapunov exponent along trajectories (Ch. 5, Algorithm alg:LLE_estimate): for
    each of `batch` sequences of T steps, the unit vector u_0 = u0[b] is pushed through the
    step Jacobians J_t = df_t/ds evaluated at s_{t-1} (s_0 for t = 1) and renormalised

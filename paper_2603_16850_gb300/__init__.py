@@ -284,10 +284,12 @@ def deer_rollout(dyn: Dynamics, s0: torch.Tensor, T: int = 0, x=None, *, offsets
 
 
 def deer_grad(dyn: Dynamics, s0, T, s_star, dl_ds, x=None, *, prec="fp64", chunk=0,
-              stream=None, workspace=None, want_ds0=True):
-    """Adjoint gradient at the converged trajectory. Returns (dl/dparams [B][P], dl/ds0);
-    dl/dparams is None for kinds without per-sequence trainable parameters (only the
-    Brusselator's (a, b) and the mass-action rate constants are differentiated)."""
+              stream=None, workspace=None, want_ds0=True, want_dx=False):
+    """Adjoint gradient at the converged trajectory. Returns (dl/dparams [B][P], dl/ds0),
+    plus dl/dx (the layout of x) when ``want_dx`` (deer_grad_ex: GRU, affine, mean-field
+    RNN and Langevin inputs); dl/dparams is None for kinds without per-sequence trainable
+    parameters (only the Brusselator's (a, b) and the mass-action rate constants are
+    differentiated)."""
     lib = N.load()
     B = s0.shape[0]
     dt = _dtype(prec)
@@ -300,12 +302,17 @@ def deer_grad(dyn: Dynamics, s0, T, s_star, dl_ds, x=None, *, prec="fp64", chunk
     need = lib.deer_grad_workspace_bytes(C.byref(cdyn), B, int(T), C.byref(o))
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=s0.device)
-    st = lib.deer_grad(C.byref(cdyn), B, int(T), _ptr(s0), _ptr(x), _ptr(s_star), _ptr(dl_ds),
-                       _ptr(dparams), _ptr(ds0), C.byref(o), _ptr(workspace), workspace.numel(),
-                       _stream_handle(stream))
+    dx = None
+    if want_dx:
+        if x is None:
+            raise ValueError("want_dx needs the inputs x")
+        dx = torch.empty_like(x)
+    st = lib.deer_grad_ex(C.byref(cdyn), B, int(T), _ptr(s0), _ptr(x), _ptr(s_star),
+                          _ptr(dl_ds), _ptr(dparams), _ptr(ds0), _ptr(dx), C.byref(o),
+                          _ptr(workspace), workspace.numel(), _stream_handle(stream))
     if st != N.DEER_OK:
         raise N.DeerError(st, "deer_grad")
-    return dparams, ds0
+    return (dparams, ds0, dx) if want_dx else (dparams, ds0)
 
 
 def selftest_wait_timeout(stream=None) -> int:
@@ -377,14 +384,15 @@ class DeerFunction(torch.autograd.Function):
     """Differentiable solve: forward = deer_solve (any mode; the result is the fixed point),
     backward = deer_grad (reverse adjoint scan at the fixed point, implicit
     differentiation, no unrolled Newton history). Gradients flow to the per-sequence
-    parameters and to s0."""
+    parameters, to s0 and, for the kinds with differentiable inputs, to x."""
 
     @staticmethod
     def forward(ctx, params, s0, dyn: Dynamics, T: int, x, opts: dict):
         d2 = Dynamics(dyn.kind, dyn.d, params.detach().contiguous(), dyn.d_in, dyn.n_reactions,
                       dyn.dt, dyn.params_stride, dyn.topology, dyn.topology_stride)
-        s, info = deer_solve(d2, s0.detach().contiguous(), T, x, **opts)
-        ctx.dyn, ctx.T, ctx.x, ctx.prec = d2, T, x, opts.get("prec", "fp64")
+        xd = None if x is None else x.detach().contiguous()
+        s, info = deer_solve(d2, s0.detach().contiguous(), T, xd, **opts)
+        ctx.dyn, ctx.T, ctx.x, ctx.prec = d2, T, xd, opts.get("prec", "fp64")
         ctx.save_for_backward(s0.detach(), s)
         ctx.info = info
         return s
@@ -392,6 +400,10 @@ class DeerFunction(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         s0, s = ctx.saved_tensors
-        dp, ds0 = deer_grad(ctx.dyn, s0, ctx.T, s, g.contiguous(), ctx.x, prec=ctx.prec)
+        want_dx = ctx.x is not None and ctx.needs_input_grad[4]
+        out = deer_grad(ctx.dyn, s0, ctx.T, s, g.contiguous(), ctx.x, prec=ctx.prec,
+                        want_dx=want_dx)
+        dp, ds0 = out[0], out[1]
+        dx = out[2] if want_dx else None
         return (None if dp is None else dp.reshape(ctx.dyn.params.shape)), ds0, None, None, \
-            None, None
+            dx, None

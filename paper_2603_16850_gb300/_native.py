@@ -69,6 +69,10 @@ SIGNATURES = {
     "deer_grad": (C.c_int32, [C.POINTER(deer_dynamics), C.c_int64, C.c_int64, C.c_void_p,
                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                               C.POINTER(deer_options), C.c_void_p, C.c_size_t, C.c_void_p]),
+    "deer_grad_ex": (C.c_int32, [C.POINTER(deer_dynamics), C.c_int64, C.c_int64, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.POINTER(deer_options), C.c_void_p, C.c_size_t,
+                                 C.c_void_p]),
     "deer_rollout": (C.c_int32, [C.POINTER(deer_dynamics), C.c_int64, C.c_int64, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "deer_solve_noalloc": (C.c_int32, [C.POINTER(deer_dynamics), C.c_int64, C.c_int64,

@@ -835,8 +835,8 @@ static deer_status jacobians_at(const deer_dynamics* f, int64_t B, int64_t T, co
 template <class real>
 static deer_status grad_impl(const deer_dynamics* f, int64_t B, int64_t T, const void* s0_,
                              const void* x_, const void* sstar_, const void* g_, void* dp_,
-                             void* ds0_, const deer_options* o, void* ws_, size_t ws_bytes,
-                             cudaStream_t st) {
+                             void* ds0_, void* dx_, const deer_options* o, void* ws_,
+                             size_t ws_bytes, cudaStream_t st) {
   const int64_t N = B * T;
   Layout ly;
   if (!make_layout(f, B, N, o, ly)) return DEER_ERR_INVALID;
@@ -876,6 +876,10 @@ static deer_status grad_impl(const deer_dynamics* f, int64_t B, int64_t T, const
   pa.ds0 = static_cast<real*>(ds0_);
   if (pa.dparams) DEER_CK(cudaMemsetAsync(pa.dparams, 0, B * pa.pstride * rs, st));
   DEER_CK(launch_param_grad<real>(pa, st));
+  if (dx_) {
+    InputGradArgs<real> ia{dv, bt, la.s0, la.s, sa.lam, static_cast<real*>(dx_)};
+    DEER_CK(launch_input_grad<real>(ia, st));
+  }
   Flags hf;
   DEER_CK(cudaMemcpyAsync(&hf, flags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
   DEER_CK(cudaStreamSynchronize(st));
@@ -950,6 +954,15 @@ deer_status deer_grad(const deer_dynamics* f, int64_t batch, int64_t T, const vo
                       const void* x, const void* s_star, const void* dl_ds, void* dl_dparams,
                       void* dl_ds0, const deer_options* opt, void* workspace,
                       size_t workspace_bytes, deer_stream_t stream) {
+  return deer_grad_ex(f, batch, T, s0, x, s_star, dl_ds, dl_dparams, dl_ds0, nullptr, opt,
+                      workspace, workspace_bytes, stream);
+}
+
+deer_status deer_grad_ex(const deer_dynamics* f, int64_t batch, int64_t T, const void* s0,
+                         const void* x, const void* s_star, const void* dl_ds,
+                         void* dl_dparams, void* dl_ds0, void* dl_dx,
+                         const deer_options* opt, void* workspace, size_t workspace_bytes,
+                         deer_stream_t stream) {
   if (!opt || !f) return DEER_ERR_INVALID;
   deer_options o = *opt;
   o.jac = DEER_JAC_FULL;
@@ -964,13 +977,16 @@ deer_status deer_grad(const deer_dynamics* f, int64_t batch, int64_t T, const vo
   const bool per_seq = f->kind == DEER_F_BRUSSELATOR_EULER ||
                        f->kind == DEER_F_MASSACTION_EULER || f->kind == DEER_F_MASSACTION_RK4;
   if (dl_dparams && !per_seq) return DEER_ERR_UNSUPPORTED;
+  const bool has_inputs = f->kind == DEER_F_GRU || f->kind == DEER_F_LINEAR ||
+                          f->kind == DEER_F_RNN_TANH || f->kind == DEER_F_LANGEVIN_2WELL;
+  if (dl_dx && (!has_inputs || !x)) return DEER_ERR_UNSUPPORTED;
   if (dl_dparams && f->params_stride == 0 && batch > 1) return DEER_ERR_UNSUPPORTED;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (o.prec == DEER_FP32)
-    return grad_impl<float>(f, batch, T, s0, x, s_star, dl_ds, dl_dparams, dl_ds0, &o,
+    return grad_impl<float>(f, batch, T, s0, x, s_star, dl_ds, dl_dparams, dl_ds0, dl_dx, &o,
                             workspace, workspace_bytes, st);
-  return grad_impl<double>(f, batch, T, s0, x, s_star, dl_ds, dl_dparams, dl_ds0, &o, workspace,
-                           workspace_bytes, st);
+  return grad_impl<double>(f, batch, T, s0, x, s_star, dl_ds, dl_dparams, dl_ds0, dl_dx, &o,
+                           workspace, workspace_bytes, st);
 }
 
 deer_status deer_selftest_wait_timeout(deer_stream_t stream) {

@@ -444,6 +444,80 @@ __device__ __forceinline__ void perm_eval(const DynView<real>& dv, int64_t row, 
   }
 }
 
+// ----------------------------------------------------------------------------
+// Input vector-Jacobian product out_k = sum_i lam_i d f_i / d x_k at s_{t-1} = h, for the
+// kinds whose inputs x_t enter f_t (Sec. 2.1): additive inputs (affine, mean-field RNN),
+// scaled noise draws (Langevin: sqrt(2 dt)), and the GRU through its three gates:
+//   dz~_i = lam_i (h~_i - h_i) z_i (1 - z_i),   da_i = lam_i z_i (1 - h~_i^2),
+//   dr~_m = h_m r_m (1 - r_m) sum_i Uh_im da_i,
+//   out_k = sum_i (Wz_ik dz~_i + Wr_ik dr~_i + Wh_ik da_i).
+// ----------------------------------------------------------------------------
+template <class real, int D, int KIND>
+__device__ __forceinline__ void input_vjp(const DynView<real>& dv, int64_t row, const real* h,
+                                          const real* lam, real* __restrict__ out) {
+  if constexpr (KIND == DEER_F_GRU) {
+    const int din = dv.d_in;
+    const real* Wz = dv.params;
+    const real* Wr = Wz + D * din;
+    const real* Wh = Wr + D * din;
+    const real* Uz = Wh + D * din;
+    const real* Ur = Uz + D * D;
+    const real* Uh = Ur + D * D;
+    const real* x = dv.x + row * din;
+    real z[D], r[D], ht[D];
+#pragma unroll Unroll<D>::n
+    for (int i = 0; i < D; ++i) {
+      real az = real(0), ar = real(0), ah = real(0);
+      for (int k = 0; k < din; ++k) {
+        const real xk = __ldg(x + k);
+        az += __ldg(Wz + i * din + k) * xk;
+        ar += __ldg(Wr + i * din + k) * xk;
+        ah += __ldg(Wh + i * din + k) * xk;
+      }
+#pragma unroll Unroll<D>::n
+      for (int j = 0; j < D; ++j) {
+        az += __ldg(Uz + i * D + j) * h[j];
+        ar += __ldg(Ur + i * D + j) * h[j];
+      }
+      z[i] = sigm(az);
+      r[i] = sigm(ar);
+      ht[i] = ah;
+    }
+#pragma unroll Unroll<D>::n
+    for (int i = 0; i < D; ++i) {
+      real ah = ht[i];
+#pragma unroll Unroll<D>::n
+      for (int j = 0; j < D; ++j) ah += __ldg(Uh + i * D + j) * (r[j] * h[j]);
+      ht[i] = tanh(ah);
+    }
+    real dz[D], da[D], dr[D];
+#pragma unroll Unroll<D>::n
+    for (int i = 0; i < D; ++i) {
+      dz[i] = lam[i] * (ht[i] - h[i]) * z[i] * (real(1) - z[i]);
+      da[i] = lam[i] * z[i] * (real(1) - ht[i] * ht[i]);
+    }
+#pragma unroll Unroll<D>::n
+    for (int m = 0; m < D; ++m) {
+      real q = real(0);
+#pragma unroll Unroll<D>::n
+      for (int i = 0; i < D; ++i) q += __ldg(Uh + i * D + m) * da[i];
+      dr[m] = q * h[m] * r[m] * (real(1) - r[m]);
+    }
+    for (int k = 0; k < din; ++k) {
+      real v = real(0);
+#pragma unroll Unroll<D>::n
+      for (int i = 0; i < D; ++i)
+        v += __ldg(Wz + i * din + k) * dz[i] + __ldg(Wr + i * din + k) * dr[i] +
+             __ldg(Wh + i * din + k) * da[i];
+      out[k] = v;
+    }
+  } else {
+    const real scale = KIND == DEER_F_LANGEVIN_2WELL ? sqrt(real(2) * dv.dt) : real(1);
+#pragma unroll Unroll<D>::n
+    for (int i = 0; i < D; ++i) out[i] = scale * lam[i];
+  }
+}
+
 // Dispatch on the dynamics kind (compile time). JM: 0 = value only, 1 = full Jacobian
 // into A, 2 = diagonal of the Jacobian into Ad.
 template <class real, int D, int KIND, int JM>

@@ -451,7 +451,20 @@ cudaError_t launch_rollout(const RolloutArgs<real>& a, cudaStream_t st) {
   return launch_rollout_models<real>(a, st);
 }
 
+template <class real>
+cudaError_t launch_input_grad(const InputGradArgs<real>& a, cudaStream_t st) {
+  if (a.bt.N == 0) return cudaSuccess;
+  switch (a.dv.kind) {
+    case DEER_F_GRU:
+    case DEER_F_LINEAR: return launch_input_grad_basic<real>(a, st);
+    case DEER_F_RNN_TANH:
+    case DEER_F_LANGEVIN_2WELL: return launch_input_grad_models<real>(a, st);
+    default: return cudaErrorInvalidValue;  // no differentiable inputs
+  }
+}
+
 #define DEER_INST(real)                                                                         \
+  template cudaError_t launch_input_grad<real>(const InputGradArgs<real>&, cudaStream_t);     \
   template cudaError_t launch_ma_setup<real>(int64_t, int, int, const real*, int64_t,          \
                                              const int32_t*, int64_t, real*, int64_t,          \
                                              int32_t*, cudaStream_t);                          \

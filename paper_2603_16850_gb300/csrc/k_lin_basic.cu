@@ -43,4 +43,16 @@ template cudaError_t launch_linearize_basic<double>(const LinArgs<double>&, cuda
 template cudaError_t launch_rollout_basic<float>(const RolloutArgs<float>&, cudaStream_t);
 template cudaError_t launch_rollout_basic<double>(const RolloutArgs<double>&, cudaStream_t);
 
+template <class real>
+cudaError_t launch_input_grad_basic(const InputGradArgs<real>& a, cudaStream_t st) {
+  switch (a.dv.kind) {
+    case DEER_F_GRU: return generic_input_grad<real, DEER_F_GRU>(a, st);
+    case DEER_F_LINEAR: return generic_input_grad<real, DEER_F_LINEAR>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_input_grad_basic<float>(const InputGradArgs<float>&, cudaStream_t);
+template cudaError_t launch_input_grad_basic<double>(const InputGradArgs<double>&, cudaStream_t);
+
 }  // namespace deer

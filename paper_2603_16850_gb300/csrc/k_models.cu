@@ -202,4 +202,16 @@ template cudaError_t launch_linearize_models<double>(const LinArgs<double>&, cud
 template cudaError_t launch_rollout_models<float>(const RolloutArgs<float>&, cudaStream_t);
 template cudaError_t launch_rollout_models<double>(const RolloutArgs<double>&, cudaStream_t);
 
+template <class real>
+cudaError_t launch_input_grad_models(const InputGradArgs<real>& a, cudaStream_t st) {
+  switch (a.dv.kind) {
+    case DEER_F_RNN_TANH: return generic_input_grad<real, DEER_F_RNN_TANH>(a, st);
+    case DEER_F_LANGEVIN_2WELL: return generic_input_grad<real, DEER_F_LANGEVIN_2WELL>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_input_grad_models<float>(const InputGradArgs<float>&, cudaStream_t);
+template cudaError_t launch_input_grad_models<double>(const InputGradArgs<double>&, cudaStream_t);
+
 }  // namespace deer

@@ -124,6 +124,24 @@ template <class real>
 cudaError_t launch_rollout(const RolloutArgs<real>& a, cudaStream_t st);
 template <class real>
 cudaError_t launch_gru_setup(int d, const real* params, int d_in, real* M, cudaStream_t st);
+// Input gradient of the adjoint: dx[row] = lambda_row^T d f_row / d x_row at s_{row-1}.
+template <class real>
+struct InputGradArgs {
+  DynView<real> dv;
+  Batch bt;           // offsets of the packed batch (rows of every sequence)
+  const real* s0;     // [B][d]
+  const real* s;      // [N][d] trajectory
+  const real* lam;    // [N][d] adjoint states
+  real* dx;           // [N][d_in]
+};
+
+template <class real>
+cudaError_t launch_input_grad(const InputGradArgs<real>& a, cudaStream_t st);
+template <class real>
+cudaError_t launch_input_grad_basic(const InputGradArgs<real>& a, cudaStream_t st);
+template <class real>
+cudaError_t launch_input_grad_models(const InputGradArgs<real>& a, cudaStream_t st);
+
 // Generic-kernel launchers per group of kinds (each group in its own translation unit):
 // Brusselator, GRU and affine ("basic"); mean-field RNN, Langevin, Lorenz-96 and
 // permutation ("models").

@@ -251,4 +251,41 @@ cudaError_t generic_rollout(const RolloutArgs<real>& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Input gradient, one thread per row.
+template <class real, int D, int KIND>
+__global__ void __launch_bounds__(128) k_input_grad(InputGradArgs<real> a) {
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= a.bt.N) return;
+  const int64_t seq = find_seq(a.bt.offsets, a.bt.B, row);
+  real h[D], lam[D];
+  if (row == __ldg(a.bt.offsets + seq)) {
+#pragma unroll Unroll<D>::n
+    for (int i = 0; i < D; ++i) h[i] = __ldg(a.s0 + seq * D + i);
+  } else {
+    load_row<real, D>(a.s + (row - 1) * D, h);
+  }
+  load_row<real, D>(a.lam + row * D, lam);
+  input_vjp<real, D, KIND>(a.dv, row, h, lam, a.dx + row * (int64_t)a.dv.d_in);
+}
+
+template <class real, int KIND>
+cudaError_t generic_input_grad(const InputGradArgs<real>& a, cudaStream_t st) {
+  const unsigned g = grid_for(a.bt.N, 128);
+  switch (a.dv.d) {
+#define CASE(DD)                                                              \
+  case DD:                                                                    \
+    if constexpr (kind_has_d(KIND, DD, true)) {                               \
+      k_input_grad<real, DD, KIND><<<g, 128, 0, st>>>(a);                     \
+      break;                                                                  \
+    }                                                                         \
+    return cudaErrorInvalidValue;
+    DEER_GENERIC_D(CASE)
+#undef CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace deer

@@ -83,3 +83,58 @@ def test_autograd_function_end_to_end():
     loss.backward()
     dth, _, _ = oadj.adjoint_grad(od, p["s0"], s, oadj.sq_loss_cotangent(s, y))
     assert _relerr(k.grad.cpu().numpy(), dth) <= 1e-9
+
+
+def _input_case(kind, B, T, d, seed):
+    import paper_2603_16850_gb300 as deer
+    if kind == "gru":
+        p = synth.gru(B, T, d, d, seed)
+        s0 = np.random.default_rng(seed).standard_normal((B, d)) * 0.5
+        return (odyn.GRU(p["W"], p["U"], p["x"]), deer.Dynamics.gru(_t(p["W"]), _t(p["U"])),
+                p["x"], s0)
+    if kind == "rnn":
+        p = synth.mean_field_rnn(B, T, d, 0.9, seed)
+        return odyn.MeanFieldRNN(p["W"], p["x"]), deer.Dynamics.rnn_tanh(_t(p["W"])), p["x"], p["s0"]
+    if kind == "langevin":
+        p = synth.two_well(B, T, d, seed)
+        return (odyn.TwoWellLangevin(p["params"], p["dt"], p["x"], d=d),
+                deer.Dynamics.langevin_2well(_t(p["params"]), p["dt"]), p["x"], p["s0"])
+    p = synth.linear_lds(B, T, d, seed)
+    return odyn.Linear(p["A"], p["x"]), deer.Dynamics.linear(_t(p["A"])), p["x"], p["s0"]
+
+
+@pytest.mark.parametrize("kind,d", [("gru", 8), ("rnn", 16), ("rnn", 32), ("langevin", 4),
+                                    ("linear", 4)])
+def test_input_gradient_matches_oracle(kind, d):
+    """dl/dx_t = lambda_t^T df_t/dx_t (deer_grad_ex) against the oracle's adjoint states and
+    input derivatives, FP64, on a 300-step trajectory (several scan chunks, ragged tail)."""
+    import paper_2603_16850_gb300 as deer
+    B, T = 2, 300
+    od, dyn, x, s0 = _input_case(kind, B, T, d, seed=6)
+    s = onewton.rollout(od, s0, T)
+    y = s + 0.2 * synth.targets_noise(s.shape, seed=7)
+    g = oadj.sq_loss_cotangent(s, y)
+    _, ds0_ref, lam = oadj.adjoint_grad(od, s0, s, g)
+    dx_ref = oadj.input_grad(od, s0, s, lam)
+    _, ds0, dx = deer.deer_grad(dyn, _t(s0), T, _t(s.reshape(-1, d)), _t(g.reshape(-1, d)),
+                                x=_t(x.reshape(-1, x.shape[-1])), want_dx=True)
+    assert _relerr(dx.cpu().numpy().reshape(dx_ref.shape), dx_ref) <= 1e-10
+    assert _relerr(ds0.cpu().numpy(), ds0_ref) <= 1e-10
+
+
+def test_autograd_reaches_the_gru_inputs():
+    """DeerFunction: the gradient of a loss of the solved GRU trajectory with respect to its
+    input sequence equals deer_grad_ex's dl/dx at the same fixed point."""
+    import paper_2603_16850_gb300 as deer
+    B, T, d = 2, 200, 8
+    p = synth.gru(B, T, d, d, seed=9)
+    dyn = deer.Dynamics.gru(_t(p["W"]), _t(p["U"]))
+    x = _t(p["x"].reshape(-1, d)).requires_grad_(True)
+    s0 = torch.zeros((B, d), dtype=torch.float64, device="cuda")
+    s = deer.DeerFunction.apply(dyn.params, s0, dyn, T, x,
+                                dict(jac="full", tol=1e-12, init="zeros"))
+    loss = (s ** 2).sum()
+    loss.backward()
+    _, _, dx = deer.deer_grad(dyn, s0, T, s.detach(), (2 * s).detach(), x=x.detach(),
+                              want_dx=True)
+    assert torch.allclose(x.grad, dx, rtol=0, atol=0)
