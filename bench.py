@@ -338,7 +338,14 @@ def adjoint_measurement(deer, N, lib, dev, stream):
     torch.cuda.synchronize()
     fwd = e0.elapsed_time(e1)
     grad = e1.elapsed_time(e2)
+    e0.record(stream)
+    deer.deer_rollout(dyn, s0, T, prec="fp32", stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    roll_ms = e0.elapsed_time(e1)
     return {"workload": "mass action d=32 R=48 B=256 T=32768 RK4, FP32, adjoint wrt rates",
+            "sequential_gpu_rollout": {"ms": roll_ms, "value": B * T / (roll_ms / 1000.0),
+                                       "unit": UNIT},
             "forward_ms": fwd, "grad_ms": grad,
             "forward_value": B * T / (fwd / 1000.0), "grad_value": B * T / (grad / 1000.0),
             "unit": UNIT, "newton_iters_max": int(info.iters.max()),
@@ -491,6 +498,33 @@ def ragged_mixed_measurement(deer, N, lib, dev, stream, B=1000):
     ms = e0.elapsed_time(e1)
     lin_rows = prof.rows[1]
     lin_s = prof.ms[1] / 1000.0
+    del ws_
+    # comparisons on the same group: plain FP32 parallel Newton (float32 Jacobians, scan and
+    # residual; tol 5e-7 twice) and the sequential GPU rollout in float64 and float32
+    dyn32 = deer.Dynamics.massaction(topo, k.float(), d, p["dt"])
+    s032 = s0.float()
+    o32 = dict(jac="full", tol=5e-7, confirm=2, prec="fp32", init="zeros", reset=True,
+               window=True, chunk=opts["chunk"])
+    ws32 = torch.empty(deer.deer_workspace_bytes(dyn32, B, ntot, **o32), dtype=torch.uint8,
+                       device=dev)
+    deer.deer_solve_batched(dyn32, s032, off, workspace=ws32, stream=stream, **o32)  # warm
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, info32 = deer.deer_solve_batched(dyn32, s032, off, workspace=ws32, stream=stream, **o32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms32 = e0.elapsed_time(e1)
+    del ws32
+    off_d = torch.tensor(off, dtype=torch.int64, device=dev)
+    roll = {}
+    for name, dd, ss in (("fp64", dyn, s0), ("fp32", dyn32, s032)):
+        deer.deer_rollout(dd, ss, 0, offsets=off_d, prec=name, stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        deer.deer_rollout(dd, ss, 0, offsets=off_d, prec=name, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        roll[name] = e0.elapsed_time(e1)
     return {"workload": f"ragged mass action d=16 R=24, T ~ U[1000,100000], B={B} (one of "
                         "ten groups), bf16 Jacobians / fp32 scan / fp64 residual",
             "chunk": {"chosen": timings["chunk"], "tuning_ms": timings["timings"],
@@ -502,7 +536,14 @@ def ragged_mixed_measurement(deer, N, lib, dev, stream, B=1000):
             "newton_iters_max": int(info.iters.max()),
             "newton_iters_p50": float(np.percentile(info.iters.numpy(), 50)),
             "converged": bool(info.converged.all()),
-            "phase_ms": {n: prof.ms[i] for i, n in enumerate(N.PHASES)}}
+            "phase_ms": {n: prof.ms[i] for i, n in enumerate(N.PHASES)},
+            "fp32_newton": {"ms": ms32, "value": ntot / (ms32 / 1000.0), "unit": UNIT,
+                            "newton_iters_max": int(info32.iters.max()),
+                            "converged": bool(info32.converged.all()),
+                            "note": "float32 everything: its fixed point is the float32 "
+                                    "rollout, not the float64 one the mixed path reaches"},
+            "sequential_gpu_rollout": {name: {"ms": v, "value": ntot / (v / 1000.0),
+                                              "unit": UNIT} for name, v in roll.items()}}
 
 
 def run_only(args):
