@@ -243,6 +243,53 @@ def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64):
             "linearize": lin_entry}
 
 
+def brusselator_measurement(deer, dev, stream, reps=20):
+    """C1: one Brusselator trajectory (d=2, a=1, b=3, s0=(1,1), explicit Euler dt=0.01,
+    T=1024), full-Jacobian Newton in FP64 to tol 1e-12 (reset heuristic on: undamped Newton
+    from the constant guess overflows on this limit cycle). A single short sequence is
+    launch- and latency-bound: reported as time per solve and per Newton iteration, next to
+    the sequential GPU rollout."""
+    import torch
+    import synth
+    p = synth.brusselator(T=1024)
+    dyn = deer.Dynamics.brusselator(torch.tensor(p["params"], device=dev), p["dt"])
+    s0 = torch.tensor(p["s0"], device=dev)
+    opts = dict(jac="full", tol=1e-12, prec="fp64", init="s0", reset=True)
+    # chunk length from the autotuner (untimed): with one short sequence the chunk pass's
+    # per-thread chain (L rows) and the carry's chain (T / L chunks) trade off
+    from paper_2603_16850_gb300 import autotune
+    tuned = autotune.pick_best(
+        (8, 16, 32, 64, 128),
+        lambda L: _time_solve1(deer, dyn, s0, 1024, None, dict(opts, chunk=L), stream))
+    opts["chunk"] = tuned["chunk"]
+    ws_ = torch.empty(deer.deer_workspace_bytes(dyn, 1, 1024, **opts), dtype=torch.uint8,
+                      device=dev)
+    for _ in range(3):
+        _, info = deer.deer_solve(dyn, s0, 1024, workspace=ws_, stream=stream, **opts)
+    torch.cuda.synchronize()
+    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    e0.record(stream)
+    for _ in range(reps):
+        _, info = deer.deer_solve(dyn, s0, 1024, workspace=ws_, stream=stream, **opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    e0.record(stream)
+    for _ in range(reps):
+        deer.deer_rollout(dyn, s0, 1024, prec="fp64", stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    roll_ms = e0.elapsed_time(e1) / reps
+    it = int(info.iters[0])
+    return {"workload": "Brusselator d=2 T=1024 Euler dt=0.01, full Newton FP64, tol 1e-12",
+            "us_per_solve": 1000 * ms, "newton_iters": it,
+            "us_per_iteration": 1000 * ms / max(it, 1), "converged": bool(info.converged[0]),
+            "value": 1024 / (ms / 1000.0), "unit": UNIT,
+            "sequential_gpu_rollout_us": 1000 * roll_ms,
+            "chunk": {"chosen": tuned["chunk"], "tuning_ms": tuned["timings"],
+                      "how": "autotune.pick_best on the problem itself"}}
+
+
 def gru_elk_measurement(deer, dev, stream, B=64, lams=(0.01, 0.1, 1.0, 10.0)):
     """The damped variant of the GRU workload (quasi-ELK, Sec. 4.3 with the diagonal
     Jacobian): the same d=64, T=65536, B=64 problem, FP32, tol 1e-5 x2, for a sweep of the
@@ -561,6 +608,8 @@ def run_only(args):
                                    B=args.batch or 64)
     elif args.only == "ragged_mixed":
         out = ragged_mixed_measurement(deer, N, lib, dev, stream, B=args.batch or 1000)
+    elif args.only == "brusselator":
+        out = brusselator_measurement(deer, dev, stream)
     elif args.only == "gru_elk":
         out = gru_elk_measurement(deer, dev, stream, B=args.batch or 64)
     elif args.only == "threshold":
@@ -699,6 +748,7 @@ def run(args):
     extra = {}
     if rank == 0 and ws == 1 and not args.no_extra:
         extra["lle"] = lle_measurement(deer, dyn, s0, s, T, d, stream)
+        extra["brusselator"] = brusselator_measurement(deer, dev, stream)
         extra["gru_quasi_deer"] = gru_diag_measurement(deer, N, lib, dev, stream)
         extra["gru_quasi_elk"] = gru_elk_measurement(deer, dev, stream)
         extra["adjoint"] = adjoint_measurement(deer, N, lib, dev, stream)
@@ -754,8 +804,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary GRU quasi-DEER measurement")
-    ap.add_argument("--only", default="", choices=["", "gru", "gru_elk", "adjoint",
-                                                   "ragged_mixed", "threshold"],
+    ap.add_argument("--only", default="", choices=["", "brusselator", "gru", "gru_elk",
+                                                   "adjoint", "ragged_mixed", "threshold"],
                     help="run one secondary workload alone (with --batch) and print it")
     ap.add_argument("--gains", default="",
                     help="--only threshold: comma-separated RNN gains g (default 0.5,1.0,2.0)")

@@ -59,6 +59,11 @@ __global__ void __launch_bounds__(kFusedBlock) k_dense_fused(FusedArgs<real> a) 
   int64_t seq = 0;
   real mx = real(0), sq = real(0);  // residual statistics in the path's own precision
   unsigned long long key = 0ull;     // first failing row (sliding window)
+  // the largest scaled residual |r| / max(1, |s|) is kept as the pair (|r|, max(1, |s|))
+  // and divided out once per chunk: no division on the per-row dependent chain (float64
+  // division is long on this GPU); the test |r| <= tol max(1, |s|) needs none either
+  real mnum = real(0), mden = real(1);
+  bool nan_seen = false;
   if (valid) {
     int64_t c, r0;
     int n;
@@ -91,12 +96,50 @@ __global__ void __launch_bounds__(kFusedBlock) k_dense_fused(FusedArgs<real> a) 
 #pragma unroll
       for (int j = 0; j < D; ++j) sP[i * D + j][tid] = i == j ? real(1) : real(0);
     }
+    // small states: the next row's pending (A, b) and state are loaded one row ahead, so
+    // their memory latency overlaps the current row's dependent arithmetic
+    constexpr bool PF = D <= 4;
+    constexpr int PE = MODE == 1 ? E : 1, PD = MODE == 1 ? D : 1;
+    real fA[PF ? PE : 1], fb[PF ? PD : 1], fs[PF ? D : 1];
+    auto fetch = [&](int t) {
+      if constexpr (PF) {
+        const real* Ar = a.Ai + ((gi * L + t) * E) * 32 + lane;
+        const real* br = a.bi + ((gi * L + t) * D) * 32 + lane;
+        if constexpr (MODE == 1) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) fA[e] = Ar[e * 32];
+#pragma unroll
+          for (int i = 0; i < D; ++i) fb[i] = br[i * 32];
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) fs[i] = a.s[(r0 + t) * D + i];
+      }
+    };
+    if (PF && n > 0) fetch(0);
     for (int t = 0; t < n; ++t) {
       const int64_t row = r0 + t;
       real* Arow = a.Ai + ((gi * L + t) * E) * 32 + lane;
       real* brow = a.bi + ((gi * L + t) * D) * 32 + lane;
-      real sn[D];
-      ld_vec<real, D>(a.s + row * D, sn);
+      real sn[D], pA[PE], pb[PD];
+      if constexpr (PF) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) sn[i] = fs[i];
+        if constexpr (MODE == 1) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) pA[e] = fA[e];
+#pragma unroll
+          for (int i = 0; i < D; ++i) pb[i] = fb[i];
+        }
+        if (t + 1 < n) fetch(t + 1);
+      } else {
+        ld_vec<real, D>(a.s + row * D, sn);
+        if constexpr (MODE == 1) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) pA[e] = Arow[e * 32];
+#pragma unroll
+          for (int i = 0; i < D; ++i) pb[i] = brow[i * 32];
+        }
+      }
       if constexpr (MODE == 1) {
         // apply the pending scan step: Delta_t = A_t Delta_{t-1} + b_t, s_t += Delta_t
         real dl[D], nd[D];
@@ -104,9 +147,9 @@ __global__ void __launch_bounds__(kFusedBlock) k_dense_fused(FusedArgs<real> a) 
         for (int i = 0; i < D; ++i) dl[i] = sD[i][tid];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-          real v = brow[i * 32];
+          real v = pb[i];
 #pragma unroll
-          for (int j = 0; j < D; ++j) v += Arow[(i * D + j) * 32] * dl[j];
+          for (int j = 0; j < D; ++j) v += pA[i * D + j] * dl[j];
           nd[i] = v;
         }
 #pragma unroll
@@ -130,10 +173,12 @@ __global__ void __launch_bounds__(kFusedBlock) k_dense_fused(FusedArgs<real> a) 
         prev[i] = x;
         r[i] = x - F[i];
         const real sabs = rabs(x);
-        const real sr = rabs(r[i]) / (sabs > real(1) ? sabs : real(1));
-        mx = (sr > mx || sr != sr) ? sr : mx;
+        const real m = sabs > real(1) ? sabs : real(1);
+        const real ra = rabs(r[i]);
+        if (ra * mden > mnum * m) { mnum = ra; mden = m; }
+        nan_seen |= ra != ra;
         sq += r[i] * r[i];
-        if (!(sr <= a.tol) && key == 0ull) key = bad_key(true, row - base);
+        if (!(ra <= a.tol * m) && key == 0ull) key = bad_key(true, row - base);
       }
 #pragma unroll
       for (int i = 0; i < D; ++i) {
@@ -186,6 +231,7 @@ __global__ void __launch_bounds__(kFusedBlock) k_dense_fused(FusedArgs<real> a) 
       for (int j = 0; j < D; ++j) Po[i * D + j] = sP[i * D + j][tid];
     }
   }
+  mx = nan_seen ? real(NAN) : mnum / mden;
   acc_resid_t(a.acc, seq, valid, mx, sq, key);
 }
 
