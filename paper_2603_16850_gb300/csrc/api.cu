@@ -113,7 +113,7 @@ static int64_t min_param_stride(const deer_dynamics* f) {
 struct Layout {
   size_t offsets, chunk_first, win_chunk, act_seq, act_row_off, act_chunk_off, acc, info, flags,
       ma, gru_M,
-      A, b, aggP, aggv, cin, gam, mob, pin, sprev, lb_ticket, lb_flags, lb_agg, lb_pre, xproj,
+      A, b, aggP, aggv, cin, mob, pin, sprev, lb_ticket, lb_flags, lb_agg, lb_pre, xproj,
       adj_off, adj_e, total;
   int64_t n_chunks_max;
   int64_t ma_stride, n_ma;
@@ -157,7 +157,7 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
   ly.acc = take((size_t)(B > 0 ? B : 1) * sizeof(SeqAcc));
   ly.info = take((size_t)(B > 0 ? B : 1) * sizeof(SeqInfo));
   ly.flags = take(sizeof(Flags));
-  ly.ma = ly.gru_M = ly.A = ly.aggP = ly.gam = ly.mob = ly.pin = p;
+  ly.ma = ly.gru_M = ly.A = ly.aggP = ly.mob = ly.pin = p;
   ly.ma_stride = 0;
   ly.n_ma = 0;
   if (f->kind == DEER_F_MASSACTION_EULER || f->kind == DEER_F_MASSACTION_RK4) {
@@ -191,7 +191,6 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
   // diag family also needs a second aggregate array; reuse aggP slot for it
   if (o->jac != DEER_JAC_FULL) ly.aggP = take((size_t)C * d * rs);
   if (o->damp == DEER_DAMP_ELK) {
-    ly.gam = take((size_t)N * d * rs);
     ly.mob = take((size_t)C * d * 4 * rs);
     ly.pin = take((size_t)C * d * rs);
   }
@@ -446,7 +445,6 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     gsa.info = info;
     gsa.elk = (o->damp == DEER_DAMP_ELK && o->damp_param > 0.0) ? 1 : 0;
     gsa.sigma2 = gsa.elk ? real(1.0 / o->damp_param) : real(0);
-    gsa.gam = reinterpret_cast<real*>(ws + ly.gam);
     gsa.mob = reinterpret_cast<real*>(ws + ly.mob);
     gsa.pin = reinterpret_cast<real*>(ws + ly.pin);
     gsa.reset = o->reset;
@@ -1217,7 +1215,6 @@ static deer_status solve_noalloc_impl(const deer_dynamics* f, int64_t B, int64_t
                          reinterpret_cast<real*>(ws + ly.aggv),
                          reinterpret_cast<real*>(ws + ly.cin), info, elk,
                          elk ? real(1.0 / o->damp_param) : real(0),
-                         reinterpret_cast<real*>(ws + ly.gam),
                          reinterpret_cast<real*>(ws + ly.mob),
                          reinterpret_cast<real*>(ws + ly.pin), o->reset, reset_thr};
   const bool lookback = use_diag_lookback(o, d);

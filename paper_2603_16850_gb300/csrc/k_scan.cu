@@ -301,13 +301,6 @@ __device__ __forceinline__ void diag_elem(const DiagScanArgs<real>& a, int64_t r
                                           real& at, real& bt) {
   at = a.amode == 0 ? __ldg(a.a + row * a.d + j) : a.aconst;
   bt = __ldg(a.b + row * a.d + j);
-  if (a.elk) {
-    // filtered mean mu_t = Gamma_t a_t mu_{t-1} + Gamma_t b_t + (1 - Gamma_t) y_t
-    const real g = a.gam[row * a.d + j];
-    const real y = a.s[row * a.d + j];
-    bt = g * bt + (real(1) - g) * y;
-    at = g * at;
-  }
 }
 
 template <class real>
@@ -418,8 +411,25 @@ __global__ void __launch_bounds__(128) k_elk_carry(DiagScanArgs<real> a) {
   }
 }
 
+// The filtered mean's transition of a row, with the attenuation recomputed from the
+// variance carried along the chunk: P^-_t = a_t^2 P_{t-1} + 1, Gamma_t = sigma2 / (P^-_t +
+// sigma2), P_t = Gamma_t P^-_t; mu_t = Gamma_t a_t mu_{t-1} + Gamma_t b_t + (1 - Gamma_t) y_t.
 template <class real>
-__global__ void __launch_bounds__(128) k_elk_gamma(DiagScanArgs<real> a) {
+__device__ __forceinline__ void elk_row(const DiagScanArgs<real>& a, int64_t row, int j,
+                                        real& P, real& at, real& bt) {
+  const real a0 = a.amode == 0 ? __ldg(a.a + row * a.d + j) : a.aconst;
+  const real Pm = a0 * a0 * P + real(1);
+  const real g = a.sigma2 / (Pm + a.sigma2);
+  P = g * Pm;
+  at = g * a0;
+  bt = g * __ldg(a.b + row * a.d + j) + (real(1) - g) * a.s[row * a.d + j];
+}
+
+// Mean aggregates of the chunks (quasi-ELK): the variance entering the chunk (pin) is known
+// from the Moebius carry, so the attenuations are formed on the fly instead of being
+// stored and read back.
+template <class real>
+__global__ void __launch_bounds__(128) k_elk_mean_chunk(DiagScanArgs<real> a) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (id >= a.bt.act_chunks * a.d) return;
   const int64_t ac = id / a.d;
@@ -428,13 +438,33 @@ __global__ void __launch_bounds__(128) k_elk_gamma(DiagScanArgs<real> a) {
   int n;
   act_chunk(a.bt, ac, seq, c, r0, n);
   real P = a.pin[c * a.d + j];
+  real A = real(1), Bv = real(0);
   for (int t = 0; t < n; ++t) {
-    const int64_t row = r0 + t;
-    const real at = a.amode == 0 ? __ldg(a.a + row * a.d + j) : a.aconst;
-    const real Pm = at * at * P + real(1);   // predicted variance
-    const real g = a.sigma2 / (Pm + a.sigma2);  // attenuation Gamma_t = 1 - gain
-    a.gam[row * a.d + j] = g;
-    P = g * Pm;                              // filtered variance
+    real at, bt;
+    elk_row(a, r0 + t, j, P, at, bt);
+    Bv = at * Bv + bt;
+    A = at * A;
+  }
+  a.aggA[c * a.d + j] = A;
+  a.aggB[c * a.d + j] = Bv;
+}
+
+template <class real>
+__global__ void __launch_bounds__(128) k_elk_apply(DiagScanArgs<real> a) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= a.bt.act_chunks * a.d) return;
+  const int64_t ac = id / a.d;
+  const int j = (int)(id - ac * a.d);
+  int64_t seq, c, r0;
+  int n;
+  act_chunk(a.bt, ac, seq, c, r0, n);
+  real P = a.pin[c * a.d + j];
+  real x = a.cin[c * a.d + j];
+  for (int t = 0; t < n; ++t) {
+    real at, bt;
+    elk_row(a, r0 + t, j, P, at, bt);  // reads y_t = s_t before it is overwritten
+    x = at * x + bt;
+    a.s[(r0 + t) * a.d + j] = reset_val(x, a.reset_thr, a.reset);
   }
 }
 
@@ -444,10 +474,15 @@ cudaError_t launch_diag_scan(const DiagScanArgs<real>& a, cudaStream_t st) {
   const unsigned gc = grid_for(a.bt.act_chunks * a.d, 128);
   const unsigned gs = grid_for(a.bt.n_act * a.d, 128);
   if (a.elk) {
+    // variance: Moebius chunk aggregates and their carry; mean: aggregates, carry and
+    // apply with the attenuations recomputed from the carried variance
     k_elk_chunk<real><<<gc, 128, 0, st>>>(a);
     k_elk_carry<real><<<gs, 128, 0, st>>>(a);
-    k_elk_gamma<real><<<gc, 128, 0, st>>>(a);
-    note_launch(3);
+    k_elk_mean_chunk<real><<<gc, 128, 0, st>>>(a);
+    k_diag_carry<real><<<gs, 128, 0, st>>>(a);
+    k_elk_apply<real><<<gc, 128, 0, st>>>(a);
+    note_launch(5);
+    return cudaGetLastError();
   }
   k_diag_chunk<real><<<gc, 128, 0, st>>>(a);
   k_diag_carry<real><<<gs, 128, 0, st>>>(a);

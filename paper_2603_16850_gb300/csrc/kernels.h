@@ -105,7 +105,6 @@ struct DiagScanArgs {
   const SeqInfo* info;
   int elk;          // 1: Kalman-filter damping with sigma2 = 1/lambda
   real sigma2;
-  real* gam;        // [N][d] attenuation Gamma_t (ELK)
   real* mob;        // [n_chunks][d][4] Moebius aggregates (ELK)
   real* pin;        // [n_chunks][d] filtered variance entering each chunk (ELK)
   int reset;
