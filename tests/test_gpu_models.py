@@ -262,3 +262,20 @@ def test_sequential_rollout_matches_oracle(kind, d):
     sn = s.cpu().numpy()
     for b, n in enumerate(lengths):
         assert _relerr(sn[off[b]:off[b + 1]], roll[b, :n]) <= 1e-12
+
+
+def test_full_size_single_trajectory_rnn_fp32():
+    """The single-trajectory workload timed by the benchmark (mean-field RNN d = 32,
+    T = 100000, g = 0.5, FP32, sliding window, chunk length 256) against the float64
+    oracle rollout over the whole trajectory."""
+    deer = _deer()
+    T, d = 100000, 32
+    p = synth.mean_field_rnn(1, T, d, 0.5, seed=0)
+    dyn = deer.Dynamics.rnn_tanh(_t(p["W"], torch.float32))
+    x = _t(p["x"].reshape(-1, d), torch.float32)
+    s, info = deer.deer_solve(dyn, _t(p["s0"], torch.float32), T, x, jac="full", tol=1e-5,
+                              prec="fp32", init="zeros", reset=True, window=True,
+                              max_iters=300, chunk=256)
+    assert bool(info.converged[0]) and int(info.iters[0]) <= 5
+    roll = onewton.rollout(odyn.MeanFieldRNN(p["W"], p["x"]), p["s0"], T)[0]
+    assert _relerr(s.cpu().numpy(), roll) <= 1e-5
