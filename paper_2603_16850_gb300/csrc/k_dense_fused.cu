@@ -483,6 +483,10 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
 template <class real, int D>
 __global__ void __launch_bounds__(128) k_dense_fused_carry(FusedArgs<real> a) {
   constexpr int E = D * D;
+  // aggregates and state rows loaded K chunks ahead (register ring of about 64 32-bit
+  // registers: deep for d <= 2, one chunk ahead for d = 8, whose aggregate is 64 values)
+  constexpr int V = (E + 2 * D) * (int)(sizeof(real) / 4);
+  constexpr int K = V >= 64 ? 1 : (64 / V > 8 ? 8 : 64 / V);
   const int64_t kq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (kq >= a.bt.n_act) return;
   const int64_t seq = a.bt.act_seq[kq];
@@ -492,46 +496,56 @@ __global__ void __launch_bounds__(128) k_dense_fused_carry(FusedArgs<real> a) {
   real x[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) x[i] = real(0);
-  real P[E], v[D];
-  if (c0 < c1) {
-    ld_vec<real, E>(a.aggP + c0 * E, *reinterpret_cast<real(*)[E]>(P));
-    ld_vec<real, D>(a.aggv + c0 * D, v);
-  }
-  for (int64_t c = c0; c < c1; ++c) {
-    real Pc[E], vc[D];
+  real Pr[K][E], vr[K][D], sr[K][D];
+  auto fetch = [&](int slot, int64_t c) {
+    if (c < c1) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) Pc[e] = P[e];
+      for (int e = 0; e < E; ++e) Pr[slot][e] = a.aggP[c * E + e];
 #pragma unroll
-    for (int i = 0; i < D; ++i) vc[i] = v[i];
-    if (c + 1 < c1) {  // prefetch the next aggregate
-      ld_vec<real, E>(a.aggP + (c + 1) * E, *reinterpret_cast<real(*)[E]>(P));
-      ld_vec<real, D>(a.aggv + (c + 1) * D, v);
-    }
+      for (int i = 0; i < D; ++i) vr[slot][i] = a.aggv[c * D + i];
+      if (c > c0) {
+        const int64_t r0 = base + ((c - cf) << a.bt.log2L);
 #pragma unroll
-    for (int i = 0; i < D; ++i) a.cin[c * D + i] = x[i];
-    if (c > c0) {
-      const int64_t r0 = base + ((c - cf) << a.bt.log2L);
-      real so[D];
-      ld_vec<real, D>(a.s + (r0 - 1) * D, so);
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        real y = so[i] + x[i];
-        if (a.reset && !(y <= a.reset_thr && y >= -a.reset_thr)) y = real(0);
-        a.sprev[c * D + i] = y;
+        for (int i = 0; i < D; ++i) sr[slot][i] = a.s[(r0 - 1) * D + i];
       }
     }
-    real nx[D];
+  };
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-      real y = vc[i];
+  for (int slot = 0; slot < K; ++slot) fetch(slot, c0 + slot);
+  for (int64_t cb = c0; cb < c1; cb += K) {
+#pragma unroll
+    for (int slot = 0; slot < K; ++slot) {
+      const int64_t c = cb + slot;
+      if (c >= c1) break;
+      real Pc[E], vc[D], so[D];
+#pragma unroll
+      for (int e = 0; e < E; ++e) Pc[e] = Pr[slot][e];
+#pragma unroll
+      for (int i = 0; i < D; ++i) { vc[i] = vr[slot][i]; so[i] = sr[slot][i]; }
+      fetch(slot, c + K);
+#pragma unroll
+      for (int i = 0; i < D; ++i) a.cin[c * D + i] = x[i];
       if (c > c0) {
 #pragma unroll
-        for (int j = 0; j < D; ++j) y += Pc[i * D + j] * x[j];
+        for (int i = 0; i < D; ++i) {
+          real y = so[i] + x[i];
+          if (a.reset && !(y <= a.reset_thr && y >= -a.reset_thr)) y = real(0);
+          a.sprev[c * D + i] = y;
+        }
       }
-      nx[i] = y;
-    }
+      real nx[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) x[i] = nx[i];
+      for (int i = 0; i < D; ++i) {
+        real y = vc[i];
+        if (c > c0) {
+#pragma unroll
+          for (int j = 0; j < D; ++j) y += Pc[i * D + j] * x[j];
+        }
+        nx[i] = y;
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i) x[i] = nx[i];
+    }
   }
 }
 
@@ -542,6 +556,10 @@ template <class real, int D>
 __global__ void __launch_bounds__(128) k_fused_carry_lps(FusedArgs<real> a) {
   constexpr int E = D * D;
   constexpr int GPB = 128 / D;
+  // the chunk aggregates and the state rows before the chunks do not depend on the carry:
+  // they are loaded K chunks ahead (a register ring), so the dependent chain costs one
+  // matrix-vector product per chunk instead of one memory round trip
+  constexpr int K = sizeof(real) == 4 ? 8 : 4;
   const int grp = threadIdx.x / D, i = threadIdx.x % D;
   const unsigned gm = ((1u << D) - 1u) << ((threadIdx.x & 31) & ~(D - 1));
   const int64_t kq = blockIdx.x * (int64_t)GPB + grp;
@@ -550,35 +568,39 @@ __global__ void __launch_bounds__(128) k_fused_carry_lps(FusedArgs<real> a) {
   const int64_t cf = a.bt.chunk_first[seq], c0 = win_first(a.bt, seq);
   const int64_t c1 = a.bt.chunk_first[seq + 1];
   const int64_t base = a.bt.offsets[seq];
+  real Pr[K][D], vr[K], sr[K];
+  auto fetch = [&](int slot, int64_t c) {
+    if (c < c1) {
+      ldrow_p<real, D>(a.aggP + c * E + i * D, Pr[slot]);
+      vr[slot] = a.aggv[c * D + i];
+      sr[slot] = c > c0 ? a.s[(base + ((c - cf) << a.bt.log2L) - 1) * D + i] : real(0);
+    }
+  };
+#pragma unroll
+  for (int slot = 0; slot < K; ++slot) fetch(slot, c0 + slot);
   real x = real(0);
-  real P[D], v = real(0);
-  if (c0 < c1) {
-    ldrow_p<real, D>(a.aggP + c0 * E + i * D, P);
-    v = a.aggv[c0 * D + i];
-  }
-  for (int64_t c = c0; c < c1; ++c) {
-    real Pc[D];
+  for (int64_t cb = c0; cb < c1; cb += K) {
 #pragma unroll
-    for (int j = 0; j < D; ++j) Pc[j] = P[j];
-    const real vc = v;
-    real so = real(0);
-    if (c > c0) so = a.s[(base + ((c - cf) << a.bt.log2L) - 1) * D + i];
-    if (c + 1 < c1) {  // prefetch the next aggregate row
-      ldrow_p<real, D>(a.aggP + (c + 1) * E + i * D, P);
-      v = a.aggv[(c + 1) * D + i];
-    }
-    a.cin[c * D + i] = x;
-    if (c > c0) {
-      real y = so + x;
-      if (a.reset && !(y <= a.reset_thr && y >= -a.reset_thr)) y = real(0);
-      a.sprev[c * D + i] = y;
-    }
-    real nx = vc;
-    if (c > c0) {
+    for (int slot = 0; slot < K; ++slot) {
+      const int64_t c = cb + slot;
+      if (c < c1) {  // uniform over the group
+        real Pc[D];
 #pragma unroll
-      for (int j = 0; j < D; ++j) nx += Pc[j] * __shfl_sync(gm, x, j, D);
+        for (int j = 0; j < D; ++j) Pc[j] = Pr[slot][j];
+        const real vc = vr[slot], so = sr[slot];
+        fetch(slot, c + K);
+        a.cin[c * D + i] = x;
+        real nx = vc;
+        if (c > c0) {
+          real y = so + x;
+          if (a.reset && !(y <= a.reset_thr && y >= -a.reset_thr)) y = real(0);
+          a.sprev[c * D + i] = y;
+#pragma unroll
+          for (int j = 0; j < D; ++j) nx += Pc[j] * __shfl_sync(gm, x, j, D);
+        }
+        x = nx;
+      }
     }
-    x = nx;
   }
 }
 
