@@ -180,7 +180,7 @@ def run_reference(args):
     return 0
 
 
-def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64):
+def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64, window=False):
     """GRU cell d=64, inputs 64, T=65536, B=64, weights N(0,1/d), inputs N(0,1), quasi-DEER
     (diagonal Jacobian), FP32: converged state-steps/s and the single-pass look-back
     diagonal scan in achieved HBM GB/s (algorithmic 12 bytes per coordinate-step: a, b read,
@@ -194,7 +194,7 @@ def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64):
                             torch.tensor(g["U"], dtype=torch.float32, device=dev))
     x = torch.tensor(g["x"].reshape(-1, d), device=dev)
     s0 = torch.zeros((B, d), dtype=torch.float32, device=dev)
-    opts = dict(jac="diag", tol=1e-5, confirm=2, prec="fp32", init="zeros")
+    opts = dict(jac="diag", tol=1e-5, confirm=2, prec="fp32", init="zeros", window=window)
     nbytes = deer.deer_workspace_bytes(dyn, B, B * T, **opts)
     ws_ = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     for _ in range(2):
@@ -610,6 +610,9 @@ def run_only(args):
         out = ragged_mixed_measurement(deer, N, lib, dev, stream, B=args.batch or 1000)
     elif args.only == "brusselator":
         out = brusselator_measurement(deer, dev, stream)
+    elif args.only == "gru_window":
+        out = gru_diag_measurement(deer, N, lib, dev, stream, steps=max(args.steps, 1),
+                                   B=args.batch or 64, window=True)
     elif args.only == "gru_elk":
         out = gru_elk_measurement(deer, dev, stream, B=args.batch or 64)
     elif args.only == "threshold":
@@ -804,8 +807,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary GRU quasi-DEER measurement")
-    ap.add_argument("--only", default="", choices=["", "brusselator", "gru", "gru_elk",
-                                                   "adjoint", "ragged_mixed", "threshold"],
+    ap.add_argument("--only", default="", choices=["", "brusselator", "gru", "gru_window",
+                                                   "gru_elk", "adjoint", "ragged_mixed",
+                                                   "threshold"],
                     help="run one secondary workload alone (with --batch) and print it")
     ap.add_argument("--gains", default="",
                     help="--only threshold: comma-separated RNN gains g (default 0.5,1.0,2.0)")

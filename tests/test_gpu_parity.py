@@ -405,17 +405,18 @@ def test_full_size_batched_massaction_fp32_sampled(window):
         assert _relerr(sv[b].cpu().numpy(), roll[i]) <= 1e-5
 
 
-def test_full_size_gru_quasi_deer_fp32_sampled():
+@pytest.mark.parametrize("window", [False, True])
+def test_full_size_gru_quasi_deer_fp32_sampled(window):
     """GRU d=64, inputs 64, T=65536, B=64, weights N(0,1/d), inputs N(0,1), quasi-DEER,
-    FP32, tol 1e-5 (scaled residual): sampled trajectories equal the FP64 oracle rollout
-    within 1e-5."""
+    FP32, tol 1e-5 (scaled residual), with and without the sliding window: sampled
+    trajectories equal the FP64 oracle rollout within 1e-5."""
     deer = _deer()
     B, T, d = 64, 65536, 64
     g = synth.gru(B, T, d, d, seed=0, dtype=np.float32)
     dyn = deer.Dynamics.gru(_t(g["W"], torch.float32), _t(g["U"], torch.float32))
     x = torch.tensor(g["x"].reshape(-1, d), device=DEV)
     s, info = deer.deer_solve(dyn, _t(g["s0"], torch.float32), T, x, jac="diag", tol=1e-5,
-                              confirm=2, prec="fp32", init="zeros")
+                              confirm=2, prec="fp32", init="zeros", window=window)
     assert bool(info.converged.all()), (info.max_resid.max(), info.iters.max())
     pick = [0, int(info.iters.argmax())]
     sub = odyn.GRU(g["W"], g["U"], g["x"][pick].astype(np.float64))
