@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -662,8 +663,10 @@ def run(args):
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) \
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else Clocks(local, "/tmp/deer_clocks.csv")
+    # raw nvidia-smi samples go to DEER_CLOCKS_DIR (default: the system temporary
+    # directory); the JSON line carries their summary
+    clocks_dir = os.environ.get("DEER_CLOCKS_DIR", tempfile.gettempdir())
+    clocks = Clocks(local, os.path.join(clocks_dir, f"deer_clocks_rank{rank}.csv"))
     lib.deer_profile_reset()
     lib.deer_profile_enable(1)
     launches0 = lib.deer_kernel_launch_count()
