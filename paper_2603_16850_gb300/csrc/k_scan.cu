@@ -673,9 +673,10 @@ template cudaError_t launch_adjoint_scan<double>(const AdjScanArgs<double>&, cud
 namespace deer {
 
 // ----------------------------------------------------------------------------
-// Dense scan, d = 16 / 32: D lanes per chunk (per sequence in the carry pass). Lane j
-// owns column j of the chunk product P and entry j of the vectors; the Jacobian rows are
-// read as warp-wide broadcasts, vector entries travel by shuffles.
+// Dense scan, d = 16 / 32: D lanes per chunk (per sequence in the carry pass; four warps
+// per chunk in the d = 32 chunk pass). Lane j owns column j of the chunk product P and
+// entry j of the vectors; the Jacobian rows and chunk aggregates are staged in a
+// shared-memory ring ahead of use, vector entries travel by shuffles.
 // ----------------------------------------------------------------------------
 // 16 bytes (four floats or two doubles) from a 16-byte aligned address. Plain (coherent)
 // load: used for data the same launch never writes, and for data written by earlier
