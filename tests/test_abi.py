@@ -151,3 +151,25 @@ def test_host_output_buffer_checked_before_any_work():
                 torch.empty((5, 2 * 7), dtype=torch.float64).t()):  # not contiguous
         with pytest.raises(ValueError, match="out must be"):
             deer.deer_solve(dyn, s0, 7, out=bad, jac="full")
+
+
+def test_dynamics_factories_describe_the_registry_layouts():
+    """The Python factories of the second-workload kinds fill the C struct the way the
+    header documents (kind, d, input size, per-sequence parameter stride)."""
+    import torch
+
+    import paper_2603_16850_gb300 as deer
+    from paper_2603_16850_gb300 import _native as N
+    W1 = torch.zeros(8, 8)
+    W3 = torch.zeros(3, 8, 8)
+    r1, r3 = deer.Dynamics.rnn_tanh(W1), deer.Dynamics.rnn_tanh(W3)
+    assert (r1.kind, r1.d, r1.d_in, r1.params_stride) == ("rnn_tanh", 8, 8, 0)
+    assert r3.params_stride == 64 and r3.params.numel() == 3 * 64
+    lw = deer.Dynamics.langevin_2well(torch.zeros(5, 4 * 2 + 2), 0.01)
+    assert (lw.d, lw.d_in, lw.params_stride, lw.dt) == (2, 2, 10, 0.01)
+    l96 = deer.Dynamics.lorenz96(torch.full((4,), 8.0), 5, 0.01)
+    assert (l96.d, l96.d_in, l96.params_stride) == (5, 0, 1)
+    pm = deer.Dynamics.permute(5, torch.float32, "cpu")
+    assert (pm.d, pm.d_in, pm.params.dtype) == (5, 5, torch.float32)
+    assert [N.KIND[k] for k in ("rnn_tanh", "langevin_2well", "lorenz96_dp5", "permute")] == \
+        [5, 6, 7, 8]
