@@ -495,9 +495,11 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
   constexpr int GROUPS = 128 / D;          // rows per block
   constexpr bool WANTA = JAC == DEER_JAC_FULL || JAC == DEER_JAC_DIAG;
   __shared__ real sG[GROUPS][D][D + 1];
-  // group stride padded by 16 bytes: the groups of a warp read their K rows from
-  // different banks
-  __shared__ __align__(16) real sK[GROUPS][D * D + 16 / sizeof(real)];
+  // rows padded by 16 bytes (the d lanes' 16-byte row writes fall in distinct banks) and
+  // the group stride by another 16 (the groups of a warp read their K rows from different
+  // banks)
+  constexpr int RSK = D + 16 / (int)sizeof(real);
+  __shared__ __align__(16) real sK[GROUPS][D * RSK + 16 / sizeof(real)];
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gmask = D == 32 ? 0xffffffffu : (0xffffu << (16 * ((threadIdx.x >> 4) & 1)));
   // each group walks kMaRows consecutive active rows and flushes the residual statistics
@@ -560,19 +562,43 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
 #pragma unroll
         for (int j = 0; j < D; ++j) Kn[j] = Gi[j];
         if (stage > 0) {
+          // row m of the previous stage Jacobian (the same for every lane of the group) in
+          // 16-byte pieces, folded in with the packed FMA row update
+          constexpr int VW = 16 / (int)sizeof(real);
 #pragma unroll
           for (int m = 0; m < D; ++m) {
             const real gm = cK * Gi[m];
+            const real* km = &sK[grp][m * RSK];
 #pragma unroll
-            for (int j = 0; j < D; ++j) Kn[j] += gm * sK[grp][m * D + j];
+            for (int j = 0; j < D; j += VW) {
+              real kv[VW], acc[VW];
+              if constexpr (sizeof(real) == 4) {
+                const float4 q = *reinterpret_cast<const float4*>(km + j);
+                kv[0] = q.x; kv[1] = q.y; kv[2] = q.z; kv[3] = q.w;
+              } else {
+                const double2 q = *reinterpret_cast<const double2*>(km + j);
+                kv[0] = q.x; kv[1] = q.y;
+              }
+#pragma unroll
+              for (int e = 0; e < VW; ++e) acc[e] = Kn[j + e];
+              axpy_row<VW>(gm, kv, acc);
+#pragma unroll
+              for (int e = 0; e < VW; ++e) Kn[j + e] = acc[e];
+            }
           }
         }
         __syncwarp(gmask);
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
-          sK[grp][lane * D + j] = Kn[j];
-          Kacc[j] += w * Kn[j];
+        for (int j = 0; j < D; j += 16 / (int)sizeof(real)) {
+          if constexpr (sizeof(real) == 4) {
+            *reinterpret_cast<float4*>(&sK[grp][lane * RSK + j]) =
+                make_float4(Kn[j], Kn[j + 1], Kn[j + 2], Kn[j + 3]);
+          } else {
+            *reinterpret_cast<double2*>(&sK[grp][lane * RSK + j]) =
+                make_double2(Kn[j], Kn[j + 1]);
+          }
         }
+        axpy_row<D>(w, Kn, Kacc);
         __syncwarp(gmask);
       }
       acc += w * g;
