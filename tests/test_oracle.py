@@ -675,3 +675,22 @@ def test_input_gradient_matches_finite_differences(kind):
     fd = adjoint.fd_input_grad(mk, x, s0, T, y, idx, h=1e-6)
     got = np.array([gx[b, t, k] for (b, t, k) in idx])
     assert np.allclose(got, fd, rtol=1e-6, atol=1e-7)
+
+
+def test_lorenz96_elk_stays_bounded_where_deer_overflows():
+    """Sec. elk_exps: on the chaotic Lorenz-96 system (F = 8, D = 5) undamped DEER from the
+    constant guess leaves the attractor within one iteration and overflows after the
+    next, while the Kalman-damped step (ELK, lambda = 1) keeps every iterate on the
+    attractor's scale."""
+    T = 200
+    p = synth.lorenz96(2, 5, seed=0)
+    dyn = dynamics.Lorenz96(p["params"], p["dt"], 5)
+    with np.errstate(all="ignore"):
+        s = newton.initial_guess(dyn, p["s0"], T, "s0")
+        for _ in range(3):
+            s = newton.quasi_newton_step(dyn, p["s0"], s, "full")
+        assert not np.all(np.isfinite(s)) or np.max(np.abs(s)) > 1e6
+        e = newton.initial_guess(dyn, p["s0"], T, "s0")
+        for _ in range(40):
+            e = elk.elk_filter_step(dyn, p["s0"], e, "full", 1.0)
+            assert np.all(np.isfinite(e)) and np.max(np.abs(e)) < 50.0
