@@ -694,3 +694,18 @@ def test_lorenz96_elk_stays_bounded_where_deer_overflows():
         for _ in range(40):
             e = elk.elk_filter_step(dyn, p["s0"], e, "full", 1.0)
             assert np.all(np.isfinite(e)) and np.max(np.abs(e)) < 50.0
+
+
+def test_rnn_iterations_flat_in_T_when_predictable_growing_when_chaotic():
+    """Theorem PL-LLE's two regimes on the mean-field RNN (d = 16): with a negative LLE
+    (g = 0.5) the DEER iteration count does not grow with the sequence length; with a
+    positive one (g = 3) it grows roughly in proportion to T."""
+    its = {}
+    for g in (0.5, 3.0):
+        for T in (50, 150):
+            p = synth.mean_field_rnn(1, T, 16, g, seed=1)
+            dyn = dynamics.MeanFieldRNN(p["W"], p["x"])
+            its[g, T] = int(newton.solve(dyn, p["s0"], T, mode="full", tol=1e-10,
+                                         init="zeros")["iters"][0])
+    assert its[0.5, 150] <= its[0.5, 50] + 1
+    assert its[3.0, 150] >= 2 * its[3.0, 50]
