@@ -173,3 +173,17 @@ def test_dynamics_factories_describe_the_registry_layouts():
     assert (pm.d, pm.d_in, pm.params.dtype) == (5, 5, torch.float32)
     assert [N.KIND[k] for k in ("rnn_tanh", "langevin_2well", "lorenz96_dp5", "permute")] == \
         [5, 6, 7, 8]
+
+
+def test_options_struct_layout_matches_the_header(lib):
+    """deer_default_options writes exactly the struct the binding declares: every field
+    reads back its documented default and the bytes past the ctypes struct stay untouched
+    (a larger C struct would overwrite them)."""
+    from paper_2603_16850_gb300 import _native as N
+    size = C.sizeof(N.deer_options)
+    buf = (C.c_ubyte * (size + 64))(*([0xAB] * (size + 64)))
+    o = N.deer_options.from_buffer(buf)
+    lib.deer_default_options(C.byref(o))
+    assert (o.max_iters, o.tol, o.jac, o.damp, o.damp_param, o.init, o.prec, o.reset,
+            o.chunk, o.confirm, o.window) == (0, 1e-10, 0, 0, 0.0, 1, 0, 0, 0, 1, 0)
+    assert all(b == 0xAB for b in bytes(buf)[size:])
