@@ -187,3 +187,33 @@ def test_options_struct_layout_matches_the_header(lib):
     assert (o.max_iters, o.tol, o.jac, o.damp, o.damp_param, o.init, o.prec, o.reset,
             o.chunk, o.confirm, o.window) == (0, 1e-10, 0, 0, 0.0, 1, 0, 0, 0, 1, 0)
     assert all(b == 0xAB for b in bytes(buf)[size:])
+
+
+def test_binding_enums_match_the_header():
+    """Every enumerator of include/deer.h's kind, Jacobian, damping, initial-guess and
+    precision enums has the same value in the Python binding's maps."""
+    import re
+
+    from paper_2603_16850_gb300 import _native as N
+    hdr = open(os.path.join(ROOT, "include", "deer.h")).read()
+    vals = {m.group(1): int(m.group(2))
+            for m in re.finditer(r"\b(DEER_[A-Z0-9_]+)\s*=\s*(-?\d+)", hdr)}
+    maps = {"DEER_F_": (N.KIND, {"brusselator_euler": "BRUSSELATOR_EULER",
+                                 "massaction_euler": "MASSACTION_EULER",
+                                 "massaction_rk4": "MASSACTION_RK4", "gru": "GRU",
+                                 "linear": "LINEAR", "rnn_tanh": "RNN_TANH",
+                                 "langevin_2well": "LANGEVIN_2WELL",
+                                 "lorenz96_dp5": "LORENZ96_DP5", "permute": "PERMUTE"}),
+            "DEER_JAC_": (N.JAC, {"full": "FULL", "diag": "DIAG", "identity": "IDENTITY",
+                                  "zero": "ZERO"}),
+            "DEER_DAMP_": (N.DAMP, {"none": "NONE", "elk": "ELK", "scale": "SCALE",
+                                    "clip": "CLIP"}),
+            "DEER_INIT_": (N.INIT, {"zeros": "ZEROS", "s0": "S0", "jacobi": "JACOBI",
+                                    "user": "USER"}),
+            "DEER_": (N.PREC, {"fp64": "FP64", "fp32": "FP32", "mixed_bf16": "MIXED_BF16"})}
+    for prefix, (pymap, names) in maps.items():
+        assert set(pymap) == set(names), prefix
+        for py, c in names.items():
+            assert pymap[py] == vals[prefix + c], (prefix, py)
+    kinds = {k for k in vals if k.startswith("DEER_F_")}
+    assert len(kinds) == len(N.KIND)
