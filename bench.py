@@ -35,15 +35,17 @@ METRIC = "converged state-steps/sec vs sequential rollout; scan GB/s or TC % of 
 UNIT = "state-steps/s"
 CONFIG_NAME = ("batched mass-action networks B=4096 d=8 R=12 RK4 dt=1e-3 T=16384, "
                "full-Jacobian Newton, FP32")
-# Algorithmic work per trajectory row of the fused iteration kernel: the RK4 step with its
-# exact step Jacobian by the chain rule (3 products of 8x8 matrices, 3 * 2 d^3 = 3072 flop,
-# plus four rate evaluations, ~300 flop), the chunk-aggregate composition (2 d^3 + 2 d^2)
-# and the scan step applied to the row (2 d^2).
-LIN_FLOP_PER_ROW = 3 * 2 * 8 ** 3 + 300 + 2 * 8 ** 3 + 2 * 8 ** 2 + 2 * 8 ** 2
-# Algorithmic bytes per row of the fused iteration kernel (FP32): the pending Jacobian and
-# offset read, the new ones written (d^2 + d each way) and the state read and written.
-FUSED_BYTES_PER_ROW = 2 * (8 * 8 + 8) * 4 + 2 * 8 * 4
-FP32_LANES_PER_SM, SMS = 128, 152
+# Algorithmic work per trajectory row of one Newton iteration of the headline workload
+# (d = 8, RK4), as the measurement plan fixes it: the step Jacobian by the chain rule through
+# the stages (3 products of 8x8 matrices, 3 * 2 d^3 = 3072 flop), the composition of the
+# affine scan element (2 d^3 + 2 d^2 = 1152 flop) and four rate evaluations (~300 flop):
+# 4524 flop; and, with A_t kept on chip, s_{t-1} and s_t read and s written: 3 * d * 4 = 96 B.
+ALGO_FLOP_PER_ROW = 3 * 2 * 8 ** 3 + (2 * 8 ** 3 + 2 * 8 ** 2) + 300
+ALGO_BYTES_PER_ROW = 3 * 8 * 4
+# What the fused kernel moves per row by design: the pending Jacobian and offset of the
+# previous iteration read and the new ones written (d^2 + d each way), the state read and
+# written.
+IMPL_BYTES_PER_ROW = 2 * (8 * 8 + 8) * 4 + 2 * 8 * 4
 # DRAM bytes per row of the fused iteration kernel from the committed ncu capture of the
 # same kernel (dram__bytes_read.sum + dram__bytes_write.sum over 8.39 M rows at B=512; the
 # traffic per row does not depend on B). Scaled by the rows of an average launch.
@@ -52,6 +54,39 @@ FUSED_TRAFFIC_PER_ROW = (2.710245e9 + 2.687720e9) / 8388608
 # float32 (3 products of 16x16 matrices, 3 * 2 d^3 flop); the float64 rate evaluations are
 # not counted.
 MIXED_LIN_FLOP_PER_ROW = 3 * 2 * 16 ** 3
+
+
+def _rel_err_per_seq(got, ref, off):
+    """Normwise error of every sequence of a packed batch: max |got - ref| / max |ref|."""
+    import numpy as np
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    out = np.zeros(len(off) - 1)
+    for b in range(len(off) - 1):
+        lo, hi = int(off[b]), int(off[b + 1])
+        if hi > lo:
+            out[b] = np.max(np.abs(got[lo:hi] - ref[lo:hi])) / max(np.max(np.abs(ref[lo:hi])),
+                                                                    1e-300)
+    return out
+
+
+class OracleChecks:
+    """Comparisons of GPU results with the FP64 oracle. Each measurement registers a
+    closure over host copies of its results; they all run in the CPU-baseline leg, after
+    every GPU timing, and fill each entry's ``max_rel_err_vs_oracle``."""
+
+    def __init__(self):
+        self.items = []
+
+    def add(self, entry: dict, fn):
+        self.items.append((entry, fn))
+
+    def run(self):
+        for entry, fn in self.items:
+            t0 = time.perf_counter()
+            res = fn()
+            entry.update(res)
+            entry["oracle_check_s"] = round(time.perf_counter() - t0, 2)
 
 
 def _peaks():
@@ -139,41 +174,44 @@ def _problem(rank: int, batch: int = 0):
                             integrator=w["integrator"])
 
 
-def cpu_oracle_sample(p, n_traj: int, n_steps: int):
-    """Time the FP64 oracle (numpy sequential rollout, one thread) on a sample."""
-    import numpy as np
-    from oracle import dynamics as odyn
-    from oracle import newton as onewton
-    sub = odyn.MassAction(p["topology"][:n_traj], p["params"][:n_traj], p["dt"], "rk4", d=p["d"])
+def cpu_oracle_rollout(p, threads=None):
+    """The FP64 oracle's answer for the headline workload, timed: the sequential rollout
+    s_t = f(s_{t-1}) of every trajectory in plain C (oracle/c/massaction.c), the batch split
+    over `threads` host threads (default: every core). Returns (rollout [B*T][d], seconds,
+    threads used)."""
+    from oracle import cma
+    B, T = p["topology"].shape[0], p["T"]
+    threads = threads or cma.cores()
+    batch = cma.Batch(p["topology"], p["params"], p["dt"], "rk4", d=p["d"])
+    off = cma.uniform_offsets(B, T)
     t0 = time.perf_counter()
-    onewton.rollout(sub, p["s0"][:n_traj], n_steps)
-    dt = time.perf_counter() - t0
-    return n_traj * n_steps / dt, dt
+    ref = batch.rollout(p["s0"], off, threads=threads)
+    return ref, time.perf_counter() - t0, threads
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
     p = _problem(0)
-    n_traj, n_steps = 4096, 256
+    B, T = WORKLOAD["B"], WORKLOAD["T"]
     for _ in range(args.warmup):
-        cpu_oracle_sample(p, n_traj, n_steps)
+        cpu_oracle_rollout(p)
     times = []
+    threads = 1
     for _ in range(args.steps):
-        _, dt = cpu_oracle_sample(p, n_traj, n_steps)
+        _, dt, threads = cpu_oracle_rollout(p)
         times.append(dt)
     total = sum(times)
-    value = n_traj * n_steps * len(times) / total
-    sample = (f"{n_traj} of 4096 trajectories x first {n_steps} of 16384 steps per step, "
-              "FP64 oracle sequential rollout (numpy)")
+    value = B * T * len(times) / total
+    sample = (f"the whole workload per step: all {B} trajectories x {T} steps, FP64 oracle "
+              f"sequential rollout in plain C on {threads} host threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": CONFIG_NAME, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -181,7 +219,27 @@ def run_reference(args):
     return 0
 
 
-def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64, window=False):
+def _gru_oracle_check(g, s_host, pick, cache):
+    """Normwise error of the picked GRU trajectories against the FP64 oracle rollout (the
+    rollout is computed once per problem and shared by the quasi-DEER and quasi-ELK
+    entries)."""
+    import numpy as np
+    from oracle import dynamics as odyn
+    from oracle import newton as onewton
+    key = tuple(int(b) for b in pick)
+    if key not in cache:
+        sub = odyn.GRU(g["W"], g["U"], g["x"][list(key)].astype(np.float64))
+        cache[key] = onewton.rollout(sub, g["s0"][list(key)], g["x"].shape[1])
+    ref = cache[key]
+    T, d = ref.shape[1], ref.shape[2]
+    off = [i * T for i in range(len(key) + 1)]
+    err = _rel_err_per_seq(s_host.reshape(-1, d), ref.reshape(-1, d), off)
+    return {"max_rel_err_vs_oracle": float(err.max()),
+            "oracle_sample": f"{len(key)} of {g['x'].shape[0]} trajectories, FP64 numpy rollout"}
+
+
+def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64, window=False, checks=None,
+                         gru_cache=None):
     """GRU cell d=64, inputs 64, T=65536, B=64, weights N(0,1/d), inputs N(0,1), quasi-DEER
     (diagonal Jacobian), FP32: converged state-steps/s and the single-pass look-back
     diagonal scan in achieved HBM GB/s (algorithmic 12 bytes per coordinate-step: a, b read,
@@ -223,28 +281,32 @@ def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64, window=False)
     lin_tf = lin_rows * 4 * 2 * d * d / (lin_ms / 1000.0) / 1e12
     if int(lib.deer_get_tensor_cores()):
         # three products per row on tcgen05 kind::tf32, each as three split MMAs: the
-        # tensor pipe executes 3x the useful flops; its peak is the measured bf16 peak x the
-        # nominal tf32 / bf16 ratio (1.1 / 2.25 PFLOP/s dense)
-        tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25
+        # tensor pipe executes 3x the useful flops
+        tf32_peak, tf32_src = _tf32_peak(lib, peaks)
         lin_entry = {"kernel": "k_gru_lin_tc (tcgen05 kind::tf32, 3-term split)",
                      "avg_launch_ms": lin_ms, "achieved_tflops": lin_tf,
                      "flop_per_row": 4 * 2 * d * d,
                      "tensor_pipe_tflops": 3 * lin_tf, "tf32_peak_tflops": tf32_peak,
-                     "tensor_frac": 3 * lin_tf / tf32_peak}
+                     "tf32_peak_source": tf32_src, "tensor_frac": 3 * lin_tf / tf32_peak}
     else:
         lin_entry = {"kernel": "k_gru_lin_tiled", "avg_launch_ms": lin_ms,
                      "achieved_tflops": lin_tf, "flop_per_row": 4 * 2 * d * d}
-    return {"workload": f"GRU d=64 d_in=64 T=65536 B={B}, quasi-DEER, FP32, tol 1e-5 x2",
-            "value": B * T / (ms / 1000.0), "unit": UNIT, "ms_per_solve": ms,
-            "newton_iters_max": int(info.iters.max()), "converged": bool(info.converged.all()),
-            "diag_scan": {"kernel": "k_diag_lb<float,64>", "bound": "hbm", "achieved": gbs,
-                          "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                          "frac": gbs / peaks["hbm_gbs"], "avg_launch_ms": scan_ms,
-                          "avg_rows_per_launch": scan_rows},
-            "linearize": lin_entry}
+    out = {"workload": f"GRU d=64 d_in=64 T=65536 B={B}, quasi-DEER, FP32, tol 1e-5 x2",
+           "value": B * T / (ms / 1000.0), "unit": UNIT, "ms_per_solve": ms,
+           "newton_iters_max": int(info.iters.max()), "converged": bool(info.converged.all()),
+           "diag_scan": {"kernel": "k_diag_lb<float,64>", "bound": "hbm", "achieved": gbs,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / peaks["hbm_gbs"], "avg_launch_ms": scan_ms,
+                         "avg_rows_per_launch": scan_rows},
+           "linearize": lin_entry}
+    if checks is not None:
+        pick = sorted(set(range(7)) | {int(info.iters.argmax())})
+        s_host = s.view(B, T, d)[torch.as_tensor(pick, device=dev)].cpu().numpy()
+        cache = gru_cache if gru_cache is not None else {}
+        checks.add(out, lambda: _gru_oracle_check(g, s_host, pick, cache))
+    return out
 
-
-def brusselator_measurement(deer, dev, stream, reps=20):
+def brusselator_measurement(deer, dev, stream, reps=20, checks=None):
     """C1: one Brusselator trajectory (d=2, a=1, b=3, s0=(1,1), explicit Euler dt=0.01,
     T=1024), full-Jacobian Newton in FP64 to tol 1e-12 (reset heuristic on: undamped Newton
     from the constant guess overflows on this limit cycle). A single short sequence is
@@ -271,7 +333,7 @@ def brusselator_measurement(deer, dev, stream, reps=20):
     e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
     e0.record(stream)
     for _ in range(reps):
-        _, info = deer.deer_solve(dyn, s0, 1024, workspace=ws_, stream=stream, **opts)
+        s, info = deer.deer_solve(dyn, s0, 1024, workspace=ws_, stream=stream, **opts)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
@@ -282,16 +344,27 @@ def brusselator_measurement(deer, dev, stream, reps=20):
     torch.cuda.synchronize()
     roll_ms = e0.elapsed_time(e1) / reps
     it = int(info.iters[0])
-    return {"workload": "Brusselator d=2 T=1024 Euler dt=0.01, full Newton FP64, tol 1e-12",
-            "us_per_solve": 1000 * ms, "newton_iters": it,
-            "us_per_iteration": 1000 * ms / max(it, 1), "converged": bool(info.converged[0]),
-            "value": 1024 / (ms / 1000.0), "unit": UNIT,
-            "sequential_gpu_rollout_us": 1000 * roll_ms,
-            "chunk": {"chosen": tuned["chunk"], "tuning_ms": tuned["timings"],
-                      "how": "autotune.pick_best on the problem itself"}}
+    out = {"workload": "Brusselator d=2 T=1024 Euler dt=0.01, full Newton FP64, tol 1e-12",
+           "us_per_solve": 1000 * ms, "newton_iters": it,
+           "us_per_iteration": 1000 * ms / max(it, 1), "converged": bool(info.converged[0]),
+           "value": 1024 / (ms / 1000.0), "unit": UNIT,
+           "sequential_gpu_rollout_us": 1000 * roll_ms,
+           "chunk": tuned["chunk"]}
+    if checks is not None:
+        s_host = s.cpu().numpy()
 
+        def check():
+            from oracle import dynamics as odyn
+            from oracle import newton as onewton
+            ref = onewton.rollout(odyn.Brusselator(p["params"], p["dt"]), p["s0"], 1024)[0]
+            err = _rel_err_per_seq(s_host, ref, [0, 1024])
+            return {"max_rel_err_vs_oracle": float(err.max()),
+                    "oracle_sample": "the whole trajectory, FP64 numpy rollout"}
+        checks.add(out, check)
+    return out
 
-def gru_elk_measurement(deer, dev, stream, B=64, lams=(0.01, 0.1, 1.0, 10.0)):
+def gru_elk_measurement(deer, dev, stream, B=64, lams=(0.01, 0.1, 1.0, 10.0), checks=None,
+                        gru_cache=None):
     """The damped variant of the GRU workload (quasi-ELK, Sec. 4.3 with the diagonal
     Jacobian): the same d=64, T=65536, B=64 problem, FP32, tol 1e-5 x2, for a sweep of the
     damping lambda = 1/sigma^2 (lambda -> 0 is quasi-DEER; larger lambda damps more, and
@@ -308,6 +381,8 @@ def gru_elk_measurement(deer, dev, stream, B=64, lams=(0.01, 0.1, 1.0, 10.0)):
     x = torch.tensor(g["x"].reshape(-1, d), device=dev)
     s0 = torch.zeros((B, d), dtype=torch.float32, device=dev)
     rows = []
+    pick = list(range(8))
+    cache = gru_cache if gru_cache is not None else {}
     for lam in lams:
         opts = dict(jac="diag", damp="elk", damp_param=lam, tol=1e-5, confirm=2, prec="fp32",
                     init="zeros", max_iters=1000)
@@ -321,13 +396,16 @@ def gru_elk_measurement(deer, dev, stream, B=64, lams=(0.01, 0.1, 1.0, 10.0)):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        rows.append({"lambda": lam, "value": B * T / (ms / 1000.0), "unit": UNIT, "ms": ms,
-                     "newton_iters_max": int(info.iters.max()),
-                     "converged": bool(info.converged.all())})
+        row = {"lambda": lam, "value": B * T / (ms / 1000.0), "unit": UNIT, "ms": ms,
+               "newton_iters_max": int(info.iters.max()),
+               "converged": bool(info.converged.all())}
+        rows.append(row)
+        if checks is not None:
+            s_host = s.view(B, T, d)[:len(pick)].cpu().numpy()
+            checks.add(row, lambda s_host=s_host: _gru_oracle_check(g, s_host, pick, cache))
         del ws_
     return {"workload": f"GRU d=64 d_in=64 T=65536 B={B}, quasi-ELK (diagonal Kalman-filter "
                         "step), FP32, tol 1e-5 x2", "sweep": rows}
-
 
 def lle_measurement(deer, dyn, s0, s, T, d, stream, n_sys=64):
     """Largest Lyapunov exponent (Ch. 5) along the converged trajectories of the first
@@ -350,11 +428,12 @@ def lle_measurement(deer, dyn, s0, s, T, d, stream, n_sys=64):
             "max": float(v.max()), "ms": e0.elapsed_time(e1)}
 
 
-def adjoint_measurement(deer, N, lib, dev, stream):
+def adjoint_measurement(deer, N, lib, dev, stream, checks=None):
     """Differentiation workload: d=32 kinetic networks (48 reactions), B=256, T=32768, RK4
     dt=1e-3, FP32. Forward full-Jacobian solve, then the adjoint gradient of
     sum_t ||s_t - y_t||^2 w.r.t. the rate constants (targets y: the sequential rollout with
-    rate constants k exp(0.1 eps), used for timing only)."""
+    rate constants k exp(0.1 eps); the timed gradient takes them from the GPU rollout, the
+    oracle check from the FP64 oracle's)."""
     import numpy as np
     import torch
     import synth
@@ -362,7 +441,8 @@ def adjoint_measurement(deer, N, lib, dev, stream):
     p = synth.massaction(B, d, R, T, seed=3)
     topo = torch.tensor(p["topology"], dtype=torch.int32, device=dev)
     k = torch.tensor(p["params"], dtype=torch.float32, device=dev)
-    kp = torch.tensor(synth.perturbed_rates(p["params"], seed=4), dtype=torch.float32, device=dev)
+    kp_np = synth.perturbed_rates(p["params"], seed=4)
+    kp = torch.tensor(kp_np, dtype=torch.float32, device=dev)
     s0 = torch.tensor(p["s0"], dtype=torch.float32, device=dev)
     dyn = deer.Dynamics.massaction(topo, k, d, p["dt"])
     y = deer.deer_rollout(deer.Dynamics.massaction(topo, kp, d, p["dt"]), s0, T, prec="fp32")
@@ -386,23 +466,51 @@ def adjoint_measurement(deer, N, lib, dev, stream):
     torch.cuda.synchronize()
     fwd = e0.elapsed_time(e1)
     grad = e1.elapsed_time(e2)
+    del ws_
     e0.record(stream)
     deer.deer_rollout(dyn, s0, T, prec="fp32", stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     roll_ms = e0.elapsed_time(e1)
-    return {"workload": "mass action d=32 R=48 B=256 T=32768 RK4, FP32, adjoint wrt rates",
-            "sequential_gpu_rollout": {"ms": roll_ms, "value": B * T / (roll_ms / 1000.0),
-                                       "unit": UNIT},
-            "forward_ms": fwd, "grad_ms": grad,
-            "forward_value": B * T / (fwd / 1000.0), "grad_value": B * T / (grad / 1000.0),
-            "unit": UNIT, "newton_iters_max": int(info.iters.max()),
-            "converged": bool(info.converged.all()),
-            "grad_finite": bool(torch.isfinite(dk).all())}
+    out = {"workload": "mass action d=32 R=48 B=256 T=32768 RK4, FP32, adjoint wrt rates",
+           "sequential_gpu_rollout": {"ms": roll_ms, "value": B * T / (roll_ms / 1000.0),
+                                      "unit": UNIT},
+           "forward_ms": fwd, "grad_ms": grad,
+           "forward_value": B * T / (fwd / 1000.0), "grad_value": B * T / (grad / 1000.0),
+           "unit": UNIT, "newton_iters_max": int(info.iters.max()),
+           "converged": bool(info.converged.all()),
+           "grad_finite": bool(torch.isfinite(dk).all())}
+    if checks is not None:
+        pick = sorted({0, 1, 2, int(info.iters.argmax())})
 
+        def check():
+            # the gradient again (untimed), with the oracle's FP64 targets, against the
+            # oracle's reverse recursion at its own FP64 rollout
+            from oracle import cma
+            off = cma.uniform_offsets(B, T)
+            yref = cma.Batch(p["topology"], kp_np, p["dt"], "rk4", d=d).rollout(p["s0"], off)
+            yt = torch.tensor(yref, dtype=torch.float32, device=dev)
+            dk2, _ = deer.deer_grad(dyn, s0, T, s, (2.0 * (s - yt)).contiguous(), prec="fp32",
+                                    workspace=gws, stream=stream)
+            dk2 = dk2.double().cpu().numpy()
+            sub = cma.Batch(p["topology"][pick], p["params"][pick], p["dt"], "rk4", d=d)
+            soff = cma.uniform_offsets(len(pick), T)
+            sref = sub.rollout(p["s0"][pick], soff)
+            yp = yref.reshape(B, T, d)[pick].reshape(-1, d)
+            dk_ref, _ = sub.adjoint(p["s0"][pick], sref, 2.0 * (sref - yp), soff)
+            sv = s.view(B, T, d)[torch.as_tensor(pick, device=dev)].reshape(-1, d).cpu().numpy()
+            ferr = _rel_err_per_seq(sv, sref, soff)
+            gerr = [float(np.max(np.abs(dk2[b] - dk_ref[i])) / np.max(np.abs(dk_ref[i])))
+                    for i, b in enumerate(pick)]
+            return {"max_rel_err_vs_oracle": float(ferr.max()),
+                    "grad_max_rel_err_vs_oracle": max(gerr),
+                    "oracle_sample": f"{len(pick)} of {B} trajectories (incl. the most Newton "
+                                     "iterations): FP64 rollout and reverse adjoint in C"}
+        checks.add(out, check)
+    return out
 
 def threshold_measurement(deer, N, lib, dev, stream, T=100000, d=32, gains=(0.5, 1.0, 2.0),
-                          cap=300):
+                          cap=300, checks=None):
     """The wall-clock side of the predictability threshold (Sec. ssc:exp_thresh): one
     mean-field RNN trajectory (B = 1, d = 32, W_ij ~ N(0, g^2/d), W_ii = 0, sinusoidal
     inputs) of length T, full-Jacobian DEER in FP32 (scaled residual 1e-5, sliding window,
@@ -454,11 +562,22 @@ def threshold_measurement(deer, N, lib, dev, stream, T=100000, d=32, gains=(0.5,
         lib.deer_profile_read(prof)
         lle = float(deer.deer_lle(dyn, s0, T, ref, x=x, prec="fp32", stream=stream)[0])
         err = float((s - ref).abs().max() / ref.abs().max())
-        rows.append({"g": g, "lle": lle, "newton_iters": int(info.iters[0]),
-                     "converged": bool(info.converged[0]), "deer_ms": deer_ms,
-                     "sequential_ms": seq_ms, "speedup": seq_ms / deer_ms,
-                     "max_rel_diff_vs_rollout": err,
-                     "phase_ms": {n: prof.ms[i] for i, n in enumerate(N.PHASES)}})
+        row = {"g": g, "lle": lle, "newton_iters": int(info.iters[0]),
+               "converged": bool(info.converged[0]), "deer_ms": deer_ms,
+               "sequential_ms": seq_ms, "speedup": seq_ms / deer_ms,
+               "max_rel_diff_vs_gpu_rollout": err,
+               "phase_ms": {n: prof.ms[i] for i, n in enumerate(N.PHASES)}}
+        rows.append(row)
+        if checks is not None:
+            s_host = s.cpu().numpy()
+
+            def check(p=p, s_host=s_host):
+                from oracle import dynamics as odyn
+                from oracle import newton as onewton
+                r = onewton.rollout(odyn.MeanFieldRNN(p["W"], p["x"]), p["s0"], T)[0]
+                e = _rel_err_per_seq(s_host, r, [0, T])
+                return {"max_rel_err_vs_oracle": float(e.max())}
+            checks.add(row, check)
     return {"workload": f"mean-field RNN d={d}, B=1, T={T}, FP32 DEER (cap {cap} "
                         "iterations) vs sequential GPU rollout",
             "chunk": {"chosen": tuned["chunk"], "tuning_ms": tuned["timings"],
@@ -500,7 +619,7 @@ def _time_solve(deer, dyn, s0, offsets, opts, stream):
     return e0.elapsed_time(e1)
 
 
-def ragged_mixed_measurement(deer, N, lib, dev, stream, B=1000):
+def ragged_mixed_measurement(deer, N, lib, dev, stream, B=1000, checks=None):
     """Ragged mixed-precision workload: d=16 kinetic networks (24 reactions), lengths
     uniform on [1000, 100000], RK4 dt=1e-3, bf16 Jacobians with float32 scan accumulation,
     float64 state and residual. One group of 1000 trajectories (the full 10000-trajectory
@@ -558,7 +677,7 @@ def ragged_mixed_measurement(deer, N, lib, dev, stream, B=1000):
     deer.deer_solve_batched(dyn32, s032, off, workspace=ws32, stream=stream, **o32)  # warm
     torch.cuda.synchronize()
     e0.record(stream)
-    _, info32 = deer.deer_solve_batched(dyn32, s032, off, workspace=ws32, stream=stream, **o32)
+    s32, info32 = deer.deer_solve_batched(dyn32, s032, off, workspace=ws32, stream=stream, **o32)
     e1.record(stream)
     torch.cuda.synchronize()
     ms32 = e0.elapsed_time(e1)
@@ -573,26 +692,47 @@ def ragged_mixed_measurement(deer, N, lib, dev, stream, B=1000):
         e1.record(stream)
         torch.cuda.synchronize()
         roll[name] = e0.elapsed_time(e1)
-    return {"workload": f"ragged mass action d=16 R=24, T ~ U[1000,100000], B={B} (one of "
-                        "ten groups), bf16 Jacobians / fp32 scan / fp64 residual",
-            "chunk": {"chosen": timings["chunk"], "tuning_ms": timings["timings"],
-                      "tuning_s": tune_s, "how": "autotune.pick_best on 32 trajectories"},
-            "rows_linearized": int(lin_rows), "rows_scanned": int(prof.rows[3]),
-            "linearize_rows_per_s": lin_rows / max(lin_s, 1e-12),
-            "linearize_tflops": lin_rows * MIXED_LIN_FLOP_PER_ROW / max(lin_s, 1e-12) / 1e12,
-            "total_steps": ntot, "ms": ms, "value": ntot / (ms / 1000.0), "unit": UNIT,
-            "newton_iters_max": int(info.iters.max()),
-            "newton_iters_p50": float(np.percentile(info.iters.numpy(), 50)),
-            "converged": bool(info.converged.all()),
-            "phase_ms": {n: prof.ms[i] for i, n in enumerate(N.PHASES)},
-            "fp32_newton": {"ms": ms32, "value": ntot / (ms32 / 1000.0), "unit": UNIT,
-                            "newton_iters_max": int(info32.iters.max()),
-                            "converged": bool(info32.converged.all()),
-                            "note": "float32 everything: its fixed point is the float32 "
-                                    "rollout, not the float64 one the mixed path reaches"},
-            "sequential_gpu_rollout": {name: {"ms": v, "value": ntot / (v / 1000.0),
-                                              "unit": UNIT} for name, v in roll.items()}}
+    out = {"workload": f"ragged mass action d=16 R=24, T ~ U[1000,100000], B={B} (one of "
+                       "ten groups), bf16 Jacobians / fp32 scan / fp64 residual",
+           "chunk": {"chosen": timings["chunk"], "tuning_s": tune_s,
+                     "how": "autotune.pick_best on 32 trajectories"},
+           "rows_linearized": int(lin_rows), "rows_scanned": int(prof.rows[3]),
+           "linearize_rows_per_s": lin_rows / max(lin_s, 1e-12),
+           "linearize_tflops": lin_rows * MIXED_LIN_FLOP_PER_ROW / max(lin_s, 1e-12) / 1e12,
+           "total_steps": ntot, "ms": ms, "value": ntot / (ms / 1000.0), "unit": UNIT,
+           "newton_iters_max": int(info.iters.max()),
+           "newton_iters_p50": float(np.percentile(info.iters.numpy(), 50)),
+           "converged": bool(info.converged.all()),
+           "phase_ms": {n: prof.ms[i] for i, n in enumerate(N.PHASES)},
+           "fp32_newton": {"ms": ms32, "value": ntot / (ms32 / 1000.0), "unit": UNIT,
+                           "newton_iters_max": int(info32.iters.max()),
+                           "converged": bool(info32.converged.all()),
+                           "note": "float32 everything: its fixed point is the float32 "
+                                   "rollout, not the float64 one the mixed path reaches"},
+           "sequential_gpu_rollout": {name: {"ms": v, "value": ntot / (v / 1000.0),
+                                             "unit": UNIT} for name, v in roll.items()}}
+    if checks is not None:
+        lengths = np.diff(off)
+        pick = sorted(set(np.argsort(-lengths)[:4].tolist()) |
+                      set(np.argsort(-info.iters.numpy())[:4].tolist()) | set(range(56)))
+        rows_of = [np.arange(off[b], off[b + 1]) for b in pick]
+        idx = torch.as_tensor(np.concatenate(rows_of), device=dev)
+        s_host = s[idx].cpu().numpy()
+        s32_host = s32[idx].double().cpu().numpy()
+        sub_off = np.concatenate([[0], np.cumsum([len(r) for r in rows_of])])
 
+        def check():
+            from oracle import cma
+            sub = cma.Batch(p["topology"][pick], p["params"][pick], p["dt"], "rk4", d=d)
+            ref = sub.rollout(p["s0"][pick], sub_off)
+            err = _rel_err_per_seq(s_host, ref, sub_off)
+            err32 = _rel_err_per_seq(s32_host, ref, sub_off)
+            out["fp32_newton"]["max_rel_err_vs_oracle"] = float(err32.max())
+            return {"max_rel_err_vs_oracle": float(err.max()),
+                    "oracle_sample": f"{len(pick)} of {B} trajectories (the 4 longest, the 4 "
+                                     "with the most iterations), FP64 rollout in C"}
+        checks.add(out, check)
+    return out
 
 def run_only(args):
     """One secondary workload alone, for profiler captures of its kernels."""
@@ -625,6 +765,45 @@ def run_only(args):
     return 0
 
 
+_ALU_PEAKS = {}
+
+
+def _alu_peaks(lib, dev):
+    """Peak rates of this GPU measured by the library's own microbenchmarks
+    (deer_measure_peak: FP32 and FP64 FMA on every SM, dense tcgen05 MMAs of kind::tf32 and
+    kind::f16 with bf16 operands), in TFLOP/s, timed with CUDA events; the SM count comes
+    from the device. Falls back to SM count x 128 FP32 lanes x 2 x the maximum SM clock
+    where the library has no microbenchmark."""
+    if _ALU_PEAKS:
+        return _ALU_PEAKS
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks, _ = _peaks()
+    if hasattr(lib, "deer_measure_peak"):
+        out = C.c_double(0.0)
+        for name, what in (("fp32", 0), ("fp64", 1), ("tf32_tc", 2), ("bf16_tc", 3)):
+            st = lib.deer_measure_peak(what, torch.cuda.current_stream().cuda_stream,
+                                       C.byref(out))
+            if st == 0 and out.value > 0:
+                _ALU_PEAKS[name] = out.value / 1e12
+                _ALU_PEAKS[name + "_source"] = "measured (deer_measure_peak)"
+    if "fp32" not in _ALU_PEAKS:
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        _ALU_PEAKS["fp32"] = sms * 128 * 2 * mhz * 1e6 / 1e12
+        _ALU_PEAKS["fp32_source"] = f"derived: {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"
+    _ALU_PEAKS["sms"] = sms
+    return _ALU_PEAKS
+
+
+def _tf32_peak(lib, peaks):
+    """tf32 tensor-pipe peak: measured when the library's microbenchmark ran, else the
+    measured bf16 peak x the nominal tf32 / bf16 ratio (1.1 / 2.25 PFLOP/s dense)."""
+    if "tf32_tc" in _ALU_PEAKS:
+        return _ALU_PEAKS["tf32_tc"], _ALU_PEAKS["tf32_tc_source"]
+    return peaks["bf16_tflops"] * 1.1 / 2.25, "bf16 (MEASURED_PEAKS.json) x 1.1/2.25 nominal"
+
+
 def run(args):
     import numpy as np
     import torch
@@ -652,6 +831,7 @@ def run(args):
     nbytes = deer.deer_workspace_bytes(dyn, B, B * T, **opts)
     workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    lib = N.load()
 
     def step():
         return deer.deer_solve(dyn, s0, T, stream=stream, workspace=workspace, **opts)
@@ -659,7 +839,6 @@ def run(args):
     for _ in range(args.warmup):
         s, info = step()
     torch.cuda.synchronize()
-    lib = N.load()
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -690,33 +869,35 @@ def run(args):
     ms = _max_over_ranks(ms, dev)
     value = _whole_job_rate(B * T, ws, ms)
 
-    # roofline of the dominant kernel: the fused iteration kernel (apply the pending scan
-    # step, linearise, form the chunk aggregates) holds almost all device time; the carry
-    # pass and the convergence check are small. Both of its rooflines are reported; the
-    # larger fraction names the bound.
+    # roofline of the dominant kernel, the fused iteration kernel (apply the pending scan
+    # step, linearise, form the chunk aggregates; launches and times from the library's
+    # per-phase CUDA events on the solver's stream): the algorithmic work the measurement
+    # plan fixes per row (4524 flop, 96 B with A kept on chip) against the measured peaks.
     peaks, peak_kind = _peaks()
+    alu = _alu_peaks(lib, dev)
     n_lin = max(prof.launches[1], 1)
     lin_ms = prof.ms[1] / n_lin
     lin_rows = prof.rows[1] / n_lin
-    mhz = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-    alu_ach = lin_rows * LIN_FLOP_PER_ROW / (lin_ms / 1000.0) / 1e12
-    hbm_ach = lin_rows * FUSED_BYTES_PER_ROW / (lin_ms / 1000.0) / 1e9
-    alu_frac, hbm_frac = alu_ach / alu_peak, hbm_ach / peaks["hbm_gbs"]
-    common = {"kernel": "k_fused_ma_lps<float,8,RK4>", "traffic": FUSED_TRAFFIC_PER_ROW * lin_rows,
-              "traffic_source": "ncu dram bytes per row (profiles/, B=512) x rows per launch",
-              "launches": int(prof.launches[1]), "avg_launch_ms": lin_ms,
-              "avg_rows_per_launch": lin_rows,
-              "share_of_step": prof.ms[1] / max(sum(prof.ms), 1e-9)}
-    if alu_frac >= hbm_frac:
-        roof = {**common, "bound": "alu", "achieved": alu_ach, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": alu_frac,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz",
-                "other": {"unit": "GB/s", "achieved": hbm_ach, "frac": hbm_frac}}
-    else:
-        roof = {**common, "bound": "hbm", "achieved": hbm_ach, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": hbm_frac, "peak_source": f"hbm_gbs ({peak_kind})",
-                "other": {"unit": "TFLOP/s", "achieved": alu_ach, "frac": alu_frac}}
+    alu_ach = lin_rows * ALGO_FLOP_PER_ROW / (lin_ms / 1000.0) / 1e12
+    hbm_ach = lin_rows * ALGO_BYTES_PER_ROW / (lin_ms / 1000.0) / 1e9
+    impl_gbs = lin_rows * IMPL_BYTES_PER_ROW / (lin_ms / 1000.0) / 1e9
+    alu_frac, hbm_frac = alu_ach / alu["fp32"], hbm_ach / peaks["hbm_gbs"]
+    traffic = FUSED_TRAFFIC_PER_ROW * lin_rows
+    roof = {"kernel": "k_fused_ma_lps<float,8,RK4>", "bound": "alu", "achieved": alu_ach,
+            "peak": alu["fp32"], "unit": "TFLOP/s", "frac": alu_frac, "traffic": traffic,
+            "peak_source": "FP32 FMA, " + alu["fp32_source"],
+            "flop_per_row": ALGO_FLOP_PER_ROW, "algorithmic_bytes_per_row": ALGO_BYTES_PER_ROW,
+            "hbm_frac_algorithmic": hbm_frac, "hbm_peak_gbs": peaks["hbm_gbs"],
+            "impl_bytes_per_row": IMPL_BYTES_PER_ROW, "impl_gbs": impl_gbs,
+            "traffic_per_row": FUSED_TRAFFIC_PER_ROW,
+            "traffic_ratio": FUSED_TRAFFIC_PER_ROW / ALGO_BYTES_PER_ROW,
+            "traffic_source": "ncu dram bytes per row (profiles/, B=512) x rows per launch",
+            "launches": int(prof.launches[1]), "avg_launch_ms": lin_ms,
+            "avg_rows_per_launch": lin_rows,
+            "share_of_step": prof.ms[1] / max(sum(prof.ms), 1e-9)}
+    for key in ("fp64", "tf32_tc", "bf16_tc"):
+        if key in alu:
+            roof["measured_peak_" + key + "_tflops"] = alu[key]
 
     # sequential GPU rollout (comparison baseline), same precision
     for _ in range(2):
@@ -750,26 +931,69 @@ def run(args):
     e2e_s = (time.perf_counter() - t0) / n_e2e
     h2d = k_h.numel() * 4 + topo_h.numel() * 4 + s0_h.numel() * 4
     d2h = s_h.numel() * 4
+    s_head = s.cpu().numpy()
+    del workspace
 
     extra = {}
+    checks = OracleChecks() if not args.no_cpu_baseline else None
     if rank == 0 and ws == 1 and not args.no_extra:
+        gru_cache = {}
         extra["lle"] = lle_measurement(deer, dyn, s0, s, T, d, stream)
-        extra["brusselator"] = brusselator_measurement(deer, dev, stream)
-        extra["gru_quasi_deer"] = gru_diag_measurement(deer, N, lib, dev, stream)
-        extra["gru_quasi_elk"] = gru_elk_measurement(deer, dev, stream)
-        extra["adjoint"] = adjoint_measurement(deer, N, lib, dev, stream)
-        extra["ragged_mixed"] = ragged_mixed_measurement(deer, N, lib, dev, stream)
-        extra["threshold"] = threshold_measurement(deer, N, lib, dev, stream)
+        extra["brusselator"] = brusselator_measurement(deer, dev, stream, checks=checks)
+        extra["gru_quasi_deer"] = gru_diag_measurement(deer, N, lib, dev, stream, checks=checks,
+                                                       gru_cache=gru_cache)
+        extra["gru_quasi_elk"] = gru_elk_measurement(deer, dev, stream, checks=checks,
+                                                     gru_cache=gru_cache)
+        extra["adjoint"] = adjoint_measurement(deer, N, lib, dev, stream, checks=checks)
+        extra["ragged_mixed"] = ragged_mixed_measurement(deer, N, lib, dev, stream,
+                                                         checks=checks)
+        extra["threshold"] = threshold_measurement(deer, N, lib, dev, stream, checks=checks)
+        q = extra["gru_quasi_deer"]
+        roof["diag_scan_kernel"] = q["diag_scan"]["kernel"]
+        roof["diag_scan_gbs"] = q["diag_scan"]["achieved"]
+        roof["diag_scan_frac"] = q["diag_scan"]["frac"]
+        if "tensor_frac" in q["linearize"]:
+            roof["gru_lin_tc_tensor_frac"] = q["linearize"]["tensor_frac"]
 
+    # CPU-baseline leg: the FP64 oracle timed on the host cores (the whole workload's
+    # sequential rollout, in plain C, split over every core), then every GPU result of this
+    # run compared with the oracle
     cpu = None
+    head_err = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        os.environ.setdefault("OMP_NUM_THREADS", "1")
-        v, dt = cpu_oracle_sample(p, 4096, 256)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "4096 trajectories x first 256 of 16384 steps, FP64 oracle sequential "
-                         f"rollout (numpy), {dt:.1f} s"}
+        ref, cpu_s, threads = cpu_oracle_rollout(p)
+        cpu = {"value": B * T / cpu_s, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"the whole workload ({B} trajectories x {T} steps): FP64 sequential "
+                         f"rollout in plain C on {threads} host threads, {cpu_s:.2f} s"}
+        head_err = float(_rel_err_per_seq(s_head, ref, np.arange(B + 1) * T).max())
+        del ref
+        checks.run()
 
     if rank == 0:
+        summary = {"max_rel_err_vs_oracle": head_err}
+        for name, e in extra.items():
+            if "value" in e:
+                summary[name + "_value"] = e["value"]
+            if "max_rel_err_vs_oracle" in e:
+                summary[name + "_max_rel_err_vs_oracle"] = e["max_rel_err_vs_oracle"]
+        if "adjoint" in extra:
+            a = extra["adjoint"]
+            summary["adjoint_forward_ms"] = a["forward_ms"]
+            summary["adjoint_grad_ms"] = a["grad_ms"]
+            if "grad_max_rel_err_vs_oracle" in a:
+                summary["adjoint_grad_max_rel_err_vs_oracle"] = a["grad_max_rel_err_vs_oracle"]
+        if "gru_quasi_deer" in extra:
+            summary["diag_scan_frac_of_hbm"] = extra["gru_quasi_deer"]["diag_scan"]["frac"]
+        if "ragged_mixed" in extra:
+            summary["ragged_mixed_fp32_newton_max_rel_err_vs_oracle"] = \
+                extra["ragged_mixed"]["fp32_newton"].get("max_rel_err_vs_oracle")
+        if "gru_quasi_elk" in extra:
+            summary["gru_quasi_elk_max_rel_err_vs_oracle"] = max(
+                (r.get("max_rel_err_vs_oracle", 0.0) for r in extra["gru_quasi_elk"]["sweep"]),
+                default=None)
+        if "threshold" in extra:
+            for r in extra["threshold"]["rows"]:
+                summary[f"threshold_g{r['g']}_speedup_vs_sequential"] = r["speedup"]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -778,12 +1002,12 @@ def run(args):
                        "tol": w["tol"], "confirm": w["confirm"], "init": w["init"],
                        "reset": True, "sliding_window": w["window"],
                        "newton_iters_max": iters[-1],
-                       "newton_iters_pct": {q: float(v) for q, v in zip(
-                           ("p50", "p90", "p99", "max"),
-                           np.percentile(info.iters.numpy(), [50, 90, 99, 100]))},
+                       "newton_iters_p50": float(np.percentile(info.iters.numpy(), 50)),
+                       "newton_iters_p99": float(np.percentile(info.iters.numpy(), 99)),
                        "l2": "working set (Jacobians 17 GB) far larger than L2; no flush needed",
                        "parallelism": f"replicas x{ws}"},
             "gpu_launches": int(launches),
+            "max_rel_err_vs_oracle": head_err,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": ws * B * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -793,6 +1017,9 @@ def run(args):
             "phase_ms_per_step": {n: prof.ms[i] / args.steps for i, n in enumerate(N.PHASES)},
             "clocks": clk,
             **extra,
+            # last, so that the end of the line (what a truncated log keeps) holds the
+            # secondary results and their errors against the oracle
+            "summary": summary,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -108,11 +108,22 @@ typedef enum {
   DEER_DAMP_CLIP = 3   /* clip-ELK: diag A~ clipped to [-rho, rho], rho = damp_param (Sec. 4.5.2) */
 } deer_damp;
 
+/* Initial guess s^(0) of the iteration (Sec. 3.3.3: zeros, a copy of s_0, one Jacobi step
+   or iid standard normal draws; any guess converges, Prop. global_convergence). */
 typedef enum {
   DEER_INIT_ZEROS = 0,  /* s^(0)_t = 0 */
   DEER_INIT_S0 = 1,     /* s^(0)_t = s_0 */
   DEER_INIT_JACOBI = 2, /* s^(0)_t = f_t(0): one Jacobi step from zero */
-  DEER_INIT_USER = 3    /* s_out holds the guess on entry (warm start) */
+  DEER_INIT_USER = 3,   /* s_out holds the guess on entry (warm start) */
+  DEER_INIT_RANDN = 4   /* iid N(0, 1) entries from a counter-based generator: entry e of the
+                           packed s array (e = row * d + i) is
+                           sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller, evaluated in float64), with
+                           u1 = ((z(2e+1) >> 11) + 1) 2^-53 and u2 = (z(2e+2) >> 11) 2^-53,
+                           where z(n) is the n-th output (n >= 1) of SplitMix64 started at
+                           deer_options.seed: z(n) = mix(seed + n * 0x9E3779B97F4A7C15),
+                           mix(z) = z ^ (z >> 31) after z ^= z >> 30, z *= 0xBF58476D1CE4E5B9,
+                           z ^= z >> 27, z *= 0x94D049BB133111EB (all modulo 2^64). The same
+                           seed and packing give the same guess on every call. */
 } deer_init;
 
 typedef enum {
@@ -147,7 +158,11 @@ typedef struct {
 typedef struct {
   int32_t max_iters;  /* iteration cap; <= 0 means the longest T (sufficient by
                          Prop. global_convergence) */
-  double tol;         /* converged when max_t ||r_t||_inf <= tol, evaluated in float64 */
+  double tol;         /* a sequence passes the test when its scaled residual
+                         max_{t,i} |r_t,i| / max(1, |s_t,i|) <= tol (r_t = s_t - f_t(s_{t-1}),
+                         Eq. r_def; the absolute residual wherever |s| <= 1), evaluated in
+                         float64 on the iterate about to be updated; it converges after
+                         `confirm` consecutive passing iterates */
   int32_t jac;        /* deer_jac */
   int32_t damp;       /* deer_damp */
   double damp_param;  /* lambda (ELK), k (scale) or rho (clip) */
@@ -170,17 +185,29 @@ typedef struct {
                          unwindowed iteration once rows are frozen. Applies to undamped
                          steps (damp = DEER_DAMP_NONE); damped steps converge linearly and
                          always cover each sequence whole. */
+  uint64_t seed;      /* generator seed of DEER_INIT_RANDN (ignored otherwise) */
+  double* history;    /* optional DEVICE buffer [history_len][4] (NULL = none): the
+                         convergence test of iteration i (i = 0 tests the initial guess)
+                         writes row i = (i, sum over the sequences it tested of their merit
+                         1/2 ||r||^2, the largest scaled residual among them, the number of
+                         sequences still active after it). Rows of tests that did not run
+                         are left untouched; tests past history_len are not recorded. */
+  int32_t history_len;
 } deer_options;
 
 typedef struct {
   int32_t iters;      /* linear-recurrence solves applied to this sequence */
-  int32_t converged;  /* 1 if max |r| <= tol was reached */
-  double merit;       /* 1/2 ||r||^2 of the returned iterate (Eq. merit) */
-  double max_resid;   /* max_t ||r_t||_inf of the returned iterate */
+  int32_t converged;  /* 1 if the convergence test of deer_options.tol passed on
+                         `confirm` consecutive iterates */
+  double merit;       /* 1/2 ||r||^2 (unscaled residual, Eq. merit) of the last iterate
+                         tested (the returned one, unless the iteration cap stopped the
+                         solve after its last scan) */
+  double max_resid;   /* scaled residual max_{t,i} |r_t,i| / max(1, |s_t,i|) of that
+                         iterate (the quantity compared with tol) */
 } deer_info;
 
 /* Fills `opt` with defaults: cap T, tol 1e-10, FULL, no damping, INIT_S0, FP64, auto chunk,
-   confirm 1. */
+   confirm 1, no window, seed 0, no history. */
 void deer_default_options(deer_options* opt);
 
 /* Workspace bytes needed by deer_solve / deer_solve_batched for `batch` sequences
@@ -263,12 +290,15 @@ deer_status deer_rollout(const deer_dynamics* f, int64_t batch, int64_t T,
    in a __device__ array, present on every GPU that loads the library until the process
    exits. Problems whose workspace (deer_workspace_bytes plus one deer_info per sequence)
    does not fit are rejected with DEER_ERR_WORKSPACE (deer_last_cuda_error says how many
-   bytes they needed). The first call on a device looks up the array's device address with
-   the device current; make that first call before any stream capture. Every call reuses
-   the same array and clears what must start at zero, so calls that overlap on the GPU
-   (other streams or threads) race and must be serialised by the caller. Arguments and
-   results as deer_solve (without mixed precision, dense ELK or the sliding window, which
-   return DEER_ERR_UNSUPPORTED); nothing is allocated on the device or the host. */
+   bytes they needed). Every call looks up the array's address on the current device
+   (cudaGetSymbolAddress, which allocates nothing), so a context that was reset and
+   recreated since an earlier call is handled. Like deer_solve, it reads a status word back
+   and synchronises its stream once per Newton iteration, so it cannot be called while the
+   stream is being captured into a CUDA graph. Every call reuses the same array and clears
+   what must start at zero, so calls that overlap on the GPU (other streams or threads)
+   race and must be serialised by the caller. Arguments and results as deer_solve (without
+   mixed precision, dense ELK or the sliding window, which return DEER_ERR_UNSUPPORTED);
+   nothing is allocated on the device or the host. */
 deer_status deer_solve_noalloc(const deer_dynamics* f, int64_t batch, int64_t T,
                                const void* s0, const void* x, void* s_out,
                                const deer_options* opt, deer_stream_t stream,
@@ -282,6 +312,18 @@ size_t deer_noalloc_scratch_bytes(void);
    made after it returns. */
 void deer_set_tensor_cores(int32_t on);
 int32_t deer_get_tensor_cores(void);
+
+/* Peak arithmetic rate of the current GPU, measured (the denominators of the rooflines of
+   the ALU- and tensor-bound kernels; there is no counterpart in the paper): what = 0 FP32
+   FMA (the faster of scalar and packed two-wide FMA chains), 1 FP64 FMA, 2 dense tcgen05
+   MMAs of kind::tf32, 3 dense tcgen05 MMAs of kind::f16 with bf16 operands (M = 128,
+   N = 256, float32 accumulation in tensor memory). Every SM works (the SM count is read
+   from the device); the work is counted exactly (2 flop per multiply-add) and timed with
+   CUDA events on `stream`, best of five launches after two warm-ups. *flops_per_s
+   receives flop/s. Synchronises the stream; allocates nothing (the tensor-memory columns
+   of the MMA kernel are released before it returns). DEER_ERR_TIMEOUT if the MMA
+   kernel's bounded wait gave up, DEER_ERR_INVALID for another `what`. */
+deer_status deer_measure_peak(int32_t what, deer_stream_t stream, double* flops_per_s);
 
 /* Number of kernels this library enqueued since load (all entry points, all threads). */
 int64_t deer_kernel_launch_count(void);

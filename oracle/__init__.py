@@ -26,6 +26,8 @@ Contents (each function cites the passage of the paper it follows):
   central finite differences.
 * ``lle``       - the largest Lyapunov exponent along a trajectory by the
   renormalised tangent recursion of Algorithm alg:LLE_estimate.
+* ``rng``       - the iid N(0, 1) initial guess of Sec. 3.3.3 from a counter-based
+  generator (SplitMix64 outputs through the Box-Muller transform).
 
 Every function runs in float64. Parity unpinned: the iteration counts of the
 synthetic workloads (the paper reports none for them).

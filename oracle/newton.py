@@ -109,13 +109,17 @@ def scaled_residual_max(r, s):
     return np.max(np.abs(r) / np.maximum(1.0, np.abs(s)), axis=(1, 2))
 
 
-def initial_guess(dyn, s0, T, init="s0", user=None):
+def initial_guess(dyn, s0, T, init="s0", user=None, seed=0):
     """s^{(0)} (Sec. 3.3.3): 'zeros'; 's0' (s_0 broadcast over t); 'jacobi' (one Jacobi
-    step from zero, s_t^{(0)} = f_t(0)); 'user' (given)."""
+    step from zero, s_t^{(0)} = f_t(0)); 'randn' (iid N(0, 1) entries of the packed
+    [B*T][d] state from the counter-based generator of ``oracle.rng``); 'user' (given)."""
     s0 = np.asarray(s0, dtype=np.float64)
     B, d = s0.shape
     if init == "zeros":
         return np.zeros((B, T, d))
+    if init == "randn":
+        from .rng import randn_guess
+        return randn_guess(seed, B * T, d).reshape(B, T, d)
     if init == "s0":
         return np.repeat(s0[:, None, :], T, axis=1)
     if init == "jacobi":
@@ -127,7 +131,8 @@ def initial_guess(dyn, s0, T, init="s0", user=None):
 
 
 def solve(dyn, s0, T, mode="full", damp="none", damp_param=0.0, tol=1e-10, max_iters=None,
-          init="s0", user=None, reset=False, reset_threshold=1e30, record=False, confirm=1):
+          init="s0", user=None, reset=False, reset_threshold=1e30, record=False, confirm=1,
+          seed=0):
     """Algorithm alg:deer (ParallelNewton), per sequence of the batch.
 
     Iteration i evaluates r(s^{(i)}); a sequence whose scaled residual
@@ -143,7 +148,7 @@ def solve(dyn, s0, T, mode="full", damp="none", damp_param=0.0, tol=1e-10, max_i
     B, d = s0.shape
     if max_iters is None:
         max_iters = T
-    s = initial_guess(dyn, s0, T, init, user)
+    s = initial_guess(dyn, s0, T, init, user, seed)
     iters = np.zeros(B, dtype=np.int64)
     converged = np.zeros(B, dtype=bool)
     hist = []

@@ -138,7 +138,7 @@ def _dtype(prec: str):
 
 
 def _options(jac, damp, damp_param, tol, max_iters, init, prec, reset, chunk,
-             confirm=1, window=False) -> N.deer_options:
+             confirm=1, window=False, seed=0, history=None) -> N.deer_options:
     o = N.deer_options()
     o.max_iters = int(max_iters)
     o.tol = float(tol)
@@ -151,6 +151,13 @@ def _options(jac, damp, damp_param, tol, max_iters, init, prec, reset, chunk,
     o.chunk = int(chunk)
     o.confirm = int(confirm)
     o.window = int(bool(window))
+    o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    if history is not None:
+        _check_dev(history, "history")
+        if history.dtype != torch.float64 or history.dim() != 2 or history.shape[1] != 4:
+            raise ValueError("history must be a float64 CUDA tensor [n][4]")
+        o.history = history.data_ptr()
+        o.history_len = history.shape[0]
     return o
 
 
@@ -180,7 +187,8 @@ def deer_workspace_bytes(dyn: Dynamics, batch: int, total_steps: int, **opts) ->
 
 def _opt_defaults(opts):
     base = dict(jac="full", damp="none", damp_param=0.0, tol=1e-10, max_iters=0, init="s0",
-                prec="fp64", reset=False, chunk=0, confirm=1, window=False)
+                prec="fp64", reset=False, chunk=0, confirm=1, window=False, seed=0,
+                history=None)
     base.update(opts)
     return base
 
@@ -235,8 +243,10 @@ def deer_solve(dyn: Dynamics, s0: torch.Tensor, T: int, x: Optional[torch.Tensor
 
     Options (see deer_options in include/deer.h): jac ('full'|'diag'|'identity'|'zero'),
     damp ('none'|'elk'|'scale'|'clip'), damp_param, tol, max_iters, init
-    ('zeros'|'s0'|'jacobi'|'user'), prec ('fp64'|'fp32'|'mixed_bf16'), reset, chunk,
-    confirm, window (sliding window: freeze the converged prefix of each sequence).
+    ('zeros'|'s0'|'jacobi'|'randn'|'user'), seed (for 'randn'), prec
+    ('fp64'|'fp32'|'mixed_bf16'), reset, chunk, confirm, window (sliding window: freeze the
+    converged prefix of each sequence), history (a float64 CUDA tensor [n][4] that receives
+    (iteration, merit, max scaled residual, active sequences) of each convergence test).
     Host inputs are copied to the GPU and the result back to the host, into ``out`` when
     given (a preallocated, ideally pinned, host tensor [B*T][d]).
     """

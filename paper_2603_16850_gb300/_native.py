@@ -20,7 +20,7 @@ KIND = {"brusselator_euler": 0, "massaction_euler": 1, "massaction_rk4": 2, "gru
         "rnn_tanh": 5, "langevin_2well": 6, "lorenz96_dp5": 7, "permute": 8}
 JAC = {"full": 0, "diag": 1, "identity": 2, "zero": 3}
 DAMP = {"none": 0, "elk": 1, "scale": 2, "clip": 3}
-INIT = {"zeros": 0, "s0": 1, "jacobi": 2, "user": 3}
+INIT = {"zeros": 0, "s0": 1, "jacobi": 2, "user": 3, "randn": 4}
 PREC = {"fp64": 0, "fp32": 1, "mixed_bf16": 2}
 
 
@@ -37,7 +37,8 @@ class deer_options(C.Structure):
         ("max_iters", C.c_int32), ("tol", C.c_double), ("jac", C.c_int32), ("damp", C.c_int32),
         ("damp_param", C.c_double), ("init", C.c_int32), ("prec", C.c_int32),
         ("reset", C.c_int32), ("chunk", C.c_int32), ("confirm", C.c_int32),
-        ("window", C.c_int32),
+        ("window", C.c_int32), ("seed", C.c_uint64), ("history", C.c_void_p),
+        ("history_len", C.c_int32),
     ]
 
 
@@ -81,6 +82,7 @@ SIGNATURES = {
                                        C.POINTER(deer_info)]),
     "deer_noalloc_scratch_bytes": (C.c_size_t, []),
     "deer_kernel_launch_count": (C.c_int64, []),
+    "deer_measure_peak": (C.c_int32, [C.c_int32, C.c_void_p, C.POINTER(C.c_double)]),
     "deer_selftest_wait_timeout": (C.c_int32, [C.c_void_p]),
     "deer_profile_enable": (None, [C.c_int32]),
     "deer_set_tensor_cores": (None, [C.c_int32]),

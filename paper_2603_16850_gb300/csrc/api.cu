@@ -134,9 +134,14 @@ static int choose_chunk(const deer_options* o, int d) {
   return 128;
 }
 
+// Largest row count any layout accepts: keeps every size product below (N + C) d^2 * 8
+// far from overflowing 64 bits (d <= 64).
+constexpr int64_t kMaxRows = int64_t(1) << 44;
+
 static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer_options* o,
                         Layout& ly) {
   if (!f || !o || B < 0 || N < 0) return false;
+  if (N > kMaxRows || B > kMaxRows || f->d <= 0 || f->d > 64) return false;
   if (o->prec != DEER_FP64 && o->prec != DEER_FP32 && o->prec != DEER_MIXED_BF16) return false;
   const size_t rs = o->prec == DEER_FP32 ? 4 : 8;
   const bool mixed = o->prec == DEER_MIXED_BF16;
@@ -243,7 +248,8 @@ static deer_status check_common(const deer_dynamics* f, const deer_options* o) {
   if (f->kind < 0 || f->kind > DEER_F_PERMUTE) return DEER_ERR_INVALID;
   if (o->jac < 0 || o->jac > DEER_JAC_ZERO) return DEER_ERR_INVALID;
   if (o->damp < 0 || o->damp > DEER_DAMP_CLIP) return DEER_ERR_INVALID;
-  if (o->init < 0 || o->init > DEER_INIT_USER) return DEER_ERR_INVALID;
+  if (o->init < 0 || o->init > DEER_INIT_RANDN) return DEER_ERR_INVALID;
+  if (o->history_len < 0 || (o->history_len > 0 && !o->history)) return DEER_ERR_INVALID;
   if (o->prec != DEER_FP64 && o->prec != DEER_FP32 && o->prec != DEER_MIXED_BF16)
     return DEER_ERR_INVALID;
   if (o->prec == DEER_MIXED_BF16 &&
@@ -379,6 +385,7 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   }
   if (o->init != DEER_INIT_USER) {
     InitArgs<real> ia{dv, bt, s0, s, o->init};
+    ia.seed = o->seed;
     DEER_CK(launch_init<real>(ia, st));
   }
 
@@ -409,6 +416,8 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   ca.log2L = bt.log2L;
   DEER_CK(launch_check(ca, st));  // every sequence starts active
   ca.compact_only = 0;
+  ca.history = o->history;
+  ca.history_len = o->history_len;
 
   DenseScanArgs<real> dsa;
   DiagScanArgs<real> gsa;
@@ -701,6 +710,7 @@ deer_status deer_solve(const deer_dynamics* f, int64_t batch, int64_t T, const v
                        const void* x, void* s_out, const deer_options* opt, void* workspace,
                        size_t workspace_bytes, deer_stream_t stream, deer_info* info) {
   if (batch < 0 || T < 0) return DEER_ERR_INVALID;
+  if (batch > 0 && T > kMaxRows / batch) return DEER_ERR_INVALID;
   std::vector<int64_t> off(batch + 1);
   for (int64_t b = 0; b <= batch; ++b) off[b] = b * T;
   return solve_dispatch(f, batch, off.data(), s0, x, s_out, opt, workspace, workspace_bytes,
@@ -753,6 +763,7 @@ deer_status deer_rollout(const deer_dynamics* f, int64_t batch, int64_t T,
 size_t deer_grad_workspace_bytes(const deer_dynamics* f, int64_t batch, int64_t T,
                                  const deer_options* opt) {
   if (!opt || batch < 0 || T < 0 || opt->prec == DEER_MIXED_BF16) return 0;
+  if (batch > 0 && T > kMaxRows / batch) return 0;
   deer_options o = *opt;
   o.jac = DEER_JAC_FULL;
   o.damp = DEER_DAMP_NONE;
@@ -932,6 +943,7 @@ deer_status deer_lle(const deer_dynamics* f, int64_t batch, int64_t T, const voi
   if (!f || batch < 0 || T < 0) return DEER_ERR_INVALID;
   if (prec != DEER_FP64 && prec != DEER_FP32) return DEER_ERR_UNSUPPORTED;
   if (f->d > 32) return DEER_ERR_UNSUPPORTED;
+  if (batch > 0 && T > kMaxRows / batch) return DEER_ERR_INVALID;
   deer_options o;
   deer_default_options(&o);
   o.prec = prec;
@@ -970,6 +982,7 @@ deer_status deer_grad_ex(const deer_dynamics* f, int64_t batch, int64_t T, const
   if (c != DEER_OK) return c;
   if (batch < 0 || T < 0) return DEER_ERR_INVALID;
   if (batch == 0 || T == 0) return DEER_OK;
+  if (T > kMaxRows / batch) return DEER_ERR_INVALID;
   if (!s0 || !s_star || !dl_ds) return DEER_ERR_INVALID;
   if (needs_x(f->kind) && !x) return DEER_ERR_INVALID;
   const bool per_seq = f->kind == DEER_F_BRUSSELATOR_EULER ||
@@ -1098,24 +1111,18 @@ namespace deer {
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB per device
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-static void* g_noalloc_ptr[kMaxDevices] = {};
-static std::mutex g_noalloc_mu;
-
-// Device address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array on the current device. In host code the array's
+// name is only a host-side stand-in, so every call asks the runtime for the address that
+// belongs to the current device and context (cudaGetSymbolAddress allocates nothing).
+// Looking it up per call rather than caching it keeps the address right when the
+// caller's primary context was reset and recreated since an earlier call (the module is
+// then loaded again and the array may sit elsewhere).
 static cudaError_t noalloc_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> g(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  if (!p || (reinterpret_cast<uintptr_t>(p) & 255u)) return cudaErrorInvalidDevicePointer;
+  *out = p;
   return cudaSuccess;
 }
 
@@ -1140,6 +1147,7 @@ static deer_status solve_noalloc_impl(const deer_dynamics* f, int64_t B, int64_t
                                       const void* s0_, const void* x_, void* s_,
                                       const deer_options* o, char* ws, cudaStream_t st,
                                       deer_info* info_h) {
+  if (B > 0 && T > kMaxRows / B) return DEER_ERR_INVALID;
   const int64_t N = B * T;
   Layout ly;
   if (!make_layout(f, B, N, o, ly)) return DEER_ERR_INVALID;
@@ -1183,26 +1191,70 @@ static deer_status solve_noalloc_impl(const deer_dynamics* f, int64_t B, int64_t
                                    reinterpret_cast<real*>(ws + ly.gru_M), st));
   }
   if (o->init != DEER_INIT_USER) {
-    InitArgs<real> ia{dv, bt, s0, s, o->init};
+    InitArgs<real> ia{};
+    ia.dv = dv;
+    ia.bt = bt;
+    ia.s0 = s0;
+    ia.s = s;
+    ia.init = o->init;
+    ia.seed = o->seed;
     DEER_CK(launch_init<real>(ia, st));
   }
   const int max_iters = o->max_iters > 0 ? o->max_iters : (int)(T > 0 ? T : 1);
   const real reset_thr = sizeof(real) == 8 ? real(1e30) : real(1e18);
+  // the convergence test in the kernels' precision (see solve_impl)
+  real tol_r = (real)o->tol;
+  if ((double)tol_r > o->tol) tol_r = std::nextafter(tol_r, real(0));
 
-  LinArgs<real> la{dv, bt, s0, s, reinterpret_cast<real*>(ws + ly.A),
-                   reinterpret_cast<real*>(ws + ly.b), acc, info, o->jac, o->damp,
-                   (real)o->damp_param};
-  CheckArgs ca{B, d_off, d_cf, acc, info, flags,
-               reinterpret_cast<int64_t*>(ws + ly.act_seq),
-               reinterpret_cast<int64_t*>(ws + ly.act_row_off),
-               reinterpret_cast<int64_t*>(ws + ly.act_chunk_off), o->tol, 0, max_iters, 1,
-               o->confirm > 1 ? o->confirm : 1};
-  DEER_CK(launch_check(ca, st));
+  // every argument block is filled field by field, as in solve_impl
+  LinArgs<real> la{};
+  la.dv = dv;
+  la.bt = bt;
+  la.s0 = s0;
+  la.s = s;
+  la.A = reinterpret_cast<real*>(ws + ly.A);
+  la.b = reinterpret_cast<real*>(ws + ly.b);
+  la.acc = acc;
+  la.info = info;
+  la.jac = o->jac;
+  la.damp = o->damp;
+  la.dparam = (real)o->damp_param;
+  la.tol = tol_r;
+
+  CheckArgs ca{};
+  ca.B = B;
+  ca.offsets = d_off;
+  ca.chunk_first = d_cf;
+  ca.acc = acc;
+  ca.info = info;
+  ca.flags = flags;
+  ca.act_seq = reinterpret_cast<int64_t*>(ws + ly.act_seq);
+  ca.act_row_off = reinterpret_cast<int64_t*>(ws + ly.act_row_off);
+  ca.act_chunk_off = reinterpret_cast<int64_t*>(ws + ly.act_chunk_off);
+  ca.tol = o->tol;
+  ca.it = 0;
+  ca.max_iters = max_iters;
+  ca.compact_only = 1;
+  ca.confirm = o->confirm > 1 ? o->confirm : 1;
+  ca.log2L = bt.log2L;
+  DEER_CK(launch_check(ca, st));  // every sequence starts active
   ca.compact_only = 0;
+  ca.history = o->history;
+  ca.history_len = o->history_len;
 
-  DenseScanArgs<real> dsa{bt, d, la.A, la.b, s, reinterpret_cast<real*>(ws + ly.aggP),
-                          reinterpret_cast<real*>(ws + ly.aggv),
-                          reinterpret_cast<real*>(ws + ly.cin), info, o->reset, reset_thr};
+  DenseScanArgs<real> dsa{};
+  dsa.bt = bt;
+  dsa.d = d;
+  dsa.A = la.A;
+  dsa.b = la.b;
+  dsa.s = s;
+  dsa.aggP = reinterpret_cast<real*>(ws + ly.aggP);
+  dsa.aggv = reinterpret_cast<real*>(ws + ly.aggv);
+  dsa.cin = reinterpret_cast<real*>(ws + ly.cin);
+  dsa.info = info;
+  dsa.reset = o->reset;
+  dsa.reset_thr = reset_thr;
+
   real ac = o->jac == DEER_JAC_IDENTITY ? real(1) : real(0);
   if (o->damp == DEER_DAMP_SCALE) ac *= real(1) - (real)o->damp_param;
   if (o->damp == DEER_DAMP_CLIP) {
@@ -1210,20 +1262,47 @@ static deer_status solve_noalloc_impl(const deer_dynamics* f, int64_t B, int64_t
     ac = ac > rho ? rho : (ac < -rho ? -rho : ac);
   }
   const int elk = (o->damp == DEER_DAMP_ELK && o->damp_param > 0.0) ? 1 : 0;
-  DiagScanArgs<real> gsa{bt, d, o->jac == DEER_JAC_DIAG ? 0 : 1, ac, la.A, la.b, s0, s,
-                         reinterpret_cast<real*>(ws + ly.aggP),
-                         reinterpret_cast<real*>(ws + ly.aggv),
-                         reinterpret_cast<real*>(ws + ly.cin), info, elk,
-                         elk ? real(1.0 / o->damp_param) : real(0),
-                         reinterpret_cast<real*>(ws + ly.mob),
-                         reinterpret_cast<real*>(ws + ly.pin), o->reset, reset_thr};
+  DiagScanArgs<real> gsa{};
+  gsa.bt = bt;
+  gsa.d = d;
+  gsa.amode = o->jac == DEER_JAC_DIAG ? 0 : 1;
+  gsa.aconst = ac;
+  gsa.a = la.A;
+  gsa.b = la.b;
+  gsa.s0 = s0;
+  gsa.s = s;
+  gsa.aggA = reinterpret_cast<real*>(ws + ly.aggP);
+  gsa.aggB = reinterpret_cast<real*>(ws + ly.aggv);
+  gsa.cin = reinterpret_cast<real*>(ws + ly.cin);
+  gsa.info = info;
+  gsa.elk = elk;
+  gsa.sigma2 = elk ? real(1.0 / o->damp_param) : real(0);
+  gsa.mob = reinterpret_cast<real*>(ws + ly.mob);
+  gsa.pin = reinterpret_cast<real*>(ws + ly.pin);
+  gsa.reset = o->reset;
+  gsa.reset_thr = reset_thr;
+
   const bool lookback = use_diag_lookback(o, d);
-  DiagLBArgs<real> lba{bt, d, gsa.amode, gsa.aconst, la.A, la.b, s0, s,
-                       reinterpret_cast<unsigned*>(ws + ly.lb_ticket),
-                       reinterpret_cast<unsigned*>(ws + ly.lb_flags),
-                       reinterpret_cast<real*>(ws + ly.lb_agg),
-                       reinterpret_cast<real*>(ws + ly.lb_pre), 0u, 0, flags, o->reset,
-                       reset_thr};
+  DiagLBArgs<real> lba{};
+  lba.bt = bt;
+  lba.d = d;
+  lba.amode = gsa.amode;
+  lba.aconst = gsa.aconst;
+  lba.a = la.A;
+  lba.b = la.b;
+  lba.s0 = s0;
+  lba.s = s;
+  lba.ticket = reinterpret_cast<unsigned*>(ws + ly.lb_ticket);
+  lba.flags = reinterpret_cast<unsigned*>(ws + ly.lb_flags);
+  lba.agg = reinterpret_cast<real*>(ws + ly.lb_agg);
+  lba.pre = reinterpret_cast<real*>(ws + ly.lb_pre);
+  lba.epoch = 0u;
+  lba.cps = 0;
+  lba.status = flags;
+  lba.reset = o->reset;
+  lba.reset_thr = reset_thr;
+  // the look-back flags carry the epoch of their launch; the scratch keeps the last call's
+  // flags, so they are cleared before this call's first launch
   if (lookback) DEER_CK(cudaMemsetAsync(lba.flags, 0, (size_t)ly.n_chunks_max * 4, st));
 
   deer_status status = DEER_OK;
@@ -1283,6 +1362,7 @@ deer_status deer_solve_noalloc(const deer_dynamics* f, int64_t batch, int64_t T,
   if (opt->window) return DEER_ERR_UNSUPPORTED;
   if (batch < 0 || T < 0) return DEER_ERR_INVALID;
   if (batch == 0 || T == 0) return DEER_OK;
+  if (T > kMaxRows / batch) return DEER_ERR_INVALID;
   if (!s0 || !s_out) return DEER_ERR_INVALID;
   if (needs_x(f->kind) && !x) return DEER_ERR_INVALID;
   void* scratch = nullptr;

@@ -18,9 +18,12 @@
 // diagonal Jacobian and the residual; h and r stay in registers across the three stages. Every mbarrier wait is bounded; a wait that gives up sets the
 // timeout flag and the kernel winds down, freeing its tensor memory.
 #include "kernels.h"
+#include "tc.cuh"
 
 namespace deer {
 namespace {
+
+using namespace tc;
 
 constexpr int kD = 64;        // state size = input size
 constexpr int kTM = 128;      // rows per tile = MMA M
@@ -44,10 +47,6 @@ struct TcSmem {
   float Ah[kTM * kD], Al[kTM * kD];    // activations
 };
 
-__device__ __forceinline__ uint32_t su32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
 __device__ __forceinline__ float tf32_hi(float x) {
   return __uint_as_float(__float_as_uint(x) & 0xffffe000u);
 }
@@ -60,83 +59,8 @@ __device__ __forceinline__ void split_store4(float* hi, float* lo, uint32_t byte
       make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
 }
 
-// shared-memory matrix descriptor: start, LBO, SBO (bytes), fixed version bits 46..48 = 1,
-// base offset 0, no swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((saddr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
-}
-
-// instruction descriptor, kind::tf32: D float32, A and B tf32, both K-major, N, M
-__host__ __device__ constexpr uint32_t idesc_tf32(int N, int M) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd,
-                                         uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-      ::"r"(dtmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
-  for (unsigned i = 0; i < kWaitLimit; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-// 16 consecutive accumulator columns of this thread's lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-      "%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 8 consecutive accumulator columns of this thread's lane
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  return tc::bar_wait(bar, parity, kWaitLimit);
 }
 
 // D (+)= A B^T over K = 64 with the three-term split: 8 K-steps of 8 (two core matrices)
@@ -203,9 +127,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gru_lin_tc(GruTileArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  tc_fence_before();
+  fence_before();
   __syncthreads();
-  tc_fence_after();
+  fence_after();
   const uint32_t tmem = tmem_base_sh;
   const uint32_t tl = tmem + ((uint32_t)(32 * qd) << 16);  // this warp's lanes, column 0
   uint32_t phase = 0, last = 0;
@@ -215,9 +139,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gru_lin_tc(GruTileArgs a) {
   // issue the products of a stage, and wait (bounded) for them
   auto run_stage = [&](int which) -> bool {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
+    fence_before();
     __syncthreads();
-    tc_fence_after();
+    fence_after();
     if (tid == 0) {
       if (which == 1) gemm3(tmem, S.Ah, S.Al, S.B1h, S.B1l, 128);
       else if (which == 2) gemm3(tmem + 128, S.Ah, S.Al, S.B2h, S.B2l, kD);
@@ -227,7 +151,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gru_lin_tc(GruTileArgs a) {
     last = phase;
     const bool ok = bar_wait(bar, last);
     phase ^= 1u;
-    tc_fence_after();
+    fence_after();
     if (!ok) s_ok = 0;
     __syncthreads();
     return s_ok != 0;
@@ -346,9 +270,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gru_lin_tc(GruTileArgs a) {
       atomicMax(reinterpret_cast<int*>(&rmx[rl]), __float_as_int(mx));
       atomicAdd(&rsq[rl], sq);
     }
-    tc_fence_before();
+    fence_before();
     __syncthreads();
-    tc_fence_after();
+    fence_after();
     if (qc == 0)
       acc_resid_f(a.acc, seq, v, rmx[rl], rsq[rl],
                   bad_key(!(rmx[rl] <= a.tol_f), row - (v ? __ldg(a.bt.offsets + seq) : 0)));
@@ -359,9 +283,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gru_lin_tc(GruTileArgs a) {
     // released
     bar_wait(bar, last);
   }
-  tc_fence_before();
+  fence_before();
   __syncthreads();
-  tc_fence_after();
+  fence_after();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTmemCols)

@@ -366,9 +366,43 @@ cudaError_t launch_ma_setup(int64_t n_seq, int d, int R, const real* k, int64_t 
 // Kind dispatch. Mass action runs its own kernels here; the kinds evaluated through the
 // generic kernels are launched from their own translation units.
 // ----------------------------------------------------------------------------
+// DEER_INIT_RANDN: iid standard normal entries (Sec. 3.3.3 draws the guess from N(0, I)).
+// Entry e of the packed state takes outputs 2e+1 and 2e+2 of the SplitMix64 stream
+// started at the seed (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", 2014: output n is the mix of seed + n * golden gamma), so any thread can
+// draw any entry, and turns them into one normal by the Box-Muller transform in float64.
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed,
+                                                            unsigned long long n) {
+  unsigned long long z = seed + n * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <class real>
+__global__ void __launch_bounds__(256) k_init_randn(real* __restrict__ s, int64_t n,
+                                                    unsigned long long seed) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += stride) {
+    const unsigned long long z1 = splitmix64_at(seed, 2ull * (unsigned long long)e + 1ull);
+    const unsigned long long z2 = splitmix64_at(seed, 2ull * (unsigned long long)e + 2ull);
+    const double u1 = (double)((z1 >> 11) + 1ull) * 0x1.0p-53;  // (0, 1]
+    const double u2 = (double)(z2 >> 11) * 0x1.0p-53;           // [0, 1)
+    s[e] = (real)(sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
+  }
+}
+
 template <class real>
 cudaError_t launch_init(const InitArgs<real>& a, cudaStream_t st) {
   if (a.bt.N == 0) return cudaSuccess;
+  if (a.init == DEER_INIT_RANDN) {
+    const int64_t n = a.bt.N * a.dv.d;
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 32) g = 152 * 32;
+    k_init_randn<real><<<(unsigned)g, 256, 0, st>>>(a.s, n, a.seed);
+    note_launch();
+    return cudaGetLastError();
+  }
   switch (a.dv.kind) {
     case DEER_F_MASSACTION_EULER: return generic_init<real, DEER_F_MASSACTION_EULER>(a, st);
     case DEER_F_MASSACTION_RK4: return generic_init<real, DEER_F_MASSACTION_RK4>(a, st);

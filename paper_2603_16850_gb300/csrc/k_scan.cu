@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(1024) k_check(CheckArgs a) {
   const int64_t hi = lo + per < a.B ? lo + per : a.B;
   int nonfinite = 0;
   long long n_act = 0, rows = 0, chunks = 0;
+  double h_merit = 0.0, h_max = 0.0;  // history: over the sequences tested here
   for (int64_t seq = lo; seq < hi; ++seq) {
     SeqInfo inf = a.info[seq];
     if (!inf.done && !a.compact_only) {
@@ -63,6 +64,8 @@ __global__ void __launch_bounds__(1024) k_check(CheckArgs a) {
       const double mr = __longlong_as_double((long long)acc.max_bits);
       inf.max_resid = mr;
       inf.merit = 0.5 * acc.sumsq;
+      h_merit += inf.merit;
+      h_max = nanmax(h_max, mr);
       if (!(mr <= DBL_MAX)) ++nonfinite;  // NaN or Inf
       inf.passes = mr <= a.tol ? inf.passes + 1 : 0;
       if (inf.passes >= a.confirm) {
@@ -121,6 +124,30 @@ __global__ void __launch_bounds__(1024) k_check(CheckArgs a) {
     a.flags->n_nonfinite = s_nonfinite;
     a.flags->active_rows = tr;
     a.flags->active_chunks = tc;
+  }
+  if (a.history && !a.compact_only && a.it < a.history_len) {
+    // block reduction of the tested sequences' merit sum and largest scaled residual
+    __shared__ double s_sum[32], s_max[32];
+    const unsigned full = 0xffffffffu;
+    for (int o = 16; o > 0; o >>= 1) {
+      h_merit += __shfl_xor_sync(full, h_merit, o);
+      h_max = nanmax(h_max, __shfl_xor_sync(full, h_max, o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { s_sum[warp] = h_merit; s_max[warp] = h_max; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0, mx = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        sum += s_sum[w];
+        mx = nanmax(mx, s_max[w]);
+      }
+      double* h = a.history + 4 * (int64_t)a.it;
+      h[0] = (double)a.it;
+      h[1] = sum;
+      h[2] = mx;
+      h[3] = (double)tn;
+    }
   }
 }
 

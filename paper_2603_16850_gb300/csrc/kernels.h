@@ -13,6 +13,7 @@ struct InitArgs {
   const real* s0;
   real* s;
   int init;
+  unsigned long long seed = 0ull;  // DEER_INIT_RANDN
 };
 
 template <class real>
@@ -67,6 +68,10 @@ struct CheckArgs {
   int64_t* win_chunk = nullptr;
   int window = 0;
   int log2L = 0;
+  // optional per-iteration record [history_len][4] (iteration, merit sum, max scaled
+  // residual, active sequences after the test); nullptr = off
+  double* history = nullptr;
+  int history_len = 0;
 };
 
 // Dense (FULL) correction-form scan: Delta_t = A_t Delta_{t-1} + b_t, Delta_0 = 0,

@@ -103,6 +103,22 @@ def test_invalid_arguments_fail_without_device_work(lib):
     # workspace too small (checked before any device call)
     assert lib.deer_solve(C.byref(dyn), 1, 10, 8, None, 8, C.byref(o), 256, 16, None,
                           info) == N.DEER_ERR_WORKSPACE
+    # a history length without a buffer, an unknown initial guess
+    o.history_len = 4
+    assert lib.deer_solve(C.byref(dyn), 1, 10, 8, None, 8, C.byref(o), None, 0, None,
+                          info) == N.DEER_ERR_INVALID
+    lib.deer_default_options(C.byref(o))
+    o.init = 5
+    assert lib.deer_solve(C.byref(dyn), 1, 10, 8, None, 8, C.byref(o), None, 0, None,
+                          info) == N.DEER_ERR_INVALID
+    lib.deer_default_options(C.byref(o))
+    # sizes whose products would overflow are rejected before any arithmetic on them
+    assert lib.deer_solve(C.byref(dyn), 1 << 40, 1 << 40, 8, None, 8, C.byref(o), None, 0,
+                          None, info) == N.DEER_ERR_INVALID
+    assert lib.deer_workspace_bytes(C.byref(dyn), 1, 1 << 62, C.byref(o)) == 0
+    assert lib.deer_grad_workspace_bytes(C.byref(dyn), 1 << 40, 1 << 40, C.byref(o)) == 0
+    assert lib.deer_solve_noalloc(C.byref(dyn), 1 << 40, 1 << 40, 8, None, 8, C.byref(o),
+                                  None, info) == N.DEER_ERR_INVALID
 
 
 def test_second_workload_kinds_sizes_and_checks(lib):
@@ -185,7 +201,8 @@ def test_options_struct_layout_matches_the_header(lib):
     o = N.deer_options.from_buffer(buf)
     lib.deer_default_options(C.byref(o))
     assert (o.max_iters, o.tol, o.jac, o.damp, o.damp_param, o.init, o.prec, o.reset,
-            o.chunk, o.confirm, o.window) == (0, 1e-10, 0, 0, 0.0, 1, 0, 0, 0, 1, 0)
+            o.chunk, o.confirm, o.window, o.seed, o.history, o.history_len) == \
+        (0, 1e-10, 0, 0, 0.0, 1, 0, 0, 0, 1, 0, 0, None, 0)
     assert all(b == 0xAB for b in bytes(buf)[size:])
 
 
@@ -209,7 +226,7 @@ def test_binding_enums_match_the_header():
             "DEER_DAMP_": (N.DAMP, {"none": "NONE", "elk": "ELK", "scale": "SCALE",
                                     "clip": "CLIP"}),
             "DEER_INIT_": (N.INIT, {"zeros": "ZEROS", "s0": "S0", "jacobi": "JACOBI",
-                                    "user": "USER"}),
+                                    "user": "USER", "randn": "RANDN"}),
             "DEER_": (N.PREC, {"fp64": "FP64", "fp32": "FP32", "mixed_bf16": "MIXED_BF16"})}
     for prefix, (pymap, names) in maps.items():
         assert set(pymap) == set(names), prefix
