@@ -193,6 +193,35 @@ typedef struct {
                          sequences still active after it). Rows of tests that did not run
                          are left untouched; tests past history_len are not recorded. */
   int32_t history_len;
+  int32_t compensate;  /* DEER_FP32 with mass-action kinetics and the full Jacobian (d = 4, 8,
+                          16, 32): 1 keeps, for every state entry, a float32 compensation
+                          term in the workspace (the state is the unevaluated sum s + lo,
+                          |lo| <= ulp(s)/2), forms the residual from the pair in increment
+                          form ((s_t - s_{t-1}) - inc_t + (lo_t - lo_{t-1}), inc_t = f(s_{t-1})
+                          - s_{t-1} from the integrator) and adds each Newton correction to
+                          the pair with error-free transformations. Near equilibrium the
+                          per-step increments of these trajectories fall below half a float32
+                          ulp of the state, where a plain float32 state loses them and the
+                          loss adds up along the conserved directions (errors of 1e-4 at
+                          T = 16384); with the pair the returned s is the float32 rounding of
+                          a trajectory accurate to the float32 rounding of the increments.
+                          Costs 8 more bytes per state entry per iteration. 0 = plain float32
+                          state. Ignored for other kinds, modes and precisions. Default 1. */
+  int64_t jac_bytes_max; /* the most bytes the stored step Jacobians may take (0 = no
+                          bound). deer_grad / deer_grad_ex: below B T d^2 values the reverse
+                          recursion runs over time windows of
+                          W = jac_bytes_max / (B d^2 sizeof(real)) rows from the end of the
+                          sequences: each window's Jacobians are formed when it is reached
+                          (each one once), its rows of the trajectory, cotangents and inputs
+                          are gathered into the workspace, and the adjoint entering it from
+                          the later window joins the cotangent of its last row; the gradient
+                          is the same up to rounding. deer_solve / deer_solve_batched with
+                          DEER_MIXED_BF16 and d = 16: when the bf16 Jacobians of all rows
+                          (N d^2 2 bytes) exceed it, none is stored: each chunk's aggregate is
+                          formed while the chunk is linearised, and the scan's final pass
+                          linearises it again (the same arithmetic from the same iterate)
+                          to apply the correction, so the iterates are the same. The
+                          workspace queries shrink accordingly. */
 } deer_options;
 
 typedef struct {
@@ -207,7 +236,7 @@ typedef struct {
 } deer_info;
 
 /* Fills `opt` with defaults: cap T, tol 1e-10, FULL, no damping, INIT_S0, FP64, auto chunk,
-   confirm 1, no window, seed 0, no history. */
+   confirm 1, no window, seed 0, no history, compensated float32 state. */
 void deer_default_options(deer_options* opt);
 
 /* Workspace bytes needed by deer_solve / deer_solve_batched for `batch` sequences
@@ -297,8 +326,9 @@ deer_status deer_rollout(const deer_dynamics* f, int64_t batch, int64_t T,
    stream is being captured into a CUDA graph. Every call reuses the same array and clears
    what must start at zero, so calls that overlap on the GPU (other streams or threads)
    race and must be serialised by the caller. Arguments and results as deer_solve (without
-   mixed precision, dense ELK or the sliding window, which return DEER_ERR_UNSUPPORTED);
-   nothing is allocated on the device or the host. */
+   mixed precision, dense ELK or the sliding window, which return DEER_ERR_UNSUPPORTED, and
+   always with a plain float32 state: `compensate` is ignored); nothing is allocated on the
+   device or the host. */
 deer_status deer_solve_noalloc(const deer_dynamics* f, int64_t batch, int64_t T,
                                const void* s0, const void* x, void* s_out,
                                const deer_options* opt, deer_stream_t stream,

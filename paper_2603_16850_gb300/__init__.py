@@ -138,7 +138,8 @@ def _dtype(prec: str):
 
 
 def _options(jac, damp, damp_param, tol, max_iters, init, prec, reset, chunk,
-             confirm=1, window=False, seed=0, history=None) -> N.deer_options:
+             confirm=1, window=False, seed=0, history=None,
+             compensate=True, jac_bytes_max=0) -> N.deer_options:
     o = N.deer_options()
     o.max_iters = int(max_iters)
     o.tol = float(tol)
@@ -152,6 +153,8 @@ def _options(jac, damp, damp_param, tol, max_iters, init, prec, reset, chunk,
     o.confirm = int(confirm)
     o.window = int(bool(window))
     o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    o.compensate = int(bool(compensate))
+    o.jac_bytes_max = int(jac_bytes_max)
     if history is not None:
         _check_dev(history, "history")
         if history.dtype != torch.float64 or history.dim() != 2 or history.shape[1] != 4:
@@ -188,7 +191,7 @@ def deer_workspace_bytes(dyn: Dynamics, batch: int, total_steps: int, **opts) ->
 def _opt_defaults(opts):
     base = dict(jac="full", damp="none", damp_param=0.0, tol=1e-10, max_iters=0, init="s0",
                 prec="fp64", reset=False, chunk=0, confirm=1, window=False, seed=0,
-                history=None)
+                history=None, compensate=True, jac_bytes_max=0)
     base.update(opts)
     return base
 
@@ -246,7 +249,9 @@ def deer_solve(dyn: Dynamics, s0: torch.Tensor, T: int, x: Optional[torch.Tensor
     ('zeros'|'s0'|'jacobi'|'randn'|'user'), seed (for 'randn'), prec
     ('fp64'|'fp32'|'mixed_bf16'), reset, chunk, confirm, window (sliding window: freeze the
     converged prefix of each sequence), history (a float64 CUDA tensor [n][4] that receives
-    (iteration, merit, max scaled residual, active sequences) of each convergence test).
+    (iteration, merit, max scaled residual, active sequences) of each convergence test),
+    compensate (fp32 mass-action kinetics with the full Jacobian: keep a compensated
+    two-float state, default True).
     Host inputs are copied to the GPU and the result back to the host, into ``out`` when
     given (a preallocated, ideally pinned, host tensor [B*T][d]).
     """
@@ -294,16 +299,17 @@ def deer_rollout(dyn: Dynamics, s0: torch.Tensor, T: int = 0, x=None, *, offsets
 
 
 def deer_grad(dyn: Dynamics, s0, T, s_star, dl_ds, x=None, *, prec="fp64", chunk=0,
-              stream=None, workspace=None, want_ds0=True, want_dx=False):
+              stream=None, workspace=None, want_ds0=True, want_dx=False, jac_bytes_max=0):
     """Adjoint gradient at the converged trajectory. Returns (dl/dparams [B][P], dl/ds0),
     plus dl/dx (the layout of x) when ``want_dx`` (deer_grad_ex: GRU, affine, mean-field
     RNN and Langevin inputs); dl/dparams is None for kinds without per-sequence trainable
     parameters (only the Brusselator's (a, b) and the mass-action rate constants are
-    differentiated)."""
+    differentiated). ``jac_bytes_max`` > 0 bounds the memory of the stored step Jacobians
+    (the reverse scan then runs over time windows, see deer_options.jac_bytes_max)."""
     lib = N.load()
     B = s0.shape[0]
     dt = _dtype(prec)
-    o = _options(**_opt_defaults(dict(prec=prec, chunk=chunk)))
+    o = _options(**_opt_defaults(dict(prec=prec, chunk=chunk, jac_bytes_max=jac_bytes_max)))
     cdyn = dyn.c_struct()
     P = dyn.params_stride if dyn.params_stride else dyn.params.numel()
     trainable = dyn.kind in ("brusselator_euler", "massaction_euler", "massaction_rk4")

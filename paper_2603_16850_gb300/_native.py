@@ -38,7 +38,8 @@ class deer_options(C.Structure):
         ("damp_param", C.c_double), ("init", C.c_int32), ("prec", C.c_int32),
         ("reset", C.c_int32), ("chunk", C.c_int32), ("confirm", C.c_int32),
         ("window", C.c_int32), ("seed", C.c_uint64), ("history", C.c_void_p),
-        ("history_len", C.c_int32),
+        ("history_len", C.c_int32), ("compensate", C.c_int32),
+        ("jac_bytes_max", C.c_int64),
     ]
 
 

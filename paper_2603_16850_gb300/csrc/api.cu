@@ -114,7 +114,9 @@ struct Layout {
   size_t offsets, chunk_first, win_chunk, act_seq, act_row_off, act_chunk_off, acc, info, flags,
       ma, gru_M,
       A, b, aggP, aggv, cin, mob, pin, sprev, lb_ticket, lb_flags, lb_agg, lb_pre, xproj,
-      adj_off, adj_e, total;
+      adj_off, adj_e, slo, sprev_lo, sbound, fastsel, total;
+  bool cs;         // compensated float32 state
+  bool mixed_rc;   // mixed precision without stored Jacobians
   int64_t n_chunks_max;
   int64_t ma_stride, n_ma;
   int L;
@@ -125,6 +127,14 @@ struct Layout {
 static bool use_diag_lookback(const deer_options* o, int d) {
   return o->jac != DEER_JAC_FULL && o->damp != DEER_DAMP_ELK && d % 4 == 0 && d >= 4 &&
          d <= 64;
+}
+
+// Compensated float32 state: the mass-action kinetics with the full Jacobian on the
+// lane-per-species fused path (d = 4, 8) and the wide path (d = 16, 32).
+static bool use_compensated(const deer_dynamics* f, const deer_options* o) {
+  const bool ma = f->kind == DEER_F_MASSACTION_EULER || f->kind == DEER_F_MASSACTION_RK4;
+  return o->prec == DEER_FP32 && o->compensate && ma && o->jac == DEER_JAC_FULL &&
+         o->damp != DEER_DAMP_ELK && (f->d == 4 || f->d == 8 || f->d == 16 || f->d == 32);
 }
 
 static int choose_chunk(const deer_options* o, int d) {
@@ -173,7 +183,14 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
     ly.ma = take((size_t)(ly.n_ma > 0 ? ly.n_ma : 1) * ly.ma_stride * rs);
   }
   if (f->kind == DEER_F_GRU) ly.gru_M = take((size_t)d * d * rs);
-  if (mixed) {
+  // mixed precision, d = 16: the Jacobians are not stored when they would exceed the bound
+  ly.mixed_rc = mixed && d == 16 && o->jac_bytes_max > 0 &&
+                (double)N * d * d * 2 > (double)o->jac_bytes_max;
+  ly.sbound = ly.fastsel = p;
+  if (ly.mixed_rc) {
+    ly.sbound = take((size_t)C * d * 8);
+    ly.fastsel = take((size_t)(B > 0 ? B : 1));
+  } else if (mixed) {
     // bfloat16 E = A - I, float32 offsets and aggregates
     ly.A = take((size_t)N * d * d * 2);
     ly.b = take((size_t)N * d * 4);
@@ -212,6 +229,12 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
   if (!mixed && o->jac == DEER_JAC_FULL && o->damp != DEER_DAMP_ELK &&
       dense_fused_supported(f->kind, d))
     ly.sprev = take((size_t)C * d * rs);
+  ly.cs = use_compensated(f, o);
+  ly.slo = ly.sprev_lo = p;
+  if (ly.cs) {
+    ly.slo = take((size_t)N * d * 4);
+    if (d <= 8) ly.sprev_lo = take((size_t)C * d * 4);
+  }
   ly.lb_ticket = ly.lb_flags = ly.lb_agg = ly.lb_pre = p;
   if (use_diag_lookback(o, d)) {
     ly.lb_ticket = take(256);
@@ -220,6 +243,45 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
     ly.lb_pre = take((size_t)C * d * rs);
   }
   ly.total = p;
+  return true;
+}
+
+// Rows per time window of the memory-bounded adjoint: the step Jacobians of all B sequences
+// over W rows take B W d^2 values; 0 = no bound (every Jacobian stored at once).
+static int64_t grad_window_rows(const deer_dynamics* f, int64_t B, int64_t T,
+                                const deer_options* o) {
+  if (o->jac_bytes_max <= 0 || B <= 0) return T;
+  const size_t rs = o->prec == DEER_FP32 ? 4 : 8;
+  const int64_t per_row = B * (int64_t)f->d * f->d * (int64_t)rs;
+  int64_t W = o->jac_bytes_max / per_row;
+  if (W < 1) W = 1;
+  return W < T ? W : T;
+}
+
+// Workspace of the windowed adjoint: the layout of a problem of B sequences of W rows, and
+// per window the adjoints, the gathered trajectory, cotangents and inputs, the states
+// before the window and two carries [B][d].
+struct GradWinLayout {
+  Layout ly;
+  size_t lam, s, g, x, dx, s0, carry0, carry1, total;
+};
+
+static bool grad_win_layout(const deer_dynamics* f, int64_t B, int64_t W, const deer_options* o,
+                            bool has_x, bool want_dx, GradWinLayout& gl) {
+  if (!make_layout(f, B, B * W, o, gl.ly)) return false;
+  const size_t rs = o->prec == DEER_FP32 ? 4 : 8;
+  const int din = input_is_d(f->kind) ? f->d : f->d_in;
+  size_t p = gl.ly.total;
+  auto take = [&](size_t bytes) { size_t at = p; p = align_up(p + bytes); return at; };
+  gl.lam = take((size_t)B * W * f->d * rs);
+  gl.s = take((size_t)B * W * f->d * rs);
+  gl.g = take((size_t)B * W * f->d * rs);
+  gl.x = has_x ? take((size_t)B * W * din * rs) : p;
+  gl.dx = want_dx ? take((size_t)B * W * din * rs) : p;
+  gl.s0 = take((size_t)B * f->d * rs);
+  gl.carry0 = take((size_t)B * f->d * rs);
+  gl.carry1 = take((size_t)B * f->d * rs);
+  gl.total = p;
   return true;
 }
 
@@ -250,6 +312,7 @@ static deer_status check_common(const deer_dynamics* f, const deer_options* o) {
   if (o->damp < 0 || o->damp > DEER_DAMP_CLIP) return DEER_ERR_INVALID;
   if (o->init < 0 || o->init > DEER_INIT_RANDN) return DEER_ERR_INVALID;
   if (o->history_len < 0 || (o->history_len > 0 && !o->history)) return DEER_ERR_INVALID;
+  if (o->jac_bytes_max < 0) return DEER_ERR_INVALID;
   if (o->prec != DEER_FP64 && o->prec != DEER_FP32 && o->prec != DEER_MIXED_BF16)
     return DEER_ERR_INVALID;
   if (o->prec == DEER_MIXED_BF16 &&
@@ -405,6 +468,12 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   la.damp = o->damp;
   la.dparam = (real)o->damp_param;
   la.tol = tol_r;
+  real* slo = ly.cs ? reinterpret_cast<real*>(ws + ly.slo) : nullptr;
+  if (slo) {
+    // the compensation terms start at zero (the initial guess is a plain float32 state)
+    DEER_CK(cudaMemsetAsync(slo, 0, (size_t)N * d * sizeof(real), st));
+    la.slo = slo;
+  }
 
   CheckArgs ca{B, d_off, d_cf, acc, info, flags,
                reinterpret_cast<int64_t*>(ws + ly.act_seq),
@@ -433,6 +502,8 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     dsa.info = info;
     dsa.reset = o->reset;
     dsa.reset_thr = reset_thr;
+    dsa.slo = slo;
+    dsa.tensor_cores = g_tensor_cores.load();
   } else {
     gsa.bt = bt;
     gsa.d = d;
@@ -463,6 +534,7 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   const bool mixed = o->prec == DEER_MIXED_BF16;
   MixedLinArgs mla;
   MixedScanArgs msa;
+  MixedRcArgs rca{};
   if constexpr (sizeof(real) == 8) {
     if (mixed) {
       const int64_t nseq = f->topology_stride ? B : 1;
@@ -496,6 +568,18 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
       msa.cin = reinterpret_cast<float*>(ws + ly.cin);
       msa.reset = o->reset;
       msa.reset_thr = 1e18;  // the scan and the Jacobians are float32
+      if (ly.mixed_rc) {
+        rca.lin = mla;
+        rca.lin.E = nullptr;
+        rca.lin.b = nullptr;
+        rca.aggP = msa.aggP;
+        rca.aggv = msa.aggv;
+        rca.cin = msa.cin;
+        rca.sbound = reinterpret_cast<double*>(ws + ly.sbound);
+        rca.fastsel = reinterpret_cast<uint8_t*>(ws + ly.fastsel);
+        rca.reset = o->reset;
+        rca.reset_thr = 1e18;
+      }
     }
   }
   const bool fused = !mixed && o->jac == DEER_JAC_FULL && o->damp != DEER_DAMP_ELK &&
@@ -519,6 +603,8 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     fa.reset_thr = reset_thr;
     fa.mode = 0;
     fa.tol = tol_r;
+    fa.slo = slo;
+    fa.sprev_lo = slo ? reinterpret_cast<real*>(ws + ly.sprev_lo) : nullptr;
   }
 
   const bool lookback = use_diag_lookback(o, d);
@@ -579,7 +665,13 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
       if constexpr (sizeof(real) == 8) {
         mla.bt = bt;
         mla.it = it;
-        DEER_CK(launch_lin_ma_mixed(mla, st));
+        if (ly.mixed_rc) {
+          rca.lin.bt = bt;
+          rca.lin.it = it;
+          DEER_CK(launch_mixed_lin_agg(rca, st));
+        } else {
+          DEER_CK(launch_lin_ma_mixed(mla, st));
+        }
       }
     } else {
       DEER_CK(launch_linearize<real>(la, st));
@@ -610,7 +702,12 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
       if (mixed) {
         if constexpr (sizeof(real) == 8) {
           msa.bt = bt;
-          DEER_CK(launch_dense_scan_mixed(msa, st));
+          if (ly.mixed_rc) {
+            rca.lin.bt = bt;
+            DEER_CK(launch_mixed_apply_rc(rca, msa, st));
+          } else {
+            DEER_CK(launch_dense_scan_mixed(msa, st));
+          }
         }
       } else if (o->jac == DEER_JAC_FULL) {
         if (o->damp == DEER_DAMP_ELK && o->damp_param > 0.0) {
@@ -680,6 +777,7 @@ void deer_default_options(deer_options* o) {
   o->chunk = 0;
   o->confirm = 1;
   o->window = 0;
+  o->compensate = 1;
 }
 
 size_t deer_workspace_bytes(const deer_dynamics* f, int64_t batch, int64_t total_steps,
@@ -767,7 +865,16 @@ size_t deer_grad_workspace_bytes(const deer_dynamics* f, int64_t batch, int64_t 
   deer_options o = *opt;
   o.jac = DEER_JAC_FULL;
   o.damp = DEER_DAMP_NONE;
+  o.compensate = 0;
   if (check_common(f, &o) != DEER_OK) return 0;
+  const int64_t W = grad_window_rows(f, batch, T, &o);
+  if (W < T) {
+    // the windowed adjoint (inputs and their gradient included where the kind has them)
+    GradWinLayout gl;
+    const bool has_x = needs_x(f->kind) || input_is_d(f->kind) || f->d_in > 0;
+    if (!grad_win_layout(f, batch, W, &o, has_x, has_x, gl)) return 0;
+    return gl.total;
+  }
   Layout ly;
   if (!make_layout(f, batch, batch * T, &o, ly)) return 0;
   const size_t rs = o.prec == DEER_FP32 ? 4 : 8;
@@ -841,27 +948,24 @@ static deer_status jacobians_at(const deer_dynamics* f, int64_t B, int64_t T, co
   return DEER_OK;
 }
 
+// One adjoint solve over B sequences of T rows whose step Jacobians all fit the workspace:
+// Jacobians at the trajectory, the reverse scan, the parameter VJP (accumulated into dp,
+// which is zeroed first when zero_dp), dl/ds0 (the sensitivity to the state before the
+// first row) and the input gradient.
 template <class real>
-static deer_status grad_impl(const deer_dynamics* f, int64_t B, int64_t T, const void* s0_,
+static deer_status grad_core(const deer_dynamics* f, int64_t B, int64_t T, const void* s0_,
                              const void* x_, const void* sstar_, const void* g_, void* dp_,
-                             void* ds0_, void* dx_, const deer_options* o, void* ws_,
-                             size_t ws_bytes, cudaStream_t st) {
-  const int64_t N = B * T;
-  Layout ly;
-  if (!make_layout(f, B, N, o, ly)) return DEER_ERR_INVALID;
-  const size_t rs = sizeof(real);
-  const size_t lam_off = ly.total;
-  const size_t need = ly.total + align_up((size_t)N * f->d * rs);
-  if (!ws_ || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws_) & 255u))
-    return DEER_ERR_WORKSPACE;
-  char* ws = static_cast<char*>(ws_);
+                             void* ds0_, void* dx_, const Layout& ly, char* ws, size_t lam_off,
+                             bool zero_dp, cudaStream_t st, Flags** flags_out) {
   const int d = f->d;
+  const size_t rs = sizeof(real);
   Batch bt;
   DynView<real> dv;
   Flags* flags = nullptr;
   LinArgs<real> la;
   deer_status js = jacobians_at<real>(f, B, T, s0_, x_, sstar_, ly, ws, st, bt, dv, flags, la);
   if (js != DEER_OK) return js;
+  *flags_out = flags;
   // reverse scan lambda_t = A_{t+1}^T lambda_{t+1} + g_t
   AdjScanArgs<real> sa;
   sa.bt = bt;
@@ -883,11 +987,105 @@ static deer_status grad_impl(const deer_dynamics* f, int64_t B, int64_t T, const
   pa.dparams = static_cast<real*>(dp_);
   pa.pstride = f->kind == DEER_F_BRUSSELATOR_EULER ? 2 : f->n_reactions;
   pa.ds0 = static_cast<real*>(ds0_);
-  if (pa.dparams) DEER_CK(cudaMemsetAsync(pa.dparams, 0, B * pa.pstride * rs, st));
+  if (pa.dparams && zero_dp) DEER_CK(cudaMemsetAsync(pa.dparams, 0, B * pa.pstride * rs, st));
   DEER_CK(launch_param_grad<real>(pa, st));
   if (dx_) {
     InputGradArgs<real> ia{dv, bt, la.s0, la.s, sa.lam, static_cast<real*>(dx_)};
     DEER_CK(launch_input_grad<real>(ia, st));
+  }
+  return DEER_OK;
+}
+
+// rows [t][d] of every sequence b: dst[b * dst_stride + (n - 1) * d + i] += add[b * d + i]
+template <class real>
+__global__ void k_add_last_rows(int64_t B, int d, const real* add, real* dst,
+                                int64_t dst_stride) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= B * d) return;
+  const int64_t b = e / d;
+  dst[b * dst_stride + e % d] += add[e];
+}
+
+template <class real>
+static deer_status grad_impl(const deer_dynamics* f, int64_t B, int64_t T, const void* s0_,
+                             const void* x_, const void* sstar_, const void* g_, void* dp_,
+                             void* ds0_, void* dx_, const deer_options* o, void* ws_,
+                             size_t ws_bytes, cudaStream_t st) {
+  const int64_t N = B * T;
+  const size_t rs = sizeof(real);
+  const int d = f->d;
+  const int64_t W = grad_window_rows(f, B, T, o);
+  Flags* flags = nullptr;
+  if (W >= T) {
+    Layout ly;
+    if (!make_layout(f, B, N, o, ly)) return DEER_ERR_INVALID;
+    const size_t lam_off = ly.total;
+    const size_t need = ly.total + align_up((size_t)N * d * rs);
+    if (!ws_ || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws_) & 255u))
+      return DEER_ERR_WORKSPACE;
+    deer_status c = grad_core<real>(f, B, T, s0_, x_, sstar_, g_, dp_, ds0_, dx_, ly,
+                                    static_cast<char*>(ws_), lam_off, true, st, &flags);
+    if (c != DEER_OK) return c;
+  } else {
+    // Memory-bounded adjoint: the reverse recursion of Eq. bptt runs over time windows of
+    // W rows from the end of the sequences. Each window's Jacobians are formed when it is
+    // reached (never all T of them at once); the adjoint entering a window from the later
+    // one, A_{t_hi}^T lambda_{t_hi}, is the later window's sensitivity to the state before
+    // its first row, and joins the cotangent of the window's last row.
+    GradWinLayout gl;
+    if (!grad_win_layout(f, B, W, o, x_ != nullptr, dx_ != nullptr, gl)) return DEER_ERR_INVALID;
+    if (!ws_ || ws_bytes < gl.total || (reinterpret_cast<uintptr_t>(ws_) & 255u))
+      return DEER_ERR_WORKSPACE;
+    char* ws = static_cast<char*>(ws_);
+    const int din = input_is_d(f->kind) ? f->d : f->d_in;
+    const char* s_all = static_cast<const char*>(sstar_);
+    const char* g_all = static_cast<const char*>(g_);
+    const char* x_all = static_cast<const char*>(x_);
+    char* carry_in = ws + gl.carry0;
+    char* carry_out = ws + gl.carry1;
+    bool first_window = true;
+    for (int64_t t_hi = T; t_hi > 0; t_hi -= W) {
+      const int64_t t_lo = t_hi > W ? t_hi - W : 0;
+      const int64_t Wk = t_hi - t_lo;
+      const size_t row_b = (size_t)d * rs, xrow_b = (size_t)din * rs;
+      // gather the window's rows of every sequence (strided by the full length T)
+      DEER_CK(cudaMemcpy2DAsync(ws + gl.s, Wk * row_b, s_all + t_lo * row_b, T * row_b,
+                                Wk * row_b, B, cudaMemcpyDeviceToDevice, st));
+      DEER_CK(cudaMemcpy2DAsync(ws + gl.g, Wk * row_b, g_all + t_lo * row_b, T * row_b,
+                                Wk * row_b, B, cudaMemcpyDeviceToDevice, st));
+      if (x_all)
+        DEER_CK(cudaMemcpy2DAsync(ws + gl.x, Wk * xrow_b, x_all + t_lo * xrow_b, T * xrow_b,
+                                  Wk * xrow_b, B, cudaMemcpyDeviceToDevice, st));
+      // the state before the window: s_0, or row t_lo - 1 of the trajectory
+      if (t_lo == 0)
+        DEER_CK(cudaMemcpyAsync(ws + gl.s0, s0_, B * row_b, cudaMemcpyDeviceToDevice, st));
+      else
+        DEER_CK(cudaMemcpy2DAsync(ws + gl.s0, row_b, s_all + (t_lo - 1) * row_b, T * row_b,
+                                  row_b, B, cudaMemcpyDeviceToDevice, st));
+      if (!first_window) {
+        k_add_last_rows<real><<<grid_for(B * d, 128), 128, 0, st>>>(
+            B, d, reinterpret_cast<const real*>(carry_in),
+            reinterpret_cast<real*>(ws + gl.g) + (Wk - 1) * d, Wk * d);
+        note_launch();
+        DEER_CK(cudaGetLastError());
+      }
+      deer_status c = grad_core<real>(f, B, Wk, ws + gl.s0, x_all ? ws + gl.x : nullptr,
+                                      ws + gl.s, ws + gl.g, dp_, carry_out,
+                                      dx_ ? ws + gl.dx : nullptr, gl.ly, ws, gl.lam,
+                                      first_window, st, &flags);
+      if (c != DEER_OK) return c;
+      if (dx_)
+        DEER_CK(cudaMemcpy2DAsync(static_cast<char*>(dx_) + t_lo * xrow_b, T * xrow_b,
+                                  ws + gl.dx, Wk * xrow_b, Wk * xrow_b, B,
+                                  cudaMemcpyDeviceToDevice, st));
+      char* tmp = carry_in;
+      carry_in = carry_out;
+      carry_out = tmp;
+      first_window = false;
+    }
+    // the earliest window's sensitivity to its initial state is dl/ds_0
+    if (ds0_)
+      DEER_CK(cudaMemcpyAsync(ds0_, carry_in, B * (size_t)d * rs, cudaMemcpyDeviceToDevice, st));
   }
   Flags hf;
   DEER_CK(cudaMemcpyAsync(&hf, flags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
@@ -977,6 +1175,7 @@ deer_status deer_grad_ex(const deer_dynamics* f, int64_t batch, int64_t T, const
   deer_options o = *opt;
   o.jac = DEER_JAC_FULL;
   o.damp = DEER_DAMP_NONE;
+  o.compensate = 0;
   if (o.prec == DEER_MIXED_BF16) return DEER_ERR_UNSUPPORTED;
   deer_status c = check_common(f, &o);
   if (c != DEER_OK) return c;
@@ -1360,6 +1559,10 @@ deer_status deer_solve_noalloc(const deer_dynamics* f, int64_t batch, int64_t T,
   if (opt->prec == DEER_MIXED_BF16) return DEER_ERR_UNSUPPORTED;
   if (opt->damp == DEER_DAMP_ELK && opt->jac == DEER_JAC_FULL) return DEER_ERR_UNSUPPORTED;
   if (opt->window) return DEER_ERR_UNSUPPORTED;
+  // the fixed scratch solves with a plain float32 state (no compensation terms)
+  deer_options plain = *opt;
+  plain.compensate = 0;
+  opt = &plain;
   if (batch < 0 || T < 0) return DEER_ERR_INVALID;
   if (batch == 0 || T == 0) return DEER_OK;
   if (T > kMaxRows / batch) return DEER_ERR_INVALID;

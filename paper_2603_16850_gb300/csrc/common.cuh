@@ -307,6 +307,38 @@ __device__ __forceinline__ void store_block_rows(real* tile, real* dst, const re
 }
 
 // ---------------------------------------------------------------------------
+// Compensated state (float32 paths of the mass-action kinetics): the state entry is the
+// unevaluated sum hi + lo of two floats, hi the stored float32 value and lo the part below
+// its half ulp (kept in the workspace). Near equilibrium the per-step increments of a
+// trajectory fall below half an ulp of the state and a plain float32 state loses them
+// (the drift then adds up along the conserved directions of the kinetics); the pair keeps
+// them.
+// ---------------------------------------------------------------------------
+// (hi, lo) += d exactly up to the rounding of lo: Knuth's two-sum of hi and d gives the
+// rounded sum and its exact error, which joins lo; a fast two-sum renormalises the pair so
+// that |lo| <= ulp(hi) / 2.
+template <class real>
+__device__ __forceinline__ void cs_add(real& hi, real& lo, real d) {
+  const real s = hi + d;
+  const real bb = s - hi;
+  const real err = (hi - (s - bb)) + (d - bb);
+  const real l = lo + err;
+  const real h2 = s + l;
+  lo = l - (h2 - s);
+  hi = h2;
+}
+
+// Residual r_t = s_t - f(s_{t-1}) of an explicit integrator step f(s) = s + inc(s) from
+// compensated states: (s_t - s_{t-1}) - inc + (lo_t - lo_{t-1}). The difference of the two
+// high parts is exact when they lie within a factor of two (Sterbenz) and otherwise rounds
+// relative to the increment, so the residual is accurate to the rounding of the increment.
+template <class real>
+__device__ __forceinline__ real cs_residual(real hi_t, real lo_t, real hi_p, real lo_p,
+                                            real inc) {
+  return ((hi_t - hi_p) - inc) + (lo_t - lo_p);
+}
+
+// ---------------------------------------------------------------------------
 // Launch bookkeeping (counted for deer_kernel_launch_count).
 // ---------------------------------------------------------------------------
 void note_launch(int n = 1);

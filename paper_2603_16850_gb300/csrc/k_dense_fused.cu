@@ -305,7 +305,7 @@ __device__ __forceinline__ void ldrow_ro(const real* __restrict__ p, real (&v)[D
 // so far more warps are resident to hide latency. The pending (A_t, b_t) of a chunk are
 // stored chunk-major: A at ((c L + t) d + i) d + j, b at (c L + t) d + i.
 // ---------------------------------------------------------------------------
-template <class real, int D, bool RK4, int MODE>
+template <class real, int D, bool RK4, int MODE, bool CS>
 __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real> a) {
   constexpr int GPB = kFusedBlock / D;                  // chunks per block
   constexpr int E = D * D;
@@ -349,10 +349,17 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
 #pragma unroll
       for (int m = 0; m < D; ++m) ldrow_ro<real, D>(Brow + m * E, Breg[m]);
     }
-    real prev;
-    if (seq_first) prev = a.s0[seq * D + i];
-    else if (MODE == 0 || first) prev = a.s[(r0 - 1) * D + i];
-    else prev = a.sprev[c * D + i];
+    // CS: the state is the pair (s, slo) (compensated float32 state, see cs_add)
+    real prev, prev_lo = real(0);
+    if (seq_first) {
+      prev = a.s0[seq * D + i];
+    } else if (MODE == 0 || first) {
+      prev = a.s[(r0 - 1) * D + i];
+      if constexpr (CS) prev_lo = a.slo[(r0 - 1) * D + i];
+    } else {
+      prev = a.sprev[c * D + i];
+      if constexpr (CS) prev_lo = a.sprev_lo[c * D + i];
+    }
     real dl = MODE == 1 ? a.cin[c * D + i] : real(0);
     real v = real(0);
 #pragma unroll
@@ -364,6 +371,8 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
       real* Arow = a.Ai + pr * E + i * D;
       real* bp = a.bi + pr * D + i;
       real sn = a.s[row * D + i];
+      real sn_lo = real(0);
+      if constexpr (CS) sn_lo = a.slo[row * D + i];
       if constexpr (MODE == 1) {
         // pending scan step: Delta_t = A_t Delta_{t-1} + b_t, s_t += Delta_t
         real Ar[D];
@@ -372,9 +381,18 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
 #pragma unroll
         for (int j = 0; j < D; ++j) nd += Ar[j] * __shfl_sync(gm, dl, j, D);
         dl = nd;
-        real x = sn + nd;
-        if (a.reset && !(x <= a.reset_thr && x >= -a.reset_thr)) x = real(0);
-        sn = x;
+        if constexpr (CS) {
+          cs_add(sn, sn_lo, nd);
+          if (a.reset && !(sn <= a.reset_thr && sn >= -a.reset_thr)) {
+            sn = real(0);
+            sn_lo = real(0);
+          }
+          a.slo[row * D + i] = sn_lo;
+        } else {
+          real x = sn + nd;
+          if (a.reset && !(x <= a.reset_thr && x >= -a.reset_thr)) x = real(0);
+          sn = x;
+        }
         a.s[row * D + i] = sn;
       }
       // linearise at the new state of the previous row
@@ -427,8 +445,13 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
         const real cs = stage == 2 ? h : real(0.5) * h;
         st = prev + cs * g;
       }
-      const real F = prev + hw * accg;
-      const real r = sn - F;
+      real r;
+      if constexpr (CS) {
+        r = cs_residual(sn, sn_lo, prev, prev_lo, hw * accg);
+      } else {
+        const real F = prev + hw * accg;
+        r = sn - F;
+      }
       const real sabs = rabs(sn);
       const real sr = rabs(r) / (sabs > real(1) ? sabs : real(1));
       mx = (sr > mx || sr != sr) ? sr : mx;
@@ -459,6 +482,7 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
         __syncwarp(gm);
       }
       prev = sn;
+      prev_lo = sn_lo;
     }
     real pf[D];
     ldrow_p<real, D>(Px + i * RS, pf);
@@ -552,7 +576,7 @@ __global__ void __launch_bounds__(128) k_dense_fused_carry(FusedArgs<real> a) {
 // Lane-per-species carry pass (d = 4, 8): d lanes per sequence, lane i owns row i of every
 // chunk aggregate and entry i of the carried Delta; the other entries arrive by shuffles.
 // The next chunk's aggregate row is loaded before the current one is applied.
-template <class real, int D>
+template <class real, int D, bool CS>
 __global__ void __launch_bounds__(128) k_fused_carry_lps(FusedArgs<real> a) {
   constexpr int E = D * D;
   constexpr int GPB = 128 / D;
@@ -568,12 +592,14 @@ __global__ void __launch_bounds__(128) k_fused_carry_lps(FusedArgs<real> a) {
   const int64_t cf = a.bt.chunk_first[seq], c0 = win_first(a.bt, seq);
   const int64_t c1 = a.bt.chunk_first[seq + 1];
   const int64_t base = a.bt.offsets[seq];
-  real Pr[K][D], vr[K], sr[K];
+  real Pr[K][D], vr[K], sr[K], sl[CS ? K : 1];
   auto fetch = [&](int slot, int64_t c) {
     if (c < c1) {
       ldrow_p<real, D>(a.aggP + c * E + i * D, Pr[slot]);
       vr[slot] = a.aggv[c * D + i];
-      sr[slot] = c > c0 ? a.s[(base + ((c - cf) << a.bt.log2L) - 1) * D + i] : real(0);
+      const int64_t rb = base + ((c - cf) << a.bt.log2L) - 1;
+      sr[slot] = c > c0 ? a.s[rb * D + i] : real(0);
+      if constexpr (CS) sl[slot] = c > c0 ? a.slo[rb * D + i] : real(0);
     }
   };
 #pragma unroll
@@ -588,13 +614,26 @@ __global__ void __launch_bounds__(128) k_fused_carry_lps(FusedArgs<real> a) {
 #pragma unroll
         for (int j = 0; j < D; ++j) Pc[j] = Pr[slot][j];
         const real vc = vr[slot], so = sr[slot];
+        real so_lo = real(0);
+        if constexpr (CS) so_lo = sl[slot];
         fetch(slot, c + K);
         a.cin[c * D + i] = x;
         real nx = vc;
         if (c > c0) {
-          real y = so + x;
-          if (a.reset && !(y <= a.reset_thr && y >= -a.reset_thr)) y = real(0);
-          a.sprev[c * D + i] = y;
+          if constexpr (CS) {
+            real y = so, ylo = so_lo;
+            cs_add(y, ylo, x);
+            if (a.reset && !(y <= a.reset_thr && y >= -a.reset_thr)) {
+              y = real(0);
+              ylo = real(0);
+            }
+            a.sprev[c * D + i] = y;
+            a.sprev_lo[c * D + i] = ylo;
+          } else {
+            real y = so + x;
+            if (a.reset && !(y <= a.reset_thr && y >= -a.reset_thr)) y = real(0);
+            a.sprev[c * D + i] = y;
+          }
 #pragma unroll
           for (int j = 0; j < D; ++j) nx += Pc[j] * __shfl_sync(gm, x, j, D);
         }
@@ -610,8 +649,13 @@ static void fused_launch(const FusedArgs<real>& a, cudaStream_t st) {
   if constexpr (MA && (D == 4 || D == 8)) {
     constexpr bool RK4 = KIND == DEER_F_MASSACTION_RK4;
     const unsigned g = grid_for(a.bt.act_chunks, kFusedBlock / D);
-    if (a.mode == 0) k_fused_ma_lps<real, D, RK4, 0><<<g, kFusedBlock, 0, st>>>(a);
-    else k_fused_ma_lps<real, D, RK4, 1><<<g, kFusedBlock, 0, st>>>(a);
+    if (a.slo) {
+      if (a.mode == 0) k_fused_ma_lps<real, D, RK4, 0, true><<<g, kFusedBlock, 0, st>>>(a);
+      else k_fused_ma_lps<real, D, RK4, 1, true><<<g, kFusedBlock, 0, st>>>(a);
+    } else {
+      if (a.mode == 0) k_fused_ma_lps<real, D, RK4, 0, false><<<g, kFusedBlock, 0, st>>>(a);
+      else k_fused_ma_lps<real, D, RK4, 1, false><<<g, kFusedBlock, 0, st>>>(a);
+    }
   } else {
     const unsigned g = grid_for(a.bt.act_chunks, kFusedBlock);
     if (a.mode == 0) k_dense_fused<real, D, KIND, 0><<<g, kFusedBlock, 0, st>>>(a);
@@ -654,8 +698,13 @@ cudaError_t launch_dense_fused_carry(const FusedArgs<real>& a, cudaStream_t st) 
   if (ma && (a.dv.d == 4 || a.dv.d == 8)) {
     // same kernels as the fused pass selects (lane-per-species layout of the aggregates is
     // row-major either way)
-    if (a.dv.d == 4) k_fused_carry_lps<real, 4><<<grid_for(a.bt.n_act, 32), 128, 0, st>>>(a);
-    else k_fused_carry_lps<real, 8><<<grid_for(a.bt.n_act, 16), 128, 0, st>>>(a);
+    if (a.slo) {
+      if (a.dv.d == 4) k_fused_carry_lps<real, 4, true><<<grid_for(a.bt.n_act, 32), 128, 0, st>>>(a);
+      else k_fused_carry_lps<real, 8, true><<<grid_for(a.bt.n_act, 16), 128, 0, st>>>(a);
+    } else {
+      if (a.dv.d == 4) k_fused_carry_lps<real, 4, false><<<grid_for(a.bt.n_act, 32), 128, 0, st>>>(a);
+      else k_fused_carry_lps<real, 8, false><<<grid_for(a.bt.n_act, 16), 128, 0, st>>>(a);
+    }
     note_launch();
     return cudaGetLastError();
   }

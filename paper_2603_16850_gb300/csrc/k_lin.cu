@@ -555,8 +555,10 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
       sq = real(0);
       key = 0ull;
     }
-    const real s_prev = row == __ldg(a.bt.offsets + seq) ? a.s0[seq * D + lane]
-                                                        : a.s[(row - 1) * D + lane];
+    const bool row_first = row == __ldg(a.bt.offsets + seq);
+    const real s_prev = row_first ? a.s0[seq * D + lane] : a.s[(row - 1) * D + lane];
+    // compensated state (float32 path): the parts below the half ulp of s_{t-1} and s_t
+    const real p_lo = (a.slo && !row_first) ? a.slo[(row - 1) * D + lane] : real(0);
     const real* kk = a.dv.params + seq * a.dv.pstride;
     const int4* tt = reinterpret_cast<const int4*>(a.dv.topo + seq * a.dv.tstride);
     const int R = a.dv.R;
@@ -643,7 +645,8 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
     const real F = s_prev + hw * acc;
     {
       const real sc = a.s[row * D + lane];
-      const real rr = sc - F;
+      const real rr = a.slo ? cs_residual(sc, a.slo[row * D + lane], s_prev, p_lo, hw * acc)
+                            : sc - F;
       const real sabs = rabs(sc);
       real m1 = rabs(rr) / (sabs > real(1) ? sabs : real(1));
       if (rr != rr) m1 = rr;  // keep NaN

@@ -87,15 +87,19 @@ __device__ __forceinline__ void ld_row4(const float* p, float (&v)[D]) {
   }
 }
 
+// The row's outputs go to Eo (its D x D block of E, row-major bf16) and bo (its entry
+// of b = -r): in global memory for the materialised path, in shared memory for the
+// recomputing one. sc is the row's own state s_t (read by the caller).
 template <class V, int D, bool RK4, int RPL>
 __device__ __forceinline__ void mixed_row(const MixedLinArgs& a, bool valid, int64_t row,
-                                          int lane, unsigned gm, double s_prev_d,
+                                          int lane, unsigned gm, double s_prev_d, double sc,
                                           const int4 (&q)[RPL], const double (&kd)[RPL],
                                           const float (&kf)[RPL], int R, const int4* tt,
                                           const int32_t* ae, int e0, int e1,
                                           float (*sG)[D + 4], float (*sK)[D + 4], V* sRate,
                                           float* sD1, float* sD2, float& mx, float& sq,
-                                          int64_t seq, unsigned long long& key) {
+                                          int64_t seq, unsigned long long& key,
+                                          __nv_bfloat16* Eo, float* bo) {
   constexpr bool F64 = sizeof(V) == 8;
   const V s_prev = F64 ? (V)s_prev_d : (V)d2f_trunc(s_prev_d);
   const V h = F64 ? (V)a.dv.dt : (V)a.dt_f;
@@ -170,7 +174,6 @@ __device__ __forceinline__ void mixed_row(const MixedLinArgs& a, bool valid, int
   const V hw = RK4 ? h / V(6) : h;
   const V F = s_prev + hw * acc;
   if (valid) {
-    const double sc = a.s[row * D + lane];
     const float scf = d2f_trunc(sc);
     float rf;
     if constexpr (F64) rf = d2f_trunc(sc - (double)F);
@@ -178,12 +181,12 @@ __device__ __forceinline__ void mixed_row(const MixedLinArgs& a, bool valid, int
     const float sabs = fabsf(scf);
     float m = fabsf(rf) / (sabs > 1.f ? sabs : 1.f);
     if (!F64 && !(m != m)) m = m > kMixedFloor ? m : kMixedFloor;
-    mx = m;
-    sq = rf * rf;
-    if (!(m <= a.tol_f)) key = bad_key(true, row - __ldg(a.bt.offsets + seq));
+    mx = nanmaxf(mx, m);
+    sq += rf * rf;
+    if (!(m <= a.tol_f) && key == 0ull) key = bad_key(true, row - __ldg(a.bt.offsets + seq));
     const float scale = a.scale_f;
     const float hwf = RK4 ? hf / 6.f : hf;
-    __nv_bfloat16* Eo = a.E + row * (int64_t)(D * D) + lane * D;
+    Eo += lane * D;
     // E = A - I with A = I + hw Kacc (scaled by (1 - k) under scale-ELK: E = s A - I)
 #pragma unroll
     for (int j = 0; j < D; j += 2) {
@@ -191,7 +194,7 @@ __device__ __forceinline__ void mixed_row(const MixedLinArgs& a, bool valid, int
       const float x1 = scale * hwf * Kacc[j + 1] + (j + 1 == lane ? scale - 1.f : 0.f);
       *reinterpret_cast<__nv_bfloat162*>(Eo + j) = __floats2bfloat162_rn(x0, x1);
     }
-    a.b[row * D + lane] = -rf;
+    bo[lane] = -rf;
   }
 }
 
@@ -235,15 +238,18 @@ __global__ void __launch_bounds__(128) k_lin_ma_mixed(MixedLinArgs a) {
   const bool fast = !valid || a.it == 0 || a.info[seq].max_resid > kMixedFastAbove;
   float mx = 0.f, sq = 0.f;
   unsigned long long key = 0ull;  // first failing row (sliding window)
+  const double sc = valid ? a.s[row * D + lane] : 0.0;
+  __nv_bfloat16* Eo = a.E + (valid ? row : 0) * (int64_t)(D * D);
+  float* bo = a.b + (valid ? row : 0) * D;
   if (fast)
-    mixed_row<float, D, RK4, RPL>(a, valid, row, lane, gm, s_prev, q, kd, kf, R, tt, ae, e0,
-                                  e1, sG[grp], sK[grp],
+    mixed_row<float, D, RK4, RPL>(a, valid, row, lane, gm, s_prev, sc, q, kd, kf, R, tt, ae,
+                                  e0, e1, sG[grp], sK[grp],
                                   reinterpret_cast<float*>(sRate[grp]), sD1[grp], sD2[grp],
-                                  mx, sq, seq, key);
+                                  mx, sq, seq, key, Eo, bo);
   else
-    mixed_row<double, D, RK4, RPL>(a, valid, row, lane, gm, s_prev, q, kd, kf, R, tt, ae, e0,
-                                   e1, sG[grp], sK[grp], sRate[grp], sD1[grp], sD2[grp], mx,
-                                   sq, seq, key);
+    mixed_row<double, D, RK4, RPL>(a, valid, row, lane, gm, s_prev, sc, q, kd, kf, R, tt, ae,
+                                   e0, e1, sG[grp], sK[grp], sRate[grp], sD1[grp], sD2[grp],
+                                   mx, sq, seq, key, Eo, bo);
   acc_resid_f(a.acc, seq, valid, mx, sq, key);
 }
 
@@ -459,6 +465,226 @@ __global__ void __launch_bounds__(128) k_mixed_apply_tc16(MixedScanArgs a) {
       *sp = v;
     }
   }
+}
+
+// ---- d = 16 without stored Jacobians: one warp per chunk ----------------------------
+// The two half-warps linearise rows t and t + 1 of the chunk (16 lanes per row, as in
+// k_lin_ma_mixed) into shared memory; the whole warp then folds them into the chunk
+// aggregate on the fragments of k_mixed_chunk_tc16 (pass 1), or applies the correction
+// to them (pass 2). Shared memory per warp: the two rows' linearisation buffers and their
+// E (bf16) and b.
+constexpr int kRcWarps = 4;
+constexpr int kRcRmax = 64;
+
+struct RcSmem {
+  float G[2][16][20];
+  float K[2][17][20];
+  double rate[2][kRcRmax];
+  float d1[2][kRcRmax], d2[2][kRcRmax];
+  __nv_bfloat16 E[2][256];
+  float b[2][16];
+  double old[16];  // pass 2: old state of the previous pair's second row
+};
+
+// per-lane network data of the sequence (reactions r = k * 16 + lane)
+struct RcNet {
+  int4 q[kRcRmax / 16];
+  double kd[kRcRmax / 16];
+  float kf[kRcRmax / 16];
+  const int4* tt;
+  const int32_t* ae;
+  int e0, e1, R;
+};
+
+__device__ __forceinline__ void rc_net(const MixedLinArgs& a, int64_t seq, int lane,
+                                       RcNet& n) {
+  const double* kk = a.dv.params + seq * a.dv.pstride;
+  n.tt = reinterpret_cast<const int4*>(a.dv.topo + seq * a.dv.tstride);
+  const int32_t* aoff = a.adj_off + (a.adj_stride ? seq : 0) * 17;
+  n.ae = a.adj_e + (a.adj_stride ? seq : 0) * a.adj_stride;
+  n.e0 = __ldg(aoff + lane);
+  n.e1 = __ldg(aoff + lane + 1);
+  n.R = a.dv.R < kRcRmax ? a.dv.R : kRcRmax;
+#pragma unroll
+  for (int k = 0; k < kRcRmax / 16; ++k) {
+    const int r = k * 16 + lane;
+    n.q[k] = __ldg(n.tt + (r < n.R ? r : 0));
+    n.kd[k] = r < n.R ? __ldg(kk + r) : 0.0;
+    n.kf[k] = d2f_trunc(n.kd[k]);
+  }
+}
+
+// linearise one row into the half-warp's shared buffers (E, b): value path per `fast`
+template <bool RK4>
+__device__ __forceinline__ void rc_row(const MixedLinArgs& a, bool fast, bool valid,
+                                       int64_t row, int half, int lane, unsigned gm,
+                                       double sp, double sc, const RcNet& n, RcSmem& S,
+                                       float& mx, float& sq, int64_t seq,
+                                       unsigned long long& key) {
+  if (fast)
+    mixed_row<float, 16, RK4, kRcRmax / 16>(
+        a, valid, row, lane, gm, sp, sc, n.q, n.kd, n.kf, n.R, n.tt, n.ae, n.e0, n.e1,
+        S.G[half], S.K[half], reinterpret_cast<float*>(S.rate[half]), S.d1[half],
+        S.d2[half], mx, sq, seq, key, S.E[half], S.b[half]);
+  else
+    mixed_row<double, 16, RK4, kRcRmax / 16>(
+        a, valid, row, lane, gm, sp, sc, n.q, n.kd, n.kf, n.R, n.tt, n.ae, n.e0, n.e1,
+        S.G[half], S.K[half], S.rate[half], S.d1[half], S.d2[half], mx, sq, seq, key,
+        S.E[half], S.b[half]);
+}
+
+// the lane's four words of E and its two entries of b, in fragment positions
+__device__ __forceinline__ void rc_frag(const RcSmem& S, int h, int g, int t, uint32_t& e0,
+                                        uint32_t& e1, uint32_t& e2, uint32_t& e3,
+                                        float& b_lo, float& b_hi) {
+  const uint32_t* Ew = reinterpret_cast<const uint32_t*>(S.E[h]);
+  e0 = Ew[g * 8 + t];
+  e1 = Ew[g * 8 + t + 4];
+  e2 = Ew[(g + 8) * 8 + t];
+  e3 = Ew[(g + 8) * 8 + t + 4];
+  b_lo = S.b[h][g];
+  b_hi = S.b[h][g + 8];
+}
+
+template <bool RK4>
+__global__ void __launch_bounds__(32 * kRcWarps) k_mixed_lin_agg16(MixedRcArgs r) {
+  __shared__ __align__(16) RcSmem smem[kRcWarps];
+  const MixedLinArgs& a = r.lin;
+  const int warp = threadIdx.x >> 5, l32 = threadIdx.x & 31;
+  const int half = l32 >> 4, lane = l32 & 15, g = l32 >> 2, tq = l32 & 3;
+  const unsigned gm = gmask_mixed<16>();
+  const int64_t ac = blockIdx.x * (int64_t)kRcWarps + warp;
+  if (ac >= a.bt.act_chunks) return;  // whole warps
+  RcSmem& S = smem[warp];
+  int64_t seq, c, r0;
+  int n;
+  act_chunk(a.bt, ac, seq, c, r0, n);
+  const int64_t base = __ldg(a.bt.offsets + seq);
+  RcNet net;
+  rc_net(a, seq, lane, net);
+  const bool fast = a.it == 0 || a.info[seq].max_resid > kMixedFastAbove;
+  if (l32 == 0) r.fastsel[seq] = fast ? 1 : 0;  // the same value from every chunk
+  // the old state before the chunk, kept for the second pass (whose neighbouring chunk may
+  // already have updated it)
+  const double prev0 = r0 == base ? a.s0[seq * 16 + lane] : a.s[(r0 - 1) * 16 + lane];
+  if (half == 0 && r0 > base) r.sbound[c * 16 + lane] = prev0;
+  const bool need_P = c != win_first(a.bt, seq);
+  float p0[4] = {g == 2 * tq ? 1.f : 0.f, g == 2 * tq + 1 ? 1.f : 0.f, 0.f, 0.f};
+  float p1[4] = {0.f, 0.f, g == 2 * tq ? 1.f : 0.f, g == 2 * tq + 1 ? 1.f : 0.f};
+  float lo = 0.f, hi = 0.f, q[4] = {0.f, 0.f, 0.f, 0.f};
+  float mx = 0.f, sq = 0.f;
+  unsigned long long key = 0ull;
+  for (int t = 0; t < n; t += 2) {
+    const int tr = t + half;
+    const bool v = tr < n;
+    const int64_t row = r0 + (v ? tr : 0);
+    const double sp = tr == 0 ? prev0 : (v ? a.s[(row - 1) * 16 + lane] : prev0);
+    const double sc = v ? a.s[row * 16 + lane] : prev0;
+    rc_row<RK4>(a, fast, v, row, half, lane, gm, sp, sc, net, S, mx, sq, seq, key);
+    __syncwarp();
+    for (int h = 0; h < 2 && t + h < n; ++h) {
+      uint32_t e0, e1, e2, e3;
+      float b_lo, b_hi;
+      rc_frag(S, h, g, tq, e0, e1, e2, e3, b_lo, b_hi);
+      if (need_P) {
+        const uint32_t A[4] = {pack_bf16x2(p0[0], p0[1]), pack_bf16x2(p0[2], p0[3]),
+                               pack_bf16x2(p1[0], p1[1]), pack_bf16x2(p1[2], p1[3])};
+        mma_bf16_16816(p0, A, e0, e1);
+        mma_bf16_16816(p1, A, e2, e3);
+      }
+      frag_matvec16(e0, e1, e2, e3, b_lo, b_hi, lo, hi, q, tq);
+    }
+    __syncwarp();
+  }
+  float* Po = r.aggP + c * 256;
+  Po[(2 * tq) * 16 + g] = p0[0];
+  Po[(2 * tq + 1) * 16 + g] = p0[1];
+  Po[(2 * tq) * 16 + g + 8] = p0[2];
+  Po[(2 * tq + 1) * 16 + g + 8] = p0[3];
+  Po[(2 * tq + 8) * 16 + g] = p1[0];
+  Po[(2 * tq + 9) * 16 + g] = p1[1];
+  Po[(2 * tq + 8) * 16 + g + 8] = p1[2];
+  Po[(2 * tq + 9) * 16 + g + 8] = p1[3];
+  if (tq == 0) {
+    r.aggv[c * 16 + g] = lo;
+    r.aggv[c * 16 + g + 8] = hi;
+  }
+  acc_resid_f(a.acc, seq, true, mx, sq, key);
+}
+
+template <bool RK4>
+__global__ void __launch_bounds__(32 * kRcWarps) k_mixed_apply_rc16(MixedRcArgs r) {
+  __shared__ __align__(16) RcSmem smem[kRcWarps];
+  const MixedLinArgs& a = r.lin;
+  const int warp = threadIdx.x >> 5, l32 = threadIdx.x & 31;
+  const int half = l32 >> 4, lane = l32 & 15, g = l32 >> 2, tq = l32 & 3;
+  const unsigned gm = gmask_mixed<16>();
+  const int64_t ac = blockIdx.x * (int64_t)kRcWarps + warp;
+  if (ac >= a.bt.act_chunks) return;  // whole warps
+  RcSmem& S = smem[warp];
+  int64_t seq, c, r0;
+  int n;
+  act_chunk(a.bt, ac, seq, c, r0, n);
+  const int64_t base = __ldg(a.bt.offsets + seq);
+  RcNet net;
+  rc_net(a, seq, lane, net);
+  const bool fast = r.fastsel[seq] != 0;
+  const double prev0 = r0 == base ? a.s0[seq * 16 + lane] : r.sbound[c * 16 + lane];
+  const float* ci = r.cin + c * 16;
+  float lo = ci[g], hi = ci[g + 8];
+  float q[4] = {ci[2 * tq], ci[2 * tq + 1], ci[2 * tq + 8], ci[2 * tq + 9]};
+  float mx = 0.f, sq = 0.f;  // recomputed statistics, not reported again
+  unsigned long long key = 0ull;
+  double* s = const_cast<double*>(a.s);
+  for (int t = 0; t < n; t += 2) {
+    const int tr = t + half;
+    const bool v = tr < n;
+    const int64_t row = r0 + (v ? tr : 0);
+    // old s_{t-1}: the chunk's saved boundary, the previous pair's second row (saved
+    // before it was updated), or row t of this pair (not updated yet)
+    double sp = prev0;
+    if (tr > 0) sp = half == 0 ? S.old[lane] : (v ? s[(row - 1) * 16 + lane] : prev0);
+    const double sc = v ? s[row * 16 + lane] : prev0;
+    rc_row<RK4>(a, fast, v, row, half, lane, gm, sp, sc, net, S, mx, sq, seq, key);
+    __syncwarp();
+    if (half == 1 && v) S.old[lane] = sc;
+    __syncwarp();
+    for (int h = 0; h < 2 && t + h < n; ++h) {
+      uint32_t e0, e1, e2, e3;
+      float b_lo, b_hi;
+      rc_frag(S, h, g, tq, e0, e1, e2, e3, b_lo, b_hi);
+      frag_matvec16(e0, e1, e2, e3, b_lo, b_hi, lo, hi, q, tq);
+      if (tq < 2) {
+        double* sp2 = s + (r0 + t + h) * 16 + g + 8 * tq;
+        double nv = *sp2 + (double)(tq == 0 ? lo : hi);
+        if (r.reset && overflowed(nv)) nv = 0.0;
+        *sp2 = nv;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_mixed_lin_agg(const MixedRcArgs& a, cudaStream_t st) {
+  if (a.lin.bt.act_chunks == 0) return cudaSuccess;
+  if (a.lin.dv.d != 16) return cudaErrorInvalidValue;
+  const unsigned g = grid_for(a.lin.bt.act_chunks, kRcWarps);
+  if (a.lin.dv.kind == DEER_F_MASSACTION_RK4) k_mixed_lin_agg16<true><<<g, 32 * kRcWarps, 0, st>>>(a);
+  else k_mixed_lin_agg16<false><<<g, 32 * kRcWarps, 0, st>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_apply_rc(const MixedRcArgs& a, const MixedScanArgs& carry,
+                                  cudaStream_t st) {
+  if (a.lin.bt.act_chunks == 0) return cudaSuccess;
+  if (a.lin.dv.d != 16) return cudaErrorInvalidValue;
+  k_mixed_carry<16><<<grid_for(carry.bt.n_act, 128 / 16), 128, 0, st>>>(carry);
+  const unsigned g = grid_for(a.lin.bt.act_chunks, kRcWarps);
+  if (a.lin.dv.kind == DEER_F_MASSACTION_RK4) k_mixed_apply_rc16<true><<<g, 32 * kRcWarps, 0, st>>>(a);
+  else k_mixed_apply_rc16<false><<<g, 32 * kRcWarps, 0, st>>>(a);
+  note_launch(2);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_lin_ma_mixed(const MixedLinArgs& a, cudaStream_t st) {

@@ -950,6 +950,153 @@ __global__ void __launch_bounds__(128) k_dense_chunk_ring4(DenseScanArgs<real> a
   }
 }
 
+// Chunk pass, d = 32, float32, on the tensor cores. P <- A_t P acts on every column of P
+// independently, so the chunk product is carried transposed, P^T <- P^T A_t^T, and split
+// by rows of P^T (columns of P) over two warps: warp w owns rows 16w .. 16w + 15 of P^T and
+// never exchanges data with the other warp. Each row step is a 16 x 32 x 32 product per
+// warp as warp-level tf32 MMAs (m16n8k8, float32 accumulation) with the three-term split
+// x = x_hi + x_lo (x_hi = x rounded to tf32): A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi, a
+// relative error of about 2^-21, so the aggregates keep float32 accuracy. The A operand is
+// the previous accumulator re-laid by shuffles within each quad of lanes (the accumulator
+// holds columns 2t, 2t+1 of a row where the operand wants t, t + 4); the B operand
+// A_t^T[k][n] = A_t[n][k] is read from the row-major staged A_t (rows padded to 36 floats:
+// the 32 lanes' words fall in distinct banks). The vector part v <- A_t v + b_t is formed
+// by lane i (row i) of warp 0. Rows are staged through the same cp.async ring as
+// k_dense_chunk_ring4.
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32_1688(float (&d)[4], uint32_t a0, uint32_t a1,
+                                              uint32_t a2, uint32_t a3, uint32_t b0,
+                                              uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(64) k_dense_chunk_mma32(DenseScanArgs<float> a) {
+  constexpr int D = 32;
+  constexpr int K = ring_depth<float>();
+  constexpr int RS = D + 4;
+  constexpr int PIECES = D * D / 4;  // 16-byte pieces of one A_t
+  __shared__ __align__(16) float sA[K][D][RS];
+  __shared__ __align__(16) float sB[K][D];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, tq = lane & 3;
+  const int64_t ac = blockIdx.x;
+  if (ac >= a.bt.act_chunks) return;  // uniform over the block
+  int64_t seq, c, r0;
+  int n;
+  act_chunk(a.bt, ac, seq, c, r0, n);
+  const bool need_P = c != win_first(a.bt, seq);
+  const float* A0 = a.A + r0 * (int64_t)(D * D);
+  const float* b0 = a.b + r0 * D;
+  auto issue = [&](int slot, int t) {
+    if (t < n) {
+      const float* src = A0 + t * (int64_t)(D * D);
+      for (int p = tid; p < PIECES; p += 64)
+        cp_async16(&sA[slot][p / (D / 4)][(p % (D / 4)) * 4], src + p * 4);
+      if (tid < D / 4) cp_async16(&sB[slot][tid * 4], b0 + t * D + tid * 4);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int s = 0; s < K; ++s) issue(s, s);
+  // accumulator of this warp's 16 rows of P^T: n-tile j holds P^T[m][8j + 2tq (+1)] for
+  // m = 16 warp + g (entries 0, 1) and m + 8 (entries 2, 3); P^T starts as I
+  float acc[4][4];
+  const int m0 = 16 * warp + g;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int n0 = 8 * j + 2 * tq;
+    acc[j][0] = m0 == n0 ? 1.f : 0.f;
+    acc[j][1] = m0 == n0 + 1 ? 1.f : 0.f;
+    acc[j][2] = m0 + 8 == n0 ? 1.f : 0.f;
+    acc[j][3] = m0 + 8 == n0 + 1 ? 1.f : 0.f;
+  }
+  float v = 0.f;
+  const int qsrc = (lane & ~3) + (tq >> 1);  // quad lane holding column tq of a tile
+  const bool odd = tq & 1;
+  for (int t0 = 0; t0 < n; t0 += K) {
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      const int t = t0 + s;
+      cp_async_wait<K - 1>();
+      __syncthreads();  // slot s complete for the block
+      if (t < n) {
+        if (warp == 0) {
+          float nv = sB[s][lane];
+#pragma unroll
+          for (int k = 0; k < D; k += 4) {
+            const float4 q = *reinterpret_cast<const float4*>(&sA[s][lane][k]);
+            nv += q.x * __shfl_sync(0xffffffffu, v, k) + q.y * __shfl_sync(0xffffffffu, v, k + 1) +
+                  q.z * __shfl_sync(0xffffffffu, v, k + 2) + q.w * __shfl_sync(0xffffffffu, v, k + 3);
+          }
+          v = nv;
+        }
+        if (need_P) {
+          // A operand (P^T rows, K = columns of P^T) from the accumulator, split
+          uint32_t ah[4][4], al[4][4];
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const float x0 = __shfl_sync(0xffffffffu, acc[kk][0], qsrc);
+            const float x1 = __shfl_sync(0xffffffffu, acc[kk][1], qsrc);
+            const float x2 = __shfl_sync(0xffffffffu, acc[kk][2], qsrc);
+            const float x3 = __shfl_sync(0xffffffffu, acc[kk][3], qsrc);
+            const float y0 = __shfl_sync(0xffffffffu, acc[kk][0], qsrc + 2);
+            const float y1 = __shfl_sync(0xffffffffu, acc[kk][1], qsrc + 2);
+            const float y2 = __shfl_sync(0xffffffffu, acc[kk][2], qsrc + 2);
+            const float y3 = __shfl_sync(0xffffffffu, acc[kk][3], qsrc + 2);
+            const float av[4] = {odd ? x1 : x0, odd ? x3 : x2, odd ? y1 : y0, odd ? y3 : y2};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              ah[kk][e] = tf32_rna(av[e]);
+              al[kk][e] = tf32_rna(av[e] - __uint_as_float(ah[kk][e]));
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float dn[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              // B[k][n] = A_t[n][k]: n = 8j + g, k = 8kk + tq (+ 4)
+              const float bx0 = sA[s][8 * j + g][8 * kk + tq];
+              const float bx1 = sA[s][8 * j + g][8 * kk + tq + 4];
+              const uint32_t bh0 = tf32_rna(bx0), bh1 = tf32_rna(bx1);
+              const uint32_t bl0 = tf32_rna(bx0 - __uint_as_float(bh0));
+              const uint32_t bl1 = tf32_rna(bx1 - __uint_as_float(bh1));
+              mma_tf32_1688(dn, al[kk][0], al[kk][1], al[kk][2], al[kk][3], bh0, bh1);
+              mma_tf32_1688(dn, ah[kk][0], ah[kk][1], ah[kk][2], ah[kk][3], bl0, bl1);
+              mma_tf32_1688(dn, ah[kk][0], ah[kk][1], ah[kk][2], ah[kk][3], bh0, bh1);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[j][e] = dn[e];
+          }
+        }
+      }
+      __syncthreads();  // every read of slot s done before it is refilled
+      issue(s, t + K);
+    }
+  }
+  cp_async_wait<0>();
+  // P[i][j] = P^T[j][i]
+  float* Po = a.aggP + c * (int64_t)(D * D);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int n0 = 8 * j + 2 * tq;
+    Po[n0 * D + m0] = acc[j][0];
+    Po[(n0 + 1) * D + m0] = acc[j][1];
+    Po[n0 * D + m0 + 8] = acc[j][2];
+    Po[(n0 + 1) * D + m0 + 8] = acc[j][3];
+  }
+  if (warp == 0) a.aggv[c * D + lane] = v;
+}
+
 // Carry pass: x_c = P_c x_{c-1} + v_c along each active sequence's chunks (one group per
 // sequence); the aggregates do not depend on x and stream through the ring.
 template <class real, int D>
@@ -1031,7 +1178,19 @@ __global__ void __launch_bounds__(32) k_dense_apply_ring(DenseScanArgs<real> a) 
         for (int k = 0; k < D; ++k) y += ar[k] * __shfl_sync(gm, x, k, D);
         x = y;
         real* sp = a.s + (r0 + t) * D + lane;
-        *sp = reset_val(*sp + y, a.reset_thr, a.reset);
+        if (a.slo) {
+          // compensated state: (s, slo) += Delta with error-free transformations
+          real hi = *sp, lo = a.slo[(r0 + t) * D + lane];
+          cs_add(hi, lo, y);
+          if (a.reset && !(hi <= a.reset_thr && hi >= -a.reset_thr)) {
+            hi = real(0);
+            lo = real(0);
+          }
+          *sp = hi;
+          a.slo[(r0 + t) * D + lane] = lo;
+        } else {
+          *sp = reset_val(*sp + y, a.reset_thr, a.reset);
+        }
       }
       if (t + K < n) R.issue(s, lane, A0 + (t + K) * (int64_t)(D * D), b0 + (t + K) * D);
       cp_async_commit();
@@ -1045,8 +1204,18 @@ void dense_launch_wide(const DenseScanArgs<real>& a, cudaStream_t st) {
   constexpr int G = 32 / D;
   const unsigned gc = grid_for(a.bt.act_chunks, G);
   const unsigned gs = grid_for(a.bt.n_act, G);
-  if constexpr (D == 32) k_dense_chunk_ring4<real><<<grid_for(a.bt.act_chunks, 1), 128, 0, st>>>(a);
-  else k_dense_chunk_ring<real, D><<<gc, 32, 0, st>>>(a);
+  if constexpr (D == 32) {
+    if constexpr (sizeof(real) == 4) {
+      if (a.tensor_cores)
+        k_dense_chunk_mma32<<<grid_for(a.bt.act_chunks, 1), 64, 0, st>>>(a);
+      else
+        k_dense_chunk_ring4<real><<<grid_for(a.bt.act_chunks, 1), 128, 0, st>>>(a);
+    } else {
+      k_dense_chunk_ring4<real><<<grid_for(a.bt.act_chunks, 1), 128, 0, st>>>(a);
+    }
+  } else {
+    k_dense_chunk_ring<real, D><<<gc, 32, 0, st>>>(a);
+  }
   k_dense_carry_ring<real, D><<<gs, 32, 0, st>>>(a);
   k_dense_apply_ring<real, D><<<gc, 32, 0, st>>>(a);
   note_launch(3);

@@ -30,6 +30,8 @@ struct LinArgs {
   real dparam;
   real tol = real(0);  // convergence test in this precision: rows with a scaled residual
                        // above it are reported (first failing row, for the sliding window)
+  const real* slo = nullptr;  // compensation of s ([N][d], the state is s + slo); nullptr =
+                              // plain state (mass-action kinetics only)
 };
 
 template <class real>
@@ -89,6 +91,8 @@ struct DenseScanArgs {
   const SeqInfo* info;
   int reset;
   real reset_thr;
+  real* slo = nullptr;  // compensation of s ([N][d]): s + slo += Delta exactly; nullptr = off
+  int tensor_cores = 0;  // d = 32 float32: chunk products on the tensor cores
 };
 
 // Diagonal-family scan in standard form: s_t = a_t s_{t-1} + b_t from s_0, where a_t is
@@ -276,6 +280,11 @@ struct FusedArgs {
   real reset_thr;
   int mode;
   real tol = real(0);  // see LinArgs::tol
+  // compensated state (mass-action kinetics, lane-per-species kernels): slo [N][d] is the
+  // part of the state below the half ulp of s, sprev_lo [n_chunks][d] that of sprev;
+  // nullptr = plain state
+  real* slo = nullptr;
+  real* sprev_lo = nullptr;
 };
 
 template <class real>
@@ -366,7 +375,26 @@ struct MixedScanArgs {
   double reset_thr;
 };
 
+// Mixed-precision iteration without stored Jacobians (d = 16): the linearisation of each
+// chunk forms the chunk's aggregate as it goes (no E, no b in HBM), and the scan's final
+// pass linearises the chunk again from the same old iterate to apply the correction.
+// The two passes take the same value path per sequence (fastsel, decided by the first),
+// so the recomputed E_t and r_t equal the ones the aggregates were formed from.
+struct MixedRcArgs {
+  MixedLinArgs lin;     // E and b unused
+  float* aggP;          // [n_chunks][16][16]
+  float* aggv;          // [n_chunks][16]
+  const float* cin;     // [n_chunks][16] Delta entering each chunk (carry pass)
+  double* sbound;       // [n_chunks][16] old state at the row before each chunk
+  uint8_t* fastsel;     // [B] value path of the sequence in this iteration (1 = float32)
+  int reset;
+  double reset_thr;
+};
+
 cudaError_t launch_lin_ma_mixed(const MixedLinArgs& a, cudaStream_t st);
+cudaError_t launch_mixed_lin_agg(const MixedRcArgs& a, cudaStream_t st);
+cudaError_t launch_mixed_apply_rc(const MixedRcArgs& a, const MixedScanArgs& carry,
+                                  cudaStream_t st);
 // per-sequence species -> (reaction, stoichiometric coefficient) lists for the mixed kernel
 cudaError_t launch_ma_adjacency(int64_t n_seq, int d, int R, const int32_t* topo,
                                 int64_t tstride, int32_t* adj_off, int32_t* adj_e,

@@ -70,9 +70,28 @@ __global__ void __launch_bounds__(512) k_peak_dfma(int iters, double seed) {
 }
 
 // dense tcgen05 MMAs, M = 128, N = 256; operands: 128 x 32 B (A) and 256 x 32 B (B) in the
-// canonical no-swizzle K-major layout (zeros: the rate does not depend on the values)
+// canonical no-swizzle K-major layout, filled with hashed values of magnitude 0.5 to 1 and
+// random signs (operands of realistic bit activity: the power a tensor core draws, and so
+// the clock it holds, depends on the data)
 constexpr int kMmaM = 128, kMmaN = 256;
 constexpr unsigned kPeakWaitLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// a word of operand data: two bf16 or one tf32 value with exponent 126 (|v| in [0.5, 1))
+template <bool BF16>
+__device__ __forceinline__ uint32_t operand_word(uint32_t i) {
+  const uint32_t h = hash32(i * 2654435761u + 12345u);
+  if (BF16) return (h & 0x807F807Fu) | 0x3F003F00u;
+  return (h & 0x807FE000u) | 0x3F000000u;
+}
 
 template <bool BF16>
 __global__ void __launch_bounds__(128, 1) k_peak_mma(int n_mma) {
@@ -81,8 +100,10 @@ __global__ void __launch_bounds__(128, 1) k_peak_mma(int n_mma) {
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ uint32_t tmem_sh;
   const int tid = threadIdx.x;
-  for (int i = tid; i < kMmaM * 32 / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(A)[i] = 0u;
-  for (int i = tid; i < kMmaN * 32 / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(B)[i] = 0u;
+  for (int i = tid; i < kMmaM * 32 / 4; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(A)[i] = operand_word<BF16>(i);
+  for (int i = tid; i < kMmaN * 32 / 4; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(B)[i] = operand_word<BF16>(i + 4096);
   const uint32_t bar = tc::su32(&mbar);
   if (tid == 0) tc::bar_init(bar, 1);
   if (tid < 32) tc::tmem_alloc(tc::su32(&tmem_sh), kMmaN);

@@ -138,3 +138,70 @@ def test_autograd_reaches_the_gru_inputs():
     _, _, dx = deer.deer_grad(dyn, s0, T, s.detach(), (2 * s).detach(), x=x.detach(),
                               want_dx=True)
     assert torch.allclose(x.grad, dx, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("d,R,T,prec", [(8, 12, 1000, "fp64"), (32, 48, 700, "fp32"),
+                                        (16, 24, 513, "fp64")])
+def test_memory_bounded_adjoint_equals_stored(d, R, T, prec):
+    """With a Jacobian memory bound the reverse recursion runs over time windows from the
+    end (each window's Jacobians formed when it is reached): the gradient w.r.t. the rate
+    constants and s0 equals the all-stored one and the FP64 oracle's (C reverse
+    recursion), for windows that do not divide T (a ragged earliest window), and the
+    workspace shrinks."""
+    import paper_2603_16850_gb300 as deer
+    from oracle import cma
+    B = 3
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    p = synth.massaction(B, d, R, T, seed=d + 1, dt=1e-2)
+    off = cma.uniform_offsets(B, T)
+    cb = cma.Batch(p["topology"], p["params"], p["dt"], "rk4", d=d)
+    s = cb.rollout(p["s0"], off)
+    kp = synth.perturbed_rates(p["params"], seed=d + 101)
+    y = cma.Batch(p["topology"], kp, p["dt"], "rk4", d=d).rollout(p["s0"], off)
+    g = 2.0 * (s - y)
+    dk_ref, ds0_ref = cb.adjoint(p["s0"], s, g, off)
+    dyn = deer.Dynamics.massaction(_t(p["topology"], torch.int32), _t(p["params"], dt), d,
+                                   p["dt"])
+    args = (dyn, _t(p["s0"], dt), T, _t(s, dt), _t(g, dt))
+    full_k, full_s0 = deer.deer_grad(*args, prec=prec)
+    W = 77
+    rs = 8 if prec == "fp64" else 4
+    budget = W * B * d * d * rs
+    win_k, win_s0 = deer.deer_grad(*args, prec=prec, jac_bytes_max=budget)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert _relerr(win_k.double().cpu().numpy(), full_k.double().cpu().numpy()) <= tol
+    assert _relerr(win_s0.double().cpu().numpy(), full_s0.double().cpu().numpy()) <= tol
+    otol = 1e-10 if prec == "fp64" else 1e-4
+    assert _relerr(win_k.double().cpu().numpy(), dk_ref) <= otol
+    assert _relerr(win_s0.double().cpu().numpy(), ds0_ref) <= otol
+    from paper_2603_16850_gb300 import _native as N
+    import ctypes as C
+    lib = N.load()
+    o_full = deer._options(**deer._opt_defaults(dict(prec=prec)))
+    o_win = deer._options(**deer._opt_defaults(dict(prec=prec, jac_bytes_max=budget)))
+    cd = dyn.c_struct()
+    assert lib.deer_grad_workspace_bytes(C.byref(cd), B, T, C.byref(o_win)) < \
+        lib.deer_grad_workspace_bytes(C.byref(cd), B, T, C.byref(o_full))
+
+
+def test_memory_bounded_adjoint_input_gradient():
+    """The windowed adjoint also gives the gradient w.r.t. the inputs curried into f_t
+    (GRU, d = 8): equal to the all-stored one and to the oracle's lambda_t^T df_t/dx_t."""
+    import paper_2603_16850_gb300 as deer
+    B, T, d = 2, 600, 8
+    gp = synth.gru(B, T, d, d, seed=3)
+    og = odyn.GRU(gp["W"], gp["U"], gp["x"])
+    s = onewton.rollout(og, gp["s0"], T)
+    y = np.sin(np.arange(B * T * d)).reshape(B, T, d) * 0.1
+    g = 2.0 * (s - y)
+    _, ds0_ref, lam = oadj.adjoint_grad(og, gp["s0"], s, g)
+    dx_ref = oadj.input_grad(og, gp["s0"], s, lam)
+    dyn = deer.Dynamics.gru(_t(gp["W"]), _t(gp["U"]))
+    x = _t(gp["x"].reshape(-1, d))
+    args = (dyn, _t(gp["s0"]), T, _t(s.reshape(-1, d)), _t(g.reshape(-1, d)), x)
+    _, ds0_f, dx_f = deer.deer_grad(*args, want_dx=True)
+    _, ds0_w, dx_w = deer.deer_grad(*args, want_dx=True, jac_bytes_max=61 * B * d * d * 8)
+    assert _relerr(dx_w.cpu().numpy(), dx_f.cpu().numpy()) <= 1e-12
+    assert _relerr(ds0_w.cpu().numpy(), ds0_f.cpu().numpy()) <= 1e-12
+    assert _relerr(dx_w.cpu().numpy().reshape(B, T, d), dx_ref) <= 1e-10
+    assert _relerr(ds0_w.cpu().numpy(), ds0_ref) <= 1e-10

@@ -78,7 +78,10 @@ def test_randn_guess_is_the_documented_draw():
         sv = s.double().cpu().numpy().reshape(B, T, d)
         # Picard step: s^(1)_t = f_t(s^(0)_{t-1}) + (s^(1)_{t-1} - s^(0)_{t-1}), f = 0
         steps = sv[:, 1:] - sv[:, :-1]
-        assert np.max(np.abs(steps + g[:, :-1])) <= tol * 10
+        # the scan's prefix sums of |s| <= 60 round to a few ulps of that magnitude
+        ulp = float(np.spacing(np.array(np.max(np.abs(sv)), dtype=np.float32 if prec == "fp32"
+                                        else np.float64)))
+        assert np.max(np.abs(steps + g[:, :-1])) <= max(tol, 16 * ulp)
         assert np.max(np.abs(sv[:, 0])) == 0.0
 
 

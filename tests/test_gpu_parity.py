@@ -544,3 +544,39 @@ def test_bounded_wait_times_out_and_context_stays_usable():
     s, info = deer.deer_solve(dyn, _t(p["s0"]), 200, jac="full", tol=1e-12, init="s0")
     ref = onewton.rollout(odyn.Brusselator(p["params"], p["dt"]), p["s0"], 200)[0]
     assert bool(info.converged[0]) and _relerr(s.cpu().numpy(), ref) <= 1e-10
+
+
+@pytest.mark.parametrize("kind", ["massaction_d32", "rnn_d32"])
+def test_dense_tensor_core_compose_matches_simt(kind):
+    """The d = 32 float32 chunk products on the tensor cores (warp-level tf32 MMAs with the
+    three-term split) give the iterates of the SIMT chunk pass to float32 accuracy, and
+    both converge to the FP64 oracle's rollout (a ragged tail of chunks, several chunks per
+    sequence)."""
+    deer = _deer()
+    B, T, d = 3, 700, 32
+    if kind == "massaction_d32":
+        p = _ma_problem(B, d, 48, T, seed=17)
+        dyn = _ma_dyn(p, torch.float32)
+        s0, x = _t(p["s0"], torch.float32), None
+        roll = onewton.rollout(_ma_oracle(p), p["s0"], T)
+    else:
+        p = synth.mean_field_rnn(B, T, d, 0.5, seed=2)
+        dyn = deer.Dynamics.rnn_tanh(_t(p["W"], torch.float32))
+        s0, x = _t(p["s0"], torch.float32), _t(p["x"].reshape(-1, d), torch.float32)
+        roll = onewton.rollout(odyn.MeanFieldRNN(p["W"], p["x"]), p["s0"], T)
+    out = {}
+    try:
+        for tc in (True, False):
+            deer.set_tensor_cores(tc)
+            it2, _ = deer.deer_solve(dyn, s0, T, x, jac="full", tol=0.0, max_iters=2,
+                                     prec="fp32", init="zeros", chunk=64)
+            full, info = deer.deer_solve(dyn, s0, T, x, jac="full", init="zeros", chunk=64,
+                                         reset=True, **dict(FP32, tol=5e-8))
+            assert bool(info.converged.all())
+            out[tc] = (it2.cpu().numpy(), full.cpu().numpy(), info.iters.tolist())
+    finally:
+        deer.set_tensor_cores(True)
+    assert _relerr(out[True][0], out[False][0]) <= 1e-5
+    for tc in (True, False):
+        for b in range(B):
+            assert _relerr(out[tc][1][b * T:(b + 1) * T], roll[b]) <= 1e-5
