@@ -337,9 +337,14 @@ size_t deer_noalloc_scratch_bytes(void);
 
 /* Tensor-core kernels (on by default): where a step of the path has a tensor-core kernel
    and a SIMT one with the same results up to rounding, the tensor-core one runs when this
-   is on (today: the GRU d = 64 float32 linearisation, whose three products per step run
-   as tcgen05 MMAs split to float32 accuracy). Process-wide, thread-safe; affects calls
-   made after it returns. */
+   is on: the GRU d = 64 float32 linearisation (tcgen05, three products per step split to
+   float32 accuracy) and the d = 32 float32 dense chunk products (warp-level tf32 MMAs split
+   to float32 accuracy). 0 = SIMT kernels; 1 = the default tensor-core kernels (the d = 16
+   mixed-precision chunk products as warp-level bf16 MMAs, one chunk per warp); 2 = as 1,
+   but the d = 16 mixed-precision chunk products run as tcgen05 MMAs with the accumulator
+   in tensor memory, 8 chunks per CTA stacked block-diagonally (1/8 of the issued
+   multiply-adds useful: the measured alternative). Process-wide, thread-safe; affects
+   calls made after it returns. */
 void deer_set_tensor_cores(int32_t on);
 int32_t deer_get_tensor_cores(void);
 

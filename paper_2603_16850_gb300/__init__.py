@@ -173,9 +173,11 @@ def kernel_launch_count() -> int:
     return int(N.load().deer_kernel_launch_count())
 
 
-def set_tensor_cores(on: bool) -> None:
-    """Select the tensor-core kernels where a step has one (deer_set_tensor_cores)."""
-    N.load().deer_set_tensor_cores(1 if on else 0)
+def set_tensor_cores(on) -> None:
+    """Select the tensor-core kernels where a step has one (deer_set_tensor_cores): False /
+    0 SIMT, True / 1 the default tensor-core kernels, 2 the tcgen05 block-diagonal form of
+    the d = 16 mixed-precision chunk products."""
+    N.load().deer_set_tensor_cores(int(on))
 
 
 def tensor_cores() -> bool:
@@ -198,6 +200,13 @@ def _opt_defaults(opts):
 
 def _run_solve(dyn, B, T, offsets, s0, x, s_init, opts, stream, workspace, device):
     lib = N.load()
+    if int(opts.get("chunk", 0)) == 0:
+        # the autotuner's cached chunk length for this GPU and configuration, if any
+        from . import autotune
+        Tmax = T if offsets is None else max(
+            (int(offsets[i + 1]) - int(offsets[i]) for i in range(B)), default=0)
+        opts = dict(opts, chunk=autotune.cached_chunk(
+            dyn, Tmax, opts["jac"], opts["prec"], gpu=torch.cuda.get_device_name(device)))
     o = _options(**opts)
     dt = _dtype(opts["prec"])
     N_rows = int(offsets[-1]) if offsets is not None else B * T

@@ -7,7 +7,8 @@ number of independent chunks (parallelism). The best L depends on the GPU, the d
 d, the Jacobian mode, the precision and T, so it is measured: ``tune_chunk`` times a
 few candidates on the caller's own problem with CUDA events and caches the fastest in a
 JSON file, keyed by (GPU name, kind, d, jac, prec, T rounded up to a power of two).
-``deer_solve(..., chunk=cached_chunk(...))`` then uses it.
+The solver's default path (``chunk=0`` in the Python binding) then uses the cached choice
+for the same configuration, and falls back to the library's own default without one.
 
 The diagonal look-back scan fixes its own tile length (it is tied to d), so tuning applies
 to the dense (full-Jacobian) paths.
@@ -96,9 +97,27 @@ def tune_chunk(dyn, s0, T: int, x=None, candidates=DEFAULT_CANDIDATES, repeats: 
 
 
 def cached_chunk(dyn, T: int, jac: str = "full", prec: str = "fp64",
-                 path: Optional[str] = None) -> int:
+                 path: Optional[str] = None, gpu: Optional[str] = None) -> int:
     """The tuned chunk length for this configuration, or 0 (the library default)."""
-    import torch
+    if gpu is None:
+        import torch
+        gpu = torch.cuda.get_device_name()
+    key = make_key(gpu, dyn.kind, dyn.d, jac, prec, T)
+    return int(_cache_cached(path or cache_path()).get(key, {}).get("chunk", 0))
 
-    key = make_key(torch.cuda.get_device_name(), dyn.kind, dyn.d, jac, prec, T)
-    return int(load_cache(path).get(key, {}).get("chunk", 0))
+
+_MEMO: Dict[str, tuple] = {}
+
+
+def _cache_cached(path: str) -> Dict[str, dict]:
+    """The cache file's contents, re-read only when the file changed (the solver's default
+    path consults it on every call)."""
+    try:
+        mtime = os.path.getmtime(path)
+    except OSError:
+        return {}
+    hit = _MEMO.get(path)
+    if hit is None or hit[0] != mtime:
+        hit = (mtime, load_cache(path))
+        _MEMO[path] = hit
+    return hit[1]

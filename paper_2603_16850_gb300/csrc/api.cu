@@ -568,6 +568,8 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
       msa.cin = reinterpret_cast<float*>(ws + ly.cin);
       msa.reset = o->reset;
       msa.reset_thr = 1e18;  // the scan and the Jacobians are float32
+      msa.tc_mode = g_tensor_cores.load() >= 2 ? 2 : 1;
+      msa.status = flags;
       if (ly.mixed_rc) {
         rca.lin = mla;
         rca.lin.E = nullptr;
@@ -1259,7 +1261,7 @@ deer_status deer_selftest_wait_timeout(deer_stream_t stream) {
 int64_t deer_kernel_launch_count(void) { return g_launches.load(); }
 
 void deer_profile_enable(int32_t on) { g_prof_on.store(on ? 1 : 0); }
-void deer_set_tensor_cores(int32_t on) { g_tensor_cores.store(on ? 1 : 0); }
+void deer_set_tensor_cores(int32_t on) { g_tensor_cores.store(on <= 0 ? 0 : (on >= 2 ? 2 : 1)); }
 int32_t deer_get_tensor_cores(void) { return g_tensor_cores.load(); }
 
 void deer_profile_reset(void) {

@@ -711,7 +711,11 @@ static void mixed_launch(const MixedScanArgs& a, cudaStream_t st) {
   const unsigned gs = grid_for(a.bt.n_act, G);
   if constexpr (D == 16) {
     const unsigned gw = grid_for(a.bt.act_chunks, 4);  // one warp per chunk
-    k_mixed_chunk_tc16<<<gw, 128, 0, st>>>(a);
+    if (a.tc_mode == 2) {
+      if (launch_mixed_chunk_tcgen05(a, st) != cudaSuccess) return;
+    } else {
+      k_mixed_chunk_tc16<<<gw, 128, 0, st>>>(a);
+    }
     k_mixed_carry<D><<<gs, 128, 0, st>>>(a);
     k_mixed_apply_tc16<<<gw, 128, 0, st>>>(a);
   } else {

@@ -373,6 +373,9 @@ struct MixedScanArgs {
   float* cin;   // [n_chunks][d]
   int reset;
   double reset_thr;
+  int tc_mode = 1;          // d = 16 chunk pass: 1 warp-level bf16 MMAs, 2 tcgen05
+                            // block-diagonal MMAs (8 chunks per CTA)
+  Flags* status = nullptr;  // timeout flag of the bounded waits (tcgen05 variant)
 };
 
 // Mixed-precision iteration without stored Jacobians (d = 16): the linearisation of each
@@ -400,6 +403,7 @@ cudaError_t launch_ma_adjacency(int64_t n_seq, int d, int R, const int32_t* topo
                                 int64_t tstride, int32_t* adj_off, int32_t* adj_e,
                                 cudaStream_t st);
 cudaError_t launch_dense_scan_mixed(const MixedScanArgs& a, cudaStream_t st);
+cudaError_t launch_mixed_chunk_tcgen05(const MixedScanArgs& a, cudaStream_t st);
 
 inline bool mixed_supported(int kind, int d, int jac) {
   return (kind == DEER_F_MASSACTION_RK4 || kind == DEER_F_MASSACTION_EULER) &&

@@ -61,3 +61,28 @@ def test_tune_chunk_on_gpu(tmp_path):
                               confirm=2, init="s0", reset=True)
     assert bool(info.converged.all())
     assert np.isfinite(s.cpu().numpy()).all()
+
+
+def test_cached_choice_serves_the_default_path(tmp_path, monkeypatch):
+    """A tuned entry for (GPU, kind, d, Jacobian mode, precision, T bucket) is what the
+    solver's default chunk (0) resolves to; other configurations keep the library default;
+    a rewritten cache file is picked up."""
+    path = str(tmp_path / "tune.json")
+    monkeypatch.setenv("DEER_AUTOTUNE_CACHE", path)
+
+    class Dyn:
+        kind, d = "massaction_rk4", 8
+
+    at.store(at.make_key("GB300", "massaction_rk4", 8, "full", "fp32", 16384),
+             {"chunk": 128, "ms": 1.0}, path)
+    assert at.cached_chunk(Dyn, 10000, "full", "fp32", gpu="GB300") == 128
+    assert at.cached_chunk(Dyn, 20000, "full", "fp32", gpu="GB300") == 0
+    assert at.cached_chunk(Dyn, 10000, "diag", "fp32", gpu="GB300") == 0
+    assert at.cached_chunk(Dyn, 10000, "full", "fp32", gpu="other") == 0
+    import os
+    import time
+    time.sleep(0.01)
+    at.store(at.make_key("GB300", "massaction_rk4", 8, "full", "fp32", 16384),
+             {"chunk": 64, "ms": 0.5}, path)
+    os.utime(path, (time.time() + 5, time.time() + 5))
+    assert at.cached_chunk(Dyn, 10000, "full", "fp32", gpu="GB300") == 64
