@@ -776,6 +776,76 @@ def ragged_mixed_measurement(deer, N, lib, dev, stream, B=10000, group=1000, che
                                      "in C"}
         checks.add(out, check)
     return out
+def compose_measurement(deer, N, lib, dev, stream, B=1000):
+    """The chunk products of the dense scan on the tensor cores, in both forms: the d = 16
+    mixed-precision chunk pass as warp-level bf16 MMAs (one chunk per warp, every
+    multiply-add useful) and as tcgen05 MMAs (8 chunks per CTA stacked block-diagonally,
+    accumulator in tensor memory, 1/8 useful), timed on the ragged d = 16 group with stored
+    Jacobians; and the d = 32 float32 chunk pass as warp-level tf32 MMAs (three-term split)
+    against the SIMT pass, on the single-trajectory RNN (T = 1e5). Scan-phase device time
+    from the library's CUDA events; the chunk passes' share and their tensor-pipe busy
+    fractions come from the ncu captures under profiles/."""
+    import numpy as np
+    import torch
+    import synth
+    d, R = 16, 24
+    lengths = synth.ragged_lengths(B, 1000, 100000, seed=5)
+    off = synth.offsets_from_lengths(lengths)
+    p = synth.massaction(B, d, R, 1, seed=6)
+    dyn = dyn_sub(deer, p, d, dev, n=B)
+    s0 = torch.tensor(p["s0"], dtype=torch.float64, device=dev)
+    opts = dict(jac="full", tol=1e-12, prec="mixed_bf16", init="zeros", reset=True,
+                window=True, chunk=128)
+    ws_ = torch.empty(deer.deer_workspace_bytes(dyn, B, int(off[-1]), **opts),
+                      dtype=torch.uint8, device=dev)
+    out = {"mixed_d16": {"workload": f"ragged mass action d=16, B={B}, stored bf16 Jacobians"}}
+    try:
+        for mode, name in ((1, "warp_mma_bf16"), (2, "tcgen05_block_diagonal")):
+            deer.set_tensor_cores(mode)
+            deer.deer_solve_batched(dyn, s0, off, workspace=ws_, stream=stream, **opts)
+            torch.cuda.synchronize()
+            lib.deer_profile_reset()
+            lib.deer_profile_enable(1)
+            e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+            e0.record(stream)
+            _, info = deer.deer_solve_batched(dyn, s0, off, workspace=ws_, stream=stream, **opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lib.deer_profile_enable(0)
+            prof = N.deer_profile()
+            lib.deer_profile_read(prof)
+            out["mixed_d16"][name] = {"ms": e0.elapsed_time(e1), "scan_ms": prof.ms[3],
+                                      "rows_scanned": int(prof.rows[3]),
+                                      "newton_iters_max": int(info.iters.max())}
+        del ws_
+        T, dr = 100000, 32
+        pr = synth.mean_field_rnn(1, T, dr, 0.5, seed=0)
+        rd = deer.Dynamics.rnn_tanh(torch.tensor(pr["W"], dtype=torch.float32, device=dev))
+        x = torch.tensor(pr["x"].reshape(-1, dr), dtype=torch.float32, device=dev)
+        s0r = torch.tensor(pr["s0"], dtype=torch.float32, device=dev)
+        ro = dict(jac="full", tol=1e-5, prec="fp32", init="zeros", reset=True, window=True,
+                  chunk=256)
+        out["dense_d32"] = {"workload": "mean-field RNN d=32, B=1, T=1e5, FP32"}
+        for mode, name in ((1, "warp_mma_tf32x3"), (0, "simt_ring4")):
+            deer.set_tensor_cores(mode)
+            deer.deer_solve(rd, s0r, T, x, stream=stream, **ro)
+            torch.cuda.synchronize()
+            lib.deer_profile_reset()
+            lib.deer_profile_enable(1)
+            e0.record(stream)
+            _, info = deer.deer_solve(rd, s0r, T, x, stream=stream, **ro)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lib.deer_profile_enable(0)
+            prof = N.deer_profile()
+            lib.deer_profile_read(prof)
+            out["dense_d32"][name] = {"ms": e0.elapsed_time(e1), "scan_ms": prof.ms[3],
+                                      "newton_iters": int(info.iters.max())}
+    finally:
+        deer.set_tensor_cores(1)
+    return out
+
+
 def run_only(args):
     """One secondary workload alone, for profiler captures of its kernels."""
     import torch
@@ -799,6 +869,8 @@ def run_only(args):
                                    B=args.batch or 64, window=True)
     elif args.only == "gru_elk":
         out = gru_elk_measurement(deer, dev, stream, B=args.batch or 64)
+    elif args.only == "compose":
+        out = compose_measurement(deer, N, lib, dev, stream, B=args.batch or 1000)
     elif args.only == "threshold":
         gains = tuple(float(v) for v in args.gains.split(",")) if args.gains else (0.5, 1.0, 2.0)
         out = threshold_measurement(deer, N, lib, dev, stream, gains=gains)
@@ -1084,7 +1156,7 @@ def main():
                     help="skip the secondary GRU quasi-DEER measurement")
     ap.add_argument("--only", default="", choices=["", "brusselator", "gru", "gru_window",
                                                    "gru_elk", "adjoint", "ragged_mixed",
-                                                   "threshold"],
+                                                   "threshold", "compose"],
                     help="run one secondary workload alone (with --batch) and print it")
     ap.add_argument("--gains", default="",
                     help="--only threshold: comma-separated RNN gains g (default 0.5,1.0,2.0)")

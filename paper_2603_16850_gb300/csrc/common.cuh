@@ -339,6 +339,33 @@ __device__ __forceinline__ real cs_residual(real hi_t, real lo_t, real hi_p, rea
 }
 
 // ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async): 16 bytes through L2 only, or 4 / 8
+// bytes; every commit closes a group, and wait_group<N> returns when all but the N most
+// recent groups of this thread have landed (the data is then visible to this thread).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
+  static_assert(BYTES == 4 || BYTES == 8, "cp.async.ca copies 4, 8 or 16 bytes");
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Launch bookkeeping (counted for deer_kernel_launch_count).
 // ---------------------------------------------------------------------------
 void note_launch(int n = 1);

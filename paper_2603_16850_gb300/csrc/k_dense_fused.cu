@@ -318,6 +318,11 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
   constexpr bool BREG = sizeof(real) == 4;
   __shared__ __align__(16) real sK[GPB][GS];
   __shared__ __align__(16) real sP[GPB][GS];
+  // per-lane prefetch ring (two rows): the pending row A_t[i][:] (mode 1), b_t[i] (mode 1),
+  // s_t[i] and its compensation term, copied one row ahead with cp.async so that their
+  // DRAM latency overlaps the previous row's work; each lane reads back only its own slot
+  constexpr int PF = D + 4;
+  __shared__ __align__(16) real sPF[2][kFusedBlock][PF];
   const int grp = threadIdx.x / D, i = threadIdx.x % D;
   const unsigned gm = ((1u << D) - 1u) << ((threadIdx.x & 31) & ~(D - 1));
   const int64_t ac = blockIdx.x * (int64_t)GPB + grp;
@@ -365,19 +370,39 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
 #pragma unroll
     for (int j = 0; j < D; ++j) Px[i * RS + j] = i == j ? real(1) : real(0);
     __syncwarp(gm);
+    auto prefetch = [&](int slot, int t) {
+      if (t < n) {
+        real* q = sPF[slot][threadIdx.x];
+        const int64_t row = r0 + t;
+        if constexpr (MODE == 1) {
+          const real* src = a.Ai + (c * L + t) * E + i * D;
+#pragma unroll
+          for (int k = 0; k < D * (int)sizeof(real) / 16; ++k)
+            cp_async16(q + k * 16 / (int)sizeof(real), src + k * 16 / (int)sizeof(real));
+          cp_async_small<sizeof(real)>(q + D, a.bi + (c * L + t) * D + i);
+        }
+        cp_async_small<sizeof(real)>(q + D + 1, a.s + row * D + i);
+        if constexpr (CS) cp_async_small<sizeof(real)>(q + D + 2, a.slo + row * D + i);
+      }
+      cp_async_commit();
+    };
+    prefetch(0, 0);
     for (int t = 0; t < n; ++t) {
       const int64_t row = r0 + t;
       const int64_t pr = (c * L + t);
       real* Arow = a.Ai + pr * E + i * D;
       real* bp = a.bi + pr * D + i;
-      real sn = a.s[row * D + i];
+      prefetch((t + 1) & 1, t + 1);
+      cp_async_wait<1>();  // this lane's copies of row t have landed
+      const real* q = sPF[t & 1][threadIdx.x];
+      real sn = q[D + 1];
       real sn_lo = real(0);
-      if constexpr (CS) sn_lo = a.slo[row * D + i];
+      if constexpr (CS) sn_lo = q[D + 2];
       if constexpr (MODE == 1) {
         // pending scan step: Delta_t = A_t Delta_{t-1} + b_t, s_t += Delta_t
         real Ar[D];
-        ldrow_p<real, D>(Arow, Ar);
-        real nd = *bp;
+        ldrow_p<real, D>(q, Ar);
+        real nd = q[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) nd += Ar[j] * __shfl_sync(gm, dl, j, D);
         dl = nd;
@@ -484,6 +509,7 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
       prev = sn;
       prev_lo = sn_lo;
     }
+    cp_async_wait<0>();
     real pf[D];
     ldrow_p<real, D>(Px + i * RS, pf);
     strow_p<real, D>(a.aggP + c * (int64_t)E + i * D, pf);
