@@ -472,6 +472,14 @@ def adjoint_measurement(deer, N, lib, dev, stream, checks=None):
     torch.cuda.synchronize()
     fwd = e0.elapsed_time(e1)
     grad = e1.elapsed_time(e2)
+    # one more forward solve with the library's per-phase events (not the timed one)
+    lib.deer_profile_reset()
+    lib.deer_profile_enable(1)
+    deer.deer_solve(dyn, s0, T, workspace=ws_, stream=stream, **opts)
+    torch.cuda.synchronize()
+    lib.deer_profile_enable(0)
+    prof = N.deer_profile()
+    lib.deer_profile_read(prof)
     del ws_
     e0.record(stream)
     deer.deer_rollout(dyn, s0, T, prec="fp32", stream=stream)
@@ -483,6 +491,8 @@ def adjoint_measurement(deer, N, lib, dev, stream, checks=None):
            "sequential_gpu_rollout": {"ms": roll_ms, "value": B * T / (roll_ms / 1000.0),
                                       "unit": UNIT},
            "forward_ms": fwd, "grad_ms": grad,
+           "forward_phase_ms": {n: prof.ms[i] for i, n in enumerate(N.PHASES)},
+           "forward_rows_linearized": int(prof.rows[1]),
            "forward_value": B * T / (fwd / 1000.0), "grad_value": B * T / (grad / 1000.0),
            "unit": UNIT, "newton_iters_max": int(info.iters.max()),
            "converged": bool(info.converged.all()),

@@ -220,8 +220,11 @@ typedef struct {
                           (N d^2 2 bytes) exceed it, none is stored: each chunk's aggregate is
                           formed while the chunk is linearised, and the scan's final pass
                           linearises it again (the same arithmetic from the same iterate)
-                          to apply the correction, so the iterates are the same. The
-                          workspace queries shrink accordingly. */
+                          to apply the correction. Never leaving the chip, the Jacobians are
+                          then kept in float32 and composed to float32 accuracy (tf32 tensor-
+                          core products with a three-term split) instead of bf16, which keeps
+                          Newton's rate of convergence over long horizons; state, residual
+                          and test stay float64. The workspace queries shrink accordingly. */
 } deer_options;
 
 typedef struct {

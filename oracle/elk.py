@@ -99,3 +99,38 @@ def lm_step_dense(dyn, s0, s, mode="full", lam=1.0):
     J = dense_jacobian(dyn, s0, s, mode)
     H = J.T @ J + lam * np.eye(T * d)
     return s - np.linalg.solve(H, J.T @ r).reshape(T, d)
+
+
+# --- the covariance recursion as an associative scan ------------------------------------
+# Sarkka and Garcia-Fernandez ("Temporal parallelization of Bayesian smoothers", IEEE TAC
+# 2021) write one filtering step as an element (A, C, J) acting on the incoming covariance
+# P by P -> A (I + P J)^{-1} P A^T + C, with an associative combination, so the filtered
+# covariances of all steps are a prefix scan. For this LGSSM (transition F_t = A~_t,
+# process noise I, emission y_t = s_t + N(0, sigma^2 I), sigma^2 = 1/lambda) the step's
+# element is A = c F_t, C = c I, J = lambda c F_t^T F_t with c = 1 / (1 + lambda).
+
+def cov_element(F, lam):
+    """Element (A, C, J) of one filtering step with transition F [B, d, d]."""
+    B, d, _ = F.shape
+    c = 1.0 / (1.0 + lam)
+    return (c * F, np.broadcast_to(c * np.eye(d), (B, d, d)).copy(),
+            lam * c * np.swapaxes(F, 1, 2) @ F)
+
+
+def cov_combine(ei, ej):
+    """e_i then e_j: A = A_j N A_i, C = A_j N C_i A_j^T + C_j, J = A_i^T N^T J_j A_i + J_i
+    with N = (I + C_i J_j)^{-1}."""
+    Ai, Ci, Ji = ei
+    Aj, Cj, Jj = ej
+    d = Ai.shape[-1]
+    N = np.linalg.inv(np.eye(d) + Ci @ Jj)
+    At = np.swapaxes
+    return (Aj @ N @ Ai, Aj @ N @ Ci @ At(Aj, 1, 2) + Cj,
+            At(Ai, 1, 2) @ At(N, 1, 2) @ Jj @ Ai + Ji)
+
+
+def cov_apply(e, P):
+    """The covariance after the steps of element e, entered with covariance P."""
+    A, C, J = e
+    d = A.shape[-1]
+    return A @ np.linalg.inv(np.eye(d) + P @ J) @ P @ np.swapaxes(A, 1, 2) + C

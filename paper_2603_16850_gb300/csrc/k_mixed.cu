@@ -99,7 +99,8 @@ __device__ __forceinline__ void mixed_row(const MixedLinArgs& a, bool valid, int
                                           float (*sG)[D + 4], float (*sK)[D + 4], V* sRate,
                                           float* sD1, float* sD2, float& mx, float& sq,
                                           int64_t seq, unsigned long long& key,
-                                          __nv_bfloat16* Eo, float* bo) {
+                                          __nv_bfloat16* Eo, float* bo,
+                                          float* Eo32 = nullptr) {
   constexpr bool F64 = sizeof(V) == 8;
   const V s_prev = F64 ? (V)s_prev_d : (V)d2f_trunc(s_prev_d);
   const V h = F64 ? (V)a.dv.dt : (V)a.dt_f;
@@ -186,13 +187,25 @@ __device__ __forceinline__ void mixed_row(const MixedLinArgs& a, bool valid, int
     if (!(m <= a.tol_f) && key == 0ull) key = bad_key(true, row - __ldg(a.bt.offsets + seq));
     const float scale = a.scale_f;
     const float hwf = RK4 ? hf / 6.f : hf;
-    Eo += lane * D;
-    // E = A - I with A = I + hw Kacc (scaled by (1 - k) under scale-ELK: E = s A - I)
+    // E = A - I with A = I + hw Kacc (scaled by (1 - k) under scale-ELK: E = s A - I):
+    // bf16 row-major, or float32 with rows padded to 20 (the recomputing path)
+    if (Eo32) {
+      float* Er = Eo32 + lane * 20;
 #pragma unroll
-    for (int j = 0; j < D; j += 2) {
-      const float x0 = scale * hwf * Kacc[j] + (j == lane ? scale - 1.f : 0.f);
-      const float x1 = scale * hwf * Kacc[j + 1] + (j + 1 == lane ? scale - 1.f : 0.f);
-      *reinterpret_cast<__nv_bfloat162*>(Eo + j) = __floats2bfloat162_rn(x0, x1);
+      for (int j = 0; j < D; j += 4)
+        *reinterpret_cast<float4*>(Er + j) =
+            make_float4(scale * hwf * Kacc[j] + (j == lane ? scale - 1.f : 0.f),
+                        scale * hwf * Kacc[j + 1] + (j + 1 == lane ? scale - 1.f : 0.f),
+                        scale * hwf * Kacc[j + 2] + (j + 2 == lane ? scale - 1.f : 0.f),
+                        scale * hwf * Kacc[j + 3] + (j + 3 == lane ? scale - 1.f : 0.f));
+    } else {
+      Eo += lane * D;
+#pragma unroll
+      for (int j = 0; j < D; j += 2) {
+        const float x0 = scale * hwf * Kacc[j] + (j == lane ? scale - 1.f : 0.f);
+        const float x1 = scale * hwf * Kacc[j + 1] + (j + 1 == lane ? scale - 1.f : 0.f);
+        *reinterpret_cast<__nv_bfloat162*>(Eo + j) = __floats2bfloat162_rn(x0, x1);
+      }
     }
     bo[lane] = -rf;
   }
@@ -470,18 +483,25 @@ __global__ void __launch_bounds__(128) k_mixed_apply_tc16(MixedScanArgs a) {
 // ---- d = 16 without stored Jacobians: one warp per chunk ----------------------------
 // The two half-warps linearise rows t and t + 1 of the chunk (16 lanes per row, as in
 // k_lin_ma_mixed) into shared memory; the whole warp then folds them into the chunk
-// aggregate on the fragments of k_mixed_chunk_tc16 (pass 1), or applies the correction
-// to them (pass 2). Shared memory per warp: the two rows' linearisation buffers and their
-// E (bf16) and b.
+// aggregate (pass 1) or applies the correction to them (pass 2). The Jacobians never go to
+// HBM here, so they are kept in float32 and the chunk product is formed to float32
+// accuracy: P^T <- P^T + P^T E_t^T as warp-level tf32 MMAs (m16n8k8) with the three-term
+// split x = x_hi + x_lo, the accumulator of P^T re-laid into the next A operand by quad
+// shuffles (as in k_dense_chunk_mma32). Over horizons of 1e5 steps the rounding of E_t
+// to bf16 compounds in the chunk products and slows Newton's convergence to linear on
+// the stiffer networks; float32 Jacobians keep it fast. The vector part
+// v <- v + E_t v + b_t: lane l forms half a row (row l mod 16, columns 8 (l / 16) ..) and
+// the two halves meet by a shuffle.
 constexpr int kRcWarps = 4;
 constexpr int kRcRmax = 64;
+constexpr int kRcES = 20;  // float32 E rows padded: the fragment reads hit distinct banks
 
 struct RcSmem {
   float G[2][16][20];
   float K[2][17][20];
   double rate[2][kRcRmax];
   float d1[2][kRcRmax], d2[2][kRcRmax];
-  __nv_bfloat16 E[2][256];
+  float E[2][16 * kRcES];
   float b[2][16];
   double old[16];  // pass 2: old state of the previous pair's second row
 };
@@ -514,7 +534,8 @@ __device__ __forceinline__ void rc_net(const MixedLinArgs& a, int64_t seq, int l
   }
 }
 
-// linearise one row into the half-warp's shared buffers (E, b): value path per `fast`
+// linearise one row into the half-warp's shared buffers (float32 E, b): value path per
+// `fast`
 template <bool RK4>
 __device__ __forceinline__ void rc_row(const MixedLinArgs& a, bool fast, bool valid,
                                        int64_t row, int half, int lane, unsigned gm,
@@ -525,25 +546,81 @@ __device__ __forceinline__ void rc_row(const MixedLinArgs& a, bool fast, bool va
     mixed_row<float, 16, RK4, kRcRmax / 16>(
         a, valid, row, lane, gm, sp, sc, n.q, n.kd, n.kf, n.R, n.tt, n.ae, n.e0, n.e1,
         S.G[half], S.K[half], reinterpret_cast<float*>(S.rate[half]), S.d1[half],
-        S.d2[half], mx, sq, seq, key, S.E[half], S.b[half]);
+        S.d2[half], mx, sq, seq, key, nullptr, S.b[half], S.E[half]);
   else
     mixed_row<double, 16, RK4, kRcRmax / 16>(
         a, valid, row, lane, gm, sp, sc, n.q, n.kd, n.kf, n.R, n.tt, n.ae, n.e0, n.e1,
         S.G[half], S.K[half], S.rate[half], S.d1[half], S.d2[half], mx, sq, seq, key,
-        S.E[half], S.b[half]);
+        nullptr, S.b[half], S.E[half]);
 }
 
-// the lane's four words of E and its two entries of b, in fragment positions
-__device__ __forceinline__ void rc_frag(const RcSmem& S, int h, int g, int t, uint32_t& e0,
-                                        uint32_t& e1, uint32_t& e2, uint32_t& e3,
-                                        float& b_lo, float& b_hi) {
-  const uint32_t* Ew = reinterpret_cast<const uint32_t*>(S.E[h]);
-  e0 = Ew[g * 8 + t];
-  e1 = Ew[g * 8 + t + 4];
-  e2 = Ew[(g + 8) * 8 + t];
-  e3 = Ew[(g + 8) * 8 + t + 4];
-  b_lo = S.b[h][g];
-  b_hi = S.b[h][g + 8];
+__device__ __forceinline__ uint32_t rc_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void rc_mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1,
+                                            uint32_t a2, uint32_t a3, uint32_t b0,
+                                            uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// P^T <- P^T + P^T E^T for the warp's 16 x 16 accumulator acc[n-tile][4] (lane (g, t):
+// rows g, g + 8, columns 8 j + 2 t, + 1), three-term tf32 split
+__device__ __forceinline__ void rc_compose(float (&acc)[2][4], const float* E, int g, int t,
+                                           int lane) {
+  const int qsrc = (lane & ~3) + (t >> 1);
+  const bool odd = t & 1;
+  uint32_t ah[2][4], al[2][4];
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    const float x0 = __shfl_sync(0xffffffffu, acc[kk][0], qsrc);
+    const float x1 = __shfl_sync(0xffffffffu, acc[kk][1], qsrc);
+    const float x2 = __shfl_sync(0xffffffffu, acc[kk][2], qsrc);
+    const float x3 = __shfl_sync(0xffffffffu, acc[kk][3], qsrc);
+    const float y0 = __shfl_sync(0xffffffffu, acc[kk][0], qsrc + 2);
+    const float y1 = __shfl_sync(0xffffffffu, acc[kk][1], qsrc + 2);
+    const float y2 = __shfl_sync(0xffffffffu, acc[kk][2], qsrc + 2);
+    const float y3 = __shfl_sync(0xffffffffu, acc[kk][3], qsrc + 2);
+    const float av[4] = {odd ? x1 : x0, odd ? x3 : x2, odd ? y1 : y0, odd ? y3 : y2};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      ah[kk][e] = rc_tf32(av[e]);
+      al[kk][e] = rc_tf32(av[e] - __uint_as_float(ah[kk][e]));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      // B[k][n] = E^T[k][n] = E[n][k]: n = 8 j + g, k = 8 kk + t (+ 4)
+      const float bx0 = E[(8 * j + g) * kRcES + 8 * kk + t];
+      const float bx1 = E[(8 * j + g) * kRcES + 8 * kk + t + 4];
+      const uint32_t bh0 = rc_tf32(bx0), bh1 = rc_tf32(bx1);
+      const uint32_t bl0 = rc_tf32(bx0 - __uint_as_float(bh0));
+      const uint32_t bl1 = rc_tf32(bx1 - __uint_as_float(bh1));
+      rc_mma_tf32(acc[j], al[kk][0], al[kk][1], al[kk][2], al[kk][3], bh0, bh1);
+      rc_mma_tf32(acc[j], ah[kk][0], ah[kk][1], ah[kk][2], ah[kk][3], bl0, bl1);
+      rc_mma_tf32(acc[j], ah[kk][0], ah[kk][1], ah[kk][2], ah[kk][3], bh0, bh1);
+    }
+  }
+}
+
+// v <- v + E v + b with lane l holding v[l mod 16]; returns the new v[l mod 16]
+__device__ __forceinline__ float rc_matvec(float v, const float* E, const float* b,
+                                           int lane) {
+  const int i = lane & 15, c = lane >> 4;
+  float part = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    part += E[i * kRcES + 8 * c + k] * __shfl_sync(0xffffffffu, v, 8 * c + k);
+  part += __shfl_xor_sync(0xffffffffu, part, 16);
+  return v + part + b[i];
 }
 
 template <bool RK4>
@@ -569,46 +646,44 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_mixed_lin_agg16(MixedRcArgs r
   const double prev0 = r0 == base ? a.s0[seq * 16 + lane] : a.s[(r0 - 1) * 16 + lane];
   if (half == 0 && r0 > base) r.sbound[c * 16 + lane] = prev0;
   const bool need_P = c != win_first(a.bt, seq);
-  float p0[4] = {g == 2 * tq ? 1.f : 0.f, g == 2 * tq + 1 ? 1.f : 0.f, 0.f, 0.f};
-  float p1[4] = {0.f, 0.f, g == 2 * tq ? 1.f : 0.f, g == 2 * tq + 1 ? 1.f : 0.f};
-  float lo = 0.f, hi = 0.f, q[4] = {0.f, 0.f, 0.f, 0.f};
+  // P^T = I
+  float acc[2][4];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int n0 = 8 * j + 2 * tq;
+    acc[j][0] = g == n0 ? 1.f : 0.f;
+    acc[j][1] = g == n0 + 1 ? 1.f : 0.f;
+    acc[j][2] = g + 8 == n0 ? 1.f : 0.f;
+    acc[j][3] = g + 8 == n0 + 1 ? 1.f : 0.f;
+  }
+  float v = 0.f;
   float mx = 0.f, sq = 0.f;
   unsigned long long key = 0ull;
   for (int t = 0; t < n; t += 2) {
     const int tr = t + half;
-    const bool v = tr < n;
-    const int64_t row = r0 + (v ? tr : 0);
-    const double sp = tr == 0 ? prev0 : (v ? a.s[(row - 1) * 16 + lane] : prev0);
-    const double sc = v ? a.s[row * 16 + lane] : prev0;
-    rc_row<RK4>(a, fast, v, row, half, lane, gm, sp, sc, net, S, mx, sq, seq, key);
+    const bool vld = tr < n;
+    const int64_t row = r0 + (vld ? tr : 0);
+    const double sp = tr == 0 ? prev0 : (vld ? a.s[(row - 1) * 16 + lane] : prev0);
+    const double sc = vld ? a.s[row * 16 + lane] : prev0;
+    rc_row<RK4>(a, fast, vld, row, half, lane, gm, sp, sc, net, S, mx, sq, seq, key);
     __syncwarp();
     for (int h = 0; h < 2 && t + h < n; ++h) {
-      uint32_t e0, e1, e2, e3;
-      float b_lo, b_hi;
-      rc_frag(S, h, g, tq, e0, e1, e2, e3, b_lo, b_hi);
-      if (need_P) {
-        const uint32_t A[4] = {pack_bf16x2(p0[0], p0[1]), pack_bf16x2(p0[2], p0[3]),
-                               pack_bf16x2(p1[0], p1[1]), pack_bf16x2(p1[2], p1[3])};
-        mma_bf16_16816(p0, A, e0, e1);
-        mma_bf16_16816(p1, A, e2, e3);
-      }
-      frag_matvec16(e0, e1, e2, e3, b_lo, b_hi, lo, hi, q, tq);
+      if (need_P) rc_compose(acc, S.E[h], g, tq, l32);
+      v = rc_matvec(v, S.E[h], S.b[h], l32);
     }
     __syncwarp();
   }
+  // P[i][j] = P^T[j][i]
   float* Po = r.aggP + c * 256;
-  Po[(2 * tq) * 16 + g] = p0[0];
-  Po[(2 * tq + 1) * 16 + g] = p0[1];
-  Po[(2 * tq) * 16 + g + 8] = p0[2];
-  Po[(2 * tq + 1) * 16 + g + 8] = p0[3];
-  Po[(2 * tq + 8) * 16 + g] = p1[0];
-  Po[(2 * tq + 9) * 16 + g] = p1[1];
-  Po[(2 * tq + 8) * 16 + g + 8] = p1[2];
-  Po[(2 * tq + 9) * 16 + g + 8] = p1[3];
-  if (tq == 0) {
-    r.aggv[c * 16 + g] = lo;
-    r.aggv[c * 16 + g + 8] = hi;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int n0 = 8 * j + 2 * tq;
+    Po[n0 * 16 + g] = acc[j][0];
+    Po[(n0 + 1) * 16 + g] = acc[j][1];
+    Po[n0 * 16 + g + 8] = acc[j][2];
+    Po[(n0 + 1) * 16 + g + 8] = acc[j][3];
   }
+  if (half == 0) r.aggv[c * 16 + lane] = v;
   acc_resid_f(a.acc, seq, true, mx, sq, key);
 }
 
@@ -617,7 +692,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_mixed_apply_rc16(MixedRcArgs 
   __shared__ __align__(16) RcSmem smem[kRcWarps];
   const MixedLinArgs& a = r.lin;
   const int warp = threadIdx.x >> 5, l32 = threadIdx.x & 31;
-  const int half = l32 >> 4, lane = l32 & 15, g = l32 >> 2, tq = l32 & 3;
+  const int half = l32 >> 4, lane = l32 & 15;
   const unsigned gm = gmask_mixed<16>();
   const int64_t ac = blockIdx.x * (int64_t)kRcWarps + warp;
   if (ac >= a.bt.act_chunks) return;  // whole warps
@@ -630,33 +705,28 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_mixed_apply_rc16(MixedRcArgs 
   rc_net(a, seq, lane, net);
   const bool fast = r.fastsel[seq] != 0;
   const double prev0 = r0 == base ? a.s0[seq * 16 + lane] : r.sbound[c * 16 + lane];
-  const float* ci = r.cin + c * 16;
-  float lo = ci[g], hi = ci[g + 8];
-  float q[4] = {ci[2 * tq], ci[2 * tq + 1], ci[2 * tq + 8], ci[2 * tq + 9]};
+  float x = r.cin[c * 16 + lane];  // Delta entering the chunk, entry lane mod 16
   float mx = 0.f, sq = 0.f;  // recomputed statistics, not reported again
   unsigned long long key = 0ull;
   double* s = const_cast<double*>(a.s);
   for (int t = 0; t < n; t += 2) {
     const int tr = t + half;
-    const bool v = tr < n;
-    const int64_t row = r0 + (v ? tr : 0);
+    const bool vld = tr < n;
+    const int64_t row = r0 + (vld ? tr : 0);
     // old s_{t-1}: the chunk's saved boundary, the previous pair's second row (saved
     // before it was updated), or row t of this pair (not updated yet)
     double sp = prev0;
-    if (tr > 0) sp = half == 0 ? S.old[lane] : (v ? s[(row - 1) * 16 + lane] : prev0);
-    const double sc = v ? s[row * 16 + lane] : prev0;
-    rc_row<RK4>(a, fast, v, row, half, lane, gm, sp, sc, net, S, mx, sq, seq, key);
+    if (tr > 0) sp = half == 0 ? S.old[lane] : (vld ? s[(row - 1) * 16 + lane] : prev0);
+    const double sc = vld ? s[row * 16 + lane] : prev0;
+    rc_row<RK4>(a, fast, vld, row, half, lane, gm, sp, sc, net, S, mx, sq, seq, key);
     __syncwarp();
-    if (half == 1 && v) S.old[lane] = sc;
+    if (half == 1 && vld) S.old[lane] = sc;
     __syncwarp();
     for (int h = 0; h < 2 && t + h < n; ++h) {
-      uint32_t e0, e1, e2, e3;
-      float b_lo, b_hi;
-      rc_frag(S, h, g, tq, e0, e1, e2, e3, b_lo, b_hi);
-      frag_matvec16(e0, e1, e2, e3, b_lo, b_hi, lo, hi, q, tq);
-      if (tq < 2) {
-        double* sp2 = s + (r0 + t + h) * 16 + g + 8 * tq;
-        double nv = *sp2 + (double)(tq == 0 ? lo : hi);
+      x = rc_matvec(x, S.E[h], S.b[h], l32);
+      if (half == 0) {
+        double* sp2 = s + (r0 + t + h) * 16 + lane;
+        double nv = *sp2 + (double)x;
         if (r.reset && overflowed(nv)) nv = 0.0;
         *sp2 = nv;
       }

@@ -1,8 +1,9 @@
 """Mixed precision without stored Jacobians (d = 16, deer_options.jac_bytes_max below the
 bf16 Jacobians of all rows): the chunk aggregates are formed while linearising and the
-scan's final pass linearises again. The recomputed Jacobians and residuals are the same
-arithmetic from the same iterate, so the iterates equal those of the stored-Jacobian path
-bit for bit, and the fixed point is the float64 rollout."""
+scan's final pass linearises again, from the same iterate, with float32 Jacobians composed
+to float32 accuracy (tf32 MMAs with the three-term split). A Newton step therefore equals
+the oracle's exact-Jacobian step to float32 accuracy (the stored-Jacobian path rounds the
+Jacobians to bf16), and the fixed point is the float64 rollout."""
 import ctypes as C
 
 import numpy as np
@@ -11,6 +12,8 @@ import torch
 
 import synth
 from oracle import cma
+from oracle import dynamics as odyn
+from oracle import newton as onewton
 
 pytestmark = pytest.mark.gpu
 
@@ -19,8 +22,8 @@ def _t(a, dt=torch.float64):
     return torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
 
 
-@pytest.mark.parametrize("window,iters", [(False, 3), (True, 0), (False, 0)])
-def test_recomputing_mixed_path_equals_stored(window, iters):
+@pytest.mark.parametrize("window", [False, True])
+def test_recomputing_mixed_path(window):
     import paper_2603_16850_gb300 as deer
     lengths = [700, 1, 0, 2049, 333, 64]
     off = synth.offsets_from_lengths(lengths)
@@ -28,27 +31,41 @@ def test_recomputing_mixed_path_equals_stored(window, iters):
     p = synth.massaction(B, 16, 24, 1, seed=31)
     dyn = deer.Dynamics.massaction(_t(p["topology"], torch.int32), _t(p["params"]), 16,
                                    p["dt"])
-    opts = dict(jac="full", tol=1e-12 if iters == 0 else 0.0, prec="mixed_bf16", init="zeros",
-                reset=True, window=window, chunk=64, max_iters=iters if iters else 600)
-    s_ref, i_ref = deer.deer_solve_batched(dyn, _t(p["s0"]), off, **opts)
-    s_rc, i_rc = deer.deer_solve_batched(dyn, _t(p["s0"]), off, jac_bytes_max=1 << 16, **opts)
-    assert torch.equal(s_rc, s_ref)
-    assert i_rc.iters.tolist() == i_ref.iters.tolist()
-    assert i_rc.converged.tolist() == i_ref.converged.tolist()
-    if iters == 0:
-        assert bool(i_rc.converged.all())
-        ref = cma.Batch(p["topology"], p["params"], p["dt"], "rk4", d=16).rollout(p["s0"], off)
-        got = s_rc.cpu().numpy()
-        for b in range(B):
-            lo, hi = off[b], off[b + 1]
-            if hi > lo:
-                err = np.max(np.abs(got[lo:hi] - ref[lo:hi])) / np.max(np.abs(ref[lo:hi]))
-                assert err <= 1e-9, (b, err)
+    base = dict(jac="full", prec="mixed_bf16", init="s0", reset=True, window=window, chunk=64)
+    # one Newton step from the constant guess against the oracle's exact-Jacobian step
+    one, _ = deer.deer_solve_batched(dyn, _t(p["s0"]), off, jac_bytes_max=1 << 16,
+                                     **dict(base, tol=0.0, max_iters=1))
+    one = one.cpu().numpy()
+    for b, L in enumerate(lengths):
+        if L == 0:
+            continue
+        od = odyn.MassAction(p["topology"][b:b + 1], p["params"][b:b + 1], p["dt"], "rk4", d=16)
+        guess = onewton.initial_guess(od, p["s0"][b:b + 1], L, "s0")
+        ref = onewton.quasi_newton_step(od, p["s0"][b:b + 1], guess, "full")[0]
+        got = one[off[b]:off[b + 1]]
+        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        # the first step evaluates the residual in float32 (far from convergence), whose
+        # rounding the correction sums over the sequence
+        assert err <= 5e-5, (b, err)
+    s_rc, i_rc = deer.deer_solve_batched(dyn, _t(p["s0"]), off, jac_bytes_max=1 << 16,
+                                         **dict(base, tol=1e-12, max_iters=600))
+    s_st, i_st = deer.deer_solve_batched(dyn, _t(p["s0"]), off, **dict(base, tol=1e-12,
+                                                                       max_iters=600))
+    assert bool(i_rc.converged.all()) and bool(i_st.converged.all())
+    # float32 Jacobians converge at least as fast as bf16 ones
+    assert max(i_rc.iters.tolist()) <= max(i_st.iters.tolist())
+    ref = cma.Batch(p["topology"], p["params"], p["dt"], "rk4", d=16).rollout(p["s0"], off)
+    got = s_rc.cpu().numpy()
+    for b in range(B):
+        lo, hi = off[b], off[b + 1]
+        if hi > lo:
+            err = np.max(np.abs(got[lo:hi] - ref[lo:hi])) / np.max(np.abs(ref[lo:hi]))
+            assert err <= 1e-9, (b, err)
     from paper_2603_16850_gb300 import _native as N
     lib = N.load()
     cd = dyn.c_struct()
-    big = deer._options(**deer._opt_defaults(dict(opts)))
-    small = deer._options(**deer._opt_defaults(dict(opts, jac_bytes_max=1 << 16)))
+    big = deer._options(**deer._opt_defaults(dict(base)))
+    small = deer._options(**deer._opt_defaults(dict(base, jac_bytes_max=1 << 16)))
     n = int(off[-1])
     assert lib.deer_workspace_bytes(C.byref(cd), B, n, C.byref(small)) < \
         lib.deer_workspace_bytes(C.byref(cd), B, n, C.byref(big)) - n * 16 * 16 * 2 // 2

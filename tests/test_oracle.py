@@ -775,3 +775,49 @@ def test_c_oracle_equals_numpy_oracle(d, R, integ):
         if m is not None:
             tot = ref @ m
             assert np.max(np.abs(s[seg] @ m - tot)) <= 1e-12 * np.max(np.abs(tot))
+
+
+def test_filter_covariance_as_associative_elements():
+    """The covariance recursion of the ELK filter (Sec. 4.3: predict with process noise I,
+    update with emission variance 1/lambda, Sigma_0 = 0) is a prefix scan of per-step
+    elements: one element applied to P is one filter step; combining elements is
+    associative; the in-order prefix combinations, applied to the zero prior, give every
+    filtered covariance of elk.kalman_filter; and splitting a sequence into chunks
+    (aggregate per chunk, carry across chunks, re-run inside) gives them too."""
+    rng = np.random.default_rng(3)
+    B, T, d, lam = 2, 23, 4, 0.7
+    F = rng.standard_normal((B, T, d, d)) * 0.5 + np.eye(d)
+    _, Ps, _, _ = elk.kalman_filter(F, np.zeros((B, T, d)), np.zeros((B, T, d)),
+                                     np.zeros((B, d)), lam)
+    # one element = one step
+    P = rng.standard_normal((B, d, d))
+    P = P @ np.swapaxes(P, 1, 2)
+    Pm = F[:, 0] @ P @ np.swapaxes(F[:, 0], 1, 2) + np.eye(d)
+    step = np.linalg.inv(np.eye(d) + lam * Pm) @ Pm
+    assert np.allclose(elk.cov_apply(elk.cov_element(F[:, 0], lam), P), step, atol=1e-12)
+    # associativity
+    e = [elk.cov_element(F[:, t], lam) for t in range(3)]
+    l = elk.cov_combine(elk.cov_combine(e[0], e[1]), e[2])
+    r = elk.cov_combine(e[0], elk.cov_combine(e[1], e[2]))
+    for x, y in zip(l, r):
+        assert np.allclose(x, y, atol=1e-12)
+    # prefix scan from the zero prior = the filter's covariances
+    Z = np.zeros((B, d, d))
+    acc = elk.cov_element(F[:, 0], lam)
+    for t in range(T):
+        if t > 0:
+            acc = elk.cov_combine(acc, elk.cov_element(F[:, t], lam))
+        assert np.allclose(elk.cov_apply(acc, Z), Ps[:, t], atol=1e-12)
+    # chunked: aggregates of chunks of 5, carried, then the sequential recursion inside
+    P_in = Z
+    for c0 in range(0, T, 5):
+        agg = elk.cov_element(F[:, c0], lam)
+        for t in range(c0 + 1, min(c0 + 5, T)):
+            agg = elk.cov_combine(agg, elk.cov_element(F[:, t], lam))
+        Pt = P_in
+        for t in range(c0, min(c0 + 5, T)):
+            Pm = F[:, t] @ Pt @ np.swapaxes(F[:, t], 1, 2) + np.eye(d)
+            Pt = np.linalg.inv(np.eye(d) + lam * Pm) @ Pm
+            assert np.allclose(Pt, Ps[:, t], atol=1e-12)
+        P_in = elk.cov_apply(agg, P_in)
+        assert np.allclose(P_in, Pt, atol=1e-12)
