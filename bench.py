@@ -856,6 +856,41 @@ def compose_measurement(deer, N, lib, dev, stream, B=1000):
     return out
 
 
+def dense_elk_measurement(deer, dev, stream, B=4, d=8, lam=1.0, iters=10):
+    """Cost of one dense-ELK iteration (full-Jacobian Kalman-filter step, Sec. 4.2-4.3)
+    against one undamped DEER iteration on the same few long sequences (mass action d=8,
+    RK4, FP64, reset heuristic on: undamped DEER overflows on these horizons; fixed
+    iteration count, tol 0). With chunks of 128 rows the covariance
+    recursion runs in parallel over time (chunk elements, carry, per-chunk restart); with
+    chunks of T/4 rows (T = 4096, chunk 1024) the library keeps one covariance chain per
+    sequence, which shows what the parallel form saves. The paper's own figures for the
+    ratio: 3.6 ms per ELK step against 0.282 ms per DEER step."""
+    import torch
+    import synth
+    R = {8: 12, 16: 24}[d]
+    out = {}
+    for T, chunks in ((65536, (128,)), (4096, (128, 1024))):
+        p = synth.massaction(B, d, R, T, seed=80, dt=0.01)
+        dyn = deer.Dynamics.massaction(
+            torch.tensor(p["topology"], dtype=torch.int32, device=dev),
+            torch.tensor(p["params"], dtype=torch.float64, device=dev), d, p["dt"])
+        s0 = torch.tensor(p["s0"], dtype=torch.float64, device=dev)
+        for chunk in chunks:
+            row = {}
+            for name, extra in (("deer", {}), ("elk", dict(damp="elk", damp_param=lam))):
+                opts = dict(jac="full", tol=0.0, max_iters=iters, init="s0", prec="fp64",
+                            chunk=chunk, reset=True, **extra)
+                ms = _time_solve1(deer, dyn, s0, T, None, opts, stream)
+                row[name + "_ms_per_iter"] = ms / iters
+            row["elk_over_deer"] = row["elk_ms_per_iter"] / row["deer_ms_per_iter"]
+            row["covariance"] = ("parallel over time" if T // chunk >= 8
+                                 else "one chain per sequence")
+            out["T%d_chunk%d" % (T, chunk)] = row
+    out["paper_elk_over_deer"] = 3.6 / 0.282
+    return {"workload": f"mass action d={d} RK4 FP64, B={B}, lambda={lam}, "
+                        f"{iters} iterations (tol 0)", **out}
+
+
 def run_only(args):
     """One secondary workload alone, for profiler captures of its kernels."""
     import torch
@@ -879,6 +914,8 @@ def run_only(args):
                                    B=args.batch or 64, window=True)
     elif args.only == "gru_elk":
         out = gru_elk_measurement(deer, dev, stream, B=args.batch or 64)
+    elif args.only == "dense_elk":
+        out = dense_elk_measurement(deer, dev, stream, B=args.batch or 4)
     elif args.only == "compose":
         out = compose_measurement(deer, N, lib, dev, stream, B=args.batch or 1000)
     elif args.only == "threshold":
@@ -1166,7 +1203,7 @@ def main():
                     help="skip the secondary GRU quasi-DEER measurement")
     ap.add_argument("--only", default="", choices=["", "brusselator", "gru", "gru_window",
                                                    "gru_elk", "adjoint", "ragged_mixed",
-                                                   "threshold", "compose"],
+                                                   "threshold", "compose", "dense_elk"],
                     help="run one secondary workload alone (with --batch) and print it")
     ap.add_argument("--gains", default="",
                     help="--only threshold: comma-separated RNN gains g (default 0.5,1.0,2.0)")

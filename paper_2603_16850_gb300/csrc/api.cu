@@ -114,7 +114,7 @@ struct Layout {
   size_t offsets, chunk_first, win_chunk, act_seq, act_row_off, act_chunk_off, acc, info, flags,
       ma, gru_M,
       A, b, aggP, aggv, cin, mob, pin, sprev, lb_ticket, lb_flags, lb_agg, lb_pre, xproj,
-      adj_off, adj_e, slo, sprev_lo, sbound, fastsel, total;
+      adj_off, adj_e, slo, sprev_lo, sbound, fastsel, cov_agg, cov_in, total;
   bool cs;         // compensated float32 state
   bool mixed_rc;   // mixed precision without stored Jacobians
   int64_t n_chunks_max;
@@ -172,7 +172,7 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
   ly.acc = take((size_t)(B > 0 ? B : 1) * sizeof(SeqAcc));
   ly.info = take((size_t)(B > 0 ? B : 1) * sizeof(SeqInfo));
   ly.flags = take(sizeof(Flags));
-  ly.ma = ly.gru_M = ly.A = ly.aggP = ly.mob = ly.pin = p;
+  ly.ma = ly.gru_M = ly.A = ly.aggP = ly.mob = ly.pin = ly.cov_agg = ly.cov_in = p;
   ly.ma_stride = 0;
   ly.n_ma = 0;
   if (f->kind == DEER_F_MASSACTION_EULER || f->kind == DEER_F_MASSACTION_RK4) {
@@ -215,6 +215,11 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
   if (o->damp == DEER_DAMP_ELK) {
     ly.mob = take((size_t)C * d * 4 * rs);
     ly.pin = take((size_t)C * d * rs);
+    if (o->jac == DEER_JAC_FULL) {
+      // dense ELK's covariance in parallel over time: chunk elements and carried covariances
+      ly.cov_agg = take((size_t)C * 3 * d * d * rs);
+      ly.cov_in = take((size_t)C * d * d * rs);
+    }
   }
   ly.adj_off = ly.adj_e = p;
   if (mixed) {
@@ -320,9 +325,9 @@ static deer_status check_common(const deer_dynamics* f, const deer_options* o) {
        (o->damp != DEER_DAMP_NONE && o->damp != DEER_DAMP_SCALE)))
     return DEER_ERR_UNSUPPORTED;
   if (!d_supported(f->kind, f->d, o->jac)) return DEER_ERR_UNSUPPORTED;
-  // dense ELK: the covariance recursion runs in registers for d <= 8
+  // dense ELK: the covariance recursion is built for d <= 16
   if (o->damp == DEER_DAMP_ELK && o->jac == DEER_JAC_FULL &&
-      !(f->d == 1 || f->d == 2 || f->d == 4 || f->d == 8))
+      !(f->d == 1 || f->d == 2 || f->d == 4 || f->d == 8 || f->d == 16))
     return DEER_ERR_UNSUPPORTED;
   if (o->damp == DEER_DAMP_CLIP && o->jac == DEER_JAC_FULL) return DEER_ERR_INVALID;
   if (o->damp == DEER_DAMP_ELK && !(o->damp_param >= 0.0)) return DEER_ERR_INVALID;
@@ -713,8 +718,15 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
         }
       } else if (o->jac == DEER_JAC_FULL) {
         if (o->damp == DEER_DAMP_ELK && o->damp_param > 0.0) {
-          // dense ELK: Kalman-filter damping of the linearised step (A, b rewritten)
+          // dense ELK: Kalman-filter damping of the linearised step (A, b rewritten). The
+          // covariance recursion runs in parallel over time (chunk elements, carry) when
+          // the sequences are long (8 or more chunks each on average) and too few to fill
+          // the GPU on their own (under 1024), as one chain per sequence otherwise
           ElkDenseArgs<real> ea{bt, d, la.A, la.b, (real)o->damp_param};
+          if (bt.n_act < 1024 && bt.act_chunks >= 8 * bt.n_act) {
+            ea.cov_agg = reinterpret_cast<real*>(ws + ly.cov_agg);
+            ea.cov_in = reinterpret_cast<real*>(ws + ly.cov_in);
+          }
           DEER_CK(launch_elk_dense<real>(ea, st));
         }
         DEER_CK(launch_dense_scan<real>(dsa, st));

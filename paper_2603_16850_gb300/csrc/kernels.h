@@ -442,6 +442,11 @@ struct ElkDenseArgs {
   real* A;
   real* b;
   real lambda;
+  // parallel-in-time covariance (nullptr = one dependent chain per sequence): the chunks'
+  // covariance elements (A, C, J) [n_chunks][3][d][d] and the filtered covariance entering
+  // each chunk [n_chunks][d][d]
+  real* cov_agg = nullptr;
+  real* cov_in = nullptr;
 };
 
 template <class real>

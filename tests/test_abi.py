@@ -68,11 +68,12 @@ def test_workspace_sizes_and_validation(lib):
     # unsupported state size / invalid combination -> 0
     bad = _dyn(N, d=3)
     assert lib.deer_workspace_bytes(C.byref(bad), 1, 10, C.byref(o)) == 0
-    # dense ELK: the full-Jacobian Kalman step is built for d <= 8 only
+    # dense ELK: the full-Jacobian Kalman step is built for d <= 16 only
     o.jac = N.JAC["full"]
     o.damp = N.DAMP["elk"]
     assert lib.deer_workspace_bytes(C.byref(dyn), 1, 10, C.byref(o)) > 0
-    assert lib.deer_workspace_bytes(C.byref(_dyn(N, d=16)), 1, 10, C.byref(o)) == 0
+    assert lib.deer_workspace_bytes(C.byref(_dyn(N, d=16)), 1, 10, C.byref(o)) > 0
+    assert lib.deer_workspace_bytes(C.byref(_dyn(N, d=32)), 1, 10, C.byref(o)) == 0
 
 
 def test_invalid_arguments_fail_without_device_work(lib):

@@ -488,6 +488,47 @@ def test_dense_elk_iterates_and_fixed_point(d, lam):
         assert _relerr(s.cpu().numpy()[b * T:(b + 1) * T], roll[b]) <= 1e-10
 
 
+@pytest.mark.parametrize("d,lam,lengths", [(4, 2.0, [6000]), (8, 0.5, [4000, 2500]),
+                                            (16, 1.0, [3000])])
+def test_dense_elk_covariance_in_parallel_over_time(d, lam, lengths):
+    """Dense ELK on few long sequences, where the covariance recursion runs in parallel
+    over time (chunk aggregates of the filter's associative elements, a carry across
+    chunks, the per-row recursion restarted from the carried covariance): two iterations
+    equal the oracle's sequential Kalman filter (elk_filter_step), and the rollout is a
+    fixed point of the step (a warm start there is accepted at once and left in place).
+    From s0 the damped iteration needs thousands of iterations at these horizons: with
+    dt = 0.01 every A_t is close to I, so the residual Jacobian has singular values of
+    order 1/T, and error along them shrinks only by lambda / (lambda + sigma^2) per step.
+    d = 16 also covers the smaller thread blocks of that size."""
+    deer = _deer()
+    off = synth.offsets_from_lengths(lengths)
+    R = {4: 6, 8: 12, 16: 24}[d]
+    p = _ma_problem(len(lengths), d, R, 1, seed=70 + d, dt=0.01)
+    dyn = _ma_dyn(p, torch.float64)
+    s2, _ = deer.deer_solve_batched(dyn, _t(p["s0"]), off, jac="full", damp="elk",
+                                    damp_param=lam, tol=0.0, max_iters=2, init="s0",
+                                    chunk=128)
+    s2 = s2.cpu().numpy()
+    for b, n in enumerate(lengths):
+        sub = odyn.MassAction(p["topology"][b:b + 1], p["params"][b:b + 1], p["dt"], "rk4", d=d)
+        s0b = p["s0"][b:b + 1]
+        ref = onewton.initial_guess(sub, s0b, n, "s0")
+        for _ in range(2):
+            ref = oelk.elk_filter_step(sub, s0b, ref, "full", lam)
+        assert _relerr(s2[off[b]:off[b + 1]], ref[0]) <= 1e-11, b
+    rolls = []
+    for b, n in enumerate(lengths):
+        sub = odyn.MassAction(p["topology"][b:b + 1], p["params"][b:b + 1], p["dt"], "rk4", d=d)
+        rolls.append(onewton.rollout(sub, p["s0"][b:b + 1], n)[0])
+    s, info = deer.deer_solve_batched(dyn, _t(p["s0"]), off, jac="full", damp="elk",
+                                      damp_param=lam, tol=1e-11, init="user", chunk=128,
+                                      s_init=_t(np.concatenate(rolls)), max_iters=3)
+    assert bool(info.converged.all()) and int(info.iters.max()) <= 2, info
+    sn = s.cpu().numpy()
+    for b in range(len(lengths)):
+        assert _relerr(sn[off[b]:off[b + 1]], rolls[b]) <= 1e-9, b
+
+
 @pytest.mark.parametrize("window", [False, True])
 def test_dense_elk_fp32_ragged_converges(window):
     """Dense ELK in float32 on a ragged batch, within 1e-5 of the float64 rollout. The
