@@ -225,6 +225,18 @@ typedef struct {
                           core products with a three-term split) instead of bf16, which keeps
                           Newton's rate of convergence over long horizons; state, residual
                           and test stay float64. The workspace queries shrink accordingly. */
+  int32_t device_loop; /* 1 = run the Newton loop of Algorithm 1 on the device: after the
+                          first iteration, the iterations are one CUDA graph, a gate node
+                          and a conditional while node whose body is one iteration (scan,
+                          linearisation, convergence check; the check sets the condition
+                          for the next), launched once per call with no host
+                          synchronisation between iterations. Every kernel then reads the
+                          active-set sizes the last check wrote to device memory, and the
+                          grids are sized for the whole problem (blocks past the active set
+                          exit at once). Results are identical to the host loop's. Ignored
+                          (host loop) while per-phase profiling is on. The call still blocks
+                          until the loop ends. Default 0. */
+  int32_t reserved_;  /* zero */
 } deer_options;
 
 typedef struct {
@@ -324,9 +336,9 @@ deer_status deer_rollout(const deer_dynamics* f, int64_t batch, int64_t T,
    does not fit are rejected with DEER_ERR_WORKSPACE (deer_last_cuda_error says how many
    bytes they needed). Every call looks up the array's address on the current device
    (cudaGetSymbolAddress, which allocates nothing), so a context that was reset and
-   recreated since an earlier call is handled. Like deer_solve, it reads a status word back
-   and synchronises its stream once per Newton iteration, so it cannot be called while the
-   stream is being captured into a CUDA graph. Every call reuses the same array and clears
+   recreated since an earlier call is handled. Like deer_solve's host-driven loop, it reads a
+   status word back and synchronises its stream once per Newton iteration (`device_loop` is
+   ignored), so it cannot be called while the stream is being captured into a CUDA graph. Every call reuses the same array and clears
    what must start at zero, so calls that overlap on the GPU (other streams or threads)
    race and must be serialised by the caller. Arguments and results as deer_solve (without
    mixed precision, dense ELK or the sliding window, which return DEER_ERR_UNSUPPORTED, and

@@ -139,7 +139,7 @@ def _dtype(prec: str):
 
 def _options(jac, damp, damp_param, tol, max_iters, init, prec, reset, chunk,
              confirm=1, window=False, seed=0, history=None,
-             compensate=True, jac_bytes_max=0) -> N.deer_options:
+             compensate=True, jac_bytes_max=0, device_loop=False) -> N.deer_options:
     o = N.deer_options()
     o.max_iters = int(max_iters)
     o.tol = float(tol)
@@ -155,6 +155,7 @@ def _options(jac, damp, damp_param, tol, max_iters, init, prec, reset, chunk,
     o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     o.compensate = int(bool(compensate))
     o.jac_bytes_max = int(jac_bytes_max)
+    o.device_loop = int(bool(device_loop))
     if history is not None:
         _check_dev(history, "history")
         if history.dtype != torch.float64 or history.dim() != 2 or history.shape[1] != 4:
@@ -193,7 +194,7 @@ def deer_workspace_bytes(dyn: Dynamics, batch: int, total_steps: int, **opts) ->
 def _opt_defaults(opts):
     base = dict(jac="full", damp="none", damp_param=0.0, tol=1e-10, max_iters=0, init="s0",
                 prec="fp64", reset=False, chunk=0, confirm=1, window=False, seed=0,
-                history=None, compensate=True, jac_bytes_max=0)
+                history=None, compensate=True, jac_bytes_max=0, device_loop=False)
     base.update(opts)
     return base
 
@@ -260,7 +261,8 @@ def deer_solve(dyn: Dynamics, s0: torch.Tensor, T: int, x: Optional[torch.Tensor
     converged prefix of each sequence), history (a float64 CUDA tensor [n][4] that receives
     (iteration, merit, max scaled residual, active sequences) of each convergence test),
     compensate (fp32 mass-action kinetics with the full Jacobian: keep a compensated
-    two-float state, default True).
+    two-float state, default True), device_loop (run the iterations after the first as one
+    CUDA graph with a conditional while node, no host synchronisation between them).
     Host inputs are copied to the GPU and the result back to the host, into ``out`` when
     given (a preallocated, ideally pinned, host tensor [B*T][d]).
     """

@@ -398,9 +398,7 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   bt.act_seq = reinterpret_cast<int64_t*>(ws + ly.act_seq);
   bt.act_row_off = reinterpret_cast<int64_t*>(ws + ly.act_row_off);
   bt.act_chunk_off = reinterpret_cast<int64_t*>(ws + ly.act_chunk_off);
-  bt.n_act = B;
-  bt.act_rows = N;
-  bt.act_chunks = nc;
+  bt.set_counts(B, N, nc);
   int64_t* d_win = reinterpret_cast<int64_t*>(ws + ly.win_chunk);
   // the window freezes rows one iterate after they qualify, which relies on the fast
   // (quadratic) convergence of undamped steps; damped steps converge linearly and run whole
@@ -643,116 +641,229 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   deer_status status = DEER_OK;
   Flags hf;
   PhaseTimer pt(st);
-  int64_t lin_rows = N;  // rows linearised in the current iteration
-  for (int it = 0;; ++it) {
-    int64_t carry_launches = 0;
-    if (fused && it > 0) {
-      // compose the aggregates of the previous pass into per-chunk carries
-      const int64_t c0l = g_launches.load();
-      fa.bt = bt;
-      pt.begin(PH_SCAN);
-      DEER_CK(launch_dense_fused_carry<real>(fa, st));
-      pt.end(PH_SCAN);
-      carry_launches = g_launches.load() - c0l;
-    }
-    const int64_t l0 = g_launches.load();
-    la.bt = bt;
-    pt.begin(PH_LIN);
+
+  // The steps of one iteration, shared by the host-driven loop and the graph of the
+  // device-resident one, enqueued on `lst`. `b` carries the active-set sizes (host values,
+  // or upper bounds with live counts).
+  cudaStream_t lst = st;
+  // fused path, iterations after the first: compose the previous pass's aggregates
+  auto carry_step = [&](const Batch& b) -> cudaError_t {
+    fa.bt = b;
+    return launch_dense_fused_carry<real>(fa, lst);
+  };
+  auto lin_step = [&](const Batch& b, int it) -> cudaError_t {
+    la.bt = b;
     if (fused) {
-      fa.bt = bt;
+      fa.bt = b;
       fa.mode = it > 0 ? 1 : 0;
-      DEER_CK(launch_dense_fused<real>(fa, st));
-    } else if (gru_tiled) {
+      return launch_dense_fused<real>(fa, lst);
+    }
+    if (gru_tiled) {
       if constexpr (sizeof(real) == 4) {
-        gta.bt = bt;
-        if (g_tensor_cores.load() != 0) DEER_CK(launch_gru_lin_tc(gta, st));
-        else DEER_CK(launch_gru_lin_tiled(gta, st));
+        gta.bt = b;
+        return g_tensor_cores.load() != 0 ? launch_gru_lin_tc(gta, lst)
+                                          : launch_gru_lin_tiled(gta, lst);
       }
-    } else if (mixed) {
+    }
+    if (mixed) {
       if constexpr (sizeof(real) == 8) {
-        mla.bt = bt;
+        mla.bt = b;
         mla.it = it;
         if (ly.mixed_rc) {
-          rca.lin.bt = bt;
+          rca.lin.bt = b;
           rca.lin.it = it;
-          DEER_CK(launch_mixed_lin_agg(rca, st));
-        } else {
-          DEER_CK(launch_lin_ma_mixed(mla, st));
+          return launch_mixed_lin_agg(rca, lst);
         }
+        return launch_lin_ma_mixed(mla, lst);
       }
-    } else {
-      DEER_CK(launch_linearize<real>(la, st));
     }
-    pt.end(PH_LIN);
-    const int64_t l1 = g_launches.load();
-    ca.it = it;
-    pt.begin(PH_CHECK);
+    return launch_linearize<real>(la, lst);
+  };
+  // non-fused paths: solve the linearised recurrence of the last linearisation
+  auto scan_step = [&](const Batch& b, bool host_loop) -> cudaError_t {
+    dsa.bt = b;
+    gsa.bt = b;
+    if (mixed) {
+      if constexpr (sizeof(real) == 8) {
+        msa.bt = b;
+        if (ly.mixed_rc) {
+          rca.lin.bt = b;
+          return launch_mixed_apply_rc(rca, msa, lst);
+        }
+        return launch_dense_scan_mixed(msa, lst);
+      }
+    }
+    if (o->jac == DEER_JAC_FULL) {
+      if (o->damp == DEER_DAMP_ELK && o->damp_param > 0.0) {
+        // dense ELK: Kalman-filter damping of the linearised step (A, b rewritten). The
+        // covariance recursion runs in parallel over time (chunk elements, carry) when
+        // the sequences are long (8 or more chunks each on average) and too few to fill
+        // the GPU on their own (under 1024), as one chain per sequence otherwise
+        ElkDenseArgs<real> ea{b, d, la.A, la.b, (real)o->damp_param};
+        if (b.n_act() < 1024 && b.act_chunks() >= 8 * b.n_act()) {
+          ea.cov_agg = reinterpret_cast<real*>(ws + ly.cov_agg);
+          ea.cov_in = reinterpret_cast<real*>(ws + ly.cov_in);
+        }
+        const cudaError_t e = launch_elk_dense<real>(ea, lst);
+        if (e != cudaSuccess) return e;
+      }
+      return launch_dense_scan<real>(dsa, lst);
+    }
+    if (lookback) {
+      lba.bt = b;
+      lba.epoch += 1;
+      // device-resident loop: the epoch comes from the check counter instead
+      lba.epoch_from = host_loop ? nullptr : flags;
+      // round-robin tile order assumes every sequence has the same chunks to solve,
+      // which a sliding window breaks
+      lba.cps = window ? 0 : uniform_chunks;
+      return launch_diag_lookback<real>(lba, lst);
+    }
+    return launch_diag_scan<real>(gsa, lst);
+  };
+
+  // Device-resident loop (opt-in): iteration 0 runs on the stream as usual; the rest is
+  // one CUDA graph, a gate node and a conditional while node whose body is one iteration
+  // (scan or carry, linearise, check), the check setting the condition for the next. No
+  // host synchronisation between iterations; every kernel reads the active-set sizes the
+  // last check wrote, and grids are sized for the whole problem (the look-back scan's
+  // surplus CTAs draw tickets past the active tiles and leave). Per-phase timing keeps
+  // the host loop.
+  if (o->device_loop && !pt.on) {
+    ca.it = 0;
+    ca.device_it = 1;
+    ca.set_cond = 0;
+    ca.reset = o->reset;
+    DEER_CK(lin_step(bt, 0));
     DEER_CK(launch_check(ca, st));
-    pt.end(PH_CHECK);
-    DEER_CK(cudaMemcpyAsync(&hf, flags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
-    DEER_CK(cudaStreamSynchronize(st));
-    bool stop = false;
-    if (hf.bad_input) { status = DEER_ERR_INVALID; stop = true; }
-    else if (hf.timeout) { status = DEER_ERR_TIMEOUT; stop = true; }
-    else if (hf.n_nonfinite > 0 && !o->reset) { status = DEER_ERR_NONFINITE; stop = true; }
-    else if (hf.n_active == 0) stop = true;
-    else if (it >= max_iters) { status = DEER_NOT_CONVERGED; stop = true; }
-    int64_t scan_launches = carry_launches;
-    bt.n_act = hf.n_active;
-    bt.act_rows = hf.active_rows;
-    bt.act_chunks = hf.active_chunks;
-    dsa.bt = bt;
-    gsa.bt = bt;
-    if (!stop && !fused) {
-      const int64_t s0c = g_launches.load();
-      pt.begin(PH_SCAN);
-      if (mixed) {
-        if constexpr (sizeof(real) == 8) {
-          msa.bt = bt;
-          if (ly.mixed_rc) {
-            rca.lin.bt = bt;
-            DEER_CK(launch_mixed_apply_rc(rca, msa, st));
-          } else {
-            DEER_CK(launch_dense_scan_mixed(msa, st));
-          }
-        }
-      } else if (o->jac == DEER_JAC_FULL) {
-        if (o->damp == DEER_DAMP_ELK && o->damp_param > 0.0) {
-          // dense ELK: Kalman-filter damping of the linearised step (A, b rewritten). The
-          // covariance recursion runs in parallel over time (chunk elements, carry) when
-          // the sequences are long (8 or more chunks each on average) and too few to fill
-          // the GPU on their own (under 1024), as one chain per sequence otherwise
-          ElkDenseArgs<real> ea{bt, d, la.A, la.b, (real)o->damp_param};
-          if (bt.n_act < 1024 && bt.act_chunks >= 8 * bt.n_act) {
-            ea.cov_agg = reinterpret_cast<real*>(ws + ly.cov_agg);
-            ea.cov_in = reinterpret_cast<real*>(ws + ly.cov_in);
-          }
-          DEER_CK(launch_elk_dense<real>(ea, st));
-        }
-        DEER_CK(launch_dense_scan<real>(dsa, st));
-      } else if (lookback) {
-        lba.bt = bt;
-        lba.epoch += 1;
-        // round-robin tile order assumes every sequence has the same chunks to solve,
-        // which a sliding window breaks
-        lba.cps = window ? 0 : uniform_chunks;
-        DEER_CK(launch_diag_lookback<real>(lba, st));
-      } else {
-        DEER_CK(launch_diag_scan<real>(gsa, st));
+    Batch gb = bt;  // upper bounds: the sizes of the whole problem
+    gb.live = flags;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // the graph is recorded on a private stream (the caller's may be the legacy default
+    // stream, which cannot capture) and launched on the caller's
+    cudaStream_t cs = nullptr;
+    cudaError_t ge = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (ge == cudaSuccess) ge = cudaGraphCreate(&graph, 0);
+    cudaGraphConditionalHandle cond = 0;
+    int64_t body_launches = 0;
+    const int64_t lg0 = g_launches.load();
+    if (ge == cudaSuccess)
+      ge = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault);
+    cudaGraphNode_t gate_node = nullptr, while_node = nullptr;
+    if (ge == cudaSuccess) {
+      // the gate: one kernel node
+      ge = cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal);
+      if (ge == cudaSuccess) {
+        const cudaError_t le = launch_loop_gate(flags, max_iters, o->reset, cond, cs);
+        cudaGraph_t g2 = nullptr;
+        ge = cudaStreamEndCapture(cs, &g2);
+        if (ge == cudaSuccess) ge = le;
       }
-      pt.end(PH_SCAN);
-      scan_launches = g_launches.load() - s0c;
     }
-    if (pt.on) {
+    if (ge == cudaSuccess) {
+      size_t nn = 0;
+      ge = cudaGraphGetNodes(graph, nullptr, &nn);
+      if (ge == cudaSuccess && nn == 1) ge = cudaGraphGetNodes(graph, &gate_node, &nn);
+      else if (ge == cudaSuccess) ge = cudaErrorInvalidValue;
+    }
+    cudaGraph_t body = nullptr;
+    if (ge == cudaSuccess) {
+      cudaGraphNodeParams cp{};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = cond;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      ge = cudaGraphAddNode(&while_node, graph, &gate_node, nullptr, 1, &cp);
+      if (ge == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    if (ge == cudaSuccess) {
+      ge = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal);
+      if (ge == cudaSuccess) {
+        const int64_t lb0 = g_launches.load();
+        lst = cs;
+        cudaError_t le = fused ? carry_step(gb) : scan_step(gb, false);
+        if (le == cudaSuccess) le = lin_step(gb, 1);
+        CheckArgs cb = ca;
+        cb.set_cond = 1;
+        cb.cond = cond;
+        if (le == cudaSuccess) le = launch_check(cb, cs);
+        lst = st;
+        body_launches = g_launches.load() - lb0;
+        cudaGraph_t g2 = nullptr;
+        ge = cudaStreamEndCapture(cs, &g2);
+        if (ge == cudaSuccess) ge = le;
+      }
+    }
+    if (ge == cudaSuccess) ge = cudaGraphInstantiate(&exec, graph, 0);
+    // the launches recorded while capturing are counted as they run (below)
+    g_launches.store(lg0);
+    if (ge == cudaSuccess) ge = cudaGraphLaunch(exec, st);
+    if (ge == cudaSuccess)
+      ge = cudaMemcpyAsync(&hf, flags, sizeof(Flags), cudaMemcpyDeviceToHost, st);
+    if (ge == cudaSuccess) ge = cudaStreamSynchronize(st);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+    if (ge != cudaSuccess) return cuda_fail(ge, "device-resident Newton loop");
+    // gate, then one body per check after the first
+    note_launch((int)(1 + body_launches * (int64_t)(hf.iter - 1)));
+    const int last = hf.iter - 1;  // index of the last check
+    if (hf.bad_input) status = DEER_ERR_INVALID;
+    else if (hf.timeout) status = DEER_ERR_TIMEOUT;
+    else if (hf.n_nonfinite > 0 && !o->reset) status = DEER_ERR_NONFINITE;
+    else if (hf.n_active == 0) status = DEER_OK;
+    else if (last >= max_iters) status = DEER_NOT_CONVERGED;
+  } else {
+    int64_t lin_rows = N;  // rows linearised in the current iteration
+    for (int it = 0;; ++it) {
+      int64_t carry_launches = 0;
+      if (fused && it > 0) {
+        const int64_t c0l = g_launches.load();
+        pt.begin(PH_SCAN);
+        DEER_CK(carry_step(bt));
+        pt.end(PH_SCAN);
+        carry_launches = g_launches.load() - c0l;
+      }
+      const int64_t l0 = g_launches.load();
+      pt.begin(PH_LIN);
+      DEER_CK(lin_step(bt, it));
+      pt.end(PH_LIN);
+      const int64_t l1 = g_launches.load();
+      ca.it = it;
+      pt.begin(PH_CHECK);
+      DEER_CK(launch_check(ca, st));
+      pt.end(PH_CHECK);
+      DEER_CK(cudaMemcpyAsync(&hf, flags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
       DEER_CK(cudaStreamSynchronize(st));
-      const int64_t launches[PH_N] = {0, l1 - l0, 1, scan_launches};
-      const int64_t rows[PH_N] = {0, lin_rows, (int64_t)B,
-                                  fused ? (carry_launches ? lin_rows : 0)
-                                        : (stop ? 0 : (int64_t)hf.active_rows)};
-      pt.collect(launches, rows);
+      bool stop = false;
+      if (hf.bad_input) { status = DEER_ERR_INVALID; stop = true; }
+      else if (hf.timeout) { status = DEER_ERR_TIMEOUT; stop = true; }
+      else if (hf.n_nonfinite > 0 && !o->reset) { status = DEER_ERR_NONFINITE; stop = true; }
+      else if (hf.n_active == 0) stop = true;
+      else if (it >= max_iters) { status = DEER_NOT_CONVERGED; stop = true; }
+      int64_t scan_launches = carry_launches;
+      bt.set_counts(hf.n_active, hf.active_rows, hf.active_chunks);
+      if (!stop && !fused) {
+        const int64_t s0c = g_launches.load();
+        pt.begin(PH_SCAN);
+        DEER_CK(scan_step(bt, true));
+        pt.end(PH_SCAN);
+        scan_launches = g_launches.load() - s0c;
+      }
+      if (pt.on) {
+        DEER_CK(cudaStreamSynchronize(st));
+        const int64_t launches[PH_N] = {0, l1 - l0, 1, scan_launches};
+        const int64_t rows[PH_N] = {0, lin_rows, (int64_t)B,
+                                    fused ? (carry_launches ? lin_rows : 0)
+                                          : (stop ? 0 : (int64_t)hf.active_rows)};
+        pt.collect(launches, rows);
+      }
+      lin_rows = hf.active_rows;
+      if (stop) break;
     }
-    lin_rows = hf.active_rows;
-    if (stop) break;
   }
 
   if (info_h && B > 0) {
@@ -1250,7 +1361,7 @@ deer_status deer_selftest_wait_timeout(deer_stream_t stream) {
                          reinterpret_cast<unsigned*>(ws + o_ticket),
                          reinterpret_cast<unsigned*>(ws + o_flags),
                          reinterpret_cast<float*>(ws + o_agg),
-                         reinterpret_cast<float*>(ws + o_pre), 1u, 0,
+                         reinterpret_cast<float*>(ws + o_pre), 1u, nullptr, 0,
                          reinterpret_cast<Flags*>(ws + o_status), 0, 0.f};
     if (launch_diag_lookback<float>(la, st, 1u) != cudaSuccess) {
       ret = DEER_ERR_CUDA;
@@ -1533,9 +1644,7 @@ static deer_status solve_noalloc_impl(const deer_dynamics* f, int64_t B, int64_t
     else if (hf.n_nonfinite > 0 && !o->reset) { status = DEER_ERR_NONFINITE; stop = true; }
     else if (hf.n_active == 0) stop = true;
     else if (it >= max_iters) { status = DEER_NOT_CONVERGED; stop = true; }
-    bt.n_act = hf.n_active;
-    bt.act_rows = hf.active_rows;
-    bt.act_chunks = hf.active_chunks;
+    bt.set_counts(hf.n_active, hf.active_rows, hf.active_chunks);
     if (stop) break;
     if (o->jac == DEER_JAC_FULL) {
       dsa.bt = bt;

@@ -37,6 +37,8 @@ struct Flags {                  // read back by the host once per iteration
   int32_t bad_input;            // set by set-up kernels that reject their inputs
   long long active_rows;        // rows of the sequences still active after the check
   long long active_chunks;      // scan chunks of those sequences
+  int32_t iter;                 // convergence checks done (device-resident loop)
+  int32_t pad_;
 };
 
 // Everything a kernel needs to evaluate f_t for a row of the packed batch.
@@ -68,10 +70,39 @@ struct Batch {
   const int64_t* act_seq;        // [n_act] active sequence ids, ascending
   const int64_t* act_row_off;    // [n_act+1] exclusive prefix of their lengths
   const int64_t* act_chunk_off;  // [n_act+1] exclusive prefix of their chunk counts
-  int64_t n_act, act_rows, act_chunks;  // sizes for the current launch
+  // sizes of the active set for the current launch, read through n_act() / act_rows() /
+  // act_chunks(): the host's values, or, when `live` is set (the Newton loop running on
+  // the device as a CUDA graph), the ones the last convergence check wrote to device
+  // memory. The host's values are then upper bounds that size the grids.
+  int64_t n_act_, act_rows_, act_chunks_;
+  const Flags* live = nullptr;
   // sliding window: [B] first chunk still solved per sequence (>= chunk_first); nullptr =
   // whole sequences. Active rows / chunks of a sequence start at its window.
   const int64_t* win_chunk = nullptr;
+
+  __host__ __device__ __forceinline__ int64_t n_act() const {
+#ifdef __CUDA_ARCH__
+    if (live) return (int64_t)live->n_active;
+#endif
+    return n_act_;
+  }
+  __host__ __device__ __forceinline__ int64_t act_rows() const {
+#ifdef __CUDA_ARCH__
+    if (live) return (int64_t)live->active_rows;
+#endif
+    return act_rows_;
+  }
+  __host__ __device__ __forceinline__ int64_t act_chunks() const {
+#ifdef __CUDA_ARCH__
+    if (live) return (int64_t)live->active_chunks;
+#endif
+    return act_chunks_;
+  }
+  void set_counts(int64_t n, int64_t rows, int64_t chunks) {
+    n_act_ = n;
+    act_rows_ = rows;
+    act_chunks_ = chunks;
+  }
 };
 
 __device__ __forceinline__ int64_t win_first(const Batch& bt, int64_t seq) {
@@ -105,7 +136,7 @@ __device__ __forceinline__ int64_t find_k(const int64_t* __restrict__ off, int64
 // active row index -> (sequence, packed row)
 __device__ __forceinline__ void act_row(const Batch& bt, int64_t ar, int64_t& seq,
                                         int64_t& row) {
-  const int64_t k = find_k(bt.act_row_off, bt.n_act, ar);
+  const int64_t k = find_k(bt.act_row_off, bt.n_act(), ar);
   seq = __ldg(bt.act_seq + k);
   const int64_t j0 = win_first(bt, seq) - __ldg(bt.chunk_first + seq);
   row = __ldg(bt.offsets + seq) + (j0 << bt.log2L) + (ar - __ldg(bt.act_row_off + k));
@@ -114,7 +145,7 @@ __device__ __forceinline__ void act_row(const Batch& bt, int64_t ar, int64_t& se
 // active chunk index -> (sequence, global chunk index, first row, row count)
 __device__ __forceinline__ void act_chunk(const Batch& bt, int64_t ac, int64_t& seq,
                                           int64_t& c, int64_t& r0, int32_t& n) {
-  const int64_t k = find_k(bt.act_chunk_off, bt.n_act, ac);
+  const int64_t k = find_k(bt.act_chunk_off, bt.n_act(), ac);
   seq = __ldg(bt.act_seq + k);
   const int64_t cf = __ldg(bt.chunk_first + seq);
   const int64_t j = (win_first(bt, seq) - cf) + (ac - __ldg(bt.act_chunk_off + k));

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kFusedBlock) k_dense_fused(FusedArgs<real> a) 
   __shared__ real sN[D][kFusedBlock];
   const int tid = threadIdx.x;
   const int64_t ac = blockIdx.x * (int64_t)blockDim.x + tid;
-  const bool valid = ac < a.bt.act_chunks;
+  const bool valid = ac < a.bt.act_chunks();
   int64_t seq = 0;
   real mx = real(0), sq = real(0);  // residual statistics in the path's own precision
   unsigned long long key = 0ull;     // first failing row (sliding window)
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
   const int grp = threadIdx.x / D, i = threadIdx.x % D;
   const unsigned gm = ((1u << D) - 1u) << ((threadIdx.x & 31) & ~(D - 1));
   const int64_t ac = blockIdx.x * (int64_t)GPB + grp;
-  const bool valid = ac < a.bt.act_chunks;
+  const bool valid = ac < a.bt.act_chunks();
   int64_t seq = 0;
   real mx = real(0), sq = real(0);  // residual statistics in the path's own precision
   unsigned long long key = 0ull;     // first failing row (sliding window)
@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(128) k_dense_fused_carry(FusedArgs<real> a) {
   constexpr int V = (E + 2 * D) * (int)(sizeof(real) / 4);
   constexpr int K = V >= 64 ? 1 : (64 / V > 8 ? 8 : 64 / V);
   const int64_t kq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (kq >= a.bt.n_act) return;
+  if (kq >= a.bt.n_act()) return;
   const int64_t seq = a.bt.act_seq[kq];
   const int64_t cf = a.bt.chunk_first[seq], c0 = win_first(a.bt, seq);
   const int64_t c1 = a.bt.chunk_first[seq + 1];
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(128) k_fused_carry_lps(FusedArgs<real> a) {
   const int grp = threadIdx.x / D, i = threadIdx.x % D;
   const unsigned gm = ((1u << D) - 1u) << ((threadIdx.x & 31) & ~(D - 1));
   const int64_t kq = blockIdx.x * (int64_t)GPB + grp;
-  if (kq >= a.bt.n_act) return;  // whole groups
+  if (kq >= a.bt.n_act()) return;  // whole groups
   const int64_t seq = a.bt.act_seq[kq];
   const int64_t cf = a.bt.chunk_first[seq], c0 = win_first(a.bt, seq);
   const int64_t c1 = a.bt.chunk_first[seq + 1];
@@ -674,7 +674,7 @@ static void fused_launch(const FusedArgs<real>& a, cudaStream_t st) {
   constexpr bool MA = KIND == DEER_F_MASSACTION_EULER || KIND == DEER_F_MASSACTION_RK4;
   if constexpr (MA && (D == 4 || D == 8)) {
     constexpr bool RK4 = KIND == DEER_F_MASSACTION_RK4;
-    const unsigned g = grid_for(a.bt.act_chunks, kFusedBlock / D);
+    const unsigned g = grid_for(a.bt.act_chunks(), kFusedBlock / D);
     if (a.slo) {
       if (a.mode == 0) k_fused_ma_lps<real, D, RK4, 0, true><<<g, kFusedBlock, 0, st>>>(a);
       else k_fused_ma_lps<real, D, RK4, 1, true><<<g, kFusedBlock, 0, st>>>(a);
@@ -683,7 +683,7 @@ static void fused_launch(const FusedArgs<real>& a, cudaStream_t st) {
       else k_fused_ma_lps<real, D, RK4, 1, false><<<g, kFusedBlock, 0, st>>>(a);
     }
   } else {
-    const unsigned g = grid_for(a.bt.act_chunks, kFusedBlock);
+    const unsigned g = grid_for(a.bt.act_chunks(), kFusedBlock);
     if (a.mode == 0) k_dense_fused<real, D, KIND, 0><<<g, kFusedBlock, 0, st>>>(a);
     else k_dense_fused<real, D, KIND, 1><<<g, kFusedBlock, 0, st>>>(a);
   }
@@ -707,7 +707,7 @@ static cudaError_t fused_kind(const FusedArgs<real>& a, cudaStream_t st) {
 
 template <class real>
 cudaError_t launch_dense_fused(const FusedArgs<real>& a, cudaStream_t st) {
-  if (a.bt.act_chunks == 0) return cudaSuccess;
+  if (a.bt.act_chunks() == 0) return cudaSuccess;
   switch (a.dv.kind) {
     case DEER_F_BRUSSELATOR_EULER: return fused_kind<real, DEER_F_BRUSSELATOR_EULER>(a, st);
     case DEER_F_MASSACTION_EULER: return fused_kind<real, DEER_F_MASSACTION_EULER>(a, st);
@@ -719,22 +719,22 @@ cudaError_t launch_dense_fused(const FusedArgs<real>& a, cudaStream_t st) {
 
 template <class real>
 cudaError_t launch_dense_fused_carry(const FusedArgs<real>& a, cudaStream_t st) {
-  if (a.bt.n_act == 0) return cudaSuccess;
+  if (a.bt.n_act() == 0) return cudaSuccess;
   const bool ma = a.dv.kind == DEER_F_MASSACTION_EULER || a.dv.kind == DEER_F_MASSACTION_RK4;
   if (ma && (a.dv.d == 4 || a.dv.d == 8)) {
     // same kernels as the fused pass selects (lane-per-species layout of the aggregates is
     // row-major either way)
     if (a.slo) {
-      if (a.dv.d == 4) k_fused_carry_lps<real, 4, true><<<grid_for(a.bt.n_act, 32), 128, 0, st>>>(a);
-      else k_fused_carry_lps<real, 8, true><<<grid_for(a.bt.n_act, 16), 128, 0, st>>>(a);
+      if (a.dv.d == 4) k_fused_carry_lps<real, 4, true><<<grid_for(a.bt.n_act(), 32), 128, 0, st>>>(a);
+      else k_fused_carry_lps<real, 8, true><<<grid_for(a.bt.n_act(), 16), 128, 0, st>>>(a);
     } else {
-      if (a.dv.d == 4) k_fused_carry_lps<real, 4, false><<<grid_for(a.bt.n_act, 32), 128, 0, st>>>(a);
-      else k_fused_carry_lps<real, 8, false><<<grid_for(a.bt.n_act, 16), 128, 0, st>>>(a);
+      if (a.dv.d == 4) k_fused_carry_lps<real, 4, false><<<grid_for(a.bt.n_act(), 32), 128, 0, st>>>(a);
+      else k_fused_carry_lps<real, 8, false><<<grid_for(a.bt.n_act(), 16), 128, 0, st>>>(a);
     }
     note_launch();
     return cudaGetLastError();
   }
-  const unsigned g = grid_for(a.bt.n_act, 128);
+  const unsigned g = grid_for(a.bt.n_act(), 128);
   switch (a.dv.d) {
     case 1: k_dense_fused_carry<real, 1><<<g, 128, 0, st>>>(a); break;
     case 2: k_dense_fused_carry<real, 2><<<g, 128, 0, st>>>(a); break;

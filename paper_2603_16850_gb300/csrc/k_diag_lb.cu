@@ -263,13 +263,14 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 8 : 4) k_diag_lb(Diag
   __shared__ real sB[Q][D];
   __shared__ real s_in[D];
   __shared__ unsigned s_tile;
+  if (a.epoch_from) a.epoch = (unsigned)a.epoch_from->iter;
   if (threadIdx.x == 0) s_tile = atomicAdd(a.ticket, 1u);
   __syncthreads();
   const int64_t tk = s_tile;
-  if (tk >= a.bt.act_chunks) return;  // uniform over the CTA
+  if (tk >= a.bt.act_chunks()) return;  // uniform over the CTA
   // ticket -> active chunk index: sequence-major, or round-robin over the sequences when
   // they all have cps chunks (a predecessor tile always holds a smaller ticket either way)
-  const int64_t ac = a.cps > 0 ? (tk % a.bt.n_act) * a.cps + tk / a.bt.n_act : tk;
+  const int64_t ac = a.cps > 0 ? (tk % a.bt.n_act()) * a.cps + tk / a.bt.n_act() : tk;
   int64_t seq, c, r0;
   int n;
   act_chunk(a.bt, ac, seq, c, r0, n);
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 8 : 4) k_diag_lb(Diag
 template <class real>
 cudaError_t launch_diag_lookback(const DiagLBArgs<real>& a, cudaStream_t st,
                                  unsigned first_ticket) {
-  if (a.bt.act_chunks == 0) return cudaSuccess;
+  if (a.bt.act_chunks() == 0) return cudaSuccess;
   // tiles are dealt from first_ticket on (0 in every solve; the wait self-test starts at 1,
   // so that no CTA ever publishes tile 0)
   static const unsigned kOne = 1u;
@@ -350,8 +351,8 @@ cudaError_t launch_diag_lookback(const DiagLBArgs<real>& a, cudaStream_t st,
                                                              cudaMemcpyHostToDevice, st)
                                            : cudaErrorInvalidValue);
   if (e != cudaSuccess) return e;
-  if ((int64_t)first_ticket >= a.bt.act_chunks) return cudaErrorInvalidValue;
-  const unsigned grid = (unsigned)(a.bt.act_chunks - first_ticket);
+  if ((int64_t)first_ticket >= a.bt.act_chunks()) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)(a.bt.act_chunks() - first_ticket);
   switch (a.d) {
     case 4: k_diag_lb<real, 4><<<grid, 256, 0, st>>>(a); break;
     case 8: k_diag_lb<real, 8><<<grid, 256, 0, st>>>(a); break;

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(128) k_elk_dense(ElkDenseArgs<real> a) {
   real (*Am)[RS] = sA[grp];
   real (*Sp)[RS] = sS[grp];
   if constexpr (CHUNKED) {
-    if (k >= a.bt.act_chunks) return;  // whole groups
+    if (k >= a.bt.act_chunks()) return;  // whole groups
     int64_t seq, c;
     int n;
     act_chunk(a.bt, k, seq, c, r_begin, n);
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(128) k_elk_dense(ElkDenseArgs<real> a) {
 #pragma unroll
     for (int j = 0; j < D; ++j) P[i][j] = Pin[i * D + j];
   } else {
-    if (k >= a.bt.n_act) return;  // whole groups
+    if (k >= a.bt.n_act()) return;  // whole groups
     const int64_t seq = a.bt.act_seq[k];
     const int64_t cf = a.bt.chunk_first[seq];
     r_begin = a.bt.offsets[seq] + ((win_first(a.bt, seq) - cf) << a.bt.log2L);
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(128) k_elk_cov_chunk(ElkDenseArgs<real> a) {
   const unsigned gm = D >= 32 ? 0xffffffffu
                               : (((1u << D) - 1u) << ((threadIdx.x & 31) & ~(D - 1)));
   const int64_t k = blockIdx.x * (int64_t)G + grp;
-  if (k >= a.bt.act_chunks) return;  // whole groups
+  if (k >= a.bt.act_chunks()) return;  // whole groups
   int64_t seq, c, r0;
   int n;
   act_chunk(a.bt, k, seq, c, r0, n);
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(128) k_elk_cov_carry(ElkDenseArgs<real> a) {
   const unsigned gm = D >= 32 ? 0xffffffffu
                               : (((1u << D) - 1u) << ((threadIdx.x & 31) & ~(D - 1)));
   const int64_t kq = blockIdx.x * (int64_t)G + grp;
-  if (kq >= a.bt.n_act) return;  // whole groups
+  if (kq >= a.bt.n_act()) return;  // whole groups
   const int64_t seq = a.bt.act_seq[kq];
   const int64_t c0 = win_first(a.bt, seq), c1 = a.bt.chunk_first[seq + 1];
   real (*Pm)[RS] = sM[grp][0];
@@ -402,20 +402,20 @@ static void elk_dense_launch(const ElkDenseArgs<real>& a, cudaStream_t st) {
   constexpr int NT = elk_block<D>();
   constexpr int G = NT / D;
   if (a.cov_agg) {
-    const unsigned gc = grid_for(a.bt.act_chunks, G);
+    const unsigned gc = grid_for(a.bt.act_chunks(), G);
     k_elk_cov_chunk<real, D><<<gc, NT, 0, st>>>(a);
-    k_elk_cov_carry<real, D><<<grid_for(a.bt.n_act, G), NT, 0, st>>>(a);
+    k_elk_cov_carry<real, D><<<grid_for(a.bt.n_act(), G), NT, 0, st>>>(a);
     k_elk_dense<real, D, true><<<gc, NT, 0, st>>>(a);
     note_launch(3);
   } else {
-    k_elk_dense<real, D, false><<<grid_for(a.bt.n_act, G), NT, 0, st>>>(a);
+    k_elk_dense<real, D, false><<<grid_for(a.bt.n_act(), G), NT, 0, st>>>(a);
     note_launch();
   }
 }
 
 template <class real>
 cudaError_t launch_elk_dense(const ElkDenseArgs<real>& a, cudaStream_t st) {
-  if (a.bt.n_act == 0) return cudaSuccess;
+  if (a.bt.n_act() == 0) return cudaSuccess;
   switch (a.d) {
     case 1: elk_dense_launch<real, 1>(a, st); break;
     case 2: elk_dense_launch<real, 2>(a, st); break;

@@ -54,12 +54,12 @@ __global__ void __launch_bounds__(kGThreads) k_gru_lin_tiled(GruTileArgs a) {
     S.diag_h[tid] = Uh[tid * kGD + tid];
   }
   __syncthreads();
-  const int64_t n_tiles = (a.bt.act_rows + kGT - 1) / kGT;
+  const int64_t n_tiles = (a.bt.act_rows() + kGT - 1) / kGT;
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     // load h (previous states) of the tile's 64 rows, transposed
     if (tid < kGT) {
       const int64_t ar = tile * kGT + tid;
-      const bool v = ar < a.bt.act_rows;
+      const bool v = ar < a.bt.act_rows();
       int64_t seq = 0, row = 0;
       if (v) act_row(a.bt, ar, seq, row);
       S.rseq[tid] = seq;
@@ -296,7 +296,7 @@ cudaError_t launch_gru_xproj(const float* W, const float* x, int64_t N, float* o
 }
 
 cudaError_t launch_gru_lin_tiled(const GruTileArgs& a, cudaStream_t st) {
-  if (a.bt.act_rows == 0) return cudaSuccess;
+  if (a.bt.act_rows() == 0) return cudaSuccess;
   const size_t smem = sizeof(GruSmem);
   static bool configured = false;
   if (!configured) {
@@ -306,7 +306,7 @@ cudaError_t launch_gru_lin_tiled(const GruTileArgs& a, cudaStream_t st) {
     configured = true;
   }
   const int g = persistent_grid((const void*)k_gru_lin_tiled, kGThreads, smem);
-  const int64_t tiles = (a.bt.act_rows + kGT - 1) / kGT;
+  const int64_t tiles = (a.bt.act_rows() + kGT - 1) / kGT;
   k_gru_lin_tiled<<<(unsigned)(tiles < g ? tiles : g), kGThreads, smem, st>>>(a);
   note_launch();
   return cudaGetLastError();

@@ -157,11 +157,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gru_lin_tc(GruTileArgs a) {
     return s_ok != 0;
   };
 
-  const int64_t n_tiles = (a.bt.act_rows + kTM - 1) / kTM;
+  const int64_t n_tiles = (a.bt.act_rows() + kTM - 1) / kTM;
   bool ok = true;
   for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
     const int64_t ar = tile * kTM + rl;
-    const bool v = ar < a.bt.act_rows;
+    const bool v = ar < a.bt.act_rows();
     int64_t seq = 0, row = 0;
     if (v) act_row(a.bt, ar, seq, row);
     const float* hp = a.s0;
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gru_lin_tc(GruTileArgs a) {
 }
 
 cudaError_t launch_gru_lin_tc(const GruTileArgs& a, cudaStream_t st) {
-  if (a.bt.act_rows == 0) return cudaSuccess;
+  if (a.bt.act_rows() == 0) return cudaSuccess;
   const int smem = (int)sizeof(TcSmem);
   static bool configured = false;
   if (!configured) {
@@ -305,7 +305,7 @@ cudaError_t launch_gru_lin_tc(const GruTileArgs& a, cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t tiles = (a.bt.act_rows + kTM - 1) / kTM;
+  const int64_t tiles = (a.bt.act_rows() + kTM - 1) / kTM;
   const int64_t g = tiles < sms ? tiles : sms;
   k_gru_lin_tc<<<(unsigned)(g > 0 ? g : 1), kThreads, smem, st>>>(a);
   note_launch();

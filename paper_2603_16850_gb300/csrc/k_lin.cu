@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(128) k_lin_ma(LinArgs<real> a) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t ar = tid / LPR;
   const int h = LPR == 2 ? (int)(tid & 1) : 0;
-  const bool valid = ar < a.bt.act_rows;
+  const bool valid = ar < a.bt.act_rows();
   int64_t seq = 0, row = 0;
   if (valid) act_row(a.bt, ar, seq, row);
   real mx = real(0), sq = real(0);
@@ -418,7 +418,7 @@ cudaError_t launch_lin_ma_wide(const LinArgs<real>& a, cudaStream_t st);
 
 template <class real, bool RK4, int JAC>
 static cudaError_t lin_ma_jac(const LinArgs<real>& a, cudaStream_t st) {
-  const unsigned g = grid_for(a.bt.act_rows, 128);
+  const unsigned g = grid_for(a.bt.act_rows(), 128);
   switch (a.dv.d) {
     case 2: k_lin_ma<real, 2, 1, RK4, JAC><<<g, 128, 0, st>>>(a); break;
     case 4: k_lin_ma<real, 4, 1, RK4, JAC><<<g, 128, 0, st>>>(a); break;
@@ -426,7 +426,7 @@ static cudaError_t lin_ma_jac(const LinArgs<real>& a, cudaStream_t st) {
       if constexpr (sizeof(real) == 4) {
         k_lin_ma<real, 8, 1, RK4, JAC><<<g, 128, 0, st>>>(a);
       } else {
-        k_lin_ma<real, 8, 2, RK4, JAC><<<grid_for(a.bt.act_rows * 2, 128), 128, 0, st>>>(a);
+        k_lin_ma<real, 8, 2, RK4, JAC><<<grid_for(a.bt.act_rows() * 2, 128), 128, 0, st>>>(a);
       }
       break;
     case 16:
@@ -449,7 +449,7 @@ static cudaError_t lin_ma(const LinArgs<real>& a, cudaStream_t st) {
 
 template <class real>
 cudaError_t launch_linearize(const LinArgs<real>& a, cudaStream_t st) {
-  if (a.bt.act_rows == 0) return cudaSuccess;
+  if (a.bt.act_rows() == 0) return cudaSuccess;
   switch (a.dv.kind) {
     case DEER_F_MASSACTION_EULER: return lin_ma<real, false>(a, st);
     case DEER_F_MASSACTION_RK4: return lin_ma<real, true>(a, st);
@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
   unsigned long long key = 0ull;  // first failing row (sliding window)
   for (int ri = 0; ri < kMaRows; ++ri) {
     const int64_t ar = ar0 + ri;
-    if (ar >= a.bt.act_rows) break;  // uniform over the group
+    if (ar >= a.bt.act_rows()) break;  // uniform over the group
     int64_t seq, row;
     act_row(a.bt, ar, seq, row);
     if (seq != cur) {
@@ -690,7 +690,7 @@ cudaError_t launch_lin_ma_wide(const LinArgs<real>& a, cudaStream_t st) {
   const bool rk4 = a.dv.kind == DEER_F_MASSACTION_RK4;
   const int d = a.dv.d;
   const int64_t rows_per_block = 128 / d * kMaRows;
-  const unsigned g = grid_for(a.bt.act_rows, (int)rows_per_block);
+  const unsigned g = grid_for(a.bt.act_rows(), (int)rows_per_block);
   if (d == 16) {
     if (rk4) k_lin_ma_wide<real, 16, true, JAC><<<g, 128, 0, st>>>(a);
     else k_lin_ma_wide<real, 16, false, JAC><<<g, 128, 0, st>>>(a);

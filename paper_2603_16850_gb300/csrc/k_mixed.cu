@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(128) k_lin_ma_mixed(MixedLinArgs a) {
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gm = gmask_mixed<D>();
   const int64_t ar = blockIdx.x * (int64_t)GROUPS + grp;
-  const bool valid = ar < a.bt.act_rows;
+  const bool valid = ar < a.bt.act_rows();
   int64_t seq = 0, row = 0;
   if (valid) act_row(a.bt, ar, seq, row);
   const double s_prev = valid ? (row == __ldg(a.bt.offsets + seq) ? a.s0[seq * D + lane]
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(128) k_mixed_chunk(MixedScanArgs a) {
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gm = gmask_mixed<D>();
   const int64_t ac = blockIdx.x * (int64_t)G + grp;
-  const bool valid = ac < a.bt.act_chunks;
+  const bool valid = ac < a.bt.act_chunks();
   int64_t seq = 0, c = 0, r0 = 0;
   int n = 0;
   if (valid) act_chunk(a.bt, ac, seq, c, r0, n);
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(128) k_mixed_carry(MixedScanArgs a) {
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gm = gmask_mixed<D>();
   const int64_t kq = blockIdx.x * (int64_t)G + grp;
-  const bool valid = kq < a.bt.n_act;
+  const bool valid = kq < a.bt.n_act();
   const int64_t seq = valid ? a.bt.act_seq[kq] : 0;
   const int64_t c0 = valid ? win_first(a.bt, seq) : 0;
   const int64_t c1 = valid ? a.bt.chunk_first[seq + 1] : 0;
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(128) k_mixed_apply(MixedScanArgs a) {
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gm = gmask_mixed<D>();
   const int64_t ac = blockIdx.x * (int64_t)G + grp;
-  const bool valid = ac < a.bt.act_chunks;
+  const bool valid = ac < a.bt.act_chunks();
   int64_t seq = 0, c = 0, r0 = 0;
   int n = 0;
   if (valid) act_chunk(a.bt, ac, seq, c, r0, n);
@@ -409,7 +409,7 @@ __device__ __forceinline__ void frag_matvec16(uint32_t e0, uint32_t e1, uint32_t
 __global__ void __launch_bounds__(128) k_mixed_chunk_tc16(MixedScanArgs a) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int64_t ac = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (ac >= a.bt.act_chunks) return;  // whole warps
+  if (ac >= a.bt.act_chunks()) return;  // whole warps
   int64_t seq, c, r0;
   int n;
   act_chunk(a.bt, ac, seq, c, r0, n);
@@ -456,7 +456,7 @@ __device__ __forceinline__ bool overflowed(double x) {
 __global__ void __launch_bounds__(128) k_mixed_apply_tc16(MixedScanArgs a) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int64_t ac = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (ac >= a.bt.act_chunks) return;  // whole warps
+  if (ac >= a.bt.act_chunks()) return;  // whole warps
   int64_t seq, c, r0;
   int n;
   act_chunk(a.bt, ac, seq, c, r0, n);
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_mixed_lin_agg16(MixedRcArgs r
   const int half = l32 >> 4, lane = l32 & 15, g = l32 >> 2, tq = l32 & 3;
   const unsigned gm = gmask_mixed<16>();
   const int64_t ac = blockIdx.x * (int64_t)kRcWarps + warp;
-  if (ac >= a.bt.act_chunks) return;  // whole warps
+  if (ac >= a.bt.act_chunks()) return;  // whole warps
   RcSmem& S = smem[warp];
   int64_t seq, c, r0;
   int n;
@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_mixed_apply_rc16(MixedRcArgs 
   const int half = l32 >> 4, lane = l32 & 15;
   const unsigned gm = gmask_mixed<16>();
   const int64_t ac = blockIdx.x * (int64_t)kRcWarps + warp;
-  if (ac >= a.bt.act_chunks) return;  // whole warps
+  if (ac >= a.bt.act_chunks()) return;  // whole warps
   RcSmem& S = smem[warp];
   int64_t seq, c, r0;
   int n;
@@ -736,9 +736,9 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_mixed_apply_rc16(MixedRcArgs 
 }
 
 cudaError_t launch_mixed_lin_agg(const MixedRcArgs& a, cudaStream_t st) {
-  if (a.lin.bt.act_chunks == 0) return cudaSuccess;
+  if (a.lin.bt.act_chunks() == 0) return cudaSuccess;
   if (a.lin.dv.d != 16) return cudaErrorInvalidValue;
-  const unsigned g = grid_for(a.lin.bt.act_chunks, kRcWarps);
+  const unsigned g = grid_for(a.lin.bt.act_chunks(), kRcWarps);
   if (a.lin.dv.kind == DEER_F_MASSACTION_RK4) k_mixed_lin_agg16<true><<<g, 32 * kRcWarps, 0, st>>>(a);
   else k_mixed_lin_agg16<false><<<g, 32 * kRcWarps, 0, st>>>(a);
   note_launch();
@@ -747,10 +747,10 @@ cudaError_t launch_mixed_lin_agg(const MixedRcArgs& a, cudaStream_t st) {
 
 cudaError_t launch_mixed_apply_rc(const MixedRcArgs& a, const MixedScanArgs& carry,
                                   cudaStream_t st) {
-  if (a.lin.bt.act_chunks == 0) return cudaSuccess;
+  if (a.lin.bt.act_chunks() == 0) return cudaSuccess;
   if (a.lin.dv.d != 16) return cudaErrorInvalidValue;
-  k_mixed_carry<16><<<grid_for(carry.bt.n_act, 128 / 16), 128, 0, st>>>(carry);
-  const unsigned g = grid_for(a.lin.bt.act_chunks, kRcWarps);
+  k_mixed_carry<16><<<grid_for(carry.bt.n_act(), 128 / 16), 128, 0, st>>>(carry);
+  const unsigned g = grid_for(a.lin.bt.act_chunks(), kRcWarps);
   if (a.lin.dv.kind == DEER_F_MASSACTION_RK4) k_mixed_apply_rc16<true><<<g, 32 * kRcWarps, 0, st>>>(a);
   else k_mixed_apply_rc16<false><<<g, 32 * kRcWarps, 0, st>>>(a);
   note_launch(2);
@@ -758,10 +758,10 @@ cudaError_t launch_mixed_apply_rc(const MixedRcArgs& a, const MixedScanArgs& car
 }
 
 cudaError_t launch_lin_ma_mixed(const MixedLinArgs& a, cudaStream_t st) {
-  if (a.bt.act_rows == 0) return cudaSuccess;
+  if (a.bt.act_rows() == 0) return cudaSuccess;
   const bool rk4 = a.dv.kind == DEER_F_MASSACTION_RK4;
   const int d = a.dv.d;
-  const unsigned g = grid_for(a.bt.act_rows, 128 / d);
+  const unsigned g = grid_for(a.bt.act_rows(), 128 / d);
   if (d == 16) {
     if (rk4) k_lin_ma_mixed<16, true><<<g, 128, 0, st>>>(a);
     else k_lin_ma_mixed<16, false><<<g, 128, 0, st>>>(a);
@@ -778,9 +778,9 @@ cudaError_t launch_lin_ma_mixed(const MixedLinArgs& a, cudaStream_t st) {
 template <int D>
 static void mixed_launch(const MixedScanArgs& a, cudaStream_t st) {
   constexpr int G = 128 / D;
-  const unsigned gs = grid_for(a.bt.n_act, G);
+  const unsigned gs = grid_for(a.bt.n_act(), G);
   if constexpr (D == 16) {
-    const unsigned gw = grid_for(a.bt.act_chunks, 4);  // one warp per chunk
+    const unsigned gw = grid_for(a.bt.act_chunks(), 4);  // one warp per chunk
     if (a.tc_mode == 2) {
       if (launch_mixed_chunk_tcgen05(a, st) != cudaSuccess) return;
     } else {
@@ -789,7 +789,7 @@ static void mixed_launch(const MixedScanArgs& a, cudaStream_t st) {
     k_mixed_carry<D><<<gs, 128, 0, st>>>(a);
     k_mixed_apply_tc16<<<gw, 128, 0, st>>>(a);
   } else {
-    const unsigned gc = grid_for(a.bt.act_chunks, G);
+    const unsigned gc = grid_for(a.bt.act_chunks(), G);
     k_mixed_chunk<D><<<gc, 128, 0, st>>>(a);
     k_mixed_carry<D><<<gs, 128, 0, st>>>(a);
     k_mixed_apply<D><<<gc, 128, 0, st>>>(a);
@@ -798,7 +798,7 @@ static void mixed_launch(const MixedScanArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_dense_scan_mixed(const MixedScanArgs& a, cudaStream_t st) {
-  if (a.bt.act_rows == 0) return cudaSuccess;
+  if (a.bt.act_rows() == 0) return cudaSuccess;
   if (a.d == 16) mixed_launch<16>(a, st);
   else if (a.d == 32) mixed_launch<32>(a, st);
   else return cudaErrorInvalidValue;

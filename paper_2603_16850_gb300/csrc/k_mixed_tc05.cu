@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kT05Threads, 1) k_mixed_chunk_tcgen05(MixedSca
   const int c_loc = tid >> 4, i = tid & 15;  // this thread's chunk of the tile, and row
   // this thread's chunk (ragged: a tile may end early)
   const int64_t ac = blockIdx.x * (int64_t)kT05Chunks + c_loc;
-  const bool has = ac < a.bt.act_chunks;
+  const bool has = ac < a.bt.act_chunks();
   int64_t seq = 0, c = 0, r0 = 0;
   int n = 0;
   if (has) act_chunk(a.bt, ac, seq, c, r0, n);
@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(kT05Threads, 1) k_mixed_chunk_tcgen05(MixedSca
 
 // enqueues the chunk pass; the caller counts the launch with the rest of its scan
 cudaError_t launch_mixed_chunk_tcgen05(const MixedScanArgs& a, cudaStream_t st) {
-  if (a.bt.act_chunks == 0) return cudaSuccess;
-  const unsigned g = grid_for(a.bt.act_chunks, kT05Chunks);
+  if (a.bt.act_chunks() == 0) return cudaSuccess;
+  const unsigned g = grid_for(a.bt.act_chunks(), kT05Chunks);
   k_mixed_chunk_tcgen05<<<g, kT05Threads, 0, st>>>(a);
   return cudaGetLastError();
 }

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(128) k_lin_rnn_wide(LinArgs<real> a) {
   unsigned long long key = 0ull;  // first failing row (sliding window)
   for (int rr_i = 0; rr_i < kRnnRows; ++rr_i) {
     const int64_t ar = ar0 + rr_i;
-    if (ar >= a.bt.act_rows) break;  // uniform over the group
+    if (ar >= a.bt.act_rows()) break;  // uniform over the group
     int64_t seq, row;
     act_row(a.bt, ar, seq, row);
     if (seq != cur) {
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(128) k_lin_rnn_wide(LinArgs<real> a) {
 template <class real, int JAC>
 static cudaError_t lin_rnn_wide(const LinArgs<real>& a, cudaStream_t st) {
   const int d = a.dv.d;
-  const unsigned g = grid_for(a.bt.act_rows, 128 / d * kRnnRows);
+  const unsigned g = grid_for(a.bt.act_rows(), 128 / d * kRnnRows);
   if (d == 16) k_lin_rnn_wide<real, 16, JAC><<<g, 128, 0, st>>>(a);
   else k_lin_rnn_wide<real, 32, JAC><<<g, 128, 0, st>>>(a);
   note_launch();

@@ -49,7 +49,34 @@ __device__ __forceinline__ void block_excl_scan3(long long& a, long long& b, lon
   a = wa + ia - a; b = wb + ib - b; c = wc + ic - c;
 }
 
+// whether the Newton loop goes on after the check of iteration `it` (the host loop's
+// stopping rules, evaluated on the device)
+__device__ __forceinline__ bool loop_goes_on(const Flags* f, int it, int max_iters,
+                                             int reset) {
+  if (f->bad_input || f->timeout) return false;
+  if (f->n_nonfinite > 0 && !reset) return false;
+  if (f->n_active == 0) return false;
+  return it < max_iters;
+}
+
+__global__ void k_loop_gate(Flags* f, int max_iters, int reset,
+                            cudaGraphConditionalHandle cond) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    cudaGraphSetConditional(cond, loop_goes_on(f, f->iter - 1, max_iters, reset) ? 1u : 0u);
+}
+
+cudaError_t launch_loop_gate(Flags* flags, int max_iters, int reset,
+                             cudaGraphConditionalHandle cond, cudaStream_t st) {
+  k_loop_gate<<<1, 32, 0, st>>>(flags, max_iters, reset, cond);
+  note_launch();
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(1024) k_check(CheckArgs a) {
+  // iteration index: the host's, or the device loop's counter (read by every thread
+  // before thread 0 advances it at the end)
+  const int it_now = a.device_it ? a.flags->iter : a.it;
+  a.it = it_now;
   const int64_t per = (a.B + blockDim.x - 1) / blockDim.x;
   const int64_t lo = threadIdx.x * per;
   const int64_t hi = lo + per < a.B ? lo + per : a.B;
@@ -125,6 +152,15 @@ __global__ void __launch_bounds__(1024) k_check(CheckArgs a) {
     a.flags->active_rows = tr;
     a.flags->active_chunks = tc;
   }
+  if (a.device_it) {
+    __syncthreads();  // every thread has read the counter
+    if (threadIdx.x == 0) {
+      a.flags->iter = it_now + 1;
+      if (a.set_cond)
+        cudaGraphSetConditional(
+            a.cond, loop_goes_on(a.flags, it_now, a.max_iters, a.reset) ? 1u : 0u);
+    }
+  }
   if (a.history && !a.compact_only && a.it < a.history_len) {
     // block reduction of the tested sequences' merit sum and largest scaled residual
     __shared__ double s_sum[32], s_max[32];
@@ -172,7 +208,7 @@ __device__ __forceinline__ real reset_val(real v, real thr, int reset) {
 template <class real, int D>
 __global__ void __launch_bounds__(128) k_dense_chunk(DenseScanArgs<real> a) {
   const int64_t ac = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (ac >= a.bt.act_chunks) return;
+  if (ac >= a.bt.act_chunks()) return;
   int64_t seq, c, r0;
   int n;
   act_chunk(a.bt, ac, seq, c, r0, n);
@@ -229,7 +265,7 @@ __global__ void __launch_bounds__(128) k_dense_chunk(DenseScanArgs<real> a) {
 template <class real, int D>
 __global__ void __launch_bounds__(128) k_dense_carry(DenseScanArgs<real> a) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= a.bt.n_act) return;
+  if (k >= a.bt.n_act()) return;
   const int64_t seq = a.bt.act_seq[k];
   const int64_t c0 = win_first(a.bt, seq), c1 = a.bt.chunk_first[seq + 1];
   real x[D];
@@ -263,7 +299,7 @@ __global__ void __launch_bounds__(128) k_dense_carry(DenseScanArgs<real> a) {
 template <class real, int D>
 __global__ void __launch_bounds__(128) k_dense_apply(DenseScanArgs<real> a) {
   const int64_t ac = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (ac >= a.bt.act_chunks) return;
+  if (ac >= a.bt.act_chunks()) return;
   int64_t seq, c, r0;
   int n;
   act_chunk(a.bt, ac, seq, c, r0, n);
@@ -293,8 +329,8 @@ __global__ void __launch_bounds__(128) k_dense_apply(DenseScanArgs<real> a) {
 
 template <class real, int D>
 static void dense_launch(const DenseScanArgs<real>& a, cudaStream_t st) {
-  const unsigned gc = grid_for(a.bt.act_chunks, 128);
-  const unsigned gs = grid_for(a.bt.n_act, 128);
+  const unsigned gc = grid_for(a.bt.act_chunks(), 128);
+  const unsigned gs = grid_for(a.bt.n_act(), 128);
   k_dense_chunk<real, D><<<gc, 128, 0, st>>>(a);
   k_dense_carry<real, D><<<gs, 128, 0, st>>>(a);
   k_dense_apply<real, D><<<gc, 128, 0, st>>>(a);
@@ -306,7 +342,7 @@ void dense_launch_wide(const DenseScanArgs<real>& a, cudaStream_t st);
 
 template <class real>
 cudaError_t launch_dense_scan(const DenseScanArgs<real>& a, cudaStream_t st) {
-  if (a.bt.act_rows == 0) return cudaSuccess;
+  if (a.bt.act_rows() == 0) return cudaSuccess;
   switch (a.d) {
     case 1: dense_launch<real, 1>(a, st); break;
     case 2: dense_launch<real, 2>(a, st); break;
@@ -333,7 +369,7 @@ __device__ __forceinline__ void diag_elem(const DiagScanArgs<real>& a, int64_t r
 template <class real>
 __global__ void __launch_bounds__(128) k_diag_chunk(DiagScanArgs<real> a) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= a.bt.act_chunks * a.d) return;
+  if (id >= a.bt.act_chunks() * a.d) return;
   const int64_t ac = id / a.d;
   const int j = (int)(id - ac * a.d);
   int64_t seq, c, r0;
@@ -353,7 +389,7 @@ __global__ void __launch_bounds__(128) k_diag_chunk(DiagScanArgs<real> a) {
 template <class real>
 __global__ void __launch_bounds__(128) k_diag_carry(DiagScanArgs<real> a) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= a.bt.n_act * a.d) return;
+  if (id >= a.bt.n_act() * a.d) return;
   const int64_t k = id / a.d;
   const int j = (int)(id - k * a.d);
   const int64_t seq = a.bt.act_seq[k];
@@ -370,7 +406,7 @@ __global__ void __launch_bounds__(128) k_diag_carry(DiagScanArgs<real> a) {
 template <class real>
 __global__ void __launch_bounds__(128) k_diag_apply(DiagScanArgs<real> a) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= a.bt.act_chunks * a.d) return;
+  if (id >= a.bt.act_chunks() * a.d) return;
   const int64_t ac = id / a.d;
   const int j = (int)(id - ac * a.d);
   int64_t seq, c, r0;
@@ -400,7 +436,7 @@ __device__ __forceinline__ void mob_elem(real at, real s2, real& m00, real& m01,
 template <class real>
 __global__ void __launch_bounds__(128) k_elk_chunk(DiagScanArgs<real> a) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= a.bt.act_chunks * a.d) return;
+  if (id >= a.bt.act_chunks() * a.d) return;
   const int64_t ac = id / a.d;
   const int j = (int)(id - ac * a.d);
   int64_t seq, c, r0;
@@ -425,7 +461,7 @@ __global__ void __launch_bounds__(128) k_elk_chunk(DiagScanArgs<real> a) {
 template <class real>
 __global__ void __launch_bounds__(128) k_elk_carry(DiagScanArgs<real> a) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= a.bt.n_act * a.d) return;
+  if (id >= a.bt.n_act() * a.d) return;
   const int64_t k = id / a.d;
   const int j = (int)(id - k * a.d);
   const int64_t seq = a.bt.act_seq[k];
@@ -458,7 +494,7 @@ __device__ __forceinline__ void elk_row(const DiagScanArgs<real>& a, int64_t row
 template <class real>
 __global__ void __launch_bounds__(128) k_elk_mean_chunk(DiagScanArgs<real> a) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= a.bt.act_chunks * a.d) return;
+  if (id >= a.bt.act_chunks() * a.d) return;
   const int64_t ac = id / a.d;
   const int j = (int)(id - ac * a.d);
   int64_t seq, c, r0;
@@ -479,7 +515,7 @@ __global__ void __launch_bounds__(128) k_elk_mean_chunk(DiagScanArgs<real> a) {
 template <class real>
 __global__ void __launch_bounds__(128) k_elk_apply(DiagScanArgs<real> a) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= a.bt.act_chunks * a.d) return;
+  if (id >= a.bt.act_chunks() * a.d) return;
   const int64_t ac = id / a.d;
   const int j = (int)(id - ac * a.d);
   int64_t seq, c, r0;
@@ -497,9 +533,9 @@ __global__ void __launch_bounds__(128) k_elk_apply(DiagScanArgs<real> a) {
 
 template <class real>
 cudaError_t launch_diag_scan(const DiagScanArgs<real>& a, cudaStream_t st) {
-  if (a.bt.act_rows == 0) return cudaSuccess;
-  const unsigned gc = grid_for(a.bt.act_chunks * a.d, 128);
-  const unsigned gs = grid_for(a.bt.n_act * a.d, 128);
+  if (a.bt.act_rows() == 0) return cudaSuccess;
+  const unsigned gc = grid_for(a.bt.act_chunks() * a.d, 128);
+  const unsigned gs = grid_for(a.bt.n_act() * a.d, 128);
   if (a.elk) {
     // variance: Moebius chunk aggregates and their carry; mean: aggregates, carry and
     // apply with the attenuations recomputed from the carried variance
@@ -781,7 +817,7 @@ __global__ void __launch_bounds__(32) k_dense_chunk_ring(DenseScanArgs<real> a) 
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gm = group_mask<D>();
   const int64_t ac = blockIdx.x * (int64_t)G + grp;
-  if (ac >= a.bt.act_chunks) return;  // whole groups; groups never synchronise with each other
+  if (ac >= a.bt.act_chunks()) return;  // whole groups; groups never synchronise with each other
   int64_t seq, c, r0;
   int n;
   act_chunk(a.bt, ac, seq, c, r0, n);
@@ -859,7 +895,7 @@ __global__ void __launch_bounds__(128) k_dense_chunk_ring4(DenseScanArgs<real> a
   __shared__ real sP[D][D + 1];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ac = blockIdx.x;
-  if (ac >= a.bt.act_chunks) return;  // uniform over the block
+  if (ac >= a.bt.act_chunks()) return;  // uniform over the block
   int64_t seq, c, r0;
   int n;
   act_chunk(a.bt, ac, seq, c, r0, n);
@@ -967,7 +1003,7 @@ __global__ void __launch_bounds__(64) k_dense_chunk_mma32(DenseScanArgs<float> a
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, tq = lane & 3;
   const int64_t ac = blockIdx.x;
-  if (ac >= a.bt.act_chunks) return;  // uniform over the block
+  if (ac >= a.bt.act_chunks()) return;  // uniform over the block
   int64_t seq, c, r0;
   int n;
   act_chunk(a.bt, ac, seq, c, r0, n);
@@ -1086,7 +1122,7 @@ __global__ void __launch_bounds__(32) k_dense_carry_ring(DenseScanArgs<real> a) 
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gm = group_mask<D>();
   const int64_t kq = blockIdx.x * (int64_t)G + grp;
-  if (kq >= a.bt.n_act) return;
+  if (kq >= a.bt.n_act()) return;
   const int64_t seq = a.bt.act_seq[kq];
   const int64_t c0 = win_first(a.bt, seq), c1 = a.bt.chunk_first[seq + 1];
   Ring& R = ring[grp];
@@ -1130,7 +1166,7 @@ __global__ void __launch_bounds__(32) k_dense_apply_ring(DenseScanArgs<real> a) 
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gm = group_mask<D>();
   const int64_t ac = blockIdx.x * (int64_t)G + grp;
-  if (ac >= a.bt.act_chunks) return;
+  if (ac >= a.bt.act_chunks()) return;
   int64_t seq, c, r0;
   int n;
   act_chunk(a.bt, ac, seq, c, r0, n);
@@ -1180,16 +1216,16 @@ __global__ void __launch_bounds__(32) k_dense_apply_ring(DenseScanArgs<real> a) 
 template <class real, int D>
 void dense_launch_wide(const DenseScanArgs<real>& a, cudaStream_t st) {
   constexpr int G = 32 / D;
-  const unsigned gc = grid_for(a.bt.act_chunks, G);
-  const unsigned gs = grid_for(a.bt.n_act, G);
+  const unsigned gc = grid_for(a.bt.act_chunks(), G);
+  const unsigned gs = grid_for(a.bt.n_act(), G);
   if constexpr (D == 32) {
     if constexpr (sizeof(real) == 4) {
       if (a.tensor_cores)
-        k_dense_chunk_mma32<<<grid_for(a.bt.act_chunks, 1), 64, 0, st>>>(a);
+        k_dense_chunk_mma32<<<grid_for(a.bt.act_chunks(), 1), 64, 0, st>>>(a);
       else
-        k_dense_chunk_ring4<real><<<grid_for(a.bt.act_chunks, 1), 128, 0, st>>>(a);
+        k_dense_chunk_ring4<real><<<grid_for(a.bt.act_chunks(), 1), 128, 0, st>>>(a);
     } else {
-      k_dense_chunk_ring4<real><<<grid_for(a.bt.act_chunks, 1), 128, 0, st>>>(a);
+      k_dense_chunk_ring4<real><<<grid_for(a.bt.act_chunks(), 1), 128, 0, st>>>(a);
     }
   } else {
     k_dense_chunk_ring<real, D><<<gc, 32, 0, st>>>(a);

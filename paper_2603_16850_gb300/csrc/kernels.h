@@ -74,7 +74,20 @@ struct CheckArgs {
   // residual, active sequences after the test); nullptr = off
   double* history = nullptr;
   int history_len = 0;
+  // device-resident Newton loop: the iteration index comes from flags->iter, which the
+  // check advances; with set_cond the check also sets the graph's while condition (go on
+  // unless the loop must stop: converged, cap reached, bad input, timeout, or non-finite
+  // residuals without the reset heuristic)
+  int device_it = 0;
+  int set_cond = 0;
+  int reset = 0;
+  cudaGraphConditionalHandle cond = 0;
 };
+
+// first node of the device-resident loop's graph: sets the while condition from the flags
+// of the check that ran before the graph
+cudaError_t launch_loop_gate(Flags* flags, int max_iters, int reset,
+                             cudaGraphConditionalHandle cond, cudaStream_t st);
 
 // Dense (FULL) correction-form scan: Delta_t = A_t Delta_{t-1} + b_t, Delta_0 = 0,
 // then s_t += Delta_t. Chunk aggregates hold (P, v) = (A_n...A_1, local Delta).
@@ -232,6 +245,9 @@ struct DiagLBArgs {
   real* agg;            // [n_chunks][d][2] tile aggregates (A, B)
   real* pre;            // [n_chunks][d] state at the end of the tile
   unsigned epoch;       // distinct per launch within one solve (starts at 1)
+  // device-resident loop: the epoch is read from epoch_from->iter, the count of checks
+  // done, which grows by one per launch; nullptr = `epoch`
+  const Flags* epoch_from = nullptr;
   int64_t cps;          // > 0: every active sequence has this many chunks and tickets
                         // are dealt round-robin over the sequences (tile k of every
                         // sequence before tile k+1 of any), which keeps look-back short

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(128) k_init(InitArgs<real> a) {
 template <class real, int D, int KIND, int JAC>
 __global__ void __launch_bounds__(128) k_linearize(LinArgs<real> a) {
   const int64_t ar = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const bool valid = ar < a.bt.act_rows;
+  const bool valid = ar < a.bt.act_rows();
   int64_t seq = 0, row = 0;
   real mx = real(0), sq = real(0);
   unsigned long long key = 0ull;  // first failing row (sliding window)
@@ -202,7 +202,7 @@ cudaError_t generic_init(const InitArgs<real>& a, cudaStream_t st) {
 
 template <class real, int KIND, int JAC>
 static cudaError_t generic_linearize_jac(const LinArgs<real>& a, cudaStream_t st) {
-  const unsigned g = grid_for(a.bt.act_rows, 128);
+  const unsigned g = grid_for(a.bt.act_rows(), 128);
   constexpr bool full = JAC == DEER_JAC_FULL;
   switch (a.dv.d) {
 #define CASE(DD)                                                              \
