@@ -139,7 +139,8 @@ def _dtype(prec: str):
 
 def _options(jac, damp, damp_param, tol, max_iters, init, prec, reset, chunk,
              confirm=1, window=False, seed=0, history=None,
-             compensate=True, jac_bytes_max=0, device_loop=False) -> N.deer_options:
+             compensate=True, jac_bytes_max=0, device_loop=False,
+             block_solve=True) -> N.deer_options:
     o = N.deer_options()
     o.max_iters = int(max_iters)
     o.tol = float(tol)
@@ -156,6 +157,7 @@ def _options(jac, damp, damp_param, tol, max_iters, init, prec, reset, chunk,
     o.compensate = int(bool(compensate))
     o.jac_bytes_max = int(jac_bytes_max)
     o.device_loop = int(bool(device_loop))
+    o.no_block_solve = 0 if block_solve else 1
     if history is not None:
         _check_dev(history, "history")
         if history.dtype != torch.float64 or history.dim() != 2 or history.shape[1] != 4:
@@ -194,7 +196,8 @@ def deer_workspace_bytes(dyn: Dynamics, batch: int, total_steps: int, **opts) ->
 def _opt_defaults(opts):
     base = dict(jac="full", damp="none", damp_param=0.0, tol=1e-10, max_iters=0, init="s0",
                 prec="fp64", reset=False, chunk=0, confirm=1, window=False, seed=0,
-                history=None, compensate=True, jac_bytes_max=0, device_loop=False)
+                history=None, compensate=True, jac_bytes_max=0, device_loop=False,
+                block_solve=True)
     base.update(opts)
     return base
 
@@ -262,7 +265,9 @@ def deer_solve(dyn: Dynamics, s0: torch.Tensor, T: int, x: Optional[torch.Tensor
     (iteration, merit, max scaled residual, active sequences) of each convergence test),
     compensate (fp32 mass-action kinetics with the full Jacobian: keep a compensated
     two-float state, default True), device_loop (run the iterations after the first as one
-    CUDA graph with a conditional while node, no host synchronisation between them).
+    CUDA graph with a conditional while node, no host synchronisation between them),
+    block_solve (default True: short sequences run the whole loop in one kernel, one
+    thread block per sequence; False keeps the multi-kernel loop).
     Host inputs are copied to the GPU and the result back to the host, into ``out`` when
     given (a preallocated, ideally pinned, host tensor [B*T][d]).
     """

@@ -39,7 +39,7 @@ class deer_options(C.Structure):
         ("reset", C.c_int32), ("chunk", C.c_int32), ("confirm", C.c_int32),
         ("window", C.c_int32), ("seed", C.c_uint64), ("history", C.c_void_p),
         ("history_len", C.c_int32), ("compensate", C.c_int32),
-        ("jac_bytes_max", C.c_int64), ("device_loop", C.c_int32), ("reserved_", C.c_int32),
+        ("jac_bytes_max", C.c_int64), ("device_loop", C.c_int32), ("no_block_solve", C.c_int32),
     ]
 
 

@@ -722,14 +722,33 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     return launch_diag_scan<real>(gsa, lst);
   };
 
-  // Device-resident loop (opt-in): iteration 0 runs on the stream as usual; the rest is
-  // one CUDA graph, a gate node and a conditional while node whose body is one iteration
-  // (scan or carry, linearise, check), the check setting the condition for the next. No
-  // host synchronisation between iterations; every kernel reads the active-set sizes the
-  // last check wrote, and grids are sized for the whole problem (the look-back scan's
-  // surplus CTAs draw tickets past the active tiles and leave). Per-phase timing keeps
-  // the host loop.
-  if (o->device_loop && !pt.on) {
+  // Short sequences (every one within what a thread block holds in registers) with the
+  // full Jacobian: the whole loop runs inside one kernel, one block per sequence
+  const bool block_solve = !o->no_block_solve && o->jac == DEER_JAC_FULL &&
+                           (o->damp == DEER_DAMP_NONE || o->damp == DEER_DAMP_SCALE) &&
+                           !mixed && !ly.cs && !o->history && !pt.on && maxT >= 1 &&
+                           maxT <= block_solve_max_T(f->kind, d) && B <= INT32_MAX;
+  if (block_solve) {
+    // the initial active-set pass counted every sequence; the block solve counts the
+    // unconverged ones itself
+    DEER_CK(cudaMemsetAsync(&flags->n_active, 0, sizeof(int32_t), st));
+    BlockSolveArgs<real> ba{dv, B, d_off, s0, s, info, flags, o->tol, max_iters,
+                            o->confirm > 1 ? o->confirm : 1, o->reset, o->damp,
+                            (real)o->damp_param, reset_thr};
+    DEER_CK(launch_block_solve<real>(ba, st));
+    DEER_CK(cudaMemcpyAsync(&hf, flags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
+    DEER_CK(cudaStreamSynchronize(st));
+    if (hf.bad_input) status = DEER_ERR_INVALID;
+    else if (hf.n_nonfinite > 0 && !o->reset) status = DEER_ERR_NONFINITE;
+    else if (hf.n_active > 0) status = DEER_NOT_CONVERGED;
+  } else if (o->device_loop && !pt.on) {
+    // Device-resident loop (opt-in): iteration 0 runs on the stream as usual; the rest is
+    // one CUDA graph, a gate node and a conditional while node whose body is one iteration
+    // (scan or carry, linearise, check), the check setting the condition for the next. No
+    // host synchronisation between iterations; every kernel reads the active-set sizes the
+    // last check wrote, and grids are sized for the whole problem (the look-back scan's
+    // surplus CTAs draw tickets past the active tiles and leave). Per-phase timing keeps
+    // the host loop.
     ca.it = 0;
     ca.device_it = 1;
     ca.set_cond = 0;

@@ -84,6 +84,26 @@ struct CheckArgs {
   cudaGraphConditionalHandle cond = 0;
 };
 
+// Whole solve of short sequences, one thread block per sequence (full Jacobian, no
+// damping or scale damping; the kinds and state sizes block_solve_max_T accepts).
+template <class real>
+struct BlockSolveArgs {
+  DynView<real> dv;
+  int64_t B;
+  const int64_t* offsets;  // [B+1]
+  const real* s0;          // [B][d]
+  real* s;                 // [N][d]: the initial guess in, the last iterate out
+  SeqInfo* info;           // [B]
+  Flags* flags;            // n_active += unconverged sequences, n_nonfinite += ...
+  double tol;
+  int max_iters, confirm, reset, damp;
+  real dparam, reset_thr;
+};
+// longest sequence the block solve takes for this kind and state size (0: not built)
+int64_t block_solve_max_T(int kind, int d);
+template <class real>
+cudaError_t launch_block_solve(const BlockSolveArgs<real>& a, cudaStream_t st);
+
 // first node of the device-resident loop's graph: sets the while condition from the flags
 // of the check that ran before the graph
 cudaError_t launch_loop_gate(Flags* flags, int max_iters, int reset,

@@ -203,7 +203,7 @@ def test_options_struct_layout_matches_the_header(lib):
     lib.deer_default_options(C.byref(o))
     assert (o.max_iters, o.tol, o.jac, o.damp, o.damp_param, o.init, o.prec, o.reset,
             o.chunk, o.confirm, o.window, o.seed, o.history, o.history_len, o.compensate,
-            o.jac_bytes_max, o.device_loop, o.reserved_) == \
+            o.jac_bytes_max, o.device_loop, o.no_block_solve) == \
         (0, 1e-10, 0, 0, 0.0, 1, 0, 0, 0, 1, 0, 0, None, 0, 1, 0, 0, 0)
     assert all(b == 0xAB for b in bytes(buf)[size:])
 

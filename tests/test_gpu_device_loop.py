@@ -49,9 +49,11 @@ def _case(name):
         p = synth.brusselator(T=1024)
         dyn = deer.Dynamics.brusselator(_t(p["params"]), p["dt"])
         s0 = _t(p["s0"])
-        # reset heuristic on: undamped Newton overflows on the way at this horizon
+        # reset heuristic on: undamped Newton overflows on the way at this horizon; the
+        # multi-kernel loop (a sequence this short otherwise runs whole in one block)
         return (lambda **e: deer.deer_solve(dyn, s0, 1024, jac="full", tol=1e-12,
-                                            prec="fp64", reset=True, **e)), True
+                                            prec="fp64", reset=True, block_solve=False,
+                                            **e)), True
     if name == "gru_diag_lookback_fp32":
         g = synth.gru(4, 4096, 64, 64, seed=2, dtype=np.float32)
         dyn = deer.Dynamics.gru(_t(g["W"], torch.float32), _t(g["U"], torch.float32))
