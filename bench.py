@@ -312,50 +312,68 @@ def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64, window=False,
         checks.add(out, lambda: _gru_oracle_check(g, s_host, pick, cache))
     return out
 
-def brusselator_measurement(deer, dev, stream, reps=20, checks=None):
+def brusselator_measurement(deer, dev, stream, reps=20, checks=None, N=None, lib=None):
     """C1: one Brusselator trajectory (d=2, a=1, b=3, s0=(1,1), explicit Euler dt=0.01,
     T=1024), full-Jacobian Newton in FP64 to tol 1e-12 (reset heuristic on: undamped Newton
-    from the constant guess overflows on this limit cycle). A single short sequence is
-    launch- and latency-bound: reported as time per solve and per Newton iteration, next to
-    the sequential GPU rollout."""
+    from the constant guess overflows on this limit cycle). The library runs a sequence this
+    short whole in one kernel (a thread-block cluster iterates it to convergence); reported
+    as time per solve through the API (host work included) and the kernel's own time from
+    the library's phase events, next to the multi-kernel loop and the sequential GPU
+    rollout."""
     import torch
     import synth
     p = synth.brusselator(T=1024)
     dyn = deer.Dynamics.brusselator(torch.tensor(p["params"], device=dev), p["dt"])
     s0 = torch.tensor(p["s0"], device=dev)
     opts = dict(jac="full", tol=1e-12, prec="fp64", init="s0", reset=True)
-    # chunk length from the autotuner (untimed): with one short sequence the chunk pass's
-    # per-thread chain (L rows) and the carry's chain (T / L chunks) trade off
-    from paper_2603_16850_gb300 import autotune
-    tuned = autotune.pick_best(
-        (8, 16, 32, 64, 128),
-        lambda L: _time_solve1(deer, dyn, s0, 1024, None, dict(opts, chunk=L), stream))
-    opts["chunk"] = tuned["chunk"]
     ws_ = torch.empty(deer.deer_workspace_bytes(dyn, 1, 1024, **opts), dtype=torch.uint8,
                       device=dev)
-    for _ in range(3):
-        _, info = deer.deer_solve(dyn, s0, 1024, workspace=ws_, stream=stream, **opts)
-    torch.cuda.synchronize()
-    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
-    e0.record(stream)
-    for _ in range(reps):
-        s, info = deer.deer_solve(dyn, s0, 1024, workspace=ws_, stream=stream, **opts)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    e0.record(stream)
-    for _ in range(reps):
-        deer.deer_rollout(dyn, s0, 1024, prec="fp64", stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    roll_ms = e0.elapsed_time(e1) / reps
+
+    def per_call(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        e0.record(stream)
+        for _ in range(reps):
+            r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, r
+
+    ms, (s, info) = per_call(
+        lambda: deer.deer_solve(dyn, s0, 1024, workspace=ws_, stream=stream, **opts))
+    kernel_us = None
+    if lib is not None and N is not None:
+        lib.deer_profile_reset()
+        lib.deer_profile_enable(1)
+        for _ in range(reps):
+            deer.deer_solve(dyn, s0, 1024, workspace=ws_, stream=stream, **opts)
+        torch.cuda.synchronize()
+        lib.deer_profile_enable(0)
+        prof = N.deer_profile()
+        lib.deer_profile_read(prof)
+        kernel_us = 1000.0 * sum(prof.ms) / reps
+    # the multi-kernel loop on the same problem, its chunk length from the autotuner
+    from paper_2603_16850_gb300 import autotune
+    mopts = dict(opts, block_solve=False)
+    tuned = autotune.pick_best(
+        (8, 16, 32, 64, 128),
+        lambda L: _time_solve1(deer, dyn, s0, 1024, None, dict(mopts, chunk=L), stream))
+    mopts["chunk"] = tuned["chunk"]
+    multi_ms, _ = per_call(
+        lambda: deer.deer_solve(dyn, s0, 1024, workspace=ws_, stream=stream, **mopts))
+    roll_ms, _ = per_call(lambda: deer.deer_rollout(dyn, s0, 1024, prec="fp64", stream=stream))
     it = int(info.iters[0])
     out = {"workload": "Brusselator d=2 T=1024 Euler dt=0.01, full Newton FP64, tol 1e-12",
            "us_per_solve": 1000 * ms, "newton_iters": it,
            "us_per_iteration": 1000 * ms / max(it, 1), "converged": bool(info.converged[0]),
            "value": 1024 / (ms / 1000.0), "unit": UNIT,
-           "sequential_gpu_rollout_us": 1000 * roll_ms,
-           "chunk": tuned["chunk"]}
+           "path": "whole solve in one kernel (one thread-block cluster)",
+           "kernel_us": kernel_us,
+           "multi_kernel_loop_us_per_solve": 1000 * multi_ms,
+           "multi_kernel_loop_chunk": tuned["chunk"],
+           "sequential_gpu_rollout_us": 1000 * roll_ms}
     if checks is not None:
         s_host = s.cpu().numpy()
 
@@ -908,7 +926,7 @@ def run_only(args):
         out = ragged_mixed_measurement(deer, N, lib, dev, stream, B=args.batch or 10000,
                                        group=min(1000, args.batch or 1000))
     elif args.only == "brusselator":
-        out = brusselator_measurement(deer, dev, stream)
+        out = brusselator_measurement(deer, dev, stream, N=N, lib=lib)
     elif args.only == "gru_window":
         out = gru_diag_measurement(deer, N, lib, dev, stream, steps=max(args.steps, 1),
                                    B=args.batch or 64, window=True)
@@ -1102,7 +1120,8 @@ def run(args):
     if rank == 0 and ws == 1 and not args.no_extra:
         gru_cache = {}
         extra["lle"] = lle_measurement(deer, dyn, s0, s, T, d, stream)
-        extra["brusselator"] = brusselator_measurement(deer, dev, stream, checks=checks)
+        extra["brusselator"] = brusselator_measurement(deer, dev, stream, checks=checks, N=N,
+                                                       lib=lib)
         extra["gru_quasi_deer"] = gru_diag_measurement(deer, N, lib, dev, stream, checks=checks,
                                                        gru_cache=gru_cache)
         extra["gru_quasi_elk"] = gru_elk_measurement(deer, dev, stream, checks=checks,

@@ -237,16 +237,17 @@ typedef struct {
                           (host loop) while per-phase profiling is on. The call still blocks
                           until the loop ends. Default 0. */
   int32_t no_block_solve; /* 0 (default): where every sequence is short enough for one
-                          thread block to hold its iterate in registers (d = 1 or 2: up to
-                          4096 steps; d = 4: up to 1024) and the step is the full Jacobian
-                          without damping or with scale damping (no mixed precision, no
-                          compensated state, no history record), the whole Newton loop runs
-                          in one kernel, one block per sequence: linearisation, convergence
-                          test and a block-wide scan per iteration, no launch or host
-                          synchronisation between iterations, every block stopping on its own
-                          convergence (for the Brusselator, Euler, mass-action, linear,
+                          thread-block cluster (up to 8 blocks) to hold its iterate in
+                          registers (d = 1 or 2: up to 8192 steps; d = 4: up to 2048) and
+                          the step is the full Jacobian without damping or with scale
+                          damping (no mixed precision, no compensated state, no history
+                          record), the whole Newton loop runs in one kernel, one cluster per
+                          sequence: linearisation, convergence test and a cluster-wide scan
+                          per iteration through distributed shared memory, no launch or host
+                          synchronisation between iterations, every cluster stopping on its
+                          own convergence (for the Brusselator, Euler, mass-action, linear,
                           mean-field RNN and Langevin kinds). The sliding window is moot
-                          there (each block iterates its whole sequence). 1 = always the
+                          there (each cluster iterates its whole sequence). 1 = always the
                           multi-kernel loop. */
 } deer_options;
 

@@ -722,22 +722,30 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
     return launch_diag_scan<real>(gsa, lst);
   };
 
-  // Short sequences (every one within what a thread block holds in registers) with the
-  // full Jacobian: the whole loop runs inside one kernel, one block per sequence
+  // Short sequences (every one within what a thread-block cluster holds in registers)
+  // with the full Jacobian: the whole loop runs inside one kernel, one cluster per
+  // sequence
   const bool block_solve = !o->no_block_solve && o->jac == DEER_JAC_FULL &&
                            (o->damp == DEER_DAMP_NONE || o->damp == DEER_DAMP_SCALE) &&
-                           !mixed && !ly.cs && !o->history && !pt.on && maxT >= 1 &&
+                           !mixed && !ly.cs && !o->history && maxT >= 1 &&
                            maxT <= block_solve_max_T(f->kind, d) && B <= INT32_MAX;
   if (block_solve) {
     // the initial active-set pass counted every sequence; the block solve counts the
     // unconverged ones itself
     DEER_CK(cudaMemsetAsync(&flags->n_active, 0, sizeof(int32_t), st));
-    BlockSolveArgs<real> ba{dv, B, d_off, s0, s, info, flags, o->tol, max_iters,
+    BlockSolveArgs<real> ba{dv, B, maxT, d_off, s0, s, info, flags, o->tol, max_iters,
                             o->confirm > 1 ? o->confirm : 1, o->reset, o->damp,
                             (real)o->damp_param, reset_thr};
+    pt.begin(PH_LIN);  // the whole loop is one launch: its time goes to linearisation
     DEER_CK(launch_block_solve<real>(ba, st));
+    pt.end(PH_LIN);
     DEER_CK(cudaMemcpyAsync(&hf, flags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
     DEER_CK(cudaStreamSynchronize(st));
+    if (pt.on) {
+      const int64_t launches[PH_N] = {0, 1, 0, 0};
+      const int64_t rows[PH_N] = {0, N, 0, 0};
+      pt.collect(launches, rows);
+    }
     if (hf.bad_input) status = DEER_ERR_INVALID;
     else if (hf.n_nonfinite > 0 && !o->reset) status = DEER_ERR_NONFINITE;
     else if (hf.n_active > 0) status = DEER_NOT_CONVERGED;

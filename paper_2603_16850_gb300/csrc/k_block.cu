@@ -1,21 +1,26 @@
-// Whole Newton solve of a short sequence inside one thread block (Algorithm 1 with the
-// full Jacobian): one block per sequence runs every iteration itself, linearisation,
-// convergence test and the scan of Eq. bin_op_affine, with the iterate kept in registers.
-// There is no launch and no host round trip per iteration, and a batch of short
-// sequences is one launch in which every block stops on its own convergence.
+// Whole Newton solve of a short sequence inside one thread-block cluster (Algorithm 1 with
+// the full Jacobian): one cluster per sequence runs every iteration itself,
+// linearisation, convergence test and the scan of Eq. bin_op_affine, with the iterate
+// kept in registers. There is no launch and no host round trip per iteration, and a
+// batch of short sequences is one launch in which every cluster stops on its own
+// convergence.
 //
-// Thread q owns the contiguous rows [q R, q R + R) of its block's sequence (R = rows per
-// thread for this T). One iteration:
+// The cluster's threads own contiguous rows of the sequence in (block rank, thread)
+// order, R rows each. One iteration:
 //   1. each thread evaluates F_t = f_t(s_{t-1}) and A_t on its rows (the row before its
-//      first comes from the previous thread through shared memory, s_0 for thread 0),
-//      forms the residual r_t = s_t - F_t and composes its rows' affine steps
-//      Delta -> A_t Delta - r_t into one element (P, v);
-//   2. a block reduction gives the largest scaled residual max |r| / max(1, |s|) and
-//      sum r^2; the test and the iteration count follow the library's convergence check;
-//   3. a block-wide exclusive scan of the elements (warp shuffles, then the warp totals)
-//      gives the correction Delta entering each thread's rows, which the thread then
-//      propagates through its rows (evaluating A_t again rather than keeping it) and adds
-//      to the iterate, with the reset heuristic.
+//      first comes from the previous thread through shared memory, from the previous
+//      block's shared memory for thread 0, s_0 at the start), forms the residual
+//      r_t = s_t - F_t and composes its rows' affine steps Delta -> A_t Delta - r_t into
+//      one element (P, v);
+//   2. a reduction over the cluster gives the largest scaled residual max |r| / max(1, |s|)
+//      and sum r^2; the test and the iteration count follow the library's convergence
+//      check, taken identically by every block;
+//   3. an exclusive scan of the elements (warp shuffles, the warp totals, then the blocks'
+//      totals read across the cluster) gives the correction Delta entering each thread's
+//      rows, which the thread propagates through its rows with the A_t and F_t it kept,
+//      adding it to the iterate with the reset heuristic.
+#include <cooperative_groups.h>
+
 #include <cfloat>
 
 #include "dyn.cuh"
@@ -74,11 +79,13 @@ __device__ __forceinline__ Aff<real, D> aff_identity() {
   return o;
 }
 
-// inclusive scan over the lanes of a warp (lane order = time order)
+// inclusive scan over the first n lanes of a warp (lane order = time order; n <= 32, the
+// steps stop at the first power of two >= n: every float64 product counts on this GPU)
 template <class real, int D>
-__device__ __forceinline__ Aff<real, D> warp_scan_aff(Aff<real, D> x, int lane) {
+__device__ __forceinline__ Aff<real, D> warp_scan_aff(Aff<real, D> x, int lane, int n = 32) {
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
+    if (off >= n) break;  // uniform over the warp
     const Aff<real, D> y = shfl_up_aff<real, D>(x, off);
     if (lane >= off) x = compose<real, D>(x, y);
   }
@@ -87,17 +94,27 @@ __device__ __forceinline__ Aff<real, D> warp_scan_aff(Aff<real, D> x, int lane) 
 
 template <class real, int D, int KIND, int NT, int RPT>
 __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
+  namespace cg = cooperative_groups;
   constexpr int NW = NT / 32;
   __shared__ real s_last[NT][D];       // each thread's last row of the iterate
   __shared__ Aff<real, D> s_warp[NW];  // inclusive warp totals, then their prefixes
+  __shared__ Aff<real, D> s_tot;       // this block's element (read by later blocks)
   __shared__ real s_mx[NW];
   __shared__ double s_sq[NW];
-  const int64_t seq = blockIdx.x;
+  __shared__ double s_part[2];         // this block's max scaled residual and sum r^2
+  __shared__ double s_stat[2];         // the cluster's
+  __shared__ real s_din[D];            // Delta entering this block's rows
+  cg::cluster_group cl = cg::this_cluster();
+  const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int64_t seq = blockIdx.x / CL;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t r0 = a.offsets[seq];
   const int64_t T = a.offsets[seq + 1] - r0;
-  const int rpt = (int)((T + NT - 1) / NT);  // rows per thread (<= RPT, checked by the host)
-  const int64_t k0 = (int64_t)tid * rpt;
+  // rows per thread (<= RPT: the host sizes the cluster), contiguous over the cluster's
+  // threads in rank order
+  const int64_t nthr = (int64_t)CL * NT;
+  const int rpt = (int)((T + nthr - 1) / nthr);
+  const int64_t k0 = ((int64_t)rank * NT + tid) * rpt;
   const int nmine = T - k0 <= 0 ? 0 : (T - k0 < rpt ? (int)(T - k0) : rpt);
   const real scale = a.damp == DEER_DAMP_SCALE ? real(1) - a.dparam : real(1);
   real s[RPT][D];
@@ -108,26 +125,37 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
   for (int k = 0; k < RPT; ++k)
 #pragma unroll
     for (int i = 0; i < D; ++i) s[k][i] = k < nmine ? a.s[(r0 + k0 + k) * D + i] : real(0);
-  SeqInfo inf = a.info[seq];
   int passes = 0;
   bool done = false, nonfinite = false;
   double merit = 0.0, mres = 0.0;
   int iters = 0;
   for (int it = 0;; ++it) {
-    // the row before this thread's first is the previous thread's last (a thread without
-    // rows is followed only by threads without rows)
+    // the row before this thread's first is the previous thread's last, in this block or
+    // (thread 0) in the previous block of the cluster; a thread without rows is followed
+    // only by threads without rows
 #pragma unroll
     for (int k = 0; k < RPT; ++k)
       if (k == nmine - 1) {
 #pragma unroll
         for (int i = 0; i < D; ++i) s_last[tid][i] = s[k][i];
       }
-    __syncthreads();
+    cl.sync();
     real prev[D];
+    if (tid > 0) {
 #pragma unroll
-    for (int i = 0; i < D; ++i) prev[i] = tid == 0 ? s0[i] : s_last[tid - 1][i];
-    // 1. linearise, residual statistics, this thread's element
+      for (int i = 0; i < D; ++i) prev[i] = s_last[tid - 1][i];
+    } else if (rank > 0) {
+      const real* pl = cl.map_shared_rank(&s_last[NT - 1][0], rank - 1);
+#pragma unroll
+      for (int i = 0; i < D; ++i) prev[i] = pl[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < D; ++i) prev[i] = s0[i];
+    }
+    // 1. linearise, residual statistics, this thread's element; F and A are kept for the
+    //    apply pass
     Aff<real, D> e = aff_identity<real, D>();
+    real Fk[RPT][D], Ak[RPT][D][D];
     real mx = real(0);
     double sq = 0.0;
     {
@@ -137,24 +165,21 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
 #pragma unroll
       for (int k = 0; k < RPT; ++k) {
         if (k < nmine) {
-          real F[D], A[D][D];
-          eval_f<real, D, KIND, 1>(a.dv, seq, r0 + k0 + k, sp, F, A, nullptr);
-          real b[D];
+          eval_f<real, D, KIND, 1>(a.dv, seq, r0 + k0 + k, sp, Fk[k], Ak[k], nullptr);
+          Aff<real, D> st;
 #pragma unroll
           for (int i = 0; i < D; ++i) {
-            const real r = s[k][i] - F[i];
-            b[i] = -r;
+            const real r = s[k][i] - Fk[k][i];
+            st.v[i] = -r;
             const real sabs = rabs(s[k][i]);
             const real sr = rabs(r) / (sabs > real(1) ? sabs : real(1));
             mx = (sr > mx || sr != sr) ? sr : mx;
             sq += (double)r * (double)r;
-          }
-          Aff<real, D> st;
 #pragma unroll
-          for (int i = 0; i < D; ++i) {
-            st.v[i] = b[i];
-#pragma unroll
-            for (int j = 0; j < D; ++j) st.P[i][j] = scale * A[i][j];
+            for (int j = 0; j < D; ++j) {
+              Ak[k][i][j] *= scale;
+              st.P[i][j] = Ak[k][i][j];
+            }
           }
           e = compose<real, D>(st, e);
 #pragma unroll
@@ -162,7 +187,8 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
         }
       }
     }
-    // 2. block reduction and the convergence test
+    // 2. reduction over the cluster and the convergence test (every block reduces the
+    //    blocks' partials in the same order, so all take the same decision)
     {
       double m = (double)mx;
 #pragma unroll
@@ -176,12 +202,36 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
       }
     }
     __syncthreads();
-    double bm = 0.0, bs = 0.0;
+    if (tid == 0) {
+      double bm = 0.0, bs = 0.0;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      bm = nanmax(bm, (double)s_mx[w]);
-      bs += s_sq[w];
+      for (int w = 0; w < NW; ++w) {
+        bm = nanmax(bm, (double)s_mx[w]);
+        bs += s_sq[w];
+      }
+      s_part[0] = bm;
+      s_part[1] = bs;
     }
+    cl.sync();
+    if (warp == 0) {
+      double bm = 0.0, bs = 0.0;
+      if (lane < CL) {
+        const double* pp = cl.map_shared_rank(&s_part[0], lane);
+        bm = pp[0];
+        bs = pp[1];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        bm = nanmax(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+        bs += __shfl_xor_sync(0xffffffffu, bs, o);
+      }
+      if (lane == 0) {
+        s_stat[0] = bm;
+        s_stat[1] = bs;
+      }
+    }
+    __syncthreads();
+    const double bm = s_stat[0], bs = s_stat[1];
     merit = 0.5 * bs;
     mres = bm;
     nonfinite = !(bm <= DBL_MAX);
@@ -193,24 +243,49 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
     }
     iters = it < a.max_iters ? it + 1 : it;
     if ((nonfinite && !a.reset) || it >= a.max_iters) break;
-    // 3. block-wide exclusive scan of the elements, then this thread's rows
+    // 3. scan of the elements: lanes, warps, then the blocks of the cluster
     const Aff<real, D> inc = warp_scan_aff<real, D>(e, lane);
     if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
     if (warp == 0) {
       Aff<real, D> wt = lane < NW ? s_warp[lane] : aff_identity<real, D>();
-      wt = warp_scan_aff<real, D>(wt, lane);
+      wt = warp_scan_aff<real, D>(wt, lane, NW);
       if (lane < NW) s_warp[lane] = wt;
+      if (lane == NW - 1) s_tot = wt;
+    }
+    cl.sync();
+    if (warp == 0) {
+      // the blocks before this one, composed in order: Delta entering this block
+      Aff<real, D> bt = lane < CL ? *cl.map_shared_rank(&s_tot, lane) : aff_identity<real, D>();
+      bt = warp_scan_aff<real, D>(bt, lane, CL);
+      const Aff<real, D> ex = shfl_up_aff<real, D>(bt, 1);
+      if (lane == rank) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) s_din[i] = rank > 0 ? ex.v[i] : real(0);
+      }
     }
     __syncthreads();
     real din[D];
     {
-      // Delta entering this thread: the warps before, then the lanes before in this warp
+      // then the warps before in this block, then the lanes before in this warp
+      real db[D], dw[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) db[i] = s_din[i];
+      if (warp > 0) {
+        const Aff<real, D>& wp = s_warp[warp - 1];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          real x = wp.v[i];
+#pragma unroll
+          for (int k = 0; k < D; ++k) x += wp.P[i][k] * db[k];
+          dw[i] = x;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) dw[i] = db[i];
+      }
       Aff<real, D> ex = shfl_up_aff<real, D>(inc, 1);
       if (lane == 0) ex = aff_identity<real, D>();
-      real dw[D];
-#pragma unroll
-      for (int i = 0; i < D; ++i) dw[i] = warp > 0 ? s_warp[warp - 1].v[i] : real(0);
 #pragma unroll
       for (int i = 0; i < D; ++i) {
         real x = ex.v[i];
@@ -219,41 +294,36 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
         din[i] = x;
       }
     }
-    {
-      real sp[D];
 #pragma unroll
-      for (int i = 0; i < D; ++i) sp[i] = prev[i];
+    for (int k = 0; k < RPT; ++k) {
+      if (k < nmine) {
+        real dn[D];
 #pragma unroll
-      for (int k = 0; k < RPT; ++k) {
-        if (k < nmine) {
-          real F[D], A[D][D];
-          eval_f<real, D, KIND, 1>(a.dv, seq, r0 + k0 + k, sp, F, A, nullptr);
-          real dn[D];
+        for (int i = 0; i < D; ++i) {
+          real x = Fk[k][i] - s[k][i];
 #pragma unroll
-          for (int i = 0; i < D; ++i) {
-            real x = F[i] - s[k][i];
+          for (int j = 0; j < D; ++j) x += Ak[k][i][j] * din[j];
+          dn[i] = x;
+        }
 #pragma unroll
-            for (int j = 0; j < D; ++j) x += scale * A[i][j] * din[j];
-            dn[i] = x;
-          }
-#pragma unroll
-          for (int i = 0; i < D; ++i) {
-            sp[i] = s[k][i];
-            const real y = s[k][i] + dn[i];
-            s[k][i] = (a.reset && !(y <= a.reset_thr && y >= -a.reset_thr)) ? real(0) : y;
-            din[i] = dn[i];
-          }
+        for (int i = 0; i < D; ++i) {
+          const real y = s[k][i] + dn[i];
+          s[k][i] = (a.reset && !(y <= a.reset_thr && y >= -a.reset_thr)) ? real(0) : y;
+          din[i] = dn[i];
         }
       }
     }
-    __syncthreads();  // s_last and s_warp are rewritten by the next iteration
+    // (the next iteration's first cluster barrier orders the rewrites of the shared
+    // buffers after every block's reads of them)
   }
+  cl.sync();  // no block leaves while another may still read its shared memory
 #pragma unroll
   for (int k = 0; k < RPT; ++k)
     if (k < nmine)
 #pragma unroll
       for (int i = 0; i < D; ++i) a.s[(r0 + k0 + k) * D + i] = s[k][i];
-  if (tid == 0) {
+  if (tid == 0 && rank == 0) {
+    SeqInfo inf = a.info[seq];
     inf.iters = iters;
     inf.done = done ? 1 : 0;
     inf.passes = passes;
@@ -265,52 +335,98 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
   }
 }
 
-// rows per thread and threads per block by state size: every row's iterate stays in
-// registers (D <= 2: 512 threads x 8 rows; D = 4: 256 x 4)
+// Threads per block and the most rows per thread by state size (each thread keeps its
+// rows' iterate, F_t and A_t in registers). A sequence is spread over a cluster of up to
+// 16 blocks (one row per thread where it fits), whose shared memory the blocks read from
+// each other: the more SMs, the more of the GPU's float64 units (a small fraction of its
+// float32 rate) a single sequence gets.
+constexpr int kBlockThreads = 128;
+constexpr int kMaxCluster = 8;    // portable cluster size: sets the longest sequence taken
+constexpr int kWideCluster = 16;  // non-portable, used when the GPU schedules it
 template <int D>
-struct BlockCfg {
-  static constexpr int NT = D <= 2 ? 512 : 256;
-  static constexpr int RPT = D <= 2 ? 8 : 4;
-};
+struct BlockRows { static constexpr int n = D <= 2 ? 8 : 2; };
 
 int64_t block_solve_max_T(int kind, int d) {
   const bool kind_ok = kind == DEER_F_BRUSSELATOR_EULER || kind == DEER_F_MASSACTION_EULER ||
                        kind == DEER_F_MASSACTION_RK4 || kind == DEER_F_LINEAR ||
                        kind == DEER_F_RNN_TANH || kind == DEER_F_LANGEVIN_2WELL;
   if (!kind_ok) return 0;
+  const int64_t per = (int64_t)kMaxCluster * kBlockThreads;
   switch (d) {
-    case 1: return (int64_t)BlockCfg<1>::NT * BlockCfg<1>::RPT;
-    case 2: return (int64_t)BlockCfg<2>::NT * BlockCfg<2>::RPT;
-    case 4: return (int64_t)BlockCfg<4>::NT * BlockCfg<4>::RPT;
+    case 1: return per * BlockRows<1>::n;
+    case 2: return per * BlockRows<2>::n;
+    case 4: return per * BlockRows<4>::n;
     default: return 0;
   }
 }
 
 template <class real, int D, int KIND>
-static void block_launch(const BlockSolveArgs<real>& a, cudaStream_t st) {
-  using C = BlockCfg<D>;
-  k_block_solve<real, D, KIND, C::NT, C::RPT><<<(unsigned)a.B, C::NT, 0, st>>>(a);
-  note_launch();
+static cudaError_t block_launch(const BlockSolveArgs<real>& a, cudaStream_t st) {
+  auto kern = k_block_solve<real, D, KIND, kBlockThreads, BlockRows<D>::n>;
+  // cluster size: one row per thread where the longest sequence allows it, up to 16
+  // blocks (more SMs' float64 units per sequence) when the GPU can schedule that, else 8
+  int64_t cl = (a.max_T + kBlockThreads - 1) / kBlockThreads;
+  cl = cl < 1 ? 1 : (cl > kWideCluster ? kWideCluster : cl);
+  if (cl > kMaxCluster) {
+    static thread_local int wide_ok = -1;  // per host thread: 1 if the attribute took
+    if (wide_ok < 0)
+      wide_ok = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                     1) == cudaSuccess ? 1 : 0;
+    if (!wide_ok) cl = kMaxCluster;
+    (void)cudaGetLastError();
+  }
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.blockDim = dim3(kBlockThreads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  for (;;) {
+    attr[0].val.clusterDim.x = (unsigned)cl;
+    cfg.gridDim = dim3((unsigned)(a.B * cl), 1, 1);
+    // a cluster of 16 that cannot be placed: take 8 instead (the longest sequence taken
+    // fits 8)
+    if (cl > kMaxCluster) {
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess ||
+          nclusters < 1) {
+        (void)cudaGetLastError();
+        cl = kMaxCluster;
+        continue;
+      }
+    }
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
+    if (e != cudaSuccess && cl > kMaxCluster) {
+      (void)cudaGetLastError();
+      cl = kMaxCluster;
+      continue;
+    }
+    if (e == cudaSuccess) note_launch();
+    return e;
+  }
 }
 
 template <class real, int D>
 static cudaError_t block_kind(const BlockSolveArgs<real>& a, cudaStream_t st) {
   switch (a.dv.kind) {
     case DEER_F_BRUSSELATOR_EULER:
-      if constexpr (D == 2) { block_launch<real, D, DEER_F_BRUSSELATOR_EULER>(a, st); break; }
+      if constexpr (D == 2) return block_launch<real, D, DEER_F_BRUSSELATOR_EULER>(a, st);
       return cudaErrorInvalidValue;
     case DEER_F_MASSACTION_EULER:
-      if constexpr (D >= 2) { block_launch<real, D, DEER_F_MASSACTION_EULER>(a, st); break; }
+      if constexpr (D >= 2) return block_launch<real, D, DEER_F_MASSACTION_EULER>(a, st);
       return cudaErrorInvalidValue;
     case DEER_F_MASSACTION_RK4:
-      if constexpr (D >= 2) { block_launch<real, D, DEER_F_MASSACTION_RK4>(a, st); break; }
+      if constexpr (D >= 2) return block_launch<real, D, DEER_F_MASSACTION_RK4>(a, st);
       return cudaErrorInvalidValue;
-    case DEER_F_LINEAR: block_launch<real, D, DEER_F_LINEAR>(a, st); break;
-    case DEER_F_RNN_TANH: block_launch<real, D, DEER_F_RNN_TANH>(a, st); break;
-    case DEER_F_LANGEVIN_2WELL: block_launch<real, D, DEER_F_LANGEVIN_2WELL>(a, st); break;
+    case DEER_F_LINEAR: return block_launch<real, D, DEER_F_LINEAR>(a, st);
+    case DEER_F_RNN_TANH: return block_launch<real, D, DEER_F_RNN_TANH>(a, st);
+    case DEER_F_LANGEVIN_2WELL: return block_launch<real, D, DEER_F_LANGEVIN_2WELL>(a, st);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 template <class real>

@@ -84,12 +84,13 @@ struct CheckArgs {
   cudaGraphConditionalHandle cond = 0;
 };
 
-// Whole solve of short sequences, one thread block per sequence (full Jacobian, no
-// damping or scale damping; the kinds and state sizes block_solve_max_T accepts).
+// Whole solve of short sequences, one thread-block cluster per sequence (full Jacobian,
+// no damping or scale damping; the kinds and state sizes block_solve_max_T accepts).
 template <class real>
 struct BlockSolveArgs {
   DynView<real> dv;
   int64_t B;
+  int64_t max_T;           // longest sequence (sets the cluster size)
   const int64_t* offsets;  // [B+1]
   const real* s0;          // [B][d]
   real* s;                 // [N][d]: the initial guess in, the last iterate out

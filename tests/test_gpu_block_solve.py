@@ -1,5 +1,5 @@
-"""The whole-solve kernel for short sequences (one thread block per sequence runs every
-Newton iteration: linearisation, convergence test, block-wide scan). Each case is solved
+"""The whole-solve kernel for short sequences (one thread-block cluster per sequence runs
+every Newton iteration: linearisation, convergence test, cluster-wide scan). Each case is solved
 with it and with the multi-kernel loop (block_solve=False): both reach the FP64 oracle's
 sequential rollout within the tolerance of their precision, two iterations from the same
 start equal the oracle's Newton iterates (the scan's association order is the only
@@ -132,10 +132,10 @@ def test_linear_recurrence_in_one_iteration():
 
 def test_one_launch_and_fallback_past_the_block_size():
     """The Brusselator at T = 1024 is the initial guess, the active-set pass and one
-    whole-solve launch; at T = 4097 (past the 4096 steps a block holds for d = 2) the
+    whole-solve launch; at T = 8193 (past the 8192 steps a cluster holds for d = 2) the
     multi-kernel loop takes over and still reaches the rollout."""
     deer = _deer()
-    p = synth.brusselator(T=4097)
+    p = synth.brusselator(T=8193)
     dyn = deer.Dynamics.brusselator(_t(p["params"]), p["dt"])
     s0 = _t(p["s0"])
     n0 = deer.kernel_launch_count()
@@ -143,10 +143,10 @@ def test_one_launch_and_fallback_past_the_block_size():
     torch.cuda.synchronize()
     assert deer.kernel_launch_count() - n0 == 3 and bool(info.converged.all())
     n1 = deer.kernel_launch_count()
-    s, info = deer.deer_solve(dyn, s0, 4097, jac="full", tol=1e-12, reset=True)
+    s, info = deer.deer_solve(dyn, s0, 8193, jac="full", tol=1e-12, reset=True)
     torch.cuda.synchronize()
     assert deer.kernel_launch_count() - n1 > 3 + 2 * int(info.iters[0])
-    roll = onewton.rollout(odyn.Brusselator(p["params"], p["dt"]), p["s0"], 4097)[0]
+    roll = onewton.rollout(odyn.Brusselator(p["params"], p["dt"]), p["s0"], 8193)[0]
     assert bool(info.converged.all()) and _relerr(s.cpu().numpy(), roll) <= 1e-10
 
 
