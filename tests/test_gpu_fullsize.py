@@ -34,7 +34,7 @@ def _per_seq_err(got, ref, off):
 
 def test_massaction_d8_B4096_T16384_fp32_every_trajectory():
     """The headline workload as bench.py runs it (B=4096 networks, d=8, 12 reactions, RK4
-    dt=1e-3, T=16384, full-Jacobian Newton in FP32 with the compensated state, zero guess,
+    dt=1e-3, T=16384, full-Jacobian Newton in FP32 with the compensated state, guess s_0,
     scaled residual 5e-8 on two consecutive iterates, sliding window): all 4096 converged
     trajectories equal the FP64 rollout within 1e-5. (With a plain float32 state the
     float32 rounding of the near-equilibrium increments leaves 37 % of them above 1e-5, as
@@ -47,7 +47,7 @@ def test_massaction_d8_B4096_T16384_fp32_every_trajectory():
     dyn = deer.Dynamics.massaction(_t(p["topology"], torch.int32),
                                    _t(p["params"], torch.float32), d, p["dt"])
     s, info = deer.deer_solve(dyn, _t(p["s0"], torch.float32), T, jac="full", tol=5e-8,
-                              confirm=2, prec="fp32", init="zeros", reset=True, window=True)
+                              confirm=2, prec="fp32", init="s0", reset=True, window=True)
     assert bool(info.converged.all())
     off = cma.uniform_offsets(B, T)
     ref = cma.Batch(p["topology"], p["params"], p["dt"], "rk4", d=d).rollout(p["s0"], off)
