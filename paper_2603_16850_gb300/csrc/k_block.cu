@@ -110,12 +110,18 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t r0 = a.offsets[seq];
   const int64_t T = a.offsets[seq + 1] - r0;
-  // rows per thread (<= RPT: the host sizes the cluster), contiguous over the cluster's
-  // threads in rank order
-  const int64_t nthr = (int64_t)CL * NT;
-  const int rpt = (int)((T + nthr - 1) / nthr);
-  const int64_t k0 = ((int64_t)rank * NT + tid) * rpt;
-  const int nmine = T - k0 <= 0 ? 0 : (T - k0 < rpt ? (int)(T - k0) : rpt);
+  // rows spread evenly over the cluster's blocks (rpc each, in rank order), then over a
+  // block's threads (rpt each, <= RPT: the host sizes the cluster); the threads with rows
+  // are a prefix of each block, and whole warps without rows skip the float64 scans
+  const int64_t rpc = (T + CL - 1) / CL;
+  const int rpt = (int)((rpc + NT - 1) / NT);
+  const int64_t cbeg = (int64_t)rank * rpc;
+  const int64_t cend = cbeg + rpc < T ? cbeg + rpc : T;
+  const int64_t k0 = cbeg + (int64_t)tid * rpt;
+  const int nmine = cend - k0 <= 0 ? 0 : (cend - k0 < rpt ? (int)(cend - k0) : rpt);
+  const bool warp_rows = cbeg + (int64_t)(warp * 32) * rpt < cend;  // uniform over the warp
+  // the previous block (full whenever this one has rows) ends with thread (rpc - 1) / rpt
+  const int prev_last = (int)((rpc - 1) / rpt);
   const real scale = a.damp == DEER_DAMP_SCALE ? real(1) - a.dparam : real(1);
   real s[RPT][D];
   real s0[D];
@@ -145,7 +151,7 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
 #pragma unroll
       for (int i = 0; i < D; ++i) prev[i] = s_last[tid - 1][i];
     } else if (rank > 0) {
-      const real* pl = cl.map_shared_rank(&s_last[NT - 1][0], rank - 1);
+      const real* pl = cl.map_shared_rank(&s_last[prev_last][0], rank - 1);
 #pragma unroll
       for (int i = 0; i < D; ++i) prev[i] = pl[i];
     } else {
@@ -189,7 +195,7 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
     }
     // 2. reduction over the cluster and the convergence test (every block reduces the
     //    blocks' partials in the same order, so all take the same decision)
-    {
+    if (warp_rows) {
       double m = (double)mx;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -200,6 +206,9 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
         s_mx[warp] = (real)m;
         s_sq[warp] = sq;
       }
+    } else if (lane == 0) {
+      s_mx[warp] = real(0);
+      s_sq[warp] = 0.0;
     }
     __syncthreads();
     if (tid == 0) {
@@ -244,7 +253,7 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
     iters = it < a.max_iters ? it + 1 : it;
     if ((nonfinite && !a.reset) || it >= a.max_iters) break;
     // 3. scan of the elements: lanes, warps, then the blocks of the cluster
-    const Aff<real, D> inc = warp_scan_aff<real, D>(e, lane);
+    const Aff<real, D> inc = warp_rows ? warp_scan_aff<real, D>(e, lane) : e;  // e = I
     if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
     if (warp == 0) {
@@ -265,8 +274,8 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
       }
     }
     __syncthreads();
-    real din[D];
-    {
+    real din[D] = {};
+    if (warp_rows) {
       // then the warps before in this block, then the lanes before in this warp
       real db[D], dw[D];
 #pragma unroll
@@ -363,9 +372,10 @@ int64_t block_solve_max_T(int kind, int d) {
 template <class real, int D, int KIND>
 static cudaError_t block_launch(const BlockSolveArgs<real>& a, cudaStream_t st) {
   auto kern = k_block_solve<real, D, KIND, kBlockThreads, BlockRows<D>::n>;
-  // cluster size: one row per thread where the longest sequence allows it, up to 16
-  // blocks (more SMs' float64 units per sequence) when the GPU can schedule that, else 8
-  int64_t cl = (a.max_T + kBlockThreads - 1) / kBlockThreads;
+  // cluster size: 64 rows per block where the longest sequence allows it (the float64
+  // pipe is the SM's, shared by its warps), up to 16 blocks when the GPU can schedule
+  // that, else 8
+  int64_t cl = (a.max_T + kBlockThreads / 2 - 1) / (kBlockThreads / 2);
   cl = cl < 1 ? 1 : (cl > kWideCluster ? kWideCluster : cl);
   if (cl > kMaxCluster) {
     static thread_local int wide_ok = -1;  // per host thread: 1 if the attribute took
