@@ -202,15 +202,22 @@ def _opt_defaults(opts):
     return base
 
 
-def _run_solve(dyn, B, T, offsets, s0, x, s_init, opts, stream, workspace, device):
+def _run_solve(dyn, B, T, offsets, s0, x, s_init, opts, stream, workspace, device,
+               explicit=()):
     lib = N.load()
-    if int(opts.get("chunk", 0)) == 0:
-        # the autotuner's cached chunk length for this GPU and configuration, if any
-        from . import autotune
-        Tmax = T if offsets is None else max(
-            (int(offsets[i + 1]) - int(offsets[i]) for i in range(B)), default=0)
-        opts = dict(opts, chunk=autotune.cached_chunk(
-            dyn, Tmax, opts["jac"], opts["prec"], gpu=torch.cuda.get_device_name(device)))
+    # the autotuner's cached configuration for this GPU and problem class, if any: its
+    # chunk length where the caller left chunk = 0, its loop forms where the caller did not
+    # choose them (``explicit``: the option names the caller passed)
+    from . import autotune
+    Tmax = T if offsets is None else max(
+        (int(offsets[i + 1]) - int(offsets[i]) for i in range(B)), default=0)
+    tuned = autotune.cached_options(dyn, Tmax, opts["jac"], opts["prec"],
+                                    gpu=torch.cuda.get_device_name(device))
+    if tuned:
+        upd = {k: v for k, v in tuned.items()
+               if (k == "chunk" and int(opts.get("chunk", 0)) == 0)
+               or (k != "chunk" and k not in explicit)}
+        opts = dict(opts, **upd)
     o = _options(**opts)
     dt = _dtype(opts["prec"])
     N_rows = int(offsets[-1]) if offsets is not None else B * T
@@ -271,6 +278,7 @@ def deer_solve(dyn: Dynamics, s0: torch.Tensor, T: int, x: Optional[torch.Tensor
     Host inputs are copied to the GPU and the result back to the host, into ``out`` when
     given (a preallocated, ideally pinned, host tensor [B*T][d]).
     """
+    explicit = frozenset(opts)
     opts = _opt_defaults(opts)
     host = not s0.is_cuda
     device = torch.device("cuda") if host else s0.device
@@ -278,13 +286,14 @@ def deer_solve(dyn: Dynamics, s0: torch.Tensor, T: int, x: Optional[torch.Tensor
         _check_out(out, (s0.shape[0] * int(T), dyn.d), _dtype(opts["prec"]))
         dyn, s0, x = _to_device(dyn, s0, x, device)
     s, info = _run_solve(dyn, s0.shape[0], int(T), None, s0, x, s_init, opts, stream,
-                         workspace, device)
+                         workspace, device, explicit)
     return (_to_host(s, out) if host else s), info
 
 
 def deer_solve_batched(dyn: Dynamics, s0: torch.Tensor, offsets, x: Optional[torch.Tensor] = None,
                        *, s_init=None, stream=None, workspace=None, out=None, **opts):
     """Ragged batch: sequence b owns rows offsets[b]..offsets[b+1]-1 of the packed output."""
+    explicit = frozenset(opts)
     opts = _opt_defaults(opts)
     offsets = [int(v) for v in (offsets.tolist() if hasattr(offsets, "tolist") else offsets)]
     host = not s0.is_cuda
@@ -293,7 +302,7 @@ def deer_solve_batched(dyn: Dynamics, s0: torch.Tensor, offsets, x: Optional[tor
         _check_out(out, (int(offsets[-1]), dyn.d), _dtype(opts["prec"]))
         dyn, s0, x = _to_device(dyn, s0, x, device)
     s, info = _run_solve(dyn, s0.shape[0], 0, offsets, s0, x, s_init, opts, stream, workspace,
-                         device)
+                         device, explicit)
     return (_to_host(s, out) if host else s), info
 
 

@@ -1,5 +1,6 @@
-"""Chunk-length autotuner: host logic on the CPU (key, cache round trip, selection with
-failing candidates), and one GPU tuning run whose choice is then read back from the cache."""
+"""Launch-configuration autotuner: host logic on the CPU (key, cache round trip, selection
+with failing candidates, which cached options the default path takes), and GPU tuning runs
+whose choices are then read back from the cache and served to the default path."""
 import math
 
 import numpy as np
@@ -86,3 +87,56 @@ def test_cached_choice_serves_the_default_path(tmp_path, monkeypatch):
              {"chunk": 64, "ms": 0.5}, path)
     os.utime(path, (time.time() + 5, time.time() + 5))
     assert at.cached_chunk(Dyn, 10000, "full", "fp32", gpu="GB300") == 64
+
+
+def test_pick_best_config_and_cached_options(tmp_path):
+    """Option dicts are timed in order, failures skipped; a cached configuration yields its
+    chunk length and loop forms, an entry with chunk only yields the chunk."""
+    times = [3.0, 1.0, float("inf")]
+    cands = [dict(chunk=32), dict(chunk=32, device_loop=True), dict(chunk=64)]
+    res = at.pick_best_config(cands, lambda c: times[cands.index(c)])
+    assert res["chunk"] == 32 and res["device_loop"] is True and res["ms"] == 1.0
+    assert [t["ms"] for t in res["timings"]][:2] == [3.0, 1.0]
+    with pytest.raises(RuntimeError):
+        at.pick_best_config(cands[:1], lambda c: float("inf"))
+    path = str(tmp_path / "t.json")
+
+    class Dyn:
+        kind, d = "brusselator_euler", 2
+
+    at.store(at.make_key("G", Dyn.kind, 2, "full", "fp64", 1024),
+             {"chunk": 16, "device_loop": True, "block_solve": False, "ms": 1.0}, path)
+    at.store(at.make_key("G", Dyn.kind, 2, "full", "fp64", 64), {"chunk": 8, "ms": 1.0}, path)
+    assert at.cached_options(Dyn, 1000, "full", "fp64", path=path, gpu="G") == \
+        {"chunk": 16, "device_loop": True, "block_solve": False}
+    assert at.cached_options(Dyn, 50, "full", "fp64", path=path, gpu="G") == {"chunk": 8}
+    assert at.cached_options(Dyn, 5000, "full", "fp64", path=path, gpu="G") == {}
+
+
+@pytest.mark.gpu
+def test_tune_configuration_serves_the_default_path(tmp_path, monkeypatch):
+    """tune() on the Brusselator (T = 1024, FP64) caches a configuration; the default path
+    then solves with it (the explicit choice of the caller still wins), and the result is
+    the rollout either way."""
+    import torch
+
+    import paper_2603_16850_gb300 as deer
+    import synth
+    from oracle import dynamics as odyn
+    from oracle import newton as onewton
+    path = str(tmp_path / "tune.json")
+    monkeypatch.setenv("DEER_AUTOTUNE_CACHE", path)
+    p = synth.brusselator(T=1024)
+    dyn = deer.Dynamics.brusselator(torch.tensor(p["params"], device="cuda"), p["dt"])
+    s0 = torch.tensor(p["s0"], device="cuda")
+    opts = dict(jac="full", prec="fp64", tol=1e-12, reset=True)
+    res = at.tune(dyn, s0, 1024, candidates=(16, 64), **opts)
+    assert res["chunk"] in (16, 64) and len(res["timings"]) == 4
+    assert at.cached_options(dyn, 1024, "full", "fp64") == \
+        {k: res[k] for k in ("chunk", "device_loop", "block_solve")}
+    ref = onewton.rollout(odyn.Brusselator(p["params"], p["dt"]), p["s0"], 1024)[0]
+    for extra in ({}, {"block_solve": False, "device_loop": True}):
+        s, info = deer.deer_solve(dyn, s0, 1024, **opts, **extra)
+        assert bool(info.converged.all())
+        err = np.max(np.abs(s.cpu().numpy() - ref)) / np.max(np.abs(ref))
+        assert err <= 1e-10
