@@ -376,8 +376,18 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   if (offsets_h[0] != 0) return DEER_ERR_INVALID;
   int64_t* d_off = reinterpret_cast<int64_t*>(ws + ly.offsets);
   int64_t* d_cf = reinterpret_cast<int64_t*>(ws + ly.chunk_first);
-  DEER_CK(cudaMemcpyAsync(d_off, offsets_h, (B + 1) * 8, cudaMemcpyHostToDevice, st));
-  DEER_CK(cudaMemcpyAsync(d_cf, chunk_first.data(), (B + 1) * 8, cudaMemcpyHostToDevice, st));
+  // sequences of one length (deer_solve): the tables are written on the device, which
+  // spares two copies from pageable host memory per call (they dominate small solves)
+  bool uniform = B > 0;
+  const int64_t T0 = B > 0 ? offsets_h[1] : 0;
+  for (int64_t b = 1; b <= B && uniform; ++b) uniform = offsets_h[b] == b * T0;
+  if (uniform) {
+    DEER_CK(launch_uniform_tables(d_off, d_cf, B, T0, (T0 + ly.L - 1) / ly.L, st));
+  } else {
+    DEER_CK(cudaMemcpyAsync(d_off, offsets_h, (B + 1) * 8, cudaMemcpyHostToDevice, st));
+    DEER_CK(cudaMemcpyAsync(d_cf, chunk_first.data(), (B + 1) * 8, cudaMemcpyHostToDevice,
+                            st));
+  }
   SeqAcc* acc = reinterpret_cast<SeqAcc*>(ws + ly.acc);
   SeqInfo* info = reinterpret_cast<SeqInfo*>(ws + ly.info);
   Flags* flags = reinterpret_cast<Flags*>(ws + ly.flags);
@@ -405,7 +415,9 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   const bool window = o->window && o->damp == DEER_DAMP_NONE;
   if (window) {
     // sliding window: every sequence starts solved from its first chunk
-    DEER_CK(cudaMemcpyAsync(d_win, chunk_first.data(), (B + 1) * 8, cudaMemcpyHostToDevice, st));
+    DEER_CK(uniform ? cudaMemcpyAsync(d_win, d_cf, (B + 1) * 8, cudaMemcpyDeviceToDevice, st)
+                    : cudaMemcpyAsync(d_win, chunk_first.data(), (B + 1) * 8,
+                                      cudaMemcpyHostToDevice, st));
     bt.win_chunk = d_win;
   }
   // the convergence test in the kernels' precision: the largest value of that type not

@@ -13,12 +13,14 @@
 //      r_t = s_t - F_t and composes its rows' affine steps Delta -> A_t Delta - r_t into
 //      one element (P, v);
 //   2. a reduction over the cluster gives the largest scaled residual max |r| / max(1, |s|)
-//      and sum r^2; the test and the iteration count follow the library's convergence
-//      check, taken identically by every block;
-//   3. an exclusive scan of the elements (warp shuffles, the warp totals, then the blocks'
-//      totals read across the cluster) gives the correction Delta entering each thread's
-//      rows, which the thread propagates through its rows with the A_t and F_t it kept,
-//      adding it to the iterate with the reset heuristic.
+//      and sum r^2, and, behind the same cluster barrier, an exclusive scan of the
+//      elements (warp shuffles, the warp totals, then the blocks' totals read across the
+//      cluster) gives the correction Delta entering each thread's rows;
+//   3. the test and the iteration count follow the library's convergence check, taken
+//      identically by every block; unless it stops, each thread propagates Delta through
+//      its rows with the A_t and F_t it kept, adding it to the iterate with the reset
+//      heuristic.
+// Two cluster barriers per iteration: the boundary rows, then statistics and scan totals.
 #include <cooperative_groups.h>
 
 #include <cfloat>
@@ -27,6 +29,9 @@
 #include "kernels.h"
 
 namespace deer {
+
+template <class real>
+constexpr real kRealMax = sizeof(real) == 8 ? real(DBL_MAX) : real(FLT_MAX);
 
 template <class real, int D>
 struct Aff {  // the affine map Delta -> P Delta + v
@@ -162,7 +167,11 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
     //    apply pass
     Aff<real, D> e = aff_identity<real, D>();
     real Fk[RPT][D], Ak[RPT][D][D];
-    real mx = real(0);
+    // largest scaled residual |r| / max(1, |s|) kept as a fraction (fn / fd, compared by
+    // cross-multiplication), so that one division per warp replaces one per entry (the
+    // float64 divide is a long sequence on this GPU); non-finite entries raise fnan
+    real fn = real(0), fd = real(1);
+    bool fnan = false;
     double sq = 0.0;
     {
       real sp[D];
@@ -178,8 +187,13 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
             const real r = s[k][i] - Fk[k][i];
             st.v[i] = -r;
             const real sabs = rabs(s[k][i]);
-            const real sr = rabs(r) / (sabs > real(1) ? sabs : real(1));
-            mx = (sr > mx || sr != sr) ? sr : mx;
+            const real num = rabs(r), den = sabs > real(1) ? sabs : real(1);
+            if (!(num <= kRealMax<real>) || !(den <= kRealMax<real>)) {
+              fnan = true;
+            } else if (num * fd > fn * den) {
+              fn = num;
+              fd = den;
+            }
             sq += (double)r * (double)r;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
@@ -193,33 +207,49 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
         }
       }
     }
-    // 2. reduction over the cluster and the convergence test (every block reduces the
-    //    blocks' partials in the same order, so all take the same decision)
+    // 2. statistics and scan totals: per warp, per block, then across the cluster with one
+    //    barrier. Every block reduces the blocks' partials in the same order, so all take
+    //    the same decision; the scan is formed before the test and unused if it stops.
     if (warp_rows) {
-      double m = (double)mx;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        m = nanmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const real on = __shfl_xor_sync(0xffffffffu, fn, o);
+        const real od = __shfl_xor_sync(0xffffffffu, fd, o);
+        fnan |= __shfl_xor_sync(0xffffffffu, (int)fnan, o) != 0;
+        if (on * fd > fn * od) {
+          fn = on;
+          fd = od;
+        }
         sq += __shfl_xor_sync(0xffffffffu, sq, o);
       }
       if (lane == 0) {
-        s_mx[warp] = (real)m;
+        s_mx[warp] = fnan ? real(NAN) : fn / fd;
         s_sq[warp] = sq;
       }
     } else if (lane == 0) {
       s_mx[warp] = real(0);
       s_sq[warp] = 0.0;
     }
+    // 3. scan of the elements: lanes, warps, then the blocks of the cluster
+    const Aff<real, D> inc = warp_rows ? warp_scan_aff<real, D>(e, lane) : e;  // e = I
+    if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
-    if (tid == 0) {
-      double bm = 0.0, bs = 0.0;
+    if (warp == 0) {
+      Aff<real, D> wt = lane < NW ? s_warp[lane] : aff_identity<real, D>();
+      wt = warp_scan_aff<real, D>(wt, lane, NW);
+      if (lane < NW) s_warp[lane] = wt;
+      if (lane == NW - 1) s_tot = wt;
+      double bm = lane < NW ? (double)s_mx[lane] : 0.0;
+      double bs = lane < NW ? s_sq[lane] : 0.0;
 #pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        bm = nanmax(bm, (double)s_mx[w]);
-        bs += s_sq[w];
+      for (int o = 16; o > 0; o >>= 1) {
+        bm = nanmax(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+        bs += __shfl_xor_sync(0xffffffffu, bs, o);
       }
-      s_part[0] = bm;
-      s_part[1] = bs;
+      if (lane == 0) {
+        s_part[0] = bm;
+        s_part[1] = bs;
+      }
     }
     cl.sync();
     if (warp == 0) {
@@ -238,6 +268,14 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
         s_stat[0] = bm;
         s_stat[1] = bs;
       }
+      // the blocks before this one, composed in order: Delta entering this block
+      Aff<real, D> bt = lane < CL ? *cl.map_shared_rank(&s_tot, lane) : aff_identity<real, D>();
+      bt = warp_scan_aff<real, D>(bt, lane, CL);
+      const Aff<real, D> ex = shfl_up_aff<real, D>(bt, 1);
+      if (lane == rank) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) s_din[i] = rank > 0 ? ex.v[i] : real(0);
+      }
     }
     __syncthreads();
     const double bm = s_stat[0], bs = s_stat[1];
@@ -252,28 +290,6 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
     }
     iters = it < a.max_iters ? it + 1 : it;
     if ((nonfinite && !a.reset) || it >= a.max_iters) break;
-    // 3. scan of the elements: lanes, warps, then the blocks of the cluster
-    const Aff<real, D> inc = warp_rows ? warp_scan_aff<real, D>(e, lane) : e;  // e = I
-    if (lane == 31) s_warp[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-      Aff<real, D> wt = lane < NW ? s_warp[lane] : aff_identity<real, D>();
-      wt = warp_scan_aff<real, D>(wt, lane, NW);
-      if (lane < NW) s_warp[lane] = wt;
-      if (lane == NW - 1) s_tot = wt;
-    }
-    cl.sync();
-    if (warp == 0) {
-      // the blocks before this one, composed in order: Delta entering this block
-      Aff<real, D> bt = lane < CL ? *cl.map_shared_rank(&s_tot, lane) : aff_identity<real, D>();
-      bt = warp_scan_aff<real, D>(bt, lane, CL);
-      const Aff<real, D> ex = shfl_up_aff<real, D>(bt, 1);
-      if (lane == rank) {
-#pragma unroll
-        for (int i = 0; i < D; ++i) s_din[i] = rank > 0 ? ex.v[i] : real(0);
-      }
-    }
-    __syncthreads();
     real din[D] = {};
     if (warp_rows) {
       // then the warps before in this block, then the lanes before in this warp

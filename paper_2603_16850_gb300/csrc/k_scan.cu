@@ -187,6 +187,24 @@ __global__ void __launch_bounds__(1024) k_check(CheckArgs a) {
   }
 }
 
+__global__ void k_uniform_tables(int64_t* off, int64_t* cf, int64_t B, int64_t T,
+                                 int64_t cps) {
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b <= B;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    off[b] = b * T;
+    cf[b] = b * cps;
+  }
+}
+
+cudaError_t launch_uniform_tables(int64_t* offsets, int64_t* chunk_first, int64_t B,
+                                  int64_t T, int64_t chunks_per_seq, cudaStream_t st) {
+  const int64_t n = B + 1;
+  const unsigned g = (unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+  k_uniform_tables<<<g, 256, 0, st>>>(offsets, chunk_first, B, T, chunks_per_seq);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check(const CheckArgs& a, cudaStream_t st) {
   k_check<<<1, 1024, 0, st>>>(a);
   note_launch();

@@ -105,6 +105,10 @@ int64_t block_solve_max_T(int kind, int d);
 template <class real>
 cudaError_t launch_block_solve(const BlockSolveArgs<real>& a, cudaStream_t st);
 
+// offsets[b] = b T and chunk_first[b] = b ceil(T / L) for b = 0..B (B + 1 entries each)
+cudaError_t launch_uniform_tables(int64_t* offsets, int64_t* chunk_first, int64_t B,
+                                  int64_t T, int64_t chunks_per_seq, cudaStream_t st);
+
 // first node of the device-resident loop's graph: sets the while condition from the flags
 // of the check that ran before the graph
 cudaError_t launch_loop_gate(Flags* flags, int max_iters, int reset,
