@@ -222,7 +222,9 @@ static bool make_layout(const deer_dynamics* f, int64_t B, int64_t N, const deer
     }
   }
   ly.adj_off = ly.adj_e = p;
-  if (mixed) {
+  const bool ma_kind = f->kind == DEER_F_MASSACTION_EULER || f->kind == DEER_F_MASSACTION_RK4;
+  if (mixed || (ma_kind && (d == 16 || d == 32))) {
+    // per-species reaction lists (the mixed path's and the wide linearisation's)
     const int64_t nseq = f->topology_stride ? (B > 0 ? B : 1) : 1;
     ly.adj_off = take((size_t)nseq * (d + 1) * 4);
     ly.adj_e = take((size_t)nseq * 4 * f->n_reactions * 4);
@@ -483,6 +485,17 @@ static deer_status solve_impl(const deer_dynamics* f, int64_t B, const int64_t* 
   la.damp = o->damp;
   la.dparam = (real)o->damp_param;
   la.tol = tol_r;
+  if (!(o->prec == DEER_MIXED_BF16) && ly.adj_off != ly.adj_e) {
+    // mass action, d = 16 / 32: each lane of the wide linearisation walks its species'
+    // reactions
+    const int64_t nseq = f->topology_stride ? B : 1;
+    DEER_CK(launch_ma_adjacency(nseq, d, f->n_reactions, f->topology, f->topology_stride,
+                                reinterpret_cast<int32_t*>(ws + ly.adj_off),
+                                reinterpret_cast<int32_t*>(ws + ly.adj_e), st));
+    la.adj_off = reinterpret_cast<const int32_t*>(ws + ly.adj_off);
+    la.adj_e = reinterpret_cast<const int32_t*>(ws + ly.adj_e);
+    la.adj_stride = f->topology_stride ? 4 * (int64_t)f->n_reactions : 0;
+  }
   real* slo = ly.cs ? reinterpret_cast<real*>(ws + ly.slo) : nullptr;
   if (slo) {
     // the compensation terms start at zero (the initial guess is a plain float32 state)

@@ -534,8 +534,14 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
   // banks)
   constexpr int RSK = D + 16 / (int)sizeof(real);
   __shared__ __align__(16) real sK[GROUPS][D * RSK + 16 / sizeof(real)];
+  // per reaction of the group's row: rate constant, first reactant concentration and the
+  // second factor (the second reactant's concentration, or 1): written by lane r mod d,
+  // read by the lanes of the species the reaction changes
+  constexpr int RMAX = 4 * D;
+  __shared__ real sKr[GROUPS][RMAX], sC1[GROUPS][RMAX], sF2[GROUPS][RMAX];
   const int grp = threadIdx.x / D, lane = threadIdx.x % D;
   const unsigned gmask = D == 32 ? 0xffffffffu : (0xffffu << (16 * ((threadIdx.x >> 4) & 1)));
+  const bool use_adj = a.adj_off != nullptr && a.dv.R <= RMAX;
   // each group walks kMaRows consecutive active rows and flushes the residual statistics
   // once per sequence it meets (not once per row): fewer atomics on the accumulator of a
   // long sequence
@@ -577,17 +583,50 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
       }
       __syncwarp(gmask);
       g = real(0);
-      for (int r = 0; r < R; ++r) {
-        const int4 q = __ldg(tt + r);
-        const real kr = __ldg(kk + r);
-        const real c1 = __shfl_sync(gmask, c, q.x, D);
-        const real c2 = __shfl_sync(gmask, c, q.y < 0 ? 0 : q.y, D);
-        const real f2 = q.y < 0 ? real(1) : c2;
-        const real nu = real((lane == q.z) + (lane == q.w) - (lane == q.x) - (lane == q.y));
-        g += nu * (kr * c1 * f2);
-        if (WANTA && nu != real(0)) {
-          sG[grp][lane][q.x] += nu * kr * f2;                  // d rate / d c_i1
-          if (q.y >= 0) sG[grp][lane][q.y] += nu * kr * c1;    // d rate / d c_i2
+      if (use_adj) {
+        // each reaction's factors once (reaction r on lane r mod d), then each lane walks
+        // the reactions that change its species, in reaction order (the same products and
+        // sums as the walk over every reaction below)
+        for (int k0 = 0; k0 < R; k0 += D) {  // uniform over the group
+          const int r = k0 + lane;
+          const int4 q = r < R ? __ldg(tt + r) : make_int4(0, -1, 0, 0);
+          const real c1 = __shfl_sync(gmask, c, q.x, D);
+          const real c2 = __shfl_sync(gmask, c, q.y < 0 ? 0 : q.y, D);
+          if (r < R) {
+            sKr[grp][r] = __ldg(kk + r);
+            sC1[grp][r] = c1;
+            sF2[grp][r] = q.y < 0 ? real(1) : c2;
+          }
+        }
+        __syncwarp(gmask);
+        const int32_t* aoff = a.adj_off + (a.adj_stride ? seq : 0) * (D + 1);
+        const int32_t* ae = a.adj_e + (a.adj_stride ? seq : 0) * a.adj_stride;
+        const int e1 = __ldg(aoff + lane + 1);
+        for (int e = __ldg(aoff + lane); e < e1; ++e) {
+          const int code = __ldg(ae + e);
+          const int r = code & 0xffff;
+          const real nu = real((code >> 16) - 4);
+          const real kr = sKr[grp][r], c1 = sC1[grp][r], f2 = sF2[grp][r];
+          g += nu * (kr * c1 * f2);
+          if (WANTA) {
+            const int4 q = __ldg(tt + r);
+            sG[grp][lane][q.x] += nu * kr * f2;                  // d rate / d c_i1
+            if (q.y >= 0) sG[grp][lane][q.y] += nu * kr * c1;    // d rate / d c_i2
+          }
+        }
+      } else {
+        for (int r = 0; r < R; ++r) {
+          const int4 q = __ldg(tt + r);
+          const real kr = __ldg(kk + r);
+          const real c1 = __shfl_sync(gmask, c, q.x, D);
+          const real c2 = __shfl_sync(gmask, c, q.y < 0 ? 0 : q.y, D);
+          const real f2 = q.y < 0 ? real(1) : c2;
+          const real nu = real((lane == q.z) + (lane == q.w) - (lane == q.x) - (lane == q.y));
+          g += nu * (kr * c1 * f2);
+          if (WANTA && nu != real(0)) {
+            sG[grp][lane][q.x] += nu * kr * f2;                  // d rate / d c_i1
+            if (q.y >= 0) sG[grp][lane][q.y] += nu * kr * c1;    // d rate / d c_i2
+          }
         }
       }
       if (WANTA) {

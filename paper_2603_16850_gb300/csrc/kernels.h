@@ -32,6 +32,12 @@ struct LinArgs {
                        // above it are reported (first failing row, for the sliding window)
   const real* slo = nullptr;  // compensation of s ([N][d], the state is s + slo); nullptr =
                               // plain state (mass-action kinetics only)
+  // mass action, d = 16 / 32: per-species lists of the reactions that change the species
+  // (launch_ma_adjacency; entry = r | (nu + 4) << 16), so that each lane walks its own
+  // reactions rather than all of them; nullptr = walk every reaction
+  const int32_t* adj_off = nullptr;  // [nseq][d+1]
+  const int32_t* adj_e = nullptr;    // [nseq][adj_stride]
+  int64_t adj_stride = 0;            // 0: one list shared by every sequence
 };
 
 template <class real>
