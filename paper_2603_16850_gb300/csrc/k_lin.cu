@@ -3,6 +3,7 @@
 #include <cstdio>
 
 #include "lin_generic.cuh"
+#include "tc.cuh"
 
 namespace deer {
 
@@ -528,7 +529,12 @@ template <class real, int D, bool RK4, int JAC>
 __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
   constexpr int GROUPS = 128 / D;          // rows per block
   constexpr bool WANTA = JAC == DEER_JAC_FULL || JAC == DEER_JAC_DIAG;
-  __shared__ real sG[GROUPS][D][D + 1];
+  // d = 32 float32: the stage-Jacobian products G_j K_{j-1} run on the tensor cores as
+  // warp-level tf32 MMAs with the three-term split (float32 accuracy); the rate-Jacobian
+  // rows are then padded to 36 floats (conflict-free fragment and 16-byte row reads)
+  constexpr bool TCW = D == 32 && sizeof(real) == 4;
+  constexpr int GS = TCW ? D + 4 : D + 1;
+  __shared__ __align__(16) real sG[GROUPS][D][GS];
   // rows padded by 16 bytes (the d lanes' 16-byte row writes fall in distinct banks) and
   // the group stride by another 16 (the groups of a warp read their K rows from different
   // banks)
@@ -578,8 +584,14 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
       const real cK = stage == 0 ? real(0) : (stage == 3 ? h : real(0.5) * h);
       const real w = (stage == 1 || stage == 2) ? real(2) : real(1);
       if (WANTA) {
+        if constexpr (TCW) {
 #pragma unroll
-        for (int j = 0; j < D; ++j) sG[grp][lane][j] = real(0);
+          for (int j = 0; j < D; j += 4)
+            *reinterpret_cast<float4*>(&sG[grp][lane][j]) = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+#pragma unroll
+          for (int j = 0; j < D; ++j) sG[grp][lane][j] = real(0);
+        }
       }
       __syncwarp(gmask);
       g = real(0);
@@ -632,11 +644,83 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
       if (WANTA) {
         __syncwarp(gmask);
         real Gi[D], Kn[D];
+        if constexpr (TCW) {
 #pragma unroll
-        for (int j = 0; j < D; ++j) Gi[j] = sG[grp][lane][j];
+          for (int j = 0; j < D; j += 4) {
+            const float4 q = *reinterpret_cast<const float4*>(&sG[grp][lane][j]);
+            Gi[j] = q.x; Gi[j + 1] = q.y; Gi[j + 2] = q.z; Gi[j + 3] = q.w;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < D; ++j) Gi[j] = sG[grp][lane][j];
+        }
 #pragma unroll
         for (int j = 0; j < D; ++j) Kn[j] = Gi[j];
-        if (stage > 0) {
+        if constexpr (TCW) {
+          if (stage > 0) {
+            // P = G_j K_{j-1} (32 x 32 x 32): 2 x 4 output tiles, 4 k-steps, three MMAs
+            // each (lo*hi, hi*lo, hi*hi); A from the rate-Jacobian rows, B from the
+            // previous stage's rows
+            const int g = lane >> 2, tq = lane & 3;
+            float P[2][4][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+              for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) P[mt][nt][e] = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              uint32_t ah[2][4], al[2][4];
+#pragma unroll
+              for (int mt = 0; mt < 2; ++mt) {
+                const float* r0 = &sG[grp][16 * mt + g][8 * kk];
+                const float* r1 = &sG[grp][16 * mt + g + 8][8 * kk];
+                const float av[4] = {r0[tq], r1[tq], r0[tq + 4], r1[tq + 4]};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  ah[mt][e] = tc::tf32_rna(av[e]);
+                  al[mt][e] = tc::tf32_rna(av[e] - __uint_as_float(ah[mt][e]));
+                }
+              }
+#pragma unroll
+              for (int nt = 0; nt < 4; ++nt) {
+                const float bx0 = sK[grp][(8 * kk + tq) * RSK + 8 * nt + g];
+                const float bx1 = sK[grp][(8 * kk + tq + 4) * RSK + 8 * nt + g];
+                const uint32_t bh0 = tc::tf32_rna(bx0), bh1 = tc::tf32_rna(bx1);
+                const uint32_t bl0 = tc::tf32_rna(bx0 - __uint_as_float(bh0));
+                const uint32_t bl1 = tc::tf32_rna(bx1 - __uint_as_float(bh1));
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                  tc::mma_1688_tf32(P[mt][nt], al[mt], bh0, bh1);
+                  tc::mma_1688_tf32(P[mt][nt], ah[mt], bl0, bl1);
+                  tc::mma_1688_tf32(P[mt][nt], ah[mt], bh0, bh1);
+                }
+              }
+            }
+            // the previous stage's rows are no longer needed: P goes there, then each lane
+            // takes its row, K_j = G_j + cK P
+            __syncwarp(gmask);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+              for (int nt = 0; nt < 4; ++nt) {
+                float* q0 = &sK[grp][(16 * mt + g) * RSK + 8 * nt + 2 * tq];
+                float* q1 = &sK[grp][(16 * mt + g + 8) * RSK + 8 * nt + 2 * tq];
+                *reinterpret_cast<float2*>(q0) = make_float2(P[mt][nt][0], P[mt][nt][1]);
+                *reinterpret_cast<float2*>(q1) = make_float2(P[mt][nt][2], P[mt][nt][3]);
+              }
+            __syncwarp(gmask);
+#pragma unroll
+            for (int j = 0; j < D; j += 4) {
+              const float4 q = *reinterpret_cast<const float4*>(&sK[grp][lane * RSK + j]);
+              Kn[j] = Gi[j] + cK * q.x;
+              Kn[j + 1] = Gi[j + 1] + cK * q.y;
+              Kn[j + 2] = Gi[j + 2] + cK * q.z;
+              Kn[j + 3] = Gi[j + 3] + cK * q.w;
+            }
+          }
+        } else if (stage > 0) {
           // row m of the previous stage Jacobian (the same for every lane of the group) in
           // 16-byte pieces, folded in with the packed FMA row update
           constexpr int VW = 16 / (int)sizeof(real);
