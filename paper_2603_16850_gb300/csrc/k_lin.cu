@@ -526,7 +526,8 @@ constexpr int kMaRows = 4;  // consecutive rows per lane group in k_lin_ma_wide
 // K_j = G_j (I + c_j K_{j-1}) reads the previous K rows from shared memory as broadcasts.
 // ----------------------------------------------------------------------------
 template <class real, int D, bool RK4, int JAC>
-__global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
+__global__ void __launch_bounds__(128, (D == 32 && sizeof(real) == 4) ? 4 : 1)
+    k_lin_ma_wide(LinArgs<real> a) {
   constexpr int GROUPS = 128 / D;          // rows per block
   constexpr bool WANTA = JAC == DEER_JAC_FULL || JAC == DEER_JAC_DIAG;
   // d = 32 float32: the stage-Jacobian products G_j K_{j-1} run on the tensor cores as
@@ -645,17 +646,21 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
         __syncwarp(gmask);
         real Gi[D], Kn[D];
         if constexpr (TCW) {
+          // (the rate-Jacobian row is read after the product, so that it is not held in
+          // registers across the MMAs)
+          if (stage == 0) {
 #pragma unroll
-          for (int j = 0; j < D; j += 4) {
-            const float4 q = *reinterpret_cast<const float4*>(&sG[grp][lane][j]);
-            Gi[j] = q.x; Gi[j + 1] = q.y; Gi[j + 2] = q.z; Gi[j + 3] = q.w;
+            for (int j = 0; j < D; j += 4) {
+              const float4 q = *reinterpret_cast<const float4*>(&sG[grp][lane][j]);
+              Kn[j] = q.x; Kn[j + 1] = q.y; Kn[j + 2] = q.z; Kn[j + 3] = q.w;
+            }
           }
         } else {
 #pragma unroll
           for (int j = 0; j < D; ++j) Gi[j] = sG[grp][lane][j];
-        }
 #pragma unroll
-        for (int j = 0; j < D; ++j) Kn[j] = Gi[j];
+          for (int j = 0; j < D; ++j) Kn[j] = Gi[j];
+        }
         if constexpr (TCW) {
           if (stage > 0) {
             // P = G_j K_{j-1} (32 x 32 x 32): 2 x 4 output tiles, 4 k-steps, three MMAs
@@ -714,10 +719,11 @@ __global__ void __launch_bounds__(128) k_lin_ma_wide(LinArgs<real> a) {
 #pragma unroll
             for (int j = 0; j < D; j += 4) {
               const float4 q = *reinterpret_cast<const float4*>(&sK[grp][lane * RSK + j]);
-              Kn[j] = Gi[j] + cK * q.x;
-              Kn[j + 1] = Gi[j + 1] + cK * q.y;
-              Kn[j + 2] = Gi[j + 2] + cK * q.z;
-              Kn[j + 3] = Gi[j + 3] + cK * q.w;
+              const float4 gq = *reinterpret_cast<const float4*>(&sG[grp][lane][j]);
+              Kn[j] = gq.x + cK * q.x;
+              Kn[j + 1] = gq.y + cK * q.y;
+              Kn[j + 2] = gq.z + cK * q.z;
+              Kn[j + 3] = gq.w + cK * q.w;
             }
           }
         } else if (stage > 0) {
