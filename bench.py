@@ -454,7 +454,7 @@ def lle_measurement(deer, dyn, s0, s, T, d, stream, n_sys=64):
             "max": float(v.max()), "ms": e0.elapsed_time(e1)}
 
 
-def adjoint_measurement(deer, N, lib, dev, stream, checks=None):
+def adjoint_measurement(deer, N, lib, dev, stream, checks=None, B=256):
     """Differentiation workload: d=32 kinetic networks (48 reactions), B=256, T=32768, RK4
     dt=1e-3, FP32. Forward full-Jacobian solve, then the adjoint gradient of
     sum_t ||s_t - y_t||^2 w.r.t. the rate constants (targets y: the sequential rollout with
@@ -463,7 +463,7 @@ def adjoint_measurement(deer, N, lib, dev, stream, checks=None):
     import numpy as np
     import torch
     import synth
-    B, d, R, T = 256, 32, 48, 32768
+    d, R, T = 32, 48, 32768
     p = synth.massaction(B, d, R, T, seed=3)
     topo = torch.tensor(p["topology"], dtype=torch.int32, device=dev)
     k = torch.tensor(p["params"], dtype=torch.float32, device=dev)
@@ -506,7 +506,7 @@ def adjoint_measurement(deer, N, lib, dev, stream, checks=None):
     e1.record(stream)
     torch.cuda.synchronize()
     roll_ms = e0.elapsed_time(e1)
-    out = {"workload": "mass action d=32 R=48 B=256 T=32768 RK4, FP32 (compensated state, "
+    out = {"workload": f"mass action d=32 R=48 B={B} T=32768 RK4, FP32 (compensated state, "
                        "tol 5e-8 x2), adjoint wrt rates",
            "sequential_gpu_rollout": {"ms": roll_ms, "value": B * T / (roll_ms / 1000.0),
                                       "unit": UNIT},
@@ -942,7 +942,7 @@ def run_only(args):
         gains = tuple(float(v) for v in args.gains.split(",")) if args.gains else (0.5, 1.0, 2.0)
         out = threshold_measurement(deer, N, lib, dev, stream, gains=gains)
     else:
-        out = adjoint_measurement(deer, N, lib, dev, stream)
+        out = adjoint_measurement(deer, N, lib, dev, stream, B=args.batch or 256)
     print(json.dumps({"only": args.only, **out}), flush=True)
     return 0
 
