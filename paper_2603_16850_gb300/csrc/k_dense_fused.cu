@@ -323,6 +323,9 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
   // DRAM latency overlaps the previous row's work; each lane reads back only its own slot
   constexpr int PF = D + 4;
   __shared__ __align__(16) real sPF[2][kFusedBlock][PF];
+  // the group's stage states (all species), exchanged through shared memory: written with
+  // the stage Jacobian's rows, read back as two 16-byte pieces (instead of d shuffles)
+  __shared__ __align__(16) real sC[GPB][D];
   const int grp = threadIdx.x / D, i = threadIdx.x % D;
   const unsigned gm = ((1u << D) - 1u) << ((threadIdx.x & 31) & ~(D - 1));
   const int64_t ac = blockIdx.x * (int64_t)GPB + grp;
@@ -345,6 +348,7 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
     const real hw = RK4 ? h / real(6) : h;
     real* Kx = sK[grp];
     real* Px = sP[grp];
+    real* Cx = sC[grp];
     const real* T = a.dv.ma + seq * a.dv.ma_stride;
     real Lrow[D];
     ldrow_ro<real, D>(T + i * D, Lrow);
@@ -369,6 +373,7 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
     real v = real(0);
 #pragma unroll
     for (int j = 0; j < D; ++j) Px[i * RS + j] = i == j ? real(1) : real(0);
+    Cx[i] = prev;  // the first row's first-stage states
     __syncwarp(gm);
     auto prefetch = [&](int slot, int t) {
       if (t < n) {
@@ -421,7 +426,7 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
         a.s[row * D + i] = sn;
       }
       // linearise at the new state of the previous row
-      real st = prev, accg = real(0);
+      real accg = real(0);
       real Kacc[D], Kown[D];
 #pragma unroll
       for (int j = 0; j < D; ++j) Kacc[j] = real(0);
@@ -432,11 +437,9 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
         const real cK = stage == 0 ? real(0) : (stage == 3 ? h : real(0.5) * h);
         const real w = (stage == 1 || stage == 2) ? real(2) : real(1);
         real cj[D], Gr[D];
+        ldrow_p<real, D>(Cx, cj);  // this stage's states of every species
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
-          cj[j] = __shfl_sync(gm, st, j, D);
-          Gr[j] = Lrow[j];
-        }
+        for (int j = 0; j < D; ++j) Gr[j] = Lrow[j];
 #pragma unroll
         for (int m = 0; m < D; ++m) {
           if constexpr (BREG) {
@@ -462,13 +465,16 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
             axpy_row<D>(cK * Gr[m], km, Kown);
           }
         }
+        // the next stage's state of this species (after the last stage: the row's new
+        // state, the next row's first-stage state)
+        const real cs = stage == 2 ? h : real(0.5) * h;
+        const real st_next = stage == NST - 1 ? sn : prev + cs * g;
         __syncwarp(gm);
         strow_p<real, D>(Kx + i * RS, Kown);
+        Cx[i] = st_next;
         __syncwarp(gm);
         axpy_row<D>(w, Kown, Kacc);
         accg += w * g;
-        const real cs = stage == 2 ? h : real(0.5) * h;
-        st = prev + cs * g;
       }
       real r;
       if constexpr (CS) {
