@@ -534,6 +534,10 @@ __global__ void __launch_bounds__(128, (D == 32 && sizeof(real) == 4) ? 4 : 1)
   // warp-level tf32 MMAs with the three-term split (float32 accuracy); the rate-Jacobian
   // rows are then padded to 36 floats (conflict-free fragment and 16-byte row reads)
   constexpr bool TCW = D == 32 && sizeof(real) == 4;
+  // full Jacobian on that path: the stage Jacobians stay in the MMA accumulator layout
+  // from stage to stage (written to shared memory only as the next product's operand), and
+  // A_t leaves through a shared-memory tile in 16-byte pieces
+  constexpr bool FRAG = TCW && JAC == DEER_JAC_FULL;
   constexpr int GS = TCW ? D + 4 : D + 1;
   __shared__ __align__(16) real sG[GROUPS][D][GS];
   // rows padded by 16 bytes (the d lanes' 16-byte row writes fall in distinct banks) and
@@ -577,6 +581,15 @@ __global__ void __launch_bounds__(128, (D == 32 && sizeof(real) == 4) ? 4 : 1)
     const int R = a.dv.R;
     const real h = a.dv.dt;
     real c = s_prev, acc = real(0), g = real(0);
+    float KaccF[2][4][4];  // FRAG: sum of w K_j, accumulator layout
+    if constexpr (FRAG) {
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) KaccF[mt][nt][e] = 0.f;
+    }
     real Kacc[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) Kacc[j] = real(0);
@@ -642,7 +655,77 @@ __global__ void __launch_bounds__(128, (D == 32 && sizeof(real) == 4) ? 4 : 1)
           }
         }
       }
-      if (WANTA) {
+      if constexpr (FRAG) {
+        __syncwarp(gmask);
+        const int g8 = lane >> 2, tq = lane & 3;
+        float Kf[2][4][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) Kf[mt][nt][e] = 0.f;
+        if (stage > 0) {
+          // P = G_j K_{j-1} (32 x 32 x 32) on the tensor cores, three-term tf32 split
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            uint32_t ah[2][4], al[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+              const float* r0 = &sG[grp][16 * mt + g8][8 * kk];
+              const float* r1 = &sG[grp][16 * mt + g8 + 8][8 * kk];
+              const float av[4] = {r0[tq], r1[tq], r0[tq + 4], r1[tq + 4]};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                ah[mt][e] = tc::tf32_rna(av[e]);
+                al[mt][e] = tc::tf32_rna(av[e] - __uint_as_float(ah[mt][e]));
+              }
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+              const float bx0 = sK[grp][(8 * kk + tq) * RSK + 8 * nt + g8];
+              const float bx1 = sK[grp][(8 * kk + tq + 4) * RSK + 8 * nt + g8];
+              const uint32_t bh0 = tc::tf32_rna(bx0), bh1 = tc::tf32_rna(bx1);
+              const uint32_t bl0 = tc::tf32_rna(bx0 - __uint_as_float(bh0));
+              const uint32_t bl1 = tc::tf32_rna(bx1 - __uint_as_float(bh1));
+#pragma unroll
+              for (int mt = 0; mt < 2; ++mt) {
+                tc::mma_1688_tf32(Kf[mt][nt], al[mt], bh0, bh1);
+                tc::mma_1688_tf32(Kf[mt][nt], ah[mt], bl0, bl1);
+                tc::mma_1688_tf32(Kf[mt][nt], ah[mt], bh0, bh1);
+              }
+            }
+          }
+        }
+        // K_j = G_j + cK P in the accumulator layout (rows 16 mt + g, + 8; columns
+        // 8 nt + 2 t, + 1)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            const float2 g0 =
+                *reinterpret_cast<const float2*>(&sG[grp][16 * mt + g8][8 * nt + 2 * tq]);
+            const float2 g1 =
+                *reinterpret_cast<const float2*>(&sG[grp][16 * mt + g8 + 8][8 * nt + 2 * tq]);
+            Kf[mt][nt][0] = g0.x + cK * Kf[mt][nt][0];
+            Kf[mt][nt][1] = g0.y + cK * Kf[mt][nt][1];
+            Kf[mt][nt][2] = g1.x + cK * Kf[mt][nt][2];
+            Kf[mt][nt][3] = g1.y + cK * Kf[mt][nt][3];
+          }
+        __syncwarp(gmask);  // every read of K_{j-1} done
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            *reinterpret_cast<float2*>(&sK[grp][(16 * mt + g8) * RSK + 8 * nt + 2 * tq]) =
+                make_float2(Kf[mt][nt][0], Kf[mt][nt][1]);
+            *reinterpret_cast<float2*>(&sK[grp][(16 * mt + g8 + 8) * RSK + 8 * nt + 2 * tq]) =
+                make_float2(Kf[mt][nt][2], Kf[mt][nt][3]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) KaccF[mt][nt][e] += (float)w * Kf[mt][nt][e];
+          }
+        __syncwarp(gmask);
+      } else if (WANTA) {
         __syncwarp(gmask);
         real Gi[D], Kn[D];
         if constexpr (TCW) {
@@ -785,12 +868,42 @@ __global__ void __launch_bounds__(128, (D == 32 && sizeof(real) == 4) ? 4 : 1)
       const real k = a.dparam;
       if constexpr (JAC == DEER_JAC_FULL) {
         const real scale = a.damp == DEER_DAMP_SCALE ? real(1) - k : real(1);
-        real An[D];
-#pragma unroll
-        for (int j = 0; j < D; ++j) An[j] = scale * (hw * Kacc[j] + (j == lane ? real(1) : real(0)));
         // the rate-Jacobian buffer is free after the last stage
         __syncwarp(gmask);
-        store_block_rows<real, D>(&sG[grp][0][0], a.A + row * (int64_t)(D * D), An, lane, gmask);
+        if constexpr (FRAG) {
+          // A = s (I + hw Kacc) from the accumulator layout into the tile, then out in
+          // 16-byte pieces (row p / 8, columns 4 (p % 8) .. + 3 of piece p)
+          const int g8 = lane >> 2, tq = lane & 3;
+          float* tile = &sG[grp][0][0];
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+              const int r0 = 16 * mt + g8, c0 = 8 * nt + 2 * tq;
+              const float sc = (float)scale, hf = (float)hw;
+              *reinterpret_cast<float2*>(tile + r0 * GS + c0) =
+                  make_float2(sc * (hf * KaccF[mt][nt][0] + (r0 == c0 ? 1.f : 0.f)),
+                              sc * (hf * KaccF[mt][nt][1] + (r0 == c0 + 1 ? 1.f : 0.f)));
+              *reinterpret_cast<float2*>(tile + (r0 + 8) * GS + c0) =
+                  make_float2(sc * (hf * KaccF[mt][nt][2] + (r0 + 8 == c0 ? 1.f : 0.f)),
+                              sc * (hf * KaccF[mt][nt][3] + (r0 + 8 == c0 + 1 ? 1.f : 0.f)));
+            }
+          __syncwarp(gmask);
+          float4* dst = reinterpret_cast<float4*>(a.A + row * (int64_t)(D * D));
+#pragma unroll
+          for (int q = 0; q < D * D / 4 / 32; ++q) {
+            const int pc = q * 32 + lane;
+            dst[pc] = *reinterpret_cast<const float4*>(tile + (pc >> 3) * GS + (pc & 7) * 4);
+          }
+          __syncwarp(gmask);
+        } else {
+          real An[D];
+#pragma unroll
+          for (int j = 0; j < D; ++j)
+            An[j] = scale * (hw * Kacc[j] + (j == lane ? real(1) : real(0)));
+          store_block_rows<real, D>(&sG[grp][0][0], a.A + row * (int64_t)(D * D), An, lane,
+                                    gmask);
+        }
         a.b[row * D + lane] = -rr;
       } else {
         real ai;
