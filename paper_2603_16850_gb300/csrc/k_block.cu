@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
   const int nmine = cend - k0 <= 0 ? 0 : (cend - k0 < rpt ? (int)(cend - k0) : rpt);
   const bool warp_rows = cbeg + (int64_t)(warp * 32) * rpt < cend;  // uniform over the warp
   // the previous block (full whenever this one has rows) ends with thread (rpc - 1) / rpt
-  const int prev_last = (int)((rpc - 1) / rpt);
+  // (an empty sequence has rpt = 0 and no thread with rows: nothing is read)
+  const int prev_last = rpt > 0 ? (int)((rpc - 1) / rpt) : 0;
   const real scale = a.damp == DEER_DAMP_SCALE ? real(1) - a.dparam : real(1);
   real s[RPT][D];
   real s0[D];
@@ -152,7 +153,10 @@ __global__ void __launch_bounds__(NT) k_block_solve(BlockSolveArgs<real> a) {
       }
     cl.sync();
     real prev[D];
-    if (tid > 0) {
+    if (nmine == 0) {
+#pragma unroll
+      for (int i = 0; i < D; ++i) prev[i] = real(0);  // unused: no rows
+    } else if (tid > 0) {
 #pragma unroll
       for (int i = 0; i < D; ++i) prev[i] = s_last[tid - 1][i];
     } else if (rank > 0) {

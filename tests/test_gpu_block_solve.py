@@ -43,7 +43,7 @@ def _problem(name, dt=torch.float64):
                 deer.Dynamics.brusselator(_t(p["params"], dt), p["dt"]), None)
     if name in ("ma4_rk4", "ma2_euler"):
         d, R, integ = (4, 6, "rk4") if name == "ma4_rk4" else (2, 3, "euler")
-        lengths = [1024, 1, 2, 300, 77, 1000] if d == 4 else [4096, 5, 2048, 33]
+        lengths = [1024, 1, 0, 2, 300, 77, 1000] if d == 4 else [4096, 5, 2048, 33]
         p = synth.massaction(len(lengths), d, R, 1, seed=21 + d, dt=0.01, integrator=integ)
 
         def od(b):
@@ -83,6 +83,8 @@ def test_fp64_solve_reaches_rollout(name, block):
                                            block_solve=block)
     assert bool(info.converged.all()), info
     for b, n in enumerate(lengths):
+        if n == 0:  # an empty sequence (converged at once, nothing to compare)
+            continue
         roll = onewton.rollout(od(b), s0[b:b + 1], n)[0]
         assert _relerr(s[off[b]:off[b + 1]], roll) <= 1e-10, (b, n)
 
@@ -97,6 +99,8 @@ def test_two_iterations_equal_the_oracle(name):
         # (sequences of one or two steps are exact after one or two iterations)
         assert info.status == 1 and max(info.iters.tolist()) == 2
         for b, n in enumerate(lengths):
+            if n == 0:
+                continue
             ref = onewton.initial_guess(od(b), s0[b:b + 1], n, "s0")
             for _ in range(2):
                 ref = onewton.quasi_newton_step(od(b), s0[b:b + 1], ref, "full")
