@@ -440,14 +440,52 @@ __global__ void __launch_bounds__(kFusedBlock, 4) k_fused_ma_lps(FusedArgs<real>
         ldrow_p<real, D>(Cx, cj);  // this stage's states of every species
 #pragma unroll
         for (int j = 0; j < D; ++j) Gr[j] = Lrow[j];
+        if constexpr (BREG && D % 2 == 0) {
+          // G row i = L_i + H c with H[m][j] = B_m[i][j] symmetric in (m, j) (second
+          // derivatives of the rates): only H's 2 x 2 blocks on and above the diagonal are
+          // read, so the compiler keeps 40 of its 64 entries in registers. A block below the
+          // diagonal enters as the dot product of c's pair with a row of its mirror block,
+          // accumulated in pairs and folded in at the end; the two-wide FMA count is the
+          // dense one.
+          float2 Tl[D / 2][2];
 #pragma unroll
-        for (int m = 0; m < D; ++m) {
-          if constexpr (BREG) {
-            axpy_row<D>(cj[m], Breg[m], Gr);
-          } else {
-            real bm[D];
-            ldrow_ro<real, D>(Brow + m * E, bm);
-            axpy_row<D>(cj[m], bm, Gr);
+          for (int q = 0; q < D / 2; ++q) Tl[q][0] = Tl[q][1] = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int p = 0; p < D / 2; ++p) {
+            const float2 c2 = make_float2(cj[2 * p], cj[2 * p + 1]);
+#pragma unroll
+            for (int q = p; q < D / 2; ++q) {
+              float2 y = make_float2(Gr[2 * q], Gr[2 * q + 1]);
+              y = __ffma2_rn(make_float2(cj[2 * p], cj[2 * p]),
+                             make_float2(Breg[2 * p][2 * q], Breg[2 * p][2 * q + 1]), y);
+              y = __ffma2_rn(make_float2(cj[2 * p + 1], cj[2 * p + 1]),
+                             make_float2(Breg[2 * p + 1][2 * q], Breg[2 * p + 1][2 * q + 1]), y);
+              Gr[2 * q] = y.x;
+              Gr[2 * q + 1] = y.y;
+            }
+#pragma unroll
+            for (int q = 0; q < p; ++q) {
+              Tl[q][0] = __ffma2_rn(c2, make_float2(Breg[2 * q][2 * p], Breg[2 * q][2 * p + 1]),
+                                    Tl[q][0]);
+              Tl[q][1] = __ffma2_rn(
+                  c2, make_float2(Breg[2 * q + 1][2 * p], Breg[2 * q + 1][2 * p + 1]), Tl[q][1]);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < D / 2 - 1; ++q) {
+            Gr[2 * q] += Tl[q][0].x + Tl[q][0].y;
+            Gr[2 * q + 1] += Tl[q][1].x + Tl[q][1].y;
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < D; ++m) {
+            if constexpr (BREG) {
+              axpy_row<D>(cj[m], Breg[m], Gr);
+            } else {
+              real bm[D];
+              ldrow_ro<real, D>(Brow + m * E, bm);
+              axpy_row<D>(cj[m], bm, Gr);
+            }
           }
         }
         real g = real(0);
