@@ -54,10 +54,10 @@ ALGO_BYTES_PER_ROW = 3 * 8 * 4
 IMPL_BYTES_PER_ROW = 2 * (8 * 8 + 8) * 4 + 2 * 2 * 8 * 4
 # DRAM bytes per row of the fused iteration kernel from the committed ncu capture of the
 # same kernel (dram__bytes_read.sum + dram__bytes_write.sum per row at B=512, two launches:
-# 4.441 GB / 6.29 M rows and 2.516 GB / 3.60 M rows; the traffic per row does not depend on
+# 4.407 GB / 6.29 M rows and 2.517 GB / 3.62 M rows; the traffic per row does not depend on
 # B), scaled by the rows of an average launch; None while the kernel has changed since its
 # capture.
-FUSED_TRAFFIC_PER_ROW = (4.440608e9 + 2.516490e9) / (6285312 + 3596288)
+FUSED_TRAFFIC_PER_ROW = (4.407065e9 + 2.516884e9) / (6285312 + 3622912)
 # Mixed-precision d=16 mass-action linearise, per row: the RK4 step Jacobian chain in
 # float32 (3 products of 16x16 matrices, 3 * 2 d^3 flop); the float64 rate evaluations are
 # not counted.
