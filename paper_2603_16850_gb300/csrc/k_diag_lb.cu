@@ -194,7 +194,7 @@ __device__ __forceinline__ void block_scan_and_lookback(const DiagLBArgs<real>& 
         const unsigned haspre = __ballot_sync(0xffffffffu, ok && (f & 3u) == 2u);
         const int run = ready == 0xffffffffu ? 32 : __ffs(~ready) - 1;  // ready from lane 0
         const int kp = haspre ? __ffs(haspre) - 1 : 32;                   // nearest prefix
-        const int nfold = kp < run ? kp : run;  // aggregates to fold this round
+        const int nfold = kp < run ? kp : run;  // aggregates to fold in this pass of the look-back
         if (nfold == 0 && kp != 0) {
           if (++spins > kSpinLimit) { timed_out = true; break; }
           __nanosleep(64);
