@@ -159,3 +159,28 @@ def test_iteration_cap_and_status():
                                            init="s0", reset=True)
     assert info.status == 1 and not bool(info.converged.any())
     assert info.iters.tolist() == [3]
+
+
+@pytest.mark.parametrize("k", [0.3, 0.7])
+def test_scale_damping_iterates_equal_the_oracle(k):
+    """Scale damping (A_t scaled by 1 - k) inside the whole-solve kernel: two iterations equal
+    the oracle's damped forward-substitution steps, and the damped iteration still reaches
+    the rollout."""
+    s, info, lengths, off, s0, od = _solve("ma4_rk4", jac="full", damp="scale", damp_param=k,
+                                           tol=0.0, max_iters=2, init="s0")
+    for b, n in enumerate(lengths):
+        if n == 0:
+            continue
+        ref = onewton.initial_guess(od(b), s0[b:b + 1], n, "s0")
+        for _ in range(2):
+            ref = onewton.quasi_newton_step(od(b), s0[b:b + 1], ref, "full", damp="scale",
+                                            damp_param=k)
+        assert _relerr(s[off[b]:off[b + 1]], ref[0]) <= 1e-11, b
+    s, info, lengths, off, s0, od = _solve("ma4_rk4", jac="full", damp="scale", damp_param=k,
+                                           tol=1e-12, init="s0", max_iters=4000)
+    assert bool(info.converged.all()), info.iters.max()
+    for b, n in enumerate(lengths):
+        if n == 0:
+            continue
+        roll = onewton.rollout(od(b), s0[b:b + 1], n)[0]
+        assert _relerr(s[off[b]:off[b + 1]], roll) <= 1e-10, b

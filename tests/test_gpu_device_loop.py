@@ -61,6 +61,14 @@ def _case(name):
         s0 = torch.zeros((4, 64), dtype=torch.float32, device=DEV)
         return (lambda **e: deer.deer_solve(dyn, s0, 4096, x, jac="diag", tol=1e-5, confirm=2,
                                             prec="fp32", init="zeros", **e)), True
+    if name == "gru_diag_lookback_window_fp32":
+        # the look-back scan with the sliding window (sequence-major tile order)
+        g = synth.gru(3, 3000, 16, 16, seed=5, dtype=np.float32)
+        dyn = deer.Dynamics.gru(_t(g["W"], torch.float32), _t(g["U"], torch.float32))
+        x = _t(g["x"].reshape(-1, 16), torch.float32)
+        s0 = torch.zeros((3, 16), dtype=torch.float32, device=DEV)
+        return (lambda **e: deer.deer_solve(dyn, s0, 3000, x, jac="diag", tol=1e-5, confirm=2,
+                                            prec="fp32", init="zeros", window=True, **e)), True
     if name == "gru_quasi_elk_fp64":
         g = synth.gru(3, 700, 8, 8, seed=4)
         dyn = deer.Dynamics.gru(_t(g["W"]), _t(g["U"]))
@@ -116,6 +124,7 @@ def _case(name):
 
 
 CASES = ["fused_fp32_window", "brusselator_fp64", "gru_diag_lookback_fp32",
+         "gru_diag_lookback_window_fp32",
          "gru_quasi_elk_fp64", "mixed_stored", "mixed_recompute",
          "dense_elk_parallel_covariance", "rnn_d32_wide", "ragged_fp64_d4",
          "word_problem_one_iteration"]
