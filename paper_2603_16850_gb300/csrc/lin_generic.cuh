@@ -180,9 +180,56 @@ constexpr bool kind_has_d(int kind, int d, bool full) {
 
 #define DEER_GENERIC_D(X) X(1) X(2) X(4) X(5) X(8) X(16) X(32) X(64)
 
+// Jacobi guess of an autonomous recurrence (mass action: f_t does not depend on t or on
+// inputs): f(0) once per sequence into its first row, then copied along the sequence,
+// instead of evaluating the same step at zero on every row
+template <class real, int D, int KIND>
+__global__ void __launch_bounds__(128) k_init_jacobi_first(InitArgs<real> a) {
+  const int64_t seq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (seq >= a.bt.B) return;
+  const int64_t r0 = a.bt.offsets[seq];
+  if (a.bt.offsets[seq + 1] == r0) return;  // empty sequence
+  real z[D], v[D];
+#pragma unroll Unroll<D>::n
+  for (int i = 0; i < D; ++i) z[i] = real(0);
+  eval_f<real, D, KIND, 0>(a.dv, seq, r0, z, v, nullptr, nullptr);
+  store_row<real, D>(a.s + r0 * D, v);
+}
+
+template <class real, int D>
+__global__ void __launch_bounds__(128) k_init_copy_first(InitArgs<real> a) {
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= a.bt.N) return;
+  const int64_t r0 = a.bt.offsets[find_seq(a.bt.offsets, a.bt.B, row)];
+  if (row == r0) return;
+  real v[D];
+#pragma unroll Unroll<D>::n
+  for (int i = 0; i < D; ++i) v[i] = a.s[r0 * D + i];
+  store_row<real, D>(a.s + row * D, v);
+}
+
 template <class real, int KIND>
 cudaError_t generic_init(const InitArgs<real>& a, cudaStream_t st) {
   const unsigned g = grid_for(a.bt.N, 128);
+  constexpr bool autonomous = KIND == DEER_F_MASSACTION_EULER || KIND == DEER_F_MASSACTION_RK4;
+  if (autonomous && a.init == DEER_INIT_JACOBI) {
+    switch (a.dv.d) {
+#define CASE(DD)                                                                   \
+  case DD:                                                                         \
+    if constexpr (kind_has_d(KIND, DD, false)) {                                   \
+      k_init_jacobi_first<real, DD, KIND><<<grid_for(a.bt.B, 128), 128, 0, st>>>(a); \
+      k_init_copy_first<real, DD><<<g, 128, 0, st>>>(a);                           \
+      break;                                                                       \
+    }                                                                              \
+    return cudaErrorInvalidValue;
+      DEER_GENERIC_D(CASE)
+#undef CASE
+      default:
+        return cudaErrorInvalidValue;
+    }
+    note_launch(2);
+    return cudaGetLastError();
+  }
   switch (a.dv.d) {
 #define CASE(DD)                                                              \
   case DD:                                                                    \
