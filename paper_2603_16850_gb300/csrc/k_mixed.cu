@@ -3,6 +3,7 @@
 // against, and the state, stay in float64; the Jacobian only steers the correction, so it
 // is formed in float32 and stored (minus the identity) in bfloat16, halving its traffic.
 #include "kernels.h"
+#include "tc.cuh"
 
 namespace deer {
 
@@ -554,22 +555,6 @@ __device__ __forceinline__ void rc_row(const MixedLinArgs& a, bool fast, bool va
         nullptr, S.b[half], S.E[half]);
 }
 
-__device__ __forceinline__ uint32_t rc_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ void rc_mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1,
-                                            uint32_t a2, uint32_t a3, uint32_t b0,
-                                            uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 // P^T <- P^T + P^T E^T for the warp's 16 x 16 accumulator acc[n-tile][4] (lane (g, t):
 // rows g, g + 8, columns 8 j + 2 t, + 1), three-term tf32 split
 __device__ __forceinline__ void rc_compose(float (&acc)[2][4], const float* E, int g, int t,
@@ -590,8 +575,8 @@ __device__ __forceinline__ void rc_compose(float (&acc)[2][4], const float* E, i
     const float av[4] = {odd ? x1 : x0, odd ? x3 : x2, odd ? y1 : y0, odd ? y3 : y2};
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      ah[kk][e] = rc_tf32(av[e]);
-      al[kk][e] = rc_tf32(av[e] - __uint_as_float(ah[kk][e]));
+      ah[kk][e] = tc::tf32_rna(av[e]);
+      al[kk][e] = tc::tf32_rna(av[e] - __uint_as_float(ah[kk][e]));
     }
   }
 #pragma unroll
@@ -601,12 +586,12 @@ __device__ __forceinline__ void rc_compose(float (&acc)[2][4], const float* E, i
       // B[k][n] = E^T[k][n] = E[n][k]: n = 8 j + g, k = 8 kk + t (+ 4)
       const float bx0 = E[(8 * j + g) * kRcES + 8 * kk + t];
       const float bx1 = E[(8 * j + g) * kRcES + 8 * kk + t + 4];
-      const uint32_t bh0 = rc_tf32(bx0), bh1 = rc_tf32(bx1);
-      const uint32_t bl0 = rc_tf32(bx0 - __uint_as_float(bh0));
-      const uint32_t bl1 = rc_tf32(bx1 - __uint_as_float(bh1));
-      rc_mma_tf32(acc[j], al[kk][0], al[kk][1], al[kk][2], al[kk][3], bh0, bh1);
-      rc_mma_tf32(acc[j], ah[kk][0], ah[kk][1], ah[kk][2], ah[kk][3], bl0, bl1);
-      rc_mma_tf32(acc[j], ah[kk][0], ah[kk][1], ah[kk][2], ah[kk][3], bh0, bh1);
+      const uint32_t bh0 = tc::tf32_rna(bx0), bh1 = tc::tf32_rna(bx1);
+      const uint32_t bl0 = tc::tf32_rna(bx0 - __uint_as_float(bh0));
+      const uint32_t bl1 = tc::tf32_rna(bx1 - __uint_as_float(bh1));
+      tc::mma_1688_tf32(acc[j], al[kk], bh0, bh1);
+      tc::mma_1688_tf32(acc[j], ah[kk], bl0, bl1);
+      tc::mma_1688_tf32(acc[j], ah[kk], bh0, bh1);
     }
   }
 }

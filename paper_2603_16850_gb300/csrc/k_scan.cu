@@ -8,6 +8,7 @@
 #include <cfloat>
 
 #include "kernels.h"
+#include "tc.cuh"
 
 namespace deer {
 
@@ -995,22 +996,6 @@ __global__ void __launch_bounds__(128) k_dense_chunk_ring4(DenseScanArgs<real> a
 // the 32 lanes' words fall in distinct banks). The vector part v <- A_t v + b_t is formed
 // by lane i (row i) of warp 0. Rows are staged through the same cp.async ring as
 // k_dense_chunk_ring4.
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ void mma_tf32_1688(float (&d)[4], uint32_t a0, uint32_t a1,
-                                              uint32_t a2, uint32_t a3, uint32_t b0,
-                                              uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 __global__ void __launch_bounds__(64) k_dense_chunk_mma32(DenseScanArgs<float> a) {
   constexpr int D = 32;
   constexpr int K = ring_depth<float>();
@@ -1087,8 +1072,8 @@ __global__ void __launch_bounds__(64) k_dense_chunk_mma32(DenseScanArgs<float> a
             const float av[4] = {odd ? x1 : x0, odd ? x3 : x2, odd ? y1 : y0, odd ? y3 : y2};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              ah[kk][e] = tf32_rna(av[e]);
-              al[kk][e] = tf32_rna(av[e] - __uint_as_float(ah[kk][e]));
+              ah[kk][e] = tc::tf32_rna(av[e]);
+              al[kk][e] = tc::tf32_rna(av[e] - __uint_as_float(ah[kk][e]));
             }
           }
 #pragma unroll
@@ -1099,12 +1084,12 @@ __global__ void __launch_bounds__(64) k_dense_chunk_mma32(DenseScanArgs<float> a
               // B[k][n] = A_t[n][k]: n = 8j + g, k = 8kk + tq (+ 4)
               const float bx0 = sA[s][8 * j + g][8 * kk + tq];
               const float bx1 = sA[s][8 * j + g][8 * kk + tq + 4];
-              const uint32_t bh0 = tf32_rna(bx0), bh1 = tf32_rna(bx1);
-              const uint32_t bl0 = tf32_rna(bx0 - __uint_as_float(bh0));
-              const uint32_t bl1 = tf32_rna(bx1 - __uint_as_float(bh1));
-              mma_tf32_1688(dn, al[kk][0], al[kk][1], al[kk][2], al[kk][3], bh0, bh1);
-              mma_tf32_1688(dn, ah[kk][0], ah[kk][1], ah[kk][2], ah[kk][3], bl0, bl1);
-              mma_tf32_1688(dn, ah[kk][0], ah[kk][1], ah[kk][2], ah[kk][3], bh0, bh1);
+              const uint32_t bh0 = tc::tf32_rna(bx0), bh1 = tc::tf32_rna(bx1);
+              const uint32_t bl0 = tc::tf32_rna(bx0 - __uint_as_float(bh0));
+              const uint32_t bl1 = tc::tf32_rna(bx1 - __uint_as_float(bh1));
+              tc::mma_1688_tf32(dn, al[kk], bh0, bh1);
+              tc::mma_1688_tf32(dn, ah[kk], bl0, bl1);
+              tc::mma_1688_tf32(dn, ah[kk], bh0, bh1);
             }
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[j][e] = dn[e];
