@@ -236,3 +236,13 @@ def test_binding_enums_match_the_header():
             assert pymap[py] == vals[prefix + c], (prefix, py)
     kinds = {k for k in vals if k.startswith("DEER_F_")}
     assert len(kinds) == len(N.KIND)
+
+
+def test_binding_options_map_the_loop_forms():
+    """The Python options reach the C struct: device_loop, and block_solve inverted into
+    no_block_solve, beside the defaults of everything else."""
+    import paper_2603_16850_gb300 as deer
+    o = deer._options(**deer._opt_defaults({}))
+    assert (o.device_loop, o.no_block_solve, o.compensate) == (0, 0, 1)
+    o = deer._options(**deer._opt_defaults(dict(device_loop=True, block_solve=False)))
+    assert (o.device_loop, o.no_block_solve) == (1, 1)
