@@ -543,7 +543,9 @@ __global__ void __launch_bounds__(128, (D == 32 && sizeof(real) == 4) ? 4 : 1)
   // rows padded by 16 bytes (the d lanes' 16-byte row writes fall in distinct banks) and
   // the group stride by another 16 (the groups of a warp read their K rows from different
   // banks)
-  constexpr int RSK = D + 16 / (int)sizeof(real);
+  // (the accumulator-layout path pads its stage rows to 40 floats instead: its fragment
+  // loads and two-float stores then fall in distinct banks)
+  constexpr int RSK = FRAG ? D + 8 : D + 16 / (int)sizeof(real);
   __shared__ __align__(16) real sK[GROUPS][D * RSK + 16 / sizeof(real)];
   // per reaction of the group's row: rate constant, first reactant concentration and the
   // second factor (the second reactant's concentration, or 1): written by lane r mod d,
