@@ -66,28 +66,6 @@ __device__ __forceinline__ void st4_hint(real* p, const real (&v)[4], uint64_t p
   }
 }
 
-template <class real>
-__device__ __forceinline__ V4<real> ld4(const real* p) {
-  if constexpr (sizeof(real) == 4) {
-    float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    return {v.x, v.y, v.z, v.w};
-  } else {
-    double2 u = __ldg(reinterpret_cast<const double2*>(p));
-    double2 v = __ldg(reinterpret_cast<const double2*>(p) + 1);
-    return {u.x, u.y, v.x, v.y};
-  }
-}
-
-template <class real>
-__device__ __forceinline__ void st4(real* p, const real (&v)[4]) {
-  if constexpr (sizeof(real) == 4) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  } else {
-    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
-    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
-  }
-}
-
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
