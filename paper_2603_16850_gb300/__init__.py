@@ -183,8 +183,9 @@ def set_tensor_cores(on) -> None:
     N.load().deer_set_tensor_cores(int(on))
 
 
-def tensor_cores() -> bool:
-    return bool(N.load().deer_get_tensor_cores())
+def tensor_cores() -> int:
+    """The current selection of set_tensor_cores (deer_get_tensor_cores): 0, 1 or 2."""
+    return int(N.load().deer_get_tensor_cores())
 
 
 def deer_workspace_bytes(dyn: Dynamics, batch: int, total_steps: int, **opts) -> int:
