@@ -98,11 +98,15 @@ class OracleChecks:
 
 
 def _peaks():
+    """HBM copy bandwidth and cuBLAS bf16 rate of this GPU model, with where they came
+    from: the measured MEASURED_PEAKS.json when present, else one earlier GB300
+    measurement (6.8 TB/s copy, 1.9 PFLOP/s bf16), reported as the fallback."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
-            return json.load(f), "measured"
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+            return json.load(f), "measured (MEASURED_PEAKS.json)"
+    return ({"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0},
+            "fallback (no MEASURED_PEAKS.json: an earlier GB300 measurement)")
 
 
 class Clocks:
@@ -284,7 +288,7 @@ def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64, window=False,
     scan_rows = prof.rows[3] / max(prof.launches[3], 1)
     lin_ms = prof.ms[1] / max(prof.launches[1], 1)
     lin_rows = prof.rows[1] / max(prof.launches[1], 1)
-    peaks, _ = _peaks()
+    peaks, peak_kind = _peaks()
     gbs = scan_rows * d * 12 / (scan_ms / 1000.0) / 1e9
     lin_tf = lin_rows * 4 * 2 * d * d / (lin_ms / 1000.0) / 1e12
     if int(lib.deer_get_tensor_cores()):
@@ -304,7 +308,8 @@ def gru_diag_measurement(deer, N, lib, dev, stream, steps=3, B=64, window=False,
            "newton_iters_max": int(info.iters.max()), "converged": bool(info.converged.all()),
            "diag_scan": {"kernel": "k_diag_lb<float,64>", "bound": "hbm", "achieved": gbs,
                          "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": gbs / peaks["hbm_gbs"], "avg_launch_ms": scan_ms,
+                         "frac": gbs / peaks["hbm_gbs"], "peak_source": peak_kind,
+                         "avg_launch_ms": scan_ms,
                          "avg_rows_per_launch": scan_rows},
            "linearize": lin_entry}
     if checks is not None:
@@ -983,7 +988,8 @@ def _tf32_peak(lib, peaks):
     measured bf16 peak x the nominal tf32 / bf16 ratio (1.1 / 2.25 PFLOP/s dense)."""
     if "tf32_tc" in _ALU_PEAKS:
         return _ALU_PEAKS["tf32_tc"], _ALU_PEAKS["tf32_tc_source"]
-    return peaks["bf16_tflops"] * 1.1 / 2.25, "bf16 (MEASURED_PEAKS.json) x 1.1/2.25 nominal"
+    _, kind = _peaks()
+    return peaks["bf16_tflops"] * 1.1 / 2.25, f"bf16 {kind} x 1.1/2.25 nominal"
 
 
 def run(args):
@@ -1070,6 +1076,7 @@ def run(args):
             "peak_source": "FP32 FMA, " + alu["fp32_source"],
             "flop_per_row": ALGO_FLOP_PER_ROW, "algorithmic_bytes_per_row": ALGO_BYTES_PER_ROW,
             "hbm_frac_algorithmic": hbm_frac, "hbm_peak_gbs": peaks["hbm_gbs"],
+            "hbm_peak_source": peak_kind,
             "impl_bytes_per_row": IMPL_BYTES_PER_ROW, "impl_gbs": impl_gbs,
             "traffic_per_row": FUSED_TRAFFIC_PER_ROW,
             "traffic_ratio": (FUSED_TRAFFIC_PER_ROW / ALGO_BYTES_PER_ROW
@@ -1136,6 +1143,7 @@ def run(args):
         roof["diag_scan_kernel"] = q["diag_scan"]["kernel"]
         roof["diag_scan_gbs"] = q["diag_scan"]["achieved"]
         roof["diag_scan_frac"] = q["diag_scan"]["frac"]
+        roof["diag_scan_peak_source"] = q["diag_scan"]["peak_source"]
         if "tensor_frac" in q["linearize"]:
             roof["gru_lin_tc_tensor_frac"] = q["linearize"]["tensor_frac"]
 
