@@ -821,3 +821,66 @@ def test_filter_covariance_as_associative_elements():
             assert np.allclose(Pt, Ps[:, t], atol=1e-12)
         P_in = elk.cov_apply(agg, P_in)
         assert np.allclose(P_in, Pt, atol=1e-12)
+
+
+# --- convergence measure, reset heuristic, loss, offsets ------------------------
+def test_scaled_residual_is_absolute_below_one_relative_above():
+    """The convergence measure (the residual of Eq. r_def scaled by max(1, |s|), the
+    reading of the paper's unspecified error test) on values worked by hand: where
+    |s| <= 1 the residual counts as it is, above 1 it is divided by |s|; the maximum runs
+    over steps and coordinates, separately per sequence."""
+    r = np.zeros((2, 3, 2))
+    s = np.zeros((2, 3, 2))
+    r[0, 0, 0], s[0, 0, 0] = 0.5, 0.1      # absolute: 0.5
+    r[0, 1, 0], s[0, 1, 0] = 3.0, 10.0     # relative: 0.3
+    r[0, 2, 1], s[0, 2, 1] = -0.2, -1.0    # |s| = 1: 0.2
+    r[1, 0, 1], s[1, 0, 1] = -4.0, -2.0    # relative: 2.0
+    r[1, 2, 0], s[1, 2, 0] = 1e-3, 0.0     # absolute: 1e-3
+    got = newton.scaled_residual_max(r, s)
+    assert got.shape == (2,)
+    assert got[0] == pytest.approx(0.5, abs=0)
+    assert got[1] == pytest.approx(2.0, abs=0)
+    # large states: a residual of 1e-6 relative to a state of 1e6 is 1e-12
+    r2 = np.full((1, 4, 1), 1.0)
+    s2 = np.full((1, 4, 1), 1e12)
+    assert newton.scaled_residual_max(r2, s2)[0] == pytest.approx(1e-12, rel=1e-15)
+
+
+def test_reset_zeroes_only_non_finite_and_overflowing_entries():
+    """The reset heuristic (Sec. 3.2): entries that are NaN, infinite or above the
+    threshold in magnitude become zero; every other entry, including one just below the
+    threshold and negative ones, is left exactly as it was."""
+    s = np.array([[[1.0, np.nan, np.inf], [-2e31, 1e29, -np.inf], [-0.5, 1e30, -1e30]]])
+    got = newton.reset_overflow(s, 1e30)
+    want = np.array([[[1.0, 0.0, 0.0], [0.0, 1e29, 0.0], [-0.5, 1e30, -1e30]]])
+    assert np.array_equal(got, want)
+    assert np.isnan(s[0, 0, 1])          # the input is not modified
+
+
+def test_squared_loss_cotangent_is_its_gradient():
+    """The adjoint's test loss and its cotangent: the cotangent equals the central
+    difference of the loss in every entry (exact up to rounding: the loss is quadratic),
+    and the loss of a trajectory equal to its target is zero."""
+    rng = np.random.default_rng(3)
+    s = rng.standard_normal((2, 5, 3))
+    y = rng.standard_normal((2, 5, 3))
+    g = adjoint.sq_loss_cotangent(s, y)
+    h = 1e-3
+    for b in range(2):
+        for t in range(5):
+            for i in range(3):
+                e = np.zeros_like(s)
+                e[b, t, i] = h
+                fd = (adjoint.sq_loss(s + e, y)[b] - adjoint.sq_loss(s - e, y)[b]) / (2 * h)
+                assert fd == pytest.approx(g[b, t, i], abs=1e-9)
+    assert np.array_equal(adjoint.sq_loss(y, y), np.zeros(2))
+
+
+def test_uniform_offsets_are_the_ragged_heads_of_equal_lengths():
+    """Equal-length batches as the ragged layout: sequence b occupies rows
+    [b T, (b + 1) T) of the packed state."""
+    from oracle import cma
+    off = cma.uniform_offsets(4, 7)
+    assert off.dtype == np.int64
+    assert off.tolist() == [0, 7, 14, 21, 28]
+    assert cma.uniform_offsets(0, 7).tolist() == [0]
